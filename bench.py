@@ -1,0 +1,416 @@
+"""Benchmark: binned FFT KDE with an unconstrained bandwidth on GB300.
+
+One step = the whole hot path on one batch: linear binning of the n samples
+(kde_bin), the kernel grid and its spectrum (kde_kernel_grid, including the
+host-side factorisation of H) and the FFT evaluation (kde_fft_eval).  Inputs
+are resident in HBM when the timed region starts; L2 is flushed (a 256 MB
+write) between timed steps.  Rank 0 prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the FP64 CPU oracle, timed on host cores
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("grid points/s and samples/s of FFT KDE at <=1e-5 rel err vs FP64; % HBM roofline")
+DEFAULT_WORKLOAD = "kde2d_1024_f32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic bytes per launch of each kernel: one read of every array a pass
+# consumes and one write of every array it produces (zero padding is never
+# stored).  cs = complex bytes, r = real bytes, Q = P_last/2 + 1.
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(info, n, x_itemsize):
+    d = info.d
+    r = 4 if info.precision == "f32" else 8
+    cs = 2 * r
+    M, L, P, Q = info.M, info.L, info.P, info.Q
+    cells = int(np.prod(M))
+    b = {"kde_bin_kernel": n * d * x_itemsize + 8 * cells}
+    if d == 1:
+        b["kde_rows_r2c_kgen_kernel"] = Q * r
+        b["kde_line1d_kernel"] = 8 * cells + Q * r + cells * r
+    elif d == 2:
+        w0 = 2 * L[0] + 1
+        b["kde_rows_r2c_kgen_kernel"] = w0 * Q * cs
+        b["kde_cols_kgen_real_kernel"] = w0 * Q * cs + P[0] * Q * r
+        b["kde_rows_r2c_counts_kernel"] = 8 * cells + M[0] * Q * cs
+        b["kde_cols_mid_kernel"] = 2 * M[0] * Q * cs + P[0] * Q * r
+        b["kde_rows_c2r_kernel"] = M[0] * Q * cs + cells * r
+    else:
+        w0, w1 = 2 * L[0] + 1, 2 * L[1] + 1
+        b["kde_rows_r2c_kgen_kernel"] = w0 * w1 * Q * cs
+        b["kde_cols_kgen_kernel"] = w0 * w1 * Q * cs + w0 * P[1] * Q * cs
+        b["kde_cols_kgen_real_kernel"] = w0 * P[1] * Q * cs + P[0] * P[1] * Q * r
+        b["kde_rows_r2c_counts_kernel"] = 8 * cells + M[0] * M[1] * Q * cs
+        b["kde_cols_fwd_kernel"] = M[0] * M[1] * Q * cs + M[0] * P[1] * Q * cs
+        b["kde_cols_mid_kernel"] = 2 * M[0] * P[1] * Q * cs + P[0] * P[1] * Q * r
+        b["kde_cols_inv_kernel"] = M[0] * P[1] * Q * cs + M[0] * M[1] * Q * cs
+        b["kde_rows_c2r_kernel"] = M[0] * M[1] * Q * cs + cells * r
+    return b
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1508_02766_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as fh:
+            t = json.load(fh)
+        e = t.get(workload, {})
+        if e.get("source_digest") != source_digest():
+            return None
+        v = e.get("kernels", {}).get(kernel)
+        return None if v is None else float(v)
+    except Exception:
+        return None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        busy = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": float(np.median(busy)) if busy else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(
+                    (float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample of the workload.
+# ---------------------------------------------------------------------------
+CPU_BASELINE_CODE = r"""
+import json, os, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle import kde_oracle as O
+from paper_1508_02766_gb300 import workloads as W
+name, n_bin, n_nodes, seed = sys.argv[2], int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[5])
+nodes_file = sys.argv[6] if len(sys.argv) > 6 else ""
+w = W.WORKLOADS[name]()
+rng = np.random.default_rng(seed)
+sub = w.X[rng.choice(w.n, size=min(n_bin, w.n), replace=False)]
+t0 = time.perf_counter()
+counts_sub, _ = O.bin_linear(sub, w.lo, w.hi, w.M)
+t_bin = time.perf_counter() - t0
+counts, _ = O.bin_linear(w.X, w.lo, w.hi, w.M)
+L = O.support_L(w.H, w.lo, w.hi, w.M, w.tau)
+k = O.kernel_weights(w.H, w.lo, w.hi, w.M, L, w.n)
+nodes = np.stack([rng.integers(0, m, n_nodes) for m in w.M], axis=1)
+t0 = time.perf_counter()
+ref = O.binned_direct_at(O.counts_to_c(counts), k, L, nodes)
+t_nodes = time.perf_counter() - t0
+cells = float(np.prod(w.M))
+t_full = t_bin * (w.n / len(sub)) + t_nodes * (cells / n_nodes)
+out = {"t_bin": t_bin, "t_nodes": t_nodes, "t_full": t_full, "cells": cells, "n": w.n,
+       "n_bin": len(sub), "n_nodes": n_nodes}
+if nodes_file:
+    np.save(nodes_file + ".nodes.npy", nodes)
+    np.save(nodes_file + ".ref.npy", ref)
+print(json.dumps(out))
+"""
+
+
+def run_cpu_oracle(workload, n_bin, n_nodes, seed=0, nodes_file=""):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, "-c", CPU_BASELINE_CODE, ROOT, workload, str(n_bin), str(n_nodes),
+           str(seed)] + ([nodes_file] if nodes_file else [])
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+CPU_SAMPLE = {"kde2d_1024_f32": (1_000_000, 20_000), "kde2d_128_f64": (10_000, 4_000),
+              "kde3d_256_f32": (1_000_000, 1_000)}
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the oracle timed per step on a bounded sample.
+# ---------------------------------------------------------------------------
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_bin, n_nodes = {"kde2d_1024_f32": (100_000, 1000), "kde2d_128_f64": (10_000, 1000),
+                      "kde3d_256_f32": (100_000, 100)}[args.workload]
+    times = []
+    info = None
+    for s in range(args.warmup + args.steps):
+        r = run_cpu_oracle(args.workload, n_bin, n_nodes, seed=s)
+        if s >= args.warmup:
+            times.append(r["t_full"])
+            info = r
+    t = float(np.mean(times))
+    value = info["cells"] / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "grid points/s",
+            "samples_per_s": info["n"] / t, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"value": value, "unit": "grid points/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step: oracle binning of {n_bin} samples and Eq. 7 "
+                                       f"summed at {n_nodes} random nodes, extrapolated to the "
+                                       f"full workload"},
+            "e2e": {"value": value, "unit": "grid points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GB300 arm.
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1508_02766_gb300 import build as B
+    from paper_1508_02766_gb300 import kde
+    from paper_1508_02766_gb300 import workloads as W
+    if not os.path.exists(B.LIB):
+        B.build()
+
+    w = W.WORKLOADS[args.workload]()
+    stream = torch.cuda.Stream(device=dev)
+    plan = kde.Plan(w.M, w.lo, w.hi, w.H, precision=w.precision, tau=w.tau)
+    info = plan.info
+    X_host = torch.from_numpy(np.ascontiguousarray(w.X)).pin_memory()
+    X = X_host.to(dev)
+    counts = torch.empty(w.M, dtype=torch.int64, device=dev)
+    Ks = torch.empty(info.kspec_elems, dtype=plan.real_dtype(), device=dev)
+    dens = torch.empty(w.M, dtype=plan.real_dtype(), device=dev)
+    ws = plan.workspace(dev)
+    dens_host = torch.empty(w.M, dtype=plan.real_dtype()).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    step_dev = kde.PreparedPath(plan, X, counts, Ks, dens, ws, stream=stream)
+    Xe = torch.empty_like(X)
+    step_e2e = kde.PreparedPath(plan, Xe, counts, Ks, dens, ws, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step_dev()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    kde.profile_enable(True)
+    l0 = kde.launch_count()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            step_dev()
+            ends[i].record(stream)
+    torch.cuda.synchronize()
+    launches = kde.launch_count() - l0
+    prof = kde.profile_read()
+    kde.profile_enable(False)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    cells = int(np.prod(w.M))
+    value = world * cells / (ms_step * 1e-3)
+    samples_s = world * w.n / (ms_step * 1e-3)
+
+    # End to end through the public API with host buffers: pinned X -> device,
+    # the three calls, density -> pinned host, every step.
+    e2e_steps = max(3, min(args.steps, 50))
+    e_s = torch.cuda.Event(enable_timing=True)
+    e_e = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            Xe.copy_(X_host, non_blocking=True)
+            step_e2e()
+            dens_host.copy_(dens, non_blocking=True)
+        torch.cuda.synchronize()
+        e_s.record(stream)
+        for _ in range(e2e_steps):
+            Xe.copy_(X_host, non_blocking=True)
+            step_e2e()
+            dens_host.copy_(dens, non_blocking=True)
+        e_e.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e_s.elapsed_time(e_e) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # Roofline of the dominant kernel.
+    alg = algorithmic_bytes(info, w.n, w.X.dtype.itemsize)
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                   "share": v[0] / max(1e-12, sum(x[0] for x in prof.values()))}
+               for k, v in prof.items()}
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    peak, peak_kind = peaks()
+    ach = alg.get(dom, 0) / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": peak_kind,
+                "traffic": measured_traffic(args.workload, dom),
+                "algorithmic_bytes": alg.get(dom, 0)}
+    step_bytes = sum(alg.values())
+    path_roof = {"algorithmic_bytes_per_step": step_bytes,
+                 "achieved_GBps": step_bytes / (ms_step * 1e-3) / 1e9,
+                 "frac": step_bytes / (ms_step * 1e-3) / 1e9 / peak}
+
+    line = {"metric": METRIC, "value": value, "unit": "grid points/s", "samples_per_s": samples_s,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if info.precision == "f32" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "d": w.d, "n": w.n, "grid": list(w.M),
+                       "L": list(info.L), "P": list(info.P), "precision": info.precision,
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline, "path_roofline": path_roof, "kernels": kernels,
+            "gpu_launches": launches,
+            "e2e": {"value": world * cells / (e2e_ms * 1e-3), "unit": "grid points/s",
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(X.numel() * X.element_size()),
+                    "d2h_bytes_per_step": int(dens.numel() * dens.element_size())},
+            "clocks": clocks}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_bin, n_nodes = CPU_SAMPLE[args.workload]
+        tmp = tempfile.mktemp(prefix="kde_nodes_")
+        r = run_cpu_oracle(args.workload, n_bin, n_nodes, seed=123, nodes_file=tmp)
+        nodes = np.load(tmp + ".nodes.npy")
+        ref = np.load(tmp + ".ref.npy")
+        for suf in (".nodes.npy", ".ref.npy"):
+            os.unlink(tmp + suf)
+        with torch.cuda.stream(stream):
+            step_dev()
+        torch.cuda.synchronize()
+        got = dens.cpu().numpy()[tuple(nodes.T)]
+        line["cpu_baseline"] = {
+            "value": r["cells"] / r["t_full"], "unit": "grid points/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle binning of {r['n_bin']} samples and Eq. 7 summed at "
+                       f"{r['n_nodes']} random nodes ({r['t_bin'] + r['t_nodes']:.1f} s), "
+                       f"extrapolated to the full workload")}
+        line["accuracy"] = {"max_rel_err_vs_oracle_sampled": float(
+            np.max(np.abs(got - ref)) / np.max(np.abs(ref))), "nodes": int(len(ref))}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

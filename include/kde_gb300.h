@@ -1,0 +1,176 @@
+/*
+ * kde_gb300.h -- C ABI of the GB300 (sm_103a) binned FFT kernel density
+ * estimator with an unconstrained (full, symmetric positive definite)
+ * bandwidth matrix H, after Gramacki & Gramacki, "FFT-Based Fast Computation
+ * of Multivariate Kernel Density Estimators with Unconstrained Bandwidth
+ * Matrices" (arXiv 1508.02766).
+ *
+ * The estimate is the truncated binned estimator of Eq. 7,
+ *     f_j = sum_{|l_k| <= L_k} c_{j-l} k_l,   k_l = (1/n) K_H(delta_1 l_1, ..., delta_d l_d)
+ * (Eq. 6), computed by the discrete convolution theorem (Eq. 10) with every
+ * signed lag of the kernel kept (the corrected layout of Eq. 12-14, in its
+ * equivalent wrapped form: k_l at index l mod P_k, counts at the origin, crop
+ * [0, M_k)), and L_k from Eq. 15.
+ *
+ * Conventions shared by every call:
+ *   - d is 1, 2 or 3.  Arrays are row-major with the last axis contiguous.
+ *   - Pointers named X, counts, n_outside, Kspec, density and workspace are
+ *     CUDA device pointers owned by the caller; the library never frees or
+ *     keeps them.  lo, hi, M, H and opts are host pointers read during the
+ *     call only.
+ *   - Calls taking a stream are asynchronous on that stream (NULL = legacy
+ *     default stream).  Host-side argument checks happen before any launch
+ *     and a failed check launches nothing.
+ *   - Every call returns a kde_status; kde_last_error() gives a message for
+ *     the most recent failure on the calling thread.
+ */
+#ifndef KDE_GB300_H
+#define KDE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* kde_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  KDE_OK = 0,
+  KDE_ERR_INVALID_ARG = 1, /* bad size, pointer, dtype, non-finite value, asymmetric H */
+  KDE_ERR_NOT_SPD = 2,     /* H is not positive definite (Cholesky failed) */
+  KDE_ERR_WORKSPACE = 4,   /* workspace smaller than the plan's workspace_bytes */
+  KDE_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
+  KDE_ERR_UNSUPPORTED = 7  /* d not in 1..3, or a padded size above KDE_MAX_P */
+} kde_status;
+
+enum { KDE_F32 = 0, KDE_F64 = 1 };                   /* element types */
+enum { KDE_RANGE_CORRECTED = 0, KDE_RANGE_PER_AXIS = 1 };
+enum { KDE_LAYOUT_CORRECTED = 0, KDE_LAYOUT_WAND = 1 };
+
+#define KDE_MAX_D 3
+#define KDE_MAX_P 4096      /* largest padded length of one axis */
+#define KDE_MAX_STAGES 16
+
+/* Evaluation options.
+ *   tau         Eq. 15's support constant (the paper finds about 3.7 for the
+ *               2-D normal kernel); a value <= 0 selects 3.7.
+ *   precision   KDE_F32 or KDE_F64: arithmetic of the kernel grid, the
+ *               transforms and the density.
+ *   range_mode  KDE_RANGE_CORRECTED: L_k = min(M_k-1, ceil(tau sqrt(lambda_max(H)) / delta_k))
+ *               (Eq. 15).  KDE_RANGE_PER_AXIS: ceil(tau sqrt(H_kk) / delta_k),
+ *               the axis-aligned range, kept to show what it truncates.
+ *   layout_mode KDE_LAYOUT_CORRECTED: all signed lags (Eq. 12).
+ *               KDE_LAYOUT_WAND: k_{|l_1|,...,|l_d|} at lag l, which is what
+ *               Wand's wrap-around layout (Eq. 8) convolves with; wrong for
+ *               non-diagonal H (Sec. 3-4.1), kept for demonstration.
+ *   P_min       optional lower bounds on the padded sizes (0 = none). */
+typedef struct {
+  double tau;
+  int precision;
+  int range_mode;
+  int layout_mode;
+  int64_t P_min[KDE_MAX_D];
+} kde_opts;
+
+/* Everything the plan derives on the host, in FP64.
+ *   delta[k]   binwidth (Eq. 4); lambda_max  largest eigenvalue of H;
+ *   L[k]       effective support (Eq. 15, or the per-axis range);
+ *   P[k]       padded FFT length: the smallest 2^a 3^b 5^c 7^e >= M_k + L_k
+ *              (and >= P_min[k]); cyclic convolution of that length equals the
+ *              linear one of Eq. 7 on [0, M_k) (Eq. 10, zero padding);
+ *   Q          P[d-1]/2 + 1, the half-spectrum length of the last axis;
+ *   kspec_elems   elements of the real kernel spectrum: P_0 ... P_{d-2} x Q;
+ *   workspace_bytes  scratch needed by kde_kernel_grid and kde_fft_eval;
+ *   radix/nstages    the mixed-radix factorisation used per axis. */
+typedef struct {
+  int d;
+  int precision;
+  int64_t M[KDE_MAX_D];
+  int64_t L[KDE_MAX_D];
+  int64_t P[KDE_MAX_D];
+  int64_t Q;
+  double delta[KDE_MAX_D];
+  double lambda_max;
+  double det_H;
+  int64_t kspec_elems;
+  size_t kspec_bytes;
+  size_t workspace_bytes;
+  int nstages[KDE_MAX_D];
+  int radix[KDE_MAX_D][KDE_MAX_STAGES];
+} kde_plan_info;
+
+typedef struct kde_plan_s* kde_plan;
+
+/* Host-only planning (no GPU needed): checks the problem and fills *info.
+ * H is d x d row-major, symmetric to 1e-12 relative (else INVALID_ARG) and
+ * positive definite (else NOT_SPD).  lo[k] < hi[k] are the first and last
+ * grid nodes g_{k1}, g_{kM_k} (Eq. 3-4); M[k] >= 2.  opts may be NULL. */
+kde_status kde_plan_info_compute(int d, const int64_t* M, const double* lo, const double* hi,
+                                 const double* H, const kde_opts* opts, kde_plan_info* info);
+
+/* As kde_plan_info_compute, then builds the device-side twiddle tables
+ * (e^{-2 pi i m / P_k}, generated in FP64) on the current device.  This is
+ * set-up, not part of an evaluation: it allocates and synchronises.  The
+ * plan owns the tables; free them with kde_plan_destroy. */
+kde_status kde_plan_create(int d, const int64_t* M, const double* lo, const double* hi,
+                           const double* H, const kde_opts* opts, kde_plan* out);
+kde_status kde_plan_get_info(kde_plan plan, kde_plan_info* info);
+kde_status kde_plan_destroy(kde_plan plan);
+
+/* Linear binning (Sec. 2, first step).  X: n x d row-major device array of
+ * float (x_dtype KDE_F32) or double (KDE_F64).  counts: prod(M) int64 in
+ * units of 2^-32 of a sample; zeroed by the call, then each sample inside
+ * the grid adds integer weights summing to exactly 2^32 to its 2^d
+ * neighbouring nodes, so sum(counts) = (n - outside) * 2^32 (the paper's
+ * requirement that counts sum to n, Sec. 3) and the result does not depend
+ * on the order of the additions.  Rounding rules, per axis:
+ *   t = (x - lo) * s in X's type, lo and s = (M-1)/(hi-lo) rounded to X's
+ *   type, no fused multiply-add; t < 0, t > M-1 or NaN on any axis drops the
+ *   sample and counts it in *n_outside; i = floor(t), f = t - i, a sample at
+ *   t = M-1 uses i = M-2, f = 1; Q = round-half-even(f 2^32); the mass 2^32
+ *   is split axis by axis (axis 0 first): part w gives
+ *   floor((w Q + 2^31) / 2^32) to node i+1 and the rest to node i.
+ * n_outside: device int64, zeroed then incremented; may be NULL.  n may be 0.
+ * Requires n < 2^31 (so no count overflows) and prod(M) < 2^40. */
+kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, const double* lo,
+                   const double* hi, const int64_t* M, int64_t* counts, int64_t* n_outside,
+                   kde_stream_t stream);
+
+/* Kernel grid and its spectrum (Eq. 6, Eq. 10's K = F(k)).  Evaluates
+ * k_l = K_H(delta o l) / (n 2^32 prod P) for |l_k| <= L_k at wrapped index
+ * l mod P_k (zero elsewhere) and transforms it.  k_{-l} = k_l, so the
+ * spectrum is real; Kspec receives it as plan.kspec_elems values of the
+ * plan's precision, laid out P_0 x ... x P_{d-2} x Q (half spectrum along the
+ * last axis).  The 1/n of Eq. 2, the 2^-32 count unit and the 1/prod(P)
+ * normalisation of Eq. 11/14 are folded in here.  n >= 1 is the number of
+ * samples that were binned (the n of Eq. 2).  workspace: at least
+ * plan.workspace_bytes of device scratch, 16-byte aligned. */
+kde_status kde_kernel_grid(kde_plan plan, int64_t n, void* Kspec, void* workspace,
+                           size_t workspace_bytes, kde_stream_t stream);
+
+/* Density on the grid (Eq. 10 then the crop of Eq. 14 in wrapped form):
+ * density = F^{-1}(F(c) K) restricted to [0, M_k) per axis.  counts come from
+ * kde_bin with the plan's M, Kspec from kde_kernel_grid with the same plan.
+ * density: prod(M) values of the plan's precision.  workspace as above;
+ * it may be shared with kde_kernel_grid's when the calls are ordered. */
+kde_status kde_fft_eval(kde_plan plan, const int64_t* counts, const void* Kspec, void* density,
+                        void* workspace, size_t workspace_bytes, kde_stream_t stream);
+
+/* Diagnostics. */
+const char* kde_status_string(kde_status s);
+const char* kde_last_error(void);
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t kde_launch_count(void);
+/* Per-kernel timing with CUDA events on the launching stream.  Enabling
+ * clears earlier records.  kde_profile_count/entry aggregate by kernel name
+ * and synchronise on the recorded events. */
+kde_status kde_profile_enable(int on);
+int kde_profile_count(void);
+kde_status kde_profile_entry(int i, const char** name, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KDE_GB300_H */

@@ -1,0 +1,305 @@
+"""Thin Python binding of the C ABI in include/kde_gb300.h.
+
+Argument marshalling only: every step of the estimator runs in the CUDA
+library.  Tensors are PyTorch device tensors (their data pointers are passed
+through); streams are the current PyTorch CUDA stream unless one is given.
+The library must be built (``build.build()``); loading fails loudly if it is
+missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+F32, F64 = 0, 1
+RANGE_CORRECTED, RANGE_PER_AXIS = 0, 1
+LAYOUT_CORRECTED, LAYOUT_WAND = 0, 1
+MAX_D, MAX_STAGES = 3, 16
+
+_STATUS = {0: "KDE_OK", 1: "KDE_ERR_INVALID_ARG", 2: "KDE_ERR_NOT_SPD", 4: "KDE_ERR_WORKSPACE",
+           5: "KDE_ERR_CUDA", 7: "KDE_ERR_UNSUPPORTED"}
+
+
+class KDEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("precision", ctypes.c_int),
+                ("range_mode", ctypes.c_int), ("layout_mode", ctypes.c_int),
+                ("P_min", ctypes.c_int64 * MAX_D)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("precision", ctypes.c_int),
+                ("M", ctypes.c_int64 * MAX_D), ("L", ctypes.c_int64 * MAX_D),
+                ("P", ctypes.c_int64 * MAX_D), ("Q", ctypes.c_int64),
+                ("delta", ctypes.c_double * MAX_D), ("lambda_max", ctypes.c_double),
+                ("det_H", ctypes.c_double), ("kspec_elems", ctypes.c_int64),
+                ("kspec_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
+                ("nstages", ctypes.c_int * MAX_D),
+                ("radix", (ctypes.c_int * MAX_STAGES) * MAX_D)]
+
+
+EXPORTS = [
+    "kde_plan_info_compute", "kde_plan_create", "kde_plan_get_info", "kde_plan_destroy",
+    "kde_bin", "kde_kernel_grid", "kde_fft_eval", "kde_status_string", "kde_last_error",
+    "kde_launch_count", "kde_profile_enable", "kde_profile_count", "kde_profile_entry",
+]
+
+_lib = None
+
+
+def lib():
+    """Load libkde_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"{_build.LIB} is missing: run paper_1508_02766_gb300.build.build()")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.kde_plan_info_compute.argtypes = [ctypes.c_int, i64p, dp, dp, dp, ctypes.POINTER(Opts),
+                                        ctypes.POINTER(PlanInfo)]
+    L.kde_plan_create.argtypes = [ctypes.c_int, i64p, dp, dp, dp, ctypes.POINTER(Opts),
+                                  ctypes.POINTER(vp)]
+    L.kde_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    L.kde_plan_destroy.argtypes = [vp]
+    L.kde_bin.argtypes = [vp, ctypes.c_int, i64, ctypes.c_int, dp, dp, i64p, vp, vp, vp]
+    L.kde_kernel_grid.argtypes = [vp, i64, vp, vp, ctypes.c_size_t, vp]
+    L.kde_fft_eval.argtypes = [vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.kde_status_string.restype = ctypes.c_char_p
+    L.kde_status_string.argtypes = [ctypes.c_int]
+    L.kde_last_error.restype = ctypes.c_char_p
+    L.kde_launch_count.restype = i64
+    L.kde_profile_enable.argtypes = [ctypes.c_int]
+    L.kde_profile_entry.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                    dp, i64p]
+    for name in ("kde_plan_info_compute", "kde_plan_create", "kde_plan_get_info",
+                 "kde_plan_destroy", "kde_bin", "kde_kernel_grid", "kde_fft_eval",
+                 "kde_profile_enable", "kde_profile_entry"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != 0:
+        raise KDEError(status, lib().kde_last_error().decode())
+
+
+def _darr(vals, n=None):
+    vals = [float(v) for v in np.asarray(vals, dtype=np.float64).ravel()]
+    return (ctypes.c_double * len(vals))(*vals)
+
+
+def _iarr(vals):
+    vals = [int(v) for v in vals]
+    return (ctypes.c_int64 * len(vals))(*vals)
+
+
+def _opts(tau=3.7, precision="f32", range_mode="corrected", layout="corrected", P_min=None):
+    o = Opts()
+    o.tau = tau
+    o.precision = F32 if precision == "f32" else F64
+    o.range_mode = RANGE_CORRECTED if range_mode == "corrected" else RANGE_PER_AXIS
+    o.layout_mode = LAYOUT_CORRECTED if layout == "corrected" else LAYOUT_WAND
+    for k, p in enumerate(P_min or []):
+        o.P_min[k] = int(p)
+    return o
+
+
+@dataclass
+class Info:
+    d: int
+    precision: str
+    M: tuple
+    L: tuple
+    P: tuple
+    Q: int
+    delta: tuple
+    lambda_max: float
+    det_H: float
+    kspec_elems: int
+    kspec_bytes: int
+    workspace_bytes: int
+    radices: tuple
+
+
+def _info(pi: PlanInfo) -> Info:
+    d = pi.d
+    return Info(d, "f32" if pi.precision == F32 else "f64", tuple(pi.M[:d]), tuple(pi.L[:d]),
+                tuple(pi.P[:d]), pi.Q, tuple(pi.delta[:d]), pi.lambda_max, pi.det_H,
+                pi.kspec_elems, pi.kspec_bytes, pi.workspace_bytes,
+                tuple(tuple(pi.radix[k][:pi.nstages[k]]) for k in range(d)))
+
+
+def kde_plan_info_compute(M, lo, hi, H, **opts) -> Info:
+    """Host-only planning (Eq. 4, Eq. 15, padded sizes); needs no GPU."""
+    H = np.asarray(H, dtype=np.float64)
+    d = H.shape[0]
+    pi = PlanInfo()
+    o = _opts(**opts)
+    _check(lib().kde_plan_info_compute(d, _iarr(M), _darr(lo), _darr(hi), _darr(H),
+                                       ctypes.byref(o), ctypes.byref(pi)))
+    return _info(pi)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Plan:
+    """kde_plan_create / kde_plan_destroy; the plan owns its twiddle tables."""
+
+    def __init__(self, M, lo, hi, H, **opts):
+        H = np.asarray(H, dtype=np.float64)
+        self.d = H.shape[0]
+        self.M = tuple(int(m) for m in M)
+        self.lo = np.asarray(lo, dtype=np.float64)
+        self.hi = np.asarray(hi, dtype=np.float64)
+        h = ctypes.c_void_p()
+        o = _opts(**opts)
+        _check(lib().kde_plan_create(self.d, _iarr(M), _darr(lo), _darr(hi), _darr(H),
+                                     ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        pi = PlanInfo()
+        _check(lib().kde_plan_get_info(h, ctypes.byref(pi)))
+        self.info = _info(pi)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().kde_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def real_dtype(self):
+        import torch
+        return torch.float32 if self.info.precision == "f32" else torch.float64
+
+    def workspace(self, device="cuda"):
+        import torch
+        nbytes = max(16, self.info.workspace_bytes)
+        return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def kde_bin(X, lo, hi, M, counts=None, n_outside=None, stream=None):
+    """Linear binning into int64 counts (units 2^-32).  X: (n, d) float32/float64 CUDA tensor."""
+    import torch
+    if not X.is_cuda or X.dim() != 2 or not X.is_contiguous():
+        raise ValueError("X must be a contiguous (n, d) CUDA tensor")
+    if X.dtype not in (torch.float32, torch.float64):
+        raise ValueError("X must be float32 or float64")
+    n, d = X.shape
+    M = tuple(int(m) for m in M)
+    if counts is None:
+        counts = torch.empty(M, dtype=torch.int64, device=X.device)
+    _check(lib().kde_bin(_ptr(X) if n else ctypes.c_void_p(0),
+                         F32 if X.dtype == torch.float32 else F64, n, d,
+                         _darr(lo), _darr(hi), _iarr(M), _ptr(counts), _ptr(n_outside),
+                         _stream_ptr(stream)))
+    return counts
+
+
+def kde_kernel_grid(plan: Plan, n, Kspec=None, workspace=None, stream=None):
+    """Real kernel spectrum K (Eq. 6 and Eq. 10) with 1/n, 2^-32 and 1/prod(P) folded in."""
+    import torch
+    if Kspec is None:
+        Kspec = torch.empty(plan.info.kspec_elems, dtype=plan.real_dtype(), device="cuda")
+    if workspace is None:
+        workspace = plan.workspace()
+    _check(lib().kde_kernel_grid(plan.handle, int(n), _ptr(Kspec), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), _stream_ptr(stream)))
+    return Kspec
+
+
+def kde_fft_eval(plan: Plan, counts, Kspec, density=None, workspace=None, stream=None):
+    """Density on the grid: F^{-1}(F(c) K) cropped to M (Eq. 10, Eq. 14)."""
+    import torch
+    if density is None:
+        density = torch.empty(plan.M, dtype=plan.real_dtype(), device="cuda")
+    if workspace is None:
+        workspace = plan.workspace()
+    _check(lib().kde_fft_eval(plan.handle, _ptr(counts), _ptr(Kspec), _ptr(density),
+                              _ptr(workspace), workspace.numel() * workspace.element_size(),
+                              _stream_ptr(stream)))
+    return density
+
+
+def kde_eval(X, H, lo, hi, M, n=None, stream=None, **opts):
+    """bin -> kernel grid -> FFT evaluation on one stream; returns (density, counts, plan)."""
+    plan = Plan(M, lo, hi, H, **opts)
+    counts = kde_bin(X, lo, hi, M, stream=stream)
+    ws = plan.workspace()
+    K = kde_kernel_grid(plan, X.shape[0] if n is None else n, workspace=ws, stream=stream)
+    dens = kde_fft_eval(plan, counts, K, workspace=ws, stream=stream)
+    return dens, counts, plan
+
+
+def launch_count() -> int:
+    return int(lib().kde_launch_count())
+
+
+def profile_enable(on: bool):
+    _check(lib().kde_profile_enable(1 if on else 0))
+
+
+def profile_read():
+    """{kernel name: (total ms, launches)} for launches since profile_enable(True)."""
+    L = lib()
+    out = {}
+    for i in range(L.kde_profile_count()):
+        name = ctypes.c_char_p()
+        ms = ctypes.c_double()
+        cnt = ctypes.c_int64()
+        _check(L.kde_profile_entry(i, ctypes.byref(name), ctypes.byref(ms), ctypes.byref(cnt)))
+        out[name.value.decode()] = (ms.value, cnt.value)
+    return out
+
+
+class PreparedPath:
+    """bin -> kernel grid -> FFT evaluation on fixed buffers and one stream,
+    with every C argument marshalled once, so that a call costs three C calls."""
+
+    def __init__(self, plan: Plan, X, counts, Kspec, density, workspace, n=None,
+                 n_outside=None, stream=None):
+        import torch
+        L = lib()
+        self._L = L
+        self.plan = plan
+        s = _stream_ptr(stream)
+        nX, d = X.shape
+        self._bin = (_ptr(X), F32 if X.dtype == torch.float32 else F64, nX, d, _darr(plan.lo),
+                     _darr(plan.hi), _iarr(plan.M), _ptr(counts), _ptr(n_outside), s)
+        wsb = workspace.numel() * workspace.element_size()
+        self._kg = (plan.handle, int(nX if n is None else n), _ptr(Kspec), _ptr(workspace), wsb, s)
+        self._ev = (plan.handle, _ptr(counts), _ptr(Kspec), _ptr(density), _ptr(workspace), wsb, s)
+        self._keep = (X, counts, Kspec, density, workspace, n_outside)
+
+    def __call__(self):
+        _check(self._L.kde_bin(*self._bin))
+        _check(self._L.kde_kernel_grid(*self._kg))
+        _check(self._L.kde_fft_eval(*self._ev))

@@ -1,0 +1,195 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Counts must be bit-identical.  Densities are compared as max |gpu - oracle|
+divided by max |oracle| over the compared nodes: at most 1e-12 on the FP64
+path and 1e-5 on the FP32 path.  Small grids are compared on every node;
+the full-size workloads on sampled nodes (plus a window around the peak),
+with the oracle evaluating Eq. 7 node by node.
+"""
+import numpy as np
+import pytest
+
+from oracle import kde_oracle as O
+from paper_1508_02766_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def K():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1508_02766_gb300 import build, kde
+    import os
+    if not os.path.exists(build.LIB):
+        build.build()
+    return kde
+
+
+def rel_err(gpu, ref):
+    return float(np.max(np.abs(gpu - ref)) / np.max(np.abs(ref)))
+
+
+def run_gpu(K, w, **opts):
+    X = torch.from_numpy(np.ascontiguousarray(w.X)).cuda()
+    plan = K.Plan(w.M, w.lo, w.hi, w.H, precision=w.precision, tau=w.tau, **opts)
+    nout = torch.zeros(1, dtype=torch.int64, device="cuda")
+    counts = K.kde_bin(X, w.lo, w.hi, w.M, n_outside=nout)
+    ws = plan.workspace()
+    Ks = K.kde_kernel_grid(plan, w.n, workspace=ws)
+    dens = K.kde_fft_eval(plan, counts, Ks, workspace=ws)
+    torch.cuda.synchronize()
+    return dens.cpu().numpy(), counts.cpu().numpy(), int(nout.item()), plan
+
+
+def oracle_full(w, range_mode="corrected", layout="corrected"):
+    return O.binned_estimate(w.X, w.H, w.lo, w.hi, w.M, tau=w.tau, range_mode=range_mode,
+                             layout=layout)
+
+
+SMALL = [
+    (1, (700,), "f64"), (1, (700,), "f32"), (1, (2,), "f64"),
+    (2, (37, 53), "f64"), (2, (37, 53), "f32"), (2, (130, 67), "f32"), (2, (2, 3), "f64"),
+    (3, (9, 13, 11), "f64"), (3, (20, 17, 24), "f32"), (3, (2, 2, 2), "f32"),
+]
+
+
+@pytest.mark.parametrize("d,M,prec", SMALL)
+def test_small_grids_every_node(K, d, M, prec):
+    w = W.small_case(100 + d * 7 + len(M) + M[0], d, M, n=3000, precision=prec)
+    dens, counts, nout, plan = run_gpu(K, w)
+    f, c_ref, L, nout_ref = oracle_full(w)
+    assert plan.info.L == L
+    assert nout == nout_ref
+    assert np.array_equal(counts, c_ref)
+    assert rel_err(dens, f) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_support_is_whole_grid(K, prec):
+    """L = M - 1 on every axis (a wide H): every lag of Eq. 5 is kept."""
+    w = W.small_case(7, 2, (24, 19), n=500, precision=prec, scale=5.0)
+    dens, counts, _, plan = run_gpu(K, w)
+    assert plan.info.L == (23, 18)
+    f, c_ref, L, _ = oracle_full(w)
+    assert np.array_equal(counts, c_ref)
+    assert rel_err(dens, f) <= TOL[prec]
+
+
+def test_kde2d_128_f64_every_node(K):
+    w = W.kde2d_128_f64()
+    dens, counts, nout, plan = run_gpu(K, w)
+    f, c_ref, L, nout_ref = oracle_full(w)
+    assert nout == nout_ref == 0
+    assert np.array_equal(counts, c_ref)
+    assert int(counts.sum()) == w.n << 32
+    assert rel_err(dens, f) <= 1e-12
+
+
+def sampled_nodes(rng, M, dens, m=3000, window=5):
+    nodes = np.stack([rng.integers(0, Mk, m) for Mk in M], axis=1)
+    peak = np.array(np.unravel_index(np.argmax(dens), dens.shape))
+    offs = np.stack(np.meshgrid(*[np.arange(-window, window + 1)] * len(M), indexing="ij"),
+                    -1).reshape(-1, len(M))
+    win = np.clip(peak + offs, 0, np.array(M) - 1)
+    return np.concatenate([nodes, win])
+
+
+@pytest.mark.parametrize("name", ["kde2d_1024_f32", "kde3d_256_f32"])
+def test_full_size_sampled_nodes(K, name):
+    w = W.WORKLOADS[name]()
+    dens, counts, nout, plan = run_gpu(K, w)
+    assert int(counts.sum()) == (w.n - nout) << 32
+    L = O.support_L(w.H, w.lo, w.hi, w.M, w.tau)
+    assert plan.info.L == L
+    k = O.kernel_weights(w.H, w.lo, w.hi, w.M, L, w.n)
+    rng = np.random.default_rng(1)
+    nodes = sampled_nodes(rng, w.M, dens, m=3000 if w.d == 2 else 1500, window=5 if w.d == 2 else 2)
+    # Counts: the oracle's binning on the same samples.
+    c_ref, nout_ref = O.bin_linear(w.X, w.lo, w.hi, w.M)
+    assert nout == nout_ref
+    assert np.array_equal(counts, c_ref)
+    ref = O.binned_direct_at(O.counts_to_c(c_ref), k, L, nodes)
+    got = dens[tuple(nodes.T)]
+    assert rel_err(got, ref) <= 1e-5
+
+
+def test_per_axis_range_truncates_correlated_kernel(K):
+    """Sec. 4.2 / Eq. 15: with correlation .95 the per-axis range drops kernel
+    mass the corrected range keeps; the GPU reproduces both estimates."""
+    w = W.kde2d_1024_f32(n=200_000)
+    w.M = (256, 256)
+    d_c, _, _, pc = run_gpu(K, w)
+    d_a, _, _, pa = run_gpu(K, w, range_mode="per_axis")
+    assert all(a < c for a, c in zip(pa.info.L, pc.info.L))
+    f_c, _, _, _ = oracle_full(w)
+    f_a, _, _, _ = oracle_full(w, range_mode="per_axis")
+    assert rel_err(d_c, f_c) <= 1e-5
+    assert rel_err(d_a, f_a) <= 1e-5
+    assert rel_err(d_a, d_c) > 1e-4
+
+
+def test_wand_layout_matches_oracle_and_fails_for_full_H(K):
+    """Wand's layout (Eq. 8) on the GPU equals the oracle's k_{|l|} sum, and
+    differs from the corrected estimate by O(1) for correlated H (Figure 1(b))."""
+    w = W.small_case(3, 2, (64, 48), n=2000, precision="f64", corr=0.9)
+    d_w, _, _, _ = run_gpu(K, w, layout="wand")
+    d_c, _, _, _ = run_gpu(K, w)
+    f_w, _, _, _ = oracle_full(w, layout="wand")
+    assert rel_err(d_w, f_w) <= 1e-12
+    assert rel_err(d_w, d_c) > 1e-2
+
+
+def test_wand_layout_exact_for_diagonal_H(K):
+    w = W.small_case(4, 3, (12, 10, 9), n=800, precision="f64", H=np.diag([0.02, 0.05, 0.03]))
+    d_w, _, _, _ = run_gpu(K, w, layout="wand")
+    d_c, _, _, _ = run_gpu(K, w)
+    assert rel_err(d_w, d_c) <= 1e-13
+
+
+def test_edge_samples_and_outside(K):
+    """Samples exactly at lo/hi, on nodes, outside and NaN (binning spec)."""
+    rng = np.random.default_rng(5)
+    for dt, prec in [(np.float64, "f64"), (np.float32, "f32")]:
+        X = rng.uniform(-0.1, 1.1, size=(4000, 2)).astype(dt)
+        X[:10] = 1.0
+        X[10:20] = 0.0
+        X[20:30, 1] = np.nan
+        X[30:60] = (rng.integers(0, 20, size=(30, 2)) / 19.0).astype(dt)
+        w = W.Workload("edges", X, np.array([[0.01, 0.004], [0.004, 0.008]]), np.zeros(2),
+                       np.ones(2), (20, 23), prec)
+        dens, counts, nout, _ = run_gpu(K, w)
+        f, c_ref, _, nout_ref = oracle_full(w)
+        assert nout == nout_ref and nout > 20
+        assert np.array_equal(counts, c_ref)
+        assert rel_err(dens, f) <= TOL[prec]
+
+
+def test_empty_input_and_errors(K):
+    X = torch.empty((0, 2), dtype=torch.float32, device="cuda")
+    nout = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+    counts = K.kde_bin(X, (0, 0), (1, 1), (5, 6), n_outside=nout)
+    torch.cuda.synchronize()
+    assert counts.abs().sum().item() == 0 and nout.item() == 0
+    plan = K.Plan((5, 6), (0, 0), (1, 1), np.eye(2) * 0.01)
+    with pytest.raises(K.KDEError) as e:
+        K.kde_kernel_grid(plan, 0)
+    assert e.value.status == 1
+    small_ws = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(K.KDEError) as e:
+        K.kde_kernel_grid(plan, 10, workspace=small_ws)
+    assert e.value.status == 4
+
+
+def test_deterministic_and_launch_count(K):
+    w = W.kde2d_1024_f32(n=300_000)
+    before = K.launch_count()
+    a, ca, _, _ = run_gpu(K, w)
+    mid = K.launch_count()
+    b, cb, _, _ = run_gpu(K, w)
+    assert np.array_equal(ca, cb)
+    assert np.array_equal(a, b)
+    assert mid - before >= 5       # twiddles, bin, kernel grid (2), eval (3)

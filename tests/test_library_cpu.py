@@ -1,0 +1,113 @@
+"""CPU-side checks of the CUDA library: it loads, exports every symbol its
+header declares, and its host planning (Eq. 4, Eq. 15, padded sizes, H
+checks) agrees with the oracle.  No compute call needs a GPU here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import kde_oracle as O
+from paper_1508_02766_gb300 import build as B
+from paper_1508_02766_gb300 import kde
+from paper_1508_02766_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    if not os.path.exists(B.LIB):
+        B.build()
+    return B.LIB
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "kde_gb300.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(kde_\w+)\s*\(", text, re.M)))
+
+
+def test_header_symbols_exported():
+    names = header_functions()
+    assert "kde_bin" in names and "kde_fft_eval" in names and "kde_kernel_grid" in names
+    L = ctypes.CDLL(B.LIB)
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(kde.EXPORTS) <= set(names)
+
+
+def _is_7smooth(x):
+    for p in (2, 3, 5, 7):
+        while x % p == 0:
+            x //= p
+    return x == 1
+
+
+@pytest.mark.parametrize("name", ["kde2d_128_f64", "kde2d_1024_f32"])
+@pytest.mark.parametrize("range_mode", ["corrected", "per_axis"])
+def test_plan_matches_oracle_support(name, range_mode):
+    w = W.WORKLOADS[name](n=2000)
+    info = kde.kde_plan_info_compute(w.M, w.lo, w.hi, w.H, precision=w.precision,
+                                     range_mode=range_mode)
+    assert info.L == O.support_L(w.H, w.lo, w.hi, w.M, range_mode=range_mode)
+    assert np.allclose(info.delta, O.binwidths(w.lo, w.hi, w.M), rtol=0, atol=0)
+    assert abs(info.lambda_max - np.linalg.eigvalsh(w.H).max()) < 1e-14
+    for k in range(w.d):
+        assert info.P[k] >= w.M[k] + info.L[k]
+        assert _is_7smooth(info.P[k])
+        assert all(not _is_7smooth(p) for p in range(w.M[k] + info.L[k], info.P[k]))
+        assert int(np.prod(info.radices[k])) == info.P[k]
+    assert info.Q == info.P[-1] // 2 + 1
+
+
+def test_plan_3d_eigenvalue_and_support():
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        H = W.random_spd(rng, 3, 1.0, 50.0, scale=0.05)
+        lo, hi, M = [0, 0, 0], [3.0, 2.0, 4.0], [64, 48, 80]
+        info = kde.kde_plan_info_compute(M, lo, hi, H)
+        assert abs(info.lambda_max - np.linalg.eigvalsh(H).max()) < 1e-13 * np.abs(H).max()
+        assert abs(info.det_H - np.linalg.det(H)) < 1e-12 * abs(np.linalg.det(H))
+        assert info.L == O.support_L(H, lo, hi, M)
+
+
+def test_plan_workload_sizes():
+    """The padded sizes of the benchmark workloads (smallest 7-smooth >= M + L)."""
+    w = W.kde2d_128_f64()
+    assert kde.kde_plan_info_compute(w.M, w.lo, w.hi, w.H, precision="f64").P == (144, 144)
+    w = W.kde2d_1024_f32(n=100_000)
+    info = kde.kde_plan_info_compute(w.M, w.lo, w.hi, w.H)
+    assert info.P == (1080, 1080)
+
+
+def test_plan_rejects_bad_input():
+    ok = dict(M=(8, 8), lo=(0, 0), hi=(1, 1))
+    with pytest.raises(kde.KDEError) as e:
+        kde.kde_plan_info_compute(H=[[1.0, 0.5], [0.4, 1.0]], **ok)
+    assert e.value.status == 1
+    with pytest.raises(kde.KDEError) as e:
+        kde.kde_plan_info_compute(H=[[1.0, 2.0], [2.0, 1.0]], **ok)
+    assert e.value.status == 2
+    with pytest.raises(kde.KDEError) as e:
+        kde.kde_plan_info_compute(M=(1, 8), lo=(0, 0), hi=(1, 1), H=np.eye(2))
+    assert e.value.status == 1
+    with pytest.raises(kde.KDEError) as e:
+        kde.kde_plan_info_compute(M=(8, 8), lo=(0, 1), hi=(1, 1), H=np.eye(2))
+    assert e.value.status == 1
+    with pytest.raises(kde.KDEError) as e:
+        kde.kde_plan_info_compute(M=(8, 8, 8, 8), lo=(0,) * 4, hi=(1,) * 4, H=np.eye(4))
+    assert e.value.status == 7
+    with pytest.raises(kde.KDEError) as e:
+        kde.kde_plan_info_compute(M=(5000,), lo=(0,), hi=(1,), H=np.eye(1) * 1e-4)
+    assert e.value.status == 7
+    with pytest.raises(kde.KDEError) as e:
+        kde.kde_plan_info_compute(H=[[np.nan, 0], [0, 1.0]], **ok)
+    assert e.value.status == 1
+
+
+def test_plan_respects_P_min_and_modes():
+    info = kde.kde_plan_info_compute((100, 60), (0, 0), (1, 1), [[0.01, 0.0], [0.0, 0.02]],
+                                     P_min=(256, 0), precision="f64")
+    assert info.P[0] == 256 and info.precision == "f64"
+    assert info.workspace_bytes > 0 and info.kspec_bytes == info.kspec_elems * 8
