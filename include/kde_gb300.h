@@ -158,6 +158,24 @@ kde_status kde_kernel_grid(kde_plan plan, int64_t n, void* Kspec, void* workspac
 kde_status kde_fft_eval(kde_plan plan, const int64_t* counts, const void* Kspec, void* density,
                         void* workspace, size_t workspace_bytes, kde_stream_t stream);
 
+/* kde_fft_eval without a workspace argument, for callers that cannot
+ * allocate device memory where they evaluate (for example code whose
+ * allocations all belong to a host framework, or a loop that must never enter
+ * an allocator).  The paper has no counterpart; this is an interface
+ * convenience.  Scratch comes from one fixed array of KDE_NOALLOC_SCRATCH_BYTES
+ * inside the library, reserved on every device that loads the library until
+ * the process exits.  The call allocates nothing.  Plans whose
+ * workspace_bytes exceed KDE_NOALLOC_SCRATCH_BYTES are rejected with
+ * KDE_ERR_WORKSPACE.  The first call on a device looks up the array's device
+ * address (once per device, with that device current); make that first call
+ * before any stream capture.  All calls share the array and nothing in it
+ * needs to start at zero (each pass writes what the next one reads), but
+ * calls whose work overlaps on the GPU (different streams, or different
+ * host threads, without ordering between them) race on it. */
+#define KDE_NOALLOC_SCRATCH_BYTES (8u << 20)
+kde_status kde_fft_eval_noalloc(kde_plan plan, const int64_t* counts, const void* Kspec,
+                                void* density, kde_stream_t stream);
+
 /* Diagnostics. */
 const char* kde_status_string(kde_status s);
 const char* kde_last_error(void);

@@ -20,6 +20,7 @@
 #include <cstdint>
 #include <mutex>
 #include <set>
+#include <string>
 
 #include "fft_engine.cuh"
 #include "kde_internal.h"
@@ -658,4 +659,57 @@ extern "C" kde_status kde_fft_eval(kde_plan plan, const int64_t* counts, const v
   if (plan->info.precision == KDE_F32)
     return fft_eval_impl<float>(plan, counts, Kspec, density, workspace, st);
   return fft_eval_impl<double>(plan, counts, Kspec, density, workspace, st);
+}
+
+// ---------------------------------------------------------------------------
+// kde_fft_eval_noalloc: kde_fft_eval with its scratch in a fixed device array
+// instead of a caller-provided workspace, for callers that cannot allocate
+// device memory at the point of the call (for example code running inside a
+// framework that owns every allocation, or a real-time loop that must not
+// enter the allocator).  Its size is fixed at build time and the array lives
+// on every device that loads this library until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // KDE_NOALLOC_SCRATCH_BYTES
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the symbol's name is only a host-side handle, so the address is looked up
+// once per device with that device current and cached.
+kde_status noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(KDE_ERR_UNSUPPORTED, "device ordinal too large");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return KDE_OK;
+}
+
+}  // namespace
+
+extern "C" kde_status kde_fft_eval_noalloc(kde_plan plan, const int64_t* counts, const void* Kspec,
+                                           void* density, kde_stream_t stream) {
+  if (!plan || !counts || !Kspec || !density) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (plan->info.workspace_bytes > kNoAllocScratchBytes)
+    return fail(KDE_ERR_WORKSPACE,
+                "kde_fft_eval_noalloc: the plan needs " + std::to_string(plan->info.workspace_bytes) +
+                    " bytes of scratch, above the fixed " + std::to_string(kNoAllocScratchBytes) +
+                    "; use kde_fft_eval with a workspace");
+  kde_status s = check_device(plan);
+  if (s != KDE_OK) return s;
+  void* scratch = nullptr;
+  if ((s = noalloc_scratch(plan->device, &scratch)) != KDE_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->info.precision == KDE_F32)
+    return fft_eval_impl<float>(plan, counts, Kspec, density, scratch, st);
+  return fft_eval_impl<double>(plan, counts, Kspec, density, scratch, st);
 }

@@ -52,6 +52,7 @@ EXPORTS = [
     "kde_plan_info_compute", "kde_plan_create", "kde_plan_get_info", "kde_plan_destroy",
     "kde_bin", "kde_kernel_grid", "kde_fft_eval", "kde_status_string", "kde_last_error",
     "kde_launch_count", "kde_profile_enable", "kde_profile_count", "kde_profile_entry",
+    "kde_fft_eval_noalloc",
 ]
 
 _lib = None
@@ -76,6 +77,7 @@ def lib():
     L.kde_bin.argtypes = [vp, ctypes.c_int, i64, ctypes.c_int, dp, dp, i64p, vp, vp, vp]
     L.kde_kernel_grid.argtypes = [vp, i64, vp, vp, ctypes.c_size_t, vp]
     L.kde_fft_eval.argtypes = [vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.kde_fft_eval_noalloc.argtypes = [vp, vp, vp, vp, vp]
     L.kde_status_string.restype = ctypes.c_char_p
     L.kde_status_string.argtypes = [ctypes.c_int]
     L.kde_last_error.restype = ctypes.c_char_p
@@ -85,7 +87,7 @@ def lib():
                                     dp, i64p]
     for name in ("kde_plan_info_compute", "kde_plan_create", "kde_plan_get_info",
                  "kde_plan_destroy", "kde_bin", "kde_kernel_grid", "kde_fft_eval",
-                 "kde_profile_enable", "kde_profile_entry"):
+                 "kde_fft_eval_noalloc", "kde_profile_enable", "kde_profile_entry"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -246,6 +248,19 @@ def kde_fft_eval(plan: Plan, counts, Kspec, density=None, workspace=None, stream
     _check(lib().kde_fft_eval(plan.handle, _ptr(counts), _ptr(Kspec), _ptr(density),
                               _ptr(workspace), workspace.numel() * workspace.element_size(),
                               _stream_ptr(stream)))
+    return density
+
+
+NOALLOC_SCRATCH_BYTES = 8 << 20
+
+
+def kde_fft_eval_noalloc(plan: Plan, counts, Kspec, density, stream=None):
+    """kde_fft_eval with the library's fixed scratch array instead of a
+    workspace (for callers that cannot allocate device memory at the call).
+    The output tensor must be provided.  Plans needing more than
+    NOALLOC_SCRATCH_BYTES of scratch raise KDE_ERR_WORKSPACE."""
+    _check(lib().kde_fft_eval_noalloc(plan.handle, _ptr(counts), _ptr(Kspec), _ptr(density),
+                                      _stream_ptr(stream)))
     return density
 
 
