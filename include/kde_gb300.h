@@ -121,8 +121,8 @@ kde_status kde_plan_destroy(kde_plan plan);
 
 /* Linear binning (Sec. 2, first step).  X: n x d row-major device array of
  * float (x_dtype KDE_F32) or double (KDE_F64).  counts: prod(M) int64 in
- * units of 2^-32 of a sample; zeroed by the call, then each sample inside
- * the grid adds integer weights summing to exactly 2^32 to its 2^d
+ * units of 2^-32 of a sample; every cell is written by the call: each sample
+ * inside the grid adds integer weights summing to exactly 2^32 to its 2^d
  * neighbouring nodes, so sum(counts) = (n - outside) * 2^32 (the paper's
  * requirement that counts sum to n, Sec. 3) and the result does not depend
  * on the order of the additions.  Rounding rules, per axis:
@@ -133,10 +133,18 @@ kde_status kde_plan_destroy(kde_plan plan);
  *   is split axis by axis (axis 0 first): part w gives
  *   floor((w Q + 2^31) / 2^32) to node i+1 and the rest to node i.
  * n_outside: device int64, zeroed then incremented; may be NULL.  n may be 0.
- * Requires n < 2^31 (so no count overflows) and prod(M) < 2^40. */
+ * workspace: NULL selects the direct method (64-bit atomics into counts);
+ * otherwise at least kde_bin_workspace_bytes(n, d, M) bytes, 256-byte
+ * aligned, select the tiled method (a counting sort of the samples by grid
+ * tile, then shared-memory accumulation per tile).  Both give identical
+ * counts.  Requires n < 2^31 and prod(M) < 2^40 (tiled: < 2^32). */
 kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, const double* lo,
                    const double* hi, const int64_t* M, int64_t* counts, int64_t* n_outside,
-                   kde_stream_t stream);
+                   void* workspace, size_t workspace_bytes, kde_stream_t stream);
+
+/* Scratch bytes the tiled binning method needs for n samples on grid M
+ * (about 16 n bytes plus per-tile tables).  Host only. */
+kde_status kde_bin_workspace_bytes(int64_t n, int d, const int64_t* M, size_t* bytes);
 
 /* Kernel grid and its spectrum (Eq. 6, Eq. 10's K = F(k)).  Evaluates
  * k_l = K_H(delta o l) / (n 2^32 prod P) for |l_k| <= L_k at wrapped index

@@ -1,8 +1,26 @@
 // Linear binning (Sec. 2, first step): each sample inside the grid spreads a
 // unit mass over its 2^d neighbouring nodes with integer weights in units of
-// 2^-32 that sum to exactly 2^32 (so the counts sum to n, Sec. 3 footnote),
-// accumulated with 64-bit integer atomics.  Integer addition is associative,
-// so the counts are bit-identical whatever order the atomics land in.
+// 2^-32 that sum to exactly 2^32 (so the counts sum to n, Sec. 3 footnote).
+// Integer addition is associative, so the counts are bit-identical whatever
+// order the additions happen in.
+//
+// Two implementations of the same arithmetic:
+//   direct  one pass, 64-bit integer atomics straight into the counts (no
+//           scratch; bound by the L2 atomic rate, ~2^d atomics per sample);
+//   tiled   a counting sort of the samples by the grid tile of their base
+//           node, then one block per tile accumulating in shared memory with
+//           shared 64-bit atomics and writing every cell of its tile once
+//           with a plain store (no memset, no global atomics on counts):
+//             hist     per-block histogram of keys (tile, face mask)
+//             scan     exclusive prefix over blocks per key, then over keys
+//             scatter  records {tile-local base, Q_0..Q_{d-1}} into key order
+//             gather   per work item of a tile: own records plus
+//                      neighbours' face records (tiles with more records
+//                      than one item holds are zeroed first and their
+//                      items add with 64-bit atomics)
+//           A sample whose base node is the last row of its tile along axis k
+//           also feeds the next tile (face-mask bit k); the owner of a cell
+//           reads those records from the neighbour's face buckets.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -13,15 +31,17 @@
 namespace {
 
 constexpr unsigned long long kOne = 1ull << 32;
+constexpr int kHistThreads = 512;
+constexpr int kGatherThreads = 256;
+constexpr int kMaxKeys = 32768;
+constexpr int kMaxBlocks = 256;
 
-// floor((w*Q + 2^31) / 2^32) for 0 <= w, Q <= 2^32 using the full 128-bit product.
-__device__ __forceinline__ unsigned long long mulhi_round(unsigned long long w,
-                                                          unsigned long long Q) {
-  unsigned long long lo = w * Q;
-  unsigned long long hi = __umul64hi(w, Q);
-  unsigned long long lo2 = lo + (1ull << 31);
-  hi += (lo2 < lo) ? 1ull : 0ull;
-  return (hi << 32) | (lo2 >> 32);
+// floor((w q + 2^31) / 2^32) for 0 <= w <= 2^32 and 0 <= q < 2^32, exactly,
+// in 32-bit arithmetic: with w = wh 2^32 + wl (wh in {0, 1}) and
+// wl q = H 2^32 + Lo, the value is wh q + H + [Lo >= 2^31].
+__device__ __forceinline__ unsigned mulhi_round(unsigned long long w, unsigned q) {
+  const unsigned wl = (unsigned)w, wh = (unsigned)(w >> 32);
+  return wh * q + __umulhi(wl, q) + ((wl * q) >> 31);
 }
 
 template <typename T>
@@ -30,7 +50,11 @@ struct BinAxis {
   T s;       // (M-1)/(hi-lo) computed in FP64, rounded to X's type
   T top;     // M - 1 in X's type
   int64_t stride;
-  int64_t M;
+  int M;
+  int tile;       // tile extent along this axis (power of two)
+  int tile_log2;
+  int ntiles;     // tiles along this axis
+  int tstride;    // stride of this axis in the tile index
 };
 
 template <typename T>
@@ -43,24 +67,66 @@ __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
-// Position of one coordinate: node index i and fixed-point fraction Q.
-// Returns false if the coordinate is outside [0, M-1] or NaN.
+// Position of one coordinate, normalised: node i and q = round-half-even(f 2^32)
+// with 0 <= q < 2^32.  A fraction that rounds to exactly 2^32 (f = 1) is
+// written as (i + 1, q = 0), which gives bit-identical weights:
+// floor((w 2^32 + 2^31) / 2^32) = w and floor((w 0 + 2^31) / 2^32) = 0.
+// The scaling by 2^32 is exact in either type; FP32 inputs stay in 32-bit
+// arithmetic throughout.  Returns false if t is outside [0, M-1] or NaN.
+__device__ __forceinline__ bool fixed_frac(float f, int& i, unsigned& q) {
+  if (f == 1.0f) {
+    i += 1;
+    q = 0;
+  } else {
+    q = __float2uint_rn(f * 4294967296.0f);  // f 2^32 < 2^32 exactly
+  }
+  return true;
+}
+__device__ __forceinline__ bool fixed_frac(double f, int& i, unsigned& q) {
+  unsigned long long Q = __double2ull_rn(f * 4294967296.0);
+  if (Q == kOne) {
+    i += 1;
+    q = 0;
+  } else {
+    q = (unsigned)Q;
+  }
+  return true;
+}
+
 template <typename T>
-__device__ __forceinline__ bool axis_position(T x, const BinAxis<T>& a, int64_t& i,
-                                              unsigned long long& Q) {
+__device__ __forceinline__ bool axis_position(T x, const BinAxis<T>& a, int& i, unsigned& q) {
   T t = mul_rn(sub_rn(x, a.lo), a.s);
   if (!(t >= T(0) && t <= a.top)) return false;
   T fl = floor(t);
-  i = (int64_t)fl;
+  i = (int)fl;
   T f = sub_rn(t, fl);  // exact
   if (i == a.M - 1) {
     i = a.M - 2;
     f = T(1);
   }
-  Q = __double2ull_rn((double)f * 4294967296.0);  // exact scaling, ties to even
-  return true;
+  return fixed_frac(f, i, q);
 }
 
+// The 2^d corner weights of the hierarchical split (axis 0 first); corner c
+// has offset bit (c >> (D-1-k)) & 1 on axis k.  Each is <= 2^32; they sum
+// to exactly 2^32.
+template <int D>
+__device__ __forceinline__ void corner_weights(const unsigned* q, unsigned long long* w) {
+  w[0] = kOne;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+#pragma unroll
+    for (int c = (1 << k) - 1; c >= 0; --c) {
+      unsigned long long hi = mulhi_round(w[c], q[k]);
+      w[2 * c + 1] = hi;
+      w[2 * c] = w[c] - hi;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Direct path.
+// ---------------------------------------------------------------------------
 template <typename T, int D>
 __global__ void __launch_bounds__(256) kde_bin_kernel(const T* __restrict__ X, int64_t n,
                                                       BinParams<T> p,
@@ -69,31 +135,20 @@ __global__ void __launch_bounds__(256) kde_bin_kernel(const T* __restrict__ X, i
   unsigned long long outside = 0;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
        s += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i[D];
-    unsigned long long Q[D];
+    int i[D];
+    unsigned q[D];
     bool in = true;
 #pragma unroll
-    for (int k = 0; k < D; ++k) in &= axis_position<T>(X[s * D + k], p.ax[k], i[k], Q[k]);
+    for (int k = 0; k < D; ++k) in &= axis_position<T>(X[s * D + k], p.ax[k], i[k], q[k]);
     if (!in) {
       ++outside;
       continue;
     }
     int64_t base = 0;
 #pragma unroll
-    for (int k = 0; k < D; ++k) base += i[k] * p.ax[k].stride;
-    // Hierarchical split of the unit mass, axis 0 first; corner c has offset
-    // bit (c >> (D-1-k)) & 1 on axis k.
+    for (int k = 0; k < D; ++k) base += (int64_t)i[k] * p.ax[k].stride;
     unsigned long long w[1 << D];
-    w[0] = kOne;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-#pragma unroll
-      for (int c = (1 << k) - 1; c >= 0; --c) {
-        unsigned long long hi = mulhi_round(w[c], Q[k]);
-        w[2 * c + 1] = hi;
-        w[2 * c] = w[c] - hi;
-      }
-    }
+    corner_weights<D>(q, w);
 #pragma unroll
     for (int c = 0; c < (1 << D); ++c) {
       if (w[c] == 0) continue;
@@ -111,27 +166,515 @@ __global__ void __launch_bounds__(256) kde_bin_kernel(const T* __restrict__ X, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tiled path.
+// ---------------------------------------------------------------------------
+// Bits per axis of a record's tile-local base node.
+template <int D> struct LocalBits { static constexpr int value = D == 1 ? 32 : (D == 2 ? 16 : 10); };
+
+// A sample's key (base tile, face mask) and record {tile-local base node,
+// q_0 .. q_{d-1}}.  Face-mask bit (D-1-k) is set when the base node is the
+// last node of its tile along axis k (and not the grid's last node): the
+// sample then also feeds the next tile along k.
+template <typename T, int D>
+__device__ __forceinline__ bool sample_key(const T* __restrict__ X, int64_t s, const BinParams<T>& p,
+                                           int& key, uint4& rec) {
+  int i[D];
+  unsigned q[3] = {0, 0, 0};
+  bool in = true;
+#pragma unroll
+  for (int k = 0; k < D; ++k) in &= axis_position<T>(X[s * D + k], p.ax[k], i[k], q[k]);
+  if (!in) return false;
+  int tile = 0, mask = 0;
+  unsigned local = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const int tk = i[k] >> p.ax[k].tile_log2;
+    const int li = i[k] & (p.ax[k].tile - 1);
+    tile += tk * p.ax[k].tstride;
+    local |= (unsigned)li << (LocalBits<D>::value * k);
+    if (li == p.ax[k].tile - 1 && i[k] + 1 < p.ax[k].M) mask |= 1 << (D - 1 - k);
+  }
+  key = (tile << D) | mask;
+  rec = make_uint4(local, q[0], q[1], q[2]);
+  return true;
+}
+
+constexpr int kUnroll = 4;
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kHistThreads)
+kde_bin_hist_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, int nkeys, BinParams<T> p,
+                    unsigned* __restrict__ mat, unsigned long long* __restrict__ n_out) {
+  extern __shared__ unsigned hist[];
+  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) hist[k] = 0;
+  __syncthreads();
+  const int64_t s0 = (int64_t)blockIdx.x * chunk;
+  const int64_t s1 = min(n, s0 + chunk);
+  unsigned long long outside = 0;
+  for (int64_t base = s0 + threadIdx.x; base < s1; base += kUnroll * (int64_t)blockDim.x) {
+    int key[kUnroll];
+    bool in[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t s = base + u * (int64_t)blockDim.x;
+      uint4 rec;
+      in[u] = s < s1 && sample_key<T, D>(X, s, p, key[u], rec);
+      if (s < s1 && !in[u]) ++outside;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (in[u]) atomicAdd(&hist[key[u]], 1u);
+  }
+  __syncthreads();
+  unsigned* row = mat + (int64_t)blockIdx.x * nkeys;
+  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) row[k] = hist[k];
+  if (n_out) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) outside += __shfl_down_sync(0xffffffffu, outside, off);
+    if ((threadIdx.x & 31) == 0 && outside) atomicAdd(n_out, outside);
+  }
+}
+
+// Exclusive prefix over blocks for each key (in place), totals per key.
+// A block takes 32 keys: the [nblocks x 32] slab is staged in shared memory
+// with coalesced rows, each key's column is split into 8 segments scanned by
+// 8 threads, then the segment offsets are applied and the slab written back.
+constexpr int kScanKeys = 32, kScanSegs = 8;
+__global__ void __launch_bounds__(kScanKeys * kScanSegs)
+kde_bin_scan_blocks_kernel(unsigned* __restrict__ mat, int nblocks, int nkeys,
+                           unsigned* __restrict__ totals) {
+  extern __shared__ unsigned slab[];  // [nblocks][kScanKeys + 1]
+  __shared__ unsigned seg_sum[kScanSegs][kScanKeys];
+  const int k0 = blockIdx.x * kScanKeys;
+  const int W = kScanKeys + 1;
+  for (int idx = threadIdx.x; idx < nblocks * kScanKeys; idx += blockDim.x) {
+    int b = idx / kScanKeys, c = idx % kScanKeys;
+    slab[b * W + c] = (k0 + c < nkeys) ? mat[(int64_t)b * nkeys + k0 + c] : 0u;
+  }
+  __syncthreads();
+  const int c = threadIdx.x % kScanKeys, sg = threadIdx.x / kScanKeys;
+  const int len = (nblocks + kScanSegs - 1) / kScanSegs;
+  const int b0 = sg * len, b1 = min(nblocks, b0 + len);
+  unsigned sum = 0;
+  for (int b = b0; b < b1; ++b) sum += slab[b * W + c];
+  seg_sum[sg][c] = sum;
+  __syncthreads();
+  unsigned run = 0, total = 0;
+  for (int g = 0; g < kScanSegs; ++g) {
+    if (g < sg) run += seg_sum[g][c];
+    total += seg_sum[g][c];
+  }
+  for (int b = b0; b < b1; ++b) {
+    unsigned v = slab[b * W + c];
+    slab[b * W + c] = run;
+    run += v;
+  }
+  if (sg == 0 && k0 + c < nkeys) totals[k0 + c] = total;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nblocks * kScanKeys; idx += blockDim.x) {
+    int b = idx / kScanKeys, cc = idx % kScanKeys;
+    if (k0 + cc < nkeys) mat[(int64_t)b * nkeys + k0 + cc] = slab[b * W + cc];
+  }
+}
+
+// Exclusive scan of one value per thread over the block; returns the
+// thread's exclusive prefix and writes the block total to *total.
+__device__ unsigned block_scan_excl(unsigned v, unsigned* warp_sums, unsigned* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned incl = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += y;
+  }
+  __syncthreads();
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned w = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0u;
+    unsigned inc = w;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    warp_sums[lane] = inc - w;
+    if (lane == 31) warp_sums[32] = inc;
+  }
+  __syncthreads();
+  unsigned r = warp_sums[warp] + incl - v;
+  *total = warp_sums[32];
+  return r;
+}
+
+struct TileGeom {
+  int64_t M[KDE_MAX_D];
+  int64_t stride[KDE_MAX_D];
+  int tile[KDE_MAX_D];
+  int ntiles[KDE_MAX_D];
+  int tstride[KDE_MAX_D];
+  int ntiles_total;
+  int tile_cells;
+  int item_cap;
+};
+
+template <int D>
+__device__ __forceinline__ void tile_coords(int t, const TileGeom& g, int* tc) {
+  int rem = t;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    tc[k] = rem / g.tstride[k];
+    rem -= tc[k] * g.tstride[k];
+  }
+}
+
+// Calls f(nb_tile, o, key) for the key ranges feeding tile t, in a fixed
+// order: the tile's own keys (o = 0, all masks), then for each o != 0 the
+// neighbour t - o and its masks that contain o.
+template <int D, typename F>
+__device__ __forceinline__ void for_each_source(const int* tc, const TileGeom& g, F f) {
+  for (int o = 0; o < (1 << D); ++o) {
+    int ntile = 0;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      int nk = tc[k] - ((o >> (D - 1 - k)) & 1);
+      ok &= nk >= 0;
+      ntile += nk * g.tstride[k];
+    }
+    if (!ok) continue;
+    for (int mask = 0; mask < (1 << D); ++mask)
+      if ((mask & o) == o) f(ntile, o, (ntile << D) | mask);
+  }
+}
+
+// One block: starts[key] = exclusive prefix of key totals (starts[nkeys] =
+// all records); per tile the records feeding it (own plus neighbours' face
+// records), its number of work items (ceil(records / cap), at least 1) and
+// the exclusive prefix of items over tiles (item_start[ntiles] = all items).
+template <int D>
+__global__ void __launch_bounds__(1024)
+kde_bin_scan_keys_kernel(const unsigned* __restrict__ totals, int nkeys, TileGeom g,
+                         unsigned* __restrict__ starts, unsigned* __restrict__ item_start) {
+  __shared__ unsigned warp_sums[33];
+  unsigned total;
+  {
+    const int per = (nkeys + blockDim.x - 1) / blockDim.x;
+    const int k0 = threadIdx.x * per;
+    const int k1 = min(nkeys, k0 + per);
+    unsigned local = 0;
+    for (int k = k0; k < k1; ++k) local += totals[k];
+    unsigned run = block_scan_excl(local, warp_sums, &total);
+    for (int k = k0; k < k1; ++k) {
+      starts[k] = run;
+      run += totals[k];
+    }
+    if (threadIdx.x == 0) starts[nkeys] = total;
+  }
+  __syncthreads();
+  const int ntiles = g.ntiles_total;
+  const int per = (ntiles + blockDim.x - 1) / blockDim.x;
+  const int t0 = threadIdx.x * per;
+  const int t1 = min(ntiles, t0 + per);
+  auto items_of = [&](int t) {
+    int tc[KDE_MAX_D];
+    tile_coords<D>(t, g, tc);
+    unsigned recs = 0;
+    for_each_source<D>(tc, g, [&](int, int, int key) { recs += starts[key + 1] - starts[key]; });
+    return recs == 0 ? 1u : (recs + g.item_cap - 1) / g.item_cap;
+  };
+  unsigned li = 0;
+  for (int t = t0; t < t1; ++t) li += items_of(t);
+  unsigned ri = block_scan_excl(li, warp_sums, &total);
+  if (threadIdx.x == 0) item_start[ntiles] = total;
+  for (int t = t0; t < t1; ++t) {
+    item_start[t] = ri;
+    ri += items_of(t);
+  }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kHistThreads)
+kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, int nkeys,
+                       BinParams<T> p, const unsigned* __restrict__ mat,
+                       const unsigned* __restrict__ starts, uint4* __restrict__ recs) {
+  extern __shared__ unsigned cursor[];
+  const unsigned* row = mat + (int64_t)blockIdx.x * nkeys;
+  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) cursor[k] = starts[k] + row[k];
+  __syncthreads();
+  const int64_t s0 = (int64_t)blockIdx.x * chunk;
+  const int64_t s1 = min(n, s0 + chunk);
+  for (int64_t base = s0 + threadIdx.x; base < s1; base += kUnroll * (int64_t)blockDim.x) {
+    int key[kUnroll];
+    uint4 rec[kUnroll];
+    bool in[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t s = base + u * (int64_t)blockDim.x;
+      in[u] = s < s1 && sample_key<T, D>(X, s, p, key[u], rec[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (in[u]) recs[atomicAdd(&cursor[key[u]], 1u)] = rec[u];
+  }
+}
+
+// Store a tile's owned cells (clipped at the grid's edge), last axis fastest.
+template <int D, typename F>
+__device__ __forceinline__ void store_tile(const int* tc, const TileGeom& g, int c0, int cstep,
+                                           unsigned long long* __restrict__ counts, F value) {
+  int64_t lo[KDE_MAX_D], ext[KDE_MAX_D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    lo[k] = (int64_t)tc[k] * g.tile[k];
+    ext[k] = min((int64_t)g.tile[k], g.M[k] - lo[k]);
+  }
+  for (int c = c0; c < g.tile_cells; c += cstep) {
+    int r = c;
+    int64_t off = 0;
+    bool in = true;
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k) {
+      int x = r % g.tile[k];
+      r /= g.tile[k];
+      in &= x < ext[k];
+      off += (lo[k] + x) * g.stride[k];
+    }
+    if (in) counts[off] = value(c);
+  }
+}
+
+// Accumulate records [r0, r1) whose base tile is nbt into this tile's cells.
+// A weight w <= 2^32 is added as two 16-bit-aligned parts into separate
+// 32-bit words: lo += w mod 2^16, hi += w >> 16 (fire-and-forget shared
+// atomics).  A work item adds at most item_cap <= 65535 records to a cell,
+// so neither word can overflow; the cell is hi 2^16 + lo.
+template <int D>
+__device__ __forceinline__ void accumulate(const uint4* __restrict__ recs, unsigned r0, unsigned r1,
+                                           int nbt, const int* tc, const TileGeom& g,
+                                           unsigned* acc_lo, unsigned* acc_hi) {
+  constexpr int B = LocalBits<D>::value;
+  const unsigned lmask = B == 32 ? 0xffffffffu : ((1u << B) - 1u);
+  int nb[KDE_MAX_D];
+  tile_coords<D>(nbt, g, nb);
+  int shift[KDE_MAX_D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) shift[k] = (nb[k] - tc[k]) * g.tile[k];
+  for (unsigned r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const uint4 rec = recs[r];
+    const unsigned q[3] = {rec.y, rec.z, rec.w};
+    int rel[KDE_MAX_D];  // base node relative to this tile's first node
+#pragma unroll
+    for (int k = 0; k < D; ++k) rel[k] = (int)((rec.x >> (B * k)) & lmask) + shift[k];
+    unsigned long long w[1 << D];
+    corner_weights<D>(q, w);
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c) {
+      if (w[c] == 0) continue;
+      bool inside = true;
+      int lidx = 0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        int x = rel[k] + ((c >> (D - 1 - k)) & 1);
+        inside &= (x >= 0) && (x < g.tile[k]);
+        lidx = lidx * g.tile[k] + x;
+      }
+      if (inside) {
+        const unsigned wl = (unsigned)w[c] & 0xffffu, wh = (unsigned)(w[c] >> 16);
+        if (wl) atomicAdd(&acc_lo[lidx], wl);
+        if (wh) atomicAdd(&acc_hi[lidx], wh);
+      }
+    }
+  }
+}
+
+// Zero the cells of tiles that are split into several work items (their
+// items add into the counts with atomics); every other cell is stored once.
+template <int D>
+__global__ void __launch_bounds__(kGatherThreads)
+kde_bin_zero_split_kernel(const unsigned* __restrict__ item_start, TileGeom g,
+                          unsigned long long* __restrict__ counts) {
+  const int t = blockIdx.x;
+  if (item_start[t + 1] - item_start[t] <= 1) return;
+  int tc[KDE_MAX_D];
+  tile_coords<D>(t, g, tc);
+  store_tile<D>(tc, g, blockIdx.y * blockDim.x + threadIdx.x, gridDim.y * blockDim.x, counts,
+                [](int) { return 0ull; });
+}
+
+// One block per work item.  The records feeding tile t (own, then each
+// neighbour's face records, in for_each_source order) are numbered
+// 0 .. R-1; item j takes [j cap, (j+1) cap).  A tile with one item stores
+// its cells; items of a split tile add their nonzero cells with 64-bit
+// atomics (integer sums: the result does not depend on their order).
+template <int D>
+__global__ void __launch_bounds__(kGatherThreads)
+kde_bin_gather_kernel(const uint4* __restrict__ recs, const unsigned* __restrict__ starts,
+                      const unsigned* __restrict__ item_start, TileGeom g,
+                      unsigned long long* __restrict__ counts) {
+  extern __shared__ unsigned acc_words[];
+  unsigned* acc_lo = acc_words;
+  unsigned* acc_hi = acc_words + g.tile_cells;
+  const unsigned b = blockIdx.x;
+  if (b >= item_start[g.ntiles_total]) return;
+  int lo = 0, hi = g.ntiles_total - 1;  // largest t with item_start[t] <= b
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (item_start[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  const int t = lo;
+  const unsigned j = b - item_start[t];
+  const unsigned items = item_start[t + 1] - item_start[t];
+  int tc[KDE_MAX_D];
+  tile_coords<D>(t, g, tc);
+  for (int c = threadIdx.x; c < 2 * g.tile_cells; c += blockDim.x) acc_words[c] = 0;
+  __syncthreads();
+  const unsigned w0 = j * (unsigned)g.item_cap, w1 = w0 + (unsigned)g.item_cap;
+  unsigned v = 0;  // running record number
+  for_each_source<D>(tc, g, [&](int nbt, int, int key) {
+    const unsigned a = starts[key], len = starts[key + 1] - a;
+    const unsigned lo_v = max(v, w0), hi_v = min(v + len, w1);
+    if (lo_v < hi_v) accumulate<D>(recs, a + (lo_v - v), a + (hi_v - v), nbt, tc, g, acc_lo, acc_hi);
+    v += len;
+  });
+  __syncthreads();
+  auto cell = [&](int c) {
+    return ((unsigned long long)acc_hi[c] << 16) + (unsigned long long)acc_lo[c];
+  };
+  if (items == 1) {
+    store_tile<D>(tc, g, threadIdx.x, blockDim.x, counts, cell);
+  } else {
+    int64_t lo[KDE_MAX_D], ext[KDE_MAX_D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      lo[k] = (int64_t)tc[k] * g.tile[k];
+      ext[k] = min((int64_t)g.tile[k], g.M[k] - lo[k]);
+    }
+    for (int c = threadIdx.x; c < g.tile_cells; c += blockDim.x) {
+      const unsigned long long v = cell(c);
+      if (!v) continue;
+      int r = c;
+      int64_t off = 0;
+      bool in = true;
+#pragma unroll
+      for (int k = D - 1; k >= 0; --k) {
+        int x = r % g.tile[k];
+        r /= g.tile[k];
+        in &= x < ext[k];
+        off += (lo[k] + x) * g.stride[k];
+      }
+      if (in) atomicAdd(counts + off, v);
+    }
+  }
+}
+
+// Tile extents: start from 2048 / 32x64 / 16x16x32 cells and grow while the
+// key count (tiles x 2^d) exceeds what one block's shared histogram holds.
+bool choose_tiles(int d, const int64_t* M, int* tile, int* ntiles, int* nkeys) {
+  static const int init[3][3] = {{2048, 0, 0}, {32, 64, 0}, {16, 16, 32}};
+  for (int k = 0; k < d; ++k) tile[k] = init[d - 1][k];
+  for (int iter = 0; iter < 64; ++iter) {
+    int64_t nt = 1;
+    for (int k = 0; k < d; ++k) {
+      ntiles[k] = (int)((M[k] + tile[k] - 1) / tile[k]);
+      nt *= ntiles[k];
+    }
+    if (nt * (1 << d) <= kMaxKeys) {
+      *nkeys = (int)(nt << d);
+      return true;
+    }
+    // grow the axis with the most tiles, keeping shared memory per tile <= 128 KB
+    int best = -1;
+    for (int k = 0; k < d; ++k)
+      if (tile[k] < 256 && (best < 0 || ntiles[k] > ntiles[best])) best = k;
+    int64_t cells = 1;
+    for (int k = 0; k < d; ++k) cells *= tile[k];
+    if (best < 0 || cells * 2 * 8 > 128 * 1024) return false;
+    tile[best] *= 2;
+  }
+  return false;
+}
+
+struct TiledLayout {
+  int tile[KDE_MAX_D], ntiles[KDE_MAX_D], nkeys, nblocks, tile_cells, item_cap, ntiles_total;
+  int64_t chunk, max_items;
+  size_t off_mat, off_tot, off_starts, off_items, off_recs, total;
+};
+
+bool tiled_layout(int64_t n, int d, const int64_t* M, TiledLayout* t) {
+  if (!choose_tiles(d, M, t->tile, t->ntiles, &t->nkeys)) return false;
+  int64_t nb = (n + 4095) / 4096;
+  t->nblocks = (int)(nb < 1 ? 1 : (nb > kMaxBlocks ? kMaxBlocks : nb));
+  t->chunk = (n + t->nblocks - 1) / t->nblocks;
+  t->tile_cells = 1;
+  t->ntiles_total = 1;
+  for (int k = 0; k < d; ++k) {
+    t->tile_cells *= t->tile[k];
+    t->ntiles_total *= t->ntiles[k];
+  }
+  t->item_cap = d == 3 ? 32768 : 16384;  // <= 65535 (accumulator bound)
+  // A record feeds at most 2^d tiles: items <= tiles + 2^d n / cap.
+  const int64_t feeds = (int64_t)n << d;
+  t->max_items = t->ntiles_total + feeds / t->item_cap + 1;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  t->off_mat = 0;
+  t->off_tot = up((size_t)t->nblocks * t->nkeys * 4);
+  t->off_starts = t->off_tot + up((size_t)t->nkeys * 4);
+  t->off_items = t->off_starts + up((size_t)(t->nkeys + 1) * 4);
+  t->off_recs = t->off_items + up((size_t)(t->ntiles_total + 1) * 4);
+  t->total = t->off_recs + up((size_t)(n > 0 ? n : 1) * 16);
+  return true;
+}
+
 template <typename T>
-kde_status launch_bin(const T* X, int64_t n, int d, const double* lo, const double* hi,
-                      const int64_t* M, unsigned long long* counts, unsigned long long* n_out,
-                      cudaStream_t stream) {
+BinParams<T> make_params(int d, const double* lo, const double* hi, const int64_t* M,
+                         const TiledLayout* t) {
   BinParams<T> p{};
   int64_t stride = 1;
+  int ts = 1;
   for (int k = d - 1; k >= 0; --k) {
     double s = (double)(M[k] - 1) / (hi[k] - lo[k]);
     p.ax[k].lo = (T)lo[k];
     p.ax[k].s = (T)s;
     p.ax[k].top = (T)(M[k] - 1);
     p.ax[k].stride = stride;
-    p.ax[k].M = M[k];
+    p.ax[k].M = (int)M[k];
     stride *= M[k];
+    if (t) {
+      p.ax[k].tile = t->tile[k];
+      int lg = 0;
+      while ((1 << lg) < t->tile[k]) ++lg;
+      p.ax[k].tile_log2 = lg;
+      p.ax[k].ntiles = t->ntiles[k];
+      p.ax[k].tstride = ts;
+      ts *= t->ntiles[k];
+    }
   }
+  return p;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+  }
+  return sms;
+}
+
+template <typename T>
+kde_status launch_direct(const T* X, int64_t n, int d, const double* lo, const double* hi,
+                         const int64_t* M, unsigned long long* counts, int64_t cells,
+                         unsigned long long* n_out, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)cells * sizeof(int64_t), stream);
+  if (e != cudaSuccess) return kde::cuda_fail(e, "cudaMemsetAsync(counts)");
   if (n == 0) return KDE_OK;
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  BinParams<T> p = make_params<T>(d, lo, hi, M, nullptr);
   int64_t want = (n + 255) / 256;
-  int64_t cap = (int64_t)sms * 8;
+  int64_t cap = (int64_t)num_sms() * 8;
   int blocks = (int)(want < cap ? want : cap);
   kde::LaunchScope ls("kde_bin_kernel", stream);
   switch (d) {
@@ -139,18 +682,99 @@ kde_status launch_bin(const T* X, int64_t n, int d, const double* lo, const doub
     case 2: kde_bin_kernel<T, 2><<<blocks, 256, 0, stream>>>(X, n, p, counts, n_out); break;
     default: kde_bin_kernel<T, 3><<<blocks, 256, 0, stream>>>(X, n, p, counts, n_out); break;
   }
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   return e == cudaSuccess ? KDE_OK : kde::cuda_fail(e, "kde_bin_kernel launch");
 }
 
-}  // namespace
+template <typename F>
+cudaError_t allow_smem(F* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
-extern "C" kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, const double* lo,
-                              const double* hi, const int64_t* M, int64_t* counts,
-                              int64_t* n_outside, kde_stream_t stream) {
+template <typename T, int D>
+kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double* hi,
+                          const int64_t* M, unsigned long long* counts,
+                          unsigned long long* n_out, const TiledLayout& t, char* ws,
+                          cudaStream_t stream) {
+  BinParams<T> p = make_params<T>(D, lo, hi, M, &t);
+  unsigned* mat = (unsigned*)(ws + t.off_mat);
+  unsigned* tot = (unsigned*)(ws + t.off_tot);
+  unsigned* starts = (unsigned*)(ws + t.off_starts);
+  unsigned* item_start = (unsigned*)(ws + t.off_items);
+  uint4* recs = (uint4*)(ws + t.off_recs);
+  TileGeom g{};
+  for (int k = 0; k < D; ++k) {
+    g.M[k] = M[k];
+    g.stride[k] = p.ax[k].stride;
+    g.tile[k] = t.tile[k];
+    g.ntiles[k] = t.ntiles[k];
+    g.tstride[k] = p.ax[k].tstride;
+  }
+  g.ntiles_total = t.ntiles_total;
+  g.tile_cells = t.tile_cells;
+  g.item_cap = t.item_cap;
+  const size_t hist_smem = (size_t)t.nkeys * 4;
+  cudaError_t e;
+  {
+    auto* fn = kde_bin_hist_kernel<T, D>;
+    if ((e = allow_smem(fn, hist_smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
+    kde::LaunchScope ls("kde_bin_hist_kernel", stream);
+    fn<<<t.nblocks, kHistThreads, hist_smem, stream>>>(X, n, t.chunk, t.nkeys, p, mat, n_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_hist_kernel");
+  }
+  {
+    const size_t smem = (size_t)t.nblocks * (kScanKeys + 1) * 4;
+    kde::LaunchScope ls("kde_bin_scan_blocks_kernel", stream);
+    kde_bin_scan_blocks_kernel<<<(t.nkeys + kScanKeys - 1) / kScanKeys, kScanKeys * kScanSegs, smem,
+                                 stream>>>(mat, t.nblocks, t.nkeys, tot);
+    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scan_blocks_kernel");
+  }
+  {
+    kde::LaunchScope ls("kde_bin_scan_keys_kernel", stream);
+    kde_bin_scan_keys_kernel<D><<<1, 1024, 0, stream>>>(tot, t.nkeys, g, starts, item_start);
+    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scan_keys_kernel");
+  }
+  {
+    auto* fn = kde_bin_scatter_kernel<T, D>;
+    if ((e = allow_smem(fn, hist_smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
+    kde::LaunchScope ls("kde_bin_scatter_kernel", stream);
+    fn<<<t.nblocks, kHistThreads, hist_smem, stream>>>(X, n, t.chunk, t.nkeys, p, mat, starts, recs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scatter_kernel");
+  }
+  {
+    kde::LaunchScope ls("kde_bin_zero_split_kernel", stream);
+    kde_bin_zero_split_kernel<D><<<dim3((unsigned)t.ntiles_total, 4), kGatherThreads, 0, stream>>>(
+        item_start, g, counts);
+    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_zero_split_kernel");
+  }
+  const size_t gsmem = (size_t)t.tile_cells * 8;
+  {
+    auto* fn = kde_bin_gather_kernel<D>;
+    if ((e = allow_smem(fn, gsmem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
+    kde::LaunchScope ls("kde_bin_gather_kernel", stream);
+    fn<<<(unsigned)t.max_items, kGatherThreads, gsmem, stream>>>(recs, starts, item_start, g, counts);
+    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_gather_kernel");
+  }
+  return KDE_OK;
+}
+
+template <typename T>
+kde_status launch_tiled(const T* X, int64_t n, int d, const double* lo, const double* hi,
+                        const int64_t* M, unsigned long long* counts, unsigned long long* n_out,
+                        const TiledLayout& t, char* ws, cudaStream_t stream) {
+  switch (d) {
+    case 1: return launch_tiled_d<T, 1>(X, n, lo, hi, M, counts, n_out, t, ws, stream);
+    case 2: return launch_tiled_d<T, 2>(X, n, lo, hi, M, counts, n_out, t, ws, stream);
+    default: return launch_tiled_d<T, 3>(X, n, lo, hi, M, counts, n_out, t, ws, stream);
+  }
+}
+
+kde_status check_bin_args(int d, int x_dtype, int64_t n, const void* X, const double* lo,
+                          const double* hi, const int64_t* M, int64_t* cells_out) {
   using kde::fail;
   if (d < 1 || d > KDE_MAX_D) return fail(KDE_ERR_UNSUPPORTED, "d must be 1, 2 or 3");
-  if (!lo || !hi || !M || !counts) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (!lo || !hi || !M) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
   if (x_dtype != KDE_F32 && x_dtype != KDE_F64) return fail(KDE_ERR_INVALID_ARG, "bad x_dtype");
   if (n < 0 || n >= (int64_t(1) << 31)) return fail(KDE_ERR_INVALID_ARG, "need 0 <= n < 2^31");
   if (n > 0 && !X) return fail(KDE_ERR_INVALID_ARG, "X is NULL");
@@ -163,16 +787,52 @@ extern "C" kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, cons
     cells *= M[k];
     if (cells >= (int64_t(1) << 40)) return fail(KDE_ERR_INVALID_ARG, "grid too large");
   }
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)cells * sizeof(int64_t), s);
-  if (e != cudaSuccess) return kde::cuda_fail(e, "cudaMemsetAsync(counts)");
-  if (n_outside) {
-    e = cudaMemsetAsync(n_outside, 0, sizeof(int64_t), s);
-    if (e != cudaSuccess) return kde::cuda_fail(e, "cudaMemsetAsync(n_outside)");
+  *cells_out = cells;
+  return KDE_OK;
+}
+
+}  // namespace
+
+extern "C" kde_status kde_bin_workspace_bytes(int64_t n, int d, const int64_t* M, size_t* bytes) {
+  if (!bytes || !M || d < 1 || d > KDE_MAX_D || n < 0)
+    return kde::fail(KDE_ERR_INVALID_ARG, "bad argument");
+  TiledLayout t{};
+  if (!tiled_layout(n, d, M, &t)) {
+    *bytes = 0;
+    return kde::fail(KDE_ERR_UNSUPPORTED, "grid too large for the tiled binning path");
   }
+  *bytes = t.total;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, const double* lo,
+                              const double* hi, const int64_t* M, int64_t* counts,
+                              int64_t* n_outside, void* workspace, size_t workspace_bytes,
+                              kde_stream_t stream) {
+  using kde::fail;
+  int64_t cells = 0;
+  kde_status st = check_bin_args(d, x_dtype, n, X, lo, hi, M, &cells);
+  if (st != KDE_OK) return st;
+  if (!counts) return fail(KDE_ERR_INVALID_ARG, "counts is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
   auto* c = reinterpret_cast<unsigned long long*>(counts);
   auto* no = reinterpret_cast<unsigned long long*>(n_outside);
+  if (n_outside) {
+    cudaError_t e = cudaMemsetAsync(n_outside, 0, sizeof(int64_t), s);
+    if (e != cudaSuccess) return kde::cuda_fail(e, "cudaMemsetAsync(n_outside)");
+  }
+  if (!workspace) {
+    if (x_dtype == KDE_F32)
+      return launch_direct<float>((const float*)X, n, d, lo, hi, M, c, cells, no, s);
+    return launch_direct<double>((const double*)X, n, d, lo, hi, M, c, cells, no, s);
+  }
+  TiledLayout t{};
+  if (!tiled_layout(n, d, M, &t))
+    return fail(KDE_ERR_UNSUPPORTED, "grid too large for the tiled binning path");
+  if (cells >= (int64_t(1) << 32)) return fail(KDE_ERR_UNSUPPORTED, "tiled binning needs prod(M) < 2^32");
+  if (workspace_bytes < t.total) return fail(KDE_ERR_WORKSPACE, "binning workspace too small");
+  if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
   if (x_dtype == KDE_F32)
-    return launch_bin<float>((const float*)X, n, d, lo, hi, M, c, no, s);
-  return launch_bin<double>((const double*)X, n, d, lo, hi, M, c, no, s);
+    return launch_tiled<float>((const float*)X, n, d, lo, hi, M, c, no, t, (char*)workspace, s);
+  return launch_tiled<double>((const double*)X, n, d, lo, hi, M, c, no, t, (char*)workspace, s);
 }

@@ -52,7 +52,7 @@ EXPORTS = [
     "kde_plan_info_compute", "kde_plan_create", "kde_plan_get_info", "kde_plan_destroy",
     "kde_bin", "kde_kernel_grid", "kde_fft_eval", "kde_status_string", "kde_last_error",
     "kde_launch_count", "kde_profile_enable", "kde_profile_count", "kde_profile_entry",
-    "kde_fft_eval_noalloc",
+    "kde_fft_eval_noalloc", "kde_bin_workspace_bytes",
 ]
 
 _lib = None
@@ -74,7 +74,9 @@ def lib():
                                   ctypes.POINTER(vp)]
     L.kde_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     L.kde_plan_destroy.argtypes = [vp]
-    L.kde_bin.argtypes = [vp, ctypes.c_int, i64, ctypes.c_int, dp, dp, i64p, vp, vp, vp]
+    L.kde_bin.argtypes = [vp, ctypes.c_int, i64, ctypes.c_int, dp, dp, i64p, vp, vp, vp,
+                          ctypes.c_size_t, vp]
+    L.kde_bin_workspace_bytes.argtypes = [i64, ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_size_t)]
     L.kde_kernel_grid.argtypes = [vp, i64, vp, vp, ctypes.c_size_t, vp]
     L.kde_fft_eval.argtypes = [vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.kde_fft_eval_noalloc.argtypes = [vp, vp, vp, vp, vp]
@@ -87,7 +89,8 @@ def lib():
                                     dp, i64p]
     for name in ("kde_plan_info_compute", "kde_plan_create", "kde_plan_get_info",
                  "kde_plan_destroy", "kde_bin", "kde_kernel_grid", "kde_fft_eval",
-                 "kde_fft_eval_noalloc", "kde_profile_enable", "kde_profile_entry"):
+                 "kde_fft_eval_noalloc", "kde_profile_enable", "kde_profile_entry",
+                 "kde_bin_workspace_bytes"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -208,8 +211,23 @@ class Plan:
         return torch.empty(nbytes, dtype=torch.uint8, device=device)
 
 
-def kde_bin(X, lo, hi, M, counts=None, n_outside=None, stream=None):
-    """Linear binning into int64 counts (units 2^-32).  X: (n, d) float32/float64 CUDA tensor."""
+def kde_bin_workspace_bytes(n, d, M) -> int:
+    """Scratch bytes of the tiled binning method (host only)."""
+    b = ctypes.c_size_t()
+    _check(lib().kde_bin_workspace_bytes(int(n), int(d), _iarr(M), ctypes.byref(b)))
+    return int(b.value)
+
+
+def bin_workspace(n, d, M, device="cuda"):
+    import torch
+    return torch.empty(max(256, kde_bin_workspace_bytes(n, d, M)), dtype=torch.uint8, device=device)
+
+
+def kde_bin(X, lo, hi, M, counts=None, n_outside=None, workspace=None, method="tiled",
+            stream=None):
+    """Linear binning into int64 counts (units 2^-32).  X: (n, d) float32/float64
+    CUDA tensor.  method "tiled" (sort by tile, shared-memory accumulation; uses
+    a workspace, allocated here if not given) or "direct" (global atomics)."""
     import torch
     if not X.is_cuda or X.dim() != 2 or not X.is_contiguous():
         raise ValueError("X must be a contiguous (n, d) CUDA tensor")
@@ -219,10 +237,15 @@ def kde_bin(X, lo, hi, M, counts=None, n_outside=None, stream=None):
     M = tuple(int(m) for m in M)
     if counts is None:
         counts = torch.empty(M, dtype=torch.int64, device=X.device)
+    if method == "tiled" and workspace is None:
+        workspace = bin_workspace(n, d, M, X.device)
+    if method == "direct":
+        workspace = None
+    wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
     _check(lib().kde_bin(_ptr(X) if n else ctypes.c_void_p(0),
                          F32 if X.dtype == torch.float32 else F64, n, d,
                          _darr(lo), _darr(hi), _iarr(M), _ptr(counts), _ptr(n_outside),
-                         _stream_ptr(stream)))
+                         _ptr(workspace), wsb, _stream_ptr(stream)))
     return counts
 
 
@@ -300,19 +323,21 @@ class PreparedPath:
     with every C argument marshalled once, so that a call costs three C calls."""
 
     def __init__(self, plan: Plan, X, counts, Kspec, density, workspace, n=None,
-                 n_outside=None, stream=None):
+                 n_outside=None, bin_workspace=None, stream=None):
         import torch
         L = lib()
         self._L = L
         self.plan = plan
         s = _stream_ptr(stream)
         nX, d = X.shape
+        bwb = 0 if bin_workspace is None else bin_workspace.numel() * bin_workspace.element_size()
         self._bin = (_ptr(X), F32 if X.dtype == torch.float32 else F64, nX, d, _darr(plan.lo),
-                     _darr(plan.hi), _iarr(plan.M), _ptr(counts), _ptr(n_outside), s)
+                     _darr(plan.hi), _iarr(plan.M), _ptr(counts), _ptr(n_outside),
+                     _ptr(bin_workspace), bwb, s)
         wsb = workspace.numel() * workspace.element_size()
         self._kg = (plan.handle, int(nX if n is None else n), _ptr(Kspec), _ptr(workspace), wsb, s)
         self._ev = (plan.handle, _ptr(counts), _ptr(Kspec), _ptr(density), _ptr(workspace), wsb, s)
-        self._keep = (X, counts, Kspec, density, workspace, n_outside)
+        self._keep = (X, counts, Kspec, density, workspace, n_outside, bin_workspace)
 
     def __call__(self):
         _check(self._L.kde_bin(*self._bin))

@@ -33,11 +33,11 @@ def rel_err(gpu, ref):
     return float(np.max(np.abs(gpu - ref)) / np.max(np.abs(ref)))
 
 
-def run_gpu(K, w, **opts):
+def run_gpu(K, w, method="tiled", **opts):
     X = torch.from_numpy(np.ascontiguousarray(w.X)).cuda()
     plan = K.Plan(w.M, w.lo, w.hi, w.H, precision=w.precision, tau=w.tau, **opts)
     nout = torch.zeros(1, dtype=torch.int64, device="cuda")
-    counts = K.kde_bin(X, w.lo, w.hi, w.M, n_outside=nout)
+    counts = K.kde_bin(X, w.lo, w.hi, w.M, n_outside=nout, method=method)
     ws = plan.workspace()
     Ks = K.kde_kernel_grid(plan, w.n, workspace=ws)
     dens = K.kde_fft_eval(plan, counts, Ks, workspace=ws)
@@ -57,10 +57,11 @@ SMALL = [
 ]
 
 
+@pytest.mark.parametrize("method", ["tiled", "direct"])
 @pytest.mark.parametrize("d,M,prec", SMALL)
-def test_small_grids_every_node(K, d, M, prec):
+def test_small_grids_every_node(K, d, M, prec, method):
     w = W.small_case(100 + d * 7 + len(M) + M[0], d, M, n=3000, precision=prec)
-    dens, counts, nout, plan = run_gpu(K, w)
+    dens, counts, nout, plan = run_gpu(K, w, method=method)
     f, c_ref, L, nout_ref = oracle_full(w)
     assert plan.info.L == L
     assert nout == nout_ref
@@ -154,7 +155,8 @@ def test_wand_layout_exact_for_diagonal_H(K):
     assert rel_err(d_w, d_c) <= 1e-13
 
 
-def test_edge_samples_and_outside(K):
+@pytest.mark.parametrize("method", ["tiled", "direct"])
+def test_edge_samples_and_outside(K, method):
     """Samples exactly at lo/hi, on nodes, outside and NaN (binning spec)."""
     rng = np.random.default_rng(5)
     for dt, prec in [(np.float64, "f64"), (np.float32, "f32")]:
@@ -165,7 +167,7 @@ def test_edge_samples_and_outside(K):
         X[30:60] = (rng.integers(0, 20, size=(30, 2)) / 19.0).astype(dt)
         w = W.Workload("edges", X, np.array([[0.01, 0.004], [0.004, 0.008]]), np.zeros(2),
                        np.ones(2), (20, 23), prec)
-        dens, counts, nout, _ = run_gpu(K, w)
+        dens, counts, nout, _ = run_gpu(K, w, method=method)
         f, c_ref, _, nout_ref = oracle_full(w)
         assert nout == nout_ref and nout > 20
         assert np.array_equal(counts, c_ref)
@@ -174,10 +176,17 @@ def test_edge_samples_and_outside(K):
 
 def test_empty_input_and_errors(K):
     X = torch.empty((0, 2), dtype=torch.float32, device="cuda")
-    nout = torch.full((1,), 7, dtype=torch.int64, device="cuda")
-    counts = K.kde_bin(X, (0, 0), (1, 1), (5, 6), n_outside=nout)
-    torch.cuda.synchronize()
-    assert counts.abs().sum().item() == 0 and nout.item() == 0
+    for method in ("tiled", "direct"):
+        nout = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+        counts = torch.full((5, 6), 3, dtype=torch.int64, device="cuda")
+        K.kde_bin(X, (0, 0), (1, 1), (5, 6), counts=counts, n_outside=nout, method=method)
+        torch.cuda.synchronize()
+        assert counts.abs().sum().item() == 0 and nout.item() == 0
+    Xs = torch.zeros((10, 2), dtype=torch.float32, device="cuda")
+    tiny = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(K.KDEError) as e:
+        K.kde_bin(Xs, (0, 0), (1, 1), (5, 6), workspace=tiny[:16])
+    assert e.value.status == 4
     plan = K.Plan((5, 6), (0, 0), (1, 1), np.eye(2) * 0.01)
     with pytest.raises(K.KDEError) as e:
         K.kde_kernel_grid(plan, 0)
@@ -197,3 +206,57 @@ def test_deterministic_and_launch_count(K):
     assert np.array_equal(ca, cb)
     assert np.array_equal(a, b)
     assert mid - before >= 5       # twiddles, bin, kernel grid (2), eval (3)
+
+
+def test_tiled_binning_heavy_tiles(K):
+    """Most samples in one tile (split into several work items whose partial
+    tiles are merged), in 2-D and 3-D."""
+    rng = np.random.default_rng(41)
+    for d, M in [(2, (128, 256)), (3, (48, 48, 96))]:
+        n = 300_000
+        X = np.concatenate([rng.normal(0.3, 0.01, size=(n, d)), rng.uniform(0, 1, size=(n // 10, d))])
+        lo, hi = np.zeros(d), np.ones(d)
+        Xd = torch.from_numpy(np.ascontiguousarray(X.astype(np.float32))).cuda()
+        counts = K.kde_bin(Xd, lo, hi, M, method="tiled").cpu().numpy()
+        c_ref, _ = O.bin_linear(X.astype(np.float32), lo, hi, M)
+        assert np.array_equal(counts, c_ref)
+
+
+@pytest.mark.parametrize("name", ["kde2d_1024_f32", "kde3d_256_f32"])
+def test_tiled_and_direct_binning_identical(K, name):
+    """The two binning methods give bit-identical counts at full size, and the
+    tiled one writes every cell (the output starts as garbage)."""
+    w = W.WORKLOADS[name]()
+    X = torch.from_numpy(np.ascontiguousarray(w.X)).cuda()
+    a = torch.full(w.M, -5, dtype=torch.int64, device="cuda")
+    b = torch.full(w.M, -7, dtype=torch.int64, device="cuda")
+    K.kde_bin(X, w.lo, w.hi, w.M, counts=a, method="tiled")
+    K.kde_bin(X, w.lo, w.hi, w.M, counts=b, method="direct")
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert int(a.sum().item()) == w.n << 32
+
+
+@pytest.mark.parametrize("d,M", [(1, (5000,)), (2, (70, 150)), (3, (40, 35, 70))])
+def test_tiled_binning_tile_faces(K, d, M):
+    """Samples whose base node is the last node of a tile along one or more
+    axes feed the neighbouring tile; place many samples there and on nodes."""
+    rng = np.random.default_rng(31 + d)
+    tile = {1: (2048,), 2: (32, 64), 3: (16, 16, 32)}[d]
+    n = 20000
+    faces = [np.arange(t - 1, m - 1, t) for t, m in zip(tile, M)]
+    idx = np.stack([rng.choice(f, n) if len(f) else rng.integers(0, m - 1, n)
+                    for f, m in zip(faces, M)], axis=1).astype(np.float64)
+    frac = rng.uniform(0, 1, size=(n, d))
+    frac[: n // 4] = 0.0
+    frac[n // 4: n // 2] = rng.integers(0, 2, size=(n // 4, d)) * 0.999999
+    lo, hi = np.zeros(d), np.array(M, dtype=np.float64) - 1.0   # s = 1: t = x
+    X = np.clip(idx + frac, 0, hi)
+    rand = rng.uniform(0, hi, size=(n, d))
+    X = np.ascontiguousarray(np.concatenate([X, rand]))
+    Xd = torch.from_numpy(X).cuda()
+    nout = torch.zeros(1, dtype=torch.int64, device="cuda")
+    counts = K.kde_bin(Xd, lo, hi, M, n_outside=nout, method="tiled").cpu().numpy()
+    c_ref, nout_ref = O.bin_linear(X, lo, hi, M)
+    assert int(nout.item()) == nout_ref == 0
+    assert np.array_equal(counts, c_ref)

@@ -111,3 +111,10 @@ def test_plan_respects_P_min_and_modes():
                                      P_min=(256, 0), precision="f64")
     assert info.P[0] == 256 and info.precision == "f64"
     assert info.workspace_bytes > 0 and info.kspec_bytes == info.kspec_elems * 8
+
+
+def test_bin_workspace_sizes():
+    for d, M, n in [(1, (5000,), 10), (2, (1024, 1024), 10**6), (3, (256, 256, 256), 10**7)]:
+        b = kde.kde_bin_workspace_bytes(n, d, M)
+        assert b >= 16 * n
+        assert b < 16 * n + (64 << 20)
