@@ -81,7 +81,7 @@ typedef struct {
  *              (and >= P_min[k]); cyclic convolution of that length equals the
  *              linear one of Eq. 7 on [0, M_k) (Eq. 10, zero padding);
  *   Q          P[d-1]/2 + 1, the half-spectrum length of the last axis;
- *   kspec_elems   elements of the real kernel spectrum: P_0 ... P_{d-2} x Q;
+ *   kspec_elems   elements of the real kernel spectrum: P_0 ... P_{d-2} Q;
  *   workspace_bytes  scratch needed by kde_kernel_grid and kde_fft_eval;
  *   radix/nstages    the mixed-radix factorisation used per axis. */
 typedef struct {
@@ -150,8 +150,9 @@ kde_status kde_bin_workspace_bytes(int64_t n, int d, const int64_t* M, size_t* b
  * k_l = K_H(delta o l) / (n 2^32 prod P) for |l_k| <= L_k at wrapped index
  * l mod P_k (zero elsewhere) and transforms it.  k_{-l} = k_l, so the
  * spectrum is real; Kspec receives it as plan.kspec_elems values of the
- * plan's precision, laid out P_0 x ... x P_{d-2} x Q (half spectrum along the
- * last axis).  The 1/n of Eq. 2, the 2^-32 count unit and the 1/prod(P)
+ * plan's precision: the half spectrum along the last axis (Q values) for
+ * every leading frequency, stored with axis 0 contiguous, i.e. as the
+ * row-major array [P_1 ... P_{d-2}][Q][P_0] (d = 1: [Q]).  The 1/n of Eq. 2, the 2^-32 count unit and the 1/prod(P)
  * normalisation of Eq. 11/14 are folded in here.  n >= 1 is the number of
  * samples that were binned (the n of Eq. 2).  workspace: at least
  * plan.workspace_bytes of device scratch, 16-byte aligned. */

@@ -3,19 +3,23 @@
 //                    without the shift), transformed to its real spectrum K;
 //   kde_fft_eval:    C = F(c) of the zero-padded counts, S = C K,
 //                    s = F^{-1}(S), cropped to [0, M_k) (Eq. 14 shifted).
-// Passes (row-major, last axis contiguous, Q = P_last/2 + 1):
+// Passes (row-major, last axis contiguous, Q = P_last/2 + 1); every line is
+// transformed by a group of tpl threads (line_fft), tpl chosen per launch:
 //   rows_r2c  real rows -> half spectra; two real rows ride in one complex
 //             FFT (x + i y) and are separated afterwards;
-//   cols      FFT along a strided axis on a tile of T adjacent columns in
-//             shared memory: forward, forward-to-real (kernel spectrum),
-//             forward * K * inverse with crop (the middle axis), or inverse
-//             with crop;
+//   cols      FFT along a strided axis: a block stages W adjacent columns in
+//             shared memory with coalesced loads, each thread group
+//             transforms one, and the block stores them back coalesced.  Modes: forward,
+//             forward-to-real (the kernel spectrum, written with the
+//             transformed axis contiguous), forward * K * inverse with crop
+//             (the leading axis), inverse with crop;
 //   rows_c2r  half spectra -> real rows, cropped (two rows per complex FFT);
-//   line1d    d = 1: forward, * K, inverse and crop in one block.
+//   line1d    d = 1: forward, * K, inverse and crop.
 // Only lines that hold data are transformed and only lines that survive the
 // crop are inverse-transformed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -27,8 +31,6 @@
 
 namespace kde {
 namespace {
-
-constexpr int kThreads = 256;
 
 template <typename T>
 struct KGen {
@@ -68,34 +70,34 @@ __device__ __forceinline__ int wrapped_lag(int p, int P, int L) {
   return L + 1;
 }
 
+template <typename V>
+__device__ __forceinline__ void load_twiddles(V* tw_s, const V* tw, int P) {
+  for (int i = threadIdx.x; i < P; i += blockDim.x) tw_s[i] = tw[i];
+}
+
 template <typename T>
 struct RowsParams {
   using V = typename Cplx<T>::type;
   int64_t nrows;      // real rows
   int Min;            // data length of a row (zero-padded to P)
   int64_t in_stride;  // elements between input rows
-  int P, Q;
+  int Q;
   V* out;             // complex half spectra, row stride Q
   T* out_real;        // real part only (d = 1 kernel spectrum)
-  int G;              // complex lines (row pairs) per block
-  Radices rp;
+  int tpl;           // threads per line
+  LinePlan lp;
   const V* tw;
 };
-
-template <typename V, typename T>
-__device__ __forceinline__ void load_twiddles(V* tw_s, const V* tw, int P) {
-  for (int i = threadIdx.x; i < P; i += blockDim.x) tw_s[i] = tw[i];
-}
 
 // Split Z = F(x + i y) into X = F(x), Y = F(y) for k in [0, Q) and store.
 template <typename T>
 __device__ __forceinline__ void store_r2c(const RowsParams<T>& p, const typename Cplx<T>::type* z,
-                                          int64_t r0, int g) {
+                                          int64_t r0, const LineGroup& g) {
   using V = typename Cplx<T>::type;
-  const int P = p.P;
-  for (int k = threadIdx.x; k < p.Q; k += blockDim.x) {
-    V zk = z[g * P + k];
-    V zm = z[g * P + (k == 0 ? 0 : P - k)];
+  const int P = p.lp.N;
+  for (int k = g.lt; k < p.Q; k += g.tpl) {
+    V zk = z[k];
+    V zm = z[k == 0 ? 0 : P - k];
     V X = mk<V>(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
     V Y = mk<V>(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x));
     if (p.out_real) {
@@ -107,65 +109,78 @@ __device__ __forceinline__ void store_r2c(const RowsParams<T>& p, const typename
   }
 }
 
-// Counts rows -> half spectra.  Counts are int64 in units of 2^-32; the unit
-// is folded into the kernel spectrum, so they enter the transform unscaled.
+// The line group of this thread (line li of the block).
+__device__ __forceinline__ LineGroup line_group(int tpl, int& li) {
+  li = threadIdx.x / tpl;
+  return LineGroup{(int)threadIdx.x - li * tpl, tpl, 1 + li};
+}
+
+// Counts rows -> half spectra, one row pair per line group.  Counts are int64
+// in units of 2^-32; the unit is folded into the kernel spectrum.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(256)
 kde_rows_r2c_counts_kernel(const long long* __restrict__ counts, RowsParams<T> p) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = p.lp.N;
   V* tw_s = reinterpret_cast<V*>(smem_raw);
-  V* a = tw_s + p.P;
-  V* b = a + p.G * p.P;
-  load_twiddles<V, T>(tw_s, p.tw, p.P);
-  const int64_t pair0 = (int64_t)blockIdx.x * p.G;
-  for (int idx = threadIdx.x; idx < p.G * p.P; idx += blockDim.x) {
-    int g = idx / p.P, x = idx - g * p.P;
-    int64_t r0 = 2 * (pair0 + g);
-    T re = 0, im = 0;
-    if (x < p.Min && r0 < p.nrows) {
-      re = (T)counts[r0 * p.in_stride + x];
-      if (r0 + 1 < p.nrows) im = (T)counts[(r0 + 1) * p.in_stride + x];
-    }
-    a[idx] = mk<V>(re, im);
-  }
+  int li;
+  const LineGroup g = line_group(p.tpl, li);
+  V* a = tw_s + P + 2 * li * P;
+  V* b = a + P;
+  load_twiddles(tw_s, p.tw, P);
   __syncthreads();
-  V* z = fft_lines<V, false, true>(a, b, p.rp, p.G, 1, p.P, tw_s);
-  for (int g = 0; g < p.G; ++g) {
-    int64_t r0 = 2 * (pair0 + g);
-    if (r0 < p.nrows) store_r2c<T>(p, z, r0, g);
+  const int64_t r0 = 2 * ((int64_t)blockIdx.x * (blockDim.x / p.tpl) + li);
+  if (r0 >= p.nrows) return;
+  const long long* c0 = counts + r0 * p.in_stride;
+  const long long* c1 = c0 + p.in_stride;
+  const bool two = r0 + 1 < p.nrows;
+#pragma unroll 4
+  for (int x = g.lt; x < P; x += g.tpl) {
+    T re = 0, im = 0;
+    if (x < p.Min) {
+      re = (T)__ldg(c0 + x);
+      if (two) im = (T)__ldg(c1 + x);
+    }
+    a[x] = mk<V>(re, im);
   }
+  g.sync();
+  V* z = line_fft<V, false>(a, b, p.lp, tw_s, g);
+  store_r2c<T>(p, z, r0, g);
 }
 
 // Kernel-grid rows -> half spectra (or real spectrum for d = 1).  Row r
 // enumerates the leading lags (l_0, ..., l_{d-2}) with |l_k| <= L_k; the last
 // axis holds lag l at position l mod P.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(256)
 kde_rows_r2c_kgen_kernel(KGen<T> gen, RowsParams<T> p) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = p.lp.N;
   V* tw_s = reinterpret_cast<V*>(smem_raw);
-  V* a = tw_s + p.P;
-  V* b = a + p.G * p.P;
-  load_twiddles<V, T>(tw_s, p.tw, p.P);
-  const int64_t pair0 = (int64_t)blockIdx.x * p.G;
+  int li;
+  const LineGroup g = line_group(p.tpl, li);
+  V* a = tw_s + P + 2 * li * P;
+  V* b = a + P;
+  load_twiddles(tw_s, p.tw, P);
+  __syncthreads();
+  const int64_t r0 = 2 * ((int64_t)blockIdx.x * (blockDim.x / p.tpl) + li);
+  if (r0 >= p.nrows) return;
   const int dl = gen.d - 1;  // index of the last axis
-  for (int idx = threadIdx.x; idx < p.G * p.P; idx += blockDim.x) {
-    int g = idx / p.P, x = idx - g * p.P;
-    int64_t r0 = 2 * (pair0 + g);
+  for (int x = g.lt; x < P; x += g.tpl) {
     T val[2] = {0, 0};
-    int ll = wrapped_lag(x, p.P, gen.L[dl]);
+    const int ll = wrapped_lag(x, P, gen.L[dl]);
     if (ll <= gen.L[dl]) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        int64_t r = r0 + h;
+        const int64_t r = r0 + h;
         if (r >= p.nrows) break;
         int l[KDE_MAX_D] = {0, 0, 0};
         if (gen.d == 2) {
           l[0] = (int)r - gen.L[0];
         } else if (gen.d == 3) {
-          int w1 = 2 * gen.L[1] + 1;
+          const int w1 = 2 * gen.L[1] + 1;
           l[0] = (int)(r / w1) - gen.L[0];
           l[1] = (int)(r % w1) - gen.L[1];
         }
@@ -173,14 +188,11 @@ kde_rows_r2c_kgen_kernel(KGen<T> gen, RowsParams<T> p) {
         val[h] = kernel_value<T>(gen, l);
       }
     }
-    a[idx] = mk<V>(val[0], val[1]);
+    a[x] = mk<V>(val[0], val[1]);
   }
-  __syncthreads();
-  V* z = fft_lines<V, false, true>(a, b, p.rp, p.G, 1, p.P, tw_s);
-  for (int g = 0; g < p.G; ++g) {
-    int64_t r0 = 2 * (pair0 + g);
-    if (r0 < p.nrows) store_r2c<T>(p, z, r0, g);
-  }
+  g.sync();
+  V* z = line_fft<V, false>(a, b, p.lp, tw_s, g);
+  store_r2c<T>(p, z, r0, g);
 }
 
 template <typename T>
@@ -190,9 +202,9 @@ struct C2RParams {
   T* out;             // real rows, row stride Mout
   int64_t nrows;
   int Mout;
-  int P, Q;
-  int G;
-  Radices rp;
+  int Q;
+  int tpl;
+  LinePlan lp;
   const V* tw;
 };
 
@@ -200,61 +212,64 @@ struct C2RParams {
 // the full length from Hermitian symmetry: Z_k = conj(X_{P-k}) + i conj(Y_{P-k})
 // for k >= Q; then x + i y = F^{-1}(Z).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) kde_rows_c2r_kernel(C2RParams<T> p) {
+__global__ void __launch_bounds__(256) kde_rows_c2r_kernel(C2RParams<T> p) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = p.lp.N;
   V* tw_s = reinterpret_cast<V*>(smem_raw);
-  V* a = tw_s + p.P;
-  V* b = a + p.G * p.P;
-  load_twiddles<V, T>(tw_s, p.tw, p.P);
-  const int64_t pair0 = (int64_t)blockIdx.x * p.G;
-  for (int idx = threadIdx.x; idx < p.G * p.P; idx += blockDim.x) {
-    int g = idx / p.P, k = idx - g * p.P;
-    int64_t r0 = 2 * (pair0 + g);
-    V z = mk<V>(0, 0);
-    if (r0 < p.nrows) {
-      bool lo_half = k < p.Q;
-      int kk = lo_half ? k : p.P - k;
-      V X = p.in[r0 * p.Q + kk];
-      V Y = (r0 + 1 < p.nrows) ? p.in[(r0 + 1) * p.Q + kk] : mk<V>(0, 0);
-      z = lo_half ? mk<V>(X.x - Y.y, X.y + Y.x) : mk<V>(X.x + Y.y, Y.x - X.y);
-    }
-    a[idx] = z;
-  }
+  int li;
+  const LineGroup g = line_group(p.tpl, li);
+  V* a = tw_s + P + 2 * li * P;
+  V* b = a + P;
+  load_twiddles(tw_s, p.tw, P);
   __syncthreads();
-  V* z = fft_lines<V, true, true>(a, b, p.rp, p.G, 1, p.P, tw_s);
-  for (int idx = threadIdx.x; idx < p.G * p.Mout; idx += blockDim.x) {
-    int g = idx / p.Mout, m = idx - g * p.Mout;
-    int64_t r0 = 2 * (pair0 + g);
-    if (r0 >= p.nrows) continue;
-    V v = z[g * p.P + m];
-    p.out[r0 * p.Mout + m] = v.x;
-    if (r0 + 1 < p.nrows) p.out[(r0 + 1) * p.Mout + m] = v.y;
+  const int64_t r0 = 2 * ((int64_t)blockIdx.x * (blockDim.x / p.tpl) + li);
+  if (r0 >= p.nrows) return;
+  const bool two = r0 + 1 < p.nrows;
+  const V* x0 = p.in + r0 * p.Q;
+  const V* x1 = x0 + p.Q;
+#pragma unroll 4
+  for (int k = g.lt; k < p.Q; k += g.tpl) {
+    V X = x0[k];
+    V Y = two ? x1[k] : mk<V>(0, 0);
+    a[k] = mk<V>(X.x - Y.y, X.y + Y.x);
+    if (k > 0 && P - k >= p.Q) a[P - k] = mk<V>(X.x + Y.y, Y.x - X.y);
+  }
+  g.sync();
+  V* z = line_fft<V, true>(a, b, p.lp, tw_s, g);
+  T* o0 = p.out + r0 * p.Mout;
+  T* o1 = o0 + p.Mout;
+  for (int m = g.lt; m < p.Mout; m += g.tpl) {
+    V v = z[m];
+    o0[m] = v.x;
+    if (two) o1[m] = v.y;
   }
 }
 
 // d = 1: counts -> F -> * K (real, even: K_k = K_{P-k}) -> F^{-1} -> crop.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(256)
 kde_line1d_kernel(const long long* __restrict__ counts, const T* __restrict__ K, T* out, int M,
-                  int P, int Q, Radices rp, const typename Cplx<T>::type* tw) {
+                  int Q, LinePlan lp, const typename Cplx<T>::type* tw) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = lp.N;
   V* tw_s = reinterpret_cast<V*>(smem_raw);
   V* a = tw_s + P;
   V* b = a + P;
-  load_twiddles<V, T>(tw_s, tw, P);
-  for (int x = threadIdx.x; x < P; x += blockDim.x) a[x] = mk<V>(x < M ? (T)counts[x] : T(0), 0);
+  const LineGroup g{(int)threadIdx.x, (int)blockDim.x, 1};
+  load_twiddles(tw_s, tw, P);
+  for (int x = g.lt; x < P; x += g.tpl) a[x] = mk<V>(x < M ? (T)counts[x] : T(0), 0);
   __syncthreads();
-  V* z = fft_lines<V, false, true>(a, b, rp, 1, 1, P, tw_s);
-  for (int k = threadIdx.x; k < P; k += blockDim.x) {
+  V* z = line_fft<V, false>(a, b, lp, tw_s, g);
+  for (int k = g.lt; k < P; k += g.tpl) {
     T kv = K[k < Q ? k : P - k];
     z[k] = mk<V>(z[k].x * kv, z[k].y * kv);
   }
-  __syncthreads();
+  g.sync();
   V* other = (z == a) ? b : a;
-  V* y = fft_lines<V, true, true>(z, other, rp, 1, 1, P, tw_s);
-  for (int m = threadIdx.x; m < M; m += blockDim.x) out[m] = y[m].x;
+  V* y = line_fft<V, true>(z, other, lp, tw_s, g);
+  for (int m = g.lt; m < M; m += g.tpl) out[m] = y[m].x;
 }
 
 enum ColMode { COL_FWD = 0, COL_FWD_REAL = 1, COL_MID = 2, COL_INV = 3 };
@@ -264,71 +279,106 @@ struct ColsParams {
   using V = typename Cplx<T>::type;
   const V* in;     // [O][Nin][S]
   V* out;          // [O][Nout][S]
-  T* out_real;     // COL_FWD_REAL: [O][P][S]
-  const T* K;      // COL_MID: [P][S] real spectrum
+  T* out_real;     // COL_FWD_REAL: [O][S][P] (transformed axis contiguous)
+  const T* K;      // COL_MID: [S][P] real spectrum, transformed axis contiguous
   int64_t S;
-  int Nin, Nout, P;
+  int Nin, Nout;
   int Lw;          // >= 0: input row n holds lag n - Lw (wrapped); < 0: row n at position n
-  int Tc;          // columns per block
-  Radices rp;
+  int tpl;         // threads per column
+  LinePlan lp;
   const V* tw;
 };
 
+// W adjacent columns (s0 .. s0+W-1) of outer slab o, one line group each.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads) kde_cols_kernel(ColsParams<T> p) {
+__device__ __forceinline__ void cols_body(const ColsParams<T>& p) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = p.lp.N;
+  const int W = blockDim.x / p.tpl;
   V* tw_s = reinterpret_cast<V*>(smem_raw);
-  V* a = tw_s + p.P;
-  V* b = a + p.Tc * p.P;
-  load_twiddles<V, T>(tw_s, p.tw, p.P);
+  // Column t owns lines[t LS ..): its buffer, then its scratch.  LS = 2P + 1
+  // puts the W columns of one position in different banks.
+  const int LS = 2 * P + 1;
+  V* lines = tw_s + P;
+  int li;
+  const LineGroup g = line_group(p.tpl, li);
+  load_twiddles(tw_s, p.tw, P);
   const int64_t o = blockIdx.y;
-  const int64_t s0 = (int64_t)blockIdx.x * p.Tc;
-  const int Tc = p.Tc;
+  const int64_t s0 = (int64_t)blockIdx.x * W;
   const V* in = p.in + o * (int64_t)p.Nin * p.S;
-  for (int idx = threadIdx.x; idx < p.P * Tc; idx += blockDim.x) {
-    int pos = idx / Tc, t = idx - pos * Tc;
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < P * W; idx += blockDim.x) {
+    const int pos = idx / W, t = idx - pos * W;
     int n;
     if (p.Lw >= 0) {
-      int l = wrapped_lag(pos, p.P, p.Lw);
+      const int l = wrapped_lag(pos, P, p.Lw);
       n = (l <= p.Lw) ? l + p.Lw : p.Nin;
     } else {
       n = pos;
     }
-    int64_t s = s0 + t;
+    const int64_t s = s0 + t;
     V v = mk<V>(0, 0);
     if (n < p.Nin && s < p.S) v = in[(int64_t)n * p.S + s];
-    a[idx] = v;
+    lines[t * LS + pos] = v;
   }
   __syncthreads();
-  V* z;
-  if (MODE == COL_INV) {
-    z = fft_lines<V, true, false>(a, b, p.rp, Tc, Tc, 1, tw_s);
-  } else {
-    z = fft_lines<V, false, false>(a, b, p.rp, Tc, Tc, 1, tw_s);
-  }
-  if (MODE == COL_MID) {
-    for (int idx = threadIdx.x; idx < p.P * Tc; idx += blockDim.x) {
-      int pos = idx / Tc, t = idx - pos * Tc;
-      int64_t s = s0 + t;
-      T kv = (s < p.S) ? p.K[(int64_t)pos * p.S + s] : T(0);
-      z[idx] = mk<V>(z[idx].x * kv, z[idx].y * kv);
-    }
-    __syncthreads();
-    V* other = (z == a) ? b : a;
-    z = fft_lines<V, true, false>(z, other, p.rp, Tc, Tc, 1, tw_s);
-  }
-  const int nout = (MODE == COL_FWD || MODE == COL_FWD_REAL) ? p.P : p.Nout;
-  for (int idx = threadIdx.x; idx < nout * Tc; idx += blockDim.x) {
-    int pos = idx / Tc, t = idx - pos * Tc;
-    int64_t s = s0 + t;
-    if (s >= p.S) continue;
-    int64_t off = (o * nout + pos) * p.S + s;
-    if (MODE == COL_FWD_REAL)
-      p.out_real[off] = z[idx].x;
+  const int64_t s = s0 + li;
+  V* a = lines + li * LS;
+  V* b = a + P;
+  V* z = a;
+  if (s < p.S) {
+    if (MODE == COL_INV)
+      z = line_fft<V, true>(a, b, p.lp, tw_s, g);
     else
-      p.out[off] = z[idx];
+      z = line_fft<V, false>(a, b, p.lp, tw_s, g);
+    if (MODE == COL_MID) {
+      const T* Kc = p.K + s * P;
+      for (int k = g.lt; k < P; k += g.tpl) {
+        const T kv = __ldg(Kc + k);
+        z[k] = mk<V>(z[k].x * kv, z[k].y * kv);
+      }
+      g.sync();
+      V* other = (z == a) ? b : a;
+      z = line_fft<V, true>(z, other, p.lp, tw_s, g);
+    }
+    if (MODE == COL_FWD_REAL) {
+      T* dst = p.out_real + (o * p.S + s) * P;
+      for (int k = g.lt; k < P; k += g.tpl) dst[k] = z[k].x;
+    }
   }
+  if (MODE == COL_FWD_REAL) return;
+  // Every warp's result sits in the same buffer of its pair (same plan).
+  const int zoff = (z == a) ? 0 : P;
+  __syncthreads();
+  const int nout = (MODE == COL_FWD) ? P : p.Nout;
+  for (int idx = threadIdx.x; idx < nout * W; idx += blockDim.x) {
+    const int pos = idx / W, t = idx - pos * W;
+    const int64_t ss = s0 + t;
+    if (ss >= p.S) continue;
+    p.out[(o * nout + pos) * p.S + ss] = lines[t * LS + zoff + pos];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kde_cols_fwd_kernel(ColsParams<T> p) {
+  cols_body<T, COL_FWD>(p);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) kde_cols_kgen_kernel(ColsParams<T> p) {
+  cols_body<T, COL_FWD>(p);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) kde_cols_kgen_real_kernel(ColsParams<T> p) {
+  cols_body<T, COL_FWD_REAL>(p);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) kde_cols_mid_kernel(ColsParams<T> p) {
+  cols_body<T, COL_MID>(p);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) kde_cols_inv_kernel(ColsParams<T> p) {
+  cols_body<T, COL_INV>(p);
 }
 
 // ---------------------------------------------------------------------------
@@ -347,12 +397,21 @@ cudaError_t allow_smem(F* fn) {
   return e;
 }
 
-Radices radices_of(const kde_plan_info& info, int k) {
-  Radices r{};
-  r.n = (int)info.P[k];
-  r.nst = info.nstages[k];
-  for (int s = 0; s < r.nst; ++s) r.r[s] = info.radix[k][s];
-  return r;
+LinePlan line_plan(const kde_plan_info& info, int k) {
+  LinePlan lp{};
+  lp.N = (int)info.P[k];
+  lp.nst = info.nstages[k];
+  int Ns = 1;
+  for (int s = 0; s < lp.nst; ++s) {
+    Stage& st = lp.st[s];
+    st.R = info.radix[k][s];
+    st.Ns = Ns;
+    st.nb = lp.N / st.R;
+    st.twstep = lp.N / (Ns * st.R);
+    st.magic = (unsigned)((1ull << 32) / (unsigned)Ns + 1ull);
+    Ns *= st.R;
+  }
+  return lp;
 }
 
 template <typename T>
@@ -371,74 +430,67 @@ static int num_sms() {
   return sms;
 }
 
-// Row pairs per block: enough lines to give the block work, few enough that
-// the grid still covers every SM twice where possible, and within shared memory.
+// Launch shape for `lines` lines of length P: threads per line (tpl) grows
+// with the work per line and shrinks as lines multiply, aiming at about 16
+// resident warps per SM; blocks hold up to 256 threads (lines * tpl) within
+// shared memory (twiddles plus two buffers per line).
+struct LineShape {
+  int tpl, lpb;
+};
+
 template <typename T>
-int rows_per_block(int64_t pairs, int P) {
-  size_t cb = sizeof(typename Cplx<T>::type);
-  int g_smem = (int)((kSmemMax / cb - P) / (2 * (size_t)P));
-  int g = (int)std::max<int64_t>(1, std::min<int64_t>(4096 / P, pairs / (2 * num_sms())));
-  g = std::max(1, std::min(g, std::min(g_smem, 8)));
-  return g;
+LineShape line_shape(int64_t lines, int P, int lpb_min) {
+  const size_t cb = sizeof(typename Cplx<T>::type);
+  const int64_t target_warps = 16LL * num_sms();
+  int64_t per_line = (target_warps + lines - 1) / std::max<int64_t>(1, lines);
+  int tpl = 32;
+  // about one radix-8 butterfly (P/8 per stage) per thread at most, and
+  // room for lpb_min lines in a 256-thread block
+  const int tpl_max = std::max(32, std::min(256 / lpb_min, ((P / 8 + 31) / 32) * 32));
+  while (tpl * 2 <= tpl_max && tpl / 32 < per_line) tpl *= 2;
+  int lpb = std::max(1, 256 / tpl);
+  const int lpb_smem = (int)((kSmemMax / cb - P) / (2 * (size_t)P + 1));
+  lpb = std::max(1, std::min(lpb, lpb_smem));
+  // keep at least two blocks per SM where the line count allows
+  while (lpb > lpb_min && (lines + lpb - 1) / lpb < 2 * num_sms()) lpb /= 2;
+  lpb = std::max(lpb, std::min(lpb_min, lpb_smem));
+  return {tpl, lpb};
 }
 
 template <typename T>
-kde_status launch_rows_r2c_counts(const long long* counts, RowsParams<T> p, cudaStream_t st) {
-  int64_t pairs = (p.nrows + 1) / 2;
-  p.G = rows_per_block<T>(pairs, p.P);
-  size_t smem = (size_t)(1 + 2 * p.G) * p.P * sizeof(typename Cplx<T>::type);
-  auto* fn = kde_rows_r2c_counts_kernel<T>;
-  cudaError_t e = allow_smem(fn);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-  LaunchScope ls("kde_rows_r2c_counts_kernel", st);
-  fn<<<(unsigned)((pairs + p.G - 1) / p.G), kThreads, smem, st>>>(counts, p);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? KDE_OK : cuda_fail(e, "kde_rows_r2c_counts_kernel");
+size_t line_smem(int P, int W) {
+  return ((size_t)(1 + 2 * W) * P + W) * sizeof(typename Cplx<T>::type);
 }
 
-template <typename T>
-kde_status launch_rows_r2c_kgen(const KGen<T>& gen, RowsParams<T> p, cudaStream_t st) {
-  int64_t pairs = (p.nrows + 1) / 2;
-  p.G = rows_per_block<T>(pairs, p.P);
-  size_t smem = (size_t)(1 + 2 * p.G) * p.P * sizeof(typename Cplx<T>::type);
-  auto* fn = kde_rows_r2c_kgen_kernel<T>;
+// Row kernels take the launch shape in their parameters (p.tpl).
+template <typename T, typename Kern, typename Params, typename... Args>
+kde_status launch_rows(Kern* fn, const char* name, int64_t nrows, Params& p, cudaStream_t st,
+                       Args... args) {
+  const int P = p.lp.N;
+  const int64_t pairs = (nrows + 1) / 2;
+  const LineShape sh = line_shape<T>(pairs, P, 1);
+  p.tpl = sh.tpl;
   cudaError_t e = allow_smem(fn);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-  LaunchScope ls("kde_rows_r2c_kgen_kernel", st);
-  fn<<<(unsigned)((pairs + p.G - 1) / p.G), kThreads, smem, st>>>(gen, p);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? KDE_OK : cuda_fail(e, "kde_rows_r2c_kgen_kernel");
-}
-
-template <typename T>
-kde_status launch_rows_c2r(C2RParams<T> p, cudaStream_t st) {
-  int64_t pairs = (p.nrows + 1) / 2;
-  p.G = rows_per_block<T>(pairs, p.P);
-  size_t smem = (size_t)(1 + 2 * p.G) * p.P * sizeof(typename Cplx<T>::type);
-  auto* fn = kde_rows_c2r_kernel<T>;
-  cudaError_t e = allow_smem(fn);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-  LaunchScope ls("kde_rows_c2r_kernel", st);
-  fn<<<(unsigned)((pairs + p.G - 1) / p.G), kThreads, smem, st>>>(p);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? KDE_OK : cuda_fail(e, "kde_rows_c2r_kernel");
-}
-
-template <typename T, int MODE>
-kde_status launch_cols(ColsParams<T> p, int64_t O, cudaStream_t st, const char* name) {
-  size_t cb = sizeof(typename Cplx<T>::type);
-  // Columns per block: a 32-byte run of each row per tile (4 complex64 or 2
-  // complex128), fewer if shared memory is short.
-  int Tc = (int)(32 / cb);
-  while (Tc > 1 && (size_t)(1 + 2 * Tc) * p.P * cb > kSmemMax) Tc /= 2;
-  p.Tc = Tc;
-  size_t smem = (size_t)(1 + 2 * Tc) * p.P * cb;
-  auto* fn = kde_cols_kernel<T, MODE>;
-  cudaError_t e = allow_smem(fn);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-  dim3 grid((unsigned)((p.S + Tc - 1) / Tc), (unsigned)O);
   LaunchScope ls(name, st);
-  fn<<<grid, kThreads, smem, st>>>(p);
+  fn<<<(unsigned)((pairs + sh.lpb - 1) / sh.lpb), sh.tpl * sh.lpb, line_smem<T>(P, sh.lpb), st>>>(
+      args..., p);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? KDE_OK : cuda_fail(e, name);
+}
+
+template <typename T>
+kde_status launch_cols(void (*fn)(ColsParams<T>), ColsParams<T> p, int64_t O, cudaStream_t st,
+                       const char* name) {
+  const int P = p.lp.N;
+  const LineShape sh = line_shape<T>(p.S * O, P, 2);
+  p.tpl = sh.tpl;
+  const int W = sh.lpb;
+  cudaError_t e = allow_smem(fn);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  dim3 grid((unsigned)((p.S + W - 1) / W), (unsigned)O);
+  LaunchScope ls(name, st);
+  fn<<<grid, sh.tpl * W, line_smem<T>(P, W), st>>>(p);
   e = cudaGetLastError();
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, name);
 }
@@ -463,22 +515,22 @@ kde_status kernel_grid_impl(kde_plan_s* plan, int64_t n, void* Kspec, void* ws, 
   gen.C = (T)C;
   const int dl = d - 1;
   RowsParams<T> rp{};
-  rp.P = (int)I.P[dl];
   rp.Q = (int)I.Q;
   rp.Min = 0;
-  rp.rp = radices_of(I, dl);
+  rp.lp = line_plan(I, dl);
   rp.tw = twiddles<T>(plan, dl);
   if (d == 1) {
     rp.nrows = 1;
     rp.out_real = (T*)Kspec;
-    return launch_rows_r2c_kgen<T>(gen, rp, st);
+    return launch_rows<T>(kde_rows_r2c_kgen_kernel<T>, "kde_rows_r2c_kgen_kernel", 1, rp, st, gen);
   }
   V* t1 = (V*)ws;
   int64_t rows = 1;
   for (int k = 0; k < d - 1; ++k) rows *= 2 * I.L[k] + 1;
   rp.nrows = rows;
   rp.out = t1;
-  kde_status s = launch_rows_r2c_kgen<T>(gen, rp, st);
+  kde_status s = launch_rows<T>(kde_rows_r2c_kgen_kernel<T>, "kde_rows_r2c_kgen_kernel", rows, rp,
+                                st, gen);
   if (s != KDE_OK) return s;
   if (d == 2) {
     ColsParams<T> cp{};
@@ -486,11 +538,10 @@ kde_status kernel_grid_impl(kde_plan_s* plan, int64_t n, void* Kspec, void* ws, 
     cp.out_real = (T*)Kspec;
     cp.S = I.Q;
     cp.Nin = (int)(2 * I.L[0] + 1);
-    cp.P = (int)I.P[0];
     cp.Lw = (int)I.L[0];
-    cp.rp = radices_of(I, 0);
+    cp.lp = line_plan(I, 0);
     cp.tw = twiddles<T>(plan, 0);
-    return launch_cols<T, COL_FWD_REAL>(cp, 1, st, "kde_cols_kgen_real_kernel");
+    return launch_cols<T>(kde_cols_kgen_real_kernel<T>, cp, 1, st, "kde_cols_kgen_real_kernel");
   }
   // d == 3: axis 1 (wrapped) into t2, then axis 0 (wrapped) to the real spectrum.
   V* t2 = t1 + rows * I.Q;
@@ -499,22 +550,20 @@ kde_status kernel_grid_impl(kde_plan_s* plan, int64_t n, void* Kspec, void* ws, 
   c1.out = t2;
   c1.S = I.Q;
   c1.Nin = (int)(2 * I.L[1] + 1);
-  c1.P = (int)I.P[1];
   c1.Lw = (int)I.L[1];
-  c1.rp = radices_of(I, 1);
+  c1.lp = line_plan(I, 1);
   c1.tw = twiddles<T>(plan, 1);
-  s = launch_cols<T, COL_FWD>(c1, 2 * I.L[0] + 1, st, "kde_cols_kgen_kernel");
+  s = launch_cols<T>(kde_cols_kgen_kernel<T>, c1, 2 * I.L[0] + 1, st, "kde_cols_kgen_kernel");
   if (s != KDE_OK) return s;
   ColsParams<T> c0{};
   c0.in = t2;
   c0.out_real = (T*)Kspec;
   c0.S = I.P[1] * I.Q;
   c0.Nin = (int)(2 * I.L[0] + 1);
-  c0.P = (int)I.P[0];
   c0.Lw = (int)I.L[0];
-  c0.rp = radices_of(I, 0);
+  c0.lp = line_plan(I, 0);
   c0.tw = twiddles<T>(plan, 0);
-  return launch_cols<T, COL_FWD_REAL>(c0, 1, st, "kde_cols_kgen_real_kernel");
+  return launch_cols<T>(kde_cols_kgen_real_kernel<T>, c0, 1, st, "kde_cols_kgen_real_kernel");
 }
 
 template <typename T>
@@ -526,13 +575,13 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
   const int dl = d - 1;
   const long long* cnt = reinterpret_cast<const long long*>(counts);
   if (d == 1) {
-    size_t smem = (size_t)3 * I.P[0] * sizeof(V);
+    const int P = (int)I.P[0];
     auto* fn = kde_line1d_kernel<T>;
     cudaError_t e = allow_smem(fn);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     LaunchScope ls("kde_line1d_kernel", st);
-    fn<<<1, kThreads, smem, st>>>(cnt, (const T*)Kspec, (T*)density, (int)I.M[0], (int)I.P[0],
-                                  (int)I.Q, radices_of(I, 0), twiddles<T>(plan, 0));
+    fn<<<1, 256, line_smem<T>(P, 1), st>>>(cnt, (const T*)Kspec, (T*)density, (int)I.M[0], (int)I.Q,
+                                          line_plan(I, 0), twiddles<T>(plan, 0));
     e = cudaGetLastError();
     return e == cudaSuccess ? KDE_OK : cuda_fail(e, "kde_line1d_kernel");
   }
@@ -543,12 +592,12 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
   rp.nrows = rows;
   rp.Min = (int)I.M[dl];
   rp.in_stride = I.M[dl];
-  rp.P = (int)I.P[dl];
   rp.Q = (int)I.Q;
   rp.out = A;
-  rp.rp = radices_of(I, dl);
+  rp.lp = line_plan(I, dl);
   rp.tw = twiddles<T>(plan, dl);
-  kde_status s = launch_rows_r2c_counts<T>(cnt, rp, st);
+  kde_status s = launch_rows<T>(kde_rows_r2c_counts_kernel<T>, "kde_rows_r2c_counts_kernel", rows,
+                                rp, st, cnt);
   if (s != KDE_OK) return s;
   if (d == 2) {
     ColsParams<T> cp{};
@@ -558,11 +607,10 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
     cp.S = I.Q;
     cp.Nin = (int)I.M[0];
     cp.Nout = (int)I.M[0];
-    cp.P = (int)I.P[0];
     cp.Lw = -1;
-    cp.rp = radices_of(I, 0);
+    cp.lp = line_plan(I, 0);
     cp.tw = twiddles<T>(plan, 0);
-    s = launch_cols<T, COL_MID>(cp, 1, st, "kde_cols_mid_kernel");
+    s = launch_cols<T>(kde_cols_mid_kernel<T>, cp, 1, st, "kde_cols_mid_kernel");
     if (s != KDE_OK) return s;
   } else {
     V* B = A + rows * I.Q;  // [M_0][P_1][Q]
@@ -571,11 +619,10 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
     c1.out = B;
     c1.S = I.Q;
     c1.Nin = (int)I.M[1];
-    c1.P = (int)I.P[1];
     c1.Lw = -1;
-    c1.rp = radices_of(I, 1);
+    c1.lp = line_plan(I, 1);
     c1.tw = twiddles<T>(plan, 1);
-    s = launch_cols<T, COL_FWD>(c1, I.M[0], st, "kde_cols_fwd_kernel");
+    s = launch_cols<T>(kde_cols_fwd_kernel<T>, c1, I.M[0], st, "kde_cols_fwd_kernel");
     if (s != KDE_OK) return s;
     ColsParams<T> c0{};
     c0.in = B;
@@ -584,11 +631,10 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
     c0.S = I.P[1] * I.Q;
     c0.Nin = (int)I.M[0];
     c0.Nout = (int)I.M[0];
-    c0.P = (int)I.P[0];
     c0.Lw = -1;
-    c0.rp = radices_of(I, 0);
+    c0.lp = line_plan(I, 0);
     c0.tw = twiddles<T>(plan, 0);
-    s = launch_cols<T, COL_MID>(c0, 1, st, "kde_cols_mid_kernel");
+    s = launch_cols<T>(kde_cols_mid_kernel<T>, c0, 1, st, "kde_cols_mid_kernel");
     if (s != KDE_OK) return s;
     ColsParams<T> ci{};
     ci.in = B;
@@ -596,11 +642,10 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
     ci.S = I.Q;
     ci.Nin = (int)I.P[1];
     ci.Nout = (int)I.M[1];
-    ci.P = (int)I.P[1];
     ci.Lw = -1;
-    ci.rp = radices_of(I, 1);
+    ci.lp = line_plan(I, 1);
     ci.tw = twiddles<T>(plan, 1);
-    s = launch_cols<T, COL_INV>(ci, I.M[0], st, "kde_cols_inv_kernel");
+    s = launch_cols<T>(kde_cols_inv_kernel<T>, ci, I.M[0], st, "kde_cols_inv_kernel");
     if (s != KDE_OK) return s;
   }
   C2RParams<T> cr{};
@@ -608,11 +653,10 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
   cr.out = (T*)density;
   cr.nrows = rows;
   cr.Mout = (int)I.M[dl];
-  cr.P = (int)I.P[dl];
   cr.Q = (int)I.Q;
-  cr.rp = radices_of(I, dl);
+  cr.lp = line_plan(I, dl);
   cr.tw = twiddles<T>(plan, dl);
-  return launch_rows_c2r<T>(cr, st);
+  return launch_rows<T>(kde_rows_c2r_kernel<T>, "kde_rows_c2r_kernel", rows, cr, st);
 }
 
 kde_status check_ws(const kde_plan_s* plan, void* ws, size_t bytes) {

@@ -1,14 +1,17 @@
-// Shared-memory mixed-radix FFT engine (radices 2, 3, 4, 5, 7, 8).
+// Mixed-radix FFT engine (radices 2, 3, 4, 5, 7, 8) for one line per group
+// of threads.
 //
-// A thread block transforms `nlines` complex lines of length N held in shared
-// memory with the self-sorting Stockham scheme: with Ns the product of the
-// radices already applied, butterfly j of a radix-R stage reads
-// x[j + r N/R], multiplies leg r by w_N^{r (j mod Ns) N/(Ns R)}, takes a
-// length-R DFT and writes leg r to (j - j mod Ns) R + (j mod Ns) + r Ns.
-// Stages ping-pong between two buffers, so the output is in natural order.
-// Element (line t, position p) lives at p*sp + t*st: line-major storage
-// (sp = 1) for rows, position-major (st = 1) for column tiles; threads are
-// mapped so that consecutive threads touch consecutive shared addresses.
+// A group of tpl threads (tpl a multiple of 32) transforms one complex line
+// of length N held in shared memory, with the self-sorting Stockham scheme:
+// with Ns the product of the radices already applied, butterfly j of a
+// radix-R stage reads x[j + r N/R], multiplies leg r by
+// w_N^{r (j mod Ns) N/(Ns R)}, takes a length-R DFT and writes leg r to
+// (j - j mod Ns) R + (j mod Ns) + r Ns.  Stages ping-pong between two buffers
+// of the line, so the output is in natural order.  A group synchronises only
+// itself: __syncwarp for one warp, a named barrier otherwise, so the lines
+// of a block run independently.  tpl is chosen per launch from the number of
+// lines: few long lines get many threads each, many lines get a warp each.
+// Divisions by Ns use a precomputed reciprocal (exact for j, Ns < 2^13).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,10 +41,17 @@ template <typename V, bool INV> __device__ __forceinline__ V rot90(V a) {
   return INV ? mk<V>(-a.y, a.x) : mk<V>(a.y, -a.x);
 }
 
-struct Radices {
-  int n;
+// One stage of a line plan.  magic = floor(2^32 / Ns) + 1, so that
+// j / Ns = umulhi(j, magic) for the j < 2^13 that occur.
+struct Stage {
+  int R, Ns, nb, twstep;
+  unsigned magic;
+};
+
+struct LinePlan {
+  int N;
   int nst;
-  int r[KDE_MAX_STAGES];
+  Stage st[KDE_MAX_STAGES];
 };
 
 // cos and sin of 2 pi m / R, m = 1 .. (R-1)/2, for the odd radices.
@@ -89,7 +99,7 @@ template <typename V, bool INV> struct SmallDFT<V, 8, INV> {
     SmallDFT<V, 4, INV>::run(e);
     SmallDFT<V, 4, INV>::run(o);
     // o_k *= w_8^k with w_8 = e^{-+ i pi / 4}
-    V o1 = rot90<V, INV>(o[1]);  // temporarily -+i o1
+    V o1 = rot90<V, INV>(o[1]);
     V w1 = mk<V>(h * (o[1].x + o1.x), h * (o[1].y + o1.y));   // (1 -+ i)/sqrt2 * o1
     V o2 = rot90<V, INV>(o[2]);
     V o3r = rot90<V, INV>(o[3]);
@@ -150,65 +160,65 @@ template <typename V, int R, bool INV> struct SmallDFT {
   }
 };
 
-template <typename V, int R, bool INV, bool LINE_MAJOR>
-__device__ __forceinline__ void stockham_stage(const V* __restrict__ in, V* __restrict__ out,
-                                               int N, int Ns, int nlines, int sp, int st,
-                                               const V* __restrict__ tw) {
-  const int nb = N / R;
-  const int total = nb * nlines;
-  const int twstep = N / (Ns * R);
-  for (int b = threadIdx.x; b < total; b += blockDim.x) {
-    int j, t;
-    if (LINE_MAJOR) {
-      t = b / nb;
-      j = b - t * nb;
-    } else {
-      j = b / nlines;
-      t = b - j * nlines;
-    }
-    const V* src = in + t * st;
+// The threads of one line: index lt in [0, tpl) and the barrier they share.
+struct LineGroup {
+  int lt, tpl, bar;
+  __device__ __forceinline__ void sync() const {
+    if (tpl == 32)
+      __syncwarp();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(tpl) : "memory");
+  }
+};
+
+template <typename V, int R, bool INV>
+__device__ __forceinline__ void line_stage(const V* __restrict__ in, V* __restrict__ out,
+                                           const Stage& s, const V* __restrict__ tw,
+                                           const LineGroup& g) {
+  for (int j = g.lt; j < s.nb; j += g.tpl) {
     V x[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = src[(j + r * nb) * sp];
-    const int k = j % Ns;
-    if (Ns > 1) {
+    for (int r = 0; r < R; ++r) x[r] = in[j + r * s.nb];
+    int base;
+    if (s.Ns > 1) {
+      const unsigned q = __umulhi((unsigned)j, s.magic);
+      const int k = j - (int)q * s.Ns;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        V w = tw[r * k * twstep];
+        V w = tw[r * k * s.twstep];
         if (INV) w = cconj(w);
         x[r] = cmul(x[r], w);
       }
+      base = (int)q * s.Ns * R + k;
+    } else {
+      base = j * R;
     }
     SmallDFT<V, R, INV>::run(x);
-    const int base = (j - k) * R + k;
-    V* dst = out + t * st;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[(base + r * Ns) * sp] = x[r];
+    for (int r = 0; r < R; ++r) out[base + r * s.Ns] = x[r];
   }
 }
 
-// Runs every stage; a holds the input on entry.  Returns the buffer holding
-// the result.  Callers synchronise before the call (loads) and the call ends
-// with a barrier.
-template <typename V, bool INV, bool LINE_MAJOR>
-__device__ V* fft_lines(V* a, V* b, const Radices& rp, int nlines, int sp, int st,
-                        const V* __restrict__ tw) {
-  int Ns = 1;
-  for (int s = 0; s < rp.nst; ++s) {
-    const int R = rp.r[s];
-    switch (R) {
-      case 2: stockham_stage<V, 2, INV, LINE_MAJOR>(a, b, rp.n, Ns, nlines, sp, st, tw); break;
-      case 3: stockham_stage<V, 3, INV, LINE_MAJOR>(a, b, rp.n, Ns, nlines, sp, st, tw); break;
-      case 4: stockham_stage<V, 4, INV, LINE_MAJOR>(a, b, rp.n, Ns, nlines, sp, st, tw); break;
-      case 5: stockham_stage<V, 5, INV, LINE_MAJOR>(a, b, rp.n, Ns, nlines, sp, st, tw); break;
-      case 7: stockham_stage<V, 7, INV, LINE_MAJOR>(a, b, rp.n, Ns, nlines, sp, st, tw); break;
-      default: stockham_stage<V, 8, INV, LINE_MAJOR>(a, b, rp.n, Ns, nlines, sp, st, tw); break;
+// All stages of a line held in a (input) and b (scratch), both in shared
+// memory and private to the group; returns the buffer holding the result.
+// Callers g.sync() before (after filling a); the call ends with g.sync().
+template <typename V, bool INV>
+__device__ V* line_fft(V* a, V* b, const LinePlan& lp, const V* __restrict__ tw,
+                       const LineGroup& g) {
+  for (int s = 0; s < lp.nst; ++s) {
+    const Stage& st = lp.st[s];
+    switch (st.R) {
+      case 2: line_stage<V, 2, INV>(a, b, st, tw, g); break;
+      case 3: line_stage<V, 3, INV>(a, b, st, tw, g); break;
+      case 4: line_stage<V, 4, INV>(a, b, st, tw, g); break;
+      case 5: line_stage<V, 5, INV>(a, b, st, tw, g); break;
+      case 7: line_stage<V, 7, INV>(a, b, st, tw, g); break;
+      default: line_stage<V, 8, INV>(a, b, st, tw, g); break;
     }
-    __syncthreads();
+    g.sync();
     V* t = a;
     a = b;
     b = t;
-    Ns *= R;
   }
   return a;
 }
