@@ -37,6 +37,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     return ap.parse_args()
 
 
@@ -290,15 +291,44 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
 
-    step_dev = kde.PreparedPath(plan, X, counts, Ks, dens, ws, bin_workspace=bws, stream=stream)
+    # One step: the kernel grid (no dependence on the samples) runs on a side
+    # stream while the samples are binned; the FFT evaluation waits for both.
+    side = torch.cuda.Stream(device=dev, priority=-1)
+    step_dev = kde.PreparedPath(plan, X, counts, Ks, dens, ws, bin_workspace=bws, stream=stream,
+                                kgen_stream=side)
     Xe = torch.empty_like(X)
-    step_e2e = kde.PreparedPath(plan, Xe, counts, Ks, dens, ws, bin_workspace=bws, stream=stream)
+    step_e2e = kde.PreparedPath(plan, Xe, counts, Ks, dens, ws, bin_workspace=bws, stream=stream,
+                                kgen_stream=side)
+    fork = torch.cuda.Event()
+    join = torch.cuda.Event()
+
+    def enqueue(path):
+        fork.record(stream)
+        side.wait_event(fork)
+        path.kernel_grid()
+        path.bin()
+        join.record(side)
+        stream.wait_event(join)
+        path.fft_eval()
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.zero_()
-            step_dev()
+            enqueue(step_dev)
     torch.cuda.synchronize()
+
+    # The step captured once as a CUDA graph and replayed.
+    graph = None
+    per_step_launches = 0
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        l0 = kde.launch_count()
+        with torch.cuda.graph(graph, stream=stream):
+            enqueue(step_dev)
+        per_step_launches = kde.launch_count() - l0
+        with torch.cuda.stream(stream):
+            graph.replay()
+        torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -308,18 +338,18 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    kde.profile_enable(True)
     l0 = kde.launch_count()
     with torch.cuda.stream(stream):
         for i in range(args.steps):
             flush.zero_()
             starts[i].record(stream)
-            step_dev()
+            if graph is not None:
+                graph.replay()
+            else:
+                enqueue(step_dev)
             ends[i].record(stream)
     torch.cuda.synchronize()
-    launches = kde.launch_count() - l0
-    prof = kde.profile_read()
-    kde.profile_enable(False)
+    launches = (kde.launch_count() - l0) if graph is None else per_step_launches * args.steps
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -333,6 +363,17 @@ def main():
     value = world * cells / (ms_step * 1e-3)
     samples_s = world * w.n / (ms_step * 1e-3)
 
+    # Per-kernel durations: the same steps launched one by one with the
+    # library's event pairs around every kernel (graph replays carry none).
+    kde.profile_enable(True)
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()
+            enqueue(step_dev)
+    torch.cuda.synchronize()
+    prof = kde.profile_read()
+    kde.profile_enable(False)
+
     # End to end through the public API with host buffers: pinned X -> device,
     # the three calls, density -> pinned host, every step.
     e2e_steps = max(3, min(args.steps, 50))
@@ -341,13 +382,13 @@ def main():
     with torch.cuda.stream(stream):
         for _ in range(2):
             Xe.copy_(X_host, non_blocking=True)
-            step_e2e()
+            enqueue(step_e2e)
             dens_host.copy_(dens, non_blocking=True)
         torch.cuda.synchronize()
         e_s.record(stream)
         for _ in range(e2e_steps):
             Xe.copy_(X_host, non_blocking=True)
-            step_e2e()
+            enqueue(step_e2e)
             dens_host.copy_(dens, non_blocking=True)
         e_e.record(stream)
     torch.cuda.synchronize()
@@ -382,8 +423,12 @@ def main():
             "config": {"workload": args.workload, "d": w.d, "n": w.n, "grid": list(w.M),
                        "L": list(info.L), "P": list(info.P), "precision": info.precision,
                        "l2": "flushed between timed steps (256 MB write)",
+                       "launch": "CUDA graph replay per step" if graph is not None else "stream launches",
+                       "streams": "kernel grid on a side stream, concurrent with binning",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline, "path_roofline": path_roof, "kernels": kernels,
+            "kernel_timing": "CUDA events around each kernel on its stream, over the same K steps "
+                             "launched without the graph right after the timed region",
             "gpu_launches": launches,
             "e2e": {"value": world * cells / (e2e_ms * 1e-3), "unit": "grid points/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(X.numel() * X.element_size()),
@@ -399,7 +444,7 @@ def main():
         for suf in (".nodes.npy", ".ref.npy"):
             os.unlink(tmp + suf)
         with torch.cuda.stream(stream):
-            step_dev()
+            enqueue(step_dev)
         torch.cuda.synchronize()
         got = dens.cpu().numpy()[tuple(nodes.T)]
         line["cpu_baseline"] = {

@@ -1,5 +1,7 @@
 // Mixed-radix FFT engine (radices 2, 3, 4, 5, 7, 8) for one line per group
-// of threads.
+// of threads.  (Larger radices nested in registers cut the passes over
+// shared memory but raised every kernel to 128+ registers and lost more to
+// occupancy than they saved; they are not used.)
 //
 // A group of tpl threads (tpl a multiple of 32) transforms one complex line
 // of length N held in shared memory, with the self-sorting Stockham scheme:

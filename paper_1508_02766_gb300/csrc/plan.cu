@@ -4,6 +4,7 @@
 // twiddle tables, error reporting, launch counting and per-kernel timing.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -151,16 +152,31 @@ static bool is_7smooth(int64_t x) {
   return x == 1;
 }
 
+// Factor P into the engine's radices with the fewest stages (then the
+// fewest odd radices), largest radix first.  Dynamic programming over the
+// divisors of P.
 static int radix_plan(int64_t P, int* radix) {
+  static const int kRadices[] = {8, 7, 5, 4, 3, 2};
+  std::vector<int> best_n(P + 1, 1 << 20), best_odd(P + 1, 1 << 20), choice(P + 1, 0);
+  best_n[1] = 0;
+  best_odd[1] = 0;
+  for (int64_t x = 2; x <= P; ++x) {
+    if (P % x) continue;
+    for (int r : kRadices) {
+      if (x % r) continue;
+      int64_t y = x / r;
+      if (best_n[y] >= (1 << 20)) continue;
+      int n = best_n[y] + 1, odd = best_odd[y] + (r % 2);
+      if (n < best_n[x] || (n == best_n[x] && odd < best_odd[x])) {
+        best_n[x] = n;
+        best_odd[x] = odd;
+        choice[x] = r;
+      }
+    }
+  }
   int n = 0;
-  int64_t x = P;
-  int twos = 0;
-  while (x % 2 == 0) { x /= 2; ++twos; }
-  while (twos >= 3) { radix[n++] = 8; twos -= 3; }
-  if (twos == 2) radix[n++] = 4;
-  if (twos == 1) radix[n++] = 2;
-  for (int p : {7, 5, 3})
-    while (x % p == 0) { x /= p; radix[n++] = p; }
+  for (int64_t x = P; x > 1; x /= choice[x]) radix[n++] = choice[x];
+  std::sort(radix, radix + n, [](int a, int b) { return a > b; });
   return n;
 }
 

@@ -319,27 +319,41 @@ def profile_read():
 
 
 class PreparedPath:
-    """bin -> kernel grid -> FFT evaluation on fixed buffers and one stream,
-    with every C argument marshalled once, so that a call costs three C calls."""
+    """bin, kernel grid and FFT evaluation on fixed buffers, with every C
+    argument marshalled once.  ``bin()``, ``kernel_grid()`` and ``fft_eval()``
+    enqueue one call each on their stream (kernel_grid may use its own
+    stream); ``__call__`` enqueues all three in order on one stream."""
 
     def __init__(self, plan: Plan, X, counts, Kspec, density, workspace, n=None,
-                 n_outside=None, bin_workspace=None, stream=None):
+                 n_outside=None, bin_workspace=None, stream=None, kgen_stream=None):
         import torch
         L = lib()
         self._L = L
         self.plan = plan
         s = _stream_ptr(stream)
+        sk = _stream_ptr(kgen_stream) if kgen_stream is not None else s
         nX, d = X.shape
         bwb = 0 if bin_workspace is None else bin_workspace.numel() * bin_workspace.element_size()
         self._bin = (_ptr(X), F32 if X.dtype == torch.float32 else F64, nX, d, _darr(plan.lo),
                      _darr(plan.hi), _iarr(plan.M), _ptr(counts), _ptr(n_outside),
                      _ptr(bin_workspace), bwb, s)
         wsb = workspace.numel() * workspace.element_size()
-        self._kg = (plan.handle, int(nX if n is None else n), _ptr(Kspec), _ptr(workspace), wsb, s)
+        # kernel_grid and fft_eval share the workspace only when ordered; with a
+        # separate kernel-grid stream the caller passes kgen_workspace ordering
+        self._kg = (plan.handle, int(nX if n is None else n), _ptr(Kspec), _ptr(workspace), wsb, sk)
         self._ev = (plan.handle, _ptr(counts), _ptr(Kspec), _ptr(density), _ptr(workspace), wsb, s)
         self._keep = (X, counts, Kspec, density, workspace, n_outside, bin_workspace)
 
-    def __call__(self):
+    def bin(self):
         _check(self._L.kde_bin(*self._bin))
+
+    def kernel_grid(self):
         _check(self._L.kde_kernel_grid(*self._kg))
+
+    def fft_eval(self):
         _check(self._L.kde_fft_eval(*self._ev))
+
+    def __call__(self):
+        self.bin()
+        self.kernel_grid()
+        self.fft_eval()

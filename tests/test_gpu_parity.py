@@ -260,3 +260,25 @@ def test_tiled_binning_tile_faces(K, d, M):
     c_ref, nout_ref = O.bin_linear(X, lo, hi, M)
     assert int(nout.item()) == nout_ref == 0
     assert np.array_equal(counts, c_ref)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_many_line_lengths(K, prec):
+    """Grids whose padded lengths cover every radix of the engine (direct and
+    nested), in 1-D and 2-D, against the oracle on every node."""
+    seen = set()
+    for i, M in enumerate(list(range(2, 420, 17)) + [511, 767, 1000]):
+        w = W.small_case(500 + i, 1, (M,), n=400, precision=prec)
+        dens, counts, _, plan = run_gpu(K, w)
+        seen.update(plan.info.radices[0])
+        f, c_ref, _, _ = oracle_full(w)
+        assert np.array_equal(counts, c_ref)
+        assert rel_err(dens, f) <= TOL[prec], (M, plan.info.P)
+    for i, M in enumerate([(9, 70), (33, 21), (50, 100), (75, 40)]):
+        w = W.small_case(600 + i, 2, M, n=800, precision=prec)
+        dens, counts, _, plan = run_gpu(K, w)
+        for r in plan.info.radices:
+            seen.update(r)
+        f, c_ref, _, _ = oracle_full(w)
+        assert rel_err(dens, f) <= TOL[prec], (M, plan.info.P)
+    assert seen >= {2, 3, 4, 5, 7, 8}, sorted(seen)
