@@ -48,6 +48,7 @@ typedef enum {
 enum { KDE_F32 = 0, KDE_F64 = 1 };                   /* element types */
 enum { KDE_RANGE_CORRECTED = 0, KDE_RANGE_PER_AXIS = 1 };
 enum { KDE_LAYOUT_CORRECTED = 0, KDE_LAYOUT_WAND = 1 };
+enum { KDE_COLS_AUTO = 0, KDE_COLS_LINES = 1, KDE_COLS_SIMD = 2 };
 
 #define KDE_MAX_D 3
 #define KDE_MAX_P 4096      /* largest padded length of one axis */
@@ -65,13 +66,19 @@ enum { KDE_LAYOUT_CORRECTED = 0, KDE_LAYOUT_WAND = 1 };
  *               KDE_LAYOUT_WAND: k_{|l_1|,...,|l_d|} at lag l, which is what
  *               Wand's wrap-around layout (Eq. 8) convolves with; wrong for
  *               non-diagonal H (Sec. 3-4.1), kept for demonstration.
- *   P_min       optional lower bounds on the padded sizes (0 = none). */
+ *   P_min       optional lower bounds on the padded sizes (0 = none).
+ *   cols_variant  how passes along strided axes are organised: KDE_COLS_AUTO
+ *               (by size), KDE_COLS_LINES (a thread group per column) or
+ *               KDE_COLS_SIMD (16 columns side by side; used only where its
+ *               shared-memory tile fits).  The result is the same up to
+ *               rounding; this exists for testing and tuning. */
 typedef struct {
   double tau;
   int precision;
   int range_mode;
   int layout_mode;
   int64_t P_min[KDE_MAX_D];
+  int cols_variant;
 } kde_opts;
 
 /* Everything the plan derives on the host, in FP64.
@@ -151,8 +158,10 @@ kde_status kde_bin_workspace_bytes(int64_t n, int d, const int64_t* M, size_t* b
  * l mod P_k (zero elsewhere) and transforms it.  k_{-l} = k_l, so the
  * spectrum is real; Kspec receives it as plan.kspec_elems values of the
  * plan's precision: the half spectrum along the last axis (Q values) for
- * every leading frequency, stored with axis 0 contiguous, i.e. as the
- * row-major array [P_1 ... P_{d-2}][Q][P_0] (d = 1: [Q]).  The 1/n of Eq. 2, the 2^-32 count unit and the 1/prod(P)
+ * every leading frequency, in a plan-defined order (row-major
+ * [P_0][P_1 ... P_{d-2}][Q], or with axis 0 innermost, depending on how the
+ * plan organises the axis-0 pass); pass it unchanged to kde_fft_eval of the
+ * same plan.  The 1/n of Eq. 2, the 2^-32 count unit and the 1/prod(P)
  * normalisation of Eq. 11/14 are folded in here.  n >= 1 is the number of
  * samples that were binned (the n of Eq. 2).  workspace: at least
  * plan.workspace_bytes of device scratch, 16-byte aligned. */

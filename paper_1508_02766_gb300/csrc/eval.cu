@@ -70,6 +70,19 @@ __device__ __forceinline__ int wrapped_lag(int p, int P, int L) {
   return L + 1;
 }
 
+// Input row feeding transform position pos: with Lw >= 0 the input rows hold
+// the lags -Lw .. Lw placed at l mod P; otherwise row n sits at position n.
+// Returns a value >= Nin for positions that hold zero padding.
+__device__ __forceinline__ int source_row(int pos, int P, int Lw, int Nin) {
+  if (Lw < 0) return pos;
+  const int l = wrapped_lag(pos, P, Lw);
+  return (l <= Lw) ? l + Lw : Nin;
+}
+
+// Global loads issued back to back by one thread before their values are
+// stored to shared memory (memory-level parallelism of the load phases).
+constexpr int kLoadBatch = 8;
+
 template <typename V>
 __device__ __forceinline__ void load_twiddles(V* tw_s, const V* tw, int P) {
   for (int i = threadIdx.x; i < P; i += blockDim.x) tw_s[i] = tw[i];
@@ -135,14 +148,19 @@ kde_rows_r2c_counts_kernel(const long long* __restrict__ counts, RowsParams<T> p
   const long long* c0 = counts + r0 * p.in_stride;
   const long long* c1 = c0 + p.in_stride;
   const bool two = r0 + 1 < p.nrows;
-#pragma unroll 4
-  for (int x = g.lt; x < P; x += g.tpl) {
-    T re = 0, im = 0;
-    if (x < p.Min) {
-      re = (T)__ldg(c0 + x);
-      if (two) im = (T)__ldg(c1 + x);
+  for (int x0 = g.lt; x0 < P; x0 += kLoadBatch * g.tpl) {
+    long long u0[kLoadBatch], u1[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int x = x0 + u * g.tpl;
+      u0[u] = x < p.Min ? __ldg(c0 + x) : 0;
+      u1[u] = (x < p.Min && two) ? __ldg(c1 + x) : 0;
     }
-    a[x] = mk<V>(re, im);
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int x = x0 + u * g.tpl;
+      if (x < P) a[x] = mk<V>((T)u0[u], (T)u1[u]);
+    }
   }
   g.sync();
   V* z = line_fft<V, false>(a, b, p.lp, tw_s, g);
@@ -228,12 +246,21 @@ __global__ void __launch_bounds__(256) kde_rows_c2r_kernel(C2RParams<T> p) {
   const bool two = r0 + 1 < p.nrows;
   const V* x0 = p.in + r0 * p.Q;
   const V* x1 = x0 + p.Q;
-#pragma unroll 4
-  for (int k = g.lt; k < p.Q; k += g.tpl) {
-    V X = x0[k];
-    V Y = two ? x1[k] : mk<V>(0, 0);
-    a[k] = mk<V>(X.x - Y.y, X.y + Y.x);
-    if (k > 0 && P - k >= p.Q) a[P - k] = mk<V>(X.x + Y.y, Y.x - X.y);
+  for (int k0 = g.lt; k0 < p.Q; k0 += kLoadBatch * g.tpl) {
+    V X[kLoadBatch], Y[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int k = k0 + u * g.tpl;
+      X[u] = k < p.Q ? x0[k] : mk<V>(0, 0);
+      Y[u] = (k < p.Q && two) ? x1[k] : mk<V>(0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int k = k0 + u * g.tpl;
+      if (k >= p.Q) continue;
+      a[k] = mk<V>(X[u].x - Y[u].y, X[u].y + Y[u].x);
+      if (k > 0 && P - k >= p.Q) a[P - k] = mk<V>(X[u].x + Y[u].y, Y[u].x - X[u].y);
+    }
   }
   g.sync();
   V* z = line_fft<V, true>(a, b, p.lp, tw_s, g);
@@ -307,20 +334,22 @@ __device__ __forceinline__ void cols_body(const ColsParams<T>& p) {
   const int64_t o = blockIdx.y;
   const int64_t s0 = (int64_t)blockIdx.x * W;
   const V* in = p.in + o * (int64_t)p.Nin * p.S;
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < P * W; idx += blockDim.x) {
-    const int pos = idx / W, t = idx - pos * W;
-    int n;
-    if (p.Lw >= 0) {
-      const int l = wrapped_lag(pos, P, p.Lw);
-      n = (l <= p.Lw) ? l + p.Lw : p.Nin;
-    } else {
-      n = pos;
+  for (int idx0 = threadIdx.x; idx0 < P * W; idx0 += kLoadBatch * blockDim.x) {
+    V v[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      const int pos = idx / W, t = idx - pos * W;
+      const int n = source_row(pos, P, p.Lw, p.Nin);
+      const int64_t s = s0 + t;
+      v[u] = (idx < P * W && n < p.Nin && s < p.S) ? in[(int64_t)n * p.S + s] : mk<V>(0, 0);
     }
-    const int64_t s = s0 + t;
-    V v = mk<V>(0, 0);
-    if (n < p.Nin && s < p.S) v = in[(int64_t)n * p.S + s];
-    lines[t * LS + pos] = v;
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      const int pos = idx / W, t = idx - pos * W;
+      if (idx < P * W) lines[t * LS + pos] = v[u];
+    }
   }
   __syncthreads();
   const int64_t s = s0 + li;
@@ -360,25 +389,150 @@ __device__ __forceinline__ void cols_body(const ColsParams<T>& p) {
   }
 }
 
-template <typename T>
+// Column passes with many columns: a block holds kSimdW adjacent columns
+// position-major in shared memory (element (pos, c) at pos kSimdW + c).
+// Thread t works on column t mod kSimdW; the kSimdW threads of a group run
+// the same butterfly on every column, so index arithmetic and twiddles are
+// uniform and each group's shared and global accesses are one contiguous
+// row segment of kSimdW elements.  The kernel spectrum of such a pass is
+// stored [P][S] (columns contiguous).
+constexpr int kSimdW = 16;
+
+template <typename V, int R, bool INV>
+__device__ __forceinline__ void simd_stage(const V* __restrict__ in, V* __restrict__ out,
+                                           const Stage& s, const V* __restrict__ tw, int c, int g,
+                                           int ng) {
+  for (int j = g; j < s.nb; j += ng) {
+    V x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = in[(j + r * s.nb) * kSimdW + c];
+    int base;
+    if (s.Ns > 1) {
+      const unsigned q = __umulhi((unsigned)j, s.magic);
+      const int k = j - (int)q * s.Ns;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        V w = tw[r * k * s.twstep];
+        if (INV) w = cconj(w);
+        x[r] = cmul(x[r], w);
+      }
+      base = (int)q * s.Ns * R + k;
+    } else {
+      base = j * R;
+    }
+    SmallDFT<V, R, INV>::run(x);
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[(base + r * s.Ns) * kSimdW + c] = x[r];
+  }
+}
+
+template <typename V, bool INV>
+__device__ V* simd_fft(V* a, V* b, const LinePlan& lp, const V* __restrict__ tw, int c, int g,
+                       int ng) {
+  for (int s = 0; s < lp.nst; ++s) {
+    const Stage& st = lp.st[s];
+    switch (st.R) {
+      case 2: simd_stage<V, 2, INV>(a, b, st, tw, c, g, ng); break;
+      case 3: simd_stage<V, 3, INV>(a, b, st, tw, c, g, ng); break;
+      case 4: simd_stage<V, 4, INV>(a, b, st, tw, c, g, ng); break;
+      case 5: simd_stage<V, 5, INV>(a, b, st, tw, c, g, ng); break;
+      case 7: simd_stage<V, 7, INV>(a, b, st, tw, c, g, ng); break;
+      default: simd_stage<V, 8, INV>(a, b, st, tw, c, g, ng); break;
+    }
+    __syncthreads();
+    V* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ void cols_simd_body(const ColsParams<T>& p) {
+  using V = typename Cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = p.lp.N;
+  V* tw_s = reinterpret_cast<V*>(smem_raw);
+  V* bufA = tw_s + P;
+  V* bufB = bufA + P * kSimdW;
+  const int c = threadIdx.x % kSimdW, g = threadIdx.x / kSimdW, ng = blockDim.x / kSimdW;
+  load_twiddles(tw_s, p.tw, P);
+  const int64_t o = blockIdx.y;
+  const int64_t s = (int64_t)blockIdx.x * kSimdW + c;
+  const bool col_ok = s < p.S;
+  const V* in = p.in + o * (int64_t)p.Nin * p.S;
+  // kLoadBatch independent loads in flight per thread before any is stored
+  for (int pos0 = g; pos0 < P; pos0 += kLoadBatch * ng) {
+    V v[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int pos = pos0 + u * ng;
+      const int n = source_row(pos, P, p.Lw, p.Nin);
+      v[u] = (pos < P && n < p.Nin && col_ok) ? in[(int64_t)n * p.S + s] : mk<V>(0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int pos = pos0 + u * ng;
+      if (pos < P) bufA[pos * kSimdW + c] = v[u];
+    }
+  }
+  __syncthreads();
+  V* z = (MODE == COL_INV) ? simd_fft<V, true>(bufA, bufB, p.lp, tw_s, c, g, ng)
+                           : simd_fft<V, false>(bufA, bufB, p.lp, tw_s, c, g, ng);
+  if (MODE == COL_MID) {
+    for (int pos = g; pos < P; pos += ng) {
+      const T kv = col_ok ? __ldg(p.K + (int64_t)pos * p.S + s) : T(0);
+      V v = z[pos * kSimdW + c];
+      z[pos * kSimdW + c] = mk<V>(v.x * kv, v.y * kv);
+    }
+    __syncthreads();
+    V* other = (z == bufA) ? bufB : bufA;
+    z = simd_fft<V, true>(z, other, p.lp, tw_s, c, g, ng);
+  }
+  if (!col_ok) return;
+  if (MODE == COL_FWD_REAL) {
+    for (int pos = g; pos < P; pos += ng)
+      p.out_real[(o * P + pos) * p.S + s] = z[pos * kSimdW + c].x;
+    return;
+  }
+  const int nout = (MODE == COL_FWD) ? P : p.Nout;
+  for (int pos = g; pos < nout; pos += ng) p.out[(o * nout + pos) * p.S + s] = z[pos * kSimdW + c];
+}
+
+template <typename T, bool SIMD>
 __global__ void __launch_bounds__(256) kde_cols_fwd_kernel(ColsParams<T> p) {
-  cols_body<T, COL_FWD>(p);
+  if (SIMD)
+    cols_simd_body<T, COL_FWD>(p);
+  else
+    cols_body<T, COL_FWD>(p);
 }
-template <typename T>
+template <typename T, bool SIMD>
 __global__ void __launch_bounds__(256) kde_cols_kgen_kernel(ColsParams<T> p) {
-  cols_body<T, COL_FWD>(p);
+  if (SIMD)
+    cols_simd_body<T, COL_FWD>(p);
+  else
+    cols_body<T, COL_FWD>(p);
 }
-template <typename T>
+template <typename T, bool SIMD>
 __global__ void __launch_bounds__(256) kde_cols_kgen_real_kernel(ColsParams<T> p) {
-  cols_body<T, COL_FWD_REAL>(p);
+  if (SIMD)
+    cols_simd_body<T, COL_FWD_REAL>(p);
+  else
+    cols_body<T, COL_FWD_REAL>(p);
 }
-template <typename T>
+template <typename T, bool SIMD>
 __global__ void __launch_bounds__(256) kde_cols_mid_kernel(ColsParams<T> p) {
-  cols_body<T, COL_MID>(p);
+  if (SIMD)
+    cols_simd_body<T, COL_MID>(p);
+  else
+    cols_body<T, COL_MID>(p);
 }
-template <typename T>
+template <typename T, bool SIMD>
 __global__ void __launch_bounds__(256) kde_cols_inv_kernel(ColsParams<T> p) {
-  cols_body<T, COL_INV>(p);
+  if (SIMD)
+    cols_simd_body<T, COL_INV>(p);
+  else
+    cols_body<T, COL_INV>(p);
 }
 
 // ---------------------------------------------------------------------------
@@ -479,21 +633,43 @@ kde_status launch_rows(Kern* fn, const char* name, int64_t nrows, Params& p, cud
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, name);
 }
 
+// Column passes with at least this many 16-column tiles per SM, and whose
+// tiles fit twice per SM, use the SIMD-across-columns body.
 template <typename T>
-kde_status launch_cols(void (*fn)(ColsParams<T>), ColsParams<T> p, int64_t O, cudaStream_t st,
-                       const char* name) {
+bool simd_cols(int variant, int64_t columns, int P) {
+  const size_t smem = (size_t)(1 + 2 * kSimdW) * P * sizeof(typename Cplx<T>::type);
+  if (variant == KDE_COLS_LINES || smem > 100 * 1024) return false;
+  return variant == KDE_COLS_SIMD || columns >= (int64_t)4 * kSimdW * num_sms();
+}
+
+template <typename T>
+using ColsKernel = void (*)(ColsParams<T>);
+
+template <typename T>
+kde_status launch_cols(ColsKernel<T> fn_lines, ColsKernel<T> fn_simd, ColsParams<T> p, int64_t O,
+                       int variant, cudaStream_t st, const char* name) {
   const int P = p.lp.N;
-  const LineShape sh = line_shape<T>(p.S * O, P, 2);
-  p.tpl = sh.tpl;
-  const int W = sh.lpb;
-  cudaError_t e = allow_smem(fn);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-  dim3 grid((unsigned)((p.S + W - 1) / W), (unsigned)O);
-  LaunchScope ls(name, st);
-  fn<<<grid, sh.tpl * W, line_smem<T>(P, W), st>>>(p);
+  cudaError_t e;
+  if (simd_cols<T>(variant, p.S * O, P)) {
+    if ((e = allow_smem(fn_simd)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    const size_t smem = (size_t)(1 + 2 * kSimdW) * P * sizeof(typename Cplx<T>::type);
+    dim3 grid((unsigned)((p.S + kSimdW - 1) / kSimdW), (unsigned)O);
+    LaunchScope ls(name, st);
+    fn_simd<<<grid, 256, smem, st>>>(p);
+  } else {
+    const LineShape sh = line_shape<T>(p.S * O, P, 2);
+    p.tpl = sh.tpl;
+    const int W = sh.lpb;
+    if ((e = allow_smem(fn_lines)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    dim3 grid((unsigned)((p.S + W - 1) / W), (unsigned)O);
+    LaunchScope ls(name, st);
+    fn_lines<<<grid, sh.tpl * W, line_smem<T>(P, W), st>>>(p);
+  }
   e = cudaGetLastError();
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, name);
 }
+
+#define KDE_COLS(kern) kern<T, false>, kern<T, true>
 
 template <typename T>
 kde_status kernel_grid_impl(kde_plan_s* plan, int64_t n, void* Kspec, void* ws, cudaStream_t st) {
@@ -541,7 +717,7 @@ kde_status kernel_grid_impl(kde_plan_s* plan, int64_t n, void* Kspec, void* ws, 
     cp.Lw = (int)I.L[0];
     cp.lp = line_plan(I, 0);
     cp.tw = twiddles<T>(plan, 0);
-    return launch_cols<T>(kde_cols_kgen_real_kernel<T>, cp, 1, st, "kde_cols_kgen_real_kernel");
+    return launch_cols<T>(KDE_COLS(kde_cols_kgen_real_kernel), cp, 1, plan->cols_variant, st, "kde_cols_kgen_real_kernel");
   }
   // d == 3: axis 1 (wrapped) into t2, then axis 0 (wrapped) to the real spectrum.
   V* t2 = t1 + rows * I.Q;
@@ -553,7 +729,7 @@ kde_status kernel_grid_impl(kde_plan_s* plan, int64_t n, void* Kspec, void* ws, 
   c1.Lw = (int)I.L[1];
   c1.lp = line_plan(I, 1);
   c1.tw = twiddles<T>(plan, 1);
-  s = launch_cols<T>(kde_cols_kgen_kernel<T>, c1, 2 * I.L[0] + 1, st, "kde_cols_kgen_kernel");
+  s = launch_cols<T>(KDE_COLS(kde_cols_kgen_kernel), c1, 2 * I.L[0] + 1, plan->cols_variant, st, "kde_cols_kgen_kernel");
   if (s != KDE_OK) return s;
   ColsParams<T> c0{};
   c0.in = t2;
@@ -563,7 +739,7 @@ kde_status kernel_grid_impl(kde_plan_s* plan, int64_t n, void* Kspec, void* ws, 
   c0.Lw = (int)I.L[0];
   c0.lp = line_plan(I, 0);
   c0.tw = twiddles<T>(plan, 0);
-  return launch_cols<T>(kde_cols_kgen_real_kernel<T>, c0, 1, st, "kde_cols_kgen_real_kernel");
+  return launch_cols<T>(KDE_COLS(kde_cols_kgen_real_kernel), c0, 1, plan->cols_variant, st, "kde_cols_kgen_real_kernel");
 }
 
 template <typename T>
@@ -610,7 +786,7 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
     cp.Lw = -1;
     cp.lp = line_plan(I, 0);
     cp.tw = twiddles<T>(plan, 0);
-    s = launch_cols<T>(kde_cols_mid_kernel<T>, cp, 1, st, "kde_cols_mid_kernel");
+    s = launch_cols<T>(KDE_COLS(kde_cols_mid_kernel), cp, 1, plan->cols_variant, st, "kde_cols_mid_kernel");
     if (s != KDE_OK) return s;
   } else {
     V* B = A + rows * I.Q;  // [M_0][P_1][Q]
@@ -622,7 +798,7 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
     c1.Lw = -1;
     c1.lp = line_plan(I, 1);
     c1.tw = twiddles<T>(plan, 1);
-    s = launch_cols<T>(kde_cols_fwd_kernel<T>, c1, I.M[0], st, "kde_cols_fwd_kernel");
+    s = launch_cols<T>(KDE_COLS(kde_cols_fwd_kernel), c1, I.M[0], plan->cols_variant, st, "kde_cols_fwd_kernel");
     if (s != KDE_OK) return s;
     ColsParams<T> c0{};
     c0.in = B;
@@ -634,7 +810,7 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
     c0.Lw = -1;
     c0.lp = line_plan(I, 0);
     c0.tw = twiddles<T>(plan, 0);
-    s = launch_cols<T>(kde_cols_mid_kernel<T>, c0, 1, st, "kde_cols_mid_kernel");
+    s = launch_cols<T>(KDE_COLS(kde_cols_mid_kernel), c0, 1, plan->cols_variant, st, "kde_cols_mid_kernel");
     if (s != KDE_OK) return s;
     ColsParams<T> ci{};
     ci.in = B;
@@ -645,7 +821,7 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
     ci.Lw = -1;
     ci.lp = line_plan(I, 1);
     ci.tw = twiddles<T>(plan, 1);
-    s = launch_cols<T>(kde_cols_inv_kernel<T>, ci, I.M[0], st, "kde_cols_inv_kernel");
+    s = launch_cols<T>(KDE_COLS(kde_cols_inv_kernel), ci, I.M[0], plan->cols_variant, st, "kde_cols_inv_kernel");
     if (s != KDE_OK) return s;
   }
   C2RParams<T> cr{};

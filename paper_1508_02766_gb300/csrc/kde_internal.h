@@ -17,6 +17,7 @@ struct kde_plan_s {
   double tau;
   int range_mode;
   int layout_mode;
+  int cols_variant;
   int device;
   // Twiddle tables e^{-2 pi i m / P_k}, m in [0, P_k): one per axis, in the
   // plan's precision (float2 or double2), owned by the plan.

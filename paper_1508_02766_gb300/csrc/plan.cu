@@ -201,6 +201,8 @@ static kde_status compute_info(int d, const int64_t* M, const double* lo, const 
     return fail(KDE_ERR_INVALID_ARG, "bad range_mode");
   if (o.layout_mode != KDE_LAYOUT_CORRECTED && o.layout_mode != KDE_LAYOUT_WAND)
     return fail(KDE_ERR_INVALID_ARG, "bad layout_mode");
+  if (o.cols_variant < KDE_COLS_AUTO || o.cols_variant > KDE_COLS_SIMD)
+    return fail(KDE_ERR_INVALID_ARG, "bad cols_variant");
   std::memset(info, 0, sizeof(*info));
   info->d = d;
   info->precision = o.precision;
@@ -298,6 +300,7 @@ kde_status kde_plan_create(int d, const int64_t* M, const double* lo, const doub
   }
   p->range_mode = opts ? opts->range_mode : KDE_RANGE_CORRECTED;
   p->layout_mode = opts ? opts->layout_mode : KDE_LAYOUT_CORRECTED;
+  p->cols_variant = opts ? opts->cols_variant : KDE_COLS_AUTO;
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) {
     delete p;

@@ -57,11 +57,11 @@ SMALL = [
 ]
 
 
-@pytest.mark.parametrize("method", ["tiled", "direct"])
+@pytest.mark.parametrize("method,cols", [("tiled", "lines"), ("direct", "simd")])
 @pytest.mark.parametrize("d,M,prec", SMALL)
-def test_small_grids_every_node(K, d, M, prec, method):
+def test_small_grids_every_node(K, d, M, prec, method, cols):
     w = W.small_case(100 + d * 7 + len(M) + M[0], d, M, n=3000, precision=prec)
-    dens, counts, nout, plan = run_gpu(K, w, method=method)
+    dens, counts, nout, plan = run_gpu(K, w, method=method, cols=cols)
     f, c_ref, L, nout_ref = oracle_full(w)
     assert plan.info.L == L
     assert nout == nout_ref
@@ -276,7 +276,7 @@ def test_many_line_lengths(K, prec):
         assert rel_err(dens, f) <= TOL[prec], (M, plan.info.P)
     for i, M in enumerate([(9, 70), (33, 21), (50, 100), (75, 40)]):
         w = W.small_case(600 + i, 2, M, n=800, precision=prec)
-        dens, counts, _, plan = run_gpu(K, w)
+        dens, counts, _, plan = run_gpu(K, w, cols=("simd" if i % 2 else "lines"))
         for r in plan.info.radices:
             seen.update(r)
         f, c_ref, _, _ = oracle_full(w)
