@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--bin-method", default="auto", choices=["auto", "direct", "tiled"])
     return ap.parse_args()
 
 
@@ -284,9 +285,12 @@ def main():
     Ks = torch.empty(info.kspec_elems, dtype=plan.real_dtype(), device=dev)
     dens = torch.empty(w.M, dtype=plan.real_dtype(), device=dev)
     ws = plan.workspace(dev)
-    # Binning method: the direct one (64-bit atomics into counts) is the
-    # faster of the two on these workloads; the tiled one needs a workspace.
-    bws = None
+    # Binning method: direct (64-bit atomics into counts) or tiled (counting
+    # sort by grid tile, shared-memory accumulation; needs a workspace).
+    method = args.bin_method
+    if method == "auto":
+        method = "direct"   # the faster of the two on every workload measured
+    bws = kde.bin_workspace(w.n, w.d, w.M, dev) if method == "tiled" else None
     dens_host = torch.empty(w.M, dtype=plan.real_dtype()).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
@@ -425,6 +429,7 @@ def main():
                        "l2": "flushed between timed steps (256 MB write)",
                        "launch": "CUDA graph replay per step" if graph is not None else "stream launches",
                        "streams": "kernel grid on a side stream, concurrent with binning",
+                       "binning": method,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline, "path_roofline": path_roof, "kernels": kernels,
             "kernel_timing": "CUDA events around each kernel on its stream, over the same K steps "
