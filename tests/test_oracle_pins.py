@@ -457,3 +457,102 @@ def test_wand_kernel_weights_direct_sum_equals_wand_layout():
         fw, _ = O.fft_wand(c, kc[tuple(slice(Lk, None) for Lk in L)], L)
         assert rel_max(O.binned_direct(c, kw, L), fw) < 1e-13
         assert rel_max(O.binned_direct(c, kc, L), fw) > 1e-3
+
+
+# --------------------------------------------------------------------------
+# LSCV on binned data (the bandwidth-selection functional the paper points to)
+# --------------------------------------------------------------------------
+def test_lscv_binned_equals_exact_for_samples_on_nodes():
+    """Samples exactly on grid nodes are binned without error; with the full
+    support (L = M-1, via a large tau) the binned pair sums equal the sums
+    over sample pairs, so binned LSCV = exact LSCV (brute-force double loop)."""
+    rng = np.random.default_rng(50)
+    M = (21, 17)
+    lo, hi = np.array([0.0, 0.0]), np.array([2.0, 1.6])      # delta = 0.1
+    nodes = np.stack([rng.integers(2, 19, 40), rng.integers(2, 15, 40)], axis=1)
+    X = lo + 0.1 * nodes
+    H = np.array([[0.02, 0.012], [0.012, 0.015]])
+    counts, n_out = O.bin_linear(X, lo, hi, M)
+    assert n_out == 0
+    got = O.lscv_binned(counts, len(X), H, lo, hi, M, tau=100.0)
+    want = O.lscv_exact(X, H)
+    assert abs(got - want) < 1e-12 * abs(want)
+
+
+def test_lscv_first_term_is_integral_of_square():
+    """(1/n^2) sum_{i,j} K_{2H}(X_i - X_j) = integral of f^2 (Gaussian
+    convolution), checked by quadrature of the estimate on a fine grid."""
+    rng = np.random.default_rng(51)
+    X = rng.normal(size=(7, 2)) * 0.3
+    H = np.array([[0.05, 0.02], [0.02, 0.04]])
+    g = np.linspace(-3, 3, 301)
+    G = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
+    f = O.direct_kde(X, H, G)
+    integral = float(np.sum(f * f)) * (g[1] - g[0]) ** 2
+    D = (X[:, None, :] - X[None, :, :]).reshape(-1, 2)
+    closed = float(np.sum(O.scaled_gaussian(D, 2 * H))) / len(X) ** 2
+    assert abs(integral - closed) < 1e-8 * closed
+
+
+def test_lscv_leave_one_out_term():
+    """The second term is (2/n) sum_i f_{-i}(X_i) with the leave-one-out
+    estimate written out sample by sample."""
+    rng = np.random.default_rng(52)
+    X = rng.normal(size=(9, 2)) * 0.5
+    H = np.array([[0.08, -0.03], [-0.03, 0.06]])
+    n = len(X)
+    loo = 0.0
+    for i in range(n):
+        others = np.delete(X, i, axis=0)
+        loo += float(np.sum(O.scaled_gaussian(X[i] - others, H))) / (n - 1)
+    D = (X[:, None, :] - X[None, :, :]).reshape(-1, 2)
+    first = float(np.sum(O.scaled_gaussian(D, 2 * H))) / n**2
+    assert abs(O.lscv_exact(X, H) - (first - 2.0 * loo / n)) < 1e-13
+
+
+def test_lscv_binned_spectral_form():
+    """S(A) = (1/prod P) sum_w |C(w)|^2 K_A(w) (Parseval on the zero-padded,
+    wrapped arrays) -- the identity the batched GPU evaluation relies on --
+    against the direct binned pair sum."""
+    rng = np.random.default_rng(53)
+    M = (24, 19)
+    X = rng.uniform(0.2, 0.8, size=(300, 2))
+    lo, hi = np.zeros(2), np.ones(2)
+    counts, _ = O.bin_linear(X, lo, hi, M)
+    c = O.counts_to_c(counts)
+    A = np.array([[0.004, 0.002], [0.002, 0.003]])
+    L = O.support_L(A, lo, hi, M)
+    P = (M[0] + L[0] + 3, M[1] + L[1] + 5)
+    k = O.kernel_weights(A, lo, hi, M, L, n=1)
+    kw = np.zeros(P)
+    for a in range(-L[0], L[0] + 1):
+        for b in range(-L[1], L[1] + 1):
+            kw[a % P[0], b % P[1]] = k[a + L[0], b + L[1]]
+    cp = np.zeros(P)
+    cp[: M[0], : M[1]] = c
+    C = O.dftn(cp, -1)
+    K = O.dftn(kw, -1)
+    spectral = float(np.sum(np.abs(C) ** 2 * K.real)) / np.prod(P)
+    direct = O.binned_pair_sum(c, A, lo, hi, M, L)
+    assert abs(spectral - direct) < 1e-12 * abs(direct)
+    assert np.max(np.abs(K.imag)) < 1e-12 * np.max(np.abs(K.real))
+
+
+def test_lscv_supports_follow_eq15_per_matrix():
+    """Each pair sum uses the support of its own matrix (Eq. 15 on H and on
+    2H): with tau = 3.7 the criterion matches the untruncated one to within
+    the tail of the Gaussian, far closer than if 2H were cut at H's support."""
+    rng = np.random.default_rng(54)
+    X = rng.normal(size=(400, 2)) * 0.4
+    H = np.array([[0.03, 0.015], [0.015, 0.02]])
+    lo, hi, M = np.array([-3.0, -3.0]), np.array([3.0, 3.0]), (61, 61)
+    counts, _ = O.bin_linear(X, lo, hi, M)
+    full = O.lscv_binned(counts, len(X), H, lo, hi, M, tau=100.0)
+    eq15 = O.lscv_binned(counts, len(X), H, lo, hi, M, tau=3.7)
+    c = O.counts_to_c(counts)
+    L1 = O.support_L(H, lo, hi, M)
+    S2_short = O.binned_pair_sum(c, 2 * H, lo, hi, M, L1)
+    S2_full = O.binned_pair_sum(c, 2 * H, lo, hi, M, (60, 60))
+    scale = S2_full / len(X) ** 2
+    assert abs(eq15 - full) < 3e-6 * scale
+    assert abs(S2_short - S2_full) / len(X) ** 2 > 3e-5 * scale
