@@ -176,6 +176,37 @@ kde_status kde_kernel_grid(kde_plan plan, int64_t n, void* Kspec, void* workspac
 kde_status kde_fft_eval(kde_plan plan, const int64_t* counts, const void* Kspec, void* density,
                         void* workspace, size_t workspace_bytes, kde_stream_t stream);
 
+/* Count spectrum for functionals of the estimate (Sec. 1 and Sec. 5: the
+ * same FFT machinery serves fast bandwidth selection).  W receives
+ * w_k |F(c)|^2 on the half spectrum, with c the counts in sample units
+ * (2^-32 folded in) and w_k = 2 on the last axis except 1 at k = 0 and at
+ * the Nyquist frequency, so that sum(W K) over the half spectrum is the
+ * full-spectrum sum.  Same element count, order and precision as the
+ * plan's kernel spectrum (plan.kspec_elems).  workspace as kde_fft_eval. */
+kde_status kde_power_spectrum(kde_plan plan, const int64_t* counts, void* W, void* workspace,
+                              size_t workspace_bytes, kde_stream_t stream);
+
+/* Least-squares cross-validation for nH candidate bandwidths H_i (host,
+ * nH x d x d row-major) on binned data, d = 1 or 2:
+ *   LSCV(H) = S(2H) / n^2 - 2 (S(H) - n K_H(0)) / (n (n - 1)),
+ *   S(A) = sum_j c_j sum_{|l| <= L(A)} c_{j-l} K_A(delta o l),
+ * the textbook criterion with every double sum over samples replaced by the
+ * binned sum (Eq. 2 form) that the FFT evaluates: S(A) = (1/prod P)
+ * sum_w |C(w)|^2 K_A(w) (Eq. 10 with Parseval), with L(A) from Eq. 15.  W is
+ * kde_power_spectrum's output for the same plan and counts; n the number of
+ * samples binned.  Every H_i and 2 H_i must be symmetric positive definite
+ * and fit the plan's padding (M_k + L_k <= P_k; raise opts.P_min), else
+ * KDE_ERR_NOT_SPD / KDE_ERR_INVALID_ARG before any launch.  Outputs (device,
+ * may alias nothing): lscv[nH]; pair_sums[2 nH] = S(H_0), S(2H_0), S(H_1), ...
+ * (may be NULL).  Kernel spectra are computed in batches of 32 candidates
+ * and never stored: their last pass is fused with the dot product against
+ * W; partial sums are FP64 and reduced in a fixed order.  workspace: at
+ * least kde_lscv_workspace_bytes(plan), 256-byte aligned. */
+kde_status kde_lscv(kde_plan plan, int64_t n, int nH, const double* H, const void* W,
+                    double* pair_sums, double* lscv, void* workspace, size_t workspace_bytes,
+                    kde_stream_t stream);
+kde_status kde_lscv_workspace_bytes(kde_plan plan, size_t* bytes);
+
 /* kde_fft_eval without a workspace argument, for callers that cannot
  * allocate device memory where they evaluate (for example code whose
  * allocations all belong to a host framework, or a loop that must never enter

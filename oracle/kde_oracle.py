@@ -414,3 +414,20 @@ def lscv_exact(X, H):
     S1 = float(np.sum(scaled_gaussian(D, H)))
     K0 = float(scaled_gaussian(np.zeros((1, X.shape[1])), H)[0])
     return S2 / n**2 - 2.0 * (S1 - n * K0) / (n * (n - 1.0))
+
+
+def binned_pair_sum_dft(c, A, lo, hi, M, L, P):
+    """S(A) by Eq. 10 and Parseval: counts zero-padded to P at the origin,
+    K_A(delta o l) at wrapped index l mod P (all signed lags), then
+    (1/prod P) sum_w |C(w)|^2 K(w).  Equals binned_pair_sum when P_k >= M_k + L_k."""
+    c = np.asarray(c, dtype=np.float64)
+    d = c.ndim
+    k = kernel_weights(A, lo, hi, M, L, n=1)
+    kw = np.zeros(P)
+    for lag in itertools.product(*[range(-Lk, Lk + 1) for Lk in L]):
+        kw[tuple(l % Pk for l, Pk in zip(lag, P))] = k[tuple(l + Lk for l, Lk in zip(lag, L))]
+    cp = np.zeros(P)
+    cp[tuple(slice(0, m) for m in M)] = c
+    C = dftn(cp, -1)
+    K = dftn(kw, -1)
+    return float(np.sum(np.abs(C) ** 2 * K.real)) / float(np.prod(P))

@@ -171,8 +171,7 @@ kde_rows_r2c_counts_kernel(const long long* __restrict__ counts, RowsParams<T> p
 // enumerates the leading lags (l_0, ..., l_{d-2}) with |l_k| <= L_k; the last
 // axis holds lag l at position l mod P.
 template <typename T>
-__global__ void __launch_bounds__(256)
-kde_rows_r2c_kgen_kernel(KGen<T> gen, RowsParams<T> p) {
+__device__ __forceinline__ void rows_kgen_body(const KGen<T>& gen, const RowsParams<T>& p) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = p.lp.N;
@@ -211,6 +210,12 @@ kde_rows_r2c_kgen_kernel(KGen<T> gen, RowsParams<T> p) {
   g.sync();
   V* z = line_fft<V, false>(a, b, p.lp, tw_s, g);
   store_r2c<T>(p, z, r0, g);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+kde_rows_r2c_kgen_kernel(KGen<T> gen, RowsParams<T> p) {
+  rows_kgen_body<T>(gen, p);
 }
 
 template <typename T>
@@ -299,7 +304,8 @@ kde_line1d_kernel(const long long* __restrict__ counts, const T* __restrict__ K,
   for (int m = g.lt; m < M; m += g.tpl) out[m] = y[m].x;
 }
 
-enum ColMode { COL_FWD = 0, COL_FWD_REAL = 1, COL_MID = 2, COL_INV = 3 };
+enum ColMode { COL_FWD = 0, COL_FWD_REAL = 1, COL_MID = 2, COL_INV = 3, COL_FWD_POWER = 4,
+               COL_FWD_DOT = 5 };
 
 template <typename T>
 struct ColsParams {
@@ -314,11 +320,37 @@ struct ColsParams {
   int tpl;         // threads per column
   LinePlan lp;
   const V* tw;
+  // COL_FWD_POWER: out_real = w(k) |2^-32 z|^2 with k = s mod Qw the
+  // last-axis frequency and w = 1 at k = 0 and k = Plw/2, else 2.
+  // COL_FWD_DOT: partial[blockIdx.x] += sum over the block of W * Re z.
+  int Qw, Plw;
+  const T* W;
+  double* partial;
 };
+
+__device__ __forceinline__ int half_weight(int64_t s, int Q, int Plast) {
+  const int k = (int)(s % Q);
+  return (k == 0 || 2 * k == Plast) ? 1 : 2;
+}
+
+// Block-wide sum of one double per thread, written by thread 0.
+__device__ __forceinline__ void block_sum_to(double v, double* out) {
+  __shared__ double warp_part[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += warp_part[w];
+    *out = t;
+  }
+}
 
 // W adjacent columns (s0 .. s0+W-1) of outer slab o, one line group each.
 template <typename T, int MODE>
-__device__ __forceinline__ void cols_body(const ColsParams<T>& p) {
+__device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t slab) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = p.lp.N;
@@ -331,7 +363,7 @@ __device__ __forceinline__ void cols_body(const ColsParams<T>& p) {
   int li;
   const LineGroup g = line_group(p.tpl, li);
   load_twiddles(tw_s, p.tw, P);
-  const int64_t o = blockIdx.y;
+  const int64_t o = slab;
   const int64_t s0 = (int64_t)blockIdx.x * W;
   const V* in = p.in + o * (int64_t)p.Nin * p.S;
   for (int idx0 = threadIdx.x; idx0 < P * W; idx0 += kLoadBatch * blockDim.x) {
@@ -375,8 +407,28 @@ __device__ __forceinline__ void cols_body(const ColsParams<T>& p) {
       T* dst = p.out_real + (o * p.S + s) * P;
       for (int k = g.lt; k < P; k += g.tpl) dst[k] = z[k].x;
     }
+    if (MODE == COL_FWD_POWER) {
+      T* dst = p.out_real + (o * p.S + s) * P;
+      const T w = (T)half_weight(s, p.Qw, p.Plw);
+      const T sc = (T)2.3283064365386963e-10;  // 2^-32
+      for (int k = g.lt; k < P; k += g.tpl) {
+        const T re = z[k].x * sc, im = z[k].y * sc;
+        dst[k] = w * (re * re + im * im);
+      }
+    }
   }
-  if (MODE == COL_FWD_REAL) return;
+  if (MODE == COL_FWD_DOT) {
+    double acc = 0.0;
+    if (s < p.S) {
+      const T* Wc = p.W + s * P;
+      T part = 0;
+      for (int k = g.lt; k < P; k += g.tpl) part += __ldg(Wc + k) * z[k].x;
+      acc = (double)part;
+    }
+    block_sum_to(acc, p.partial + blockIdx.x);
+    return;
+  }
+  if (MODE == COL_FWD_REAL || MODE == COL_FWD_POWER) return;
   // Every warp's result sits in the same buffer of its pair (same plan).
   const int zoff = (z == a) ? 0 : P;
   __syncthreads();
@@ -387,6 +439,11 @@ __device__ __forceinline__ void cols_body(const ColsParams<T>& p) {
     if (ss >= p.S) continue;
     p.out[(o * nout + pos) * p.S + ss] = lines[t * LS + zoff + pos];
   }
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ void cols_body(const ColsParams<T>& p) {
+  cols_body_slab<T, MODE>(p, blockIdx.y);
 }
 
 // Column passes with many columns: a block holds kSimdW adjacent columns
@@ -448,7 +505,7 @@ __device__ V* simd_fft(V* a, V* b, const LinePlan& lp, const V* __restrict__ tw,
 }
 
 template <typename T, int MODE>
-__device__ __forceinline__ void cols_simd_body(const ColsParams<T>& p) {
+__device__ __forceinline__ void cols_simd_body_slab(const ColsParams<T>& p, int64_t slab) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = p.lp.N;
@@ -457,7 +514,7 @@ __device__ __forceinline__ void cols_simd_body(const ColsParams<T>& p) {
   V* bufB = bufA + P * kSimdW;
   const int c = threadIdx.x % kSimdW, g = threadIdx.x / kSimdW, ng = blockDim.x / kSimdW;
   load_twiddles(tw_s, p.tw, P);
-  const int64_t o = blockIdx.y;
+  const int64_t o = slab;
   const int64_t s = (int64_t)blockIdx.x * kSimdW + c;
   const bool col_ok = s < p.S;
   const V* in = p.in + o * (int64_t)p.Nin * p.S;
@@ -489,14 +546,40 @@ __device__ __forceinline__ void cols_simd_body(const ColsParams<T>& p) {
     V* other = (z == bufA) ? bufB : bufA;
     z = simd_fft<V, true>(z, other, p.lp, tw_s, c, g, ng);
   }
+  if (MODE == COL_FWD_DOT) {
+    double acc = 0.0;
+    if (col_ok) {
+      T part = 0;
+      for (int pos = g; pos < P; pos += ng)
+        part += __ldg(p.W + (int64_t)pos * p.S + s) * z[pos * kSimdW + c].x;
+      acc = (double)part;
+    }
+    block_sum_to(acc, p.partial + blockIdx.x);
+    return;
+  }
   if (!col_ok) return;
   if (MODE == COL_FWD_REAL) {
     for (int pos = g; pos < P; pos += ng)
       p.out_real[(o * P + pos) * p.S + s] = z[pos * kSimdW + c].x;
     return;
   }
+  if (MODE == COL_FWD_POWER) {
+    const T w = (T)half_weight(s, p.Qw, p.Plw);
+    const T sc = (T)2.3283064365386963e-10;  // 2^-32
+    for (int pos = g; pos < P; pos += ng) {
+      const V v = z[pos * kSimdW + c];
+      const T re = v.x * sc, im = v.y * sc;
+      p.out_real[(o * P + pos) * p.S + s] = w * (re * re + im * im);
+    }
+    return;
+  }
   const int nout = (MODE == COL_FWD) ? P : p.Nout;
   for (int pos = g; pos < nout; pos += ng) p.out[(o * nout + pos) * p.S + s] = z[pos * kSimdW + c];
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ void cols_simd_body(const ColsParams<T>& p) {
+  cols_simd_body_slab<T, MODE>(p, blockIdx.y);
 }
 
 template <typename T, bool SIMD>
@@ -528,6 +611,103 @@ __global__ void __launch_bounds__(256) kde_cols_mid_kernel(ColsParams<T> p) {
     cols_body<T, COL_MID>(p);
 }
 template <typename T, bool SIMD>
+__global__ void __launch_bounds__(256) kde_cols_power_kernel(ColsParams<T> p) {
+  if (SIMD)
+    cols_simd_body<T, COL_FWD_POWER>(p);
+  else
+    cols_body<T, COL_FWD_POWER>(p);
+}
+
+// Batched kernel spectra (Eq. 6 and Eq. 10 for many matrices at once): one
+// chunk holds up to kBatch matrices; blockIdx.y picks the matrix.
+constexpr int kBatch = 64;
+
+template <typename T>
+struct BatchKGen {
+  int nb;
+  KGen<T> gen[kBatch];
+  int rows[kBatch];       // rows of the matrix's lag grid (2 L_0 + 1; 1 for d = 1)
+  int64_t off[kBatch];    // its first row in the chunk's scratch (complex elements)
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) kde_rows_kgen_batch_kernel(BatchKGen<T> bk, RowsParams<T> p) {
+  const int b = blockIdx.y;
+  if (b >= bk.nb) return;
+  RowsParams<T> q = p;
+  q.nrows = bk.rows[b];
+  if (p.out_real)
+    q.out_real = p.out_real + (int64_t)b * p.Q;
+  else
+    q.out = p.out + bk.off[b];
+  rows_kgen_body<T>(bk.gen[b], q);
+}
+
+// Axis-0 pass of the batched spectra, fused with the dot product against the
+// count spectrum W: no kernel spectrum is written.  Partials are laid out
+// [matrix][column block].
+template <typename T, bool SIMD>
+__global__ void __launch_bounds__(256) kde_cols_kgen_dot_kernel(BatchKGen<T> bk, ColsParams<T> p) {
+  const int b = blockIdx.y;
+  if (b >= bk.nb) return;
+  ColsParams<T> q = p;
+  q.in = p.in + bk.off[b];
+  q.Nin = bk.rows[b];
+  q.Lw = bk.gen[b].L[0];
+  q.partial = p.partial + (int64_t)b * gridDim.x;
+  // the bodies index the outer slab by blockIdx.y; here there is one slab
+  if (SIMD)
+    cols_simd_body_slab<T, COL_FWD_DOT>(q, 0);
+  else
+    cols_body_slab<T, COL_FWD_DOT>(q, 0);
+}
+
+// d = 1: dot of the real spectrum of matrix b with W.
+template <typename T>
+__global__ void __launch_bounds__(256) kde_dot1d_kernel(int nb, const T* __restrict__ K, int Q,
+                                                        const T* __restrict__ W,
+                                                        double* __restrict__ partial) {
+  const int b = blockIdx.x;
+  if (b >= nb) return;
+  T part = 0;
+  for (int k = threadIdx.x; k < Q; k += blockDim.x) part += W[k] * K[(int64_t)b * Q + k];
+  block_sum_to((double)part, partial + b);
+}
+
+// Pair sums S_b = scale * sum of the matrix's partials (fixed order, FP64),
+// then LSCV_i = S(2H_i) / n^2 - 2 (S(H_i) - n K_{H_i}(0)) / (n (n - 1)) for
+// matrices ordered H_0, 2H_0, H_1, 2H_1, ...
+struct LscvReduce {
+  int nb, nparts;
+  double scale, n;
+  double K0[kBatch / 2];
+};
+
+__global__ void __launch_bounds__(32) kde_lscv_reduce_kernel(LscvReduce r, const double* __restrict__ partial,
+                                                             double* __restrict__ S_out,
+                                                             double* __restrict__ lscv_out) {
+  const int i = blockIdx.x;  // candidate within the chunk
+  if (2 * i + 1 >= r.nb) return;
+  double s[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const double* pp = partial + (int64_t)(2 * i + h) * r.nparts;
+    double v = 0.0;
+    for (int j = threadIdx.x; j < r.nparts; j += 32) v += pp[j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    s[h] = __shfl_sync(0xffffffffu, v, 0) * r.scale;
+  }
+  if (threadIdx.x == 0) {
+    if (S_out) {
+      S_out[2 * i] = s[0];
+      S_out[2 * i + 1] = s[1];
+    }
+    lscv_out[i] = s[1] / (r.n * r.n) - 2.0 * (s[0] - r.n * r.K0[i]) / (r.n * (r.n - 1.0));
+  }
+}
+
+template <typename T, bool SIMD>
 __global__ void __launch_bounds__(256) kde_cols_inv_kernel(ColsParams<T> p) {
   if (SIMD)
     cols_simd_body<T, COL_INV>(p);
@@ -546,7 +726,12 @@ cudaError_t allow_smem(F* fn) {
   static std::set<const void*> done;
   std::lock_guard<std::mutex> lk(mu);
   if (done.count((const void*)fn)) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+  // the opt-in limit covers static and dynamic shared memory together
+  cudaFuncAttributes attr{};
+  cudaError_t e = cudaFuncGetAttributes(&attr, fn);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kSmemMax - attr.sharedSizeBytes));
   if (e == cudaSuccess) done.insert((const void*)fn);
   return e;
 }
@@ -835,6 +1020,219 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
   return launch_rows<T>(kde_rows_c2r_kernel<T>, "kde_rows_c2r_kernel", rows, cr, st);
 }
 
+// ---------------------------------------------------------------------------
+// Count spectrum and batched pair sums (bandwidth selection by LSCV).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) kde_power1d_kernel(const typename Cplx<T>::type* __restrict__ X,
+                                                          T* __restrict__ W, int Q, int P) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Q; k += gridDim.x * blockDim.x) {
+    const T sc = (T)2.3283064365386963e-10;  // 2^-32
+    const T re = X[k].x * sc, im = X[k].y * sc;
+    W[k] = (T)half_weight(k, Q, P) * (re * re + im * im);
+  }
+}
+
+// W = w(k) |2^-32 C|^2 on the half spectrum, in the kernel spectrum's order.
+template <typename T>
+kde_status power_spectrum_impl(kde_plan_s* plan, const int64_t* counts, void* Wout, void* ws,
+                               cudaStream_t st) {
+  using V = typename Cplx<T>::type;
+  const kde_plan_info& I = plan->info;
+  const int d = I.d, dl = d - 1;
+  const long long* cnt = reinterpret_cast<const long long*>(counts);
+  V* A = (V*)ws;
+  int64_t rows = 1;
+  for (int k = 0; k < d - 1; ++k) rows *= I.M[k];
+  RowsParams<T> rp{};
+  rp.nrows = rows;
+  rp.Min = (int)I.M[dl];
+  rp.in_stride = I.M[dl];
+  rp.Q = (int)I.Q;
+  rp.out = A;
+  rp.lp = line_plan(I, dl);
+  rp.tw = twiddles<T>(plan, dl);
+  kde_status s = launch_rows<T>(kde_rows_r2c_counts_kernel<T>, "kde_rows_r2c_counts_kernel", rows,
+                                rp, st, cnt);
+  if (s != KDE_OK) return s;
+  if (d == 1) {
+    LaunchScope ls("kde_power1d_kernel", st);
+    kde_power1d_kernel<T><<<(unsigned)((I.Q + 255) / 256), 256, 0, st>>>(A, (T*)Wout, (int)I.Q,
+                                                                         (int)I.P[0]);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KDE_OK : cuda_fail(e, "kde_power1d_kernel");
+  }
+  const V* src = A;
+  int64_t S = I.Q;
+  if (d == 3) {
+    V* B = A + rows * I.Q;
+    ColsParams<T> c1{};
+    c1.in = A;
+    c1.out = B;
+    c1.S = I.Q;
+    c1.Nin = (int)I.M[1];
+    c1.Lw = -1;
+    c1.lp = line_plan(I, 1);
+    c1.tw = twiddles<T>(plan, 1);
+    s = launch_cols<T>(KDE_COLS(kde_cols_fwd_kernel), c1, I.M[0], plan->cols_variant, st,
+                       "kde_cols_fwd_kernel");
+    if (s != KDE_OK) return s;
+    src = B;
+    S = I.P[1] * I.Q;
+  }
+  ColsParams<T> c0{};
+  c0.in = src;
+  c0.out_real = (T*)Wout;
+  c0.S = S;
+  c0.Nin = (int)I.M[0];
+  c0.Lw = -1;
+  c0.lp = line_plan(I, 0);
+  c0.tw = twiddles<T>(plan, 0);
+  c0.Qw = (int)I.Q;
+  c0.Plw = (int)I.P[dl];
+  return launch_cols<T>(KDE_COLS(kde_cols_power_kernel), c0, 1, plan->cols_variant, st,
+                        "kde_cols_power_kernel");
+}
+
+// Kernel-grid parameters of K_A (no 1/n, 2^-32 or 1/prod P folded in).
+template <typename T>
+KGen<T> kgen_for(const kde_plan_info& I, const double* Ainv, double detA, const int64_t* L,
+                 int wand) {
+  KGen<T> g{};
+  g.d = I.d;
+  g.wand = wand;
+  for (int k = 0; k < I.d; ++k) g.L[k] = (int)L[k];
+  for (int a = 0; a < I.d; ++a)
+    for (int b = 0; b < I.d; ++b) g.A[a][b] = (T)(I.delta[a] * I.delta[b] * Ainv[a * I.d + b]);
+  g.C = (T)(std::pow(6.283185307179586476925287, -0.5 * I.d) / std::sqrt(detA));
+  return g;
+}
+
+// Scratch for one chunk of kBatch matrices: lag-grid rows (at most
+// 2 (P_0 - M_0) + 1 per matrix, since every accepted matrix has
+// M_0 + L_0 <= P_0) and the partial sums.
+size_t lscv_workspace(const kde_plan_info& I) {
+  const size_t cb = (I.precision == KDE_F32) ? 8 : 16;
+  const int64_t rows_max = (I.d == 1) ? 1 : 2 * (I.P[0] - I.M[0]) + 1;
+  int64_t S = I.Q;
+  if (I.d == 3) S = I.P[1] * I.Q;
+  // lag rows of the last axis for d = 2; d = 1 keeps one real spectrum row
+  const size_t t1 = (size_t)kBatch * rows_max * I.Q * cb;
+  const size_t parts = (size_t)kBatch * (size_t)(S + 1) * sizeof(double);
+  return ((t1 + 255) & ~(size_t)255) + parts;
+}
+
+template <typename T>
+kde_status lscv_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, const void* Wsp,
+                     double* S_out, double* lscv_out, void* ws, cudaStream_t st) {
+  using V = typename Cplx<T>::type;
+  const kde_plan_info& I = plan->info;
+  const int d = I.d;
+  double prodP = 1.0;
+  for (int k = 0; k < d; ++k) prodP *= (double)I.P[k];
+  const size_t cb = sizeof(V);
+  const int64_t rows_max = (d == 1) ? 1 : 2 * (I.P[0] - I.M[0]) + 1;
+  const size_t t1_bytes = ((size_t)kBatch * rows_max * I.Q * cb + 255) & ~(size_t)255;
+  V* T1 = (V*)ws;
+  double* partial = (double*)((char*)ws + t1_bytes);
+  int64_t S = I.Q;
+  const int chunk_h = kBatch / 2;
+  for (int h0 = 0; h0 < nH; h0 += chunk_h) {
+    const int nh = std::min(chunk_h, nH - h0);
+    BatchKGen<T> bk{};
+    LscvReduce red{};
+    bk.nb = 2 * nh;
+    int64_t off = 0;
+    int max_rows = 1;
+    for (int i = 0; i < nh; ++i) {
+      const double* H = Hs + (size_t)(h0 + i) * d * d;
+      for (int h = 0; h < 2; ++h) {
+        double A[9], Ainv[9], detA;
+        int64_t L[KDE_MAX_D];
+        for (int e = 0; e < d * d; ++e) A[e] = (h ? 2.0 : 1.0) * H[e];
+        kde_status st2 = kde::matrix_support(plan, A, Ainv, &detA, L);
+        if (st2 != KDE_OK) return st2;
+        const int b = 2 * i + h;
+        bk.gen[b] = kgen_for<T>(I, Ainv, detA, L, plan->layout_mode == KDE_LAYOUT_WAND);
+        bk.rows[b] = (d == 1) ? 1 : (int)(2 * L[0] + 1);
+        bk.off[b] = off;
+        off += (int64_t)bk.rows[b] * I.Q;
+        max_rows = std::max(max_rows, bk.rows[b]);
+        if (h == 0) red.K0[i] = std::pow(6.283185307179586476925287, -0.5 * d) / std::sqrt(detA);
+      }
+    }
+    const int dl = d - 1;
+    RowsParams<T> rp{};
+    rp.Q = (int)I.Q;
+    rp.lp = line_plan(I, dl);
+    rp.tw = twiddles<T>(plan, dl);
+    if (d == 1)
+      rp.out_real = (T*)T1;
+    else
+      rp.out = T1;
+    {
+      const int P = rp.lp.N;
+      const int64_t pairs = (max_rows + 1) / 2;
+      const LineShape sh = line_shape<T>(pairs * bk.nb, P, 1);
+      rp.tpl = sh.tpl;
+      auto* fn = kde_rows_kgen_batch_kernel<T>;
+      cudaError_t e = allow_smem(fn);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      LaunchScope ls("kde_rows_kgen_batch_kernel", st);
+      dim3 grid((unsigned)((pairs + sh.lpb - 1) / sh.lpb), (unsigned)bk.nb);
+      fn<<<grid, sh.tpl * sh.lpb, line_smem<T>(P, sh.lpb), st>>>(bk, rp);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_rows_kgen_batch_kernel");
+    }
+    int nparts;
+    if (d == 1) {
+      nparts = 1;
+      LaunchScope ls("kde_dot1d_kernel", st);
+      kde_dot1d_kernel<T><<<bk.nb, 256, 0, st>>>(bk.nb, (const T*)T1, (int)I.Q, (const T*)Wsp, partial);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "kde_dot1d_kernel");
+    } else {
+      ColsParams<T> cp{};
+      cp.in = T1;
+      cp.S = S;
+      cp.lp = line_plan(I, 0);
+      cp.tw = twiddles<T>(plan, 0);
+      cp.W = (const T*)Wsp;
+      cp.partial = partial;
+      const int P = cp.lp.N;
+      cudaError_t e;
+      if (simd_cols<T>(plan->cols_variant, S, P)) {
+        auto* fn = kde_cols_kgen_dot_kernel<T, true>;
+        if ((e = allow_smem(fn)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        nparts = (int)((S + kSimdW - 1) / kSimdW);
+        LaunchScope ls("kde_cols_kgen_dot_kernel", st);
+        fn<<<dim3((unsigned)nparts, (unsigned)bk.nb), 256,
+             (size_t)(1 + 2 * kSimdW) * P * sizeof(V), st>>>(bk, cp);
+      } else {
+        const LineShape sh = line_shape<T>(S * bk.nb, P, 2);
+        cp.tpl = sh.tpl;
+        auto* fn = kde_cols_kgen_dot_kernel<T, false>;
+        if ((e = allow_smem(fn)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        nparts = (int)((S + sh.lpb - 1) / sh.lpb);
+        LaunchScope ls("kde_cols_kgen_dot_kernel", st);
+        fn<<<dim3((unsigned)nparts, (unsigned)bk.nb), sh.tpl * sh.lpb, line_smem<T>(P, sh.lpb), st>>>(bk, cp);
+      }
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_cols_kgen_dot_kernel");
+    }
+    red.nb = bk.nb;
+    red.nparts = nparts;
+    red.scale = 1.0 / prodP;
+    red.n = (double)n;
+    {
+      LaunchScope ls("kde_lscv_reduce_kernel", st);
+      kde_lscv_reduce_kernel<<<nh, 32, 0, st>>>(red, partial, S_out ? S_out + 2 * h0 : nullptr,
+                                                lscv_out + h0);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "kde_lscv_reduce_kernel");
+    }
+  }
+  return KDE_OK;
+}
+
 kde_status check_ws(const kde_plan_s* plan, void* ws, size_t bytes) {
   if (plan->info.workspace_bytes == 0) return KDE_OK;
   if (!ws) return fail(KDE_ERR_WORKSPACE, "workspace is NULL");
@@ -932,4 +1330,45 @@ extern "C" kde_status kde_fft_eval_noalloc(kde_plan plan, const int64_t* counts,
   if (plan->info.precision == KDE_F32)
     return fft_eval_impl<float>(plan, counts, Kspec, density, scratch, st);
   return fft_eval_impl<double>(plan, counts, Kspec, density, scratch, st);
+}
+
+// ---------------------------------------------------------------------------
+// Count spectrum and LSCV entry points.
+// ---------------------------------------------------------------------------
+extern "C" kde_status kde_power_spectrum(kde_plan plan, const int64_t* counts, void* W,
+                                         void* workspace, size_t workspace_bytes,
+                                         kde_stream_t stream) {
+  if (!plan || !counts || !W) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  kde_status s = check_ws(plan, workspace, workspace_bytes);
+  if (s != KDE_OK) return s;
+  if ((s = check_device(plan)) != KDE_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->info.precision == KDE_F32) return power_spectrum_impl<float>(plan, counts, W, workspace, st);
+  return power_spectrum_impl<double>(plan, counts, W, workspace, st);
+}
+
+extern "C" kde_status kde_lscv_workspace_bytes(kde_plan plan, size_t* bytes) {
+  if (!plan || !bytes) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (plan->info.d == 3) return fail(KDE_ERR_UNSUPPORTED, "LSCV batches support d = 1, 2");
+  *bytes = lscv_workspace(plan->info);
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_lscv(kde_plan plan, int64_t n, int nH, const double* H, const void* W,
+                               double* pair_sums, double* lscv, void* workspace,
+                               size_t workspace_bytes, kde_stream_t stream) {
+  if (!plan || !H || !W || !lscv) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (plan->info.d == 3) return fail(KDE_ERR_UNSUPPORTED, "LSCV batches support d = 1, 2");
+  if (n < 2) return fail(KDE_ERR_INVALID_ARG, "LSCV needs n >= 2");
+  if (nH < 0) return fail(KDE_ERR_INVALID_ARG, "nH < 0");
+  if (nH == 0) return KDE_OK;
+  if (!workspace || workspace_bytes < lscv_workspace(plan->info))
+    return fail(KDE_ERR_WORKSPACE, "workspace smaller than kde_lscv_workspace_bytes");
+  if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  kde_status s = check_device(plan);
+  if (s != KDE_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->info.precision == KDE_F32)
+    return lscv_impl<float>(plan, n, nH, H, W, pair_sums, lscv, workspace, st);
+  return lscv_impl<double>(plan, n, nH, H, W, pair_sums, lscv, workspace, st);
 }

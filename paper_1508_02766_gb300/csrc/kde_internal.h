@@ -28,6 +28,8 @@ struct kde_plan_s {
 namespace kde {
 
 kde_status fail(kde_status s, const std::string& msg);
+kde_status matrix_support(const kde_plan_s* plan, const double* A, double* Ainv, double* detA,
+                          int64_t* L);
 kde_status cuda_fail(cudaError_t e, const char* what);
 
 // Launch bookkeeping: counts launches and, when profiling is on, records a

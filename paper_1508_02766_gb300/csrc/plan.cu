@@ -180,6 +180,42 @@ static int radix_plan(int64_t P, int* radix) {
   return n;
 }
 
+// Factors of a bandwidth matrix A evaluated under an existing plan: A^-1,
+// |A| and the support L (Eq. 15 with the plan's tau and range mode).  Fails
+// if A is not symmetric positive definite or needs more padding than the
+// plan has (M_k + L_k > P_k).
+kde_status matrix_support(const kde_plan_s* plan, const double* A, double* Ainv, double* detA,
+                          int64_t* L) {
+  const kde_plan_info& I = plan->info;
+  const int d = I.d;
+  double amax = 0.0;
+  for (int i = 0; i < d * d; ++i) {
+    if (!std::isfinite(A[i])) return fail(KDE_ERR_INVALID_ARG, "bandwidth has a non-finite entry");
+    amax = std::fmax(amax, std::fabs(A[i]));
+  }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(A[i * d + j] - A[j * d + i]) > 1e-12 * amax)
+        return fail(KDE_ERR_INVALID_ARG, "bandwidth is not symmetric");
+  double R[9];
+  if (!cholesky(d, A, R)) return fail(KDE_ERR_NOT_SPD, "bandwidth is not positive definite");
+  double det = 1.0;
+  for (int i = 0; i < d; ++i) det *= R[i * 3 + i] * R[i * 3 + i];
+  *detA = det;
+  spd_inverse(d, R, Ainv);
+  const double lam = lambda_max(d, A);
+  for (int k = 0; k < d; ++k) {
+    const double half = (plan->range_mode == KDE_RANGE_CORRECTED)
+                            ? plan->tau * std::sqrt(std::fabs(lam))
+                            : plan->tau * std::sqrt(A[k * d + k]);
+    const double c = std::ceil(half / I.delta[k]);
+    L[k] = (c >= (double)(I.M[k] - 1)) ? I.M[k] - 1 : (int64_t)c;
+    if (I.M[k] + L[k] > I.P[k])
+      return fail(KDE_ERR_INVALID_ARG, "bandwidth needs more padding than the plan has (raise P_min)");
+  }
+  return KDE_OK;
+}
+
 }  // namespace kde
 
 using namespace kde;
@@ -251,7 +287,9 @@ static kde_status compute_info(int d, const int64_t* M, const double* lo, const 
   info->kspec_bytes = (size_t)ke * real_b;
   // Scratch (complex elements): evaluation and kernel-grid intermediates.
   int64_t Q = info->Q, ev = 0, kg = 0;
-  if (d == 2) {
+  if (d == 1) {
+    ev = Q;  // the half spectrum of the count spectrum (kde_power_spectrum)
+  } else if (d == 2) {
     ev = M[0] * Q;
     kg = (2 * info->L[0] + 1) * Q;
   } else if (d == 3) {

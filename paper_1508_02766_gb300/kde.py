@@ -52,7 +52,8 @@ EXPORTS = [
     "kde_plan_info_compute", "kde_plan_create", "kde_plan_get_info", "kde_plan_destroy",
     "kde_bin", "kde_kernel_grid", "kde_fft_eval", "kde_status_string", "kde_last_error",
     "kde_launch_count", "kde_profile_enable", "kde_profile_count", "kde_profile_entry",
-    "kde_fft_eval_noalloc", "kde_bin_workspace_bytes",
+    "kde_fft_eval_noalloc", "kde_bin_workspace_bytes", "kde_power_spectrum", "kde_lscv",
+    "kde_lscv_workspace_bytes",
 ]
 
 _lib = None
@@ -80,6 +81,9 @@ def lib():
     L.kde_kernel_grid.argtypes = [vp, i64, vp, vp, ctypes.c_size_t, vp]
     L.kde_fft_eval.argtypes = [vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.kde_fft_eval_noalloc.argtypes = [vp, vp, vp, vp, vp]
+    L.kde_power_spectrum.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.kde_lscv.argtypes = [vp, i64, ctypes.c_int, dp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.kde_lscv_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.kde_status_string.restype = ctypes.c_char_p
     L.kde_status_string.argtypes = [ctypes.c_int]
     L.kde_last_error.restype = ctypes.c_char_p
@@ -90,7 +94,8 @@ def lib():
     for name in ("kde_plan_info_compute", "kde_plan_create", "kde_plan_get_info",
                  "kde_plan_destroy", "kde_bin", "kde_kernel_grid", "kde_fft_eval",
                  "kde_fft_eval_noalloc", "kde_profile_enable", "kde_profile_entry",
-                 "kde_bin_workspace_bytes"):
+                 "kde_bin_workspace_bytes", "kde_power_spectrum", "kde_lscv",
+                 "kde_lscv_workspace_bytes"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -277,6 +282,42 @@ def kde_fft_eval(plan: Plan, counts, Kspec, density=None, workspace=None, stream
                               _ptr(workspace), workspace.numel() * workspace.element_size(),
                               _stream_ptr(stream)))
     return density
+
+
+def kde_power_spectrum(plan: Plan, counts, W=None, workspace=None, stream=None):
+    """w |F(c)|^2 on the half spectrum, in the plan's kernel-spectrum order."""
+    import torch
+    if W is None:
+        W = torch.empty(plan.info.kspec_elems, dtype=plan.real_dtype(), device="cuda")
+    if workspace is None:
+        workspace = plan.workspace()
+    _check(lib().kde_power_spectrum(plan.handle, _ptr(counts), _ptr(W), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(),
+                                    _stream_ptr(stream)))
+    return W
+
+
+def kde_lscv_workspace_bytes(plan: Plan) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().kde_lscv_workspace_bytes(plan.handle, ctypes.byref(b)))
+    return int(b.value)
+
+
+def kde_lscv(plan: Plan, n, H, W, lscv=None, pair_sums=None, workspace=None, stream=None):
+    """LSCV(H_i) for a batch of candidate bandwidths (host array nH x d x d)."""
+    import torch
+    H = np.ascontiguousarray(np.asarray(H, dtype=np.float64))
+    nH = H.shape[0]
+    if lscv is None:
+        lscv = torch.empty(nH, dtype=torch.float64, device="cuda")
+    if workspace is None:
+        workspace = torch.empty(max(256, kde_lscv_workspace_bytes(plan)), dtype=torch.uint8,
+                                device="cuda")
+    Hc = (ctypes.c_double * H.size)(*[float(v) for v in H.ravel()])
+    _check(lib().kde_lscv(plan.handle, int(n), nH, Hc, _ptr(W), _ptr(pair_sums), _ptr(lscv),
+                          _ptr(workspace), workspace.numel() * workspace.element_size(),
+                          _stream_ptr(stream)))
+    return lscv
 
 
 NOALLOC_SCRATCH_BYTES = 8 << 20

@@ -153,3 +153,67 @@ def small_case(seed, d, M, n, precision="f64", H=None, corr=0.7, scale=0.05):
     dt = np.float64 if precision == "f64" else np.float32
     return Workload(f"small_d{d}", X.astype(dt), np.asarray(H, dtype=np.float64),
                     lo, hi, tuple(int(m) for m in M), precision)
+
+
+def log_cholesky_candidates(rng, count, d=2, diag_lo=-4.0, diag_hi=0.0, off=1.0):
+    """Candidate bandwidths H = R R^T, R lower triangular with diagonal
+    exp(U[diag_lo, diag_hi]) and off-diagonal U[-off, off]."""
+    out = np.empty((count, d, d))
+    for i in range(count):
+        R = np.zeros((d, d))
+        R[np.diag_indices(d)] = np.exp(rng.uniform(diag_lo, diag_hi, size=d))
+        for a in range(d):
+            for b in range(a):
+                R[a, b] = rng.uniform(-off, off)
+        out[i] = R @ R.T
+    return out
+
+
+@dataclass
+class LscvWorkload:
+    """Bandwidth selection: one binned grid, many candidate bandwidths."""
+
+    name: str
+    X: np.ndarray
+    H: np.ndarray          # (count, d, d)
+    lo: np.ndarray
+    hi: np.ndarray
+    M: tuple
+    precision: str
+    tau: float = 3.7
+
+    @property
+    def d(self):
+        return self.X.shape[1]
+
+    @property
+    def n(self):
+        return self.X.shape[0]
+
+
+def lscv2d_512_f32(seed=4, n=2_000_000, count=1024):
+    """d=2, n=2e6 from the 3-component mixture, 512^2 grid, 1024 candidate H
+    sampled in log-Cholesky space; the grid covers the data plus
+    4 sqrt(largest eigenvalue over the candidates)."""
+    rng = np.random.default_rng(seed)
+    X = mixture_samples(rng, n, MIX2_MEANS, MIX2_COVS)
+    H = log_cholesky_candidates(rng, count)
+    lam = max(float(np.linalg.eigvalsh(h).max()) for h in H)
+    pad = 4.0 * np.sqrt(lam)
+    lo = X.min(axis=0) - pad
+    hi = X.max(axis=0) + pad
+    return LscvWorkload("lscv2d_512_f32", X.astype(np.float32), H, lo, hi, (512, 512), "f32")
+
+
+def lscv_small(seed, d, M, n, count, precision="f64", diag_lo=-4.0, diag_hi=-1.5):
+    """A small bandwidth-selection problem for parity tests."""
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(-1.0, 1.0, size=(2, d))
+    covs = [np.eye(d) * 0.2, np.eye(d) * 0.05]
+    X = mixture_samples(rng, n, means, covs)
+    H = log_cholesky_candidates(rng, count, d, diag_lo, diag_hi, off=0.1)
+    lam = max(float(np.linalg.eigvalsh(h).max()) for h in H)
+    pad = 4.0 * np.sqrt(lam)
+    dt = np.float64 if precision == "f64" else np.float32
+    return LscvWorkload(f"lscv_small_d{d}", X.astype(dt), H, X.min(axis=0) - pad,
+                        X.max(axis=0) + pad, tuple(int(m) for m in M), precision)

@@ -556,3 +556,20 @@ def test_lscv_supports_follow_eq15_per_matrix():
     scale = S2_full / len(X) ** 2
     assert abs(eq15 - full) < 3e-6 * scale
     assert abs(S2_short - S2_full) / len(X) ** 2 > 3e-5 * scale
+
+
+def test_pair_sum_dft_equals_direct():
+    """The spectral pair sum (zero-padded, wrapped, Parseval) equals the direct
+    binned pair sum for any padding P >= M + L, in 1-D and 2-D."""
+    rng = np.random.default_rng(55)
+    for d, M in [(1, (40,)), (2, (18, 23))]:
+        X = rng.uniform(0.1, 0.9, size=(200, d))
+        lo, hi = np.zeros(d), np.ones(d)
+        counts, _ = O.bin_linear(X, lo, hi, M)
+        c = O.counts_to_c(counts)
+        A = random_spd(rng, d, 0.003)
+        L = O.support_L(A, lo, hi, M)
+        direct = O.binned_pair_sum(c, A, lo, hi, M, L)
+        for extra in (0, 7):
+            P = tuple(m + l + extra for m, l in zip(M, L))
+            assert abs(O.binned_pair_sum_dft(c, A, lo, hi, M, L, P) - direct) < 1e-12 * abs(direct)
