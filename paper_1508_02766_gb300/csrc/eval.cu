@@ -354,10 +354,14 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = p.lp.N;
-  const int W = blockDim.x / p.tpl;
+  // Passes whose columns are Hermitian (the kernel spectrum's last pass: k is
+  // real and even, so every column transforms to a real line) transform two
+  // columns per FFT: F(x1 + i x2) = F(x1) + i F(x2) with both real.
+  constexpr bool PAIRED = MODE == COL_FWD_REAL || MODE == COL_FWD_DOT;
+  const int W = (PAIRED ? 2 : 1) * (blockDim.x / p.tpl);
   V* tw_s = reinterpret_cast<V*>(smem_raw);
-  // Column t owns lines[t LS ..): its buffer, then its scratch.  LS = 2P + 1
-  // puts the W columns of one position in different banks.
+  // Line t owns lines[t LS ..): its buffer, then its scratch.  LS = 2P + 1
+  // puts the lines of one position in different banks.
   const int LS = 2 * P + 1;
   V* lines = tw_s + P;
   int li;
@@ -366,6 +370,54 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
   const int64_t o = slab;
   const int64_t s0 = (int64_t)blockIdx.x * W;
   const V* in = p.in + o * (int64_t)p.Nin * p.S;
+  if (PAIRED) {
+    // line t holds columns s0 + 2t (real part) and s0 + 2t + 1 (imaginary)
+    const int npair = W / 2;
+    for (int idx0 = threadIdx.x; idx0 < P * npair; idx0 += kLoadBatch * blockDim.x) {
+      V v1[kLoadBatch], v2[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = idx0 + u * blockDim.x;
+        const int pos = idx / npair, t = idx - pos * npair;
+        const int n = source_row(pos, P, p.Lw, p.Nin);
+        const int64_t s = s0 + 2 * t;
+        const bool ok = idx < P * npair && n < p.Nin;
+        v1[u] = (ok && s < p.S) ? in[(int64_t)n * p.S + s] : mk<V>(0, 0);
+        v2[u] = (ok && s + 1 < p.S) ? in[(int64_t)n * p.S + s + 1] : mk<V>(0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = idx0 + u * blockDim.x;
+        const int pos = idx / npair, t = idx - pos * npair;
+        if (idx < P * npair) lines[t * LS + pos] = mk<V>(v1[u].x - v2[u].y, v1[u].y + v2[u].x);
+      }
+    }
+    __syncthreads();
+    const int64_t s1 = s0 + 2 * li;
+    V* a = lines + li * LS;
+    double acc = 0.0;
+    if (s1 < p.S) {
+      const V* z = line_fft<V, false>(a, a + P, p.lp, tw_s, g);
+      const bool two = s1 + 1 < p.S;
+      if (MODE == COL_FWD_REAL) {
+        T* d1 = p.out_real + (o * p.S + s1) * P;
+        for (int k = g.lt; k < P; k += g.tpl) {
+          d1[k] = z[k].x;
+          if (two) d1[P + k] = z[k].y;
+        }
+      } else {
+        const T* W1 = p.W + s1 * P;
+        T part = 0;
+        for (int k = g.lt; k < P; k += g.tpl) {
+          part += __ldg(W1 + k) * z[k].x;
+          if (two) part += __ldg(W1 + P + k) * z[k].y;
+        }
+        acc = (double)part;
+      }
+    }
+    if (MODE == COL_FWD_DOT) block_sum_to(acc, p.partial + blockIdx.x);
+    return;
+  }
   for (int idx0 = threadIdx.x; idx0 < P * W; idx0 += kLoadBatch * blockDim.x) {
     V v[kLoadBatch];
 #pragma unroll
@@ -403,10 +455,6 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
       V* other = (z == a) ? b : a;
       z = line_fft<V, true>(z, other, p.lp, tw_s, g);
     }
-    if (MODE == COL_FWD_REAL) {
-      T* dst = p.out_real + (o * p.S + s) * P;
-      for (int k = g.lt; k < P; k += g.tpl) dst[k] = z[k].x;
-    }
     if (MODE == COL_FWD_POWER) {
       T* dst = p.out_real + (o * p.S + s) * P;
       const T w = (T)half_weight(s, p.Qw, p.Plw);
@@ -417,18 +465,7 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
       }
     }
   }
-  if (MODE == COL_FWD_DOT) {
-    double acc = 0.0;
-    if (s < p.S) {
-      const T* Wc = p.W + s * P;
-      T part = 0;
-      for (int k = g.lt; k < P; k += g.tpl) part += __ldg(Wc + k) * z[k].x;
-      acc = (double)part;
-    }
-    block_sum_to(acc, p.partial + blockIdx.x);
-    return;
-  }
-  if (MODE == COL_FWD_REAL || MODE == COL_FWD_POWER) return;
+  if (MODE == COL_FWD_POWER) return;
   // Every warp's result sits in the same buffer of its pair (same plan).
   const int zoff = (z == a) ? 0 : P;
   __syncthreads();
@@ -515,9 +552,49 @@ __device__ __forceinline__ void cols_simd_body_slab(const ColsParams<T>& p, int6
   const int c = threadIdx.x % kSimdW, g = threadIdx.x / kSimdW, ng = blockDim.x / kSimdW;
   load_twiddles(tw_s, p.tw, P);
   const int64_t o = slab;
+  const V* in = p.in + o * (int64_t)p.Nin * p.S;
+  // Hermitian columns (see cols_body_slab): a block takes 2 kSimdW columns,
+  // column c and c + kSimdW share one FFT as real and imaginary parts.
+  constexpr bool PAIRED = MODE == COL_FWD_REAL || MODE == COL_FWD_DOT;
+  if (PAIRED) {
+    const int64_t sA = (int64_t)blockIdx.x * 2 * kSimdW + c, sB = sA + kSimdW;
+    for (int pos0 = g; pos0 < P; pos0 += kLoadBatch * ng) {
+      V va[kLoadBatch], vb[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int pos = pos0 + u * ng;
+        const int n = source_row(pos, P, p.Lw, p.Nin);
+        const bool ok = pos < P && n < p.Nin;
+        va[u] = (ok && sA < p.S) ? in[(int64_t)n * p.S + sA] : mk<V>(0, 0);
+        vb[u] = (ok && sB < p.S) ? in[(int64_t)n * p.S + sB] : mk<V>(0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int pos = pos0 + u * ng;
+        if (pos < P) bufA[pos * kSimdW + c] = mk<V>(va[u].x - vb[u].y, va[u].y + vb[u].x);
+      }
+    }
+    __syncthreads();
+    const V* z = simd_fft<V, false>(bufA, bufB, p.lp, tw_s, c, g, ng);
+    if (MODE == COL_FWD_DOT) {
+      T part = 0;
+      for (int pos = g; pos < P; pos += ng) {
+        const V v = z[pos * kSimdW + c];
+        if (sA < p.S) part += __ldg(p.W + (int64_t)pos * p.S + sA) * v.x;
+        if (sB < p.S) part += __ldg(p.W + (int64_t)pos * p.S + sB) * v.y;
+      }
+      block_sum_to((double)part, p.partial + blockIdx.x);
+    } else {
+      for (int pos = g; pos < P; pos += ng) {
+        const V v = z[pos * kSimdW + c];
+        if (sA < p.S) p.out_real[(o * P + pos) * p.S + sA] = v.x;
+        if (sB < p.S) p.out_real[(o * P + pos) * p.S + sB] = v.y;
+      }
+    }
+    return;
+  }
   const int64_t s = (int64_t)blockIdx.x * kSimdW + c;
   const bool col_ok = s < p.S;
-  const V* in = p.in + o * (int64_t)p.Nin * p.S;
   // kLoadBatch independent loads in flight per thread before any is stored
   for (int pos0 = g; pos0 < P; pos0 += kLoadBatch * ng) {
     V v[kLoadBatch];
@@ -546,23 +623,7 @@ __device__ __forceinline__ void cols_simd_body_slab(const ColsParams<T>& p, int6
     V* other = (z == bufA) ? bufB : bufA;
     z = simd_fft<V, true>(z, other, p.lp, tw_s, c, g, ng);
   }
-  if (MODE == COL_FWD_DOT) {
-    double acc = 0.0;
-    if (col_ok) {
-      T part = 0;
-      for (int pos = g; pos < P; pos += ng)
-        part += __ldg(p.W + (int64_t)pos * p.S + s) * z[pos * kSimdW + c].x;
-      acc = (double)part;
-    }
-    block_sum_to(acc, p.partial + blockIdx.x);
-    return;
-  }
   if (!col_ok) return;
-  if (MODE == COL_FWD_REAL) {
-    for (int pos = g; pos < P; pos += ng)
-      p.out_real[(o * P + pos) * p.S + s] = z[pos * kSimdW + c].x;
-    return;
-  }
   if (MODE == COL_FWD_POWER) {
     const T w = (T)half_weight(s, p.Qw, p.Plw);
     const T sc = (T)2.3283064365386963e-10;  // 2^-32
@@ -832,23 +893,24 @@ using ColsKernel = void (*)(ColsParams<T>);
 
 template <typename T>
 kde_status launch_cols(ColsKernel<T> fn_lines, ColsKernel<T> fn_simd, ColsParams<T> p, int64_t O,
-                       int variant, cudaStream_t st, const char* name) {
+                       int variant, cudaStream_t st, const char* name, bool paired = false) {
   const int P = p.lp.N;
+  const int per = paired ? 2 : 1;  // columns per transformed line
   cudaError_t e;
   if (simd_cols<T>(variant, p.S * O, P)) {
     if ((e = allow_smem(fn_simd)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     const size_t smem = (size_t)(1 + 2 * kSimdW) * P * sizeof(typename Cplx<T>::type);
-    dim3 grid((unsigned)((p.S + kSimdW - 1) / kSimdW), (unsigned)O);
+    dim3 grid((unsigned)((p.S + per * kSimdW - 1) / (per * kSimdW)), (unsigned)O);
     LaunchScope ls(name, st);
     fn_simd<<<grid, 256, smem, st>>>(p);
   } else {
-    const LineShape sh = line_shape<T>(p.S * O, P, 2);
+    const LineShape sh = line_shape<T>((p.S + per - 1) / per * O, P, 2);
     p.tpl = sh.tpl;
-    const int W = sh.lpb;
+    const int W = sh.lpb * per;  // columns per block
     if ((e = allow_smem(fn_lines)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     dim3 grid((unsigned)((p.S + W - 1) / W), (unsigned)O);
     LaunchScope ls(name, st);
-    fn_lines<<<grid, sh.tpl * W, line_smem<T>(P, W), st>>>(p);
+    fn_lines<<<grid, sh.tpl * sh.lpb, line_smem<T>(P, sh.lpb), st>>>(p);
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, name);
@@ -902,7 +964,8 @@ kde_status kernel_grid_impl(kde_plan_s* plan, int64_t n, void* Kspec, void* ws, 
     cp.Lw = (int)I.L[0];
     cp.lp = line_plan(I, 0);
     cp.tw = twiddles<T>(plan, 0);
-    return launch_cols<T>(KDE_COLS(kde_cols_kgen_real_kernel), cp, 1, plan->cols_variant, st, "kde_cols_kgen_real_kernel");
+    return launch_cols<T>(KDE_COLS(kde_cols_kgen_real_kernel), cp, 1, plan->cols_variant, st,
+                          "kde_cols_kgen_real_kernel", true);
   }
   // d == 3: axis 1 (wrapped) into t2, then axis 0 (wrapped) to the real spectrum.
   V* t2 = t1 + rows * I.Q;
@@ -924,7 +987,8 @@ kde_status kernel_grid_impl(kde_plan_s* plan, int64_t n, void* Kspec, void* ws, 
   c0.Lw = (int)I.L[0];
   c0.lp = line_plan(I, 0);
   c0.tw = twiddles<T>(plan, 0);
-  return launch_cols<T>(KDE_COLS(kde_cols_kgen_real_kernel), c0, 1, plan->cols_variant, st, "kde_cols_kgen_real_kernel");
+  return launch_cols<T>(KDE_COLS(kde_cols_kgen_real_kernel), c0, 1, plan->cols_variant, st,
+                        "kde_cols_kgen_real_kernel", true);
 }
 
 template <typename T>
@@ -1203,16 +1267,17 @@ kde_status lscv_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, cons
       if (simd_cols<T>(plan->cols_variant, S, P)) {
         auto* fn = kde_cols_kgen_dot_kernel<T, true>;
         if ((e = allow_smem(fn)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-        nparts = (int)((S + kSimdW - 1) / kSimdW);
+        nparts = (int)((S + 2 * kSimdW - 1) / (2 * kSimdW));
         LaunchScope ls("kde_cols_kgen_dot_kernel", st);
         fn<<<dim3((unsigned)nparts, (unsigned)bk.nb), 256,
              (size_t)(1 + 2 * kSimdW) * P * sizeof(V), st>>>(bk, cp);
       } else {
-        const LineShape sh = line_shape<T>(S * bk.nb, P, 2);
+        const LineShape sh = line_shape<T>((S + 1) / 2 * bk.nb, P, 2);
         cp.tpl = sh.tpl;
+        const int Wc = 2 * sh.lpb;
         auto* fn = kde_cols_kgen_dot_kernel<T, false>;
         if ((e = allow_smem(fn)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-        nparts = (int)((S + sh.lpb - 1) / sh.lpb);
+        nparts = (int)((S + Wc - 1) / Wc);
         LaunchScope ls("kde_cols_kgen_dot_kernel", st);
         fn<<<dim3((unsigned)nparts, (unsigned)bk.nb), sh.tpl * sh.lpb, line_smem<T>(P, sh.lpb), st>>>(bk, cp);
       }
