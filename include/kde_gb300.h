@@ -207,6 +207,40 @@ kde_status kde_lscv(kde_plan plan, int64_t n, int nH, const double* H, const voi
                     kde_stream_t stream);
 kde_status kde_lscv_workspace_bytes(kde_plan plan, size_t* bytes);
 
+/* Ragged batches of independent 2-D problems (each with its own samples,
+ * grid and bandwidth; Sec. 2 for each).  The batch runs as seven launches:
+ * a memset and one persistent grid-stride kernel per pass (binning, kernel
+ * rows, kernel spectrum, count rows, middle axis, output rows), each
+ * covering the work of every problem, so small and large grids share the
+ * GPU.  X: the problems' samples concatenated in problem order (x_rows rows
+ * of 2 values, the plan's precision).  density: the problems' grids
+ * concatenated (density_elems values).  Dropped samples are not reported.
+ * The plan allocates device tables (set-up, not per evaluation). */
+typedef struct {
+  int64_t M[2];
+  double lo[2], hi[2];
+  double H[4];
+  int64_t n;
+} kde_batch_item;
+typedef struct kde_batch_plan_s* kde_batch_plan;
+kde_status kde_batch_plan_create(int count, const kde_batch_item* items, const kde_opts* opts,
+                                 kde_batch_plan* out);
+kde_status kde_batch_plan_query(kde_batch_plan plan, int64_t* x_rows, int64_t* density_elems,
+                                size_t* workspace_bytes);
+/* Threads per line of the row passes and of the column passes (32, 64 or
+ * 128); chosen by a caller-side tuner. */
+kde_status kde_batch_set_shape(kde_batch_plan plan, int tpl_rows, int tpl_cols);
+kde_status kde_batch_get_shape(kde_batch_plan plan, int* tpl_rows, int* tpl_cols);
+/* Autotuner: times kde_batch_eval on the given buffers for every launch
+ * shape in {32, 64, 128}^2 (reps timed runs each, CUDA events on the stream,
+ * which it synchronises) and keeps the fastest in the plan; *best_ms (may be
+ * NULL) receives its time.  Set-up, not part of an evaluation. */
+kde_status kde_batch_tune(kde_batch_plan plan, const void* X, void* density, void* workspace,
+                          size_t workspace_bytes, kde_stream_t stream, int reps, float* best_ms);
+kde_status kde_batch_eval(kde_batch_plan plan, const void* X, void* density, void* workspace,
+                          size_t workspace_bytes, kde_stream_t stream);
+kde_status kde_batch_plan_destroy(kde_batch_plan plan);
+
 /* kde_fft_eval without a workspace argument, for callers that cannot
  * allocate device memory where they evaluate (for example code whose
  * allocations all belong to a host framework, or a loop that must never enter

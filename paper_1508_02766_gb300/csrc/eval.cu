@@ -25,6 +25,7 @@
 #include <mutex>
 #include <set>
 #include <string>
+#include <vector>
 
 #include "fft_engine.cuh"
 #include "kde_internal.h"
@@ -131,8 +132,8 @@ __device__ __forceinline__ LineGroup line_group(int tpl, int& li) {
 // Counts rows -> half spectra, one row pair per line group.  Counts are int64
 // in units of 2^-32; the unit is folded into the kernel spectrum.
 template <typename T>
-__global__ void __launch_bounds__(256)
-kde_rows_r2c_counts_kernel(const long long* __restrict__ counts, RowsParams<T> p) {
+__device__ __forceinline__ void rows_counts_body(const long long* __restrict__ counts,
+                                                 const RowsParams<T>& p, int64_t vb) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = p.lp.N;
@@ -143,7 +144,7 @@ kde_rows_r2c_counts_kernel(const long long* __restrict__ counts, RowsParams<T> p
   V* b = a + P;
   load_twiddles(tw_s, p.tw, P);
   __syncthreads();
-  const int64_t r0 = 2 * ((int64_t)blockIdx.x * (blockDim.x / p.tpl) + li);
+  const int64_t r0 = 2 * (vb * (blockDim.x / p.tpl) + li);
   if (r0 >= p.nrows) return;
   const long long* c0 = counts + r0 * p.in_stride;
   const long long* c1 = c0 + p.in_stride;
@@ -167,11 +168,18 @@ kde_rows_r2c_counts_kernel(const long long* __restrict__ counts, RowsParams<T> p
   store_r2c<T>(p, z, r0, g);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256)
+kde_rows_r2c_counts_kernel(const long long* __restrict__ counts, RowsParams<T> p) {
+  rows_counts_body<T>(counts, p, blockIdx.x);
+}
+
 // Kernel-grid rows -> half spectra (or real spectrum for d = 1).  Row r
 // enumerates the leading lags (l_0, ..., l_{d-2}) with |l_k| <= L_k; the last
 // axis holds lag l at position l mod P.
 template <typename T>
-__device__ __forceinline__ void rows_kgen_body(const KGen<T>& gen, const RowsParams<T>& p) {
+__device__ __forceinline__ void rows_kgen_body(const KGen<T>& gen, const RowsParams<T>& p,
+                                               int64_t vb) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = p.lp.N;
@@ -182,7 +190,7 @@ __device__ __forceinline__ void rows_kgen_body(const KGen<T>& gen, const RowsPar
   V* b = a + P;
   load_twiddles(tw_s, p.tw, P);
   __syncthreads();
-  const int64_t r0 = 2 * ((int64_t)blockIdx.x * (blockDim.x / p.tpl) + li);
+  const int64_t r0 = 2 * (vb * (blockDim.x / p.tpl) + li);
   if (r0 >= p.nrows) return;
   const int dl = gen.d - 1;  // index of the last axis
   for (int x = g.lt; x < P; x += g.tpl) {
@@ -215,7 +223,7 @@ __device__ __forceinline__ void rows_kgen_body(const KGen<T>& gen, const RowsPar
 template <typename T>
 __global__ void __launch_bounds__(256)
 kde_rows_r2c_kgen_kernel(KGen<T> gen, RowsParams<T> p) {
-  rows_kgen_body<T>(gen, p);
+  rows_kgen_body<T>(gen, p, blockIdx.x);
 }
 
 template <typename T>
@@ -235,7 +243,7 @@ struct C2RParams {
 // the full length from Hermitian symmetry: Z_k = conj(X_{P-k}) + i conj(Y_{P-k})
 // for k >= Q; then x + i y = F^{-1}(Z).
 template <typename T>
-__global__ void __launch_bounds__(256) kde_rows_c2r_kernel(C2RParams<T> p) {
+__device__ __forceinline__ void rows_c2r_body(const C2RParams<T>& p, int64_t vb) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = p.lp.N;
@@ -246,7 +254,7 @@ __global__ void __launch_bounds__(256) kde_rows_c2r_kernel(C2RParams<T> p) {
   V* b = a + P;
   load_twiddles(tw_s, p.tw, P);
   __syncthreads();
-  const int64_t r0 = 2 * ((int64_t)blockIdx.x * (blockDim.x / p.tpl) + li);
+  const int64_t r0 = 2 * (vb * (blockDim.x / p.tpl) + li);
   if (r0 >= p.nrows) return;
   const bool two = r0 + 1 < p.nrows;
   const V* x0 = p.in + r0 * p.Q;
@@ -276,6 +284,11 @@ __global__ void __launch_bounds__(256) kde_rows_c2r_kernel(C2RParams<T> p) {
     o0[m] = v.x;
     if (two) o1[m] = v.y;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kde_rows_c2r_kernel(C2RParams<T> p) {
+  rows_c2r_body<T>(p, blockIdx.x);
 }
 
 // d = 1: counts -> F -> * K (real, even: K_k = K_{P-k}) -> F^{-1} -> crop.
@@ -350,7 +363,8 @@ __device__ __forceinline__ void block_sum_to(double v, double* out) {
 
 // W adjacent columns (s0 .. s0+W-1) of outer slab o, one line group each.
 template <typename T, int MODE>
-__device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t slab) {
+__device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t slab,
+                                               int64_t vbx) {
   using V = typename Cplx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = p.lp.N;
@@ -368,7 +382,7 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
   const LineGroup g = line_group(p.tpl, li);
   load_twiddles(tw_s, p.tw, P);
   const int64_t o = slab;
-  const int64_t s0 = (int64_t)blockIdx.x * W;
+  const int64_t s0 = vbx * W;
   const V* in = p.in + o * (int64_t)p.Nin * p.S;
   if (PAIRED) {
     // line t holds columns s0 + 2t (real part) and s0 + 2t + 1 (imaginary)
@@ -480,7 +494,7 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
 
 template <typename T, int MODE>
 __device__ __forceinline__ void cols_body(const ColsParams<T>& p) {
-  cols_body_slab<T, MODE>(p, blockIdx.y);
+  cols_body_slab<T, MODE>(p, blockIdx.y, blockIdx.x);
 }
 
 // Column passes with many columns: a block holds kSimdW adjacent columns
@@ -701,7 +715,7 @@ __global__ void __launch_bounds__(256) kde_rows_kgen_batch_kernel(BatchKGen<T> b
     q.out_real = p.out_real + (int64_t)b * p.Q;
   else
     q.out = p.out + bk.off[b];
-  rows_kgen_body<T>(bk.gen[b], q);
+  rows_kgen_body<T>(bk.gen[b], q, blockIdx.x);
 }
 
 // Axis-0 pass of the batched spectra, fused with the dot product against the
@@ -720,7 +734,7 @@ __global__ void __launch_bounds__(256) kde_cols_kgen_dot_kernel(BatchKGen<T> bk,
   if (SIMD)
     cols_simd_body_slab<T, COL_FWD_DOT>(q, 0);
   else
-    cols_body_slab<T, COL_FWD_DOT>(q, 0);
+    cols_body_slab<T, COL_FWD_DOT>(q, 0, blockIdx.x);
 }
 
 // d = 1: dot of the real spectrum of matrix b with W.
@@ -1436,4 +1450,523 @@ extern "C" kde_status kde_lscv(kde_plan plan, int64_t n, int nH, const double* H
   if (plan->info.precision == KDE_F32)
     return lscv_impl<float>(plan, n, nH, H, W, pair_sums, lscv, workspace, st);
   return lscv_impl<double>(plan, n, nH, H, W, pair_sums, lscv, workspace, st);
+}
+
+// ---------------------------------------------------------------------------
+// Ragged batches: many independent 2-D problems (own samples, grid, H) in one
+// set of launches.  Every pass is a persistent grid-stride kernel over the
+// work items of all problems (a block maps its work index to a problem by
+// binary search over per-pass prefix sums), so the batch costs seven launches
+// whatever its size; problems of different sizes share each launch.
+// ---------------------------------------------------------------------------
+namespace kde {
+namespace {
+
+// Linear binning arithmetic for the batch kernel (the rounding rules of
+// kde_bin: t = (x - lo) s rounded in the samples' type, i = floor(t),
+// f = t - i, the last node folded to (M-2, 1), q = round-half-even(f 2^32)
+// with q = 2^32 written as (i+1, 0); part w of the unit mass gives
+// floor((w q + 2^31) / 2^32) to node i+1, axis 0 first).
+template <typename T>
+struct BinAxisLite {
+  T lo, s, top;
+  int M;
+};
+
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+
+__device__ __forceinline__ bool lite_fixed(float f, int& i, unsigned& q) {
+  if (f == 1.0f) {
+    i += 1;
+    q = 0;
+  } else {
+    q = __float2uint_rn(f * 4294967296.0f);  // f 2^32 < 2^32 exactly
+  }
+  return true;
+}
+__device__ __forceinline__ bool lite_fixed(double f, int& i, unsigned& q) {
+  const unsigned long long Q = __double2ull_rn(f * 4294967296.0);
+  if (Q == (1ull << 32)) {
+    i += 1;
+    q = 0;
+  } else {
+    q = (unsigned)Q;
+  }
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ bool lite_position(T x, const BinAxisLite<T>& a, int& i, unsigned& q) {
+  const T t = rn_mul(rn_sub(x, a.lo), a.s);
+  if (!(t >= T(0) && t <= a.top)) return false;
+  const T fl = floor(t);
+  i = (int)fl;
+  T f = rn_sub(t, fl);
+  if (i == a.M - 1) {
+    i = a.M - 2;
+    f = T(1);
+  }
+  return lite_fixed(f, i, q);
+}
+
+__device__ __forceinline__ unsigned lite_mulhi(unsigned long long w, unsigned q) {
+  const unsigned wl = (unsigned)w, wh = (unsigned)(w >> 32);
+  return wh * q + __umulhi(wl, q) + ((wl * q) >> 31);
+}
+
+// corners (0,0), (0,1), (1,0), (1,1) (axis-0 offset first)
+__device__ __forceinline__ void lite_corner_weights2(const unsigned* q, unsigned long long* w) {
+  const unsigned long long one = 1ull << 32;
+  const unsigned long long a1 = lite_mulhi(one, q[0]), a0 = one - a1;
+  w[1] = lite_mulhi(a0, q[1]);
+  w[0] = a0 - w[1];
+  w[3] = lite_mulhi(a1, q[1]);
+  w[2] = a1 - w[3];
+}
+
+enum BatchPass { BP_BIN = 0, BP_KROWS, BP_KCOLS, BP_ROWS, BP_MID, BP_C2R, BP_COUNT };
+
+template <typename T>
+struct BatchItem {
+  using V = typename Cplx<T>::type;
+  int64_t x_off, n;          // samples [x_off, x_off + n) of the concatenated X
+  T lo[2], s[2], top[2];     // binning: lo, (M-1)/(hi-lo), M-1 in the samples' type
+  int M[2], P[2], Q, L[2];
+  int64_t counts_off;        // int64 elements
+  int64_t kspec_off;         // real elements, [Q][P0] (column-major spectrum)
+  int64_t A_off;             // complex elements, [M0][Q]
+  int64_t T1_off;            // complex elements, [2 L0 + 1][Q]
+  int64_t dens_off;          // real elements, [M0][M1]
+  LinePlan lp[2];
+  const V* tw[2];
+  KGen<T> gen;
+};
+
+__device__ __forceinline__ int find_item(const int* __restrict__ start, int count, int w) {
+  int lo = 0, hi = count - 1;  // largest i with start[i] <= w
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+struct BatchArgs {
+  const BatchItem<T>* items;
+  const int* wstart;   // [BP_COUNT][count + 1] work prefix per pass
+  int count;
+  int tpl_rows, tpl_cols;
+  const T* X;
+  long long* counts;
+  T* kspec;
+  typename Cplx<T>::type* A;
+  typename Cplx<T>::type* T1;
+  T* density;
+};
+
+// Binning of every problem's samples: the same arithmetic as the direct
+// method, one thread per sample of the concatenated array.
+template <typename T>
+__global__ void __launch_bounds__(256) kde_batch_bin_kernel(BatchArgs<T> a, int64_t total) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = a.count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.items[mid].x_off <= s) lo = mid; else hi = mid - 1;
+    }
+    const BatchItem<T>& B = a.items[lo];
+    int i[2];
+    unsigned q[2];
+    bool in = true;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      BinAxisLite<T> ax{B.lo[k], B.s[k], B.top[k], B.M[k]};
+      in &= lite_position<T>(a.X[s * 2 + k], ax, i[k], q[k]);
+    }
+    if (!in) continue;
+    unsigned long long w[4];
+    lite_corner_weights2(q, w);
+    unsigned long long* c = reinterpret_cast<unsigned long long*>(a.counts + B.counts_off);
+    const int64_t base = (int64_t)i[0] * B.M[1] + i[1];
+    if (w[0]) atomicAdd(c + base, w[0]);
+    if (w[1]) atomicAdd(c + base + 1, w[1]);
+    if (w[2]) atomicAdd(c + base + B.M[1], w[2]);
+    if (w[3]) atomicAdd(c + base + B.M[1] + 1, w[3]);
+  }
+}
+
+template <typename T, int PASS>
+__global__ void __launch_bounds__(256) kde_batch_pass_kernel(BatchArgs<T> a) {
+  using V = typename Cplx<T>::type;
+  __shared__ RowsParams<T> rp;
+  __shared__ C2RParams<T> cr;
+  __shared__ ColsParams<T> cp;
+  __shared__ KGen<T> gen;
+  __shared__ int item, base;
+  const int* wst = a.wstart + PASS * (a.count + 1);
+  const int total = wst[a.count];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const int it = find_item(wst, a.count, w);
+      const BatchItem<T>& B = a.items[it];
+      item = it;
+      base = wst[it];
+      if (PASS == BP_KROWS || PASS == BP_ROWS) {
+        RowsParams<T> r{};
+        r.Q = B.Q;
+        r.lp = B.lp[1];
+        r.tw = B.tw[1];
+        r.tpl = a.tpl_rows;
+        if (PASS == BP_KROWS) {
+          r.nrows = 2 * B.L[0] + 1;
+          r.out = a.T1 + B.T1_off;
+          gen = B.gen;
+        } else {
+          r.nrows = B.M[0];
+          r.Min = B.M[1];
+          r.in_stride = B.M[1];
+          r.out = a.A + B.A_off;
+        }
+        rp = r;
+      } else if (PASS == BP_C2R) {
+        C2RParams<T> c{};
+        c.in = a.A + B.A_off;
+        c.out = a.density + B.dens_off;
+        c.nrows = B.M[0];
+        c.Mout = B.M[1];
+        c.Q = B.Q;
+        c.tpl = a.tpl_rows;
+        c.lp = B.lp[1];
+        c.tw = B.tw[1];
+        cr = c;
+      } else {
+        ColsParams<T> c{};
+        c.S = B.Q;
+        c.lp = B.lp[0];
+        c.tw = B.tw[0];
+        c.tpl = a.tpl_cols;
+        if (PASS == BP_KCOLS) {
+          c.in = a.T1 + B.T1_off;
+          c.out_real = a.kspec + B.kspec_off;
+          c.Nin = 2 * B.L[0] + 1;
+          c.Lw = B.L[0];
+        } else {
+          c.in = a.A + B.A_off;
+          c.out = a.A + B.A_off;
+          c.K = a.kspec + B.kspec_off;
+          c.Nin = B.M[0];
+          c.Nout = B.M[0];
+          c.Lw = -1;
+        }
+        cp = c;
+      }
+    }
+    __syncthreads();
+    const int64_t vb = w - base;
+    if (PASS == BP_KROWS) rows_kgen_body<T>(gen, rp, vb);
+    if (PASS == BP_ROWS) rows_counts_body<T>(a.counts + a.items[item].counts_off, rp, vb);
+    if (PASS == BP_C2R) rows_c2r_body<T>(cr, vb);
+    if (PASS == BP_KCOLS) cols_body_slab<T, COL_FWD_REAL>(cp, 0, vb);
+    if (PASS == BP_MID) cols_body_slab<T, COL_MID>(cp, 0, vb);
+    __syncthreads();  // the next item reloads twiddles and parameters
+  }
+}
+
+}  // namespace
+}  // namespace kde
+
+struct kde_batch_plan_s {
+  int count;
+  int precision;
+  std::vector<kde_plan_s*> plans;   // per problem: info and twiddles
+  void* items_dev;                  // BatchItem<T>[count]
+  int* wstart_dev;                  // [BP_COUNT][count + 1]
+  std::vector<int> wstart;          // host copy
+  int64_t x_total, counts_elems, kspec_elems, A_elems, T1_elems, dens_elems;
+  int Pmax;
+  int tpl_rows, tpl_cols;           // launch shape (tunable)
+  size_t workspace_bytes;
+};
+
+namespace kde {
+namespace {
+
+constexpr int kBatchLines = 2;  // lines per block in the batch passes
+
+template <typename T>
+kde_status batch_upload(kde_batch_plan_s* bp, const kde_batch_item* items) {
+  using V = typename Cplx<T>::type;
+  std::vector<BatchItem<T>> h(bp->count);
+  int64_t x = 0, cnt = 0, ks = 0, A = 0, T1 = 0, de = 0;
+  for (int i = 0; i < bp->count; ++i) {
+    const kde_plan_s* pl = bp->plans[i];
+    const kde_plan_info& I = pl->info;
+    BatchItem<T>& B = h[i];
+    B.x_off = x;
+    B.n = items[i].n;
+    for (int k = 0; k < 2; ++k) {
+      const double sk = (double)(I.M[k] - 1) / (pl->hi[k] - pl->lo[k]);
+      B.lo[k] = (T)pl->lo[k];
+      B.s[k] = (T)sk;
+      B.top[k] = (T)(I.M[k] - 1);
+      B.M[k] = (int)I.M[k];
+      B.P[k] = (int)I.P[k];
+      B.L[k] = (int)I.L[k];
+      B.lp[k] = line_plan(I, k);
+      B.tw[k] = twiddles<T>(pl, k);
+    }
+    B.Q = (int)I.Q;
+    B.counts_off = cnt;
+    B.kspec_off = ks;
+    B.A_off = A;
+    B.T1_off = T1;
+    B.dens_off = de;
+    double Ainv[9];
+    for (int e = 0; e < 4; ++e) Ainv[e] = pl->Hinv[e];
+    B.gen = kgen_for<T>(I, Ainv, I.det_H, I.L, pl->layout_mode == KDE_LAYOUT_WAND);
+    B.gen.C = (T)(std::pow(6.283185307179586476925287, -1.0) / std::sqrt(I.det_H) /
+                  ((double)items[i].n * 4294967296.0 * (double)I.P[0] * (double)I.P[1]));
+    x += items[i].n;
+    cnt += I.M[0] * I.M[1];
+    ks += I.P[0] * I.Q;
+    A += I.M[0] * I.Q;
+    T1 += (2 * I.L[0] + 1) * I.Q;
+    de += I.M[0] * I.M[1];
+  }
+  bp->x_total = x;
+  bp->counts_elems = cnt;
+  bp->kspec_elems = ks;
+  bp->A_elems = A;
+  bp->T1_elems = T1;
+  bp->dens_elems = de;
+  cudaError_t e = cudaMalloc(&bp->items_dev, sizeof(BatchItem<T>) * bp->count);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch items)");
+  e = cudaMemcpy(bp->items_dev, h.data(), sizeof(BatchItem<T>) * bp->count, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(batch items)");
+  const size_t cb = sizeof(V), rb = sizeof(T);
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  bp->workspace_bytes = up(cnt * 8) + up(ks * rb) + up(A * cb) + up(T1 * cb);
+  return KDE_OK;
+}
+
+// Work items per problem and pass for the current launch shape; uploaded.
+kde_status batch_work(kde_batch_plan_s* bp) {
+  const int c = bp->count;
+  bp->wstart.assign((size_t)BP_COUNT * (c + 1), 0);
+  const int lr = kBatchLines, lc = kBatchLines;
+  for (int i = 0; i < c; ++i) {
+    const kde_plan_info& I = bp->plans[i]->info;
+    int w[BP_COUNT];
+    w[BP_BIN] = 0;
+    w[BP_KROWS] = (int)((((2 * I.L[0] + 1) + 1) / 2 + lr - 1) / lr);
+    w[BP_KCOLS] = (int)((I.Q + 2 * lc - 1) / (2 * lc));
+    w[BP_ROWS] = (int)(((I.M[0] + 1) / 2 + lr - 1) / lr);
+    w[BP_MID] = (int)((I.Q + lc - 1) / lc);
+    w[BP_C2R] = w[BP_ROWS];
+    for (int pss = 0; pss < BP_COUNT; ++pss)
+      bp->wstart[(size_t)pss * (c + 1) + i + 1] = bp->wstart[(size_t)pss * (c + 1) + i] + w[pss];
+  }
+  cudaError_t e = cudaMemcpy(bp->wstart_dev, bp->wstart.data(), sizeof(int) * bp->wstart.size(),
+                             cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? KDE_OK : cuda_fail(e, "cudaMemcpy(batch work)");
+}
+
+template <typename T>
+kde_status batch_eval_impl(kde_batch_plan_s* bp, const void* X, void* density, void* ws,
+                           cudaStream_t st) {
+  using V = typename Cplx<T>::type;
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  char* w = (char*)ws;
+  BatchArgs<T> a{};
+  a.items = (const BatchItem<T>*)bp->items_dev;
+  a.wstart = bp->wstart_dev;
+  a.count = bp->count;
+  a.tpl_rows = bp->tpl_rows;
+  a.tpl_cols = bp->tpl_cols;
+  a.X = (const T*)X;
+  a.counts = (long long*)w;
+  w += up(bp->counts_elems * 8);
+  a.kspec = (T*)w;
+  w += up(bp->kspec_elems * sizeof(T));
+  a.A = (V*)w;
+  w += up(bp->A_elems * sizeof(V));
+  a.T1 = (V*)w;
+  a.density = (T*)density;
+  cudaError_t e = cudaMemsetAsync(a.counts, 0, bp->counts_elems * 8, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counts)");
+  const int sms = num_sms();
+  {
+    LaunchScope ls("kde_batch_bin_kernel", st);
+    const int64_t blocks = std::min<int64_t>((bp->x_total + 255) / 256, (int64_t)sms * 8);
+    if (blocks > 0) kde_batch_bin_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(a, bp->x_total);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_batch_bin_kernel");
+  }
+  const int c = bp->count;
+  auto run = [&](auto fn, int pass, int tpl, const char* name) -> kde_status {
+    const int total = bp->wstart[(size_t)pass * (c + 1) + c];
+    if (total == 0) return KDE_OK;
+    cudaError_t e2 = allow_smem(fn);
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFuncSetAttribute");
+    const size_t smem = line_smem<T>(bp->Pmax, kBatchLines);
+    const int grid = std::min(total, sms * 8);
+    LaunchScope ls(name, st);
+    fn<<<grid, tpl * kBatchLines, smem, st>>>(a);
+    e2 = cudaGetLastError();
+    return e2 == cudaSuccess ? KDE_OK : cuda_fail(e2, name);
+  };
+  kde_status s;
+  if ((s = run(kde_batch_pass_kernel<T, BP_KROWS>, BP_KROWS, bp->tpl_rows, "kde_batch_krows_kernel")) != KDE_OK) return s;
+  if ((s = run(kde_batch_pass_kernel<T, BP_KCOLS>, BP_KCOLS, bp->tpl_cols, "kde_batch_kcols_kernel")) != KDE_OK) return s;
+  if ((s = run(kde_batch_pass_kernel<T, BP_ROWS>, BP_ROWS, bp->tpl_rows, "kde_batch_rows_kernel")) != KDE_OK) return s;
+  if ((s = run(kde_batch_pass_kernel<T, BP_MID>, BP_MID, bp->tpl_cols, "kde_batch_mid_kernel")) != KDE_OK) return s;
+  return run(kde_batch_pass_kernel<T, BP_C2R>, BP_C2R, bp->tpl_rows, "kde_batch_c2r_kernel");
+}
+
+}  // namespace
+}  // namespace kde
+
+extern "C" kde_status kde_batch_plan_create(int count, const kde_batch_item* items,
+                                            const kde_opts* opts, kde_batch_plan* out) {
+  if (!out || !items || count < 1) return fail(KDE_ERR_INVALID_ARG, "bad argument");
+  *out = nullptr;
+  kde_batch_plan_s* bp = new (std::nothrow) kde_batch_plan_s();
+  if (!bp) return fail(KDE_ERR_INVALID_ARG, "out of host memory");
+  bp->count = count;
+  bp->precision = opts ? opts->precision : KDE_F32;
+  bp->Pmax = 0;
+  bp->tpl_rows = 64;
+  bp->tpl_cols = 64;
+  bp->items_dev = nullptr;
+  bp->wstart_dev = nullptr;
+  kde_opts o{};
+  o.tau = 3.7;
+  if (opts) o = *opts;
+  o.cols_variant = KDE_COLS_LINES;
+  auto cleanup = [&](kde_status s) {
+    for (auto* p : bp->plans) kde_plan_destroy(p);
+    if (bp->items_dev) cudaFree(bp->items_dev);
+    if (bp->wstart_dev) cudaFree(bp->wstart_dev);
+    delete bp;
+    return s;
+  };
+  for (int i = 0; i < count; ++i) {
+    if (items[i].n < 1 || items[i].n >= (int64_t(1) << 31))
+      return cleanup(fail(KDE_ERR_INVALID_ARG, "every problem needs 1 <= n < 2^31"));
+    kde_plan p = nullptr;
+    kde_status s = kde_plan_create(2, items[i].M, items[i].lo, items[i].hi, items[i].H, &o, &p);
+    if (s != KDE_OK) return cleanup(s);
+    bp->plans.push_back(p);
+    for (int k = 0; k < 2; ++k) bp->Pmax = std::max(bp->Pmax, (int)p->info.P[k]);
+  }
+  const size_t cb = (bp->precision == KDE_F32) ? 8 : 16;
+  if (line_smem<float>(bp->Pmax, kBatchLines) / 8 * cb > kSmemMax)
+    return cleanup(fail(KDE_ERR_UNSUPPORTED, "padded size too large for the batch passes"));
+  cudaError_t e = cudaMalloc((void**)&bp->wstart_dev, sizeof(int) * BP_COUNT * (count + 1));
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc(batch work)"));
+  kde_status s = (bp->precision == KDE_F32) ? batch_upload<float>(bp, items) : batch_upload<double>(bp, items);
+  if (s == KDE_OK) s = batch_work(bp);
+  if (s != KDE_OK) return cleanup(s);
+  *out = bp;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_batch_plan_query(kde_batch_plan bp, int64_t* x_rows, int64_t* density_elems,
+                                           size_t* workspace_bytes) {
+  if (!bp) return fail(KDE_ERR_INVALID_ARG, "NULL plan");
+  if (x_rows) *x_rows = bp->x_total;
+  if (density_elems) *density_elems = bp->dens_elems;
+  if (workspace_bytes) *workspace_bytes = bp->workspace_bytes;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_batch_set_shape(kde_batch_plan bp, int tpl_rows, int tpl_cols) {
+  if (!bp) return fail(KDE_ERR_INVALID_ARG, "NULL plan");
+  for (int t : {tpl_rows, tpl_cols})
+    if (t != 32 && t != 64 && t != 128) return fail(KDE_ERR_INVALID_ARG, "threads per line: 32, 64 or 128");
+  bp->tpl_rows = tpl_rows;
+  bp->tpl_cols = tpl_cols;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_batch_eval(kde_batch_plan bp, const void* X, void* density, void* workspace,
+                                     size_t workspace_bytes, kde_stream_t stream) {
+  if (!bp || !density || (!X && bp->x_total > 0)) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (!workspace || workspace_bytes < bp->workspace_bytes)
+    return fail(KDE_ERR_WORKSPACE, "workspace smaller than the batch plan needs");
+  if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (bp->precision == KDE_F32) return batch_eval_impl<float>(bp, X, density, workspace, st);
+  return batch_eval_impl<double>(bp, X, density, workspace, st);
+}
+
+extern "C" kde_status kde_batch_plan_destroy(kde_batch_plan bp) {
+  if (!bp) return KDE_OK;
+  for (auto* p : bp->plans) kde_plan_destroy(p);
+  cudaError_t e = cudaSuccess;
+  if (bp->items_dev) e = cudaFree(bp->items_dev);
+  if (bp->wstart_dev) cudaFree(bp->wstart_dev);
+  delete bp;
+  return e == cudaSuccess ? KDE_OK : cuda_fail(e, "cudaFree(batch)");
+}
+
+// Launch-shape tuner for a batch plan: times kde_batch_eval for every
+// (threads per row line, threads per column line) in {32, 64, 128}^2 with
+// CUDA events on the stream (reps runs each, after one warm-up run) and
+// keeps the fastest.  Synchronises the stream; set-up, not per evaluation.
+extern "C" kde_status kde_batch_tune(kde_batch_plan bp, const void* X, void* density,
+                                     void* workspace, size_t workspace_bytes, kde_stream_t stream,
+                                     int reps, float* best_ms) {
+  if (!bp) return fail(KDE_ERR_INVALID_ARG, "NULL plan");
+  if (reps < 1) reps = 3;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(KDE_ERR_CUDA, "cudaEventCreate");
+  float best = 1e30f;
+  int br = bp->tpl_rows, bc = bp->tpl_cols;
+  kde_status s = KDE_OK;
+  for (int tr : {32, 64, 128}) {
+    for (int tc : {32, 64, 128}) {
+      bp->tpl_rows = tr;
+      bp->tpl_cols = tc;
+      if ((s = kde_batch_eval(bp, X, density, workspace, workspace_bytes, stream)) != KDE_OK) break;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && s == KDE_OK; ++r)
+        s = kde_batch_eval(bp, X, density, workspace, workspace_bytes, stream);
+      cudaEventRecord(e1, st);
+      if (s != KDE_OK) break;
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        s = cuda_fail(e, "tuning run");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (ms < best) {
+        best = ms;
+        br = tr;
+        bc = tc;
+      }
+    }
+    if (s != KDE_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  bp->tpl_rows = br;
+  bp->tpl_cols = bc;
+  if (best_ms) *best_ms = best;
+  return s;
+}
+
+extern "C" kde_status kde_batch_get_shape(kde_batch_plan bp, int* tpl_rows, int* tpl_cols) {
+  if (!bp) return fail(KDE_ERR_INVALID_ARG, "NULL plan");
+  if (tpl_rows) *tpl_rows = bp->tpl_rows;
+  if (tpl_cols) *tpl_cols = bp->tpl_cols;
+  return KDE_OK;
 }

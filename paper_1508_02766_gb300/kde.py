@@ -48,12 +48,19 @@ class PlanInfo(ctypes.Structure):
                 ("radix", (ctypes.c_int * MAX_STAGES) * MAX_D)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64 * 2), ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2),
+                ("H", ctypes.c_double * 4), ("n", ctypes.c_int64)]
+
+
 EXPORTS = [
     "kde_plan_info_compute", "kde_plan_create", "kde_plan_get_info", "kde_plan_destroy",
     "kde_bin", "kde_kernel_grid", "kde_fft_eval", "kde_status_string", "kde_last_error",
     "kde_launch_count", "kde_profile_enable", "kde_profile_count", "kde_profile_entry",
     "kde_fft_eval_noalloc", "kde_bin_workspace_bytes", "kde_power_spectrum", "kde_lscv",
-    "kde_lscv_workspace_bytes",
+    "kde_lscv_workspace_bytes", "kde_batch_plan_create", "kde_batch_plan_query",
+    "kde_batch_set_shape", "kde_batch_get_shape", "kde_batch_tune", "kde_batch_eval",
+    "kde_batch_plan_destroy",
 ]
 
 _lib = None
@@ -84,6 +91,15 @@ def lib():
     L.kde_power_spectrum.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.kde_lscv.argtypes = [vp, i64, ctypes.c_int, dp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.kde_lscv_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.kde_batch_plan_create.argtypes = [ctypes.c_int, ctypes.POINTER(BatchItem), ctypes.POINTER(Opts),
+                                        ctypes.POINTER(vp)]
+    L.kde_batch_plan_query.argtypes = [vp, i64p, i64p, ctypes.POINTER(ctypes.c_size_t)]
+    L.kde_batch_set_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.kde_batch_get_shape.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.kde_batch_tune.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_float)]
+    L.kde_batch_eval.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.kde_batch_plan_destroy.argtypes = [vp]
     L.kde_status_string.restype = ctypes.c_char_p
     L.kde_status_string.argtypes = [ctypes.c_int]
     L.kde_last_error.restype = ctypes.c_char_p
@@ -95,7 +111,9 @@ def lib():
                  "kde_plan_destroy", "kde_bin", "kde_kernel_grid", "kde_fft_eval",
                  "kde_fft_eval_noalloc", "kde_profile_enable", "kde_profile_entry",
                  "kde_bin_workspace_bytes", "kde_power_spectrum", "kde_lscv",
-                 "kde_lscv_workspace_bytes"):
+                 "kde_lscv_workspace_bytes", "kde_batch_plan_create", "kde_batch_plan_query",
+                 "kde_batch_set_shape", "kde_batch_get_shape", "kde_batch_tune", "kde_batch_eval",
+                 "kde_batch_plan_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -318,6 +336,77 @@ def kde_lscv(plan: Plan, n, H, W, lscv=None, pair_sums=None, workspace=None, str
                           _ptr(workspace), workspace.numel() * workspace.element_size(),
                           _stream_ptr(stream)))
     return lscv
+
+
+class BatchPlan:
+    """A ragged batch of 2-D problems (kde_batch_plan_*): problems is a list of
+    (M, lo, hi, H, n); samples are passed concatenated in problem order."""
+
+    def __init__(self, problems, **opts):
+        arr = (BatchItem * len(problems))()
+        for i, (M, lo, hi, H, n) in enumerate(problems):
+            arr[i].M[:] = [int(m) for m in M]
+            arr[i].lo[:] = [float(v) for v in lo]
+            arr[i].hi[:] = [float(v) for v in hi]
+            arr[i].H[:] = [float(v) for v in np.asarray(H, dtype=np.float64).ravel()]
+            arr[i].n = int(n)
+        o = _opts(**opts)
+        h = ctypes.c_void_p()
+        _check(lib().kde_batch_plan_create(len(problems), arr, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.precision = opts.get("precision", "f32")
+        xr, de, wb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        _check(lib().kde_batch_plan_query(h, ctypes.byref(xr), ctypes.byref(de), ctypes.byref(wb)))
+        self.x_rows, self.density_elems, self.workspace_bytes = xr.value, de.value, wb.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().kde_batch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def real_dtype(self):
+        import torch
+        return torch.float32 if self.precision == "f32" else torch.float64
+
+    def workspace(self, device="cuda"):
+        import torch
+        return torch.empty(max(256, self.workspace_bytes), dtype=torch.uint8, device=device)
+
+    def set_shape(self, tpl_rows, tpl_cols):
+        _check(lib().kde_batch_set_shape(self._h, int(tpl_rows), int(tpl_cols)))
+
+    def shape(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().kde_batch_get_shape(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def tune(self, X, density, workspace, reps=3, stream=None):
+        ms = ctypes.c_float()
+        _check(lib().kde_batch_tune(self._h, _ptr(X), _ptr(density), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(),
+                                    _stream_ptr(stream), int(reps), ctypes.byref(ms)))
+        return ms.value
+
+    def eval(self, X, density=None, workspace=None, stream=None):
+        import torch
+        if density is None:
+            density = torch.empty(self.density_elems, dtype=self.real_dtype(), device="cuda")
+        if workspace is None:
+            workspace = self.workspace()
+        _check(lib().kde_batch_eval(self._h, _ptr(X), _ptr(density), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(),
+                                    _stream_ptr(stream)))
+        return density
 
 
 NOALLOC_SCRATCH_BYTES = 8 << 20

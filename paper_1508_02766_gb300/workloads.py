@@ -217,3 +217,21 @@ def lscv_small(seed, d, M, n, count, precision="f64", diag_lo=-4.0, diag_hi=-1.5
     dt = np.float64 if precision == "f64" else np.float32
     return LscvWorkload(f"lscv_small_d{d}", X.astype(dt), H, X.min(axis=0) - pad,
                         X.max(axis=0) + pad, tuple(int(m) for m in M), precision)
+
+
+def ragged64_f32(seed=5, count=64):
+    """A ragged batch: 64 independent 2-D datasets, n log-uniform in
+    [1e3, 1e6], grids drawn from {64, 128, 256, 512, 1024}^2, each with its
+    own correlated bandwidth (normal-reference scale, random orientation)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(round(10 ** rng.uniform(3.0, 6.0)))
+        m = int(rng.choice([64, 128, 256, 512, 1024]))
+        X = mixture_samples(rng, n, MIX2_MEANS, MIX2_COVS)
+        scale = n ** (-1.0 / 3.0)
+        H = rotated_bandwidth(scale * rng.uniform(0.5, 2.0), scale * rng.uniform(0.02, 0.3),
+                              rng.uniform(0, np.pi))
+        lo, hi = grid_range(X, H)
+        out.append(Workload("ragged", X.astype(np.float32), H, lo, hi, (m, m), "f32"))
+    return out

@@ -1,0 +1,94 @@
+"""Ragged batches (kde_batch_*): every problem of the batch against the
+oracle, against the single-problem path, for every launch shape."""
+import numpy as np
+import pytest
+
+from oracle import kde_oracle as O
+from paper_1508_02766_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def K():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import os
+
+    from paper_1508_02766_gb300 import build, kde
+    if not os.path.exists(build.LIB):
+        build.build()
+    return kde
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def small_batch(prec, count=9, seed=70):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        M = (int(rng.integers(8, 90)), int(rng.integers(8, 120)))
+        out.append(W.small_case(seed + i, 2, M, n=int(rng.integers(50, 3000)), precision=prec,
+                                corr=float(rng.uniform(-0.8, 0.9)), scale=float(rng.uniform(0.01, 0.1))))
+    return out
+
+
+def run_batch(K, problems, prec, shape=None):
+    bp = K.BatchPlan([(w.M, w.lo, w.hi, w.H, w.n) for w in problems], precision=prec)
+    if shape:
+        bp.set_shape(*shape)
+    X = torch.from_numpy(np.ascontiguousarray(np.concatenate([w.X for w in problems]))).cuda()
+    dens = bp.eval(X)
+    torch.cuda.synchronize()
+    out, off = [], 0
+    d = dens.cpu().numpy()
+    for w in problems:
+        m = int(np.prod(w.M))
+        out.append(d[off:off + m].reshape(w.M))
+        off += m
+    return out, bp, X
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_small_ragged_batch_every_node(K, prec):
+    problems = small_batch(prec)
+    dens, _, _ = run_batch(K, problems, prec)
+    for w, g in zip(problems, dens):
+        f, _, _, _ = O.binned_estimate(w.X, w.H, w.lo, w.hi, w.M, tau=w.tau)
+        assert rel_err(g, f) <= TOL[prec]
+
+
+@pytest.mark.parametrize("shape", [(32, 32), (64, 128), (128, 64), (128, 128)])
+def test_every_launch_shape(K, shape):
+    problems = small_batch("f64", count=5, seed=90)
+    dens, _, _ = run_batch(K, problems, "f64", shape)
+    for w, g in zip(problems, dens):
+        f, _, _, _ = O.binned_estimate(w.X, w.H, w.lo, w.hi, w.M, tau=w.tau)
+        assert rel_err(g, f) <= 1e-12
+
+
+def test_ragged64_against_single_problem_path_and_tuner(K):
+    problems = W.ragged64_f32()
+    dens, bp, X = run_batch(K, problems, "f32")
+    density = torch.empty(bp.density_elems, dtype=torch.float32, device="cuda")
+    ws = bp.workspace()
+    ms = bp.tune(X, density, ws, reps=2)
+    assert ms > 0 and bp.shape()[0] in (32, 64, 128)
+    tuned = bp.eval(X, density, ws).cpu().numpy()
+    off = 0
+    rng = np.random.default_rng(2)
+    check = set(rng.choice(len(problems), 10, replace=False).tolist())
+    for i, (w, g) in enumerate(zip(problems, dens)):
+        m = int(np.prod(w.M))
+        assert np.allclose(tuned[off:off + m].reshape(w.M), g, rtol=0, atol=1e-5 * np.abs(g).max())
+        off += m
+        if i not in check:
+            continue
+        Xd = torch.from_numpy(np.ascontiguousarray(w.X)).cuda()
+        single, _, _ = K.kde_eval(Xd, w.H, w.lo, w.hi, w.M, precision="f32")
+        assert rel_err(g, single.cpu().numpy()) <= 1e-5
