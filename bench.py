@@ -371,13 +371,15 @@ def main():
     value = world * cells / (ms_step * 1e-3)
     samples_s = world * w.n / (ms_step * 1e-3)
 
-    # Per-kernel durations: the same steps launched one by one with the
+    # Per-kernel durations: the same steps launched one by one on one stream
+    # (no overlap, so each event pair measures its kernel alone) with the
     # library's event pairs around every kernel (graph replays carry none).
+    step_serial = kde.PreparedPath(plan, X, counts, Ks, dens, ws, bin_workspace=bws, stream=stream)
     kde.profile_enable(True)
     with torch.cuda.stream(stream):
         for i in range(args.steps):
             flush.zero_()
-            enqueue(step_dev)
+            step_serial()
     torch.cuda.synchronize()
     prof = kde.profile_read()
     kde.profile_enable(False)
@@ -436,8 +438,8 @@ def main():
                        "binning": method,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline, "path_roofline": path_roof, "kernels": kernels,
-            "kernel_timing": "CUDA events around each kernel on its stream, over the same K steps "
-                             "launched without the graph right after the timed region",
+            "kernel_timing": "CUDA events around each kernel, over the same K steps launched "
+                             "one by one on one stream right after the timed region",
             "gpu_launches": launches,
             "e2e": {"value": world * cells / (e2e_ms * 1e-3), "unit": "grid points/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(X.numel() * X.element_size()),

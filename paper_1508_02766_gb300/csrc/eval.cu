@@ -1569,17 +1569,21 @@ struct BatchArgs {
 };
 
 // Binning of every problem's samples: the same arithmetic as the direct
-// method, one thread per sample of the concatenated array.
+// method.  Work item = (problem, chunk of kBinChunk samples); a block takes
+// whole work items, so each knows its problem without a per-sample search.
+constexpr int kBinChunk = 8192;
+
 template <typename T>
-__global__ void __launch_bounds__(256) kde_batch_bin_kernel(BatchArgs<T> a, int64_t total) {
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < total;
-       s += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = a.count - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (a.items[mid].x_off <= s) lo = mid; else hi = mid - 1;
-    }
-    const BatchItem<T>& B = a.items[lo];
+__global__ void __launch_bounds__(256) kde_batch_bin_kernel(BatchArgs<T> a) {
+  const int* wst = a.wstart + BP_BIN * (a.count + 1);
+  const int total = wst[a.count];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int it = find_item(wst, a.count, w);
+    const BatchItem<T>& B = a.items[it];
+    const int64_t c0 = (int64_t)(w - wst[it]) * kBinChunk;
+    const int64_t c1 = min(B.n, c0 + kBinChunk);
+    for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+    const int64_t s = B.x_off + j;
     int i[2];
     unsigned q[2];
     bool in = true;
@@ -1589,14 +1593,15 @@ __global__ void __launch_bounds__(256) kde_batch_bin_kernel(BatchArgs<T> a, int6
       in &= lite_position<T>(a.X[s * 2 + k], ax, i[k], q[k]);
     }
     if (!in) continue;
-    unsigned long long w[4];
-    lite_corner_weights2(q, w);
+    unsigned long long wt[4];
+    lite_corner_weights2(q, wt);
     unsigned long long* c = reinterpret_cast<unsigned long long*>(a.counts + B.counts_off);
     const int64_t base = (int64_t)i[0] * B.M[1] + i[1];
-    if (w[0]) atomicAdd(c + base, w[0]);
-    if (w[1]) atomicAdd(c + base + 1, w[1]);
-    if (w[2]) atomicAdd(c + base + B.M[1], w[2]);
-    if (w[3]) atomicAdd(c + base + B.M[1] + 1, w[3]);
+    if (wt[0]) atomicAdd(c + base, wt[0]);
+    if (wt[1]) atomicAdd(c + base + 1, wt[1]);
+    if (wt[2]) atomicAdd(c + base + B.M[1], wt[2]);
+    if (wt[3]) atomicAdd(c + base + B.M[1] + 1, wt[3]);
+    }
   }
 }
 
@@ -1691,6 +1696,7 @@ struct kde_batch_plan_s {
   int Pmax;
   int tpl_rows, tpl_cols;           // launch shape (tunable)
   size_t workspace_bytes;
+  std::vector<int64_t> n;           // samples per problem
 };
 
 namespace kde {
@@ -1754,6 +1760,8 @@ kde_status batch_upload(kde_batch_plan_s* bp, const kde_batch_item* items) {
   return KDE_OK;
 }
 
+int64_t items_n(const kde_batch_plan_s* bp, int i) { return bp->n[i]; }
+
 // Work items per problem and pass for the current launch shape; uploaded.
 kde_status batch_work(kde_batch_plan_s* bp) {
   const int c = bp->count;
@@ -1762,7 +1770,7 @@ kde_status batch_work(kde_batch_plan_s* bp) {
   for (int i = 0; i < c; ++i) {
     const kde_plan_info& I = bp->plans[i]->info;
     int w[BP_COUNT];
-    w[BP_BIN] = 0;
+    w[BP_BIN] = (int)((bp->plans[i] ? items_n(bp, i) : 0) + kBinChunk - 1) / kBinChunk;
     w[BP_KROWS] = (int)((((2 * I.L[0] + 1) + 1) / 2 + lr - 1) / lr);
     w[BP_KCOLS] = (int)((I.Q + 2 * lc - 1) / (2 * lc));
     w[BP_ROWS] = (int)(((I.M[0] + 1) / 2 + lr - 1) / lr);
@@ -1800,13 +1808,13 @@ kde_status batch_eval_impl(kde_batch_plan_s* bp, const void* X, void* density, v
   cudaError_t e = cudaMemsetAsync(a.counts, 0, bp->counts_elems * 8, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counts)");
   const int sms = num_sms();
+  const int c = bp->count;
   {
+    const int total = bp->wstart[(size_t)BP_BIN * (c + 1) + c];
     LaunchScope ls("kde_batch_bin_kernel", st);
-    const int64_t blocks = std::min<int64_t>((bp->x_total + 255) / 256, (int64_t)sms * 8);
-    if (blocks > 0) kde_batch_bin_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(a, bp->x_total);
+    if (total > 0) kde_batch_bin_kernel<T><<<std::min(total, sms * 8), 256, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_batch_bin_kernel");
   }
-  const int c = bp->count;
   auto run = [&](auto fn, int pass, int tpl, const char* name) -> kde_status {
     const int total = bp->wstart[(size_t)pass * (c + 1) + c];
     if (total == 0) return KDE_OK;
@@ -1858,6 +1866,7 @@ extern "C" kde_status kde_batch_plan_create(int count, const kde_batch_item* ite
     if (items[i].n < 1 || items[i].n >= (int64_t(1) << 31))
       return cleanup(fail(KDE_ERR_INVALID_ARG, "every problem needs 1 <= n < 2^31"));
     kde_plan p = nullptr;
+    bp->n.push_back(items[i].n);
     kde_status s = kde_plan_create(2, items[i].M, items[i].lo, items[i].hi, items[i].H, &o, &p);
     if (s != KDE_OK) return cleanup(s);
     bp->plans.push_back(p);
