@@ -80,13 +80,47 @@ __device__ __forceinline__ int source_row(int pos, int P, int Lw, int Nin) {
   return (l <= Lw) ? l + Lw : Nin;
 }
 
+// A count (int64, units of 2^-32) in the evaluation type.  Converting a
+// 64-bit integer directly is slow on sm_103 (measured: about 2 us of a
+// 1024-row pass); the value is rebuilt from its two 32-bit halves instead.
+// FP64: hi 2^32 + lo is exact and the fma rounds once, the same result as a
+// direct conversion.  FP32: the low half rounds once more (within one ulp).
+template <typename T> __device__ __forceinline__ T count_value(long long v);
+template <> __device__ __forceinline__ float count_value<float>(long long v) {
+  return fmaf((float)(int)(v >> 32), 4294967296.0f, (float)(unsigned)(unsigned long long)v);
+}
+template <> __device__ __forceinline__ double count_value<double>(long long v) {
+  return fma((double)(int)(v >> 32), 4294967296.0, (double)(unsigned)(unsigned long long)v);
+}
+
 // Global loads issued back to back by one thread before their values are
 // stored to shared memory (memory-level parallelism of the load phases).
 constexpr int kLoadBatch = 8;
 
+// Twiddle table -> shared memory by asynchronous copies (cp.async): they
+// hold no registers and are in flight together with a pass's own data
+// loads; twiddles_wait() completes this thread's copies, and the block
+// barrier after it publishes the table.  Every thread of the block calls
+// both.  Tables start on 256-byte boundaries; one whose size is an odd
+// multiple of 8 bytes ends with an 8-byte copy.
 template <typename V>
-__device__ __forceinline__ void load_twiddles(V* tw_s, const V* tw, int P) {
-  for (int i = threadIdx.x; i < P; i += blockDim.x) tw_s[i] = tw[i];
+__device__ __forceinline__ void twiddles_async(V* tw_s, const V* tw, int P) {
+  const int bytes = P * (int)sizeof(V);
+  const int n16 = bytes >> 4;
+  const size_t src = __cvta_generic_to_global(tw);
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(tw_s);
+  for (int i = threadIdx.x; i < n16; i += blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16u * i),
+                 "l"(src + 16ull * i)
+                 : "memory");
+  if ((bytes & 15) && threadIdx.x == 0)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst + 16u * n16),
+                 "l"(src + 16ull * n16)
+                 : "memory");
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void twiddles_wait() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <typename T>
@@ -142,14 +176,13 @@ __device__ __forceinline__ void rows_counts_body(const long long* __restrict__ c
   const LineGroup g = line_group(p.tpl, li);
   V* a = tw_s + P + 2 * li * P;
   V* b = a + P;
-  load_twiddles(tw_s, p.tw, P);
-  __syncthreads();
+  twiddles_async(tw_s, p.tw, P);
   const int64_t r0 = 2 * (vb * (blockDim.x / p.tpl) + li);
-  if (r0 >= p.nrows) return;
+  const bool act = r0 < p.nrows;
   const long long* c0 = counts + r0 * p.in_stride;
   const long long* c1 = c0 + p.in_stride;
   const bool two = r0 + 1 < p.nrows;
-  for (int x0 = g.lt; x0 < P; x0 += kLoadBatch * g.tpl) {
+  for (int x0 = g.lt; act && x0 < P; x0 += kLoadBatch * g.tpl) {
     long long u0[kLoadBatch], u1[kLoadBatch];
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
@@ -160,10 +193,12 @@ __device__ __forceinline__ void rows_counts_body(const long long* __restrict__ c
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
       const int x = x0 + u * g.tpl;
-      if (x < P) a[x] = mk<V>((T)u0[u], (T)u1[u]);
+      if (x < P) a[x] = mk<V>(count_value<T>(u0[u]), count_value<T>(u1[u]));
     }
   }
-  g.sync();
+  twiddles_wait();
+  __syncthreads();
+  if (!act) return;
   V* z = line_fft<V, false>(a, b, p.lp, tw_s, g);
   store_r2c<T>(p, z, r0, g);
 }
@@ -188,34 +223,38 @@ __device__ __forceinline__ void rows_kgen_body(const KGen<T>& gen, const RowsPar
   const LineGroup g = line_group(p.tpl, li);
   V* a = tw_s + P + 2 * li * P;
   V* b = a + P;
-  load_twiddles(tw_s, p.tw, P);
-  __syncthreads();
+  twiddles_async(tw_s, p.tw, P);
   const int64_t r0 = 2 * (vb * (blockDim.x / p.tpl) + li);
-  if (r0 >= p.nrows) return;
-  const int dl = gen.d - 1;  // index of the last axis
-  for (int x = g.lt; x < P; x += g.tpl) {
+  const bool act = r0 < p.nrows;
+  const int Llast = gen.d == 1 ? gen.L[0] : (gen.d == 2 ? gen.L[1] : gen.L[2]);
+  for (int x = g.lt; act && x < P; x += g.tpl) {
     T val[2] = {0, 0};
-    const int ll = wrapped_lag(x, P, gen.L[dl]);
-    if (ll <= gen.L[dl]) {
+    const int ll = wrapped_lag(x, P, Llast);
+    if (ll <= Llast) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int64_t r = r0 + h;
         if (r >= p.nrows) break;
-        int l[KDE_MAX_D] = {0, 0, 0};
+        // lags of this row and position, indexed statically (a runtime
+        // index would put the array in local memory)
+        int l[KDE_MAX_D] = {ll, 0, 0};
         if (gen.d == 2) {
           l[0] = (int)r - gen.L[0];
+          l[1] = ll;
         } else if (gen.d == 3) {
           const int w1 = 2 * gen.L[1] + 1;
           l[0] = (int)(r / w1) - gen.L[0];
           l[1] = (int)(r % w1) - gen.L[1];
+          l[2] = ll;
         }
-        l[dl] = ll;
         val[h] = kernel_value<T>(gen, l);
       }
     }
     a[x] = mk<V>(val[0], val[1]);
   }
-  g.sync();
+  twiddles_wait();
+  __syncthreads();
+  if (!act) return;
   V* z = line_fft<V, false>(a, b, p.lp, tw_s, g);
   store_r2c<T>(p, z, r0, g);
 }
@@ -252,14 +291,13 @@ __device__ __forceinline__ void rows_c2r_body(const C2RParams<T>& p, int64_t vb)
   const LineGroup g = line_group(p.tpl, li);
   V* a = tw_s + P + 2 * li * P;
   V* b = a + P;
-  load_twiddles(tw_s, p.tw, P);
-  __syncthreads();
+  twiddles_async(tw_s, p.tw, P);
   const int64_t r0 = 2 * (vb * (blockDim.x / p.tpl) + li);
-  if (r0 >= p.nrows) return;
+  const bool act = r0 < p.nrows;
   const bool two = r0 + 1 < p.nrows;
   const V* x0 = p.in + r0 * p.Q;
   const V* x1 = x0 + p.Q;
-  for (int k0 = g.lt; k0 < p.Q; k0 += kLoadBatch * g.tpl) {
+  for (int k0 = g.lt; act && k0 < p.Q; k0 += kLoadBatch * g.tpl) {
     V X[kLoadBatch], Y[kLoadBatch];
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
@@ -275,7 +313,9 @@ __device__ __forceinline__ void rows_c2r_body(const C2RParams<T>& p, int64_t vb)
       if (k > 0 && P - k >= p.Q) a[P - k] = mk<V>(X[u].x + Y[u].y, Y[u].x - X[u].y);
     }
   }
-  g.sync();
+  twiddles_wait();
+  __syncthreads();
+  if (!act) return;
   V* z = line_fft<V, true>(a, b, p.lp, tw_s, g);
   T* o0 = p.out + r0 * p.Mout;
   T* o1 = o0 + p.Mout;
@@ -303,8 +343,9 @@ kde_line1d_kernel(const long long* __restrict__ counts, const T* __restrict__ K,
   V* a = tw_s + P;
   V* b = a + P;
   const LineGroup g{(int)threadIdx.x, (int)blockDim.x, 1};
-  load_twiddles(tw_s, tw, P);
-  for (int x = g.lt; x < P; x += g.tpl) a[x] = mk<V>(x < M ? (T)counts[x] : T(0), 0);
+  twiddles_async(tw_s, tw, P);
+  for (int x = g.lt; x < P; x += g.tpl) a[x] = mk<V>(x < M ? count_value<T>(counts[x]) : T(0), 0);
+  twiddles_wait();
   __syncthreads();
   V* z = line_fft<V, false>(a, b, lp, tw_s, g);
   for (int k = g.lt; k < P; k += g.tpl) {
@@ -380,11 +421,11 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
   V* lines = tw_s + P;
   int li;
   const LineGroup g = line_group(p.tpl, li);
-  load_twiddles(tw_s, p.tw, P);
+  twiddles_async(tw_s, p.tw, P);
   const int64_t o = slab;
   const int64_t s0 = vbx * W;
   const V* in = p.in + o * (int64_t)p.Nin * p.S;
-  if (PAIRED) {
+  if constexpr (PAIRED) {
     // line t holds columns s0 + 2t (real part) and s0 + 2t + 1 (imaginary)
     const int npair = W / 2;
     for (int idx0 = threadIdx.x; idx0 < P * npair; idx0 += kLoadBatch * blockDim.x) {
@@ -406,6 +447,7 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
         if (idx < P * npair) lines[t * LS + pos] = mk<V>(v1[u].x - v2[u].y, v1[u].y + v2[u].x);
       }
     }
+    twiddles_wait();
     __syncthreads();
     const int64_t s1 = s0 + 2 * li;
     V* a = lines + li * LS;
@@ -422,9 +464,19 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
       } else {
         const T* W1 = p.W + s1 * P;
         T part = 0;
-        for (int k = g.lt; k < P; k += g.tpl) {
-          part += __ldg(W1 + k) * z[k].x;
-          if (two) part += __ldg(W1 + P + k) * z[k].y;
+        for (int k0 = g.lt; k0 < P; k0 += kLoadBatch * g.tpl) {
+          T w1[kLoadBatch], w2[kLoadBatch];
+#pragma unroll
+          for (int u = 0; u < kLoadBatch; ++u) {
+            const int k = k0 + u * g.tpl;
+            w1[u] = k < P ? __ldg(W1 + k) : T(0);
+            w2[u] = (k < P && two) ? __ldg(W1 + P + k) : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < kLoadBatch; ++u) {
+            const int k = k0 + u * g.tpl;
+            if (k < P) part += w1[u] * z[k].x + w2[u] * z[k].y;
+          }
         }
         acc = (double)part;
       }
@@ -449,21 +501,46 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
       if (idx < P * W) lines[t * LS + pos] = v[u];
     }
   }
+  twiddles_wait();
   __syncthreads();
   const int64_t s = s0 + li;
   V* a = lines + li * LS;
   V* b = a + P;
   V* z = a;
   if (s < p.S) {
+    // COL_MID: the first kLoadBatch values of the column's K per thread are
+    // loaded before the forward transform, which hides their latency.
+    T kpre[kLoadBatch];
+    const T* Kc = p.K + s * P;
+    if (MODE == COL_MID) {
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int k = g.lt + u * g.tpl;
+        kpre[u] = k < P ? __ldg(Kc + k) : T(0);
+      }
+    }
     if (MODE == COL_INV)
       z = line_fft<V, true>(a, b, p.lp, tw_s, g);
     else
       z = line_fft<V, false>(a, b, p.lp, tw_s, g);
     if (MODE == COL_MID) {
-      const T* Kc = p.K + s * P;
-      for (int k = g.lt; k < P; k += g.tpl) {
-        const T kv = __ldg(Kc + k);
-        z[k] = mk<V>(z[k].x * kv, z[k].y * kv);
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int k = g.lt + u * g.tpl;
+        if (k < P) z[k] = mk<V>(z[k].x * kpre[u], z[k].y * kpre[u]);
+      }
+      for (int k0 = g.lt + kLoadBatch * g.tpl; k0 < P; k0 += kLoadBatch * g.tpl) {
+        T kv[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+          const int k = k0 + u * g.tpl;
+          kv[u] = k < P ? __ldg(Kc + k) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+          const int k = k0 + u * g.tpl;
+          if (k < P) z[k] = mk<V>(z[k].x * kv[u], z[k].y * kv[u]);
+        }
       }
       g.sync();
       V* other = (z == a) ? b : a;
@@ -564,13 +641,13 @@ __device__ __forceinline__ void cols_simd_body_slab(const ColsParams<T>& p, int6
   V* bufA = tw_s + P;
   V* bufB = bufA + P * kSimdW;
   const int c = threadIdx.x % kSimdW, g = threadIdx.x / kSimdW, ng = blockDim.x / kSimdW;
-  load_twiddles(tw_s, p.tw, P);
+  twiddles_async(tw_s, p.tw, P);
   const int64_t o = slab;
   const V* in = p.in + o * (int64_t)p.Nin * p.S;
   // Hermitian columns (see cols_body_slab): a block takes 2 kSimdW columns,
   // column c and c + kSimdW share one FFT as real and imaginary parts.
   constexpr bool PAIRED = MODE == COL_FWD_REAL || MODE == COL_FWD_DOT;
-  if (PAIRED) {
+  if constexpr (PAIRED) {
     const int64_t sA = (int64_t)blockIdx.x * 2 * kSimdW + c, sB = sA + kSimdW;
     for (int pos0 = g; pos0 < P; pos0 += kLoadBatch * ng) {
       V va[kLoadBatch], vb[kLoadBatch];
@@ -588,14 +665,27 @@ __device__ __forceinline__ void cols_simd_body_slab(const ColsParams<T>& p, int6
         if (pos < P) bufA[pos * kSimdW + c] = mk<V>(va[u].x - vb[u].y, va[u].y + vb[u].x);
       }
     }
+    twiddles_wait();
     __syncthreads();
     const V* z = simd_fft<V, false>(bufA, bufB, p.lp, tw_s, c, g, ng);
     if (MODE == COL_FWD_DOT) {
       T part = 0;
-      for (int pos = g; pos < P; pos += ng) {
-        const V v = z[pos * kSimdW + c];
-        if (sA < p.S) part += __ldg(p.W + (int64_t)pos * p.S + sA) * v.x;
-        if (sB < p.S) part += __ldg(p.W + (int64_t)pos * p.S + sB) * v.y;
+      for (int pos0 = g; pos0 < P; pos0 += kLoadBatch * ng) {
+        T wa[kLoadBatch], wb[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+          const int pos = pos0 + u * ng;
+          wa[u] = (pos < P && sA < p.S) ? __ldg(p.W + (int64_t)pos * p.S + sA) : T(0);
+          wb[u] = (pos < P && sB < p.S) ? __ldg(p.W + (int64_t)pos * p.S + sB) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+          const int pos = pos0 + u * ng;
+          if (pos < P) {
+            const V v = z[pos * kSimdW + c];
+            part += wa[u] * v.x + wb[u] * v.y;
+          }
+        }
       }
       block_sum_to((double)part, p.partial + blockIdx.x);
     } else {
@@ -624,14 +714,44 @@ __device__ __forceinline__ void cols_simd_body_slab(const ColsParams<T>& p, int6
       if (pos < P) bufA[pos * kSimdW + c] = v[u];
     }
   }
+  twiddles_wait();
   __syncthreads();
+  // COL_MID: this thread's first kLoadBatch values of K, loaded before the
+  // forward transform.
+  T kpre[kLoadBatch];
+  if (MODE == COL_MID) {
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int pos = g + u * ng;
+      kpre[u] = (pos < P && col_ok) ? __ldg(p.K + (int64_t)pos * p.S + s) : T(0);
+    }
+  }
   V* z = (MODE == COL_INV) ? simd_fft<V, true>(bufA, bufB, p.lp, tw_s, c, g, ng)
                            : simd_fft<V, false>(bufA, bufB, p.lp, tw_s, c, g, ng);
   if (MODE == COL_MID) {
-    for (int pos = g; pos < P; pos += ng) {
-      const T kv = col_ok ? __ldg(p.K + (int64_t)pos * p.S + s) : T(0);
-      V v = z[pos * kSimdW + c];
-      z[pos * kSimdW + c] = mk<V>(v.x * kv, v.y * kv);
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int pos = g + u * ng;
+      if (pos < P) {
+        V v = z[pos * kSimdW + c];
+        z[pos * kSimdW + c] = mk<V>(v.x * kpre[u], v.y * kpre[u]);
+      }
+    }
+    for (int pos0 = g + kLoadBatch * ng; pos0 < P; pos0 += kLoadBatch * ng) {
+      T kv[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int pos = pos0 + u * ng;
+        kv[u] = (pos < P && col_ok) ? __ldg(p.K + (int64_t)pos * p.S + s) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int pos = pos0 + u * ng;
+        if (pos < P) {
+          V v = z[pos * kSimdW + c];
+          z[pos * kSimdW + c] = mk<V>(v.x * kv[u], v.y * kv[u]);
+        }
+      }
     }
     __syncthreads();
     V* other = (z == bufA) ? bufB : bufA;
@@ -709,13 +829,21 @@ template <typename T>
 __global__ void __launch_bounds__(256) kde_rows_kgen_batch_kernel(BatchKGen<T> bk, RowsParams<T> p) {
   const int b = blockIdx.y;
   if (b >= bk.nb) return;
-  RowsParams<T> q = p;
-  q.nrows = bk.rows[b];
-  if (p.out_real)
-    q.out_real = p.out_real + (int64_t)b * p.Q;
-  else
-    q.out = p.out + bk.off[b];
-  rows_kgen_body<T>(bk.gen[b], q, blockIdx.x);
+  // this matrix's parameters in shared memory (a per-thread copy indexed at
+  // run time would live in local memory)
+  __shared__ RowsParams<T> q;
+  __shared__ KGen<T> gen;
+  if (threadIdx.x == 0) {
+    q = p;
+    q.nrows = bk.rows[b];
+    if (p.out_real)
+      q.out_real = p.out_real + (int64_t)b * p.Q;
+    else
+      q.out = p.out + bk.off[b];
+    gen = bk.gen[b];
+  }
+  __syncthreads();
+  rows_kgen_body<T>(gen, q, blockIdx.x);
 }
 
 // Axis-0 pass of the batched spectra, fused with the dot product against the
@@ -725,11 +853,15 @@ template <typename T, bool SIMD>
 __global__ void __launch_bounds__(256) kde_cols_kgen_dot_kernel(BatchKGen<T> bk, ColsParams<T> p) {
   const int b = blockIdx.y;
   if (b >= bk.nb) return;
-  ColsParams<T> q = p;
-  q.in = p.in + bk.off[b];
-  q.Nin = bk.rows[b];
-  q.Lw = bk.gen[b].L[0];
-  q.partial = p.partial + (int64_t)b * gridDim.x;
+  __shared__ ColsParams<T> q;
+  if (threadIdx.x == 0) {
+    q = p;
+    q.in = p.in + bk.off[b];
+    q.Nin = bk.rows[b];
+    q.Lw = bk.gen[b].L[0];
+    q.partial = p.partial + (int64_t)b * gridDim.x;
+  }
+  __syncthreads();
   // the bodies index the outer slab by blockIdx.y; here there is one slab
   if (SIMD)
     cols_simd_body_slab<T, COL_FWD_DOT>(q, 0);
