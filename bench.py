@@ -77,6 +77,36 @@ def algorithmic_bytes(info, n, x_itemsize):
     return b
 
 
+# ---------------------------------------------------------------------------
+# Replicas (one process per GPU): the slowest rank times the job.
+# ---------------------------------------------------------------------------
+def rank_max(value, device=None):
+    """Max of a per-rank scalar over all ranks of the default process group
+    (the value itself when there is no group or one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, ms_step):
+    """Whole-job rate: every rank's units over the slowest rank's step time."""
+    return world * units_per_rank / (ms_step * 1e-3)
+
+
+# FP32 ALU roofline: 152 SMs x 128 FP32 lanes x 2 flops (FMA) at the SM clock.
+def fp32_peak_tflops(sm_mhz=2070.0, sms=152):
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fft_flops(n_lines, N):
+    """The conventional 5 N log2 N flops of a complex FFT of length N."""
+    return n_lines * 5.0 * N * np.log2(N)
+
+
 def source_digest():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1508_02766_gb300", "csrc")
@@ -361,15 +391,11 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rank_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), dev)
     ms_step = ms / args.steps
     cells = int(np.prod(w.M))
-    value = world * cells / (ms_step * 1e-3)
-    samples_s = world * w.n / (ms_step * 1e-3)
+    value = job_throughput(world, cells, ms_step)
+    samples_s = job_throughput(world, w.n, ms_step)
 
     # Per-kernel durations: the same steps launched one by one on one stream
     # (no overlap, so each event pair measures its kernel alone) with the
@@ -402,11 +428,7 @@ def main():
             dens_host.copy_(dens, non_blocking=True)
         e_e.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e_s.elapsed_time(e_e) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = rank_max(e_s.elapsed_time(e_e) / e2e_steps, dev)
 
     # Roofline of the dominant kernel.
     alg = algorithmic_bytes(info, w.n, w.X.dtype.itemsize)
@@ -441,7 +463,7 @@ def main():
             "kernel_timing": "CUDA events around each kernel, over the same K steps launched "
                              "one by one on one stream right after the timed region",
             "gpu_launches": launches,
-            "e2e": {"value": world * cells / (e2e_ms * 1e-3), "unit": "grid points/s",
+            "e2e": {"value": job_throughput(world, cells, e2e_ms), "unit": "grid points/s",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(X.numel() * X.element_size()),
                     "d2h_bytes_per_step": int(dens.numel() * dens.element_size())},
             "clocks": clocks}
@@ -530,6 +552,26 @@ def ragged_main(args):
                    "share": v[0] / max(1e-12, sum(x[0] for x in prof.values()))}
                for k, v in prof.items()}
     cells = sum(int(np.prod(w.M)) for w in problems)
+    # algorithmic bytes of each pass summed over the problems (the same
+    # per-problem formulas as the single-problem path)
+    alg = {}
+    for w in problems:
+        pi = kde.kde_plan_info_compute(w.M, w.lo, w.hi, w.H, precision="f32", tau=w.tau)
+        b = algorithmic_bytes(pi, w.n, 4)
+        for src, dst in (("kde_bin_kernel", "kde_batch_bin_kernel"),
+                         ("kde_rows_r2c_kgen_kernel", "kde_batch_krows_kernel"),
+                         ("kde_cols_kgen_real_kernel", "kde_batch_kcols_kernel"),
+                         ("kde_rows_r2c_counts_kernel", "kde_batch_rows_kernel"),
+                         ("kde_cols_mid_kernel", "kde_batch_mid_kernel"),
+                         ("kde_rows_c2r_kernel", "kde_batch_c2r_kernel")):
+            alg[dst] = alg.get(dst, 0) + b[src]
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    peak, peak_kind = peaks()
+    ach = alg.get(dom, 0) / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": peak_kind, "traffic": None,
+                "algorithmic_bytes": alg.get(dom, 0)}
     line = {"metric": RAGGED_METRIC, "value": len(problems) / (ms_step * 1e-3), "unit": "datasets/s",
             "grid_points_per_s": cells / (ms_step * 1e-3),
             "samples_per_s": sum(w.n for w in problems) / (ms_step * 1e-3), "n_gpus": 1,
@@ -540,7 +582,8 @@ def ragged_main(args):
                        "grids": sorted({w.M[0] for w in problems}), "total_samples": int(X.shape[0]),
                        "launch": "one CUDA graph replay per step", "launch_shape": list(bp.shape()),
                        "tuned_ms": tuned_ms, "l2": "flushed between timed steps (256 MB write)"},
-            "kernels": kernels, "gpu_launches": per_step * args.steps, "clocks": clocks}
+            "roofline": roofline, "kernels": kernels, "gpu_launches": per_step * args.steps,
+            "clocks": clocks}
     print(json.dumps(line))
 
 
@@ -608,6 +651,23 @@ def lscv_main(args):
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
                    "share": v[0] / max(1e-12, sum(x[0] for x in prof.values()))}
                for k, v in prof.items()}
+    # FFT flops (5 N log2 N per complex line) of the batched kernel-spectrum
+    # passes, per launch: every chunk holds 64 matrices (H_i and 2 H_i).
+    P0, P1, Q = info.P[0], info.P[1], info.Q
+    Ls = [kde.kde_plan_info_compute(w.M, w.lo, w.hi, A, precision=w.precision, tau=w.tau).L[0]
+          for h in w.H for A in (h, 2 * h)]
+    nlaunch = max(1, prof.get("kde_cols_kgen_dot_kernel", (0, 1))[1] // args.steps)
+    flops = {"kde_rows_kgen_batch_kernel": sum(fft_flops((2 * L0 + 2) // 2, P1) for L0 in Ls) / nlaunch,
+             "kde_cols_kgen_dot_kernel": len(Ls) * (fft_flops((Q + 1) // 2, P0) + 2.0 * P0 * Q) / nlaunch}
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = fp32_peak_tflops(sm_max)
+    ach = flops.get(dom, 0.0) / (dom_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x SM max clock",
+                "traffic": None, "flops_per_launch": flops.get(dom, 0.0),
+                "flop_model": "5 N log2 N per complex FFT line + 2 per dot-product term"}
     line = {"metric": LSCV_METRIC, "value": value, "unit": "candidates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -615,7 +675,7 @@ def lscv_main(args):
             "config": {"workload": w.name, "d": w.d, "n": w.n, "grid": list(w.M),
                        "candidates": len(w.H), "P": list(info.P),
                        "l2": "flushed between timed steps (256 MB write)"},
-            "kernels": kernels, "gpu_launches": launches, "clocks": clocks}
+            "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks}
     if not args.no_cpu_baseline:
         # the oracle's spectral pair sums for a few candidates, timed, and the
         # GPU's values for the same candidates compared with them
