@@ -271,6 +271,66 @@ kde_status kde_profile_enable(int on);
 int kde_profile_count(void);
 kde_status kde_profile_entry(int i, const char** name, double* total_ms, int64_t* launches);
 
+/* ---- Learned bandwidth proposal --------------------------------------------
+ * The paper points to fast bandwidth selection with the same FFT machinery
+ * (Sec. 1, Sec. 5) but gives no method; the network below is not from the
+ * paper.  Its inputs are features of a 2-D sample: the samples standardised
+ * per axis, binned (kde_bin) on a fixed M x M grid of the standardised
+ * coordinates, downsampled to 32 x 32 block masses, plus moments.  Its
+ * outputs are a log-Cholesky proposal for H in standardised coordinates,
+ * which the caller scores with kde_lscv. */
+
+#define KDE_FEAT_DIM 1088 /* 32 x 32 block features + 64 moment slots */
+
+/* One block reduction over n >= 2 samples (X: n x 2 FP32, device):
+ * Z = (X - mean) / sd per axis (FP32, device, n x 2) and moments[8] (FP64,
+ * device) = mean0, mean1, sd0, sd1, correlation, skewness0, skewness1,
+ * mean excess kurtosis of the two axes (population moments). */
+kde_status kde_standardize2(const float* X, int64_t n, float* Z, double* moments,
+                            kde_stream_t stream);
+/* feat[KDE_FEAT_DIM] (FP32, device) from counts (M x M int64 from kde_bin,
+ * M a multiple of 32) of n samples and the moments above: feat[32 by + bx]
+ * = 8 sqrt(mass of block (by, bx) / n), feat[1024 ..] = correlation, the two
+ * skewnesses, excess kurtosis, log10(n)/4, 1, then zeros. */
+kde_status kde_features2(const int64_t* counts, int M, int64_t n, const double* moments,
+                         float* feat, kde_stream_t stream);
+
+/* Three-layer perceptron y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with
+ * BF16 operands and FP32 accumulation on the tensor cores (tcgen05),
+ * FP32 master parameters and Adam (beta 0.9, 0.999, eps 1e-8).  Sizes:
+ * in_dim % 64 == 0, hidden % 128 == 0, 1 <= out_dim <= 16, batches of at
+ * most max_batch rows.  Parameters are laid out flat as W1 (hidden x in_dim,
+ * row-major), b1, W2 (hidden x hidden), b2, W3 (out_dim x hidden), b3 and
+ * start He-normal (biases zero) from the seeded generator.  X (B x in_dim),
+ * T and Y (B x out_dim), loss (one float) and grads are device pointers;
+ * the parameter/state copies are host pointers and synchronise.  The loss
+ * is (1/B) sum over rows and outputs of (y - t)^2.  create allocates (set-up,
+ * not per step).  kde_mlp_status synchronises and reports 1 if a wait for
+ * the tensor cores gave up (the results of that call are then invalid). */
+typedef struct kde_mlp_s* kde_mlp;
+kde_status kde_mlp_create(int in_dim, int hidden, int out_dim, int max_batch, uint64_t seed,
+                          kde_mlp* out);
+kde_status kde_mlp_destroy(kde_mlp mlp);
+kde_status kde_mlp_param_count(kde_mlp mlp, int64_t* count);
+kde_status kde_mlp_get_params(kde_mlp mlp, float* host, int64_t count);
+kde_status kde_mlp_set_params(kde_mlp mlp, const float* host, int64_t count);
+kde_status kde_mlp_get_state(kde_mlp mlp, float* adam_m, float* adam_v, int64_t* step);
+kde_status kde_mlp_set_state(kde_mlp mlp, const float* adam_m, const float* adam_v, int64_t step);
+kde_status kde_mlp_forward(kde_mlp mlp, const float* X, int B, float* Y, kde_stream_t stream);
+kde_status kde_mlp_loss_grad(kde_mlp mlp, const float* X, const float* T, int B, float* loss,
+                             float* grads, kde_stream_t stream);
+kde_status kde_mlp_train_step(kde_mlp mlp, const float* X, const float* T, int B, float lr,
+                              float* loss, kde_stream_t stream);
+kde_status kde_mlp_status(kde_mlp mlp, int* flag);
+
+/* The tensor-core matrix product behind the network, exposed for testing:
+ * C[M x N] (FP32, row stride ldc) = A[M x K] B[N x K]^T with A and B BF16
+ * row-major (row strides lda, ldb elements), M % 128 == 0, N % 16 == 0,
+ * K % 64 == 0, strides multiples of 8, 16-byte aligned bases.  *status
+ * (device int) is set to 1 if a wait for the tensor cores gave up. */
+kde_status kde_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb,
+                         float* C, int ldc, int* status, kde_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

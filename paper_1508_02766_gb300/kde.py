@@ -60,8 +60,12 @@ EXPORTS = [
     "kde_fft_eval_noalloc", "kde_bin_workspace_bytes", "kde_power_spectrum", "kde_lscv",
     "kde_lscv_workspace_bytes", "kde_batch_plan_create", "kde_batch_plan_query",
     "kde_batch_set_shape", "kde_batch_get_shape", "kde_batch_tune", "kde_batch_eval",
-    "kde_batch_plan_destroy",
+    "kde_batch_plan_destroy", "kde_standardize2", "kde_features2", "kde_mlp_create",
+    "kde_mlp_destroy", "kde_mlp_param_count", "kde_mlp_get_params", "kde_mlp_set_params",
+    "kde_mlp_get_state", "kde_mlp_set_state", "kde_mlp_forward", "kde_mlp_loss_grad",
+    "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16",
 ]
+FEAT_DIM = 1088
 
 _lib = None
 
@@ -100,6 +104,23 @@ def lib():
                                  ctypes.POINTER(ctypes.c_float)]
     L.kde_batch_eval.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.kde_batch_plan_destroy.argtypes = [vp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.kde_standardize2.argtypes = [vp, i64, vp, vp, vp]
+    L.kde_features2.argtypes = [vp, ctypes.c_int, i64, vp, vp, vp]
+    L.kde_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_uint64, ctypes.POINTER(vp)]
+    L.kde_mlp_destroy.argtypes = [vp]
+    L.kde_mlp_param_count.argtypes = [vp, i64p]
+    L.kde_mlp_get_params.argtypes = [vp, fp, i64]
+    L.kde_mlp_set_params.argtypes = [vp, fp, i64]
+    L.kde_mlp_get_state.argtypes = [vp, fp, fp, i64p]
+    L.kde_mlp_set_state.argtypes = [vp, fp, fp, i64]
+    L.kde_mlp_forward.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    L.kde_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, vp]
+    L.kde_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, vp, vp]
+    L.kde_mlp_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.kde_gemm_bf16.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp,
+                                ctypes.c_int, vp, ctypes.c_int, vp, vp]
     L.kde_status_string.restype = ctypes.c_char_p
     L.kde_status_string.argtypes = [ctypes.c_int]
     L.kde_last_error.restype = ctypes.c_char_p
@@ -113,7 +134,11 @@ def lib():
                  "kde_bin_workspace_bytes", "kde_power_spectrum", "kde_lscv",
                  "kde_lscv_workspace_bytes", "kde_batch_plan_create", "kde_batch_plan_query",
                  "kde_batch_set_shape", "kde_batch_get_shape", "kde_batch_tune", "kde_batch_eval",
-                 "kde_batch_plan_destroy"):
+                 "kde_batch_plan_destroy", "kde_standardize2", "kde_features2",
+                 "kde_mlp_create", "kde_mlp_destroy", "kde_mlp_param_count",
+                 "kde_mlp_get_params", "kde_mlp_set_params", "kde_mlp_get_state",
+                 "kde_mlp_set_state", "kde_mlp_forward", "kde_mlp_loss_grad",
+                 "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -492,3 +517,114 @@ class PreparedPath:
         self.bin()
         self.kernel_grid()
         self.fft_eval()
+
+
+# ---------------------------------------------------------------------------
+# Learned bandwidth proposal (features, MLP, tensor-core GEMM).
+# ---------------------------------------------------------------------------
+def kde_standardize2(X, Z=None, moments=None, stream=None):
+    """Standardised samples Z (n x 2 float32) and moments[8] (float64)."""
+    import torch
+    if Z is None:
+        Z = torch.empty_like(X)
+    if moments is None:
+        moments = torch.empty(8, dtype=torch.float64, device=X.device)
+    _check(lib().kde_standardize2(_ptr(X), X.shape[0], _ptr(Z), _ptr(moments), _stream_ptr(stream)))
+    return Z, moments
+
+
+def kde_features2(counts, n, moments, feat=None, stream=None):
+    """feat[FEAT_DIM] from M x M counts of n standardised samples."""
+    import torch
+    if feat is None:
+        feat = torch.empty(FEAT_DIM, dtype=torch.float32, device=counts.device)
+    _check(lib().kde_features2(_ptr(counts), counts.shape[0], int(n), _ptr(moments), _ptr(feat),
+                               _stream_ptr(stream)))
+    return feat
+
+
+def kde_gemm_bf16(A, B, C=None, status=None, stream=None):
+    """C = A B^T on the tensor cores (A: M x K, B: N x K, bfloat16)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if C is None:
+        C = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib().kde_gemm_bf16(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C),
+                               C.stride(0), _ptr(status), _stream_ptr(stream)))
+    return C, status
+
+
+class MLP:
+    """kde_mlp_create / kde_mlp_destroy and the calls on one network."""
+
+    def __init__(self, in_dim=FEAT_DIM, hidden=256, out_dim=3, max_batch=256, seed=0):
+        L = lib()
+        h = ctypes.c_void_p()
+        _check(L.kde_mlp_create(in_dim, hidden, out_dim, max_batch, seed, ctypes.byref(h)))
+        self.handle = h
+        self.in_dim, self.hidden, self.out_dim, self.max_batch = in_dim, hidden, out_dim, max_batch
+        n = ctypes.c_int64()
+        _check(L.kde_mlp_param_count(h, ctypes.byref(n)))
+        self.nparam = n.value
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().kde_mlp_destroy(self.handle)
+            self.handle = None
+
+    def get_params(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        _check(lib().kde_mlp_get_params(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        self.nparam))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().kde_mlp_set_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        self.nparam))
+
+    def get_state(self):
+        m = np.empty(self.nparam, dtype=np.float32)
+        v = np.empty(self.nparam, dtype=np.float32)
+        step = ctypes.c_int64()
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(lib().kde_mlp_get_state(self.handle, m.ctypes.data_as(fp), v.ctypes.data_as(fp),
+                                       ctypes.byref(step)))
+        return m, v, step.value
+
+    def set_state(self, m, v, step):
+        m = np.ascontiguousarray(m, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        _check(lib().kde_mlp_set_state(self.handle, m.ctypes.data_as(fp), v.ctypes.data_as(fp),
+                                       int(step)))
+
+    def forward(self, X, Y=None, stream=None):
+        import torch
+        if Y is None:
+            Y = torch.empty(X.shape[0], self.out_dim, dtype=torch.float32, device=X.device)
+        _check(lib().kde_mlp_forward(self.handle, _ptr(X), X.shape[0], _ptr(Y), _stream_ptr(stream)))
+        return Y
+
+    def loss_grad(self, X, T, loss=None, grads=None, stream=None):
+        import torch
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        if grads is None:
+            grads = torch.empty(self.nparam, dtype=torch.float32, device=X.device)
+        _check(lib().kde_mlp_loss_grad(self.handle, _ptr(X), _ptr(T), X.shape[0], _ptr(loss),
+                                       _ptr(grads), _stream_ptr(stream)))
+        return loss, grads
+
+    def train_step(self, X, T, lr, loss=None, stream=None):
+        _check(lib().kde_mlp_train_step(self.handle, _ptr(X), _ptr(T), X.shape[0], float(lr),
+                                        _ptr(loss), _stream_ptr(stream)))
+        return loss
+
+    def status(self):
+        f = ctypes.c_int()
+        _check(lib().kde_mlp_status(self.handle, ctypes.byref(f)))
+        return f.value

@@ -1,0 +1,189 @@
+"""Learned bandwidth proposal on top of the binned FFT LSCV search.
+
+Orchestration only: every numerical step (standardisation, binning, features,
+count spectrum, LSCV of every candidate, the network's forward and backward
+passes, Adam) runs in the CUDA library through ``kde``; this module picks
+which calls to make, holds the candidate grid and keeps the buffers.
+
+Coordinates: each dataset is standardised per axis (Z = (X - mean) / sd) and
+binned on one fixed grid of the standardised plane, so every dataset shares
+one plan, one padding and one candidate set.  A bandwidth is proposed in
+those coordinates as log-Cholesky parameters theta = (a, beta, c),
+H_z = R R^T with R = [[e^a, 0], [beta e^c, e^c]]; in the data's coordinates
+it is H = D H_z D with D = diag(sd).  The plain method is the batched LSCV
+search over the whole candidate grid; the learned method scores the network's
+proposal and a small neighbourhood of it with the same FFT-evaluated LSCV and
+falls back to the plain search when the best of those is worse than the
+normal-reference bandwidth's score.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import kde
+
+GRID_M = 256
+GRID_LO, GRID_HI = -6.0, 6.0
+A_GRID = np.linspace(-2.8, -0.6, 12)      # log of the first Cholesky diagonal
+BETA_GRID = np.linspace(-1.2, 1.2, 7)     # off-diagonal over the second diagonal
+C_GRID = np.linspace(-2.8, -0.6, 12)      # log of the second Cholesky diagonal
+STEP = np.array([A_GRID[1] - A_GRID[0], BETA_GRID[1] - BETA_GRID[0], C_GRID[1] - C_GRID[0]])
+
+
+def theta_to_H(theta):
+    a, beta, c = (float(v) for v in theta)
+    R = np.array([[math.exp(a), 0.0], [beta * math.exp(c), math.exp(c)]])
+    return R @ R.T
+
+
+def candidate_thetas():
+    """The plain search's candidates: every (a, beta, c) of the grids."""
+    return np.array(list(itertools.product(A_GRID, BETA_GRID, C_GRID)), dtype=np.float64)
+
+
+def normal_reference_theta(n):
+    """Textbook normal-reference rule in standardised coordinates:
+    H = (4/(d+2))^(2/(d+4)) n^(-2/(d+4)) S with S the identity (d = 2)."""
+    h2 = (4.0 / 4.0) ** (2.0 / 6.0) * n ** (-2.0 / 6.0)
+    return np.array([0.5 * math.log(h2), 0.0, 0.5 * math.log(h2)])
+
+
+def neighbourhood(theta, scale=0.5):
+    """3 x 3 x 3 candidates around theta, spaced scale grid steps apart."""
+    offs = np.array(list(itertools.product((-1, 0, 1), repeat=3)), dtype=np.float64)
+    return theta[None, :] + scale * offs * STEP[None, :]
+
+
+class LscvScorer:
+    """One shared plan for the standardised grid and the buffers of one
+    dataset at a time: standardise, bin, features, count spectrum, then the
+    LSCV of any list of candidates."""
+
+    def __init__(self, n_max, device="cuda", tau=3.7):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        cand = candidate_thetas()
+        # padding sized by the widest 2 H over the candidate box (and its edges)
+        big = max((2.0 * theta_to_H(t) for t in itertools.product(
+            (A_GRID[-1] + STEP[0],), (BETA_GRID[0] - STEP[1], BETA_GRID[-1] + STEP[1]),
+            (C_GRID[-1] + STEP[2],))), key=lambda h: np.linalg.eigvalsh(h).max())
+        M = (GRID_M, GRID_M)
+        lo, hi = (GRID_LO, GRID_LO), (GRID_HI, GRID_HI)
+        pinfo = kde.kde_plan_info_compute(M, lo, hi, big, precision="f32", tau=tau)
+        self.plan = kde.Plan(M, lo, hi, big, precision="f32", tau=tau, P_min=pinfo.P)
+        self.M, self.lo, self.hi, self.tau = M, lo, hi, tau
+        info = self.plan.info
+        self.counts = torch.empty(M, dtype=torch.int64, device=self.device)
+        self.Z = torch.empty(n_max, 2, dtype=torch.float32, device=self.device)
+        self.mom = torch.empty(8, dtype=torch.float64, device=self.device)
+        self.feat = torch.empty(kde.FEAT_DIM, dtype=torch.float32, device=self.device)
+        self.W = torch.empty(info.kspec_elems, dtype=torch.float32, device=self.device)
+        self.ws = self.plan.workspace(self.device)
+        self.lws = torch.empty(max(256, kde.kde_lscv_workspace_bytes(self.plan)), dtype=torch.uint8,
+                               device=self.device)
+        self.n = 0
+        self.cand = cand
+        self.cand_H = np.stack([theta_to_H(t) for t in cand])
+
+    def prepare(self, X):
+        """X: n x 2 float32 CUDA tensor of one dataset."""
+        n = X.shape[0]
+        Z = self.Z[:n]
+        kde.kde_standardize2(X, Z=Z, moments=self.mom)
+        kde.kde_bin(Z, self.lo, self.hi, self.M, counts=self.counts, method="direct")
+        kde.kde_features2(self.counts, n, self.mom, feat=self.feat)
+        kde.kde_power_spectrum(self.plan, self.counts, W=self.W, workspace=self.ws)
+        self.n = n
+        return self.feat
+
+    def scores(self, H):
+        """LSCV of every H (k x 2 x 2, standardised coordinates), on the GPU."""
+        torch = self.torch
+        out = torch.empty(len(H), dtype=torch.float64, device=self.device)
+        kde.kde_lscv(self.plan, self.n, np.asarray(H, dtype=np.float64), self.W, lscv=out,
+                     workspace=self.lws)
+        return out
+
+    def search(self):
+        """The plain method: argmin of LSCV over the whole candidate grid."""
+        s = self.scores(self.cand_H)
+        i = int(self.torch.argmin(s).item())
+        return self.cand[i], float(s[i].item())
+
+    def moments(self):
+        return self.mom.cpu().numpy()
+
+
+@dataclass
+class LabelledSet:
+    feats: np.ndarray      # D x FEAT_DIM float32
+    theta: np.ndarray      # D x 3 (LSCV argmin)
+    best: np.ndarray       # D (its LSCV)
+    n: np.ndarray          # D
+
+
+def label_datasets(scorer, datasets):
+    """Features and plain-search labels for every dataset."""
+    torch = scorer.torch
+    D = len(datasets)
+    feats = np.empty((D, kde.FEAT_DIM), dtype=np.float32)
+    theta = np.empty((D, 3))
+    best = np.empty(D)
+    ns = np.empty(D, dtype=np.int64)
+    for i, X in enumerate(datasets):
+        Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(scorer.device)
+        f = scorer.prepare(Xd)
+        theta[i], best[i] = scorer.search()
+        feats[i] = f.cpu().numpy()
+        ns[i] = X.shape[0]
+    return LabelledSet(feats, theta, best, ns)
+
+
+def train(mlp, feats, theta, epochs=30, batch=256, lr=1e-3, seed=0, device="cuda"):
+    """Adam on mean squared error between network output and labels; the
+    whole set stays on the device; returns the per-epoch mean loss."""
+    import torch
+    F = torch.from_numpy(np.ascontiguousarray(feats, dtype=np.float32)).to(device)
+    T = torch.from_numpy(np.ascontiguousarray(theta, dtype=np.float32)).to(device)
+    rng = np.random.default_rng(seed)
+    loss = torch.zeros(1, dtype=torch.float32, device=device)
+    hist = []
+    D = F.shape[0]
+    for _ in range(epochs):
+        perm = torch.from_numpy(rng.permutation(D)).to(device)
+        acc, nb = 0.0, 0
+        for s in range(0, D - batch + 1, batch):
+            idx = perm[s:s + batch]
+            mlp.train_step(F[idx].contiguous(), T[idx].contiguous(), lr, loss=loss)
+            acc += float(loss.item())
+            nb += 1
+        hist.append(acc / max(1, nb))
+    return hist
+
+
+def select(scorer, mlp, X, refine=True, fallback=True):
+    """The learned method on one dataset: score the network's proposal (and
+    its 3 x 3 x 3 neighbourhood), compare with the normal-reference score and
+    fall back to the plain search when the proposal is worse.  Returns
+    (theta, lscv, candidates scored, fell back)."""
+    torch = scorer.torch
+    f = scorer.prepare(X)
+    th = mlp.forward(f.view(1, -1)).cpu().numpy()[0].astype(np.float64)
+    # keep the neighbourhood inside the box the plan's padding was sized for
+    lo = np.array([A_GRID[0], BETA_GRID[0], C_GRID[0]]) - 0.5 * STEP
+    hi = np.array([A_GRID[-1], BETA_GRID[-1], C_GRID[-1]]) + 0.5 * STEP
+    th = np.clip(th, lo, hi)
+    cands = neighbourhood(th) if refine else th[None, :]
+    ref = normal_reference_theta(X.shape[0])
+    H = np.stack([theta_to_H(t) for t in cands] + [theta_to_H(ref)])
+    s = scorer.scores(H).cpu().numpy()
+    i = int(np.argmin(s[:-1]))
+    if fallback and s[i] > s[-1]:
+        t, v = scorer.search()
+        return t, v, len(H) + len(scorer.cand), True
+    return cands[i], float(s[i]), len(H), False

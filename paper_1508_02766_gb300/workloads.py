@@ -235,3 +235,25 @@ def ragged64_f32(seed=5, count=64):
         lo, hi = grid_range(X, H)
         out.append(Workload("ragged", X.astype(np.float32), H, lo, hi, (m, m), "f32"))
     return out
+
+
+def mixture_datasets(seed, count, n=10_000):
+    """Datasets for the learned bandwidth proposal: 2-D Gaussian mixtures with
+    2-5 components, weights Dirichlet(2), means U[-3, 3]^2 and covariances
+    Q diag(s1, s2) Q^T with s ~ exp(U[log 0.05, log 1.5]) and Q a random
+    rotation; n samples each (float32)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        k = int(rng.integers(2, 6))
+        w = rng.dirichlet(np.full(k, 2.0))
+        means = rng.uniform(-3.0, 3.0, size=(k, 2))
+        covs = []
+        for _ in range(k):
+            ang = rng.uniform(0, np.pi)
+            c, s = np.cos(ang), np.sin(ang)
+            Q = np.array([[c, -s], [s, c]])
+            ev = np.exp(rng.uniform(np.log(0.05), np.log(1.5), size=2))
+            covs.append((Q * ev) @ Q.T)
+        out.append(mixture_samples(rng, n, means, covs, w).astype(np.float32))
+    return out
