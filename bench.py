@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--bin-method", default="auto", choices=["auto", "direct", "tiled"])
+    ap.add_argument("--train-sets", type=int, default=20_000,
+                    help="learned2d_256: training datasets labelled by the plain search")
     return ap.parse_args()
 
 
@@ -292,6 +294,8 @@ def main():
         return lscv_main(args)
     if args.workload.startswith("ragged"):
         return ragged_main(args)
+    if args.workload.startswith("learned"):
+        return learned_main(args)
     import torch
     import torch.distributed as dist
 
@@ -717,6 +721,165 @@ print(json.dumps({"t": time.perf_counter() - t0, "S": out}))
                                 "sample": f"oracle spectral pair sums (plain DFT) for {len(idx)} "
                                           f"candidates ({res['t']:.1f} s)"}
         line["accuracy"] = {"max_rel_err_pair_sums_vs_oracle": float(np.max(np.abs(have - want) / np.abs(want)))}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# Learned bandwidth proposal vs the plain batched LSCV search.
+# ---------------------------------------------------------------------------
+LEARN_METRIC = ("bandwidth selections/s of the learned proposal (scored and refined by FFT LSCV) "
+                "vs the plain batched LSCV search, same grid and accuracy")
+
+
+def learned_main(args):
+    import torch
+    from paper_1508_02766_gb300 import build as B
+    from paper_1508_02766_gb300 import kde
+    from paper_1508_02766_gb300 import learned as Lm
+    from paper_1508_02766_gb300 import workloads as W
+    if not os.path.exists(B.LIB):
+        B.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = 10_000
+    train_sets = W.mixture_datasets(31, args.train_sets, n=n)
+    test_sets = W.mixture_datasets(32, args.warmup + args.steps, n=n)
+    sc = Lm.LscvScorer(n)
+    # labels: the plain search on every training dataset
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lab = Lm.label_datasets(sc, train_sets)
+    torch.cuda.synchronize()
+    t_label = time.perf_counter() - t0
+    # training, with the library's per-kernel events
+    mlp = kde.MLP(in_dim=kde.FEAT_DIM, hidden=256, out_dim=3, max_batch=256, seed=0)
+    epochs, batch = 40, 256
+    kde.profile_enable(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = Lm.train(mlp, lab.feats, lab.theta, epochs=epochs, batch=batch, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    prof_train = kde.profile_read()
+    kde.profile_enable(False)
+    steps_train = epochs * (len(train_sets) // batch)
+    Bp, hid, din = 256, 256, kde.FEAT_DIM
+    gemm_flops_step = 2.0 * Bp * (din * hid + hid * hid + hid * 16) + 2.0 * (
+        hid * 16 * Bp + Bp * hid * 64 + hid * hid * Bp + Bp * hid * hid + hid * din * Bp)
+    g_ms, g_n = prof_train.get("kde_gemm_tc_kernel", (0.0, 1))
+    peak_bf16 = 1897.8
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        with open(pp) as fh:
+            peak_bf16 = float(json.load(fh).get("bf16_tflops", peak_bf16))
+    gemm_tf = gemm_flops_step * steps_train / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
+
+    def upload(X):
+        return torch.from_numpy(X).to(dev)
+
+    for X in test_sets[:args.warmup]:
+        Xd = upload(X)
+        sc.prepare(Xd)
+        sc.search()
+        Lm.select(sc, mlp, Xd)
+    evals = test_sets[args.warmup:]
+    K = len(evals)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    # plain method: standardise, bin, count spectrum, LSCV of every candidate, argmin
+    torch.cuda.synchronize()
+    l0 = kde.launch_count()
+    t0 = time.perf_counter()
+    best = []
+    for X in evals:
+        sc.prepare(upload(X))
+        best.append(sc.search()[1])
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    launches_plain = kde.launch_count() - l0
+    # learned method: features, network, 28 scored candidates, fallback rule
+    kde.profile_enable(True)
+    scored = []
+    torch.cuda.synchronize()
+    l0 = kde.launch_count()
+    t0 = time.perf_counter()
+    got, fell, ncand = [], 0, 0
+    for X in evals:
+        th, v, k, fb = Lm.select(sc, mlp, upload(X), scored=scored)
+        got.append(v)
+        fell += int(fb)
+        ncand += k
+    torch.cuda.synchronize()
+    t_learn = time.perf_counter() - t0
+    launches_learn = kde.launch_count() - l0
+    prof = kde.profile_read()
+    kde.profile_enable(False)
+    clocks = sampler.stop()
+    # the method without the network: the normal-reference bandwidth refined
+    # over the same neighbourhood
+    reg_ref = []
+    for X, b in zip(evals[:200], best[:200]):
+        sc.prepare(upload(X))
+        ref = Lm.normal_reference_theta(X.shape[0])
+        s = sc.scores(np.stack([Lm.theta_to_H(t) for t in Lm.neighbourhood(ref)])).cpu().numpy()
+        reg_ref.append((s.min() - b) / abs(b))
+    best, got = np.array(best), np.array(got)
+    rel_regret = (got - best) / np.abs(best)
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                   "share": v[0] / max(1e-12, sum(x[0] for x in prof.values()))}
+               for k, v in prof.items()}
+    # roofline of the selection loop's dominant kernel
+    info = sc.plan.info
+    P0, P1, Q = info.P[0], info.P[1], info.Q
+    Ls = [kde.kde_plan_info_compute(sc.M, sc.lo, sc.hi, A, precision="f32").L[0]
+          for h in scored for A in (h, 2.0 * h)]
+    flops = {"kde_rows_kgen_batch_kernel": sum(fft_flops(L0 + 1, P1) for L0 in Ls),
+             "kde_cols_kgen_dot_kernel": len(Ls) * (fft_flops((Q + 1) // 2, P0) + 2.0 * P0 * Q),
+             "kde_gemm_tc_kernel": K * 2.0 * 128 * (din * hid + hid * hid + hid * 16)}
+    dom = max(prof, key=lambda k: prof[k][0])
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    if dom == "kde_gemm_tc_kernel":
+        ach = flops[dom] / (prof[dom][0] * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": peak_bf16,
+                    "unit": "TFLOP/s", "frac": ach / peak_bf16, "traffic": None,
+                    "peak_source": "measured (bf16 burst)",
+                    "flops_per_launch": flops[dom] / prof[dom][1]}
+    elif dom in flops:
+        ach = flops[dom] / (prof[dom][0] * 1e-3) / 1e12
+        peak = fp32_peak_tflops(sm_max)
+        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x SM max clock",
+                    "flops_per_launch": flops[dom] / prof[dom][1]}
+    else:
+        roofline = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None,
+                    "unit": "TFLOP/s", "frac": None, "traffic": None}
+    line = {"metric": LEARN_METRIC, "value": K / t_learn, "unit": "datasets/s",
+            "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_learn / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+            "data": "synthetic",
+            "config": {"workload": "learned2d_256", "grid": [256, 256], "n": n,
+                       "train_datasets": len(train_sets), "test_datasets": K,
+                       "candidates_plain": int(len(sc.cand)), "P": list(info.P),
+                       "mlp": f"{kde.FEAT_DIM}-256-256-3 ReLU, BF16 operands, FP32 accumulation",
+                       "timing": "wall clock around the loop with device synchronisation, "
+                                 "host-to-device copy of each dataset included"},
+            "plain_search": {"value": K / t_plain, "unit": "datasets/s",
+                             "ms_per_dataset": 1e3 * t_plain / K,
+                             "gpu_launches": launches_plain},
+            "speedup_vs_plain": t_plain / t_learn,
+            "quality": {"mean_rel_regret": float(rel_regret.mean()),
+                        "p95_rel_regret": float(np.percentile(rel_regret, 95)),
+                        "fraction_exact_best": float(np.mean(rel_regret <= 1e-12)),
+                        "fallbacks": fell, "mean_candidates": ncand / K,
+                        "normal_reference_refined_mean_rel_regret": float(np.mean(reg_ref))},
+            "labels": {"datasets_per_s": len(train_sets) / t_label},
+            "training": {"samples_per_s": steps_train * batch / t_train, "epochs": epochs,
+                         "loss_first_last": [hist[0], hist[-1]],
+                         "gemm_tflops": gemm_tf, "gemm_frac_of_bf16_peak": gemm_tf / peak_bf16},
+            "roofline": roofline, "kernels": kernels, "gpu_launches": launches_learn,
+            "clocks": clocks}
     print(json.dumps(line))
 
 

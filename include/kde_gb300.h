@@ -285,7 +285,8 @@ kde_status kde_profile_entry(int i, const char** name, double* total_ms, int64_t
 /* One block reduction over n >= 2 samples (X: n x 2 FP32, device):
  * Z = (X - mean) / sd per axis (FP32, device, n x 2) and moments[8] (FP64,
  * device) = mean0, mean1, sd0, sd1, correlation, skewness0, skewness1,
- * mean excess kurtosis of the two axes (population moments). */
+ * mean excess kurtosis of the two axes (population moments).  The sums are
+ * FP32 trees, so the moments carry FP32-level relative error (about 1e-6). */
 kde_status kde_standardize2(const float* X, int64_t n, float* Z, double* moments,
                             kde_stream_t stream);
 /* feat[KDE_FEAT_DIM] (FP32, device) from counts (M x M int64 from kde_bin,

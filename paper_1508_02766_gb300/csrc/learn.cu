@@ -84,12 +84,35 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
   return done != 0;
 }
 
+// Stage the 64-wide K slice k0 of A's rows m0.. and B's rows n0.. into one
+// shared-memory stage with 16-byte cp.async copies (one commit group).
+template <int BN>
+__device__ __forceinline__ void stage_tiles(const GemmArgs& g, uint8_t* sA, uint8_t* sB, int m0,
+                                            int n0, int k0) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 128 * 8; i += 128) {
+    const int r = i >> 3, c = i & 7;
+    const size_t src = __cvta_generic_to_global(g.A + (size_t)(m0 + r) * g.lda + k0 + 8 * c);
+    const uint32_t dst = smem_u32(sA + (r >> 3) * 1024 + c * 128 + (r & 7) * 16);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  }
+  for (int i = tid; i < BN * 8; i += 128) {
+    const int r = i >> 3, c = i & 7;
+    const size_t src = __cvta_generic_to_global(g.B + (size_t)(n0 + r) * g.ldb + k0 + 8 * c);
+    const uint32_t dst = smem_u32(sB + (r >> 3) * 1024 + c * 128 + (r & 7) * 16);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Two shared-memory stages: the copies of K slice k+1 are in flight while
+// the tensor cores work on slice k; a stage is refilled only after the MMAs
+// that read it have completed (its mbarrier).
 template <int BN, int EPI>
 __global__ void __launch_bounds__(128) kde_gemm_tc_kernel(GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA = smem;          // 128 x 64 BF16: 16 KB
-  uint8_t* sB = smem + 16384;  // BN x 64 BF16
-  __shared__ __align__(8) uint64_t mbar;
+  constexpr int kStageBytes = 16384 + BN * 128;  // A 128 x 64 + B BN x 64, BF16
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   constexpr uint32_t kCols = BN < 32 ? 32 : BN;  // TMEM columns: a power of two >= 32
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -102,7 +125,8 @@ __global__ void __launch_bounds__(128) kde_gemm_tc_kernel(GemmArgs g) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -113,33 +137,40 @@ __global__ void __launch_bounds__(128) kde_gemm_tc_kernel(GemmArgs g) {
   // (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                          ((uint32_t)(128 >> 4) << 24);
-  uint32_t phase = 0;
+  uint32_t phase = 0u, used = 0u;  // bit b: stage b's barrier phase / MMAs pending
   bool ok = true;
-  for (int k0 = 0; k0 < g.K; k0 += 64) {
-    for (int i = tid; i < 128 * 8; i += 128) {
-      const int r = i >> 3, c = i & 7;
-      const size_t src = __cvta_generic_to_global(g.A + (size_t)(m0 + r) * g.lda + k0 + 8 * c);
-      const uint32_t dst = smem_u32(sA + (r >> 3) * 1024 + c * 128 + (r & 7) * 16);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  const int nk = g.K / 64;
+  stage_tiles<BN>(g, smem, smem + 16384, m0, n0, 0);
+  for (int kt = 0; kt < nk; ++kt) {
+    const int st = kt & 1, nx = st ^ 1;
+    if (kt + 1 < nk) {
+      // the other stage was read by the MMAs of slice kt - 1: wait for them
+      if ((used >> nx) & 1u) {
+        const bool done = mbar_wait(smem_u32(&mbar[nx]), (phase >> nx) & 1u);
+        if (!__syncthreads_and(done)) {
+          ok = false;
+          break;
+        }
+        phase ^= 1u << nx;
+        used &= ~(1u << nx);
+      }
+      stage_tiles<BN>(g, smem + nx * kStageBytes, smem + nx * kStageBytes + 16384, m0, n0,
+                      (kt + 1) * 64);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
-    for (int i = tid; i < BN * 8; i += 128) {
-      const int r = i >> 3, c = i & 7;
-      const size_t src = __cvta_generic_to_global(g.B + (size_t)(n0 + r) * g.ldb + k0 + 8 * c);
-      const uint32_t dst = smem_u32(sB + (r >> 3) * 1024 + c * 128 + (r & 7) * 16);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
     // the tensor cores read shared memory through the async proxy
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(smem + st * kStageBytes), b0 = a0 + 16384u;
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        const uint64_t da = umma_desc(smem_u32(sA) + 256u * s);
-        const uint64_t db = umma_desc(smem_u32(sB) + 256u * s);
-        const uint32_t acc = (k0 > 0 || s > 0) ? 1u : 0u;
+        const uint64_t da = umma_desc(a0 + 256u * s);
+        const uint64_t db = umma_desc(b0 + 256u * s);
+        const uint32_t acc = (kt > 0 || s > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -148,19 +179,23 @@ __global__ void __launch_bounds__(128) kde_gemm_tc_kernel(GemmArgs g) {
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&mbar))
+              smem_u32(&mbar[st]))
           : "memory");
     }
-    // the MMAs also read the staged tiles: wait before they are overwritten;
-    // the block agrees on the outcome so that every thread leaves together
-    const bool done = mbar_wait(smem_u32(&mbar), phase);
-    if (!__syncthreads_and(done)) {
-      ok = false;
-      if (tid == 0) atomicExch(g.status, 1);
-      mbar_wait(smem_u32(&mbar), phase);  // one more bounded chance before TMEM is freed
-      break;
-    }
-    phase ^= 1u;
+    used |= 1u << st;
+  }
+  // every MMA has been committed; the last commit tracks them all
+  if (ok) {
+    const int last = (nk - 1) & 1;
+    const bool done = mbar_wait(smem_u32(&mbar[last]), (phase >> last) & 1u);
+    ok = __syncthreads_and(done);
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(g.status, 1);
+    // one more bounded chance for the MMAs in flight before TMEM is freed
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    for (int b = 0; b < 2; ++b)
+      if ((used >> b) & 1u) mbar_wait(smem_u32(&mbar[b]), (phase >> b) & 1u);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
@@ -207,9 +242,10 @@ __global__ void __launch_bounds__(128) kde_gemm_tc_kernel(GemmArgs g) {
 
 template <int BN, int EPI>
 cudaError_t launch_gemm_bn(const GemmArgs& g, cudaStream_t st) {
-  // 28 KB of dynamic shared memory caps the CTAs per SM at 8, so the tensor
-  // memory they hold (8 x 64 columns) never exceeds the SM's 512 columns.
-  const int smem = 28 * 1024;
+  // Two stages of A (16 KB) and B (BN x 128 bytes); 56 KB of dynamic shared
+  // memory caps the CTAs per SM at 4, so the tensor memory they hold
+  // (4 x 64 columns) stays within the SM's 512 columns.
+  const int smem = 56 * 1024;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kde_gemm_tc_kernel<BN, EPI>,
@@ -378,83 +414,107 @@ __global__ void __launch_bounds__(256) kde_mlp_take_kernel(const float* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Standardisation and features (d = 2).
+// Standardisation and features (d = 2).  FP64 arithmetic runs at a small
+// fraction of FP32's rate on this GPU, so the sums are FP32 trees (each
+// thread about ten samples, then warp shuffles and one warp over the warp
+// partials); only thread 0 forms the FP64 outputs.
 // ---------------------------------------------------------------------------
-__device__ double block_sum_d(double v, double* buf) {
-  buf[threadIdx.x] = v;
+__device__ float block_sum_f(float v, float* wbuf) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) wbuf[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) buf[threadIdx.x] += buf[threadIdx.x + s];
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    float w = threadIdx.x < (blockDim.x >> 5) ? wbuf[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) w += __shfl_down_sync(0xffffffffu, w, off);
+    if (threadIdx.x == 0) wbuf[32] = w;
   }
-  const double r = buf[0];
+  __syncthreads();
+  const float r = wbuf[32];
   __syncthreads();
   return r;
 }
 
 // One block of 1024 threads.  moments = {mean0, mean1, sd0, sd1, corr,
-// skew0, skew1, (kurt0 + kurt1)/2 - 3} (population moments, FP64);
-// Z = (X - mean) / sd in FP32.
+// skew0, skew1, (kurt0 + kurt1)/2 - 3} (population moments); Z = (X - mean)
+// / sd in FP32.
 __global__ void __launch_bounds__(1024) kde_standardize2_kernel(const float* __restrict__ X,
                                                                 int64_t n, float* __restrict__ Z,
                                                                 double* __restrict__ mom) {
-  __shared__ double buf[1024];
-  double s0 = 0, s1 = 0;
+  __shared__ float wbuf[33];
+  const float inv_n = 1.0f / (float)n;
+  float s0 = 0.f, s1 = 0.f;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     s0 += X[2 * i];
     s1 += X[2 * i + 1];
   }
-  const double m0 = block_sum_d(s0, buf) / n, m1 = block_sum_d(s1, buf) / n;
-  double q00 = 0, q11 = 0, q01 = 0;
+  const float m0 = block_sum_f(s0, wbuf) * inv_n, m1 = block_sum_f(s1, wbuf) * inv_n;
+  float q00 = 0.f, q11 = 0.f, q01 = 0.f;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double a = X[2 * i] - m0, b = X[2 * i + 1] - m1;
-    q00 += a * a;
-    q11 += b * b;
-    q01 += a * b;
+    const float a = X[2 * i] - m0, b = X[2 * i + 1] - m1;
+    q00 = fmaf(a, a, q00);
+    q11 = fmaf(b, b, q11);
+    q01 = fmaf(a, b, q01);
   }
-  const double v0 = block_sum_d(q00, buf) / n, v1 = block_sum_d(q11, buf) / n,
-               c01 = block_sum_d(q01, buf) / n;
-  const double sd0 = sqrt(v0), sd1 = sqrt(v1);
-  double t3a = 0, t3b = 0, t4a = 0, t4b = 0;
+  const float v0 = block_sum_f(q00, wbuf) * inv_n, v1 = block_sum_f(q11, wbuf) * inv_n;
+  const float c01 = block_sum_f(q01, wbuf) * inv_n;
+  const float sd0 = sqrtf(v0), sd1 = sqrtf(v1);
+  const float r0 = 1.0f / sd0, r1 = 1.0f / sd1;
+  float t3a = 0.f, t3b = 0.f, t4a = 0.f, t4b = 0.f;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double a = (X[2 * i] - m0) / sd0, b = (X[2 * i + 1] - m1) / sd1;
-    Z[2 * i] = (float)a;
-    Z[2 * i + 1] = (float)b;
-    t3a += a * a * a;
-    t3b += b * b * b;
-    t4a += a * a * a * a;
-    t4b += b * b * b * b;
+    const float a = (X[2 * i] - m0) * r0, b = (X[2 * i + 1] - m1) * r1;
+    Z[2 * i] = a;
+    Z[2 * i + 1] = b;
+    const float a2 = a * a, b2 = b * b;
+    t3a = fmaf(a2, a, t3a);
+    t3b = fmaf(b2, b, t3b);
+    t4a = fmaf(a2, a2, t4a);
+    t4b = fmaf(b2, b2, t4b);
   }
-  const double sk0 = block_sum_d(t3a, buf) / n, sk1 = block_sum_d(t3b, buf) / n;
-  const double ku = 0.5 * (block_sum_d(t4a, buf) + block_sum_d(t4b, buf)) / n - 3.0;
+  const float sk0 = block_sum_f(t3a, wbuf) * inv_n, sk1 = block_sum_f(t3b, wbuf) * inv_n;
+  const float k0 = block_sum_f(t4a, wbuf), k1 = block_sum_f(t4b, wbuf);
   if (threadIdx.x == 0) {
     mom[0] = m0;
     mom[1] = m1;
     mom[2] = sd0;
     mom[3] = sd1;
-    mom[4] = c01 / (sd0 * sd1);
+    mom[4] = (double)c01 / ((double)sd0 * sd1);
     mom[5] = sk0;
     mom[6] = sk1;
-    mom[7] = ku;
+    mom[7] = 0.5 * ((double)k0 + k1) / (double)n - 3.0;
   }
 }
 
-// One block of 1024 threads, one per 32 x 32 block of the M x M grid:
-// feat[b] = 8 sqrt(block mass / n) (mass = sum of counts 2^-32), then
-// feat[1024..1029] = corr, skew0, skew1, excess kurtosis, log10(n)/4, 1;
-// the rest of the kKdeFeat entries are zero.
-__global__ void __launch_bounds__(1024) kde_features2_kernel(const long long* __restrict__ counts,
-                                                             int M, int64_t n,
-                                                             const double* __restrict__ mom,
-                                                             float* __restrict__ feat) {
-  const int t = threadIdx.x;
-  const int by = t / 32, bx = t % 32, w = M / 32;
-  long long s = 0;
-  for (int y = 0; y < w; ++y)
-    for (int x = 0; x < w; ++x) s += counts[(size_t)(by * w + y) * M + bx * w + x];
-  const double mass = (double)s * 2.3283064365386963e-10 / (double)n;
-  feat[t] = (float)(8.0 * sqrt(mass));
-  if (t < 64) {
+// 32 blocks of 256 threads, block `by` for the 32 block-features of one
+// block row of the M x M grid (w = M/32 cells a side): thread (y0, bx) sums
+// rows y0, y0 + 8, ... of block (by, bx); the rows are then added in shared
+// memory.  feat[32 by + bx] = 8 sqrt(mass / n) with mass the block's counts
+// times 2^-32; block 0 also writes feat[1024..] = corr, skew0, skew1, excess
+// kurtosis, log10(n)/4, 1, then zeros.
+__global__ void __launch_bounds__(256) kde_features2_kernel(const long long* __restrict__ counts,
+                                                            int M, int64_t n,
+                                                            const double* __restrict__ mom,
+                                                            float* __restrict__ feat) {
+  __shared__ unsigned long long part[8][32];
+  const int by = blockIdx.x, t = threadIdx.x, bx = t & 31, y0 = t >> 5, w = M / 32;
+  unsigned long long s = 0;
+  for (int y = y0; y < w; y += 8) {
+    const long long* row = counts + (size_t)(by * w + y) * M + bx * w;
+    for (int x = 0; x < w; ++x) s += (unsigned long long)row[x];
+  }
+  part[y0][bx] = s;
+  __syncthreads();
+  if (t < 32) {
+    unsigned long long tot = 0;
+    for (int k = 0; k < 8; ++k) tot += part[k][t];
+    // tot 2^-32 from its two 32-bit halves (no 64-bit integer conversion)
+    const float mass =
+        fmaf((float)(unsigned)(tot >> 32), 1.0f, (float)(unsigned)tot * 2.3283064365386963e-10f) /
+        (float)n;
+    feat[by * 32 + t] = 8.0f * sqrtf(mass);
+  }
+  if (by == 0 && t < 64) {
     float v = 0.f;
     if (t == 0) v = (float)mom[4];
     if (t == 1) v = (float)mom[5];
@@ -822,7 +882,7 @@ kde_status kde_features2(const int64_t* counts, int M, int64_t n, const double* 
     return fail(KDE_ERR_INVALID_ARG, "features: M must be a multiple of 32");
   cudaStream_t st = (cudaStream_t)stream;
   LaunchScope ls("kde_features2_kernel", st);
-  kde_features2_kernel<<<1, 1024, 0, st>>>((const long long*)counts, M, n, moments, feat);
+  kde_features2_kernel<<<32, 256, 0, st>>>((const long long*)counts, M, n, moments, feat);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, "kde_features2_kernel");
 }

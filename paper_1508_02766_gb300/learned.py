@@ -166,11 +166,12 @@ def train(mlp, feats, theta, epochs=30, batch=256, lr=1e-3, seed=0, device="cuda
     return hist
 
 
-def select(scorer, mlp, X, refine=True, fallback=True):
+def select(scorer, mlp, X, refine=True, fallback=True, scored=None):
     """The learned method on one dataset: score the network's proposal (and
     its 3 x 3 x 3 neighbourhood), compare with the normal-reference score and
     fall back to the plain search when the proposal is worse.  Returns
-    (theta, lscv, candidates scored, fell back)."""
+    (theta, lscv, candidates scored, fell back); appends the scored H
+    matrices to ``scored`` if given."""
     torch = scorer.torch
     f = scorer.prepare(X)
     th = mlp.forward(f.view(1, -1)).cpu().numpy()[0].astype(np.float64)
@@ -182,8 +183,12 @@ def select(scorer, mlp, X, refine=True, fallback=True):
     ref = normal_reference_theta(X.shape[0])
     H = np.stack([theta_to_H(t) for t in cands] + [theta_to_H(ref)])
     s = scorer.scores(H).cpu().numpy()
+    if scored is not None:
+        scored.extend(H)
     i = int(np.argmin(s[:-1]))
     if fallback and s[i] > s[-1]:
         t, v = scorer.search()
+        if scored is not None:
+            scored.extend(scorer.cand_H)
         return t, v, len(H) + len(scorer.cand), True
     return cands[i], float(s[i]), len(H), False

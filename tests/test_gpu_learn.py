@@ -49,7 +49,8 @@ def test_standardize_and_features_match_oracle():
     Xd = torch.from_numpy(X).to(DEV)
     Z, mom = kde.kde_standardize2(Xd)
     Zo, momo = LO.standardize(X)
-    assert np.allclose(mom.cpu().numpy(), momo, rtol=1e-9, atol=1e-12)
+    # FP32 tree sums
+    assert np.allclose(mom.cpu().numpy(), momo, rtol=1e-5, atol=1e-5)
     assert np.max(np.abs(Z.cpu().numpy() - Zo)) < 1e-5
     # features from the GPU's counts of the GPU's Z; the counts are checked
     # bit-exact against the oracle's binning of the same Z
