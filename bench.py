@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--bin-method", default="auto", choices=["auto", "direct", "tiled"])
+    ap.add_argument("--dft", default="fft", choices=["fft", "tc"],
+                    help="first pass: mixed-radix FFT, or split-TF32 DFT matrix on the tensor cores")
     ap.add_argument("--train-sets", type=int, default=20_000,
                     help="learned2d_256: training datasets labelled by the plain search")
     return ap.parse_args()
@@ -76,6 +78,8 @@ def algorithmic_bytes(info, n, x_itemsize):
         b["kde_cols_mid_kernel"] = 2 * M[0] * P[1] * Q * cs + P[0] * P[1] * Q * r
         b["kde_cols_inv_kernel"] = M[0] * P[1] * Q * cs + M[0] * M[1] * Q * cs
         b["kde_rows_c2r_kernel"] = M[0] * M[1] * Q * cs + cells * r
+    if "kde_rows_r2c_counts_kernel" in b:  # the same pass on the tensor cores
+        b["kde_rows_r2c_tc_kernel"] = b["kde_rows_r2c_counts_kernel"]
     return b
 
 
@@ -315,7 +319,7 @@ def main():
 
     w = W.WORKLOADS[args.workload]()
     stream = torch.cuda.Stream(device=dev)
-    plan = kde.Plan(w.M, w.lo, w.hi, w.H, precision=w.precision, tau=w.tau)
+    plan = kde.Plan(w.M, w.lo, w.hi, w.H, precision=w.precision, tau=w.tau, dft=args.dft)
     info = plan.info
     X_host = torch.from_numpy(np.ascontiguousarray(w.X)).pin_memory()
     X = X_host.to(dev)
@@ -462,6 +466,8 @@ def main():
                        "launch": "CUDA graph replay per step" if graph is not None else "stream launches",
                        "streams": "kernel grid on a side stream, concurrent with binning",
                        "binning": method,
+                       "first_pass": "split-TF32 DFT matrix on the tensor cores" if args.dft == "tc"
+                       else "mixed-radix FFT",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline, "path_roofline": path_roof, "kernels": kernels,
             "kernel_timing": "CUDA events around each kernel, over the same K steps launched "

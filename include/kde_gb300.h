@@ -71,7 +71,15 @@ enum { KDE_COLS_AUTO = 0, KDE_COLS_LINES = 1, KDE_COLS_SIMD = 2 };
  *               (by size), KDE_COLS_LINES (a thread group per column) or
  *               KDE_COLS_SIMD (16 columns side by side; used only where its
  *               shared-memory tile fits).  The result is the same up to
- *               rounding; this exists for testing and tuning. */
+ *               rounding; this exists for testing and tuning.
+ *   dft_tc      0: every transform is a mixed-radix FFT.  1 (KDE_F32 plans,
+ *               d >= 2): the first pass of kde_fft_eval and kde_power_spectrum
+ *               (each zero-padded row of counts -> its half spectrum, Eq. 10
+ *               along the last axis) is a dense DFT-matrix product on the
+ *               tensor cores in split TF32 (operands x = x_hi + x_lo, three
+ *               products hi*hi + hi*lo + lo*hi, FP32 accumulation), about 2^-21
+ *               relative per product; the plan then holds the DFT matrix
+ *               (2 x 4 x roundup(2Q, 64) x roundup(M_last, 32) bytes). */
 typedef struct {
   double tau;
   int precision;
@@ -79,6 +87,7 @@ typedef struct {
   int layout_mode;
   int64_t P_min[KDE_MAX_D];
   int cols_variant;
+  int dft_tc;
 } kde_opts;
 
 /* Everything the plan derives on the host, in FP64.

@@ -1137,6 +1137,16 @@ kde_status kernel_grid_impl(kde_plan_s* plan, int64_t n, void* Kspec, void* ws, 
                         "kde_cols_kgen_real_kernel", true);
 }
 
+// First pass: counts rows -> half spectra, by the FFT engine or (plans
+// with dft_tc) by the tensor-core DFT-matrix product.
+template <typename T>
+kde_status counts_rows(kde_plan_s* plan, const long long* cnt, int64_t rows, RowsParams<T>& rp,
+                       cudaStream_t st) {
+  if (plan->dft_tc && sizeof(T) == sizeof(float)) return dft_tc_rows(plan, cnt, rows, rp.out, st);
+  return launch_rows<T>(kde_rows_r2c_counts_kernel<T>, "kde_rows_r2c_counts_kernel", rows, rp, st,
+                        cnt);
+}
+
 template <typename T>
 kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Kspec, void* density,
                          void* ws, cudaStream_t st) {
@@ -1167,8 +1177,7 @@ kde_status fft_eval_impl(kde_plan_s* plan, const int64_t* counts, const void* Ks
   rp.out = A;
   rp.lp = line_plan(I, dl);
   rp.tw = twiddles<T>(plan, dl);
-  kde_status s = launch_rows<T>(kde_rows_r2c_counts_kernel<T>, "kde_rows_r2c_counts_kernel", rows,
-                                rp, st, cnt);
+  kde_status s = counts_rows<T>(plan, cnt, rows, rp, st);
   if (s != KDE_OK) return s;
   if (d == 2) {
     ColsParams<T> cp{};
@@ -1262,8 +1271,7 @@ kde_status power_spectrum_impl(kde_plan_s* plan, const int64_t* counts, void* Wo
   rp.out = A;
   rp.lp = line_plan(I, dl);
   rp.tw = twiddles<T>(plan, dl);
-  kde_status s = launch_rows<T>(kde_rows_r2c_counts_kernel<T>, "kde_rows_r2c_counts_kernel", rows,
-                                rp, st, cnt);
+  kde_status s = counts_rows<T>(plan, cnt, rows, rp, st);
   if (s != KDE_OK) return s;
   if (d == 1) {
     LaunchScope ls("kde_power1d_kernel", st);

@@ -23,6 +23,13 @@ struct kde_plan_s {
   // plan's precision (float2 or double2), owned by the plan.
   void* tw_dev;
   size_t tw_offset[KDE_MAX_D];  // byte offset of axis k's table in tw_dev
+  // Tensor-core DFT of the first pass (opts.dft_tc): the real DFT matrix of
+  // the last axis restricted to its M_last data points, split into TF32
+  // high and low parts, each dft_N x dft_K floats (rows 2q, 2q+1 = cos,
+  // -sin of 2 pi q x / P; zero beyond 2Q and M_last).
+  int dft_tc;
+  float* dft_tab;
+  int dft_N, dft_K, dft_BN;
 };
 
 namespace kde {
@@ -31,6 +38,11 @@ kde_status fail(kde_status s, const std::string& msg);
 kde_status matrix_support(const kde_plan_s* plan, const double* A, double* Ainv, double* detA,
                           int64_t* L);
 kde_status cuda_fail(cudaError_t e, const char* what);
+// Tensor-core first pass (dft_tc.cu): build the plan's DFT matrix; run the
+// counts rows -> half spectra pass (rows of length M_last, out [rows][Q]).
+kde_status dft_tc_setup(kde_plan_s* plan);
+kde_status dft_tc_rows(const kde_plan_s* plan, const long long* counts, int64_t rows, void* out,
+                       cudaStream_t st);
 
 // Launch bookkeeping: counts launches and, when profiling is on, records a
 // pair of events around each launch on its stream.

@@ -339,6 +339,11 @@ kde_status kde_plan_create(int d, const int64_t* M, const double* lo, const doub
   p->range_mode = opts ? opts->range_mode : KDE_RANGE_CORRECTED;
   p->layout_mode = opts ? opts->layout_mode : KDE_LAYOUT_CORRECTED;
   p->cols_variant = opts ? opts->cols_variant : KDE_COLS_AUTO;
+  p->dft_tc = opts ? opts->dft_tc : 0;
+  if (p->dft_tc && (p->info.precision != KDE_F32 || d < 2)) {
+    delete p;
+    return fail(KDE_ERR_UNSUPPORTED, "dft_tc needs a KDE_F32 plan with d >= 2");
+  }
   cudaError_t e = cudaGetDevice(&p->device);
   if (e != cudaSuccess) {
     delete p;
@@ -373,6 +378,14 @@ kde_status kde_plan_create(int d, const int64_t* M, const double* lo, const doub
     delete p;
     return cuda_fail(e, "twiddle generation");
   }
+  if (p->dft_tc) {
+    st = dft_tc_setup(p);
+    if (st != KDE_OK) {
+      cudaFree(p->tw_dev);
+      delete p;
+      return st;
+    }
+  }
   *out = p;
   return KDE_OK;
 }
@@ -387,6 +400,7 @@ kde_status kde_plan_destroy(kde_plan plan) {
   if (!plan) return KDE_OK;
   cudaError_t e = cudaSuccess;
   if (plan->tw_dev) e = cudaFree(plan->tw_dev);
+  if (plan->dft_tab) cudaFree(plan->dft_tab);
   delete plan;
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, "cudaFree(twiddles)");
 }

@@ -34,7 +34,8 @@ class KDEError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("precision", ctypes.c_int),
                 ("range_mode", ctypes.c_int), ("layout_mode", ctypes.c_int),
-                ("P_min", ctypes.c_int64 * MAX_D), ("cols_variant", ctypes.c_int)]
+                ("P_min", ctypes.c_int64 * MAX_D), ("cols_variant", ctypes.c_int),
+                ("dft_tc", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -163,9 +164,10 @@ COLS_VARIANTS = {"auto": 0, "lines": 1, "simd": 2}
 
 
 def _opts(tau=3.7, precision="f32", range_mode="corrected", layout="corrected", P_min=None,
-          cols="auto"):
+          cols="auto", dft="fft"):
     o = Opts()
     o.cols_variant = COLS_VARIANTS[cols]
+    o.dft_tc = {"fft": 0, "tc": 1}[dft]
     o.tau = tau
     o.precision = F32 if precision == "f32" else F64
     o.range_mode = RANGE_CORRECTED if range_mode == "corrected" else RANGE_PER_AXIS
