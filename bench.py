@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--bin-method", default="auto", choices=["auto", "direct", "tiled"])
     ap.add_argument("--dft", default="fft", choices=["fft", "tc"],
                     help="first pass: mixed-radix FFT, or split-TF32 DFT matrix on the tensor cores")
+    ap.add_argument("--lscv", default="autocorr", choices=["autocorr", "spectrum"],
+                    help="lscv2d_512_f32: pair sums from the counts' autocorrelation, or from "
+                         "the count spectrum against per-candidate kernel spectra")
     ap.add_argument("--train-sets", type=int, default=20_000,
                     help="learned2d_256: training datasets labelled by the plain search")
     return ap.parse_args()
@@ -106,6 +109,13 @@ def job_throughput(world, units_per_rank, ms_step):
 # FP32 ALU roofline: 152 SMs x 128 FP32 lanes x 2 flops (FMA) at the SM clock.
 def fp32_peak_tflops(sm_mhz=2070.0, sms=152):
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def ac_flops(L):
+    """Lag terms of the half-plane autocorrelation sum of one matrix with
+    support L (rows 0..L_0, all 2 L_1 + 1 columns), 13 flops each: the
+    quadratic form (8), exp (1), scale (1), weight x R and accumulate (3)."""
+    return 13.0 * (L[0] + 1) * (2 * L[1] + 1)
 
 
 def fft_flops(n_lines, N):
@@ -628,10 +638,19 @@ def lscv_main(args):
     pair = torch.empty(2 * len(w.H), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    R = torch.empty(info.P[0], info.P[1], dtype=plan.real_dtype(), device=dev)
+    acws = torch.empty(kde.kde_lscv_autocorr_workspace_bytes(plan), dtype=torch.uint8, device=dev)
+
     def step():
         kde.kde_bin(X, w.lo, w.hi, w.M, counts=counts, method="direct", stream=stream)
-        kde.kde_power_spectrum(plan, counts, W=Wsp, workspace=ws, stream=stream)
-        kde.kde_lscv(plan, w.n, w.H, Wsp, lscv=scores, pair_sums=pair, workspace=lws, stream=stream)
+        if args.lscv == "spectrum":
+            kde.kde_power_spectrum(plan, counts, W=Wsp, workspace=ws, stream=stream)
+            kde.kde_lscv(plan, w.n, w.H, Wsp, lscv=scores, pair_sums=pair, workspace=lws,
+                         stream=stream)
+        else:
+            kde.kde_autocorrelation(plan, counts, R=R, workspace=acws, stream=stream)
+            kde.kde_lscv_autocorr(plan, w.n, w.H, R, lscv=scores, pair_sums=pair, workspace=acws,
+                                  stream=stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -664,11 +683,13 @@ def lscv_main(args):
     # FFT flops (5 N log2 N per complex line) of the batched kernel-spectrum
     # passes, per launch: every chunk holds 64 matrices (H_i and 2 H_i).
     P0, P1, Q = info.P[0], info.P[1], info.Q
-    Ls = [kde.kde_plan_info_compute(w.M, w.lo, w.hi, A, precision=w.precision, tau=w.tau).L[0]
+    Ls = [kde.kde_plan_info_compute(w.M, w.lo, w.hi, A, precision=w.precision, tau=w.tau).L
           for h in w.H for A in (h, 2 * h)]
-    nlaunch = max(1, prof.get("kde_cols_kgen_dot_kernel", (0, 1))[1] // args.steps)
-    flops = {"kde_rows_kgen_batch_kernel": sum(fft_flops((2 * L0 + 2) // 2, P1) for L0 in Ls) / nlaunch,
-             "kde_cols_kgen_dot_kernel": len(Ls) * (fft_flops((Q + 1) // 2, P0) + 2.0 * P0 * Q) / nlaunch}
+    nlaunch = max(1, max(prof.get("kde_cols_kgen_dot_kernel", (0, 1))[1],
+                         prof.get("kde_lscv_ac_kernel", (0, 1))[1]) // args.steps)
+    flops = {"kde_rows_kgen_batch_kernel": sum(fft_flops(L[0] + 1, P1) for L in Ls) / nlaunch,
+             "kde_cols_kgen_dot_kernel": len(Ls) * (fft_flops((Q + 1) // 2, P0) + 2.0 * P0 * Q) / nlaunch,
+             "kde_lscv_ac_kernel": sum(ac_flops(L) for L in Ls) / nlaunch}
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
     sm_max = clocks.get("sm_max_mhz") or 2070.0
@@ -677,13 +698,16 @@ def lscv_main(args):
     roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x SM max clock",
                 "traffic": None, "flops_per_launch": flops.get(dom, 0.0),
-                "flop_model": "5 N log2 N per complex FFT line + 2 per dot-product term"}
+                "flop_model": "5 N log2 N per complex FFT line + 2 per dot-product term; "
+                              "13 per lag term of the autocorrelation sum (exp counted as 1)"}
     line = {"metric": LSCV_METRIC, "value": value, "unit": "candidates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": info.precision, "data": "synthetic",
             "config": {"workload": w.name, "d": w.d, "n": w.n, "grid": list(w.M),
                        "candidates": len(w.H), "P": list(info.P),
+                       "pair_sums": "counts' autocorrelation" if args.lscv == "autocorr"
+                       else "count spectrum x per-candidate kernel spectra",
                        "l2": "flushed between timed steps (256 MB write)"},
             "roofline": roofline, "kernels": kernels, "gpu_launches": launches, "clocks": clocks}
     if not args.no_cpu_baseline:
@@ -838,10 +862,9 @@ def learned_main(args):
     # roofline of the selection loop's dominant kernel
     info = sc.plan.info
     P0, P1, Q = info.P[0], info.P[1], info.Q
-    Ls = [kde.kde_plan_info_compute(sc.M, sc.lo, sc.hi, A, precision="f32").L[0]
+    Ls = [kde.kde_plan_info_compute(sc.M, sc.lo, sc.hi, A, precision="f32").L
           for h in scored for A in (h, 2.0 * h)]
-    flops = {"kde_rows_kgen_batch_kernel": sum(fft_flops(L0 + 1, P1) for L0 in Ls),
-             "kde_cols_kgen_dot_kernel": len(Ls) * (fft_flops((Q + 1) // 2, P0) + 2.0 * P0 * Q),
+    flops = {"kde_lscv_ac_kernel": sum(ac_flops(L) for L in Ls),
              "kde_gemm_tc_kernel": K * 2.0 * 128 * (din * hid + hid * hid + hid * 16)}
     dom = max(prof, key=lambda k: prof[k][0])
     sm_max = clocks.get("sm_max_mhz") or 2070.0

@@ -216,6 +216,28 @@ kde_status kde_lscv(kde_plan plan, int64_t n, int nH, const double* H, const voi
                     kde_stream_t stream);
 kde_status kde_lscv_workspace_bytes(kde_plan plan, size_t* bytes);
 
+/* The same criterion from the counts' autocorrelation (d = 2).  The binned
+ * pair sum is S(A) = sum_j c_j sum_{|l| <= L(A)} c_{j-l} K_A(delta o l)
+ * = sum_{|l| <= L(A)} K_A(delta o l) R(l) with R(l) = sum_j c_j c_{j-l}, the
+ * autocorrelation of the counts (sample units), which the FFT gives once per
+ * grid: R = F^{-1}(|F(c)|^2) on the plan's padding (Eq. 10 with the kernel
+ * replaced by the counts; P_k >= M_k + L_k makes the cyclic sum the linear
+ * one for every lag of the support).  Each candidate then costs one weighted
+ * sum over its support (half of it: K_A and R are even) and no transform.
+ *   kde_autocorrelation: R (device, P_0 x P_1 values of the plan's
+ *     precision, lag (l_0, l_1) at (l_0 mod P_0, l_1 mod P_1)) from counts.
+ *   kde_lscv_autocorr: as kde_lscv, with R in place of W.
+ * Both take a workspace of at least kde_lscv_autocorr_workspace_bytes,
+ * 256-byte aligned.  kde_lscv_autocorr copies the candidates' kernel
+ * parameters (host-prepared, FP64 factorisations) into the workspace with
+ * host-to-device copies on the stream, up to 1024 candidates per launch. */
+kde_status kde_lscv_autocorr_workspace_bytes(kde_plan plan, size_t* bytes);
+kde_status kde_autocorrelation(kde_plan plan, const int64_t* counts, void* R, void* workspace,
+                               size_t workspace_bytes, kde_stream_t stream);
+kde_status kde_lscv_autocorr(kde_plan plan, int64_t n, int nH, const double* H, const void* R,
+                             double* pair_sums, double* lscv, void* workspace,
+                             size_t workspace_bytes, kde_stream_t stream);
+
 /* Ragged batches of independent 2-D problems (each with its own samples,
  * grid and bandwidth; Sec. 2 for each).  The batch runs as seven launches:
  * a memset and one persistent grid-stride kernel per pass (binning, kernel

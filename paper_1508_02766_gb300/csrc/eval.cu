@@ -359,7 +359,7 @@ kde_line1d_kernel(const long long* __restrict__ counts, const T* __restrict__ K,
 }
 
 enum ColMode { COL_FWD = 0, COL_FWD_REAL = 1, COL_MID = 2, COL_INV = 3, COL_FWD_POWER = 4,
-               COL_FWD_DOT = 5 };
+               COL_FWD_DOT = 5, COL_AUTO = 6 };
 
 template <typename T>
 struct ColsParams {
@@ -380,6 +380,9 @@ struct ColsParams {
   int Qw, Plw;
   const T* W;
   double* partial;
+  // COL_AUTO: z <- |s_pre z|^2 s_post between the forward and inverse
+  // transforms (the counts' power spectrum, for their autocorrelation).
+  T s_pre, s_post;
 };
 
 __device__ __forceinline__ int half_weight(int64_t s, int Q, int Plast) {
@@ -541,6 +544,15 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
           const int k = k0 + u * g.tpl;
           if (k < P) z[k] = mk<V>(z[k].x * kv[u], z[k].y * kv[u]);
         }
+      }
+      g.sync();
+      V* other = (z == a) ? b : a;
+      z = line_fft<V, true>(z, other, p.lp, tw_s, g);
+    }
+    if (MODE == COL_AUTO) {
+      for (int k = g.lt; k < P; k += g.tpl) {
+        const T re = z[k].x * p.s_pre, im = z[k].y * p.s_pre;
+        z[k] = mk<V>((re * re + im * im) * p.s_post, T(0));
       }
       g.sync();
       V* other = (z == a) ? b : a;
@@ -757,6 +769,16 @@ __device__ __forceinline__ void cols_simd_body_slab(const ColsParams<T>& p, int6
     V* other = (z == bufA) ? bufB : bufA;
     z = simd_fft<V, true>(z, other, p.lp, tw_s, c, g, ng);
   }
+  if (MODE == COL_AUTO) {
+    for (int pos = g; pos < P; pos += ng) {
+      const V v = z[pos * kSimdW + c];
+      const T re = v.x * p.s_pre, im = v.y * p.s_pre;
+      z[pos * kSimdW + c] = mk<V>((re * re + im * im) * p.s_post, T(0));
+    }
+    __syncthreads();
+    V* other = (z == bufA) ? bufB : bufA;
+    z = simd_fft<V, true>(z, other, p.lp, tw_s, c, g, ng);
+  }
   if (!col_ok) return;
   if (MODE == COL_FWD_POWER) {
     const T w = (T)half_weight(s, p.Qw, p.Plw);
@@ -812,6 +834,15 @@ __global__ void __launch_bounds__(256) kde_cols_power_kernel(ColsParams<T> p) {
   else
     cols_body<T, COL_FWD_POWER>(p);
 }
+template <typename T, bool SIMD>
+__global__ void __launch_bounds__(256) kde_cols_auto_kernel(ColsParams<T> p) {
+  if (SIMD)
+    cols_simd_body<T, COL_AUTO>(p);
+  else
+    cols_body<T, COL_AUTO>(p);
+}
+
+
 
 // Batched kernel spectra (Eq. 6 and Eq. 10 for many matrices at once): one
 // chunk holds up to kBatch matrices; blockIdx.y picks the matrix.
@@ -911,6 +942,73 @@ __global__ void __launch_bounds__(32) kde_lscv_reduce_kernel(LscvReduce r, const
       S_out[2 * i + 1] = s[1];
     }
     lscv_out[i] = s[1] / (r.n * r.n) - 2.0 * (s[0] - r.n * r.K0[i]) / (r.n * (r.n - 1.0));
+  }
+}
+
+// Binned pair sums from the counts' autocorrelation R (P_0 x P_1, lag
+// (l_0, l_1) at (l_0 mod P_0, l_1 mod P_1)):
+//   S(A) = sum_{|l_k| <= L_k} K_A(delta o l) R(l).
+// K_A and R are even, so the sum runs over the half plane l_0 > 0, or
+// l_0 = 0 and l_1 > 0, twice, plus the lag 0 once.  Block (x, b) takes lag
+// rows x rpb .. x rpb + rpb - 1 of matrix b and writes one FP64 partial.
+// One block covers a whole support (rpb = the largest L_0 + 1 of the
+// launch): small supports would otherwise leave most blocks empty.
+constexpr int kAcRows = 4;  // row granularity the workspace is sized for
+
+// Up to kAcChunk candidates (2 kAcChunk matrices) per launch; their kernel
+// parameters are uploaded to the workspace.
+constexpr int kAcChunk = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(256) kde_lscv_ac_kernel(const KGen<T>* __restrict__ gens,
+                                                          const T* __restrict__ R, int P1, int rpb,
+                                                          double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  __shared__ KGen<T> gen;
+  if (threadIdx.x == 0) gen = gens[b];
+  __syncthreads();
+  const int L0 = gen.L[0], L1 = gen.L[1];
+  const int r0 = blockIdx.x * rpb;
+  T acc = 0;
+  if (r0 <= L0) {
+    const int r1 = min(L0, r0 + rpb - 1);
+    const int W1 = 2 * L1 + 1;
+    const int total = (r1 - r0 + 1) * W1;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int dr = t / W1;
+      const int l0 = r0 + dr, l1 = t - dr * W1 - L1;
+      if (l0 == 0 && l1 < 0) continue;
+      const T w = (l0 == 0 && l1 == 0) ? T(1) : T(2);
+      const int l[KDE_MAX_D] = {l0, l1, 0};
+      acc += w * kernel_value<T>(gen, l) * __ldg(R + (size_t)l0 * P1 + (l1 < 0 ? l1 + P1 : l1));
+    }
+  }
+  block_sum_to((double)acc, partial + (size_t)b * gridDim.x + blockIdx.x);
+}
+
+// As kde_lscv_reduce_kernel with K_{H_i}(0) read from memory and scale 1.
+__global__ void __launch_bounds__(32) kde_lscv_ac_reduce_kernel(int nparts, double n,
+                                                                const double* __restrict__ K0,
+                                                                const double* __restrict__ partial,
+                                                                double* __restrict__ S_out,
+                                                                double* __restrict__ lscv_out) {
+  const int i = blockIdx.x;
+  double s[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const double* pp = partial + (int64_t)(2 * i + h) * nparts;
+    double v = 0.0;
+    for (int j = threadIdx.x; j < nparts; j += 32) v += pp[j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    s[h] = __shfl_sync(0xffffffffu, v, 0);
+  }
+  if (threadIdx.x == 0) {
+    if (S_out) {
+      S_out[2 * i] = s[0];
+      S_out[2 * i + 1] = s[1];
+    }
+    lscv_out[i] = s[1] / (n * n) - 2.0 * (s[0] - n * K0[i]) / (n * (n - 1.0));
   }
 }
 
@@ -1452,6 +1550,120 @@ kde_status lscv_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, cons
   return KDE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// LSCV from the counts' autocorrelation (d = 2): R = F^{-1}|F(c)|^2 once per
+// grid, then S(A) = sum over the support of K_A(delta o l) R(l) for every
+// candidate -- no transform per candidate.
+// ---------------------------------------------------------------------------
+// Workspace: the autocorrelation's spectra, or (lag sums) the uploaded
+// kernel parameters, K_H(0) and the FP64 partials of one chunk.
+size_t ac_param_bytes() { return ((size_t)2 * kAcChunk * sizeof(KGen<double>) + 255) & ~(size_t)255; }
+size_t ac_k0_bytes() { return ((size_t)kAcChunk * sizeof(double) + 255) & ~(size_t)255; }
+
+size_t ac_workspace(const kde_plan_info& I) {
+  const size_t cb = (I.precision == KDE_F32) ? 8 : 16;
+  const size_t spec = ((size_t)(I.M[0] + I.P[0]) * I.Q * cb + 255) & ~(size_t)255;
+  const size_t parts = (size_t)2 * kAcChunk * (size_t)((I.P[0] + kAcRows - 1) / kAcRows + 1) *
+                       sizeof(double);
+  return std::max(spec, ac_param_bytes() + ac_k0_bytes() + parts);
+}
+
+template <typename T>
+kde_status autocorr_impl(kde_plan_s* plan, const int64_t* counts, void* Rout, void* ws,
+                         cudaStream_t st) {
+  using V = typename Cplx<T>::type;
+  const kde_plan_info& I = plan->info;
+  V* A = (V*)ws;              // [M_0][Q] half spectra of the counts rows
+  V* B = A + I.M[0] * I.Q;    // [P_0][Q] after the axis-0 round trip
+  RowsParams<T> rp{};
+  rp.nrows = I.M[0];
+  rp.Min = (int)I.M[1];
+  rp.in_stride = I.M[1];
+  rp.Q = (int)I.Q;
+  rp.out = A;
+  rp.lp = line_plan(I, 1);
+  rp.tw = twiddles<T>(plan, 1);
+  kde_status s = counts_rows<T>(plan, reinterpret_cast<const long long*>(counts), I.M[0], rp, st);
+  if (s != KDE_OK) return s;
+  ColsParams<T> cp{};
+  cp.in = A;
+  cp.out = B;
+  cp.S = I.Q;
+  cp.Nin = (int)I.M[0];
+  cp.Nout = (int)I.P[0];
+  cp.Lw = -1;
+  cp.lp = line_plan(I, 0);
+  cp.tw = twiddles<T>(plan, 0);
+  // counts are in units of 2^-32; the inverse transforms are unnormalised
+  cp.s_pre = (T)2.3283064365386963e-10;
+  cp.s_post = (T)(1.0 / ((double)I.P[0] * (double)I.P[1]));
+  s = launch_cols<T>(KDE_COLS(kde_cols_auto_kernel), cp, 1, plan->cols_variant, st,
+                     "kde_cols_auto_kernel");
+  if (s != KDE_OK) return s;
+  C2RParams<T> cr{};
+  cr.in = B;
+  cr.out = (T*)Rout;
+  cr.nrows = I.P[0];
+  cr.Mout = (int)I.P[1];
+  cr.Q = (int)I.Q;
+  cr.lp = line_plan(I, 1);
+  cr.tw = twiddles<T>(plan, 1);
+  return launch_rows<T>(kde_rows_c2r_kernel<T>, "kde_rows_c2r_kernel", I.P[0], cr, st);
+}
+
+template <typename T>
+kde_status lscv_ac_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, const void* R,
+                        double* S_out, double* lscv_out, void* ws, cudaStream_t st) {
+  const kde_plan_info& I = plan->info;
+  const int d = I.d;
+  KGen<T>* gens_dev = (KGen<T>*)ws;
+  double* K0_dev = (double*)((char*)ws + ac_param_bytes());
+  double* partial = (double*)((char*)ws + ac_param_bytes() + ac_k0_bytes());
+  std::vector<KGen<T>> gens;
+  std::vector<double> K0;
+  for (int h0 = 0; h0 < nH; h0 += kAcChunk) {
+    const int nh = std::min(kAcChunk, nH - h0);
+    gens.assign(2 * nh, KGen<T>{});
+    K0.assign(nh, 0.0);
+    int64_t max_rows = 1;
+    for (int i = 0; i < nh; ++i) {
+      const double* H = Hs + (size_t)(h0 + i) * d * d;
+      for (int h = 0; h < 2; ++h) {
+        double A[9], Ainv[9], detA;
+        int64_t L[KDE_MAX_D];
+        for (int e = 0; e < d * d; ++e) A[e] = (h ? 2.0 : 1.0) * H[e];
+        kde_status st2 = kde::matrix_support(plan, A, Ainv, &detA, L);
+        if (st2 != KDE_OK) return st2;
+        gens[2 * i + h] = kgen_for<T>(I, Ainv, detA, L, plan->layout_mode == KDE_LAYOUT_WAND);
+        max_rows = std::max<int64_t>(max_rows, L[0] + 1);
+        if (h == 0) K0[i] = std::pow(6.283185307179586476925287, -0.5 * d) / std::sqrt(detA);
+      }
+    }
+    // pageable sources: the copies are staged before these calls return
+    cudaError_t e = cudaMemcpyAsync(gens_dev, gens.data(), gens.size() * sizeof(KGen<T>),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(K0_dev, K0.data(), K0.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(kernel parameters)");
+    const int gx = 1;
+    {
+      LaunchScope ls("kde_lscv_ac_kernel", st);
+      kde_lscv_ac_kernel<T><<<dim3((unsigned)gx, (unsigned)(2 * nh)), 256, 0, st>>>(
+          gens_dev, (const T*)R, (int)I.P[1], (int)max_rows, partial);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_kernel");
+    }
+    {
+      LaunchScope ls("kde_lscv_reduce_kernel", st);
+      kde_lscv_ac_reduce_kernel<<<nh, 32, 0, st>>>(gx, (double)n, K0_dev, partial,
+                                                   S_out ? S_out + 2 * h0 : nullptr, lscv_out + h0);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_reduce_kernel");
+    }
+  }
+  return KDE_OK;
+}
+
 kde_status check_ws(const kde_plan_s* plan, void* ws, size_t bytes) {
   if (plan->info.workspace_bytes == 0) return KDE_OK;
   if (!ws) return fail(KDE_ERR_WORKSPACE, "workspace is NULL");
@@ -1590,6 +1802,48 @@ extern "C" kde_status kde_lscv(kde_plan plan, int64_t n, int nH, const double* H
   if (plan->info.precision == KDE_F32)
     return lscv_impl<float>(plan, n, nH, H, W, pair_sums, lscv, workspace, st);
   return lscv_impl<double>(plan, n, nH, H, W, pair_sums, lscv, workspace, st);
+}
+
+extern "C" kde_status kde_lscv_autocorr_workspace_bytes(kde_plan plan, size_t* bytes) {
+  if (!plan || !bytes) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (plan->info.d != 2) return fail(KDE_ERR_UNSUPPORTED, "autocorrelation LSCV supports d = 2");
+  *bytes = ac_workspace(plan->info);
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_autocorrelation(kde_plan plan, const int64_t* counts, void* R,
+                                          void* workspace, size_t workspace_bytes,
+                                          kde_stream_t stream) {
+  if (!plan || !counts || !R) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (plan->info.d != 2) return fail(KDE_ERR_UNSUPPORTED, "autocorrelation LSCV supports d = 2");
+  if (!workspace || workspace_bytes < ac_workspace(plan->info))
+    return fail(KDE_ERR_WORKSPACE, "workspace smaller than kde_lscv_autocorr_workspace_bytes");
+  if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  kde_status s = check_device(plan);
+  if (s != KDE_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->info.precision == KDE_F32) return autocorr_impl<float>(plan, counts, R, workspace, st);
+  return autocorr_impl<double>(plan, counts, R, workspace, st);
+}
+
+extern "C" kde_status kde_lscv_autocorr(kde_plan plan, int64_t n, int nH, const double* H,
+                                        const void* R, double* pair_sums, double* lscv,
+                                        void* workspace, size_t workspace_bytes,
+                                        kde_stream_t stream) {
+  if (!plan || !H || !R || !lscv) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (plan->info.d != 2) return fail(KDE_ERR_UNSUPPORTED, "autocorrelation LSCV supports d = 2");
+  if (n < 2) return fail(KDE_ERR_INVALID_ARG, "LSCV needs n >= 2");
+  if (nH < 0) return fail(KDE_ERR_INVALID_ARG, "nH < 0");
+  if (nH == 0) return KDE_OK;
+  if (!workspace || workspace_bytes < ac_workspace(plan->info))
+    return fail(KDE_ERR_WORKSPACE, "workspace smaller than kde_lscv_autocorr_workspace_bytes");
+  if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  kde_status s = check_device(plan);
+  if (s != KDE_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->info.precision == KDE_F32)
+    return lscv_ac_impl<float>(plan, n, nH, H, R, pair_sums, lscv, workspace, st);
+  return lscv_ac_impl<double>(plan, n, nH, H, R, pair_sums, lscv, workspace, st);
 }
 
 // ---------------------------------------------------------------------------

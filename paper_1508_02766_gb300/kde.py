@@ -64,7 +64,8 @@ EXPORTS = [
     "kde_batch_plan_destroy", "kde_standardize2", "kde_features2", "kde_mlp_create",
     "kde_mlp_destroy", "kde_mlp_param_count", "kde_mlp_get_params", "kde_mlp_set_params",
     "kde_mlp_get_state", "kde_mlp_set_state", "kde_mlp_forward", "kde_mlp_loss_grad",
-    "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16",
+    "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16", "kde_autocorrelation",
+    "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes",
 ]
 FEAT_DIM = 1088
 
@@ -105,6 +106,9 @@ def lib():
                                  ctypes.POINTER(ctypes.c_float)]
     L.kde_batch_eval.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.kde_batch_plan_destroy.argtypes = [vp]
+    L.kde_lscv_autocorr_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.kde_autocorrelation.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.kde_lscv_autocorr.argtypes = [vp, i64, ctypes.c_int, dp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     fp = ctypes.POINTER(ctypes.c_float)
     L.kde_standardize2.argtypes = [vp, i64, vp, vp, vp]
     L.kde_features2.argtypes = [vp, ctypes.c_int, i64, vp, vp, vp]
@@ -139,7 +143,8 @@ def lib():
                  "kde_mlp_create", "kde_mlp_destroy", "kde_mlp_param_count",
                  "kde_mlp_get_params", "kde_mlp_set_params", "kde_mlp_get_state",
                  "kde_mlp_set_state", "kde_mlp_forward", "kde_mlp_loss_grad",
-                 "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16"):
+                 "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16",
+                 "kde_autocorrelation", "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -358,10 +363,48 @@ def kde_lscv(plan: Plan, n, H, W, lscv=None, pair_sums=None, workspace=None, str
     if workspace is None:
         workspace = torch.empty(max(256, kde_lscv_workspace_bytes(plan)), dtype=torch.uint8,
                                 device="cuda")
-    Hc = (ctypes.c_double * H.size)(*[float(v) for v in H.ravel()])
+    Hc = H.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     _check(lib().kde_lscv(plan.handle, int(n), nH, Hc, _ptr(W), _ptr(pair_sums), _ptr(lscv),
                           _ptr(workspace), workspace.numel() * workspace.element_size(),
                           _stream_ptr(stream)))
+    return lscv
+
+
+def kde_lscv_autocorr_workspace_bytes(plan: Plan) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().kde_lscv_autocorr_workspace_bytes(plan.handle, ctypes.byref(b)))
+    return int(b.value)
+
+
+def kde_autocorrelation(plan: Plan, counts, R=None, workspace=None, stream=None):
+    """R = F^{-1}|F(c)|^2 on the plan's padding (P_0 x P_1, sample units)."""
+    import torch
+    if R is None:
+        R = torch.empty(plan.info.P[0], plan.info.P[1], dtype=plan.real_dtype(), device="cuda")
+    if workspace is None:
+        workspace = torch.empty(kde_lscv_autocorr_workspace_bytes(plan), dtype=torch.uint8,
+                                device="cuda")
+    _check(lib().kde_autocorrelation(plan.handle, _ptr(counts), _ptr(R), _ptr(workspace),
+                                     workspace.numel() * workspace.element_size(),
+                                     _stream_ptr(stream)))
+    return R
+
+
+def kde_lscv_autocorr(plan: Plan, n, H, R, lscv=None, pair_sums=None, workspace=None, stream=None):
+    """LSCV(H_i) from the counts' autocorrelation (host array nH x 2 x 2)."""
+    import torch
+    H = np.ascontiguousarray(np.asarray(H, dtype=np.float64))
+    nH = H.shape[0]
+    if lscv is None:
+        lscv = torch.empty(nH, dtype=torch.float64, device="cuda")
+    if workspace is None:
+        workspace = torch.empty(kde_lscv_autocorr_workspace_bytes(plan), dtype=torch.uint8,
+                                device="cuda")
+    Hc = H.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    _check(lib().kde_lscv_autocorr(plan.handle, int(n), nH, Hc, _ptr(R), _ptr(pair_sums),
+                                   _ptr(lscv), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(),
+                                   _stream_ptr(stream)))
     return lscv
 
 

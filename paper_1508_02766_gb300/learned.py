@@ -1,7 +1,7 @@
 """Learned bandwidth proposal on top of the binned FFT LSCV search.
 
 Orchestration only: every numerical step (standardisation, binning, features,
-count spectrum, LSCV of every candidate, the network's forward and backward
+the counts' autocorrelation, LSCV of every candidate, the network's forward and backward
 passes, Adam) runs in the CUDA library through ``kde``; this module picks
 which calls to make, holds the candidate grid and keeps the buffers.
 
@@ -60,8 +60,8 @@ def neighbourhood(theta, scale=0.5):
 
 class LscvScorer:
     """One shared plan for the standardised grid and the buffers of one
-    dataset at a time: standardise, bin, features, count spectrum, then the
-    LSCV of any list of candidates."""
+    dataset at a time: standardise, bin, features, the counts'
+    autocorrelation, then the LSCV of any list of candidates."""
 
     def __init__(self, n_max, device="cuda", tau=3.7):
         import torch
@@ -82,9 +82,8 @@ class LscvScorer:
         self.Z = torch.empty(n_max, 2, dtype=torch.float32, device=self.device)
         self.mom = torch.empty(8, dtype=torch.float64, device=self.device)
         self.feat = torch.empty(kde.FEAT_DIM, dtype=torch.float32, device=self.device)
-        self.W = torch.empty(info.kspec_elems, dtype=torch.float32, device=self.device)
-        self.ws = self.plan.workspace(self.device)
-        self.lws = torch.empty(max(256, kde.kde_lscv_workspace_bytes(self.plan)), dtype=torch.uint8,
+        self.R = torch.empty(info.P[0], info.P[1], dtype=torch.float32, device=self.device)
+        self.lws = torch.empty(kde.kde_lscv_autocorr_workspace_bytes(self.plan), dtype=torch.uint8,
                                device=self.device)
         self.n = 0
         self.cand = cand
@@ -97,7 +96,7 @@ class LscvScorer:
         kde.kde_standardize2(X, Z=Z, moments=self.mom)
         kde.kde_bin(Z, self.lo, self.hi, self.M, counts=self.counts, method="direct")
         kde.kde_features2(self.counts, n, self.mom, feat=self.feat)
-        kde.kde_power_spectrum(self.plan, self.counts, W=self.W, workspace=self.ws)
+        kde.kde_autocorrelation(self.plan, self.counts, R=self.R, workspace=self.lws)
         self.n = n
         return self.feat
 
@@ -105,8 +104,8 @@ class LscvScorer:
         """LSCV of every H (k x 2 x 2, standardised coordinates), on the GPU."""
         torch = self.torch
         out = torch.empty(len(H), dtype=torch.float64, device=self.device)
-        kde.kde_lscv(self.plan, self.n, np.asarray(H, dtype=np.float64), self.W, lscv=out,
-                     workspace=self.lws)
+        kde.kde_lscv_autocorr(self.plan, self.n, np.asarray(H, dtype=np.float64), self.R,
+                              lscv=out, workspace=self.lws)
         return out
 
     def search(self):

@@ -126,9 +126,9 @@ def test_training_reduces_loss_and_checkpoint_resumes():
 
 
 def test_scorer_pair_sums_match_oracle():
-    """The scorer's wiring (standardise, bin, count spectrum, kernel spectra
-    on the shared plan): pair sums S(H), S(2H) of a few candidates against
-    the oracle's spectral pair sums at the plan's padding."""
+    """The scorer's wiring (standardise, bin, the counts' autocorrelation on
+    the shared plan): pair sums S(H), S(2H) of a few candidates against the
+    oracle's spectral pair sums at the plan's padding."""
     n = 2000
     X = W.mixture_datasets(5, 1, n=n)[0]
     sc = Lm.LscvScorer(n)
@@ -136,7 +136,7 @@ def test_scorer_pair_sums_match_oracle():
     idx = [0, 300, 1007]
     H = sc.cand_H[idx]
     pair = torch.empty(2 * len(idx), dtype=torch.float64, device=DEV)
-    kde.kde_lscv(sc.plan, n, H, sc.W, pair_sums=pair, workspace=sc.lws)
+    kde.kde_lscv_autocorr(sc.plan, n, H, sc.R, pair_sums=pair, workspace=sc.lws)
     got = pair.cpu().numpy()
     c = O.counts_to_c(sc.counts.cpu().numpy())
     lo, hi, M = np.array([Lm.GRID_LO] * 2), np.array([Lm.GRID_HI] * 2), (Lm.GRID_M, Lm.GRID_M)

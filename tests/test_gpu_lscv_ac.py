@@ -1,0 +1,135 @@
+"""LSCV from the counts' autocorrelation (kde_autocorrelation +
+kde_lscv_autocorr) against the FP64 oracle: the autocorrelation itself by
+brute force, every pair sum and score on small grids, sampled candidates at
+full size, and agreement with the spectrum-dot path."""
+import numpy as np
+import pytest
+
+from oracle import kde_oracle as O
+from paper_1508_02766_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import os
+
+    from paper_1508_02766_gb300 import build, kde
+    if not os.path.exists(build.LIB):
+        build.build()
+    return kde
+
+
+def plan_for(K, w, **opts):
+    lam = [np.linalg.eigvalsh(h).max() for h in w.H]
+    big = 2.0 * w.H[int(np.argmax(lam))]
+    info = K.kde_plan_info_compute(w.M, w.lo, w.hi, big, precision=w.precision, tau=w.tau)
+    return K.Plan(w.M, w.lo, w.hi, big, precision=w.precision, tau=w.tau, P_min=info.P, **opts)
+
+
+def run(K, w, **opts):
+    plan = plan_for(K, w, **opts)
+    X = torch.from_numpy(np.ascontiguousarray(w.X)).cuda()
+    counts = K.kde_bin(X, w.lo, w.hi, w.M)
+    R = K.kde_autocorrelation(plan, counts)
+    S = torch.empty(2 * len(w.H), dtype=torch.float64, device="cuda")
+    lscv = K.kde_lscv_autocorr(plan, w.n, w.H, R, pair_sums=S)
+    torch.cuda.synchronize()
+    return lscv.cpu().numpy(), S.cpu().numpy(), counts.cpu().numpy(), R.cpu().numpy(), plan
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_autocorrelation_by_brute_force(K, prec):
+    """R(l) = sum_j c_j c_{j-l} on a 12 x 10 grid at every lag |l_k| <= P_k - M_k
+    (the largest support any candidate of the plan may have; larger lags
+    wrap around the cyclic grid and are never read)."""
+    w = W.lscv_small(4, 2, (12, 10), n=400, count=2, precision=prec)
+    _, _, counts, R, plan = run(K, w)
+    c = O.counts_to_c(counts)
+    P0, P1 = plan.info.P
+    M0, M1 = w.M
+    A0, A1 = min(P0 - M0, M0 - 1), min(P1 - M1, M1 - 1)
+    got, ref = [], []
+    for a in range(-A0, A0 + 1):
+        for b in range(-A1, A1 + 1):
+            s = 0.0
+            for j0 in range(max(0, a), min(M0, M0 + a)):
+                for j1 in range(max(0, b), min(M1, M1 + b)):
+                    s += c[j0, j1] * c[j0 - a, j1 - b]
+            ref.append(s)
+            got.append(R[a % P0, b % P1])
+    got, ref = np.array(got), np.array(ref)
+    tol = 1e-12 if prec == "f64" else 2e-6
+    assert np.max(np.abs(got - ref)) <= tol * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec,layout", [("f64", "corrected"), ("f32", "corrected"),
+                                         ("f64", "wand")])
+def test_every_candidate(K, prec, layout):
+    """40 candidates (two chunks): every pair sum and score against the oracle."""
+    w = W.lscv_small(7, 2, (36, 44), n=3000, count=40, precision=prec)
+    lscv, S, counts, _, _ = run(K, w, layout=layout)
+    c = O.counts_to_c(counts)
+    Sref, ref = [], []
+    for H in w.H:
+        s = []
+        for A in (H, 2 * H):
+            L = O.support_L(A, w.lo, w.hi, w.M, w.tau)
+            if layout == "wand":
+                k = O.kernel_weights(A, w.lo, w.hi, w.M, L, n=1, layout="wand")
+                s.append(float(np.sum(c * O.binned_direct(c, k, L))))
+            else:
+                s.append(O.binned_pair_sum(c, A, w.lo, w.hi, w.M, L))
+        Sref.append(s)
+        if layout == "corrected":
+            ref.append(O.lscv_binned(counts, w.n, H, w.lo, w.hi, w.M, w.tau))
+    Sref = np.array(Sref)
+    tol = 1e-12 if prec == "f64" else 2e-6
+    assert np.max(np.abs(S.reshape(-1, 2) - Sref) / np.abs(Sref)) < tol
+    if layout == "corrected":
+        ref = np.array(ref)
+        scale = np.max(np.abs(Sref[:, 1])) / w.n ** 2
+        assert np.max(np.abs(lscv - ref)) < tol * 10 * scale
+        assert int(np.argmin(lscv)) == int(np.argmin(ref))
+
+
+def test_full_size_sampled_candidates_and_spectrum_path(K):
+    """512^2, n = 2e6, 1024 candidates: five candidates against the oracle's
+    spectral pair sums, and every score against the spectrum-dot path."""
+    w = W.lscv2d_512_f32()
+    lscv, S, counts, _, plan = run(K, w)
+    assert np.all(np.isfinite(lscv))
+    c = O.counts_to_c(counts)
+    P = plan.info.P
+    rng = np.random.default_rng(3)
+    for i in [int(np.argmin(lscv))] + list(rng.choice(len(w.H), 4, replace=False)):
+        for h, A in enumerate((w.H[i], 2 * w.H[i])):
+            L = O.support_L(A, w.lo, w.hi, w.M, w.tau)
+            ref = O.binned_pair_sum_dft(c, A, w.lo, w.hi, w.M, L, P)
+            # the FP32 LSCV bound of the spectrum path's tests
+            assert abs(S[2 * i + h] - ref) < 2e-5 * abs(ref), (i, h)
+    cd = torch.from_numpy(counts).cuda()
+    Wsp = K.kde_power_spectrum(plan, cd)
+    S2 = torch.empty(2 * len(w.H), dtype=torch.float64, device="cuda")
+    K.kde_lscv(plan, w.n, w.H, Wsp, pair_sums=S2)
+    S2 = S2.cpu().numpy()
+    assert np.max(np.abs(S - S2) / np.abs(S2)) < 2e-5
+
+
+def test_rejects_unsupported(K):
+    w = W.lscv_small(9, 2, (30, 30), n=500, count=3, precision="f64")
+    plan = K.Plan(w.M, w.lo, w.hi, w.H[0], precision="f64")
+    X = torch.from_numpy(np.ascontiguousarray(w.X)).cuda()
+    counts = K.kde_bin(X, w.lo, w.hi, w.M)
+    R = K.kde_autocorrelation(plan, counts)
+    with pytest.raises(K.KDEError) as e:
+        K.kde_lscv_autocorr(plan, w.n, np.stack([w.H[0] * 400.0]), R)
+    assert e.value.status == 1
+    p1 = K.Plan((300,), (0.0,), (1.0,), np.eye(1) * 1e-3, precision="f64")
+    with pytest.raises(K.KDEError) as e:
+        K.kde_lscv_autocorr_workspace_bytes(p1)
+    assert e.value.status == 7
