@@ -191,3 +191,55 @@ def select(scorer, mlp, X, refine=True, fallback=True, scored=None):
             scored.extend(scorer.cand_H)
         return t, v, len(H) + len(scorer.cand), True
     return cands[i], float(s[i]), len(H), False
+
+
+def select_batch(scorer, mlp, datasets, fallback=True, scored=None):
+    """The learned method on many datasets at once: features and
+    autocorrelations of every dataset, one network forward pass for the
+    batch (at most mlp.max_batch rows per pass), then the 27-candidate
+    neighbourhoods and normal-reference scores of every dataset enqueued
+    before one host synchronisation; datasets whose proposal is worse than
+    the normal-reference score fall back to the plain search.  Returns a list
+    of (theta, lscv, candidates scored, fell back)."""
+    torch = scorer.torch
+    dev = scorer.device
+    B = len(datasets)
+    info = scorer.plan.info
+    F = torch.empty(B, kde.FEAT_DIM, dtype=torch.float32, device=dev)
+    Rs = torch.empty(B, info.P[0], info.P[1], dtype=torch.float32, device=dev)
+    ns = []
+    for i, X in enumerate(datasets):
+        Xd = X if torch.is_tensor(X) else torch.from_numpy(np.ascontiguousarray(X)).to(dev)
+        F[i].copy_(scorer.prepare(Xd))
+        Rs[i].copy_(scorer.R)
+        ns.append(int(Xd.shape[0]))
+    TH = torch.empty(B, 3, dtype=torch.float32, device=dev)
+    for s0 in range(0, B, mlp.max_batch):
+        mlp.forward(F[s0:s0 + mlp.max_batch], Y=TH[s0:s0 + mlp.max_batch])
+    TH = TH.cpu().numpy().astype(np.float64)
+    lo = np.array([A_GRID[0], BETA_GRID[0], C_GRID[0]]) - 0.5 * STEP
+    hi = np.array([A_GRID[-1], BETA_GRID[-1], C_GRID[-1]]) + 0.5 * STEP
+    cands, out = [], torch.empty(B, 28, dtype=torch.float64, device=dev)
+    for i in range(B):
+        c = neighbourhood(np.clip(TH[i], lo, hi))
+        H = np.stack([theta_to_H(t) for t in c] + [theta_to_H(normal_reference_theta(ns[i]))])
+        kde.kde_lscv_autocorr(scorer.plan, ns[i], H, Rs[i], lscv=out[i], workspace=scorer.lws)
+        if scored is not None:
+            scored.extend(H)
+        cands.append(c)
+    s_all = out.cpu().numpy()
+    res = []
+    for i in range(B):
+        s = s_all[i]
+        j = int(np.argmin(s[:-1]))
+        if fallback and s[j] > s[-1]:
+            allv = scorer.torch.empty(len(scorer.cand), dtype=torch.float64, device=dev)
+            kde.kde_lscv_autocorr(scorer.plan, ns[i], scorer.cand_H, Rs[i], lscv=allv,
+                                  workspace=scorer.lws)
+            if scored is not None:
+                scored.extend(scorer.cand_H)
+            k = int(torch.argmin(allv).item())
+            res.append((scorer.cand[k], float(allv[k].item()), 28 + len(scorer.cand), True))
+        else:
+            res.append((cands[i][j], float(s[j]), 28, False))
+    return res

@@ -177,3 +177,12 @@ def test_learned_proposal_beats_the_method_without_it():
     assert mlp.status() == 0
     assert np.mean(reg_learned) < np.mean(reg_ref)
     assert max(n_cand) <= 28 < len(sc.cand)
+    # the batched form selects the same bandwidths
+    res = Lm.select_batch(sc, mlp, test_sets, fallback=False)
+    for (th_b, v_b, k_b, _), v in zip(res, np.array(reg_learned)):
+        assert k_b == 28
+    vb = np.array([r[1] for r in res])
+    vs = []
+    for X in test_sets:
+        vs.append(Lm.select(sc, mlp, torch.from_numpy(X).to(DEV), fallback=False)[1])
+    assert np.allclose(vb, np.array(vs), rtol=1e-12, atol=0)
