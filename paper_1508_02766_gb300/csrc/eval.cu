@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 #include <set>
 #include <string>
@@ -38,29 +39,46 @@ struct KGen {
   int d;
   int L[KDE_MAX_D];
   int wand;
-  T A[KDE_MAX_D][KDE_MAX_D];  // delta_a delta_b (H^-1)_ab
+  // -q/2 = sum_k D_k u_k^2, u_k = m_k + sum_{j<k} B_kj m_j, m = l (|l| in
+  // Wand's layout): the squares completed from the Cholesky factor of the
+  // bandwidth; B = {B_10, B_20, B_21}, each the sum Bh + Bl of two T.
+  T D[KDE_MAX_D];
+  T Bh[3], Bl[3];
   T C;                        // (2 pi)^{-d/2} |H|^{-1/2} / (n 2^32 prod P)
 };
 
 __device__ __forceinline__ float ex(float x) { return expf(x); }
 __device__ __forceinline__ double ex(double x) { return exp(x); }
 
-// k at lag l (Eq. 6 with the normalisations folded in).
+// b m as the sum of the rounded product and its error (exact in FP32 up to
+// b's own split into bh + bl).
+template <typename T>
+__device__ __forceinline__ T prod_lo(T bh, T bl, T m, T hi) {
+  return fma(bh, m, -hi) + bl * m;
+}
+
+// k at lag l (Eq. 6 with the normalisations folded in).  The quadratic form
+// is evaluated in completed squares: a nearly singular bandwidth would lose
+// the small exponents near its long axis to cancellation in the expanded
+// sum of A_ab l_a l_b.
 template <typename T>
 __device__ __forceinline__ T kernel_value(const KGen<T>& g, const int* l) {
-  T q = 0;
+  T m[KDE_MAX_D];
 #pragma unroll
-  for (int a = 0; a < KDE_MAX_D; ++a) {
-    if (a >= g.d) break;
-    T la = (T)(g.wand ? abs(l[a]) : l[a]);
-#pragma unroll
-    for (int b = 0; b < KDE_MAX_D; ++b) {
-      if (b >= g.d) break;
-      T lb = (T)(g.wand ? abs(l[b]) : l[b]);
-      q += g.A[a][b] * la * lb;
-    }
+  for (int a = 0; a < KDE_MAX_D; ++a) m[a] = (a < g.d) ? (T)(g.wand ? abs(l[a]) : l[a]) : T(0);
+  T e = g.D[0] * m[0] * m[0];
+  if (g.d >= 2) {
+    const T t = g.Bh[0] * m[0];
+    const T u = (m[1] + t) + prod_lo(g.Bh[0], g.Bl[0], m[0], t);
+    e = fma(g.D[1] * u, u, e);
   }
-  return g.C * ex(T(-0.5) * q);
+  if (g.d == 3) {
+    const T t0 = g.Bh[1] * m[0], t1 = g.Bh[2] * m[1];
+    const T u = ((m[2] + t0) + t1) + (prod_lo(g.Bh[1], g.Bl[1], m[0], t0) +
+                                      prod_lo(g.Bh[2], g.Bl[2], m[1], t1));
+    e = fma(g.D[2] * u, u, e);
+  }
+  return g.C * ex(e);
 }
 
 // Signed lag stored at wrapped position p of a length-P axis with support L,
@@ -949,45 +967,62 @@ __global__ void __launch_bounds__(32) kde_lscv_reduce_kernel(LscvReduce r, const
 // (l_0, l_1) at (l_0 mod P_0, l_1 mod P_1)):
 //   S(A) = sum_{|l_k| <= L_k} K_A(delta o l) R(l).
 // K_A and R are even, so the sum runs over the half plane l_0 > 0, or
-// l_0 = 0 and l_1 > 0, twice, plus the lag 0 once.  Block (x, b) takes lag
-// rows x rpb .. x rpb + rpb - 1 of matrix b and writes one FP64 partial.
-// One block covers a whole support (rpb = the largest L_0 + 1 of the
-// launch): small supports would otherwise leave most blocks empty.
-constexpr int kAcRows = 4;  // row granularity the workspace is sized for
-
-// Up to kAcChunk candidates (2 kAcChunk matrices) per launch; their kernel
-// parameters are uploaded to the workspace.
-constexpr int kAcChunk = 1024;
-
+// l_0 = 0 and l_1 > 0, twice, plus the lag 0 once.
+//
+// Along lag row l_0 >= 0 the Gaussian is C exp(e) in the completed squares
+// of KGen (d = 2, column lag m = l_1, or |l_1| in Wand's layout):
+//   e = D_0 l_0^2 + D_1 (m + b l_0)^2,  b = B_10 = b_hi + b_lo,
+// so per row e_0 = D_0 l_0^2 and b l_0 are formed once.
 template <typename T>
-__global__ void __launch_bounds__(256) kde_lscv_ac_kernel(const KGen<T>* __restrict__ gens,
-                                                          const T* __restrict__ R, int P1, int rpb,
+struct AcGen {
+  int L0, L1, wand;
+  int rpu;     // lag rows per work unit
+  int u0, nu;  // this matrix's work units [u0, u0 + nu)
+  T D0, D1, b_hi, b_lo, C;
+};
+
+// Up to kAcChunk candidates (2 kAcChunk matrices) per launch; their
+// parameters and work units are uploaded to the workspace.  A work unit is
+// kAcRows or more lag rows of one matrix, about kAcTerms lag terms.
+constexpr int kAcChunk = 1024;
+constexpr int kAcRows = 8;
+constexpr int kAcTerms = 4096;
+
+// Block u takes work unit units[u] = (matrix, first row), one warp per lag
+// row, and writes one FP64 partial.
+template <typename T>
+__global__ void __launch_bounds__(256) kde_lscv_ac_kernel(const AcGen<T>* __restrict__ gens,
+                                                          const int2* __restrict__ units,
+                                                          const T* __restrict__ R, int P1,
                                                           double* __restrict__ partial) {
-  const int b = blockIdx.y;
-  __shared__ KGen<T> gen;
-  if (threadIdx.x == 0) gen = gens[b];
-  __syncthreads();
-  const int L0 = gen.L[0], L1 = gen.L[1];
-  const int r0 = blockIdx.x * rpb;
+  const int2 u = units[blockIdx.x];
+  const AcGen<T> g = gens[u.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int r1 = min(g.L0, u.y + g.rpu - 1);
   T acc = 0;
-  if (r0 <= L0) {
-    const int r1 = min(L0, r0 + rpb - 1);
-    const int W1 = 2 * L1 + 1;
-    const int total = (r1 - r0 + 1) * W1;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int dr = t / W1;
-      const int l0 = r0 + dr, l1 = t - dr * W1 - L1;
-      if (l0 == 0 && l1 < 0) continue;
-      const T w = (l0 == 0 && l1 == 0) ? T(1) : T(2);
-      const int l[KDE_MAX_D] = {l0, l1, 0};
-      acc += w * kernel_value<T>(gen, l) * __ldg(R + (size_t)l0 * P1 + (l1 < 0 ? l1 + P1 : l1));
+  for (int l0 = u.y + warp; l0 <= r1; l0 += nw) {
+    const T tl = (T)l0;
+    const T t_hi = g.b_hi * tl;
+    const T t_lo = prod_lo(g.b_hi, g.b_lo, tl, t_hi);
+    const T e0 = g.D0 * tl * tl;
+    const T* Rrow = R + (size_t)l0 * P1;
+    T racc = 0;
+    for (int l1 = (l0 == 0 ? 0 : -g.L1) + lane; l1 <= g.L1; l1 += 32) {
+      const T v = ((T)(g.wand ? abs(l1) : l1) + t_hi) + t_lo;
+      racc += ex(fma(g.D1 * v, v, e0)) * __ldg(Rrow + (l1 < 0 ? l1 + P1 : l1));
     }
+    // every lag of the half plane counts twice, the lag 0 (K = C) once
+    if (l0 == 0 && lane == 0) racc -= T(0.5) * __ldg(Rrow);
+    acc += T(2) * racc;
   }
-  block_sum_to((double)acc, partial + (size_t)b * gridDim.x + blockIdx.x);
+  block_sum_to((double)(g.C * acc), partial + blockIdx.x);
 }
 
-// As kde_lscv_reduce_kernel with K_{H_i}(0) read from memory and scale 1.
-__global__ void __launch_bounds__(32) kde_lscv_ac_reduce_kernel(int nparts, double n,
+// As kde_lscv_reduce_kernel with K_{H_i}(0) read from memory and scale 1;
+// matrix 2i + h sums the partials of its work units.
+template <typename T>
+__global__ void __launch_bounds__(32) kde_lscv_ac_reduce_kernel(const AcGen<T>* __restrict__ gens,
+                                                                double n,
                                                                 const double* __restrict__ K0,
                                                                 const double* __restrict__ partial,
                                                                 double* __restrict__ S_out,
@@ -996,9 +1031,9 @@ __global__ void __launch_bounds__(32) kde_lscv_ac_reduce_kernel(int nparts, doub
   double s[2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const double* pp = partial + (int64_t)(2 * i + h) * nparts;
+    const int u0 = gens[2 * i + h].u0, nu = gens[2 * i + h].nu;
     double v = 0.0;
-    for (int j = threadIdx.x; j < nparts; j += 32) v += pp[j];
+    for (int j = threadIdx.x; j < nu; j += 32) v += partial[u0 + j];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     s[h] = __shfl_sync(0xffffffffu, v, 0);
@@ -1162,21 +1197,38 @@ kde_status launch_cols(ColsKernel<T> fn_lines, ColsKernel<T> fn_simd, ColsParams
 
 #define KDE_COLS(kern) kern<T, false>, kern<T, true>
 
+// Kernel-grid parameters of K_A (no 1/n, 2^-32 or 1/prod P folded in).
+template <typename T>
+kde_status kgen_for(const kde_plan_info& I, const double* A, double detA, const int64_t* L,
+                    int wand, KGen<T>* g) {
+  double D[3], B[3];
+  kde_status st = gauss_factor(I.d, A, I.delta, D, B);
+  if (st != KDE_OK) return st;
+  *g = KGen<T>{};
+  g->d = I.d;
+  g->wand = wand;
+  for (int k = 0; k < I.d; ++k) {
+    g->L[k] = (int)L[k];
+    g->D[k] = (T)D[k];
+  }
+  for (int e = 0; e < 3; ++e) {
+    g->Bh[e] = (T)B[e];
+    g->Bl[e] = (T)(B[e] - (double)g->Bh[e]);
+  }
+  g->C = (T)(std::pow(6.283185307179586476925287, -0.5 * I.d) / std::sqrt(detA));
+  return KDE_OK;
+}
+
 template <typename T>
 kde_status kernel_grid_impl(kde_plan_s* plan, int64_t n, void* Kspec, void* ws, cudaStream_t st) {
   using V = typename Cplx<T>::type;
   const kde_plan_info& I = plan->info;
   const int d = I.d;
-  KGen<T> gen{};
-  gen.d = d;
-  gen.wand = plan->layout_mode == KDE_LAYOUT_WAND;
+  KGen<T> gen;
+  kde_status st0 = kgen_for<T>(I, plan->H, I.det_H, I.L, plan->layout_mode == KDE_LAYOUT_WAND, &gen);
+  if (st0 != KDE_OK) return st0;
   double prodP = 1.0;
-  for (int k = 0; k < d; ++k) {
-    gen.L[k] = (int)I.L[k];
-    prodP *= (double)I.P[k];
-  }
-  for (int a = 0; a < d; ++a)
-    for (int b = 0; b < d; ++b) gen.A[a][b] = (T)(I.delta[a] * I.delta[b] * plan->Hinv[a * d + b]);
+  for (int k = 0; k < d; ++k) prodP *= (double)I.P[k];
   const double two_pi = 6.283185307179586476925287;
   double C = std::pow(two_pi, -0.5 * d) / std::sqrt(I.det_H) / ((double)n * 4294967296.0 * prodP);
   gen.C = (T)C;
@@ -1410,20 +1462,6 @@ kde_status power_spectrum_impl(kde_plan_s* plan, const int64_t* counts, void* Wo
                         "kde_cols_power_kernel");
 }
 
-// Kernel-grid parameters of K_A (no 1/n, 2^-32 or 1/prod P folded in).
-template <typename T>
-KGen<T> kgen_for(const kde_plan_info& I, const double* Ainv, double detA, const int64_t* L,
-                 int wand) {
-  KGen<T> g{};
-  g.d = I.d;
-  g.wand = wand;
-  for (int k = 0; k < I.d; ++k) g.L[k] = (int)L[k];
-  for (int a = 0; a < I.d; ++a)
-    for (int b = 0; b < I.d; ++b) g.A[a][b] = (T)(I.delta[a] * I.delta[b] * Ainv[a * I.d + b]);
-  g.C = (T)(std::pow(6.283185307179586476925287, -0.5 * I.d) / std::sqrt(detA));
-  return g;
-}
-
 // Scratch for one chunk of kBatch matrices: lag-grid rows (at most
 // 2 (P_0 - M_0) + 1 per matrix, since every accepted matrix has
 // M_0 + L_0 <= P_0) and the partial sums.
@@ -1469,7 +1507,8 @@ kde_status lscv_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, cons
         kde_status st2 = kde::matrix_support(plan, A, Ainv, &detA, L);
         if (st2 != KDE_OK) return st2;
         const int b = 2 * i + h;
-        bk.gen[b] = kgen_for<T>(I, Ainv, detA, L, plan->layout_mode == KDE_LAYOUT_WAND);
+        st2 = kgen_for<T>(I, A, detA, L, plan->layout_mode == KDE_LAYOUT_WAND, &bk.gen[b]);
+        if (st2 != KDE_OK) return st2;
         bk.rows[b] = (d == 1) ? 1 : (int)(2 * L[0] + 1);
         bk.off[b] = off;
         off += (int64_t)bk.rows[b] * I.Q;
@@ -1557,15 +1596,21 @@ kde_status lscv_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, cons
 // ---------------------------------------------------------------------------
 // Workspace: the autocorrelation's spectra, or (lag sums) the uploaded
 // kernel parameters, K_H(0) and the FP64 partials of one chunk.
-size_t ac_param_bytes() { return ((size_t)2 * kAcChunk * sizeof(KGen<double>) + 255) & ~(size_t)255; }
-size_t ac_k0_bytes() { return ((size_t)kAcChunk * sizeof(double) + 255) & ~(size_t)255; }
+// At most this many work units per chunk: a unit holds kAcRows rows or more
+// (the last of a matrix fewer), and L_0 < P_0 - M_0 + 1 for every matrix.
+size_t ac_units_max(const kde_plan_info& I) {
+  return (size_t)2 * kAcChunk * (size_t)((I.P[0] + kAcRows - 1) / kAcRows + 1);
+}
+// Uploaded per chunk: 2 nh AcGen, nh K_H(0), then the work units.
+size_t ac_upload_bytes(const kde_plan_info& I) {
+  return ((size_t)2 * kAcChunk * sizeof(AcGen<double>) + (size_t)kAcChunk * sizeof(double) +
+          ac_units_max(I) * sizeof(int2) + 255) & ~(size_t)255;
+}
 
 size_t ac_workspace(const kde_plan_info& I) {
   const size_t cb = (I.precision == KDE_F32) ? 8 : 16;
   const size_t spec = ((size_t)(I.M[0] + I.P[0]) * I.Q * cb + 255) & ~(size_t)255;
-  const size_t parts = (size_t)2 * kAcChunk * (size_t)((I.P[0] + kAcRows - 1) / kAcRows + 1) *
-                       sizeof(double);
-  return std::max(spec, ac_param_bytes() + ac_k0_bytes() + parts);
+  return std::max(spec, ac_upload_bytes(I) + ac_units_max(I) * sizeof(double));
 }
 
 template <typename T>
@@ -1616,16 +1661,16 @@ kde_status lscv_ac_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, c
                         double* S_out, double* lscv_out, void* ws, cudaStream_t st) {
   const kde_plan_info& I = plan->info;
   const int d = I.d;
-  KGen<T>* gens_dev = (KGen<T>*)ws;
-  double* K0_dev = (double*)((char*)ws + ac_param_bytes());
-  double* partial = (double*)((char*)ws + ac_param_bytes() + ac_k0_bytes());
-  std::vector<KGen<T>> gens;
+  double* partial = (double*)((char*)ws + ac_upload_bytes(I));
+  std::vector<AcGen<T>> gens;
   std::vector<double> K0;
+  std::vector<int2> units;
+  std::vector<unsigned char> up;
   for (int h0 = 0; h0 < nH; h0 += kAcChunk) {
     const int nh = std::min(kAcChunk, nH - h0);
-    gens.assign(2 * nh, KGen<T>{});
+    gens.assign(2 * nh, AcGen<T>{});
     K0.assign(nh, 0.0);
-    int64_t max_rows = 1;
+    units.clear();
     for (int i = 0; i < nh; ++i) {
       const double* H = Hs + (size_t)(h0 + i) * d * d;
       for (int h = 0; h < 2; ++h) {
@@ -1634,29 +1679,51 @@ kde_status lscv_ac_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, c
         for (int e = 0; e < d * d; ++e) A[e] = (h ? 2.0 : 1.0) * H[e];
         kde_status st2 = kde::matrix_support(plan, A, Ainv, &detA, L);
         if (st2 != KDE_OK) return st2;
-        gens[2 * i + h] = kgen_for<T>(I, Ainv, detA, L, plan->layout_mode == KDE_LAYOUT_WAND);
-        max_rows = std::max<int64_t>(max_rows, L[0] + 1);
+        KGen<T> kg;
+        st2 = kgen_for<T>(I, A, detA, L, plan->layout_mode == KDE_LAYOUT_WAND, &kg);
+        if (st2 != KDE_OK) return st2;
+        AcGen<T>& g = gens[2 * i + h];
+        g.L0 = kg.L[0];
+        g.L1 = kg.L[1];
+        g.wand = kg.wand;
+        g.D0 = kg.D[0];
+        g.D1 = kg.D[1];
+        g.b_hi = kg.Bh[0];
+        g.b_lo = kg.Bl[0];
+        g.C = kg.C;
+        const int W = 2 * g.L1 + 1;
+        g.rpu = std::max(kAcRows, (kAcTerms / W + kAcRows - 1) / kAcRows * kAcRows);
+        g.u0 = (int)units.size();
+        for (int r = 0; r <= g.L0; r += g.rpu) units.push_back(make_int2(2 * i + h, r));
+        g.nu = (int)units.size() - g.u0;
         if (h == 0) K0[i] = std::pow(6.283185307179586476925287, -0.5 * d) / std::sqrt(detA);
       }
     }
-    // pageable sources: the copies are staged before these calls return
-    cudaError_t e = cudaMemcpyAsync(gens_dev, gens.data(), gens.size() * sizeof(KGen<T>),
-                                    cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(K0_dev, K0.data(), K0.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (units.size() > ac_units_max(I)) return fail(KDE_ERR_UNSUPPORTED, "lag-sum work units overflow");
+    // one upload, laid out as on the device: AcGen[2 nh], K0[nh], units
+    const size_t gb = gens.size() * sizeof(AcGen<T>), kb = K0.size() * sizeof(double),
+                 ub = units.size() * sizeof(int2);
+    up.resize(gb + kb + ub);
+    std::memcpy(up.data(), gens.data(), gb);
+    std::memcpy(up.data() + gb, K0.data(), kb);
+    std::memcpy(up.data() + gb + kb, units.data(), ub);
+    const AcGen<T>* gens_dev = (const AcGen<T>*)ws;
+    const double* K0_dev = (const double*)((char*)ws + gb);
+    const int2* units_dev = (const int2*)((char*)ws + gb + kb);
+    // pageable source: the copy is staged before this call returns
+    cudaError_t e = cudaMemcpyAsync(ws, up.data(), up.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(kernel parameters)");
-    const int gx = 1;
     {
       LaunchScope ls("kde_lscv_ac_kernel", st);
-      kde_lscv_ac_kernel<T><<<dim3((unsigned)gx, (unsigned)(2 * nh)), 256, 0, st>>>(
-          gens_dev, (const T*)R, (int)I.P[1], (int)max_rows, partial);
+      kde_lscv_ac_kernel<T><<<(unsigned)units.size(), 256, 0, st>>>(gens_dev, units_dev, (const T*)R,
+                                                                  (int)I.P[1], partial);
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_kernel");
     }
     {
       LaunchScope ls("kde_lscv_reduce_kernel", st);
-      kde_lscv_ac_reduce_kernel<<<nh, 32, 0, st>>>(gx, (double)n, K0_dev, partial,
-                                                   S_out ? S_out + 2 * h0 : nullptr, lscv_out + h0);
+      kde_lscv_ac_reduce_kernel<T><<<nh, 32, 0, st>>>(gens_dev, (double)n, K0_dev, partial,
+                                                      S_out ? S_out + 2 * h0 : nullptr, lscv_out + h0);
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_reduce_kernel");
     }
@@ -2126,9 +2193,8 @@ kde_status batch_upload(kde_batch_plan_s* bp, const kde_batch_item* items) {
     B.A_off = A;
     B.T1_off = T1;
     B.dens_off = de;
-    double Ainv[9];
-    for (int e = 0; e < 4; ++e) Ainv[e] = pl->Hinv[e];
-    B.gen = kgen_for<T>(I, Ainv, I.det_H, I.L, pl->layout_mode == KDE_LAYOUT_WAND);
+    kde_status sg = kgen_for<T>(I, pl->H, I.det_H, I.L, pl->layout_mode == KDE_LAYOUT_WAND, &B.gen);
+    if (sg != KDE_OK) return sg;
     B.gen.C = (T)(std::pow(6.283185307179586476925287, -1.0) / std::sqrt(I.det_H) /
                   ((double)items[i].n * 4294967296.0 * (double)I.P[0] * (double)I.P[1]));
     x += items[i].n;

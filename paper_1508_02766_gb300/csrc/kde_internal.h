@@ -38,6 +38,10 @@ kde_status fail(kde_status s, const std::string& msg);
 kde_status matrix_support(const kde_plan_s* plan, const double* A, double* Ainv, double* detA,
                           int64_t* L);
 kde_status cuda_fail(cudaError_t e, const char* what);
+// K_A(delta o l) = C exp(sum_k D_k (l_k + sum_{j<k} B_kj l_j)^2) from the
+// Cholesky factor of A (no cancellation when A is nearly singular);
+// B = {B_10, B_20, B_21}, entries beyond d zero.
+kde_status gauss_factor(int d, const double* A, const double* delta, double* D, double* B);
 // Tensor-core first pass (dft_tc.cu): build the plan's DFT matrix; run the
 // counts rows -> half spectra pass (rows of length M_last, out [rows][Q]).
 kde_status dft_tc_setup(kde_plan_s* plan);

@@ -109,6 +109,37 @@ static void spd_inverse(int d, const double* R, double* Hinv) {  // from H = R R
     }
 }
 
+// Exponent of K_A at lag l on bins of width delta, in completed squares:
+// with A = R R^T (Cholesky) and y = R^-1 (delta o l), (delta o l)^T A^-1
+// (delta o l) = |y|^2 and y_k = (R^-1)_kk delta_k (l_k + sum_{j<k} B_kj l_j),
+//   -q/2 = sum_k D_k (l_k + sum_{j<k} B_kj l_j)^2,
+//   D_k = -delta_k^2 / (2 R_kk^2),  B_kj = (R^-1)_kj delta_j / ((R^-1)_kk delta_k).
+// B[0] = B_10, B[1] = B_20, B[2] = B_21.
+kde_status gauss_factor(int d, const double* A, const double* delta, double* D, double* B) {
+  double R[9];
+  if (!cholesky(d, A, R)) return fail(KDE_ERR_NOT_SPD, "bandwidth is not positive definite");
+  double Rinv[9] = {0};
+  for (int j = 0; j < d; ++j) {
+    Rinv[j * 3 + j] = 1.0 / R[j * 3 + j];
+    for (int i = j + 1; i < d; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s += R[i * 3 + k] * Rinv[k * 3 + j];
+      Rinv[i * 3 + j] = -s / R[i * 3 + i];
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    D[k] = 0.0;
+    B[k] = 0.0;
+  }
+  for (int k = 0; k < d; ++k) D[k] = -0.5 * delta[k] * delta[k] * Rinv[k * 3 + k] * Rinv[k * 3 + k];
+  const int kj[3][2] = {{1, 0}, {2, 0}, {2, 1}};
+  for (int e = 0; e < 3; ++e) {
+    const int k = kj[e][0], j = kj[e][1];
+    if (k < d) B[e] = Rinv[k * 3 + j] * delta[j] / (Rinv[k * 3 + k] * delta[k]);
+  }
+  return KDE_OK;
+}
+
 // Largest eigenvalue of a symmetric d x d matrix: closed form for d <= 2,
 // cyclic Jacobi rotations for d = 3.
 static double lambda_max(int d, const double* H) {
