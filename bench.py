@@ -113,9 +113,11 @@ def fp32_peak_tflops(sm_mhz=2070.0, sms=152):
 
 def ac_flops(L):
     """Lag terms of the half-plane autocorrelation sum of one matrix with
-    support L (rows 0..L_0, all 2 L_1 + 1 columns), 13 flops each: the
-    quadratic form (8), exp (1), scale (1), weight x R and accumulate (3)."""
-    return 13.0 * (L[0] + 1) * (2 * L[1] + 1)
+    support L (rows 0..L_0, all 2 L_1 + 1 columns), 8 flops each: the
+    exponent in completed squares along the row, D_1 (m + b l_0)^2 + e_0
+    (5: two adds, a multiply and an FMA), exp (1), times R and accumulate
+    (2)."""
+    return 8.0 * (L[0] + 1) * (2 * L[1] + 1)
 
 
 def fft_flops(n_lines, N):
@@ -698,13 +700,24 @@ def lscv_main(args):
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = fp32_peak_tflops(sm_max)
-    ach = flops.get(dom, 0.0) / (dom_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x SM max clock",
-                "traffic": None, "flops_per_launch": flops.get(dom, 0.0),
-                "flop_model": "5 N log2 N per complex FFT line + 2 per dot-product term; "
-                              "13 per lag term of the autocorrelation sum (exp counted as 1)"}
+    if dom == "kde_bin_kernel":
+        # binning: HBM-bound model, X read once and the counts written once
+        hbm, src = peaks()
+        nbytes = w.n * w.d * w.X.dtype.itemsize + 8 * int(np.prod(w.M))
+        ach = nbytes / (dom_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)"
+                    if src == "measured" else "fallback 6.8 TB/s",
+                    "traffic": None, "bytes_per_launch": nbytes}
+    else:
+        peak = fp32_peak_tflops(sm_max)
+        ach = flops.get(dom, 0.0) / (dom_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x SM max clock",
+                    "traffic": None, "flops_per_launch": flops.get(dom, 0.0),
+                    "flop_model": "5 N log2 N per complex FFT line + 2 per dot-product term; "
+                                  "8 per lag term of the autocorrelation sum (exp counted as 1)"}
     line = {"metric": LSCV_METRIC, "value": value, "unit": "candidates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -127,36 +127,51 @@ __device__ __forceinline__ void corner_weights(const unsigned* q, unsigned long 
 // ---------------------------------------------------------------------------
 // Direct path.
 // ---------------------------------------------------------------------------
+// A pair of adjacent lanes takes one sample: lane parity p adds the 2^(D-1)
+// corners at offset p along the last axis.  Corners (.., j) and (.., j + 1)
+// are adjacent 8-byte words, in one 32-byte sector unless j = 3 mod 4, so
+// each warp instruction's lane pairs coalesce into one sector request where
+// one lane per sample would issue two: the scattered-sector rate of the L2
+// is what bounds this kernel.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) kde_bin_kernel(const T* __restrict__ X, int64_t n,
                                                       BinParams<T> p,
                                                       unsigned long long* __restrict__ counts,
                                                       unsigned long long* __restrict__ n_out) {
+  constexpr int H = 1 << (D - 1);
+  const int par = threadIdx.x & 1;
   unsigned long long outside = 0;
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
-       s += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t step = ((int64_t)gridDim.x * blockDim.x) >> 1;
+  for (int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 1; s < n; s += step) {
     int i[D];
     unsigned q[D];
     bool in = true;
 #pragma unroll
     for (int k = 0; k < D; ++k) in &= axis_position<T>(X[s * D + k], p.ax[k], i[k], q[k]);
     if (!in) {
-      ++outside;
+      outside += par == 0;
       continue;
     }
-    int64_t base = 0;
+    int64_t base = par;
 #pragma unroll
     for (int k = 0; k < D; ++k) base += (int64_t)i[k] * p.ax[k].stride;
-    unsigned long long w[1 << D];
-    corner_weights<D>(q, w);
+    // weights over the first D - 1 axes, then this lane's half of the last split
+    unsigned long long w[H];
+    if (D == 1) {
+      w[0] = kOne;
+    } else {
+      corner_weights<D - 1>(q, w);
+    }
 #pragma unroll
-    for (int c = 0; c < (1 << D); ++c) {
-      if (w[c] == 0) continue;
+    for (int c = 0; c < H; ++c) {
+      const unsigned long long hi = mulhi_round(w[c], q[D - 1]);
+      const unsigned long long wc = par ? hi : w[c] - hi;
+      if (wc == 0) continue;
       int64_t idx = base;
 #pragma unroll
-      for (int k = 0; k < D; ++k)
-        if ((c >> (D - 1 - k)) & 1) idx += p.ax[k].stride;
-      atomicAdd(counts + idx, w[c]);
+      for (int k = 0; k < D - 1; ++k)
+        if ((c >> (D - 2 - k)) & 1) idx += p.ax[k].stride;
+      atomicAdd(counts + idx, wc);
     }
   }
   if (n_out) {
@@ -673,7 +688,7 @@ kde_status launch_direct(const T* X, int64_t n, int d, const double* lo, const d
   if (e != cudaSuccess) return kde::cuda_fail(e, "cudaMemsetAsync(counts)");
   if (n == 0) return KDE_OK;
   BinParams<T> p = make_params<T>(d, lo, hi, M, nullptr);
-  int64_t want = (n + 255) / 256;
+  int64_t want = (2 * n + 255) / 256;  // two lanes per sample
   int64_t cap = (int64_t)num_sms() * 8;
   int blocks = (int)(want < cap ? want : cap);
   kde::LaunchScope ls("kde_bin_kernel", stream);
