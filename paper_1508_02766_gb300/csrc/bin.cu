@@ -23,6 +23,7 @@
 //           reads those records from the neighbour's face buckets.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -34,7 +35,7 @@ constexpr unsigned long long kOne = 1ull << 32;
 constexpr int kHistThreads = 512;
 constexpr int kGatherThreads = 256;
 constexpr int kMaxKeys = 32768;
-constexpr int kMaxBlocks = 256;
+constexpr int kMaxBlocks = 1024;
 
 // floor((w q + 2^31) / 2^32) for 0 <= w <= 2^32 and 0 <= q < 2^32, exactly,
 // in 32-bit arithmetic: with w = wh 2^32 + wl (wh in {0, 1}) and
@@ -326,7 +327,8 @@ __device__ unsigned block_scan_excl(unsigned v, unsigned* warp_sums, unsigned* t
 struct TileGeom {
   int64_t M[KDE_MAX_D];
   int64_t stride[KDE_MAX_D];
-  int tile[KDE_MAX_D];
+  int tile[KDE_MAX_D];      // powers of two
+  int tile_log2[KDE_MAX_D];
   int ntiles[KDE_MAX_D];
   int tstride[KDE_MAX_D];
   int ntiles_total;
@@ -368,35 +370,42 @@ __device__ __forceinline__ void for_each_source(const int* tc, const TileGeom& g
 // all records); per tile the records feeding it (own plus neighbours' face
 // records), its number of work items (ceil(records / cap), at least 1) and
 // the exclusive prefix of items over tiles (item_start[ntiles] = all items).
+// The prefix is built in shared memory (nkeys + 1 words), where the per-tile
+// sums read it back.
 template <int D>
 __global__ void __launch_bounds__(1024)
 kde_bin_scan_keys_kernel(const unsigned* __restrict__ totals, int nkeys, TileGeom g,
                          unsigned* __restrict__ starts, unsigned* __restrict__ item_start) {
+  extern __shared__ unsigned s_starts[];
   __shared__ unsigned warp_sums[33];
+  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) s_starts[k] = totals[k];
+  __syncthreads();
   unsigned total;
   {
     const int per = (nkeys + blockDim.x - 1) / blockDim.x;
-    const int k0 = threadIdx.x * per;
+    const int k0 = min(nkeys, (int)threadIdx.x * per);
     const int k1 = min(nkeys, k0 + per);
     unsigned local = 0;
-    for (int k = k0; k < k1; ++k) local += totals[k];
+    for (int k = k0; k < k1; ++k) local += s_starts[k];
     unsigned run = block_scan_excl(local, warp_sums, &total);
     for (int k = k0; k < k1; ++k) {
-      starts[k] = run;
-      run += totals[k];
+      const unsigned v = s_starts[k];
+      s_starts[k] = run;
+      run += v;
     }
-    if (threadIdx.x == 0) starts[nkeys] = total;
+    if (threadIdx.x == 0) s_starts[nkeys] = total;
   }
   __syncthreads();
+  for (int k = threadIdx.x; k <= nkeys; k += blockDim.x) starts[k] = s_starts[k];
   const int ntiles = g.ntiles_total;
   const int per = (ntiles + blockDim.x - 1) / blockDim.x;
-  const int t0 = threadIdx.x * per;
+  const int t0 = min(ntiles, (int)threadIdx.x * per);
   const int t1 = min(ntiles, t0 + per);
   auto items_of = [&](int t) {
     int tc[KDE_MAX_D];
     tile_coords<D>(t, g, tc);
     unsigned recs = 0;
-    for_each_source<D>(tc, g, [&](int, int, int key) { recs += starts[key + 1] - starts[key]; });
+    for_each_source<D>(tc, g, [&](int, int, int key) { recs += s_starts[key + 1] - s_starts[key]; });
     return recs == 0 ? 1u : (recs + g.item_cap - 1) / g.item_cap;
   };
   unsigned li = 0;
@@ -435,68 +444,94 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, int nk
   }
 }
 
+// Global offset of tile-local cell c (last axis fastest; tile extents are
+// powers of two), or -1 if the cell lies beyond the grid's edge.
+template <int D>
+__device__ __forceinline__ int64_t tile_cell_offset(const int* tc, const TileGeom& g, int c) {
+  int64_t off = 0;
+  bool in = true;
+#pragma unroll
+  for (int k = D - 1; k >= 0; --k) {
+    const int x = c & (g.tile[k] - 1);
+    c >>= g.tile_log2[k];
+    const int64_t gx = (int64_t)tc[k] * g.tile[k] + x;
+    in &= gx < g.M[k];
+    off += gx * g.stride[k];
+  }
+  return in ? off : -1;
+}
+
 // Store a tile's owned cells (clipped at the grid's edge), last axis fastest.
 template <int D, typename F>
 __device__ __forceinline__ void store_tile(const int* tc, const TileGeom& g, int c0, int cstep,
                                            unsigned long long* __restrict__ counts, F value) {
-  int64_t lo[KDE_MAX_D], ext[KDE_MAX_D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    lo[k] = (int64_t)tc[k] * g.tile[k];
-    ext[k] = min((int64_t)g.tile[k], g.M[k] - lo[k]);
-  }
   for (int c = c0; c < g.tile_cells; c += cstep) {
-    int r = c;
-    int64_t off = 0;
-    bool in = true;
-#pragma unroll
-    for (int k = D - 1; k >= 0; --k) {
-      int x = r % g.tile[k];
-      r /= g.tile[k];
-      in &= x < ext[k];
-      off += (lo[k] + x) * g.stride[k];
-    }
-    if (in) counts[off] = value(c);
+    const int64_t off = tile_cell_offset<D>(tc, g, c);
+    if (off >= 0) counts[off] = value(c);
   }
 }
 
-// Accumulate records [r0, r1) whose base tile is nbt into this tile's cells.
-// A weight w <= 2^32 is added as two 16-bit-aligned parts into separate
-// 32-bit words: lo += w mod 2^16, hi += w >> 16 (fire-and-forget shared
-// atomics).  A work item adds at most item_cap <= 65535 records to a cell,
-// so neither word can overflow; the cell is hi 2^16 + lo.
+// Accumulate records [r0, r1) of one source bucket into this tile's cells.
+// The bucket is (neighbour tile t - o, face mask m ⊇ o): along axis k its
+// records' corners at offset 1 land here if o has axis k (the base is the
+// neighbour's last row), only those at offset 0 if m has axis k but o not
+// (the offset-1 corner belongs to the next tile), and both otherwise.  So
+// the corners to add are the same for every record of the bucket (mask cm)
+// and land inside the tile; a corner beyond the grid's last node has weight
+// 0 and is skipped with every other zero weight.  A weight w <= 2^32 is
+// added as two parts into separate 32-bit words, lo += w mod 2^16 and
+// hi += w >> 16 (shared 32-bit atomics run about six times faster than
+// 64-bit ones).  A work item adds at most item_cap <= 65535 records to a
+// cell, so neither word can overflow; the cell is hi 2^16 + lo.
 template <int D>
 __device__ __forceinline__ void accumulate(const uint4* __restrict__ recs, unsigned r0, unsigned r1,
-                                           int nbt, const int* tc, const TileGeom& g,
-                                           unsigned* acc_lo, unsigned* acc_hi) {
+                                           int o, int m, const TileGeom& g, unsigned* acc_lo,
+                                           unsigned* acc_hi) {
   constexpr int B = LocalBits<D>::value;
   const unsigned lmask = B == 32 ? 0xffffffffu : ((1u << B) - 1u);
-  int nb[KDE_MAX_D];
-  tile_coords<D>(nbt, g, nb);
-  int shift[KDE_MAX_D];
+  int cm = 0;
 #pragma unroll
-  for (int k = 0; k < D; ++k) shift[k] = (nb[k] - tc[k]) * g.tile[k];
+  for (int c = 0; c < (1 << D); ++c) {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int bit = D - 1 - k, ck = (c >> bit) & 1;
+      if ((o >> bit) & 1) ok &= ck == 1;
+      else if ((m >> bit) & 1) ok &= ck == 0;
+    }
+    cm |= (int)ok << c;
+  }
+  // tile-local index of corner c of a record whose base is at local index 0
+  // of its own tile: the base shifts by -tile along every axis of o
+  int cstride[KDE_MAX_D];
+  int shift = 0;
+  {
+    int st = 1;
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k) {
+      cstride[k] = st;
+      if ((o >> (D - 1 - k)) & 1) shift -= g.tile[k] * st;
+      st *= g.tile[k];
+    }
+  }
+  const unsigned cells = (unsigned)g.tile_cells;
   for (unsigned r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     const uint4 rec = recs[r];
     const unsigned q[3] = {rec.y, rec.z, rec.w};
-    int rel[KDE_MAX_D];  // base node relative to this tile's first node
+    int base = shift;
 #pragma unroll
-    for (int k = 0; k < D; ++k) rel[k] = (int)((rec.x >> (B * k)) & lmask) + shift[k];
+    for (int k = 0; k < D; ++k) base += (int)((rec.x >> (B * k)) & lmask) * cstride[k];
     unsigned long long w[1 << D];
     corner_weights<D>(q, w);
 #pragma unroll
     for (int c = 0; c < (1 << D); ++c) {
-      if (w[c] == 0) continue;
-      bool inside = true;
-      int lidx = 0;
+      if (!((cm >> c) & 1)) continue;
+      int lidx = base;
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        int x = rel[k] + ((c >> (D - 1 - k)) & 1);
-        inside &= (x >= 0) && (x < g.tile[k]);
-        lidx = lidx * g.tile[k] + x;
-      }
-      if (inside) {
-        const unsigned wl = (unsigned)w[c] & 0xffffu, wh = (unsigned)(w[c] >> 16);
+      for (int k = 0; k < D; ++k)
+        if ((c >> (D - 1 - k)) & 1) lidx += cstride[k];
+      const unsigned wl = (unsigned)w[c] & 0xffffu, wh = (unsigned)(w[c] >> 16);
+      if ((unsigned)lidx < cells) {
         if (wl) atomicAdd(&acc_lo[lidx], wl);
         if (wh) atomicAdd(&acc_hi[lidx], wh);
       }
@@ -547,10 +582,11 @@ kde_bin_gather_kernel(const uint4* __restrict__ recs, const unsigned* __restrict
   __syncthreads();
   const unsigned w0 = j * (unsigned)g.item_cap, w1 = w0 + (unsigned)g.item_cap;
   unsigned v = 0;  // running record number
-  for_each_source<D>(tc, g, [&](int nbt, int, int key) {
+  for_each_source<D>(tc, g, [&](int, int o, int key) {
     const unsigned a = starts[key], len = starts[key + 1] - a;
     const unsigned lo_v = max(v, w0), hi_v = min(v + len, w1);
-    if (lo_v < hi_v) accumulate<D>(recs, a + (lo_v - v), a + (hi_v - v), nbt, tc, g, acc_lo, acc_hi);
+    if (lo_v < hi_v)
+      accumulate<D>(recs, a + (lo_v - v), a + (hi_v - v), o, key & ((1 << D) - 1), g, acc_lo, acc_hi);
     v += len;
   });
   __syncthreads();
@@ -560,26 +596,11 @@ kde_bin_gather_kernel(const uint4* __restrict__ recs, const unsigned* __restrict
   if (items == 1) {
     store_tile<D>(tc, g, threadIdx.x, blockDim.x, counts, cell);
   } else {
-    int64_t lo[KDE_MAX_D], ext[KDE_MAX_D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      lo[k] = (int64_t)tc[k] * g.tile[k];
-      ext[k] = min((int64_t)g.tile[k], g.M[k] - lo[k]);
-    }
     for (int c = threadIdx.x; c < g.tile_cells; c += blockDim.x) {
       const unsigned long long v = cell(c);
       if (!v) continue;
-      int r = c;
-      int64_t off = 0;
-      bool in = true;
-#pragma unroll
-      for (int k = D - 1; k >= 0; --k) {
-        int x = r % g.tile[k];
-        r /= g.tile[k];
-        in &= x < ext[k];
-        off += (lo[k] + x) * g.stride[k];
-      }
-      if (in) atomicAdd(counts + off, v);
+      const int64_t off = tile_cell_offset<D>(tc, g, c);
+      if (off >= 0) atomicAdd(counts + off, v);
     }
   }
 }
@@ -617,10 +638,26 @@ struct TiledLayout {
   size_t off_mat, off_tot, off_starts, off_items, off_recs, total;
 };
 
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+  }
+  return sms;
+}
+
 bool tiled_layout(int64_t n, int d, const int64_t* M, TiledLayout* t) {
   if (!choose_tiles(d, M, t->tile, t->ntiles, &t->nkeys)) return false;
+  // chunks of at least 4096 samples, at most one resident wave of
+  // histogram blocks (their shared key histograms bound the blocks per SM)
+  const int64_t per_sm = std::max<int64_t>(
+      1, std::min<int64_t>(2048 / kHistThreads, (int64_t)(200 * 1024) / ((int64_t)t->nkeys * 4)));
+  const int64_t cap = std::min<int64_t>(kMaxBlocks, per_sm * num_sms());
   int64_t nb = (n + 4095) / 4096;
-  t->nblocks = (int)(nb < 1 ? 1 : (nb > kMaxBlocks ? kMaxBlocks : nb));
+  t->nblocks = (int)(nb < 1 ? 1 : (nb > cap ? cap : nb));
   t->chunk = (n + t->nblocks - 1) / t->nblocks;
   t->tile_cells = 1;
   t->ntiles_total = 1;
@@ -669,16 +706,6 @@ BinParams<T> make_params(int d, const double* lo, const double* hi, const int64_
   return p;
 }
 
-int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-      sms = 152;
-  }
-  return sms;
-}
 
 template <typename T>
 kde_status launch_direct(const T* X, int64_t n, int d, const double* lo, const double* hi,
@@ -723,6 +750,7 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
     g.M[k] = M[k];
     g.stride[k] = p.ax[k].stride;
     g.tile[k] = t.tile[k];
+    g.tile_log2[k] = p.ax[k].tile_log2;
     g.ntiles[k] = t.ntiles[k];
     g.tstride[k] = p.ax[k].tstride;
   }
@@ -740,14 +768,19 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
   }
   {
     const size_t smem = (size_t)t.nblocks * (kScanKeys + 1) * 4;
+    if ((e = allow_smem(kde_bin_scan_blocks_kernel, smem)) != cudaSuccess)
+      return kde::cuda_fail(e, "smem attr");
     kde::LaunchScope ls("kde_bin_scan_blocks_kernel", stream);
     kde_bin_scan_blocks_kernel<<<(t.nkeys + kScanKeys - 1) / kScanKeys, kScanKeys * kScanSegs, smem,
                                  stream>>>(mat, t.nblocks, t.nkeys, tot);
     if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scan_blocks_kernel");
   }
   {
+    auto* fn = kde_bin_scan_keys_kernel<D>;
+    const size_t ssmem = (size_t)(t.nkeys + 1) * 4;
+    if ((e = allow_smem(fn, ssmem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
     kde::LaunchScope ls("kde_bin_scan_keys_kernel", stream);
-    kde_bin_scan_keys_kernel<D><<<1, 1024, 0, stream>>>(tot, t.nkeys, g, starts, item_start);
+    fn<<<1, 1024, ssmem, stream>>>(tot, t.nkeys, g, starts, item_start);
     if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scan_keys_kernel");
   }
   {
