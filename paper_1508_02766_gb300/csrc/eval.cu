@@ -2043,7 +2043,11 @@ __global__ void __launch_bounds__(256) kde_batch_bin_kernel(BatchArgs<T> a) {
     const BatchItem<T>& B = a.items[it];
     const int64_t c0 = (int64_t)(w - wst[it]) * kBinChunk;
     const int64_t c1 = min(B.n, c0 + kBinChunk);
-    for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+    // two adjacent lanes per sample: lane parity p adds the corners at
+    // offset p along the last axis, so a lane pair's two words share a
+    // 32-byte sector three times in four and coalesce into one request
+    const int par = threadIdx.x & 1;
+    for (int64_t j = c0 + (threadIdx.x >> 1); j < c1; j += blockDim.x >> 1) {
     const int64_t s = B.x_off + j;
     int i[2];
     unsigned q[2];
@@ -2056,12 +2060,11 @@ __global__ void __launch_bounds__(256) kde_batch_bin_kernel(BatchArgs<T> a) {
     if (!in) continue;
     unsigned long long wt[4];
     lite_corner_weights2(q, wt);
+    const unsigned long long w0 = par ? wt[1] : wt[0], w1 = par ? wt[3] : wt[2];
     unsigned long long* c = reinterpret_cast<unsigned long long*>(a.counts + B.counts_off);
-    const int64_t base = (int64_t)i[0] * B.M[1] + i[1];
-    if (wt[0]) atomicAdd(c + base, wt[0]);
-    if (wt[1]) atomicAdd(c + base + 1, wt[1]);
-    if (wt[2]) atomicAdd(c + base + B.M[1], wt[2]);
-    if (wt[3]) atomicAdd(c + base + B.M[1] + 1, wt[3]);
+    const int64_t base = (int64_t)i[0] * B.M[1] + i[1] + par;
+    if (w0) atomicAdd(c + base, w0);
+    if (w1) atomicAdd(c + base + B.M[1], w1);
     }
   }
 }

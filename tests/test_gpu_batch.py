@@ -92,3 +92,30 @@ def test_ragged64_against_single_problem_path_and_tuner(K):
         Xd = torch.from_numpy(np.ascontiguousarray(w.X)).cuda()
         single, _, _ = K.kde_eval(Xd, w.H, w.lo, w.hi, w.M, precision="f32")
         assert rel_err(g, single.cpu().numpy()) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_samples_on_grid_edges_and_outside(K, prec):
+    """Samples exactly on the grid's edges and corners (a node of the last
+    row or column: its far corners have weight 0) and outside the grid
+    (dropped; in FP32 an edge sample may round outside, as in the oracle),
+    in a batch of three grids, against the oracle."""
+    import dataclasses
+    problems = []
+    for i, M in enumerate([(17, 23), (40, 9), (64, 64)]):
+        w = W.small_case(400 + i, 2, M, n=500, precision=prec)
+        lo, hi = np.asarray(w.lo, dtype=np.float64), np.asarray(w.hi, dtype=np.float64)
+        t = np.linspace(0.0, 1.0, 7)
+        edge = np.concatenate([
+            np.stack([np.full(7, hi[0]), lo[1] + t * (hi[1] - lo[1])], 1),
+            np.stack([lo[0] + t * (hi[0] - lo[0]), np.full(7, hi[1])], 1),
+            np.array([[lo[0], lo[1]], [hi[0], hi[1]], [lo[0], hi[1]], [hi[0], lo[1]]]),
+            np.array([[hi[0] + 1.0, 0.5 * (lo[1] + hi[1])], [lo[0] - 1.0, lo[1] - 1.0]]),
+        ])
+        X = np.concatenate([w.X.astype(np.float64), edge]).astype(w.X.dtype)
+        problems.append(dataclasses.replace(w, X=X))
+    dens, _, _ = run_batch(K, problems, prec)
+    for w, g in zip(problems, dens):
+        f, _, _, n_out = O.binned_estimate(w.X, w.H, w.lo, w.hi, w.M, tau=w.tau)
+        assert n_out >= 2
+        assert rel_err(g, f) <= TOL[prec]
