@@ -39,6 +39,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--bin-method", default="auto", choices=["auto", "direct", "tiled"])
+    ap.add_argument("--range", default="corrected", choices=["corrected", "per_axis"],
+                    help="support of the kernel grid: the corrected range of Eq. 15 or the "
+                         "per-axis (diagonal) range")
+    ap.add_argument("--layout", default="corrected", choices=["corrected", "wand"],
+                    help="kernel-grid layout: corrected (all signed lags) or Wand's (k_|l|)")
     ap.add_argument("--dft", default="fft", choices=["fft", "tc"],
                     help="first pass: mixed-radix FFT, or split-TF32 DFT matrix on the tensor cores")
     ap.add_argument("--lscv", default="autocorr", choices=["autocorr", "spectrum"],
@@ -227,6 +232,8 @@ from oracle import kde_oracle as O
 from paper_1508_02766_gb300 import workloads as W
 name, n_bin, n_nodes, seed = sys.argv[2], int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[5])
 nodes_file = sys.argv[6] if len(sys.argv) > 6 else ""
+range_mode = sys.argv[7] if len(sys.argv) > 7 else "corrected"
+layout = sys.argv[8] if len(sys.argv) > 8 else "corrected"
 w = W.WORKLOADS[name]()
 rng = np.random.default_rng(seed)
 sub = w.X[rng.choice(w.n, size=min(n_bin, w.n), replace=False)]
@@ -234,8 +241,8 @@ t0 = time.perf_counter()
 counts_sub, _ = O.bin_linear(sub, w.lo, w.hi, w.M)
 t_bin = time.perf_counter() - t0
 counts, _ = O.bin_linear(w.X, w.lo, w.hi, w.M)
-L = O.support_L(w.H, w.lo, w.hi, w.M, w.tau)
-k = O.kernel_weights(w.H, w.lo, w.hi, w.M, L, w.n)
+L = O.support_L(w.H, w.lo, w.hi, w.M, w.tau, range_mode)
+k = O.kernel_weights(w.H, w.lo, w.hi, w.M, L, w.n, layout)
 nodes = np.stack([rng.integers(0, m, n_nodes) for m in w.M], axis=1)
 t0 = time.perf_counter()
 ref = O.binned_direct_at(O.counts_to_c(counts), k, L, nodes)
@@ -251,12 +258,13 @@ print(json.dumps(out))
 """
 
 
-def run_cpu_oracle(workload, n_bin, n_nodes, seed=0, nodes_file=""):
+def run_cpu_oracle(workload, n_bin, n_nodes, seed=0, nodes_file="", range_mode="corrected",
+                   layout="corrected"):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
     cmd = [sys.executable, "-c", CPU_BASELINE_CODE, ROOT, workload, str(n_bin), str(n_nodes),
-           str(seed)] + ([nodes_file] if nodes_file else [])
+           str(seed), nodes_file, range_mode, layout]
     r = subprocess.run(cmd, capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
@@ -331,7 +339,8 @@ def main():
 
     w = W.WORKLOADS[args.workload]()
     stream = torch.cuda.Stream(device=dev)
-    plan = kde.Plan(w.M, w.lo, w.hi, w.H, precision=w.precision, tau=w.tau, dft=args.dft)
+    plan = kde.Plan(w.M, w.lo, w.hi, w.H, precision=w.precision, tau=w.tau, dft=args.dft,
+                    range_mode=args.range, layout=args.layout)
     info = plan.info
     X_host = torch.from_numpy(np.ascontiguousarray(w.X)).pin_memory()
     X = X_host.to(dev)
@@ -516,7 +525,7 @@ def main():
                        "l2": "flushed between timed steps (256 MB write)",
                        "launch": "CUDA graph replay per step" if graph is not None else "stream launches",
                        "streams": "kernel grid on a side stream, concurrent with binning",
-                       "binning": method,
+                       "binning": method, "range": args.range, "layout": args.layout,
                        "first_pass": "split-TF32 DFT matrix on the tensor cores" if args.dft == "tc"
                        else "mixed-radix FFT",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -534,7 +543,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_bin, n_nodes = CPU_SAMPLE[args.workload]
         tmp = tempfile.mktemp(prefix="kde_nodes_")
-        r = run_cpu_oracle(args.workload, n_bin, n_nodes, seed=123, nodes_file=tmp)
+        r = run_cpu_oracle(args.workload, n_bin, n_nodes, seed=123, nodes_file=tmp,
+                           range_mode=args.range, layout=args.layout)
         nodes = np.load(tmp + ".nodes.npy")
         ref = np.load(tmp + ".ref.npy")
         for suf in (".nodes.npy", ".ref.npy"):
@@ -550,6 +560,19 @@ def main():
                        f"extrapolated to the full workload")}
         line["accuracy"] = {"max_rel_err_vs_oracle_sampled": float(
             np.max(np.abs(got - ref)) / np.max(np.abs(ref))), "nodes": int(len(ref))}
+    if rank == 0 and (args.range != "corrected" or args.layout != "corrected"):
+        # what the per-axis range or Wand's layout changes: this estimate
+        # against the corrected one from the same counts (Sec. 4.2, Fig. 1)
+        pc = kde.Plan(w.M, w.lo, w.hi, w.H, precision=w.precision, tau=w.tau)
+        wsc = pc.workspace(dev)
+        with torch.cuda.stream(stream):
+            enqueue(step_dev)
+            Kc = kde.kde_kernel_grid(pc, w.n, workspace=wsc)
+            dc = kde.kde_fft_eval(pc, counts, Kc, workspace=wsc)
+        torch.cuda.synchronize()
+        line["vs_corrected"] = {
+            "max_rel_diff": float((dens - dc).abs().max() / dc.abs().max()),
+            "L": list(info.L), "L_corrected": list(pc.info.L)}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
