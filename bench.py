@@ -44,6 +44,9 @@ def parse():
                          "per-axis (diagonal) range")
     ap.add_argument("--layout", default="corrected", choices=["corrected", "wand"],
                     help="kernel-grid layout: corrected (all signed lags) or Wand's (k_|l|)")
+    ap.add_argument("--P-min", type=int, nargs="*", default=None,
+                    help="smallest padded length per axis (the plan takes the smallest "
+                         "7-smooth size at or above it and at or above M + L)")
     ap.add_argument("--dft", default="fft", choices=["fft", "tc"],
                     help="first pass: mixed-radix FFT, or split-TF32 DFT matrix on the tensor cores")
     ap.add_argument("--lscv", default="autocorr", choices=["autocorr", "spectrum"],
@@ -340,7 +343,7 @@ def main():
     w = W.WORKLOADS[args.workload]()
     stream = torch.cuda.Stream(device=dev)
     plan = kde.Plan(w.M, w.lo, w.hi, w.H, precision=w.precision, tau=w.tau, dft=args.dft,
-                    range_mode=args.range, layout=args.layout)
+                    range_mode=args.range, layout=args.layout, P_min=args.P_min)
     info = plan.info
     X_host = torch.from_numpy(np.ascontiguousarray(w.X)).pin_memory()
     X = X_host.to(dev)
