@@ -193,13 +193,12 @@ template <int D> struct LocalBits { static constexpr int value = D == 1 ? 32 : (
 // last node of its tile along axis k (and not the grid's last node): the
 // sample then also feeds the next tile along k.
 template <typename T, int D>
-__device__ __forceinline__ bool sample_key(const T* __restrict__ X, int64_t s, const BinParams<T>& p,
-                                           int& key, uint4& rec) {
+__device__ __forceinline__ bool sample_key(const T* x, const BinParams<T>& p, int& key, uint4& rec) {
   int i[D];
   unsigned q[3] = {0, 0, 0};
   bool in = true;
 #pragma unroll
-  for (int k = 0; k < D; ++k) in &= axis_position<T>(X[s * D + k], p.ax[k], i[k], q[k]);
+  for (int k = 0; k < D; ++k) in &= axis_position<T>(x[k], p.ax[k], i[k], q[k]);
   if (!in) return false;
   int tile = 0, mask = 0;
   unsigned local = 0;
@@ -218,6 +217,18 @@ __device__ __forceinline__ bool sample_key(const T* __restrict__ X, int64_t s, c
 
 constexpr int kUnroll = 4;
 
+// Coordinates of samples base + u blockDim (u < kUnroll) that lie below s1.
+template <typename T, int D>
+__device__ __forceinline__ void load_samples(const T* __restrict__ X, int64_t base, int64_t s1,
+                                             T (&x)[kUnroll][D]) {
+#pragma unroll
+  for (int u = 0; u < kUnroll; ++u) {
+    const int64_t s = base + u * (int64_t)blockDim.x;
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[u][k] = s < s1 ? X[s * D + k] : T(0);
+  }
+}
+
 template <typename T, int D>
 __global__ void __launch_bounds__(kHistThreads)
 kde_bin_hist_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, int nkeys, BinParams<T> p,
@@ -228,19 +239,27 @@ kde_bin_hist_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, int nkeys
   const int64_t s0 = (int64_t)blockIdx.x * chunk;
   const int64_t s1 = min(n, s0 + chunk);
   unsigned long long outside = 0;
+  // the next iteration's samples are loaded before this one's are keyed
+  T xc[kUnroll][D], xn[kUnroll][D];
+  load_samples<T, D>(X, s0 + threadIdx.x, s1, xc);
   for (int64_t base = s0 + threadIdx.x; base < s1; base += kUnroll * (int64_t)blockDim.x) {
+    load_samples<T, D>(X, base + kUnroll * (int64_t)blockDim.x, s1, xn);
     int key[kUnroll];
     bool in[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int64_t s = base + u * (int64_t)blockDim.x;
       uint4 rec;
-      in[u] = s < s1 && sample_key<T, D>(X, s, p, key[u], rec);
+      in[u] = s < s1 && sample_key<T, D>(xc[u], p, key[u], rec);
       if (s < s1 && !in[u]) ++outside;
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u)
       if (in[u]) atomicAdd(&hist[key[u]], 1u);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+      for (int k = 0; k < D; ++k) xc[u][k] = xn[u][k];
   }
   __syncthreads();
   unsigned* row = mat + (int64_t)blockIdx.x * nkeys;
@@ -264,9 +283,21 @@ kde_bin_scan_blocks_kernel(unsigned* __restrict__ mat, int nblocks, int nkeys,
   __shared__ unsigned seg_sum[kScanSegs][kScanKeys];
   const int k0 = blockIdx.x * kScanKeys;
   const int W = kScanKeys + 1;
-  for (int idx = threadIdx.x; idx < nblocks * kScanKeys; idx += blockDim.x) {
-    int b = idx / kScanKeys, c = idx % kScanKeys;
-    slab[b * W + c] = (k0 + c < nkeys) ? mat[(int64_t)b * nkeys + k0 + c] : 0u;
+  // eight independent loads in flight per thread before their shared stores
+  constexpr int kBatch = 8;
+  for (int idx0 = threadIdx.x; idx0 < nblocks * kScanKeys; idx0 += kBatch * blockDim.x) {
+    unsigned v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      const int b = idx / kScanKeys, c = idx % kScanKeys;
+      v[u] = (idx < nblocks * kScanKeys && k0 + c < nkeys) ? mat[(int64_t)b * nkeys + k0 + c] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      if (idx < nblocks * kScanKeys) slab[(idx / kScanKeys) * W + idx % kScanKeys] = v[u];
+    }
   }
   __syncthreads();
   const int c = threadIdx.x % kScanKeys, sg = threadIdx.x / kScanKeys;
@@ -292,36 +323,6 @@ kde_bin_scan_blocks_kernel(unsigned* __restrict__ mat, int nblocks, int nkeys,
     int b = idx / kScanKeys, cc = idx % kScanKeys;
     if (k0 + cc < nkeys) mat[(int64_t)b * nkeys + k0 + cc] = slab[b * W + cc];
   }
-}
-
-// Exclusive scan of one value per thread over the block; returns the
-// thread's exclusive prefix and writes the block total to *total.
-__device__ unsigned block_scan_excl(unsigned v, unsigned* warp_sums, unsigned* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned incl = v;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += y;
-  }
-  __syncthreads();
-  if (lane == 31) warp_sums[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    unsigned w = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0u;
-    unsigned inc = w;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
-      if (lane >= off) inc += y;
-    }
-    warp_sums[lane] = inc - w;
-    if (lane == 31) warp_sums[32] = inc;
-  }
-  __syncthreads();
-  unsigned r = warp_sums[warp] + incl - v;
-  *total = warp_sums[32];
-  return r;
 }
 
 struct TileGeom {
@@ -366,56 +367,78 @@ __device__ __forceinline__ void for_each_source(const int* tc, const TileGeom& g
   }
 }
 
+// Exclusive prefix of v[0, n) into out[0, n) and the total into out[n],
+// by the whole block: each warp scans a contiguous segment 32 values at a
+// time (coalesced, no bank conflicts), after an exclusive scan of the
+// segments' totals.  v and out may live in global or shared memory.
+__device__ void block_segment_scan(const unsigned* v, int n, unsigned* out, unsigned* warp_sums) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int seg = (n + nw - 1) / nw;
+  const int k0 = min(n, warp * seg), k1 = min(n, k0 + seg);
+  unsigned sum = 0;
+  for (int k = k0 + lane; k < k1; k += 32) sum += v[k];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  __syncthreads();
+  if (lane == 0) warp_sums[warp] = sum;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned x = lane < nw ? warp_sums[lane] : 0u;
+    unsigned inc = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    warp_sums[lane] = inc - x;
+    if (lane == 31) warp_sums[32] = inc;
+  }
+  __syncthreads();
+  unsigned carry = warp_sums[warp];
+  for (int kb = k0; kb < k1; kb += 32) {
+    const int k = kb + lane;
+    const unsigned x = k < k1 ? v[k] : 0u;
+    unsigned inc = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += y;
+    }
+    if (k < k1) out[k] = carry + inc - x;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (threadIdx.x == 0) out[n] = warp_sums[32];
+  __syncthreads();
+}
+
 // One block: starts[key] = exclusive prefix of key totals (starts[nkeys] =
 // all records); per tile the records feeding it (own plus neighbours' face
 // records), its number of work items (ceil(records / cap), at least 1) and
-// the exclusive prefix of items over tiles (item_start[ntiles] = all items).
-// The prefix is built in shared memory (nkeys + 1 words), where the per-tile
-// sums read it back.
+// the exclusive prefix of items over tiles (item_start[ntiles] = all
+// items).  The per-tile sums read a mask-major copy of the totals in shared
+// memory, so the lanes of a warp (consecutive tiles) read consecutive words.
 template <int D>
 __global__ void __launch_bounds__(1024)
 kde_bin_scan_keys_kernel(const unsigned* __restrict__ totals, int nkeys, TileGeom g,
                          unsigned* __restrict__ starts, unsigned* __restrict__ item_start) {
-  extern __shared__ unsigned s_starts[];
+  extern __shared__ unsigned smem_scan[];
   __shared__ unsigned warp_sums[33];
-  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) s_starts[k] = totals[k];
-  __syncthreads();
-  unsigned total;
-  {
-    const int per = (nkeys + blockDim.x - 1) / blockDim.x;
-    const int k0 = min(nkeys, (int)threadIdx.x * per);
-    const int k1 = min(nkeys, k0 + per);
-    unsigned local = 0;
-    for (int k = k0; k < k1; ++k) local += s_starts[k];
-    unsigned run = block_scan_excl(local, warp_sums, &total);
-    for (int k = k0; k < k1; ++k) {
-      const unsigned v = s_starts[k];
-      s_starts[k] = run;
-      run += v;
-    }
-    if (threadIdx.x == 0) s_starts[nkeys] = total;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k <= nkeys; k += blockDim.x) starts[k] = s_starts[k];
-  const int ntiles = g.ntiles_total;
-  const int per = (ntiles + blockDim.x - 1) / blockDim.x;
-  const int t0 = min(ntiles, (int)threadIdx.x * per);
-  const int t1 = min(ntiles, t0 + per);
-  auto items_of = [&](int t) {
+  const int ntiles = g.ntiles_total, nm = 1 << D;
+  unsigned* s_tot = smem_scan;            // [mask][tile]
+  unsigned* s_items = smem_scan + nkeys;  // [tile]
+  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) s_tot[(k & (nm - 1)) * ntiles + (k >> D)] = totals[k];
+  block_segment_scan(totals, nkeys, starts, warp_sums);
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
     int tc[KDE_MAX_D];
     tile_coords<D>(t, g, tc);
     unsigned recs = 0;
-    for_each_source<D>(tc, g, [&](int, int, int key) { recs += s_starts[key + 1] - s_starts[key]; });
-    return recs == 0 ? 1u : (recs + g.item_cap - 1) / g.item_cap;
-  };
-  unsigned li = 0;
-  for (int t = t0; t < t1; ++t) li += items_of(t);
-  unsigned ri = block_scan_excl(li, warp_sums, &total);
-  if (threadIdx.x == 0) item_start[ntiles] = total;
-  for (int t = t0; t < t1; ++t) {
-    item_start[t] = ri;
-    ri += items_of(t);
+    for_each_source<D>(tc, g, [&](int nbt, int, int key) {
+      recs += s_tot[(key & (nm - 1)) * ntiles + nbt];
+    });
+    s_items[t] = recs == 0 ? 1u : (recs + g.item_cap - 1) / g.item_cap;
   }
+  __syncthreads();
+  block_segment_scan(s_items, ntiles, item_start, warp_sums);
 }
 
 template <typename T, int D>
@@ -429,18 +452,25 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, int nk
   __syncthreads();
   const int64_t s0 = (int64_t)blockIdx.x * chunk;
   const int64_t s1 = min(n, s0 + chunk);
+  T xc[kUnroll][D], xn[kUnroll][D];
+  load_samples<T, D>(X, s0 + threadIdx.x, s1, xc);
   for (int64_t base = s0 + threadIdx.x; base < s1; base += kUnroll * (int64_t)blockDim.x) {
+    load_samples<T, D>(X, base + kUnroll * (int64_t)blockDim.x, s1, xn);
     int key[kUnroll];
     uint4 rec[kUnroll];
     bool in[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int64_t s = base + u * (int64_t)blockDim.x;
-      in[u] = s < s1 && sample_key<T, D>(X, s, p, key[u], rec[u]);
+      in[u] = s < s1 && sample_key<T, D>(xc[u], p, key[u], rec[u]);
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u)
       if (in[u]) recs[atomicAdd(&cursor[key[u]], 1u)] = rec[u];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+      for (int k = 0; k < D; ++k) xc[u][k] = xn[u][k];
   }
 }
 
@@ -483,12 +513,72 @@ __device__ __forceinline__ void store_tile(const int* tc, const TileGeom& g, int
 // hi += w >> 16 (shared 32-bit atomics run about six times faster than
 // 64-bit ones).  A work item adds at most item_cap <= 65535 records to a
 // cell, so neither word can overflow; the cell is hi 2^16 + lo.
+// One record's corners (those in cm) added into the tile's two accumulator
+// words per cell; base is the record's base node as a tile-local index.
+template <int D, bool ALL>
+__device__ __forceinline__ void add_record(const uint4& rec, int base, int cm, const int* cstride,
+                                           unsigned cells, unsigned* acc_lo, unsigned* acc_hi) {
+  const unsigned q[3] = {rec.y, rec.z, rec.w};
+  unsigned long long w[1 << D];
+  corner_weights<D>(q, w);
+#pragma unroll
+  for (int c = 0; c < (1 << D); ++c) {
+    if (!ALL && !((cm >> c) & 1)) continue;
+    int lidx = base;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if ((c >> (D - 1 - k)) & 1) lidx += cstride[k];
+    const unsigned wl = (unsigned)w[c] & 0xffffu, wh = (unsigned)(w[c] >> 16);
+    if ((unsigned)lidx < cells) {
+      if (wl) atomicAdd(&acc_lo[lidx], wl);
+      if (wh) atomicAdd(&acc_hi[lidx], wh);
+    }
+  }
+}
+
+// Records [r0, r1) of one bucket, one per thread per iteration, the next
+// record's load issued before the current one is added.
+template <int D, bool ALL>
+__device__ __forceinline__ void add_records(const uint4* __restrict__ recs, unsigned r0, unsigned r1,
+                                            int shift, int cm, const int* cstride, unsigned cells,
+                                            unsigned* acc_lo, unsigned* acc_hi) {
+  constexpr int B = LocalBits<D>::value;
+  const unsigned lmask = B == 32 ? 0xffffffffu : ((1u << B) - 1u);
+  unsigned r = r0 + threadIdx.x;
+  if (r >= r1) return;
+  uint4 cur = recs[r];
+  for (;;) {
+    const unsigned rn = r + blockDim.x;
+    uint4 nxt;
+    if (rn < r1) nxt = recs[rn];
+    int base = shift;
+#pragma unroll
+    for (int k = 0; k < D; ++k) base += (int)((cur.x >> (B * k)) & lmask) * cstride[k];
+    add_record<D, ALL>(cur, base, cm, cstride, cells, acc_lo, acc_hi);
+    if (rn >= r1) break;
+    cur = nxt;
+    r = rn;
+  }
+}
+
+// Accumulate records [r0, r1) of one source bucket into this tile's cells.
+// The bucket is (neighbour tile t - o, face mask m ⊇ o): along axis k its
+// records' corners at offset 1 land here if o has axis k (the base is the
+// neighbour's last row), only those at offset 0 if m has axis k but o not
+// (the offset-1 corner belongs to the next tile), and both otherwise.  So
+// the corners to add are the same for every record of the bucket (mask cm)
+// and land inside the tile; a corner beyond the grid's last node has weight
+// 0 and is skipped with every other zero weight.  Own records off every face
+// (o = m = 0, nearly all of them) take all corners with no mask test.  A
+// weight w <= 2^32 is added as two parts into separate 32-bit words,
+// lo += w mod 2^16 and hi += w >> 16 (shared 32-bit atomics run about six
+// times faster than 64-bit ones).  A work item adds at most
+// item_cap <= 65535 records to a cell, so neither word can overflow; the
+// cell is hi 2^16 + lo.
 template <int D>
 __device__ __forceinline__ void accumulate(const uint4* __restrict__ recs, unsigned r0, unsigned r1,
                                            int o, int m, const TileGeom& g, unsigned* acc_lo,
                                            unsigned* acc_hi) {
-  constexpr int B = LocalBits<D>::value;
-  const unsigned lmask = B == 32 ? 0xffffffffu : ((1u << B) - 1u);
   int cm = 0;
 #pragma unroll
   for (int c = 0; c < (1 << D); ++c) {
@@ -501,8 +591,7 @@ __device__ __forceinline__ void accumulate(const uint4* __restrict__ recs, unsig
     }
     cm |= (int)ok << c;
   }
-  // tile-local index of corner c of a record whose base is at local index 0
-  // of its own tile: the base shifts by -tile along every axis of o
+  // tile-local index strides; the base shifts by -tile along every axis of o
   int cstride[KDE_MAX_D];
   int shift = 0;
   {
@@ -515,28 +604,10 @@ __device__ __forceinline__ void accumulate(const uint4* __restrict__ recs, unsig
     }
   }
   const unsigned cells = (unsigned)g.tile_cells;
-  for (unsigned r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    const uint4 rec = recs[r];
-    const unsigned q[3] = {rec.y, rec.z, rec.w};
-    int base = shift;
-#pragma unroll
-    for (int k = 0; k < D; ++k) base += (int)((rec.x >> (B * k)) & lmask) * cstride[k];
-    unsigned long long w[1 << D];
-    corner_weights<D>(q, w);
-#pragma unroll
-    for (int c = 0; c < (1 << D); ++c) {
-      if (!((cm >> c) & 1)) continue;
-      int lidx = base;
-#pragma unroll
-      for (int k = 0; k < D; ++k)
-        if ((c >> (D - 1 - k)) & 1) lidx += cstride[k];
-      const unsigned wl = (unsigned)w[c] & 0xffffu, wh = (unsigned)(w[c] >> 16);
-      if ((unsigned)lidx < cells) {
-        if (wl) atomicAdd(&acc_lo[lidx], wl);
-        if (wh) atomicAdd(&acc_hi[lidx], wh);
-      }
-    }
-  }
+  if (cm == (1 << (1 << D)) - 1)
+    add_records<D, true>(recs, r0, r1, shift, cm, cstride, cells, acc_lo, acc_hi);
+  else
+    add_records<D, false>(recs, r0, r1, shift, cm, cstride, cells, acc_lo, acc_hi);
 }
 
 // Zero the cells of tiles that are split into several work items (their
@@ -665,7 +736,10 @@ bool tiled_layout(int64_t n, int d, const int64_t* M, TiledLayout* t) {
     t->tile_cells *= t->tile[k];
     t->ntiles_total *= t->ntiles[k];
   }
-  t->item_cap = d == 3 ? 32768 : 16384;  // <= 65535 (accumulator bound)
+  // records per work item: about twice the tile's cells (each item zeroes
+  // and stores a whole tile; larger items leave the heaviest tiles to few
+  // blocks), at most 65535 (the accumulator bound)
+  t->item_cap = std::max(2048, std::min(65535, 2 * t->tile_cells));
   // A record feeds at most 2^d tiles: items <= tiles + 2^d n / cap.
   const int64_t feeds = (int64_t)n << d;
   t->max_items = t->ntiles_total + feeds / t->item_cap + 1;
@@ -777,7 +851,7 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
   }
   {
     auto* fn = kde_bin_scan_keys_kernel<D>;
-    const size_t ssmem = (size_t)(t.nkeys + 1) * 4;
+    const size_t ssmem = (size_t)(t.nkeys + t.ntiles_total) * 4;
     if ((e = allow_smem(fn, ssmem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
     kde::LaunchScope ls("kde_bin_scan_keys_kernel", stream);
     fn<<<1, 1024, ssmem, stream>>>(tot, t.nkeys, g, starts, item_start);
