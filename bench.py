@@ -444,11 +444,13 @@ def main():
     kde.profile_enable(False)
 
     # End to end through the public API with host buffers, as a stream of
-    # datasets: every step uploads its samples from pinned memory (copy
-    # stream), runs the three calls (compute stream; kernel grid beside the
-    # binning) and reads its density back to pinned memory (second copy
-    # stream).  Two sample and two density buffers let step i+1's upload and
-    # step i-1's read-back overlap step i's kernels.
+    # datasets.  One pipeline stage uploads the next step's samples from
+    # pinned memory (upload stream), runs this step's three calls (compute
+    # stream; kernel grid beside the binning) and reads the previous step's
+    # density back to pinned memory (read-back stream); two sample and two
+    # density buffers alternate between stages.  Each stage is captured once
+    # per buffer parity as a CUDA graph and replayed, one replay per step:
+    # every step still makes one upload, one evaluation and one read-back.
     e2e_steps = max(3, min(args.steps, 50))
     up_s = torch.cuda.Stream(device=dev)
     down_s = torch.cuda.Stream(device=dev)
@@ -457,46 +459,51 @@ def main():
     Hb = [dens_host, torch.empty(w.M, dtype=plan.real_dtype()).pin_memory()]
     paths = [step_e2e, kde.PreparedPath(plan, Xb[1], counts, Ks, Db[1], ws, bin_workspace=bws,
                                         stream=stream, kgen_stream=side)]
-    ev_up = [torch.cuda.Event() for _ in range(2)]
-    ev_binned = [torch.cuda.Event() for _ in range(2)]
-    ev_eval = [torch.cuda.Event() for _ in range(2)]
-    ev_down = [torch.cuda.Event() for _ in range(2)]
+    ev_fork, ev_up, ev_down = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+
+    def stage(b):
+        ev_fork.record(stream)
+        up_s.wait_event(ev_fork)
+        down_s.wait_event(ev_fork)
+        with torch.cuda.stream(up_s):
+            Xb[1 - b].copy_(X_host, non_blocking=True)        # next step's samples
+        with torch.cuda.stream(down_s):
+            Hb[1 - b].copy_(Db[1 - b], non_blocking=True)     # previous step's density
+        ev_up.record(up_s)
+        ev_down.record(down_s)
+        enqueue(paths[b])                                      # this step
+        stream.wait_event(ev_up)
+        stream.wait_event(ev_down)
+
+    with torch.cuda.stream(stream):
+        Xb[0].copy_(X_host, non_blocking=True)
+        for i in range(4):
+            stage(i % 2)
+    torch.cuda.synchronize()
+    stage_graphs = []
+    if graph is not None:
+        for b in range(2):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                stage(b)
+            stage_graphs.append(g)
+        torch.cuda.synchronize()
 
     def e2e_step(i):
-        b = i % 2
-        up_s.wait_event(ev_binned[b])        # step i-2 has binned from Xb[b]
-        with torch.cuda.stream(up_s):
-            Xb[b].copy_(X_host, non_blocking=True)
-        ev_up[b].record(up_s)
-        fork.record(stream)                  # the kernel grid needs no samples
-        side.wait_event(fork)
-        paths[b].kernel_grid()
-        stream.wait_event(ev_up[b])
-        paths[b].bin()
-        ev_binned[b].record(stream)
-        join.record(side)
-        stream.wait_event(join)
-        stream.wait_event(ev_down[b])        # step i-2's density has left Db[b]
-        paths[b].fft_eval()
-        ev_eval[b].record(stream)
-        down_s.wait_event(ev_eval[b])
-        with torch.cuda.stream(down_s):
-            Hb[b].copy_(Db[b], non_blocking=True)
-        ev_down[b].record(down_s)
+        if stage_graphs:
+            stage_graphs[i % 2].replay()
+        else:
+            stage(i % 2)
 
     e_s = torch.cuda.Event(enable_timing=True)
     e_e = torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
-        for i in range(4):
+        Xb[0].copy_(X_host, non_blocking=True)
+        for i in range(2):
             e2e_step(i)
-        torch.cuda.synchronize()
         e_s.record(stream)
-        up_s.wait_event(e_s)
-        down_s.wait_event(e_s)
         for i in range(e2e_steps):
             e2e_step(i)
-        stream.wait_event(ev_down[(e2e_steps - 1) % 2])
-        stream.wait_event(ev_down[e2e_steps % 2])
         e_e.record(stream)
     torch.cuda.synchronize()
     e2e_ms = rank_max(e_s.elapsed_time(e_e) / e2e_steps, dev)
@@ -538,7 +545,12 @@ def main():
             "gpu_launches": launches,
             "e2e": {"value": job_throughput(world, cells, e2e_ms), "unit": "grid points/s",
                     "overlap": "step i+1's upload and step i-1's read-back run beside step i's "
-                               "kernels (two sample and two density buffers, two copy streams)",
+                               "kernels (two sample and two density buffers, two copy streams, "
+                               "one captured graph per buffer parity, one replay per step)",
+                    "l2": "not flushed between the steps of the stream: every array a step "
+                          "reads is written within that step (its samples by its own upload; "
+                          "counts, kernel spectrum and spectra by its kernels); only the plan's "
+                          "twiddle tables persist",
                     "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(X.numel() * X.element_size()),
                     "d2h_bytes_per_step": int(dens.numel() * dens.element_size())},
             "clocks": clocks}
