@@ -237,6 +237,19 @@ kde_status kde_autocorrelation(kde_plan plan, const int64_t* counts, void* R, vo
 kde_status kde_lscv_autocorr(kde_plan plan, int64_t n, int nH, const double* H, const void* R,
                              double* pair_sums, double* lscv, void* workspace,
                              size_t workspace_bytes, kde_stream_t stream);
+/* The same for nsets datasets on one plan, each with its own candidates:
+ * R holds the sets' autocorrelations back to back (nsets x P_0 x P_1), n
+ * (host) the sets' sample counts, H (host) nsets x nH matrices (set-major),
+ * lscv and pair_sums (device; pair_sums may be NULL) nsets x nH and
+ * nsets x nH x 2 values.  Every candidate of every set goes into the same
+ * lag-sum launches (up to 1024 candidates each), so a batch of small
+ * candidate lists costs a few launches instead of two per set.  Same
+ * workspace and errors as kde_lscv_autocorr; nsets = 0 or nH = 0 does
+ * nothing.  (Batching over datasets has no counterpart in the paper.) */
+kde_status kde_lscv_autocorr_batch(kde_plan plan, int nsets, const int64_t* n, int nH,
+                                   const double* H, const void* R, double* pair_sums,
+                                   double* lscv, void* workspace, size_t workspace_bytes,
+                                   kde_stream_t stream);
 
 /* Ragged batches of independent 2-D problems (each with its own samples,
  * grid and bandwidth; Sec. 2 for each).  The batch runs as seven launches:

@@ -978,6 +978,7 @@ struct AcGen {
   int L0, L1, wand;
   int rpu;     // lag rows per work unit
   int u0, nu;  // this matrix's work units [u0, u0 + nu)
+  int set;     // whose autocorrelation: R + set * (P_0 P_1)
   T D0, D1, b_hi, b_lo, C;
 };
 
@@ -993,10 +994,12 @@ constexpr int kAcTerms = 4096;
 template <typename T>
 __global__ void __launch_bounds__(256) kde_lscv_ac_kernel(const AcGen<T>* __restrict__ gens,
                                                           const int2* __restrict__ units,
-                                                          const T* __restrict__ R, int P1,
+                                                          const T* __restrict__ Rall, int P1,
+                                                          int64_t set_stride,
                                                           double* __restrict__ partial) {
   const int2 u = units[blockIdx.x];
   const AcGen<T> g = gens[u.x];
+  const T* __restrict__ R = Rall + (int64_t)g.set * set_stride;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int r1 = min(g.L0, u.y + g.rpu - 1);
   T acc = 0;
@@ -1018,12 +1021,11 @@ __global__ void __launch_bounds__(256) kde_lscv_ac_kernel(const AcGen<T>* __rest
   block_sum_to((double)(g.C * acc), partial + blockIdx.x);
 }
 
-// As kde_lscv_reduce_kernel with K_{H_i}(0) read from memory and scale 1;
-// matrix 2i + h sums the partials of its work units.
+// As kde_lscv_reduce_kernel with K_{H_i}(0) and n read from memory (kn[2i],
+// kn[2i + 1]) and scale 1; matrix 2i + h sums the partials of its work units.
 template <typename T>
 __global__ void __launch_bounds__(32) kde_lscv_ac_reduce_kernel(const AcGen<T>* __restrict__ gens,
-                                                                double n,
-                                                                const double* __restrict__ K0,
+                                                                const double* __restrict__ kn,
                                                                 const double* __restrict__ partial,
                                                                 double* __restrict__ S_out,
                                                                 double* __restrict__ lscv_out) {
@@ -1043,7 +1045,8 @@ __global__ void __launch_bounds__(32) kde_lscv_ac_reduce_kernel(const AcGen<T>* 
       S_out[2 * i] = s[0];
       S_out[2 * i + 1] = s[1];
     }
-    lscv_out[i] = s[1] / (n * n) - 2.0 * (s[0] - n * K0[i]) / (n * (n - 1.0));
+    const double K0 = kn[2 * i], n = kn[2 * i + 1];
+    lscv_out[i] = s[1] / (n * n) - 2.0 * (s[0] - n * K0) / (n * (n - 1.0));
   }
 }
 
@@ -1601,9 +1604,9 @@ kde_status lscv_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, cons
 size_t ac_units_max(const kde_plan_info& I) {
   return (size_t)2 * kAcChunk * (size_t)((I.P[0] + kAcRows - 1) / kAcRows + 1);
 }
-// Uploaded per chunk: 2 nh AcGen, nh K_H(0), then the work units.
+// Uploaded per chunk: 2 nh AcGen, nh (K_H(0), n) pairs, then the work units.
 size_t ac_upload_bytes(const kde_plan_info& I) {
-  return ((size_t)2 * kAcChunk * sizeof(AcGen<double>) + (size_t)kAcChunk * sizeof(double) +
+  return ((size_t)2 * kAcChunk * sizeof(AcGen<double>) + (size_t)2 * kAcChunk * sizeof(double) +
           ac_units_max(I) * sizeof(int2) + 255) & ~(size_t)255;
 }
 
@@ -1656,23 +1659,27 @@ kde_status autocorr_impl(kde_plan_s* plan, const int64_t* counts, void* Rout, vo
   return launch_rows<T>(kde_rows_c2r_kernel<T>, "kde_rows_c2r_kernel", I.P[0], cr, st);
 }
 
+// Candidates c = 0 .. nsets nH - 1 of set c / nH, bandwidth Hs[c], n[c / nH].
 template <typename T>
-kde_status lscv_ac_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, const void* R,
-                        double* S_out, double* lscv_out, void* ws, cudaStream_t st) {
+kde_status lscv_ac_impl(kde_plan_s* plan, int nsets, const int64_t* ns, int nH, const double* Hs,
+                        const void* R, double* S_out, double* lscv_out, void* ws,
+                        cudaStream_t st) {
   const kde_plan_info& I = plan->info;
   const int d = I.d;
+  const int64_t total = (int64_t)nsets * nH;
   double* partial = (double*)((char*)ws + ac_upload_bytes(I));
   std::vector<AcGen<T>> gens;
-  std::vector<double> K0;
+  std::vector<double> kn;
   std::vector<int2> units;
   std::vector<unsigned char> up;
-  for (int h0 = 0; h0 < nH; h0 += kAcChunk) {
-    const int nh = std::min(kAcChunk, nH - h0);
+  for (int64_t h0 = 0; h0 < total; h0 += kAcChunk) {
+    const int nh = (int)std::min<int64_t>(kAcChunk, total - h0);
     gens.assign(2 * nh, AcGen<T>{});
-    K0.assign(nh, 0.0);
+    kn.assign(2 * nh, 0.0);
     units.clear();
     for (int i = 0; i < nh; ++i) {
-      const double* H = Hs + (size_t)(h0 + i) * d * d;
+      const int64_t c = h0 + i;
+      const double* H = Hs + (size_t)c * d * d;
       for (int h = 0; h < 2; ++h) {
         double A[9], Ainv[9], detA;
         int64_t L[KDE_MAX_D];
@@ -1686,6 +1693,7 @@ kde_status lscv_ac_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, c
         g.L0 = kg.L[0];
         g.L1 = kg.L[1];
         g.wand = kg.wand;
+        g.set = (int)(c / nH);
         g.D0 = kg.D[0];
         g.D1 = kg.D[1];
         g.b_hi = kg.Bh[0];
@@ -1696,33 +1704,36 @@ kde_status lscv_ac_impl(kde_plan_s* plan, int64_t n, int nH, const double* Hs, c
         g.u0 = (int)units.size();
         for (int r = 0; r <= g.L0; r += g.rpu) units.push_back(make_int2(2 * i + h, r));
         g.nu = (int)units.size() - g.u0;
-        if (h == 0) K0[i] = std::pow(6.283185307179586476925287, -0.5 * d) / std::sqrt(detA);
+        if (h == 0) {
+          kn[2 * i] = std::pow(6.283185307179586476925287, -0.5 * d) / std::sqrt(detA);
+          kn[2 * i + 1] = (double)ns[c / nH];
+        }
       }
     }
     if (units.size() > ac_units_max(I)) return fail(KDE_ERR_UNSUPPORTED, "lag-sum work units overflow");
-    // one upload, laid out as on the device: AcGen[2 nh], K0[nh], units
-    const size_t gb = gens.size() * sizeof(AcGen<T>), kb = K0.size() * sizeof(double),
+    // one upload, laid out as on the device: AcGen[2 nh], (K0, n)[nh], units
+    const size_t gb = gens.size() * sizeof(AcGen<T>), kb = kn.size() * sizeof(double),
                  ub = units.size() * sizeof(int2);
     up.resize(gb + kb + ub);
     std::memcpy(up.data(), gens.data(), gb);
-    std::memcpy(up.data() + gb, K0.data(), kb);
+    std::memcpy(up.data() + gb, kn.data(), kb);
     std::memcpy(up.data() + gb + kb, units.data(), ub);
     const AcGen<T>* gens_dev = (const AcGen<T>*)ws;
-    const double* K0_dev = (const double*)((char*)ws + gb);
+    const double* kn_dev = (const double*)((char*)ws + gb);
     const int2* units_dev = (const int2*)((char*)ws + gb + kb);
     // pageable source: the copy is staged before this call returns
     cudaError_t e = cudaMemcpyAsync(ws, up.data(), up.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(kernel parameters)");
     {
       LaunchScope ls("kde_lscv_ac_kernel", st);
-      kde_lscv_ac_kernel<T><<<(unsigned)units.size(), 256, 0, st>>>(gens_dev, units_dev, (const T*)R,
-                                                                  (int)I.P[1], partial);
+      kde_lscv_ac_kernel<T><<<(unsigned)units.size(), 256, 0, st>>>(
+          gens_dev, units_dev, (const T*)R, (int)I.P[1], (int64_t)I.P[0] * I.P[1], partial);
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_kernel");
     }
     {
       LaunchScope ls("kde_lscv_reduce_kernel", st);
-      kde_lscv_ac_reduce_kernel<T><<<nh, 32, 0, st>>>(gens_dev, (double)n, K0_dev, partial,
+      kde_lscv_ac_reduce_kernel<T><<<nh, 32, 0, st>>>(gens_dev, kn_dev, partial,
                                                       S_out ? S_out + 2 * h0 : nullptr, lscv_out + h0);
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_reduce_kernel");
@@ -1893,15 +1904,15 @@ extern "C" kde_status kde_autocorrelation(kde_plan plan, const int64_t* counts, 
   return autocorr_impl<double>(plan, counts, R, workspace, st);
 }
 
-extern "C" kde_status kde_lscv_autocorr(kde_plan plan, int64_t n, int nH, const double* H,
-                                        const void* R, double* pair_sums, double* lscv,
-                                        void* workspace, size_t workspace_bytes,
-                                        kde_stream_t stream) {
-  if (!plan || !H || !R || !lscv) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+static kde_status lscv_ac_entry(kde_plan plan, int nsets, const int64_t* n, int nH,
+                                const double* H, const void* R, double* pair_sums, double* lscv,
+                                void* workspace, size_t workspace_bytes, kde_stream_t stream) {
+  if (!plan || !n || !H || !R || !lscv) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
   if (plan->info.d != 2) return fail(KDE_ERR_UNSUPPORTED, "autocorrelation LSCV supports d = 2");
-  if (n < 2) return fail(KDE_ERR_INVALID_ARG, "LSCV needs n >= 2");
-  if (nH < 0) return fail(KDE_ERR_INVALID_ARG, "nH < 0");
-  if (nH == 0) return KDE_OK;
+  if (nsets < 0 || nH < 0) return fail(KDE_ERR_INVALID_ARG, "nsets < 0 or nH < 0");
+  for (int s = 0; s < nsets; ++s)
+    if (n[s] < 2) return fail(KDE_ERR_INVALID_ARG, "LSCV needs n >= 2");
+  if (nsets == 0 || nH == 0) return KDE_OK;
   if (!workspace || workspace_bytes < ac_workspace(plan->info))
     return fail(KDE_ERR_WORKSPACE, "workspace smaller than kde_lscv_autocorr_workspace_bytes");
   if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
@@ -1909,8 +1920,22 @@ extern "C" kde_status kde_lscv_autocorr(kde_plan plan, int64_t n, int nH, const 
   if (s != KDE_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   if (plan->info.precision == KDE_F32)
-    return lscv_ac_impl<float>(plan, n, nH, H, R, pair_sums, lscv, workspace, st);
-  return lscv_ac_impl<double>(plan, n, nH, H, R, pair_sums, lscv, workspace, st);
+    return lscv_ac_impl<float>(plan, nsets, n, nH, H, R, pair_sums, lscv, workspace, st);
+  return lscv_ac_impl<double>(plan, nsets, n, nH, H, R, pair_sums, lscv, workspace, st);
+}
+
+extern "C" kde_status kde_lscv_autocorr(kde_plan plan, int64_t n, int nH, const double* H,
+                                        const void* R, double* pair_sums, double* lscv,
+                                        void* workspace, size_t workspace_bytes,
+                                        kde_stream_t stream) {
+  return lscv_ac_entry(plan, 1, &n, nH, H, R, pair_sums, lscv, workspace, workspace_bytes, stream);
+}
+
+extern "C" kde_status kde_lscv_autocorr_batch(kde_plan plan, int nsets, const int64_t* n, int nH,
+                                              const double* H, const void* R, double* pair_sums,
+                                              double* lscv, void* workspace,
+                                              size_t workspace_bytes, kde_stream_t stream) {
+  return lscv_ac_entry(plan, nsets, n, nH, H, R, pair_sums, lscv, workspace, workspace_bytes, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -65,7 +65,7 @@ EXPORTS = [
     "kde_mlp_destroy", "kde_mlp_param_count", "kde_mlp_get_params", "kde_mlp_set_params",
     "kde_mlp_get_state", "kde_mlp_set_state", "kde_mlp_forward", "kde_mlp_loss_grad",
     "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16", "kde_autocorrelation",
-    "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes",
+    "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes", "kde_lscv_autocorr_batch",
 ]
 FEAT_DIM = 1088
 
@@ -144,7 +144,8 @@ def lib():
                  "kde_mlp_get_params", "kde_mlp_set_params", "kde_mlp_get_state",
                  "kde_mlp_set_state", "kde_mlp_forward", "kde_mlp_loss_grad",
                  "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16",
-                 "kde_autocorrelation", "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes"):
+                 "kde_autocorrelation", "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes",
+                 "kde_lscv_autocorr_batch"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -405,6 +406,29 @@ def kde_lscv_autocorr(plan: Plan, n, H, R, lscv=None, pair_sums=None, workspace=
                                    _ptr(lscv), _ptr(workspace),
                                    workspace.numel() * workspace.element_size(),
                                    _stream_ptr(stream)))
+    return lscv
+
+
+def kde_lscv_autocorr_batch(plan: Plan, ns, H, R, lscv=None, pair_sums=None, workspace=None,
+                            stream=None):
+    """LSCV of nH candidates for each of nsets datasets: ns (nsets sample
+    counts), H (host, nsets x nH x 2 x 2), R (device, nsets x P_0 x P_1);
+    returns lscv (nsets x nH, FP64)."""
+    import torch
+    H = np.ascontiguousarray(np.asarray(H, dtype=np.float64))
+    nsets, nH = H.shape[0], H.shape[1]
+    n = np.ascontiguousarray(np.asarray(ns, dtype=np.int64))
+    if n.shape != (nsets,):
+        raise ValueError("ns must hold one sample count per set")
+    if lscv is None:
+        lscv = torch.empty(nsets, nH, dtype=torch.float64, device="cuda")
+    if workspace is None:
+        workspace = torch.empty(kde_lscv_autocorr_workspace_bytes(plan), dtype=torch.uint8,
+                                device="cuda")
+    _check(lib().kde_lscv_autocorr_batch(
+        plan.handle, nsets, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), nH,
+        H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(R), _ptr(pair_sums), _ptr(lscv),
+        _ptr(workspace), workspace.numel() * workspace.element_size(), _stream_ptr(stream)))
     return lscv
 
 

@@ -34,10 +34,22 @@ C_GRID = np.linspace(-2.8, -0.6, 12)      # log of the second Cholesky diagonal
 STEP = np.array([A_GRID[1] - A_GRID[0], BETA_GRID[1] - BETA_GRID[0], C_GRID[1] - C_GRID[0]])
 
 
+def thetas_to_H(T):
+    """H = R R^T for every theta = (a, beta, c) along the last axis of T
+    (shape ... x 3 -> ... x 2 x 2), R = [[e^a, 0], [beta e^c, e^c]]."""
+    T = np.asarray(T, dtype=np.float64)
+    ea, ec = np.exp(T[..., 0]), np.exp(T[..., 2])
+    b = T[..., 1] * ec
+    H = np.empty(T.shape[:-1] + (2, 2))
+    H[..., 0, 0] = ea * ea
+    H[..., 0, 1] = ea * b
+    H[..., 1, 0] = ea * b
+    H[..., 1, 1] = b * b + ec * ec
+    return H
+
+
 def theta_to_H(theta):
-    a, beta, c = (float(v) for v in theta)
-    R = np.array([[math.exp(a), 0.0], [beta * math.exp(c), math.exp(c)]])
-    return R @ R.T
+    return thetas_to_H(np.asarray(theta, dtype=np.float64)[None, :])[0]
 
 
 def candidate_thetas():
@@ -52,10 +64,14 @@ def normal_reference_theta(n):
     return np.array([0.5 * math.log(h2), 0.0, 0.5 * math.log(h2)])
 
 
+NEIGHBOUR_OFFSETS = np.array(list(itertools.product((-1, 0, 1), repeat=3)), dtype=np.float64)
+
+
 def neighbourhood(theta, scale=0.5):
-    """3 x 3 x 3 candidates around theta, spaced scale grid steps apart."""
-    offs = np.array(list(itertools.product((-1, 0, 1), repeat=3)), dtype=np.float64)
-    return theta[None, :] + scale * offs * STEP[None, :]
+    """3 x 3 x 3 candidates around theta, spaced scale grid steps apart
+    (theta: 3, or B x 3 for B neighbourhoods at once)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    return theta[..., None, :] + scale * NEIGHBOUR_OFFSETS * STEP
 
 
 class LscvScorer:
@@ -89,16 +105,19 @@ class LscvScorer:
         self.cand = cand
         self.cand_H = np.stack([theta_to_H(t) for t in cand])
 
-    def prepare(self, X):
-        """X: n x 2 float32 CUDA tensor of one dataset."""
+    def prepare(self, X, feat=None, R=None):
+        """X: n x 2 float32 CUDA tensor of one dataset.  Features go to feat
+        and the autocorrelation to R (the scorer's own buffers by default)."""
         n = X.shape[0]
         Z = self.Z[:n]
+        feat = self.feat if feat is None else feat
+        R = self.R if R is None else R
         kde.kde_standardize2(X, Z=Z, moments=self.mom)
         kde.kde_bin(Z, self.lo, self.hi, self.M, counts=self.counts, method="direct")
-        kde.kde_features2(self.counts, n, self.mom, feat=self.feat)
-        kde.kde_autocorrelation(self.plan, self.counts, R=self.R, workspace=self.lws)
+        kde.kde_features2(self.counts, n, self.mom, feat=feat)
+        kde.kde_autocorrelation(self.plan, self.counts, R=R, workspace=self.lws)
         self.n = n
-        return self.feat
+        return feat
 
     def scores(self, H):
         """LSCV of every H (k x 2 x 2, standardised coordinates), on the GPU."""
@@ -210,8 +229,7 @@ def select_batch(scorer, mlp, datasets, fallback=True, scored=None):
     ns = []
     for i, X in enumerate(datasets):
         Xd = X if torch.is_tensor(X) else torch.from_numpy(np.ascontiguousarray(X)).to(dev)
-        F[i].copy_(scorer.prepare(Xd))
-        Rs[i].copy_(scorer.R)
+        scorer.prepare(Xd, feat=F[i], R=Rs[i])
         ns.append(int(Xd.shape[0]))
     TH = torch.empty(B, 3, dtype=torch.float32, device=dev)
     for s0 in range(0, B, mlp.max_batch):
@@ -219,14 +237,13 @@ def select_batch(scorer, mlp, datasets, fallback=True, scored=None):
     TH = TH.cpu().numpy().astype(np.float64)
     lo = np.array([A_GRID[0], BETA_GRID[0], C_GRID[0]]) - 0.5 * STEP
     hi = np.array([A_GRID[-1], BETA_GRID[-1], C_GRID[-1]]) + 0.5 * STEP
-    cands, out = [], torch.empty(B, 28, dtype=torch.float64, device=dev)
-    for i in range(B):
-        c = neighbourhood(np.clip(TH[i], lo, hi))
-        H = np.stack([theta_to_H(t) for t in c] + [theta_to_H(normal_reference_theta(ns[i]))])
-        kde.kde_lscv_autocorr(scorer.plan, ns[i], H, Rs[i], lscv=out[i], workspace=scorer.lws)
-        if scored is not None:
-            scored.extend(H)
-        cands.append(c)
+    # every dataset's 27 neighbours and its normal-reference bandwidth, at once
+    cands = neighbourhood(np.clip(TH, lo, hi))                        # B x 27 x 3
+    refs = np.stack([normal_reference_theta(n) for n in ns])          # B x 3
+    Hs = thetas_to_H(np.concatenate([cands, refs[:, None, :]], axis=1))  # B x 28 x 2 x 2
+    out = kde.kde_lscv_autocorr_batch(scorer.plan, ns, Hs, Rs, workspace=scorer.lws)
+    if scored is not None:
+        scored.extend(Hs.reshape(-1, 2, 2))
     s_all = out.cpu().numpy()
     res = []
     for i in range(B):

@@ -137,3 +137,42 @@ def test_rejects_unsupported(K):
     with pytest.raises(K.KDEError) as e:
         K.kde_lscv_autocorr_workspace_bytes(p1)
     assert e.value.status == 7
+
+
+def test_batch_over_datasets_matches_single_calls(K):
+    """kde_lscv_autocorr_batch: three datasets (different n, own candidate
+    lists, 600 candidates each so the batch spans two launches) scored in one
+    call equal the per-dataset calls bit for bit, and the first set's pair
+    sums match the oracle."""
+    sets = [W.lscv_small(40 + i, 2, (36, 44), n=n, count=600, precision="f32")
+            for i, n in enumerate((900, 2500, 4000))]
+    w0 = sets[0]
+    lam = [np.linalg.eigvalsh(h).max() for w in sets for h in w.H]
+    big = 2.0 * [h for w in sets for h in w.H][int(np.argmax(lam))]
+    # one grid for every set (the grid of set 0, widened to hold them all)
+    lo = np.min([w.lo for w in sets], axis=0)
+    hi = np.max([w.hi for w in sets], axis=0)
+    info = K.kde_plan_info_compute(w0.M, lo, hi, big, precision="f32", tau=w0.tau)
+    plan = K.Plan(w0.M, lo, hi, big, precision="f32", tau=w0.tau, P_min=info.P)
+    P0, P1 = plan.info.P
+    R = torch.empty(len(sets), P0, P1, dtype=torch.float32, device="cuda")
+    counts = []
+    for i, w in enumerate(sets):
+        X = torch.from_numpy(np.ascontiguousarray(w.X)).cuda()
+        c = K.kde_bin(X, lo, hi, w.M)
+        K.kde_autocorrelation(plan, c, R=R[i])
+        counts.append(c.cpu().numpy())
+    H = np.stack([w.H for w in sets])
+    ns = [w.n for w in sets]
+    S = torch.empty(len(sets), 600, 2, dtype=torch.float64, device="cuda")
+    got = K.kde_lscv_autocorr_batch(plan, ns, H, R, pair_sums=S).cpu().numpy()
+    for i, w in enumerate(sets):
+        one = K.kde_lscv_autocorr(plan, w.n, w.H, R[i]).cpu().numpy()
+        assert np.array_equal(got[i], one)
+    c = O.counts_to_c(counts[0])
+    S = S.cpu().numpy()
+    for j in (0, 17, 599):
+        for h, A in enumerate((w0.H[j], 2 * w0.H[j])):
+            L = O.support_L(A, lo, hi, w0.M, w0.tau)
+            ref = O.binned_pair_sum(c, A, lo, hi, w0.M, L)
+            assert abs(S[0, j, h] - ref) < 2e-6 * abs(ref)
