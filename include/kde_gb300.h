@@ -250,6 +250,22 @@ kde_status kde_lscv_autocorr_batch(kde_plan plan, int nsets, const int64_t* n, i
                                    const double* H, const void* R, double* pair_sums,
                                    double* lscv, void* workspace, size_t workspace_bytes,
                                    kde_stream_t stream);
+/* A candidate list prepared once for repeated scoring (the plain search
+ * scores the same candidates on every dataset): kde_lscv_cands_create
+ * factorises the nH bandwidths H (host, nH x 2 x 2) on the host in FP64 and
+ * keeps their lag-sum parameters in device memory it allocates (set-up, not
+ * per evaluation; KDE_ERR_CUDA if the allocation fails); the set refers to
+ * its plan, which must outlive it.  kde_lscv_autocorr_cands then scores the
+ * set against the autocorrelation R of n samples exactly as
+ * kde_lscv_autocorr(plan, n, nH, H, R, ...) does — same workspace, outputs
+ * and results — with no host work and no copy: two launches per 1024
+ * candidates.  (Caching candidates has no counterpart in the paper.) */
+typedef struct kde_lscv_cands_s* kde_lscv_cands;
+kde_status kde_lscv_cands_create(kde_plan plan, int nH, const double* H, kde_lscv_cands* out);
+kde_status kde_lscv_cands_destroy(kde_lscv_cands cands);
+kde_status kde_lscv_autocorr_cands(kde_lscv_cands cands, int64_t n, const void* R,
+                                   double* pair_sums, double* lscv, void* workspace,
+                                   size_t workspace_bytes, kde_stream_t stream);
 
 /* Ragged batches of independent 2-D problems (each with its own samples,
  * grid and bandwidth; Sec. 2 for each).  The batch runs as seven launches:

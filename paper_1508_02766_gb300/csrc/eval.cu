@@ -1022,10 +1022,12 @@ __global__ void __launch_bounds__(256) kde_lscv_ac_kernel(const AcGen<T>* __rest
 }
 
 // As kde_lscv_reduce_kernel with K_{H_i}(0) and n read from memory (kn[2i],
-// kn[2i + 1]) and scale 1; matrix 2i + h sums the partials of its work units.
+// kn[2i + 1]; n_all > 0 replaces every n) and scale 1; matrix 2i + h sums
+// the partials of its work units.
 template <typename T>
 __global__ void __launch_bounds__(32) kde_lscv_ac_reduce_kernel(const AcGen<T>* __restrict__ gens,
                                                                 const double* __restrict__ kn,
+                                                                double n_all,
                                                                 const double* __restrict__ partial,
                                                                 double* __restrict__ S_out,
                                                                 double* __restrict__ lscv_out) {
@@ -1045,7 +1047,7 @@ __global__ void __launch_bounds__(32) kde_lscv_ac_reduce_kernel(const AcGen<T>* 
       S_out[2 * i] = s[0];
       S_out[2 * i + 1] = s[1];
     }
-    const double K0 = kn[2 * i], n = kn[2 * i + 1];
+    const double K0 = kn[2 * i], n = n_all > 0.0 ? n_all : kn[2 * i + 1];
     lscv_out[i] = s[1] / (n * n) - 2.0 * (s[0] - n * K0) / (n * (n - 1.0));
   }
 }
@@ -1659,85 +1661,109 @@ kde_status autocorr_impl(kde_plan_s* plan, const int64_t* counts, void* Rout, vo
   return launch_rows<T>(kde_rows_c2r_kernel<T>, "kde_rows_c2r_kernel", I.P[0], cr, st);
 }
 
-// Candidates c = 0 .. nsets nH - 1 of set c / nH, bandwidth Hs[c], n[c / nH].
+// Host side of one chunk of lag-sum candidates: candidates c = c0 ..
+// c0 + nh - 1 of set c / nH, bandwidth Hs[c], sample count ns[c / nH] (ns may
+// be NULL: n is then given at launch).  Fills `up` with the device image
+// AcGen[2 nh], (K0, n)[nh], work units; returns the unit count in *nunits.
+template <typename T>
+kde_status ac_build_chunk(kde_plan_s* plan, int64_t c0, int nh, int nH, const double* Hs,
+                          const int64_t* ns, std::vector<unsigned char>& up, int* nunits) {
+  const kde_plan_info& I = plan->info;
+  const int d = I.d;
+  std::vector<AcGen<T>> gens(2 * nh, AcGen<T>{});
+  std::vector<double> kn(2 * nh, 0.0);
+  std::vector<int2> units;
+  for (int i = 0; i < nh; ++i) {
+    const int64_t c = c0 + i;
+    const double* H = Hs + (size_t)c * d * d;
+    for (int h = 0; h < 2; ++h) {
+      double A[9], Ainv[9], detA;
+      int64_t L[KDE_MAX_D];
+      for (int e = 0; e < d * d; ++e) A[e] = (h ? 2.0 : 1.0) * H[e];
+      kde_status st2 = kde::matrix_support(plan, A, Ainv, &detA, L);
+      if (st2 != KDE_OK) return st2;
+      KGen<T> kg;
+      st2 = kgen_for<T>(I, A, detA, L, plan->layout_mode == KDE_LAYOUT_WAND, &kg);
+      if (st2 != KDE_OK) return st2;
+      AcGen<T>& g = gens[2 * i + h];
+      g.L0 = kg.L[0];
+      g.L1 = kg.L[1];
+      g.wand = kg.wand;
+      g.set = (int)(c / nH);
+      g.D0 = kg.D[0];
+      g.D1 = kg.D[1];
+      g.b_hi = kg.Bh[0];
+      g.b_lo = kg.Bl[0];
+      g.C = kg.C;
+      const int W = 2 * g.L1 + 1;
+      g.rpu = std::max(kAcRows, (kAcTerms / W + kAcRows - 1) / kAcRows * kAcRows);
+      g.u0 = (int)units.size();
+      for (int r = 0; r <= g.L0; r += g.rpu) units.push_back(make_int2(2 * i + h, r));
+      g.nu = (int)units.size() - g.u0;
+      if (h == 0) {
+        kn[2 * i] = std::pow(6.283185307179586476925287, -0.5 * d) / std::sqrt(detA);
+        kn[2 * i + 1] = ns ? (double)ns[c / nH] : 0.0;
+      }
+    }
+  }
+  if (units.size() > ac_units_max(I)) return fail(KDE_ERR_UNSUPPORTED, "lag-sum work units overflow");
+  const size_t gb = gens.size() * sizeof(AcGen<T>), kb = kn.size() * sizeof(double),
+               ub = units.size() * sizeof(int2);
+  up.resize(gb + kb + ub);
+  std::memcpy(up.data(), gens.data(), gb);
+  std::memcpy(up.data() + gb, kn.data(), kb);
+  std::memcpy(up.data() + gb + kb, units.data(), ub);
+  *nunits = (int)units.size();
+  return KDE_OK;
+}
+
+// Device side of one chunk whose image (ac_build_chunk) is at `img`.
+template <typename T>
+kde_status ac_launch_chunk(const kde_plan_info& I, const void* img, int nh, int nunits,
+                           const void* R, double* partial, double n_all, double* S_out,
+                           double* lscv_out, cudaStream_t st) {
+  const AcGen<T>* gens_dev = (const AcGen<T>*)img;
+  const double* kn_dev = (const double*)((const char*)img + 2 * nh * sizeof(AcGen<T>));
+  const int2* units_dev = (const int2*)((const char*)kn_dev + 2 * nh * sizeof(double));
+  cudaError_t e;
+  {
+    LaunchScope ls("kde_lscv_ac_kernel", st);
+    kde_lscv_ac_kernel<T><<<(unsigned)nunits, 256, 0, st>>>(
+        gens_dev, units_dev, (const T*)R, (int)I.P[1], (int64_t)I.P[0] * I.P[1], partial);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_kernel");
+  }
+  {
+    LaunchScope ls("kde_lscv_reduce_kernel", st);
+    kde_lscv_ac_reduce_kernel<T><<<nh, 32, 0, st>>>(gens_dev, kn_dev, n_all, partial, S_out, lscv_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_reduce_kernel");
+  }
+  return KDE_OK;
+}
+
+// Candidates c = 0 .. nsets nH - 1 of set c / nH, bandwidth Hs[c], n[c / nH]:
+// per chunk, the parameters are built on the host, copied into the
+// workspace and launched.
 template <typename T>
 kde_status lscv_ac_impl(kde_plan_s* plan, int nsets, const int64_t* ns, int nH, const double* Hs,
                         const void* R, double* S_out, double* lscv_out, void* ws,
                         cudaStream_t st) {
   const kde_plan_info& I = plan->info;
-  const int d = I.d;
   const int64_t total = (int64_t)nsets * nH;
   double* partial = (double*)((char*)ws + ac_upload_bytes(I));
-  std::vector<AcGen<T>> gens;
-  std::vector<double> kn;
-  std::vector<int2> units;
   std::vector<unsigned char> up;
   for (int64_t h0 = 0; h0 < total; h0 += kAcChunk) {
     const int nh = (int)std::min<int64_t>(kAcChunk, total - h0);
-    gens.assign(2 * nh, AcGen<T>{});
-    kn.assign(2 * nh, 0.0);
-    units.clear();
-    for (int i = 0; i < nh; ++i) {
-      const int64_t c = h0 + i;
-      const double* H = Hs + (size_t)c * d * d;
-      for (int h = 0; h < 2; ++h) {
-        double A[9], Ainv[9], detA;
-        int64_t L[KDE_MAX_D];
-        for (int e = 0; e < d * d; ++e) A[e] = (h ? 2.0 : 1.0) * H[e];
-        kde_status st2 = kde::matrix_support(plan, A, Ainv, &detA, L);
-        if (st2 != KDE_OK) return st2;
-        KGen<T> kg;
-        st2 = kgen_for<T>(I, A, detA, L, plan->layout_mode == KDE_LAYOUT_WAND, &kg);
-        if (st2 != KDE_OK) return st2;
-        AcGen<T>& g = gens[2 * i + h];
-        g.L0 = kg.L[0];
-        g.L1 = kg.L[1];
-        g.wand = kg.wand;
-        g.set = (int)(c / nH);
-        g.D0 = kg.D[0];
-        g.D1 = kg.D[1];
-        g.b_hi = kg.Bh[0];
-        g.b_lo = kg.Bl[0];
-        g.C = kg.C;
-        const int W = 2 * g.L1 + 1;
-        g.rpu = std::max(kAcRows, (kAcTerms / W + kAcRows - 1) / kAcRows * kAcRows);
-        g.u0 = (int)units.size();
-        for (int r = 0; r <= g.L0; r += g.rpu) units.push_back(make_int2(2 * i + h, r));
-        g.nu = (int)units.size() - g.u0;
-        if (h == 0) {
-          kn[2 * i] = std::pow(6.283185307179586476925287, -0.5 * d) / std::sqrt(detA);
-          kn[2 * i + 1] = (double)ns[c / nH];
-        }
-      }
-    }
-    if (units.size() > ac_units_max(I)) return fail(KDE_ERR_UNSUPPORTED, "lag-sum work units overflow");
-    // one upload, laid out as on the device: AcGen[2 nh], (K0, n)[nh], units
-    const size_t gb = gens.size() * sizeof(AcGen<T>), kb = kn.size() * sizeof(double),
-                 ub = units.size() * sizeof(int2);
-    up.resize(gb + kb + ub);
-    std::memcpy(up.data(), gens.data(), gb);
-    std::memcpy(up.data() + gb, kn.data(), kb);
-    std::memcpy(up.data() + gb + kb, units.data(), ub);
-    const AcGen<T>* gens_dev = (const AcGen<T>*)ws;
-    const double* kn_dev = (const double*)((char*)ws + gb);
-    const int2* units_dev = (const int2*)((char*)ws + gb + kb);
+    int nunits = 0;
+    kde_status s = ac_build_chunk<T>(plan, h0, nh, nH, Hs, ns, up, &nunits);
+    if (s != KDE_OK) return s;
     // pageable source: the copy is staged before this call returns
     cudaError_t e = cudaMemcpyAsync(ws, up.data(), up.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(kernel parameters)");
-    {
-      LaunchScope ls("kde_lscv_ac_kernel", st);
-      kde_lscv_ac_kernel<T><<<(unsigned)units.size(), 256, 0, st>>>(
-          gens_dev, units_dev, (const T*)R, (int)I.P[1], (int64_t)I.P[0] * I.P[1], partial);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_kernel");
-    }
-    {
-      LaunchScope ls("kde_lscv_reduce_kernel", st);
-      kde_lscv_ac_reduce_kernel<T><<<nh, 32, 0, st>>>(gens_dev, kn_dev, partial,
-                                                      S_out ? S_out + 2 * h0 : nullptr, lscv_out + h0);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_reduce_kernel");
-    }
+    s = ac_launch_chunk<T>(I, ws, nh, nunits, R, partial, 0.0, S_out ? S_out + 2 * h0 : nullptr,
+                           lscv_out + h0, st);
+    if (s != KDE_OK) return s;
   }
   return KDE_OK;
 }
@@ -1936,6 +1962,92 @@ extern "C" kde_status kde_lscv_autocorr_batch(kde_plan plan, int nsets, const in
                                               double* lscv, void* workspace,
                                               size_t workspace_bytes, kde_stream_t stream) {
   return lscv_ac_entry(plan, nsets, n, nH, H, R, pair_sums, lscv, workspace, workspace_bytes, stream);
+}
+
+// A candidate set prepared once: its lag-sum parameters and work units live
+// on the device, so scoring it against another dataset's autocorrelation is
+// two launches per chunk of 1024 candidates with no host work.
+struct kde_lscv_cands_s {
+  kde_plan_s* plan;
+  int nH;
+  struct Chunk {
+    void* dev;
+    int64_t c0;
+    int nh, nunits;
+  };
+  std::vector<Chunk> chunks;
+};
+
+static void cands_free(kde_lscv_cands_s* c) {
+  for (auto& ch : c->chunks) cudaFree(ch.dev);
+  delete c;
+}
+
+template <typename T>
+static kde_status cands_build(kde_lscv_cands_s* c, const double* H) {
+  std::vector<unsigned char> up;
+  for (int64_t h0 = 0; h0 < c->nH; h0 += kAcChunk) {
+    const int nh = (int)std::min<int64_t>(kAcChunk, c->nH - h0);
+    int nunits = 0;
+    kde_status s = ac_build_chunk<T>(c->plan, h0, nh, c->nH, H, nullptr, up, &nunits);
+    if (s != KDE_OK) return s;
+    kde_lscv_cands_s::Chunk ch{nullptr, h0, nh, nunits};
+    cudaError_t e = cudaMalloc(&ch.dev, up.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(candidate set)");
+    c->chunks.push_back(ch);
+    e = cudaMemcpy(ch.dev, up.data(), up.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(candidate set)");
+  }
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_lscv_cands_create(kde_plan plan, int nH, const double* H,
+                                            kde_lscv_cands* out) {
+  if (!plan || !H || !out) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (plan->info.d != 2) return fail(KDE_ERR_UNSUPPORTED, "autocorrelation LSCV supports d = 2");
+  if (nH < 1) return fail(KDE_ERR_INVALID_ARG, "nH must be >= 1");
+  kde_status s = check_device(plan);
+  if (s != KDE_OK) return s;
+  auto* c = new kde_lscv_cands_s{plan, nH, {}};
+  s = plan->info.precision == KDE_F32 ? cands_build<float>(c, H) : cands_build<double>(c, H);
+  if (s != KDE_OK) {
+    cands_free(c);
+    return s;
+  }
+  *out = c;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_lscv_cands_destroy(kde_lscv_cands cands) {
+  if (!cands) return KDE_OK;
+  cands_free(cands);
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_lscv_autocorr_cands(kde_lscv_cands cands, int64_t n, const void* R,
+                                              double* pair_sums, double* lscv, void* workspace,
+                                              size_t workspace_bytes, kde_stream_t stream) {
+  if (!cands || !R || !lscv) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (n < 2) return fail(KDE_ERR_INVALID_ARG, "LSCV needs n >= 2");
+  kde_plan_s* plan = cands->plan;
+  if (!workspace || workspace_bytes < ac_workspace(plan->info))
+    return fail(KDE_ERR_WORKSPACE, "workspace smaller than kde_lscv_autocorr_workspace_bytes");
+  if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  kde_status s = check_device(plan);
+  if (s != KDE_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* partial = (double*)((char*)workspace + ac_upload_bytes(plan->info));
+  for (const auto& ch : cands->chunks) {
+    double* S = pair_sums ? pair_sums + 2 * ch.c0 : nullptr;
+    s = plan->info.precision == KDE_F32
+            ? ac_launch_chunk<float>(plan->info, ch.dev, ch.nh, ch.nunits, R, partial, (double)n, S,
+                                     lscv + ch.c0, st)
+            : ac_launch_chunk<double>(plan->info, ch.dev, ch.nh, ch.nunits, R, partial, (double)n, S,
+                                      lscv + ch.c0, st);
+    if (s != KDE_OK) return s;
+  }
+  return KDE_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -66,6 +66,7 @@ EXPORTS = [
     "kde_mlp_get_state", "kde_mlp_set_state", "kde_mlp_forward", "kde_mlp_loss_grad",
     "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16", "kde_autocorrelation",
     "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes", "kde_lscv_autocorr_batch",
+    "kde_lscv_cands_create", "kde_lscv_cands_destroy", "kde_lscv_autocorr_cands",
 ]
 FEAT_DIM = 1088
 
@@ -145,7 +146,8 @@ def lib():
                  "kde_mlp_set_state", "kde_mlp_forward", "kde_mlp_loss_grad",
                  "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16",
                  "kde_autocorrelation", "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes",
-                 "kde_lscv_autocorr_batch"):
+                 "kde_lscv_autocorr_batch", "kde_lscv_cands_create", "kde_lscv_cands_destroy",
+                 "kde_lscv_autocorr_cands"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -430,6 +432,42 @@ def kde_lscv_autocorr_batch(plan: Plan, ns, H, R, lscv=None, pair_sums=None, wor
         H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(R), _ptr(pair_sums), _ptr(lscv),
         _ptr(workspace), workspace.numel() * workspace.element_size(), _stream_ptr(stream)))
     return lscv
+
+
+class LscvCands:
+    """A candidate list prepared once on a plan (kde_lscv_cands_*): its
+    parameters stay on the device, so scoring it against a dataset's
+    autocorrelation launches kernels only.  Keeps its plan alive."""
+
+    def __init__(self, plan: Plan, H):
+        H = np.ascontiguousarray(np.asarray(H, dtype=np.float64))
+        self.plan = plan
+        self.nH = H.shape[0]
+        h = ctypes.c_void_p()
+        _check(lib().kde_lscv_cands_create(plan.handle, self.nH,
+                                           H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           ctypes.byref(h)))
+        self.handle = h
+
+    def score(self, n, R, lscv=None, pair_sums=None, workspace=None, stream=None):
+        """LSCV of every candidate for n samples with autocorrelation R."""
+        import torch
+        if lscv is None:
+            lscv = torch.empty(self.nH, dtype=torch.float64, device="cuda")
+        if workspace is None:
+            workspace = torch.empty(kde_lscv_autocorr_workspace_bytes(self.plan), dtype=torch.uint8,
+                                    device="cuda")
+        _check(lib().kde_lscv_autocorr_cands(self.handle, int(n), _ptr(R), _ptr(pair_sums),
+                                             _ptr(lscv), _ptr(workspace),
+                                             workspace.numel() * workspace.element_size(),
+                                             _stream_ptr(stream)))
+        return lscv
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.kde_lscv_cands_destroy(h)
+            self.handle = None
 
 
 class BatchPlan:

@@ -103,7 +103,9 @@ class LscvScorer:
                                device=self.device)
         self.n = 0
         self.cand = cand
-        self.cand_H = np.stack([theta_to_H(t) for t in cand])
+        self.cand_H = thetas_to_H(cand)
+        # the plain search scores the same candidates on every dataset
+        self.cand_set = kde.LscvCands(self.plan, self.cand_H)
 
     def prepare(self, X, feat=None, R=None):
         """X: n x 2 float32 CUDA tensor of one dataset.  Features go to feat
@@ -127,9 +129,11 @@ class LscvScorer:
                               lscv=out, workspace=self.lws)
         return out
 
-    def search(self):
-        """The plain method: argmin of LSCV over the whole candidate grid."""
-        s = self.scores(self.cand_H)
+    def search(self, R=None, n=None):
+        """The plain method: argmin of LSCV over the whole candidate grid (of
+        the last prepared dataset, or of autocorrelation R with n samples)."""
+        s = self.cand_set.score(self.n if n is None else n, self.R if R is None else R,
+                                workspace=self.lws)
         i = int(self.torch.argmin(s).item())
         return self.cand[i], float(s[i].item())
 
@@ -250,13 +254,10 @@ def select_batch(scorer, mlp, datasets, fallback=True, scored=None):
         s = s_all[i]
         j = int(np.argmin(s[:-1]))
         if fallback and s[j] > s[-1]:
-            allv = scorer.torch.empty(len(scorer.cand), dtype=torch.float64, device=dev)
-            kde.kde_lscv_autocorr(scorer.plan, ns[i], scorer.cand_H, Rs[i], lscv=allv,
-                                  workspace=scorer.lws)
+            t, v = scorer.search(R=Rs[i], n=ns[i])
             if scored is not None:
                 scored.extend(scorer.cand_H)
-            k = int(torch.argmin(allv).item())
-            res.append((scorer.cand[k], float(allv[k].item()), 28 + len(scorer.cand), True))
+            res.append((t, v, 28 + len(scorer.cand), True))
         else:
             res.append((cands[i][j], float(s[j]), 28, False))
     return res

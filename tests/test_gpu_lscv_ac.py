@@ -176,3 +176,27 @@ def test_batch_over_datasets_matches_single_calls(K):
             L = O.support_L(A, lo, hi, w0.M, w0.tau)
             ref = O.binned_pair_sum(c, A, lo, hi, w0.M, L)
             assert abs(S[0, j, h] - ref) < 2e-6 * abs(ref)
+
+
+def test_prepared_candidate_set_matches_per_call_scoring(K):
+    """kde_lscv_cands_*: 1500 candidates (two chunks) prepared once and
+    scored against two datasets' autocorrelations equal kde_lscv_autocorr
+    on the same inputs bit for bit, pair sums included."""
+    a = W.lscv_small(50, 2, (40, 40), n=1500, count=1500, precision="f32")
+    b = W.lscv_small(51, 2, (40, 40), n=3500, count=1, precision="f32")
+    lam = [np.linalg.eigvalsh(h).max() for h in a.H]
+    big = 2.0 * a.H[int(np.argmax(lam))]
+    lo = np.minimum(a.lo, b.lo)
+    hi = np.maximum(a.hi, b.hi)
+    info = K.kde_plan_info_compute(a.M, lo, hi, big, precision="f32", tau=a.tau)
+    plan = K.Plan(a.M, lo, hi, big, precision="f32", tau=a.tau, P_min=info.P)
+    cs = K.LscvCands(plan, a.H)
+    for w in (a, b):
+        X = torch.from_numpy(np.ascontiguousarray(w.X)).cuda()
+        R = K.kde_autocorrelation(plan, K.kde_bin(X, lo, hi, w.M))
+        S1 = torch.empty(1500, 2, dtype=torch.float64, device="cuda")
+        S2 = torch.empty(1500, 2, dtype=torch.float64, device="cuda")
+        got = cs.score(w.n, R, pair_sums=S1).cpu().numpy()
+        ref = K.kde_lscv_autocorr(plan, w.n, a.H, R, pair_sums=S2).cpu().numpy()
+        assert np.array_equal(got, ref)
+        assert torch.equal(S1, S2)
