@@ -230,7 +230,10 @@ kde_status kde_lscv_workspace_bytes(kde_plan plan, size_t* bytes);
  * Both take a workspace of at least kde_lscv_autocorr_workspace_bytes,
  * 256-byte aligned.  kde_lscv_autocorr copies the candidates' kernel
  * parameters (host-prepared, FP64 factorisations) into the workspace with
- * host-to-device copies on the stream, up to 1024 candidates per launch. */
+ * host-to-device copies on the stream, up to 1024 candidates per launch;
+ * the copies read pageable host memory that the call frees on return, so
+ * these calls are not for CUDA-graph capture (kde_lscv_autocorr_cands,
+ * below, launches kernels only and can be captured). */
 kde_status kde_lscv_autocorr_workspace_bytes(kde_plan plan, size_t* bytes);
 kde_status kde_autocorrelation(kde_plan plan, const int64_t* counts, void* R, void* workspace,
                                size_t workspace_bytes, kde_stream_t stream);
