@@ -1,8 +1,8 @@
 """Plain FP64 CPU oracle for binned FFT kernel density estimation with an
 unconstrained bandwidth matrix (Gramacki & Gramacki, arXiv 1508.02766).
 
-TEST INFRASTRUCTURE ONLY.  This module is the independent judge of the CUDA
-path: only the test suite, the package's smoke check and the benchmark's CPU
+TEST INFRASTRUCTURE ONLY.  This module is the independent reference the CUDA
+path is checked against: only the test suite, the package's smoke check and the benchmark's CPU
 baseline may import it.  It shares no code, tables or helpers with the CUDA
 library and never imports it.
 
