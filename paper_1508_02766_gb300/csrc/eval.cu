@@ -612,6 +612,9 @@ __device__ __forceinline__ void cols_body(const ColsParams<T>& p) {
 // row segment of kSimdW elements.  The kernel spectrum of such a pass is
 // stored [P][S] (columns contiguous).
 constexpr int kSimdW = 16;
+// Column kernels launch with up to this many threads (SIMD blocks: kSimdW
+// lanes per butterfly group times 16 to 32 groups).
+constexpr int kColsMaxThreads = 512;
 
 template <typename V, int R, bool INV>
 __device__ __forceinline__ void simd_stage(const V* __restrict__ in, V* __restrict__ out,
@@ -818,42 +821,42 @@ __device__ __forceinline__ void cols_simd_body(const ColsParams<T>& p) {
 }
 
 template <typename T, bool SIMD>
-__global__ void __launch_bounds__(256) kde_cols_fwd_kernel(ColsParams<T> p) {
+__global__ void __launch_bounds__(kColsMaxThreads) kde_cols_fwd_kernel(ColsParams<T> p) {
   if (SIMD)
     cols_simd_body<T, COL_FWD>(p);
   else
     cols_body<T, COL_FWD>(p);
 }
 template <typename T, bool SIMD>
-__global__ void __launch_bounds__(256) kde_cols_kgen_kernel(ColsParams<T> p) {
+__global__ void __launch_bounds__(kColsMaxThreads) kde_cols_kgen_kernel(ColsParams<T> p) {
   if (SIMD)
     cols_simd_body<T, COL_FWD>(p);
   else
     cols_body<T, COL_FWD>(p);
 }
 template <typename T, bool SIMD>
-__global__ void __launch_bounds__(256) kde_cols_kgen_real_kernel(ColsParams<T> p) {
+__global__ void __launch_bounds__(kColsMaxThreads) kde_cols_kgen_real_kernel(ColsParams<T> p) {
   if (SIMD)
     cols_simd_body<T, COL_FWD_REAL>(p);
   else
     cols_body<T, COL_FWD_REAL>(p);
 }
 template <typename T, bool SIMD>
-__global__ void __launch_bounds__(256) kde_cols_mid_kernel(ColsParams<T> p) {
+__global__ void __launch_bounds__(kColsMaxThreads) kde_cols_mid_kernel(ColsParams<T> p) {
   if (SIMD)
     cols_simd_body<T, COL_MID>(p);
   else
     cols_body<T, COL_MID>(p);
 }
 template <typename T, bool SIMD>
-__global__ void __launch_bounds__(256) kde_cols_power_kernel(ColsParams<T> p) {
+__global__ void __launch_bounds__(kColsMaxThreads) kde_cols_power_kernel(ColsParams<T> p) {
   if (SIMD)
     cols_simd_body<T, COL_FWD_POWER>(p);
   else
     cols_body<T, COL_FWD_POWER>(p);
 }
 template <typename T, bool SIMD>
-__global__ void __launch_bounds__(256) kde_cols_auto_kernel(ColsParams<T> p) {
+__global__ void __launch_bounds__(kColsMaxThreads) kde_cols_auto_kernel(ColsParams<T> p) {
   if (SIMD)
     cols_simd_body<T, COL_AUTO>(p);
   else
@@ -1053,7 +1056,7 @@ __global__ void __launch_bounds__(32) kde_lscv_ac_reduce_kernel(const AcGen<T>* 
 }
 
 template <typename T, bool SIMD>
-__global__ void __launch_bounds__(256) kde_cols_inv_kernel(ColsParams<T> p) {
+__global__ void __launch_bounds__(kColsMaxThreads) kde_cols_inv_kernel(ColsParams<T> p) {
   if (SIMD)
     cols_simd_body<T, COL_INV>(p);
   else
@@ -1172,6 +1175,30 @@ bool simd_cols(int variant, int64_t columns, int P) {
   return variant == KDE_COLS_SIMD || columns >= (int64_t)4 * kSimdW * num_sms();
 }
 
+// Threads of a SIMD column block: kSimdW lanes per butterfly group and the
+// number of groups ng in 16..32 that leaves the fewest idle lanes over the
+// plan's stages (a stage of nb butterflies takes ceil(nb / ng) rounds; for
+// P = 280 = 8 7 5 the stages hold 35, 40, 56 butterflies: 82% of the lanes
+// busy with 16 groups, 94% with 20), the larger ng on a tie.
+static int simd_threads(const LinePlan& lp) {
+  int best_ng = 16;
+  double best = -1.0;
+  for (int ng = 16; ng <= kColsMaxThreads / kSimdW; ng += 4) {
+    int64_t work = 0, slots = 0;
+    for (int s = 0; s < lp.nst; ++s) {
+      const int nb = lp.st[s].nb;
+      work += nb;
+      slots += (int64_t)((nb + ng - 1) / ng) * ng;
+    }
+    const double u = (double)work / (double)slots;
+    if (u > best + 1e-12 || (u > best - 1e-12 && ng > best_ng)) {
+      best = u;
+      best_ng = ng;
+    }
+  }
+  return best_ng * kSimdW;
+}
+
 template <typename T>
 using ColsKernel = void (*)(ColsParams<T>);
 
@@ -1186,7 +1213,7 @@ kde_status launch_cols(ColsKernel<T> fn_lines, ColsKernel<T> fn_simd, ColsParams
     const size_t smem = (size_t)(1 + 2 * kSimdW) * P * sizeof(typename Cplx<T>::type);
     dim3 grid((unsigned)((p.S + per * kSimdW - 1) / (per * kSimdW)), (unsigned)O);
     LaunchScope ls(name, st);
-    fn_simd<<<grid, 256, smem, st>>>(p);
+    fn_simd<<<grid, simd_threads(p.lp), smem, st>>>(p);
   } else {
     const LineShape sh = line_shape<T>((p.S + per - 1) / per * O, P, 2);
     p.tpl = sh.tpl;
