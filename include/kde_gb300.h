@@ -275,7 +275,10 @@ kde_status kde_lscv_autocorr_cands(kde_lscv_cands cands, int64_t n, const void* 
  * a memset and one persistent grid-stride kernel per pass (binning, kernel
  * rows, kernel spectrum, count rows, middle axis, output rows), each
  * covering the work of every problem, so small and large grids share the
- * GPU.  X: the problems' samples concatenated in problem order (x_rows rows
+ * GPU.  The two kernel-grid passes need no samples and run on a stream the
+ * plan owns, beside the memset and the binning (fork and join through
+ * events on the caller's stream; graph capture follows them), so one plan
+ * evaluates one batch at a time.  X: the problems' samples concatenated in problem order (x_rows rows
  * of 2 values, the plan's precision).  density: the problems' grids
  * concatenated (density_elems values).  Dropped samples are not reported.
  * The plan allocates device tables (set-up, not per evaluation). */

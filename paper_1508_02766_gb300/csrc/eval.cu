@@ -2325,6 +2325,10 @@ struct kde_batch_plan_s {
   int tpl_rows, tpl_cols;           // launch shape (tunable)
   size_t workspace_bytes;
   std::vector<int64_t> n;           // samples per problem
+  // the kernel-grid passes need no samples: they run on this stream beside
+  // the binning (fork and join events on the caller's stream)
+  cudaStream_t side;
+  cudaEvent_t fork, join;
 };
 
 namespace kde {
@@ -2432,7 +2436,12 @@ kde_status batch_eval_impl(kde_batch_plan_s* bp, const void* X, void* density, v
   w += up(bp->A_elems * sizeof(V));
   a.T1 = (V*)w;
   a.density = (T*)density;
-  cudaError_t e = cudaMemsetAsync(a.counts, 0, bp->counts_elems * 8, st);
+  // the kernel-grid passes (no samples needed) fork onto the plan's side
+  // stream and join before the count rows
+  cudaError_t e = cudaEventRecord(bp->fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(bp->side, bp->fork, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "fork (batch kernel grid)");
+  e = cudaMemsetAsync(a.counts, 0, bp->counts_elems * 8, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counts)");
   const int sms = num_sms();
   const int c = bp->count;
@@ -2442,24 +2451,27 @@ kde_status batch_eval_impl(kde_batch_plan_s* bp, const void* X, void* density, v
     if (total > 0) kde_batch_bin_kernel<T><<<std::min(total, sms * 8), 256, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_batch_bin_kernel");
   }
-  auto run = [&](auto fn, int pass, int tpl, const char* name) -> kde_status {
+  auto run = [&](auto fn, int pass, int tpl, const char* name, cudaStream_t ss) -> kde_status {
     const int total = bp->wstart[(size_t)pass * (c + 1) + c];
     if (total == 0) return KDE_OK;
     cudaError_t e2 = allow_smem(fn);
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFuncSetAttribute");
     const size_t smem = line_smem<T>(bp->Pmax, kBatchLines);
     const int grid = std::min(total, sms * 8);
-    LaunchScope ls(name, st);
-    fn<<<grid, tpl * kBatchLines, smem, st>>>(a);
+    LaunchScope ls(name, ss);
+    fn<<<grid, tpl * kBatchLines, smem, ss>>>(a);
     e2 = cudaGetLastError();
     return e2 == cudaSuccess ? KDE_OK : cuda_fail(e2, name);
   };
   kde_status s;
-  if ((s = run(kde_batch_pass_kernel<T, BP_KROWS>, BP_KROWS, bp->tpl_rows, "kde_batch_krows_kernel")) != KDE_OK) return s;
-  if ((s = run(kde_batch_pass_kernel<T, BP_KCOLS>, BP_KCOLS, bp->tpl_cols, "kde_batch_kcols_kernel")) != KDE_OK) return s;
-  if ((s = run(kde_batch_pass_kernel<T, BP_ROWS>, BP_ROWS, bp->tpl_rows, "kde_batch_rows_kernel")) != KDE_OK) return s;
-  if ((s = run(kde_batch_pass_kernel<T, BP_MID>, BP_MID, bp->tpl_cols, "kde_batch_mid_kernel")) != KDE_OK) return s;
-  return run(kde_batch_pass_kernel<T, BP_C2R>, BP_C2R, bp->tpl_rows, "kde_batch_c2r_kernel");
+  if ((s = run(kde_batch_pass_kernel<T, BP_KROWS>, BP_KROWS, bp->tpl_rows, "kde_batch_krows_kernel", bp->side)) != KDE_OK) return s;
+  if ((s = run(kde_batch_pass_kernel<T, BP_KCOLS>, BP_KCOLS, bp->tpl_cols, "kde_batch_kcols_kernel", bp->side)) != KDE_OK) return s;
+  e = cudaEventRecord(bp->join, bp->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, bp->join, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "join (batch kernel grid)");
+  if ((s = run(kde_batch_pass_kernel<T, BP_ROWS>, BP_ROWS, bp->tpl_rows, "kde_batch_rows_kernel", st)) != KDE_OK) return s;
+  if ((s = run(kde_batch_pass_kernel<T, BP_MID>, BP_MID, bp->tpl_cols, "kde_batch_mid_kernel", st)) != KDE_OK) return s;
+  return run(kde_batch_pass_kernel<T, BP_C2R>, BP_C2R, bp->tpl_rows, "kde_batch_c2r_kernel", st);
 }
 
 }  // namespace
@@ -2478,6 +2490,8 @@ extern "C" kde_status kde_batch_plan_create(int count, const kde_batch_item* ite
   bp->tpl_cols = 64;
   bp->items_dev = nullptr;
   bp->wstart_dev = nullptr;
+  bp->side = nullptr;
+  bp->fork = bp->join = nullptr;
   kde_opts o{};
   o.tau = 3.7;
   if (opts) o = *opts;
@@ -2486,6 +2500,9 @@ extern "C" kde_status kde_batch_plan_create(int count, const kde_batch_item* ite
     for (auto* p : bp->plans) kde_plan_destroy(p);
     if (bp->items_dev) cudaFree(bp->items_dev);
     if (bp->wstart_dev) cudaFree(bp->wstart_dev);
+    if (bp->side) cudaStreamDestroy(bp->side);
+    if (bp->fork) cudaEventDestroy(bp->fork);
+    if (bp->join) cudaEventDestroy(bp->join);
     delete bp;
     return s;
   };
@@ -2507,6 +2524,12 @@ extern "C" kde_status kde_batch_plan_create(int count, const kde_batch_item* ite
   kde_status s = (bp->precision == KDE_F32) ? batch_upload<float>(bp, items) : batch_upload<double>(bp, items);
   if (s == KDE_OK) s = batch_work(bp);
   if (s != KDE_OK) return cleanup(s);
+  int lo_prio = 0, hi_prio = 0;
+  cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+  e = cudaStreamCreateWithPriority(&bp->side, cudaStreamNonBlocking, hi_prio);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bp->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bp->join, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "side stream (batch kernel grid)"));
   *out = bp;
   return KDE_OK;
 }
@@ -2544,6 +2567,9 @@ extern "C" kde_status kde_batch_plan_destroy(kde_batch_plan bp) {
   if (!bp) return KDE_OK;
   for (auto* p : bp->plans) kde_plan_destroy(p);
   cudaError_t e = cudaSuccess;
+  if (bp->side) cudaStreamDestroy(bp->side);
+  if (bp->fork) cudaEventDestroy(bp->fork);
+  if (bp->join) cudaEventDestroy(bp->join);
   if (bp->items_dev) e = cudaFree(bp->items_dev);
   if (bp->wstart_dev) cudaFree(bp->wstart_dev);
   delete bp;
