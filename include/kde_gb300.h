@@ -336,6 +336,15 @@ int64_t kde_launch_count(void);
 kde_status kde_profile_enable(int on);
 int kde_profile_count(void);
 kde_status kde_profile_entry(int i, const char** name, double* total_ms, int64_t* launches);
+/* Check of the bounded wait the tensor-core kernels use on their mbarriers
+ * (a diagnostic; the paper has no counterpart): one block of 32 threads
+ * initialises an mbarrier expecting one arrival, arrives on it if `arrive`
+ * is nonzero, and waits for it with at most `limit` polls.  out (device,
+ * 2 int64, caller-owned) receives 0 if the wait completed or 1 if it gave
+ * up, then the cycles the wait took.  With arrive = 0 nothing ever completes
+ * the phase: the kernel must still end, reporting 1.  KDE_ERR_INVALID_ARG
+ * for out = NULL or limit = 0. */
+kde_status kde_wait_probe(int arrive, uint32_t limit, long long* out, kde_stream_t stream);
 
 /* ---- Learned bandwidth proposal --------------------------------------------
  * The paper points to fast bandwidth selection with the same FFT machinery

@@ -30,11 +30,11 @@
 #include <vector>
 
 #include "kde_internal.h"
+#include "tc_wait.cuh"
 
 namespace kde {
 namespace {
 
-constexpr uint32_t kWait = 1u << 22;
 constexpr int kSlice = 32;  // K elements per shared-memory stage
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -44,19 +44,6 @@ __device__ __forceinline__ uint32_t su32(const void* p) {
 __device__ __forceinline__ uint64_t desc_nosw(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) |
          ((uint64_t)(1024u >> 4) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t phase) {
-  uint32_t done = 0;
-  for (uint32_t it = 0; it < kWait && !done; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(phase)
-        : "memory");
-  }
-  return done != 0;
 }
 
 // x rounded to TF32 (10 significand bits, ties away from zero in magnitude).
@@ -199,7 +186,7 @@ __global__ void __launch_bounds__(128) kde_rows_r2c_tc_kernel(TcArgs a) {
     if (kt + 1 < nk) {
       // the other stage was read by the MMAs of slice kt - 1
       if ((used >> nx) & 1u) {
-        const bool done = wait_phase(su32(&mbar[nx]), (phase >> nx) & 1u);
+        const bool done = mbar_wait(su32(&mbar[nx]), (phase >> nx) & 1u);
         if (!__syncthreads_and(done)) {
           ok = false;
           break;
@@ -218,14 +205,14 @@ __global__ void __launch_bounds__(128) kde_rows_r2c_tc_kernel(TcArgs a) {
   }
   if (ok) {
     const int last = (nk - 1) & 1;
-    const bool done = wait_phase(su32(&mbar[last]), (phase >> last) & 1u);
+    const bool done = mbar_wait(su32(&mbar[last]), (phase >> last) & 1u);
     ok = __syncthreads_and(done);
   }
   if (!ok) {
     if (tid == 0) atomicExch(a.status, 1);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     for (int b = 0; b < 2; ++b)
-      if ((used >> b) & 1u) wait_phase(su32(&mbar[b]), (phase >> b) & 1u);
+      if ((used >> b) & 1u) mbar_wait(su32(&mbar[b]), (phase >> b) & 1u);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "kde_internal.h"
+#include "tc_wait.cuh"
 
 namespace kde {
 namespace {
@@ -56,7 +57,6 @@ struct GemmArgs {
   int* status;         // set to 1 if a wait for the tensor cores gave up
 };
 
-constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -68,20 +68,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) |
          ((uint64_t)(1024u >> 4) << 32) | (1ull << 46);
-}
-
-// Bounded wait for an mbarrier phase; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-  uint32_t done = 0;
-  for (uint32_t it = 0; it < kWaitLimit && !done; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(phase)
-        : "memory");
-  }
-  return done != 0;
 }
 
 // Stage the 64-wide K slice k0 of A's rows m0.. and B's rows n0.. into one

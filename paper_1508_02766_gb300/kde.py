@@ -67,6 +67,7 @@ EXPORTS = [
     "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16", "kde_autocorrelation",
     "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes", "kde_lscv_autocorr_batch",
     "kde_lscv_cands_create", "kde_lscv_cands_destroy", "kde_lscv_autocorr_cands",
+    "kde_wait_probe",
 ]
 FEAT_DIM = 1088
 
@@ -147,7 +148,7 @@ def lib():
                  "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16",
                  "kde_autocorrelation", "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes",
                  "kde_lscv_autocorr_batch", "kde_lscv_cands_create", "kde_lscv_cands_destroy",
-                 "kde_lscv_autocorr_cands"):
+                 "kde_lscv_autocorr_cands", "kde_wait_probe"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -432,6 +433,18 @@ def kde_lscv_autocorr_batch(plan: Plan, ns, H, R, lscv=None, pair_sums=None, wor
         H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(R), _ptr(pair_sums), _ptr(lscv),
         _ptr(workspace), workspace.numel() * workspace.element_size(), _stream_ptr(stream)))
     return lscv
+
+
+def kde_wait_probe(arrive, limit, out=None, stream=None):
+    """The tensor-core kernels' bounded mbarrier wait on a barrier that is
+    (arrive=True) or is never (arrive=False) completed; returns a device
+    int64 pair (0 completed / 1 gave up, cycles waited)."""
+    import torch
+    if out is None:
+        out = torch.empty(2, dtype=torch.int64, device="cuda")
+    _check(lib().kde_wait_probe(int(bool(arrive)), ctypes.c_uint32(int(limit)), _ptr(out),
+                                _stream_ptr(stream)))
+    return out
 
 
 class LscvCands:
