@@ -140,39 +140,51 @@ __global__ void __launch_bounds__(256) kde_bin_kernel(const T* __restrict__ X, i
                                                       unsigned long long* __restrict__ counts,
                                                       unsigned long long* __restrict__ n_out) {
   constexpr int H = 1 << (D - 1);
+  constexpr int U = 8;  // samples whose coordinates are loaded before any is added
   const int par = threadIdx.x & 1;
   unsigned long long outside = 0;
   const int64_t step = ((int64_t)gridDim.x * blockDim.x) >> 1;
-  for (int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 1; s < n; s += step) {
-    int i[D];
-    unsigned q[D];
-    bool in = true;
+  for (int64_t s0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 1; s0 < n; s0 += U * step) {
+    T xs[U][D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) in &= axis_position<T>(X[s * D + k], p.ax[k], i[k], q[k]);
-    if (!in) {
-      outside += par == 0;
-      continue;
-    }
-    int64_t base = par;
+    for (int u = 0; u < U; ++u) {
+      const int64_t s = s0 + u * step;
 #pragma unroll
-    for (int k = 0; k < D; ++k) base += (int64_t)i[k] * p.ax[k].stride;
-    // weights over the first D - 1 axes, then this lane's half of the last split
-    unsigned long long w[H];
-    if (D == 1) {
-      w[0] = kOne;
-    } else {
-      corner_weights<D - 1>(q, w);
+      for (int k = 0; k < D; ++k) xs[u][k] = s < n ? X[s * D + k] : T(0);
     }
 #pragma unroll
-    for (int c = 0; c < H; ++c) {
-      const unsigned long long hi = mulhi_round(w[c], q[D - 1]);
-      const unsigned long long wc = par ? hi : w[c] - hi;
-      if (wc == 0) continue;
-      int64_t idx = base;
+    for (int u = 0; u < U; ++u) {
+      if (s0 + u * step >= n) break;
+      int i[D];
+      unsigned q[D];
+      bool in = true;
 #pragma unroll
-      for (int k = 0; k < D - 1; ++k)
-        if ((c >> (D - 2 - k)) & 1) idx += p.ax[k].stride;
-      atomicAdd(counts + idx, wc);
+      for (int k = 0; k < D; ++k) in &= axis_position<T>(xs[u][k], p.ax[k], i[k], q[k]);
+      if (!in) {
+        outside += par == 0;
+        continue;
+      }
+      int64_t base = par;
+#pragma unroll
+      for (int k = 0; k < D; ++k) base += (int64_t)i[k] * p.ax[k].stride;
+      // weights over the first D - 1 axes, then this lane's half of the last split
+      unsigned long long w[H];
+      if (D == 1) {
+        w[0] = kOne;
+      } else {
+        corner_weights<D - 1>(q, w);
+      }
+#pragma unroll
+      for (int c = 0; c < H; ++c) {
+        const unsigned long long hi = mulhi_round(w[c], q[D - 1]);
+        const unsigned long long wc = par ? hi : w[c] - hi;
+        if (wc == 0) continue;
+        int64_t idx = base;
+#pragma unroll
+        for (int k = 0; k < D - 1; ++k)
+          if ((c >> (D - 2 - k)) & 1) idx += p.ax[k].stride;
+        atomicAdd(counts + idx, wc);
+      }
     }
   }
   if (n_out) {
