@@ -2211,24 +2211,36 @@ __global__ void __launch_bounds__(256) kde_batch_bin_kernel(BatchArgs<T> a) {
     // offset p along the last axis, so a lane pair's two words share a
     // 32-byte sector three times in four and coalesce into one request
     const int par = threadIdx.x & 1;
-    for (int64_t j = c0 + (threadIdx.x >> 1); j < c1; j += blockDim.x >> 1) {
-    const int64_t s = B.x_off + j;
-    int i[2];
-    unsigned q[2];
-    bool in = true;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      BinAxisLite<T> ax{B.lo[k], B.s[k], B.top[k], B.M[k]};
-      in &= lite_position<T>(a.X[s * 2 + k], ax, i[k], q[k]);
-    }
-    if (!in) continue;
-    unsigned long long wt[4];
-    lite_corner_weights2(q, wt);
-    const unsigned long long w0 = par ? wt[1] : wt[0], w1 = par ? wt[3] : wt[2];
+    const int64_t jstep = blockDim.x >> 1;
+    constexpr int U = 8;  // samples whose coordinates are loaded before any is added
     unsigned long long* c = reinterpret_cast<unsigned long long*>(a.counts + B.counts_off);
-    const int64_t base = (int64_t)i[0] * B.M[1] + i[1] + par;
-    if (w0) atomicAdd(c + base, w0);
-    if (w1) atomicAdd(c + base + B.M[1], w1);
+    for (int64_t j0 = c0 + (threadIdx.x >> 1); j0 < c1; j0 += U * jstep) {
+      T xs[U][2];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t j = j0 + u * jstep;
+        xs[u][0] = j < c1 ? a.X[(B.x_off + j) * 2] : T(0);
+        xs[u][1] = j < c1 ? a.X[(B.x_off + j) * 2 + 1] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (j0 + u * jstep >= c1) break;
+        int i[2];
+        unsigned q[2];
+        bool in = true;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          BinAxisLite<T> ax{B.lo[k], B.s[k], B.top[k], B.M[k]};
+          in &= lite_position<T>(xs[u][k], ax, i[k], q[k]);
+        }
+        if (!in) continue;
+        unsigned long long wt[4];
+        lite_corner_weights2(q, wt);
+        const unsigned long long w0 = par ? wt[1] : wt[0], w1 = par ? wt[3] : wt[2];
+        const int64_t base = (int64_t)i[0] * B.M[1] + i[1] + par;
+        if (w0) atomicAdd(c + base, w0);
+        if (w1) atomicAdd(c + base + B.M[1], w1);
+      }
     }
   }
 }
