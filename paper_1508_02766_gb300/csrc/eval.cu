@@ -49,6 +49,8 @@ struct KGen {
 
 __device__ __forceinline__ float ex(float x) { return expf(x); }
 __device__ __forceinline__ double ex(double x) { return exp(x); }
+__device__ __forceinline__ float ex2(float x) { return exp2f(x); }
+__device__ __forceinline__ double ex2(double x) { return exp2(x); }
 
 // b m as the sum of the rounded product and its error (exact in FP32 up to
 // b's own split into bh + bl).
@@ -975,7 +977,9 @@ __global__ void __launch_bounds__(32) kde_lscv_reduce_kernel(LscvReduce r, const
 // Along lag row l_0 >= 0 the Gaussian is C exp(e) in the completed squares
 // of KGen (d = 2, column lag m = l_1, or |l_1| in Wand's layout):
 //   e = D_0 l_0^2 + D_1 (m + b l_0)^2,  b = B_10 = b_hi + b_lo,
-// so per row e_0 = D_0 l_0^2 and b l_0 are formed once.
+// so per row e_0 = D_0 l_0^2 and b l_0 are formed once.  D_0 and D_1 are
+// stored times log2(e) (scaled in FP64 on the host), so each term is one
+// exp2 of the exponent in base-2 units.
 template <typename T>
 struct AcGen {
   int L0, L1, wand;
@@ -1015,7 +1019,7 @@ __global__ void __launch_bounds__(256) kde_lscv_ac_kernel(const AcGen<T>* __rest
     T racc = 0;
     for (int l1 = (l0 == 0 ? 0 : -g.L1) + lane; l1 <= g.L1; l1 += 32) {
       const T v = ((T)(g.wand ? abs(l1) : l1) + t_hi) + t_lo;
-      racc += ex(fma(g.D1 * v, v, e0)) * __ldg(Rrow + (l1 < 0 ? l1 + P1 : l1));
+      racc += ex2(fma(g.D1 * v, v, e0)) * __ldg(Rrow + (l1 < 0 ? l1 + P1 : l1));
     }
     // every lag of the half plane counts twice, the lag 0 (K = C) once
     if (l0 == 0 && lane == 0) racc -= T(0.5) * __ldg(Rrow);
@@ -1712,13 +1716,17 @@ kde_status ac_build_chunk(kde_plan_s* plan, int64_t c0, int nh, int nH, const do
       KGen<T> kg;
       st2 = kgen_for<T>(I, A, detA, L, plan->layout_mode == KDE_LAYOUT_WAND, &kg);
       if (st2 != KDE_OK) return st2;
+      double Dd[3], Bd[3];
+      st2 = gauss_factor(I.d, A, I.delta, Dd, Bd);
+      if (st2 != KDE_OK) return st2;
+      const double log2e = 1.4426950408889634073599246810;  // 1 / ln 2
       AcGen<T>& g = gens[2 * i + h];
       g.L0 = kg.L[0];
       g.L1 = kg.L[1];
       g.wand = kg.wand;
       g.set = (int)(c / nH);
-      g.D0 = kg.D[0];
-      g.D1 = kg.D[1];
+      g.D0 = (T)(Dd[0] * log2e);
+      g.D1 = (T)(Dd[1] * log2e);
       g.b_hi = kg.Bh[0];
       g.b_lo = kg.Bl[0];
       g.C = kg.C;
