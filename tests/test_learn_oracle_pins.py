@@ -100,3 +100,27 @@ def test_bf16_gradient_is_the_fp64_one_on_bf16_grid_values():
     a = LO.mlp_loss_grad(p, X, T, 2, 2, 1)
     b = LO.mlp_loss_grad(p, X, T, 2, 2, 1, bf16=True)
     assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+def test_batched_candidate_construction_matches_oracle():
+    """The learned selection builds every dataset's candidates at once
+    (thetas_to_H over arrays, neighbourhood of many thetas); each matrix must
+    equal the oracle's R R^T for its theta, and each neighbourhood the
+    single-theta one."""
+    from paper_1508_02766_gb300 import learned as Lm
+    rng = np.random.default_rng(12)
+    T = np.stack([rng.uniform(-3, 0, 40), rng.uniform(-1.5, 1.5, 40), rng.uniform(-3, 0, 40)], 1)
+    H = Lm.thetas_to_H(T)
+    for t, h in zip(T, H):
+        ref = LO.theta_to_H(t)
+        assert np.allclose(h, ref, rtol=1e-14, atol=0.0)
+        assert h[0, 1] == h[1, 0]
+    N = Lm.neighbourhood(T[:5])
+    assert N.shape == (5, 27, 3)
+    for i in range(5):
+        assert np.array_equal(N[i], Lm.neighbourhood(T[i]))
+    # the centre of each neighbourhood is the theta itself
+    assert np.array_equal(N[:, 13], T[:5])
+    HH = Lm.thetas_to_H(N)
+    assert HH.shape == (5, 27, 2, 2)
+    assert np.array_equal(HH[2, 7], Lm.theta_to_H(N[2, 7]))
