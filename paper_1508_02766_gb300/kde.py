@@ -663,6 +663,49 @@ def kde_features2(counts, n, moments, feat=None, stream=None):
     return feat
 
 
+class FeaturePrep:
+    """The per-dataset preparation of the learned selection with every fixed
+    argument marshalled once: kde_standardize2 into Z, kde_bin (direct) of Z
+    on the plan's grid, kde_features2, kde_autocorrelation.  run(X, feat, R)
+    then makes the four C calls with only X's pointer and length and the two
+    outputs changing, on the stream given at construction; Z, counts,
+    moments and the workspace are owned here."""
+
+    def __init__(self, plan: Plan, n_max, workspace, stream=None):
+        import torch
+        dev = workspace.device
+        self.plan = plan
+        self.Z = torch.empty(n_max, 2, dtype=torch.float32, device=dev)
+        self.counts = torch.empty(plan.M, dtype=torch.int64, device=dev)
+        self.moments = torch.empty(8, dtype=torch.float64, device=dev)
+        self.ws = workspace
+        self._L = lib()
+        self._s = _stream_ptr(stream)
+        self._lo, self._hi, self._M = _darr(plan.lo), _darr(plan.hi), _iarr(plan.M)
+        self._pZ, self._pc, self._pm = _ptr(self.Z), _ptr(self.counts), _ptr(self.moments)
+        self._pws = _ptr(workspace)
+        self._wsb = workspace.numel() * workspace.element_size()
+        self._null = ctypes.c_void_p(0)
+
+    def run(self, X, feat, R):
+        """X: n x 2 float32 CUDA tensor (n <= n_max); feat (FEAT_DIM) and R
+        (P_0 x P_1) receive the features and the autocorrelation."""
+        L, s = self._L, self._s
+        n = int(X.shape[0])
+        if n > self.Z.shape[0] or X.dim() != 2 or X.shape[1] != 2 or not X.is_contiguous() \
+                or X.dtype != self.Z.dtype or not X.is_cuda:
+            raise ValueError("X must be a contiguous (n, 2) float32 CUDA tensor with n <= n_max")
+        px = ctypes.c_void_p(X.data_ptr())
+        _check(L.kde_standardize2(px, n, self._pZ, self._pm, s))
+        _check(L.kde_bin(self._pZ, F32, n, 2, self._lo, self._hi, self._M, self._pc, self._null,
+                         self._null, 0, s))
+        _check(L.kde_features2(self._pc, self.plan.M[0], n, self._pm,
+                               ctypes.c_void_p(feat.data_ptr()), s))
+        _check(L.kde_autocorrelation(self.plan.handle, self._pc, ctypes.c_void_p(R.data_ptr()),
+                                     self._pws, self._wsb, s))
+        return feat
+
+
 def kde_gemm_bf16(A, B, C=None, status=None, stream=None):
     """C = A B^T on the tensor cores (A: M x K, B: N x K, bfloat16)."""
     import torch

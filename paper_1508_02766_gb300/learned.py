@@ -94,13 +94,13 @@ class LscvScorer:
         self.plan = kde.Plan(M, lo, hi, big, precision="f32", tau=tau, P_min=pinfo.P)
         self.M, self.lo, self.hi, self.tau = M, lo, hi, tau
         info = self.plan.info
-        self.counts = torch.empty(M, dtype=torch.int64, device=self.device)
-        self.Z = torch.empty(n_max, 2, dtype=torch.float32, device=self.device)
-        self.mom = torch.empty(8, dtype=torch.float64, device=self.device)
         self.feat = torch.empty(kde.FEAT_DIM, dtype=torch.float32, device=self.device)
         self.R = torch.empty(info.P[0], info.P[1], dtype=torch.float32, device=self.device)
         self.lws = torch.empty(kde.kde_lscv_autocorr_workspace_bytes(self.plan), dtype=torch.uint8,
                                device=self.device)
+        # standardise, bin, features, autocorrelation with arguments marshalled once
+        self.prep = kde.FeaturePrep(self.plan, n_max, self.lws)
+        self.counts, self.Z, self.mom = self.prep.counts, self.prep.Z, self.prep.moments
         self.n = 0
         self.cand = cand
         self.cand_H = thetas_to_H(cand)
@@ -110,15 +110,10 @@ class LscvScorer:
     def prepare(self, X, feat=None, R=None):
         """X: n x 2 float32 CUDA tensor of one dataset.  Features go to feat
         and the autocorrelation to R (the scorer's own buffers by default)."""
-        n = X.shape[0]
-        Z = self.Z[:n]
         feat = self.feat if feat is None else feat
         R = self.R if R is None else R
-        kde.kde_standardize2(X, Z=Z, moments=self.mom)
-        kde.kde_bin(Z, self.lo, self.hi, self.M, counts=self.counts, method="direct")
-        kde.kde_features2(self.counts, n, self.mom, feat=feat)
-        kde.kde_autocorrelation(self.plan, self.counts, R=R, workspace=self.lws)
-        self.n = n
+        self.prep.run(X, feat, R)
+        self.n = int(X.shape[0])
         return feat
 
     def scores(self, H):
