@@ -185,7 +185,7 @@ def test_empty_input_and_errors(K):
     Xs = torch.zeros((10, 2), dtype=torch.float32, device="cuda")
     tiny = torch.empty(256, dtype=torch.uint8, device="cuda")
     with pytest.raises(K.KDEError) as e:
-        K.kde_bin(Xs, (0, 0), (1, 1), (5, 6), workspace=tiny[:16])
+        K.kde_bin(Xs, (0, 0), (1, 1), (5, 6), workspace=tiny[:16], method="tiled")
     assert e.value.status == 4
     plan = K.Plan((5, 6), (0, 0), (1, 1), np.eye(2) * 0.01)
     with pytest.raises(K.KDEError) as e:
