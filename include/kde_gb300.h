@@ -38,11 +38,13 @@ typedef struct CUstream_st* kde_stream_t; /* same type as cudaStream_t */
 
 typedef enum {
   KDE_OK = 0,
-  KDE_ERR_INVALID_ARG = 1, /* bad size, pointer, dtype, non-finite value, asymmetric H */
-  KDE_ERR_NOT_SPD = 2,     /* H is not positive definite (Cholesky failed) */
-  KDE_ERR_WORKSPACE = 4,   /* workspace smaller than the plan's workspace_bytes */
-  KDE_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
-  KDE_ERR_UNSUPPORTED = 7  /* d not in 1..3, or a padded size above KDE_MAX_P */
+  KDE_ERR_INVALID_ARG = 1,  /* bad size, pointer, dtype, non-finite value, asymmetric H */
+  KDE_ERR_NOT_SPD = 2,      /* H is not positive definite (Cholesky failed) */
+  KDE_ERR_OUT_OF_RANGE = 3, /* samples fell outside the grid (kde_outside_check) */
+  KDE_ERR_WORKSPACE = 4,    /* workspace smaller than the plan's workspace_bytes */
+  KDE_ERR_CUDA = 5,         /* a CUDA runtime call or launch failed */
+  KDE_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up (kde_plan_check) */
+  KDE_ERR_UNSUPPORTED = 7   /* d not in 1..3, or a padded size above KDE_MAX_P */
 } kde_status;
 
 enum { KDE_F32 = 0, KDE_F64 = 1 };                   /* element types */
@@ -324,6 +326,27 @@ kde_status kde_batch_plan_destroy(kde_batch_plan plan);
 #define KDE_NOALLOC_SCRATCH_BYTES (8u << 20)
 kde_status kde_fft_eval_noalloc(kde_plan plan, const int64_t* counts, const void* Kspec,
                                 void* density, kde_stream_t stream);
+/* The size of that fixed array as the library was built (bindings read it
+ * here rather than repeating the constant).  The looked-up device address
+ * is kept per device for the life of the process; it is no longer valid
+ * after cudaDeviceReset, so do not use this entry point after resetting a
+ * device in the same process. */
+size_t kde_noalloc_scratch_bytes(void);
+
+/* Device-side status of a plan.  Kernels that wait on a barrier inside the
+ * GPU (the tensor-core first pass) bound every wait; a wait that gives up
+ * records that in a status word the plan owns and the kernel returns
+ * without finishing its work, so the call's output is then invalid.
+ * kde_plan_check synchronises the stream, reads and clears that word and
+ * returns KDE_ERR_TIMEOUT if any wait gave up since the previous check
+ * (KDE_OK otherwise). */
+kde_status kde_plan_check(kde_plan plan, kde_stream_t stream);
+
+/* Binning's dropped samples as a status (Sec. 3 requires the grid to cover
+ * the data): synchronises the stream, copies the device counter n_outside
+ * filled by kde_bin into *count (host, may be NULL) and returns
+ * KDE_ERR_OUT_OF_RANGE if it is nonzero, KDE_OK if it is zero. */
+kde_status kde_outside_check(const int64_t* n_outside, kde_stream_t stream, int64_t* count);
 
 /* Diagnostics. */
 const char* kde_status_string(kde_status s);

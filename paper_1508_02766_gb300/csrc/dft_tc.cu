@@ -322,12 +322,11 @@ kde_status dft_tc_setup(kde_plan_s* p) {
         tab[(size_t)N * K + (size_t)(2 * q + h) * K + x] = lo;
       }
     }
-  // the table, then one int: the kernel's wait status
+  // the table (the kernel's wait status goes to the plan's status word)
   void* d = nullptr;
-  cudaError_t e = cudaMalloc(&d, tab.size() * sizeof(float) + 256);
+  cudaError_t e = cudaMalloc(&d, tab.size() * sizeof(float));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(DFT matrix)");
   e = cudaMemcpy(d, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset((char*)d + tab.size() * sizeof(float), 0, 256);
   if (e != cudaSuccess) {
     cudaFree(d);
     return cuda_fail(e, "cudaMemcpy(DFT matrix)");
@@ -350,7 +349,7 @@ kde_status dft_tc_rows(const kde_plan_s* p, const long long* counts, int64_t row
   a.Fhi = p->dft_tab;
   a.Flo = p->dft_tab + (size_t)p->dft_N * p->dft_K;
   a.out = (float2*)out;
-  a.status = (int*)(p->dft_tab + (size_t)2 * p->dft_N * p->dft_K);
+  a.status = p->status_dev;
   cudaError_t e;
   switch (p->dft_BN) {
     case 256: e = launch_tc<256>(a, p->dft_N, st); break;

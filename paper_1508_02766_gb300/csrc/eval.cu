@@ -1859,7 +1859,8 @@ extern "C" kde_status kde_fft_eval(kde_plan plan, const int64_t* counts, const v
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // KDE_NOALLOC_SCRATCH_BYTES
+constexpr size_t kNoAllocScratchBytes = KDE_NOALLOC_SCRATCH_BYTES;
+static_assert(kNoAllocScratchBytes % 256 == 0, "the scratch array is a whole number of 256-byte blocks");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -1883,6 +1884,8 @@ kde_status noalloc_scratch(int dev, void** out) {
 }
 
 }  // namespace
+
+extern "C" size_t kde_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
 
 extern "C" kde_status kde_fft_eval_noalloc(kde_plan plan, const int64_t* counts, const void* Kspec,
                                            void* density, kde_stream_t stream) {

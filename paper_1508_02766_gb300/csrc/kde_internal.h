@@ -23,6 +23,9 @@ struct kde_plan_s {
   // plan's precision (float2 or double2), owned by the plan.
   void* tw_dev;
   size_t tw_offset[KDE_MAX_D];  // byte offset of axis k's table in tw_dev
+  // Device status word (inside the twiddle allocation, after the tables):
+  // nonzero once a bounded wait in one of the plan's kernels gave up.
+  int* status_dev;
   // Tensor-core DFT of the first pass (opts.dft_tc): the real DFT matrix of
   // the last axis restricted to its M_last data points, split into TF32
   // high and low parts, each dft_N x dft_K floats (rows 2q, 2q+1 = cos,

@@ -386,10 +386,17 @@ kde_status kde_plan_create(int d, const int64_t* M, const double* lo, const doub
     p->tw_offset[k] = total;
     total += ((size_t)p->info.P[k] * cb + 255) & ~(size_t)255;
   }
-  e = cudaMalloc(&p->tw_dev, total);
+  e = cudaMalloc(&p->tw_dev, total + 256);
   if (e != cudaSuccess) {
     delete p;
     return cuda_fail(e, "cudaMalloc(twiddles)");
+  }
+  p->status_dev = (int*)((char*)p->tw_dev + total);
+  e = cudaMemset(p->status_dev, 0, 256);
+  if (e != cudaSuccess) {
+    cudaFree(p->tw_dev);
+    delete p;
+    return cuda_fail(e, "cudaMemset(status)");
   }
   for (int k = 0; k < d; ++k) {
     int P = (int)p->info.P[k];
@@ -442,10 +449,35 @@ const char* kde_status_string(kde_status s) {
     case KDE_ERR_INVALID_ARG: return "KDE_ERR_INVALID_ARG";
     case KDE_ERR_NOT_SPD: return "KDE_ERR_NOT_SPD";
     case KDE_ERR_WORKSPACE: return "KDE_ERR_WORKSPACE";
+    case KDE_ERR_OUT_OF_RANGE: return "KDE_ERR_OUT_OF_RANGE";
     case KDE_ERR_CUDA: return "KDE_ERR_CUDA";
+    case KDE_ERR_TIMEOUT: return "KDE_ERR_TIMEOUT";
     case KDE_ERR_UNSUPPORTED: return "KDE_ERR_UNSUPPORTED";
   }
   return "unknown kde_status";
+}
+
+kde_status kde_plan_check(kde_plan plan, kde_stream_t stream) {
+  if (!plan) return fail(KDE_ERR_INVALID_ARG, "plan is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  int flag = 0;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, plan->status_dev, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && flag) e = cudaMemset(plan->status_dev, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "kde_plan_check");
+  if (flag) return fail(KDE_ERR_TIMEOUT, "a bounded device-side wait gave up; the output is invalid");
+  return KDE_OK;
+}
+
+kde_status kde_outside_check(const int64_t* n_outside, kde_stream_t stream, int64_t* count) {
+  if (!n_outside) return fail(KDE_ERR_INVALID_ARG, "n_outside is NULL");
+  int64_t v = 0;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&v, n_outside, sizeof(int64_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "kde_outside_check");
+  if (count) *count = v;
+  if (v) return fail(KDE_ERR_OUT_OF_RANGE, "samples fell outside the grid");
+  return KDE_OK;
 }
 
 const char* kde_last_error(void) { return g_last_error.c_str(); }

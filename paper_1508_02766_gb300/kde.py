@@ -67,7 +67,7 @@ EXPORTS = [
     "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16", "kde_autocorrelation",
     "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes", "kde_lscv_autocorr_batch",
     "kde_lscv_cands_create", "kde_lscv_cands_destroy", "kde_lscv_autocorr_cands",
-    "kde_wait_probe",
+    "kde_wait_probe", "kde_plan_check", "kde_outside_check", "kde_noalloc_scratch_bytes",
 ]
 FEAT_DIM = 1088
 
@@ -128,6 +128,10 @@ def lib():
     L.kde_mlp_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.kde_gemm_bf16.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp,
                                 ctypes.c_int, vp, ctypes.c_int, vp, vp]
+    L.kde_plan_check.argtypes = [vp, vp]
+    L.kde_outside_check.argtypes = [vp, vp, i64p]
+    L.kde_noalloc_scratch_bytes.argtypes = []
+    L.kde_noalloc_scratch_bytes.restype = ctypes.c_size_t
     L.kde_status_string.restype = ctypes.c_char_p
     L.kde_status_string.argtypes = [ctypes.c_int]
     L.kde_last_error.restype = ctypes.c_char_p
@@ -148,7 +152,8 @@ def lib():
                  "kde_mlp_train_step", "kde_mlp_status", "kde_gemm_bf16",
                  "kde_autocorrelation", "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes",
                  "kde_lscv_autocorr_batch", "kde_lscv_cands_create", "kde_lscv_cands_destroy",
-                 "kde_lscv_autocorr_cands", "kde_wait_probe"):
+                 "kde_lscv_autocorr_cands", "kde_wait_probe", "kde_plan_check",
+                 "kde_outside_check"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -560,14 +565,16 @@ class BatchPlan:
         return density
 
 
-NOALLOC_SCRATCH_BYTES = 8 << 20
+def noalloc_scratch_bytes() -> int:
+    """Size of the library's fixed scratch array (kde_noalloc_scratch_bytes)."""
+    return int(lib().kde_noalloc_scratch_bytes())
 
 
 def kde_fft_eval_noalloc(plan: Plan, counts, Kspec, density, stream=None):
     """kde_fft_eval with the library's fixed scratch array instead of a
     workspace (for callers that cannot allocate device memory at the call).
     The output tensor must be provided.  Plans needing more than
-    NOALLOC_SCRATCH_BYTES of scratch raise KDE_ERR_WORKSPACE."""
+    noalloc_scratch_bytes() of scratch raise KDE_ERR_WORKSPACE."""
     _check(lib().kde_fft_eval_noalloc(plan.handle, _ptr(counts), _ptr(Kspec), _ptr(density),
                                       _stream_ptr(stream)))
     return density
@@ -581,6 +588,24 @@ def kde_eval(X, H, lo, hi, M, n=None, stream=None, **opts):
     K = kde_kernel_grid(plan, X.shape[0] if n is None else n, workspace=ws, stream=stream)
     dens = kde_fft_eval(plan, counts, K, workspace=ws, stream=stream)
     return dens, counts, plan
+
+
+def plan_check(plan: Plan, stream=None):
+    """Raises KDEError(KDE_ERR_TIMEOUT) if a bounded device-side wait in one
+    of the plan's kernels gave up since the last check (synchronises)."""
+    _check(lib().kde_plan_check(plan.handle, _stream_ptr(stream)))
+
+
+def outside_check(n_outside, stream=None) -> int:
+    """Number of samples kde_bin dropped (device counter n_outside); raises
+    KDEError(KDE_ERR_OUT_OF_RANGE) if it is nonzero (synchronises)."""
+    v = ctypes.c_int64(0)
+    st = lib().kde_outside_check(_ptr(n_outside), _stream_ptr(stream), ctypes.byref(v))
+    if st not in (0, 3):
+        _check(st)
+    if st == 3:
+        raise KDEError(st, f"{v.value} samples fell outside the grid")
+    return v.value
 
 
 def launch_count() -> int:
@@ -674,10 +699,11 @@ class FeaturePrep:
     argument marshalled once: kde_standardize2 into Z, kde_bin (direct) of Z
     on the plan's grid, kde_features2, kde_autocorrelation.  run(X, feat, R)
     then makes the four C calls with only X's pointer and length and the two
-    outputs changing, on the stream given at construction; Z, counts,
-    moments and the workspace are owned here."""
+    outputs changing, on the stream passed to run() (default: torch's current
+    stream at that call, like every other binding); Z, counts, moments and
+    the workspace are owned here."""
 
-    def __init__(self, plan: Plan, n_max, workspace, stream=None):
+    def __init__(self, plan: Plan, n_max, workspace):
         import torch
         dev = workspace.device
         self.plan = plan
@@ -686,17 +712,16 @@ class FeaturePrep:
         self.moments = torch.empty(8, dtype=torch.float64, device=dev)
         self.ws = workspace
         self._L = lib()
-        self._s = _stream_ptr(stream)
         self._lo, self._hi, self._M = _darr(plan.lo), _darr(plan.hi), _iarr(plan.M)
         self._pZ, self._pc, self._pm = _ptr(self.Z), _ptr(self.counts), _ptr(self.moments)
         self._pws = _ptr(workspace)
         self._wsb = workspace.numel() * workspace.element_size()
         self._null = ctypes.c_void_p(0)
 
-    def run(self, X, feat, R):
+    def run(self, X, feat, R, stream=None):
         """X: n x 2 float32 CUDA tensor (n <= n_max); feat (FEAT_DIM) and R
         (P_0 x P_1) receive the features and the autocorrelation."""
-        L, s = self._L, self._s
+        L, s = self._L, _stream_ptr(stream)
         n = int(X.shape[0])
         if n > self.Z.shape[0] or X.dim() != 2 or X.shape[1] != 2 or not X.is_contiguous() \
                 or X.dtype != self.Z.dtype or not X.is_cuda:
@@ -797,3 +822,9 @@ class MLP:
         f = ctypes.c_int()
         _check(lib().kde_mlp_status(self.handle, ctypes.byref(f)))
         return f.value
+
+    def check(self):
+        """Raises KDEError(KDE_ERR_TIMEOUT) if a tensor-core wait of this
+        network gave up (its last results are then invalid); synchronises."""
+        if self.status():
+            raise KDEError(6, "a tensor-core wait of the network gave up; results are invalid")

@@ -180,6 +180,7 @@ def train(mlp, feats, theta, epochs=30, batch=256, lr=1e-3, seed=0, device="cuda
             acc += float(loss.item())
             nb += 1
         hist.append(acc / max(1, nb))
+    mlp.check()
     return hist
 
 
@@ -192,6 +193,7 @@ def select(scorer, mlp, X, refine=True, fallback=True, scored=None):
     torch = scorer.torch
     f = scorer.prepare(X)
     th = mlp.forward(f.view(1, -1)).cpu().numpy()[0].astype(np.float64)
+    mlp.check()
     # keep the neighbourhood inside the box the plan's padding was sized for
     lo = np.array([A_GRID[0], BETA_GRID[0], C_GRID[0]]) - 0.5 * STEP
     hi = np.array([A_GRID[-1], BETA_GRID[-1], C_GRID[-1]]) + 0.5 * STEP
@@ -233,6 +235,7 @@ def select_batch(scorer, mlp, datasets, fallback=True, scored=None):
     TH = torch.empty(B, 3, dtype=torch.float32, device=dev)
     for s0 in range(0, B, mlp.max_batch):
         mlp.forward(F[s0:s0 + mlp.max_batch], Y=TH[s0:s0 + mlp.max_batch])
+    mlp.check()
     TH = TH.cpu().numpy().astype(np.float64)
     lo = np.array([A_GRID[0], BETA_GRID[0], C_GRID[0]]) - 0.5 * STEP
     hi = np.array([A_GRID[-1], BETA_GRID[-1], C_GRID[-1]]) + 0.5 * STEP

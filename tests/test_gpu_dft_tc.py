@@ -36,6 +36,7 @@ def run(K, w, **opts):
     Ks = K.kde_kernel_grid(plan, w.n, workspace=ws)
     dens = K.kde_fft_eval(plan, counts, Ks, workspace=ws)
     torch.cuda.synchronize()
+    K.plan_check(plan)   # no tensor-core wait gave up (else the output is invalid)
     return dens.cpu().numpy(), counts, plan
 
 
@@ -75,6 +76,7 @@ def test_power_spectrum_matches_fft_path(K):
     for dft in ("fft", "tc"):
         plan = K.Plan(w.M, w.lo, w.hi, w.H, precision="f32", dft=dft)
         out.append(K.kde_power_spectrum(plan, counts, workspace=plan.workspace()).cpu().numpy())
+        K.plan_check(plan)
     assert rel_err(out[1], out[0]) <= 2e-5
 
 

@@ -186,3 +186,28 @@ def test_learned_proposal_beats_the_method_without_it():
     for X in test_sets:
         vs.append(Lm.select(sc, mlp, torch.from_numpy(X).to(DEV), fallback=False)[1])
     assert np.allclose(vb, np.array(vs), rtol=1e-12, atol=0)
+
+
+def test_fallback_replaces_a_bad_proposal_by_the_plain_search():
+    """A network that always proposes the most oversmoothed, most correlated
+    corner of the candidate box: its neighbourhood scores worse than the
+    normal-reference bandwidth, so both select and select_batch must fall
+    back to the plain search and return exactly its (theta, LSCV)."""
+    sc = Lm.LscvScorer(10_000)
+    mlp = kde.MLP(in_dim=kde.FEAT_DIM, hidden=256, out_dim=3, max_batch=256, seed=0)
+    p = mlp.get_params()
+    p[:] = 0.0
+    p[-3:] = [Lm.A_GRID[-1], Lm.BETA_GRID[-1], Lm.C_GRID[-1]]
+    mlp.set_params(p)
+    sets = W.mixture_datasets(41, 6)
+    res_b = Lm.select_batch(sc, mlp, sets, fallback=True)
+    for X, rb in zip(sets, res_b):
+        Xd = torch.from_numpy(X).to(DEV)
+        th, v, k, fell = Lm.select(sc, mlp, Xd, fallback=True)
+        sc.prepare(Xd)
+        t_s, v_s = sc.search()
+        assert fell and rb[3]
+        assert k == 28 + len(sc.cand) and rb[2] == 28 + len(sc.cand)
+        assert np.array_equal(th, t_s) and v == v_s
+        assert np.array_equal(rb[0], t_s) and rb[1] == v_s
+    mlp.check()
