@@ -51,10 +51,12 @@ enum { KDE_F32 = 0, KDE_F64 = 1 };                   /* element types */
 enum { KDE_RANGE_CORRECTED = 0, KDE_RANGE_PER_AXIS = 1 };
 enum { KDE_LAYOUT_CORRECTED = 0, KDE_LAYOUT_WAND = 1 };
 enum { KDE_COLS_AUTO = 0, KDE_COLS_LINES = 1, KDE_COLS_SIMD = 2 };
+enum { KDE_ENGINE_AUTO = 0, KDE_ENGINE_STOCKHAM = 1, KDE_ENGINE_TWO_PHASE = 2 };
 
 #define KDE_MAX_D 3
 #define KDE_MAX_P 4096      /* largest padded length of one axis */
 #define KDE_MAX_STAGES 16
+#define KDE_TWO_PHASE_MAX 40 /* largest factor N1, N2 of a two-phase line length */
 
 /* Evaluation options.
  *   tau         Eq. 15's support constant (the paper finds about 3.7 for the
@@ -81,7 +83,18 @@ enum { KDE_COLS_AUTO = 0, KDE_COLS_LINES = 1, KDE_COLS_SIMD = 2 };
  *               tensor cores in split TF32 (operands x = x_hi + x_lo, three
  *               products hi*hi + hi*lo + lo*hi, FP32 accumulation), about 2^-21
  *               relative per product; the plan then holds the DFT matrix
- *               (2 x 4 x roundup(2Q, 64) x roundup(M_last, 32) bytes). */
+ *               (2 x 4 x roundup(2Q, 64) x roundup(M_last, 32) bytes).
+ *   engine      how kde_kernel_grid and kde_fft_eval transform.
+ *               KDE_ENGINE_TWO_PHASE (KDE_F32 plans, d >= 2): every line of
+ *               length P_k = N1 N2 (N1, N2 <= KDE_TWO_PHASE_MAX, 7-smooth) is
+ *               an N1-point DFT per thread in registers, one exchange
+ *               through shared memory, an N2-point DFT per thread; P_k is
+ *               then the smallest such product >= M_k + L_k.
+ *               KDE_ENGINE_STOCKHAM: mixed-radix passes through shared
+ *               memory, P_k the smallest 7-smooth size >= M_k + L_k.
+ *               KDE_ENGINE_AUTO: two-phase where it applies (KDE_F32, d >= 2,
+ *               every padded length a product as above), else Stockham.
+ *               The result is the same up to rounding. */
 typedef struct {
   double tau;
   int precision;
@@ -90,18 +103,23 @@ typedef struct {
   int64_t P_min[KDE_MAX_D];
   int cols_variant;
   int dft_tc;
+  int engine;
 } kde_opts;
 
 /* Everything the plan derives on the host, in FP64.
  *   delta[k]   binwidth (Eq. 4); lambda_max  largest eigenvalue of H;
  *   L[k]       effective support (Eq. 15, or the per-axis range);
- *   P[k]       padded FFT length: the smallest 2^a 3^b 5^c 7^e >= M_k + L_k
- *              (and >= P_min[k]); cyclic convolution of that length equals the
- *              linear one of Eq. 7 on [0, M_k) (Eq. 10, zero padding);
+ *   P[k]       padded FFT length >= M_k + L_k (and >= P_min[k]): the smallest
+ *              2^a 3^b 5^c 7^e (Stockham engine) or the smallest product N1 N2
+ *              of two such factors <= KDE_TWO_PHASE_MAX (two-phase engine);
+ *              cyclic convolution of that length equals the linear one of
+ *              Eq. 7 on [0, M_k) (Eq. 10, zero padding);
  *   Q          P[d-1]/2 + 1, the half-spectrum length of the last axis;
  *   kspec_elems   elements of the real kernel spectrum: P_0 ... P_{d-2} Q;
  *   workspace_bytes  scratch needed by kde_kernel_grid and kde_fft_eval;
- *   radix/nstages    the mixed-radix factorisation used per axis. */
+ *   radix/nstages    the mixed-radix factorisation used per axis;
+ *   engine     KDE_ENGINE_STOCKHAM or KDE_ENGINE_TWO_PHASE, as chosen;
+ *   split[k]   N1, N2 of axis k with the two-phase engine (0 otherwise). */
 typedef struct {
   int d;
   int precision;
@@ -117,6 +135,8 @@ typedef struct {
   size_t workspace_bytes;
   int nstages[KDE_MAX_D];
   int radix[KDE_MAX_D][KDE_MAX_STAGES];
+  int engine;
+  int split[KDE_MAX_D][2];
 } kde_plan_info;
 
 typedef struct kde_plan_s* kde_plan;

@@ -1,0 +1,248 @@
+// Two-phase FFT passes (FP32) for kde_kernel_grid and kde_fft_eval: the
+// convolution of Eq. 10 in the wrapped, zero-padded form, with every line of
+// padded length P = N1 N2 transformed as
+//   phase A: thread n2 (0 <= n2 < N2) holds x[n2 + N2 n1], n1 < N1, takes
+//            their N1-point DFT in registers, multiplies entry k1 by
+//            e^{-2 pi i n2 k1 / P} and writes it to shared memory;
+//   phase B: thread k1 (0 <= k1 < N1) reads those N2 values and takes their
+//            N2-point DFT in registers, which gives X[k1 + N1 k2], k2 < N2.
+// The inverse runs the same steps backwards (B then A, conjugate twiddles),
+// so a forward transform, a pointwise product and the inverse need two
+// exchanges through shared memory.  Input positions n2 + N2 n1 and output
+// positions k1 + N1 k2 are contiguous across neighbouring threads, so lines
+// are read from and written to global memory directly.
+//
+// Passes (row-major, last axis contiguous, Q = P_last/2 + 1):
+//   rows:  two real rows ride in one complex line (x + i y), split into their
+//          half spectra after phase B (counts, or the kernel grid generated
+//          on the fly); the inverse rebuilds the pair from Hermitian symmetry
+//          and writes the rows cropped;
+//   cols:  B adjacent columns per block (column index fastest across
+//          threads); modes forward, forward to the real kernel spectrum (two
+//          Hermitian columns per line), forward * K * inverse with crop (the
+//          leading axis), inverse with crop.
+// Only lines that hold data are transformed and only lines that survive the
+// crop are inverse-transformed; positions beyond the data are zero padding.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+
+#include "fx_kernels.cuh"
+
+namespace kde {
+namespace fx {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+  }
+  return sms;
+}
+
+Line line_of(const kde_plan_info& I, int k) {
+  Line l;
+  l.P = (int)I.P[k];
+  l.N1 = I.split[k][0];
+  l.N2 = I.split[k][1];
+  l.magic1 = (unsigned)((1ull << 32) / (unsigned)l.N1 + 1ull);
+  return l;
+}
+
+int cls_of(const Line& l) { return std::max(l.N1, l.N2) <= kSmallMax ? 0 : 1; }
+int max_threads(int cls) { return cls == 0 ? kThreadsSmall : kThreadsLarge; }
+
+// Lanes in use over both phases of a block of B lines (phase A uses B N2
+// threads, phase B B N1, the block rounds max of them up to whole warps).
+double lane_use(int B, const Line& l) {
+  const int T = B * std::max(l.N1, l.N2);
+  const double warps = (double)((T + 31) / 32 * 32);
+  return 0.5 * (B * l.N1 + B * l.N2) / warps;
+}
+
+// Lines per block for nlines lines: the block count should cover the SMs,
+// and whole warps should be busy; score = min(1, blocks / SMs) x lane use.
+int pick_lines(int64_t nlines, const Line& l, int cls, bool pow2) {
+  const int maxN = std::max(l.N1, l.N2);
+  int best = 1;
+  double best_s = -1.0;
+  for (int B = 1; B * maxN <= max_threads(cls) && B <= 64; B = pow2 ? 2 * B : B + 1) {
+    const int64_t blocks = (nlines + B - 1) / B;
+    const double cover = std::min(1.0, (double)blocks / (double)num_sms());
+    const double s = cover * lane_use(B, l);
+    if (s > best_s + 1e-9) {
+      best_s = s;
+      best = B;
+    }
+  }
+  return best;
+}
+
+kde_status done(cudaError_t e, const char* name) {
+  return e == cudaSuccess ? KDE_OK : cuda_fail(e, name);
+}
+
+const float2* twiddles(const kde_plan_s* plan, int k) {
+  return reinterpret_cast<const float2*>((const char*)plan->tw_dev + plan->tw_offset[k]);
+}
+
+// Row pass: SRC_COUNTS (counts rows -> half spectra), SRC_KGEN (kernel-grid
+// rows -> half spectra) or the inverse (half spectra -> rows, cropped).
+kde_status rows_pass(const kde_plan_s* plan, int kind, int64_t nrows, const long long* counts,
+                     int Min, int64_t in_stride, const KGen<float>* g, float2* out,
+                     const float2* in, float* out_real, int Mout, cudaStream_t st) {
+  const kde_plan_info& I = plan->info;
+  const int dl = I.d - 1;
+  RowsArgs a{};
+  a.nrows = nrows;
+  a.Min = Min;
+  a.in_stride = in_stride;
+  a.Q = (int)I.Q;
+  a.Mout = Mout;
+  a.ln = line_of(I, dl);
+  a.out = out;
+  a.in = in;
+  a.out_real = out_real;
+  a.tw = twiddles(plan, dl);
+  a.SK = a.ln.N2 | 1;
+  const int cls = cls_of(a.ln);
+  const int64_t pairs = (nrows + 1) / 2;
+  a.B = pick_lines(pairs, a.ln, cls, false);
+  const int threads = (a.B * std::max(a.ln.N1, a.ln.N2) + 31) / 32 * 32;
+  // exchange buffers, plus the staged kernel values of the kernel-grid rows
+  const size_t smem = ((size_t)a.B * a.ln.N1 * a.SK + (kind == SRC_KGEN ? (size_t)a.B * a.ln.P : 0)) *
+                      sizeof(float2);
+  if (smem > kSmemMax) return fail(KDE_ERR_UNSUPPORTED, "two-phase row block too large");
+  const Launch l{cls, dim3((unsigned)((pairs + a.B - 1) / a.B)), threads, smem, st};
+  if (kind == 2) {
+    LaunchScope ls("kde_fx_rows_c2r_kernel", st);
+    return done(launch_rows_c2r(l, a), "kde_fx_rows_c2r_kernel");
+  }
+  if (kind == SRC_COUNTS) {
+    LaunchScope ls("kde_fx_rows_r2c_counts_kernel", st);
+    return done(launch_rows_counts(l, a, counts), "kde_fx_rows_r2c_counts_kernel");
+  }
+  LaunchScope ls("kde_fx_rows_r2c_kgen_kernel", st);
+  return done(launch_rows_kgen(l, a, *g), "kde_fx_rows_r2c_kgen_kernel");
+}
+
+// Column pass along axis k over S columns of O slabs.
+template <int MODE>
+kde_status cols_pass(const kde_plan_s* plan, int k, const char* name, const float2* in,
+                     float2* out, float* out_real, const float* K, int64_t S, int64_t O, int Nin,
+                     int Nout, int Lw, cudaStream_t st) {
+  const kde_plan_info& I = plan->info;
+  ColsArgs a{};
+  a.in = in;
+  a.out = out;
+  a.out_real = out_real;
+  a.K = K;
+  a.S = S;
+  a.Nin = Nin;
+  a.Nout = Nout;
+  a.Lw = Lw;
+  a.ln = line_of(I, k);
+  a.tw = twiddles(plan, k);
+  const int cls = cls_of(a.ln);
+  const int64_t lines = (MODE == COL_FWD_REAL ? (S + 1) / 2 : S);
+  // lines per block over all slabs; at most 16 adjacent columns
+  int B = pick_lines(lines * O, a.ln, cls, true);
+  while (B > 1 && B > lines) B /= 2;
+  B = std::min(B, 16);
+  a.B = B;
+  a.lgB = 0;
+  while ((1 << a.lgB) < B) ++a.lgB;
+  if (B < 16) {
+    a.SK = B * a.ln.N2;
+    while (a.SK % 16 != B % 16) ++a.SK;
+  } else {
+    a.SK = B * a.ln.N2;
+  }
+  const int threads = (B * std::max(a.ln.N1, a.ln.N2) + 31) / 32 * 32;
+  const size_t smem = (size_t)a.ln.N1 * a.SK * sizeof(float2);
+  if (smem > kSmemMax) return fail(KDE_ERR_UNSUPPORTED, "two-phase column block too large");
+  const Launch l{cls, dim3((unsigned)((lines + B - 1) / B), (unsigned)O), threads, smem, st};
+  LaunchScope ls(name, st);
+  cudaError_t e;
+  switch (MODE) {
+    case COL_FWD: e = launch_cols_fwd(l, a); break;
+    case COL_FWD_REAL: e = launch_cols_real(l, a); break;
+    case COL_MID: e = launch_cols_mid(l, a); break;
+    default: e = launch_cols_inv(l, a); break;
+  }
+  return done(e, name);
+}
+
+}  // namespace
+}  // namespace fx
+
+// Kernel grid and its real spectrum, two-phase engine (FP32, d = 2 or 3).
+// Layout of Kspec: row-major [P_0][P_1 ... P_{d-2}][Q].
+kde_status fx_kernel_grid(kde_plan_s* plan, const KGen<float>& gen, void* Kspec, void* ws,
+                          cudaStream_t st) {
+  using namespace fx;
+  const kde_plan_info& I = plan->info;
+  const int d = I.d;
+  float2* t1 = (float2*)ws;
+  int64_t rows = 1;
+  for (int k = 0; k < d - 1; ++k) rows *= 2 * I.L[k] + 1;
+  kde_status s = rows_pass(plan, SRC_KGEN, rows, nullptr, 0, 0, &gen, t1, nullptr, nullptr, 0, st);
+  if (s != KDE_OK) return s;
+  if (d == 2)
+    return cols_pass<COL_FWD_REAL>(plan, 0, "kde_fx_cols_kgen_real_kernel", t1, nullptr,
+                                   (float*)Kspec, nullptr, I.Q, 1, (int)(2 * I.L[0] + 1), 0,
+                                   (int)I.L[0], st);
+  // d == 3: axis 1 (wrapped lags) into t2, then axis 0 to the real spectrum
+  float2* t2 = t1 + rows * I.Q;
+  s = cols_pass<COL_FWD>(plan, 1, "kde_fx_cols_kgen_kernel", t1, t2, nullptr, nullptr, I.Q,
+                         2 * I.L[0] + 1, (int)(2 * I.L[1] + 1), (int)I.P[1], (int)I.L[1], st);
+  if (s != KDE_OK) return s;
+  return cols_pass<COL_FWD_REAL>(plan, 0, "kde_fx_cols_kgen_real_kernel", t2, nullptr,
+                                 (float*)Kspec, nullptr, I.P[1] * I.Q, 1, (int)(2 * I.L[0] + 1), 0,
+                                 (int)I.L[0], st);
+}
+
+// Density from counts and the kernel spectrum, two-phase engine.
+kde_status fx_fft_eval(kde_plan_s* plan, const long long* counts, const float* Kspec,
+                       float* density, void* ws, cudaStream_t st) {
+  using namespace fx;
+  const kde_plan_info& I = plan->info;
+  const int d = I.d, dl = d - 1;
+  float2* A = (float2*)ws;  // [M_0 .. M_{d-2}][Q]
+  int64_t rows = 1;
+  for (int k = 0; k < dl; ++k) rows *= I.M[k];
+  kde_status s;
+  if (plan->dft_tc)
+    s = dft_tc_rows(plan, counts, rows, A, st);
+  else
+    s = rows_pass(plan, SRC_COUNTS, rows, counts, (int)I.M[dl], I.M[dl], nullptr, A, nullptr,
+                  nullptr, 0, st);
+  if (s != KDE_OK) return s;
+  if (d == 2) {
+    s = cols_pass<COL_MID>(plan, 0, "kde_fx_cols_mid_kernel", A, A, nullptr, Kspec, I.Q, 1,
+                           (int)I.M[0], (int)I.M[0], -1, st);
+  } else {
+    float2* Bf = A + rows * I.Q;  // [M_0][P_1][Q]
+    s = cols_pass<COL_FWD>(plan, 1, "kde_fx_cols_fwd_kernel", A, Bf, nullptr, nullptr, I.Q, I.M[0],
+                           (int)I.M[1], (int)I.P[1], -1, st);
+    if (s != KDE_OK) return s;
+    s = cols_pass<COL_MID>(plan, 0, "kde_fx_cols_mid_kernel", Bf, Bf, nullptr, Kspec,
+                           I.P[1] * I.Q, 1, (int)I.M[0], (int)I.M[0], -1, st);
+    if (s != KDE_OK) return s;
+    s = cols_pass<COL_INV>(plan, 1, "kde_fx_cols_inv_kernel", Bf, A, nullptr, nullptr, I.Q, I.M[0],
+                           (int)I.P[1], (int)I.M[1], -1, st);
+  }
+  if (s != KDE_OK) return s;
+  return rows_pass(plan, 2, rows, nullptr, 0, 0, nullptr, nullptr, A, density, (int)I.M[dl], st);
+}
+
+}  // namespace kde

@@ -51,6 +51,16 @@ kde_status dft_tc_setup(kde_plan_s* plan);
 kde_status dft_tc_rows(const kde_plan_s* plan, const long long* counts, int64_t rows, void* out,
                        cudaStream_t st);
 
+// Two-phase engine (eval_fx.cu, KDE_F32 plans with engine
+// KDE_ENGINE_TWO_PHASE): the kernel grid and its spectrum, and the
+// evaluation, with the same arguments as the Stockham passes.
+template <typename T>
+struct KGen;
+kde_status fx_kernel_grid(kde_plan_s* plan, const KGen<float>& gen, void* Kspec, void* ws,
+                          cudaStream_t st);
+kde_status fx_fft_eval(kde_plan_s* plan, const long long* counts, const float* Kspec,
+                       float* density, void* ws, cudaStream_t st);
+
 // Launch bookkeeping: counts launches and, when profiling is on, records a
 // pair of events around each launch on its stream.
 struct LaunchScope {

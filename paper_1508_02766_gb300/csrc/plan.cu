@@ -183,6 +183,23 @@ static bool is_7smooth(int64_t x) {
   return x == 1;
 }
 
+// Two-phase engine: a line length P = N1 N2 with 2 <= N1 <= N2 <=
+// KDE_TWO_PHASE_MAX, both 7-smooth (the register DFT sizes).  Returns the
+// most balanced such split of P (smallest N2), or false if there is none.
+static bool two_phase_split(int64_t P, int* N1, int* N2) {
+  int best = 0;
+  for (int a = 2; a * a <= P; ++a) {
+    if (P % a) continue;
+    const int64_t b = P / a;
+    if (b > KDE_TWO_PHASE_MAX || !is_7smooth(a) || !is_7smooth(b)) continue;
+    best = a;  // later a are larger, so b is smaller: more balanced
+  }
+  if (!best) return false;
+  *N1 = best;
+  *N2 = (int)(P / best);
+  return true;
+}
+
 // Factor P into the engine's radices with the fewest stages (then the
 // fewest odd radices), largest radix first.  Dynamic programming over the
 // divisors of P.
@@ -304,8 +321,40 @@ static kde_status compute_info(int d, const int64_t* M, const double* lo, const 
     int64_t need = M[k] + L;
     if (o.P_min[k] > need) need = o.P_min[k];
     if (need > KDE_MAX_P) return fail(KDE_ERR_UNSUPPORTED, "padded size above KDE_MAX_P");
-    int64_t P = need;
-    while (!is_7smooth(P)) ++P;
+    info->P[k] = need;
+  }
+  // Engine and padded sizes.  The two-phase engine takes the smallest
+  // product N1 N2 >= M_k + L_k per axis; the Stockham engine the smallest
+  // 7-smooth size.  Either is a valid P (Eq. 10 needs only P_k >= M_k + L_k).
+  if (o.engine < KDE_ENGINE_AUTO || o.engine > KDE_ENGINE_TWO_PHASE)
+    return fail(KDE_ERR_INVALID_ARG, "bad engine");
+  const bool tp_ok = o.precision == KDE_F32 && d >= 2;
+  if (o.engine == KDE_ENGINE_TWO_PHASE && !tp_ok)
+    return fail(KDE_ERR_UNSUPPORTED, "the two-phase engine needs a KDE_F32 plan with d >= 2");
+  bool tp = tp_ok && o.engine != KDE_ENGINE_STOCKHAM;
+  int64_t Ptp[KDE_MAX_D] = {0, 0, 0};
+  int sp[KDE_MAX_D][2] = {};
+  for (int k = 0; tp && k < d; ++k) {
+    int64_t P = info->P[k];
+    const int64_t pmax = (int64_t)KDE_TWO_PHASE_MAX * KDE_TWO_PHASE_MAX;
+    while (P <= pmax && !two_phase_split(P, &sp[k][0], &sp[k][1])) ++P;
+    if (P > pmax) {
+      if (o.engine == KDE_ENGINE_TWO_PHASE)
+        return fail(KDE_ERR_UNSUPPORTED, "padded size above the two-phase engine's largest line");
+      tp = false;
+    }
+    Ptp[k] = P;
+  }
+  info->engine = tp ? KDE_ENGINE_TWO_PHASE : KDE_ENGINE_STOCKHAM;
+  for (int k = 0; k < d; ++k) {
+    int64_t P = info->P[k];
+    if (tp) {
+      P = Ptp[k];
+      info->split[k][0] = sp[k][0];
+      info->split[k][1] = sp[k][1];
+    } else {
+      while (!is_7smooth(P)) ++P;
+    }
     if (P > KDE_MAX_P) return fail(KDE_ERR_UNSUPPORTED, "padded size above KDE_MAX_P");
     info->P[k] = P;
     info->nstages[k] = radix_plan(P, info->radix[k]);

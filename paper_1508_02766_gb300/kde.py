@@ -35,7 +35,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("precision", ctypes.c_int),
                 ("range_mode", ctypes.c_int), ("layout_mode", ctypes.c_int),
                 ("P_min", ctypes.c_int64 * MAX_D), ("cols_variant", ctypes.c_int),
-                ("dft_tc", ctypes.c_int)]
+                ("dft_tc", ctypes.c_int), ("engine", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -46,7 +46,8 @@ class PlanInfo(ctypes.Structure):
                 ("det_H", ctypes.c_double), ("kspec_elems", ctypes.c_int64),
                 ("kspec_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
                 ("nstages", ctypes.c_int * MAX_D),
-                ("radix", (ctypes.c_int * MAX_STAGES) * MAX_D)]
+                ("radix", (ctypes.c_int * MAX_STAGES) * MAX_D), ("engine", ctypes.c_int),
+                ("split", (ctypes.c_int * 2) * MAX_D)]
 
 
 class BatchItem(ctypes.Structure):
@@ -175,12 +176,14 @@ def _iarr(vals):
 
 
 COLS_VARIANTS = {"auto": 0, "lines": 1, "simd": 2}
+ENGINES = {"auto": 0, "stockham": 1, "two_phase": 2}
 
 
 def _opts(tau=3.7, precision="f32", range_mode="corrected", layout="corrected", P_min=None,
-          cols="auto", dft="fft"):
+          cols="auto", dft="fft", engine="auto"):
     o = Opts()
     o.cols_variant = COLS_VARIANTS[cols]
+    o.engine = ENGINES[engine]
     o.dft_tc = {"fft": 0, "tc": 1}[dft]
     o.tau = tau
     o.precision = F32 if precision == "f32" else F64
@@ -206,6 +209,8 @@ class Info:
     kspec_bytes: int
     workspace_bytes: int
     radices: tuple
+    engine: str
+    split: tuple
 
 
 def _info(pi: PlanInfo) -> Info:
@@ -213,7 +218,9 @@ def _info(pi: PlanInfo) -> Info:
     return Info(d, "f32" if pi.precision == F32 else "f64", tuple(pi.M[:d]), tuple(pi.L[:d]),
                 tuple(pi.P[:d]), pi.Q, tuple(pi.delta[:d]), pi.lambda_max, pi.det_H,
                 pi.kspec_elems, pi.kspec_bytes, pi.workspace_bytes,
-                tuple(tuple(pi.radix[k][:pi.nstages[k]]) for k in range(d)))
+                tuple(tuple(pi.radix[k][:pi.nstages[k]]) for k in range(d)),
+                {1: "stockham", 2: "two_phase"}.get(pi.engine, "stockham"),
+                tuple((pi.split[k][0], pi.split[k][1]) for k in range(d)))
 
 
 def kde_plan_info_compute(M, lo, hi, H, **opts) -> Info:

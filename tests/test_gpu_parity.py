@@ -57,11 +57,12 @@ SMALL = [
 ]
 
 
-@pytest.mark.parametrize("method,cols", [("tiled", "lines"), ("direct", "simd")])
+@pytest.mark.parametrize("method,cols,engine", [("tiled", "lines", "auto"), ("direct", "simd", "auto"),
+                                                ("direct", "lines", "stockham")])
 @pytest.mark.parametrize("d,M,prec", SMALL)
-def test_small_grids_every_node(K, d, M, prec, method, cols):
+def test_small_grids_every_node(K, d, M, prec, method, cols, engine):
     w = W.small_case(100 + d * 7 + len(M) + M[0], d, M, n=3000, precision=prec)
-    dens, counts, nout, plan = run_gpu(K, w, method=method, cols=cols)
+    dens, counts, nout, plan = run_gpu(K, w, method=method, cols=cols, engine=engine)
     f, c_ref, L, nout_ref = oracle_full(w)
     assert plan.info.L == L
     assert nout == nout_ref

@@ -44,21 +44,58 @@ def _is_7smooth(x):
     return x == 1
 
 
+def _two_phase(P, limit=40):
+    """Most balanced split P = N1 N2 with 2 <= N1 <= N2 <= limit, both 7-smooth."""
+    best = None
+    for a in range(2, int(P ** 0.5) + 1):
+        if P % a == 0 and P // a <= limit and _is_7smooth(a) and _is_7smooth(P // a):
+            best = (a, P // a)
+    return best
+
+
 @pytest.mark.parametrize("name", ["kde2d_128_f64", "kde2d_1024_f32"])
 @pytest.mark.parametrize("range_mode", ["corrected", "per_axis"])
-def test_plan_matches_oracle_support(name, range_mode):
+@pytest.mark.parametrize("engine", ["auto", "stockham"])
+def test_plan_matches_oracle_support(name, range_mode, engine):
     w = W.WORKLOADS[name](n=2000)
     info = kde.kde_plan_info_compute(w.M, w.lo, w.hi, w.H, precision=w.precision,
-                                     range_mode=range_mode)
+                                     range_mode=range_mode, engine=engine)
     assert info.L == O.support_L(w.H, w.lo, w.hi, w.M, range_mode=range_mode)
     assert np.allclose(info.delta, O.binwidths(w.lo, w.hi, w.M), rtol=0, atol=0)
     assert abs(info.lambda_max - np.linalg.eigvalsh(w.H).max()) < 1e-14
+    two = engine == "auto" and w.precision == "f32"
+    assert info.engine == ("two_phase" if two else "stockham")
     for k in range(w.d):
-        assert info.P[k] >= w.M[k] + info.L[k]
+        need = w.M[k] + info.L[k]
+        assert info.P[k] >= need
         assert _is_7smooth(info.P[k])
-        assert all(not _is_7smooth(p) for p in range(w.M[k] + info.L[k], info.P[k]))
+        if two:
+            # the smallest product of two register-DFT sizes, split most evenly
+            assert info.split[k] == _two_phase(info.P[k])
+            assert all(_two_phase(p) is None for p in range(need, info.P[k]))
+        else:
+            assert info.split[k] == (0, 0)
+            assert all(not _is_7smooth(p) for p in range(need, info.P[k]))
         assert int(np.prod(info.radices[k])) == info.P[k]
     assert info.Q == info.P[-1] // 2 + 1
+
+
+def test_plan_two_phase_engine_limits():
+    # forced two-phase needs FP32 and d >= 2, and lines of at most 40 x 40
+    with pytest.raises(kde.KDEError) as e:
+        kde.kde_plan_info_compute((64, 64), (0, 0), (1, 1), np.eye(2) * 1e-3, precision="f64",
+                                  engine="two_phase")
+    assert e.value.status == 7
+    with pytest.raises(kde.KDEError) as e:
+        kde.kde_plan_info_compute((2000, 64), (0, 0), (1, 1), np.eye(2) * 1e-3, engine="two_phase")
+    assert e.value.status == 7
+    # auto falls back to the Stockham engine there
+    info = kde.kde_plan_info_compute((2000, 64), (0, 0), (1, 1), np.eye(2) * 1e-3)
+    assert info.engine == "stockham" and info.split == ((0, 0), (0, 0))
+    info = kde.kde_plan_info_compute((256, 256, 256), (0,) * 3, (1,) * 3, np.eye(3) * 1e-3)
+    assert info.engine == "two_phase"
+    for k in range(3):
+        assert info.split[k][0] * info.split[k][1] == info.P[k]
 
 
 def test_plan_3d_eigenvalue_and_support():
@@ -73,12 +110,14 @@ def test_plan_3d_eigenvalue_and_support():
 
 
 def test_plan_workload_sizes():
-    """The padded sizes of the benchmark workloads (smallest 7-smooth >= M + L)."""
+    """The padded sizes of the benchmark workloads (>= M + L)."""
     w = W.kde2d_128_f64()
     assert kde.kde_plan_info_compute(w.M, w.lo, w.hi, w.H, precision="f64").P == (144, 144)
     w = W.kde2d_1024_f32(n=100_000)
     info = kde.kde_plan_info_compute(w.M, w.lo, w.hi, w.H)
-    assert info.P == (1080, 1080)
+    assert info.P == (1080, 1080) and info.split == ((30, 36), (30, 36))
+    info = kde.kde_plan_info_compute(w.M, w.lo, w.hi, w.H, engine="stockham")
+    assert info.P == (1080, 1080) and info.engine == "stockham"
 
 
 def test_plan_rejects_bad_input():
