@@ -122,7 +122,7 @@ kde_status rows_pass(const kde_plan_s* plan, int kind, int64_t nrows, const long
   const size_t smem = ((size_t)a.B * a.ln.N1 * a.SK + (kind == SRC_KGEN ? (size_t)a.B * a.ln.P : 0)) *
                       sizeof(float2);
   if (smem > kSmemMax) return fail(KDE_ERR_UNSUPPORTED, "two-phase row block too large");
-  const Launch l{cls, dim3((unsigned)((pairs + a.B - 1) / a.B)), threads, smem, st};
+  const Launch l{a.ln.N1, a.ln.N2, dim3((unsigned)((pairs + a.B - 1) / a.B)), threads, smem, st};
   if (kind == 2) {
     LaunchScope ls("kde_fx_rows_c2r_kernel", st);
     return done(launch_rows_c2r(l, a), "kde_fx_rows_c2r_kernel");
@@ -170,7 +170,7 @@ kde_status cols_pass(const kde_plan_s* plan, int k, const char* name, const floa
   const int threads = (B * std::max(a.ln.N1, a.ln.N2) + 31) / 32 * 32;
   const size_t smem = (size_t)a.ln.N1 * a.SK * sizeof(float2);
   if (smem > kSmemMax) return fail(KDE_ERR_UNSUPPORTED, "two-phase column block too large");
-  const Launch l{cls, dim3((unsigned)((lines + B - 1) / B), (unsigned)O), threads, smem, st};
+  const Launch l{a.ln.N1, a.ln.N2, dim3((unsigned)((lines + B - 1) / B), (unsigned)O), threads, smem, st};
   LaunchScope ls(name, st);
   cudaError_t e;
   switch (MODE) {

@@ -34,6 +34,7 @@
 #include <type_traits>
 
 #include "fx_dft.cuh"
+#include "fx_pairs.h"
 #include "kde_internal.h"
 #include "kgen.cuh"
 
@@ -79,6 +80,21 @@ __device__ __forceinline__ void with_size(int n, F&& f) {
     }
   }
 #undef KDE_FX_CASE
+}
+
+// A kernel compiled for one split calls f with its fixed size NT; a generic
+// kernel (NT = 0) dispatches on the runtime size.
+template <int NT, int CLS, typename F>
+__device__ __forceinline__ void size_call(int n, F&& f) {
+  if constexpr (NT > 0)
+    f(std::integral_constant<int, NT>{});
+  else
+    with_size<CLS>(n, f);
+}
+
+template <int N1T, int N2T>
+constexpr int block_limit() {
+  return (N1T > 0 && N1T <= kSmallMax && N2T <= kSmallMax) || N1T == 0 ? kThreadsSmall : kThreadsLarge;
 }
 
 // Runtime split of a line: P = N1 N2; k / N1 = umulhi(k, magic1) for the
@@ -237,17 +253,17 @@ __device__ __forceinline__ void rows_stage_kgen(const RowsArgs& a, const KGen<fl
   }
 }
 
-template <int CLS, int SRC>
-__global__ void __launch_bounds__(CLS == 0 ? kThreadsSmall : kThreadsLarge)
+template <int CLS, int N1T, int N2T, int SRC>
+__global__ void __launch_bounds__(block_limit<N1T, N2T>())
 kde_fx_rows_fwd_kernel(RowsArgs a, const long long* __restrict__ counts, KGen<float> g) {
   extern __shared__ float2 fx_sm[];
   if constexpr (SRC == SRC_KGEN) {
     rows_stage_kgen(a, g, fx_sm + a.B * a.ln.N1 * a.SK);
     __syncthreads();
   }
-  with_size<CLS>(a.ln.N1, [&](auto N) { rows_a_fwd<decltype(N)::value, SRC>(a, counts, g, fx_sm); });
+  size_call<N1T, CLS>(a.ln.N1, [&](auto N) { rows_a_fwd<decltype(N)::value, SRC>(a, counts, g, fx_sm); });
   __syncthreads();
-  with_size<CLS>(a.ln.N2, [&](auto N) { rows_b_fwd<decltype(N)::value>(a, fx_sm); });
+  size_call<N2T, CLS>(a.ln.N2, [&](auto N) { rows_b_fwd<decltype(N)::value>(a, fx_sm); });
   __syncthreads();
   rows_split_store(a, fx_sm);
 }
@@ -304,13 +320,13 @@ __device__ __forceinline__ void rows_a_inv(const RowsArgs& a, const float2* sm) 
   }
 }
 
-template <int CLS>
-__global__ void __launch_bounds__(CLS == 0 ? kThreadsSmall : kThreadsLarge)
+template <int CLS, int N1T, int N2T>
+__global__ void __launch_bounds__(block_limit<N1T, N2T>())
 kde_fx_rows_c2r_kernel(RowsArgs a) {
   extern __shared__ float2 fx_sm[];
-  with_size<CLS>(a.ln.N2, [&](auto N) { rows_b_inv<decltype(N)::value>(a, fx_sm); });
+  size_call<N2T, CLS>(a.ln.N2, [&](auto N) { rows_b_inv<decltype(N)::value>(a, fx_sm); });
   __syncthreads();
-  with_size<CLS>(a.ln.N1, [&](auto N) { rows_a_inv<decltype(N)::value>(a, fx_sm); });
+  size_call<N1T, CLS>(a.ln.N1, [&](auto N) { rows_a_inv<decltype(N)::value>(a, fx_sm); });
 }
 
 // ---------------------------------------------------------------------------
@@ -462,24 +478,34 @@ __device__ __forceinline__ void cols_a_inv(const ColsArgs& a, const float2* sm) 
   }
 }
 
-template <int CLS, int MODE>
-__global__ void __launch_bounds__(CLS == 0 ? kThreadsSmall : kThreadsLarge)
+template <int CLS, int N1T, int N2T, int MODE>
+__global__ void __launch_bounds__(block_limit<N1T, N2T>())
 kde_fx_cols_kernel(ColsArgs a) {
   extern __shared__ float2 fx_sm[];
   if constexpr (MODE == COL_INV) {
-    with_size<CLS>(a.ln.N2, [&](auto N) { cols_b_inv<decltype(N)::value>(a, fx_sm); });
+    size_call<N2T, CLS>(a.ln.N2, [&](auto N) { cols_b_inv<decltype(N)::value>(a, fx_sm); });
     __syncthreads();
-    with_size<CLS>(a.ln.N1, [&](auto N) { cols_a_inv<decltype(N)::value, MODE>(a, fx_sm); });
+    size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_inv<decltype(N)::value, MODE>(a, fx_sm); });
   } else {
-    with_size<CLS>(a.ln.N1, [&](auto N) { cols_a_fwd<decltype(N)::value, MODE>(a, fx_sm); });
+    size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_fwd<decltype(N)::value, MODE>(a, fx_sm); });
     __syncthreads();
-    with_size<CLS>(a.ln.N2, [&](auto N) { cols_b_fwd<decltype(N)::value, MODE>(a, fx_sm); });
+    size_call<N2T, CLS>(a.ln.N2, [&](auto N) { cols_b_fwd<decltype(N)::value, MODE>(a, fx_sm); });
     if constexpr (MODE == COL_MID) {
       __syncthreads();
-      with_size<CLS>(a.ln.N1, [&](auto N) { cols_a_inv<decltype(N)::value, MODE>(a, fx_sm); });
+      size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_inv<decltype(N)::value, MODE>(a, fx_sm); });
     }
   }
 }
+
+// Launch of the kernel for the split (N1, N2): the one compiled for it if it
+// is in the list, else the generic kernel for factors up to 20.
+#define KDE_FX_DISPATCH(KERNEL_T, ...)                                                   \
+  switch (l.n1 * 64 + l.n2) {                                                          \
+    KDE_FX_PAIRS(KDE_FX_CASE_PAIR)                                                     \
+    default:                                                                           \
+      if (l.n1 > kSmallMax || l.n2 > kSmallMax) return cudaErrorInvalidConfiguration;  \
+      return launch_kernel(KERNEL_T(0, 0), l.grid, l.threads, l.smem, l.st, __VA_ARGS__); \
+  }
 
 // ---------------------------------------------------------------------------
 // Launchers, one translation unit each (fx_launch_*.cu, compiled in
@@ -512,7 +538,7 @@ cudaError_t launch_kernel(Kern* fn, dim3 grid, int threads, size_t smem, cudaStr
 }
 
 struct Launch {
-  int cls;
+  int n1, n2;  // the line split
   dim3 grid;
   int threads;
   size_t smem;

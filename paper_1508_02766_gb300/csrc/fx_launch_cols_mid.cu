@@ -6,8 +6,13 @@ namespace kde {
 namespace fx {
 
 cudaError_t launch_cols_mid(const Launch& l, const ColsArgs& a) {
-  if (l.cls == 0) return launch_kernel(kde_fx_cols_kernel<0, COL_MID>, l.grid, l.threads, l.smem, l.st, a);
-  return launch_kernel(kde_fx_cols_kernel<1, COL_MID>, l.grid, l.threads, l.smem, l.st, a);
+#define KDE_FX_KERNEL(n1, n2) kde_fx_cols_kernel<0, n1, n2, COL_MID>
+#define KDE_FX_CASE_PAIR(n1, n2) \
+  case n1 * 64 + n2:             \
+    return launch_kernel(KDE_FX_KERNEL(n1, n2), l.grid, l.threads, l.smem, l.st, a);
+  KDE_FX_DISPATCH(KDE_FX_KERNEL, a)
+#undef KDE_FX_CASE_PAIR
+#undef KDE_FX_KERNEL
 }
 
 }  // namespace fx

@@ -6,8 +6,13 @@ namespace kde {
 namespace fx {
 
 cudaError_t launch_rows_counts(const Launch& l, const RowsArgs& a, const long long* counts) {
-  if (l.cls == 0) return launch_kernel(kde_fx_rows_fwd_kernel<0, SRC_COUNTS>, l.grid, l.threads, l.smem, l.st, a, counts, KGen<float>{});
-  return launch_kernel(kde_fx_rows_fwd_kernel<1, SRC_COUNTS>, l.grid, l.threads, l.smem, l.st, a, counts, KGen<float>{});
+#define KDE_FX_KERNEL(n1, n2) kde_fx_rows_fwd_kernel<0, n1, n2, SRC_COUNTS>
+#define KDE_FX_CASE_PAIR(n1, n2) \
+  case n1 * 64 + n2:             \
+    return launch_kernel(KDE_FX_KERNEL(n1, n2), l.grid, l.threads, l.smem, l.st, a, counts, KGen<float>{});
+  KDE_FX_DISPATCH(KDE_FX_KERNEL, a, counts, KGen<float>{})
+#undef KDE_FX_CASE_PAIR
+#undef KDE_FX_KERNEL
 }
 
 }  // namespace fx

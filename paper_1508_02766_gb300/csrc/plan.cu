@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "fx_pairs.h"
 #include "kde_internal.h"
 
 namespace kde {
@@ -183,21 +184,39 @@ static bool is_7smooth(int64_t x) {
   return x == 1;
 }
 
-// Two-phase engine: a line length P = N1 N2 with 2 <= N1 <= N2 <=
-// KDE_TWO_PHASE_MAX, both 7-smooth (the register DFT sizes).  Returns the
-// most balanced such split of P (smallest N2), or false if there is none.
-static bool two_phase_split(int64_t P, int* N1, int* N2) {
-  int best = 0;
-  for (int a = 2; a * a <= P; ++a) {
-    if (P % a) continue;
-    const int64_t b = P / a;
-    if (b > KDE_TWO_PHASE_MAX || !is_7smooth(a) || !is_7smooth(b)) continue;
-    best = a;  // later a are larger, so b is smaller: more balanced
+// Two-phase engine: a line length P = N1 N2.  Up to 400 the generic kernels
+// take any split with 2 <= N1 <= N2 <= 20, both 7-smooth (the most balanced
+// one, smallest N2), unless a split with kernels of its own (fx_pairs.h) is
+// at most 10% longer; above 400 only those splits are used.  Returns the
+// chosen length >= need and its split, or 0 if there is none.
+static int64_t two_phase_plan(int64_t need, int* N1, int* N2) {
+  int64_t best_c = 0;
+  int c1 = 0, c2 = 0;
+  for (int i = 0; i < fxp::kNumPairs; ++i) {
+    const int64_t P = (int64_t)fxp::kPairs[i].N1 * fxp::kPairs[i].N2;
+    if (P >= need && (best_c == 0 || P < best_c)) {
+      best_c = P;
+      c1 = fxp::kPairs[i].N1;
+      c2 = fxp::kPairs[i].N2;
+    }
   }
-  if (!best) return false;
-  *N1 = best;
-  *N2 = (int)(P / best);
-  return true;
+  for (int64_t P = need; P <= fxp::kGenericMaxP; ++P) {
+    int a_best = 0;
+    for (int a = 2; a * a <= P; ++a) {
+      if (P % a) continue;
+      const int64_t b = P / a;
+      if (b > fxp::kGenericMax || !is_7smooth(a) || !is_7smooth(b)) continue;
+      a_best = a;  // later a are larger, so b is smaller: more balanced
+    }
+    if (!a_best) continue;
+    if (best_c && (double)best_c <= 1.1 * (double)P) break;  // the compiled split
+    *N1 = a_best;
+    *N2 = (int)(P / a_best);
+    return P;
+  }
+  *N1 = c1;
+  *N2 = c2;
+  return best_c;
 }
 
 // Factor P into the engine's radices with the fewest stages (then the
@@ -335,10 +354,8 @@ static kde_status compute_info(int d, const int64_t* M, const double* lo, const 
   int64_t Ptp[KDE_MAX_D] = {0, 0, 0};
   int sp[KDE_MAX_D][2] = {};
   for (int k = 0; tp && k < d; ++k) {
-    int64_t P = info->P[k];
-    const int64_t pmax = (int64_t)KDE_TWO_PHASE_MAX * KDE_TWO_PHASE_MAX;
-    while (P <= pmax && !two_phase_split(P, &sp[k][0], &sp[k][1])) ++P;
-    if (P > pmax) {
+    const int64_t P = two_phase_plan(info->P[k], &sp[k][0], &sp[k][1]);
+    if (P == 0) {
       if (o.engine == KDE_ENGINE_TWO_PHASE)
         return fail(KDE_ERR_UNSUPPORTED, "padded size above the two-phase engine's largest line");
       tp = false;

@@ -1,8 +1,12 @@
-"""The two-phase FFT engine (FP32): every register-DFT size it has, as both
-factors of a line (P = s^2, split s x s), on the row axis and on the column
-axis of small 2-D grids, each node against the FP64 oracle within the FP32
-path's 1e-5 (max error over max value); a few unbalanced splits; and the
-full-size workloads against the Stockham engine on the same counts."""
+"""The two-phase FFT engine (FP32): every factor size of its generic kernels
+as both factors of a line (P = s^2, split s x s) and every split that has
+kernels of its own, on the row axis and on the column axis of small 2-D
+grids, each node against the FP64 oracle within the FP32 path's 1e-5 (max
+error over max value); a few unbalanced splits; 3-D grids; and the
+full-size workloads against the Stockham engine."""
+import os
+import re
+
 import numpy as np
 import pytest
 
@@ -12,8 +16,18 @@ from paper_1508_02766_gb300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SIZES = [2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 18, 20, 21, 24, 25, 27, 28, 30, 32, 35,
-         36, 40]
+SIZES = [2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 18, 20]
+
+
+def compiled_pairs():
+    """The splits listed in the library's source (KDE_FX_PAIRS)."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "paper_1508_02766_gb300", "csrc", "fx_pairs.h")).read()
+    body = text[text.index("#define KDE_FX_PAIRS"):text.index("namespace kde")]
+    return [(int(a), int(b)) for a, b in re.findall(r"X\((\d+),\s*(\d+)\)", body)]
+
+
+PAIRS = compiled_pairs()
 
 
 @pytest.fixture(scope="module")
@@ -72,7 +86,19 @@ def test_every_factor_size(K, s, axis):
     assert rel_err(dens, f) <= 1e-5
 
 
-@pytest.mark.parametrize("split", [(2, 3), (5, 7), (8, 9), (21, 25), (35, 36), (30, 36), (14, 20)])
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("split", PAIRS)
+def test_every_compiled_split(K, split, axis):
+    P = split[0] * split[1]
+    w, Pmin, info = case_with_P(K, 800 + P, axis, P)
+    assert info.P[axis] == P and info.split[axis] == split
+    dens, counts, _ = run(K, w, P_min=Pmin, engine="two_phase")
+    f, c_ref, _, _ = O.binned_estimate(w.X, w.H, w.lo, w.hi, w.M, tau=w.tau)
+    assert np.array_equal(counts.cpu().numpy(), c_ref)
+    assert rel_err(dens, f) <= 1e-5
+
+
+@pytest.mark.parametrize("split", [(2, 3), (3, 7), (5, 7), (8, 9), (9, 14), (12, 15)])
 def test_unbalanced_splits(K, split):
     P = split[0] * split[1]
     for axis in (0, 1):

@@ -44,13 +44,26 @@ def _is_7smooth(x):
     return x == 1
 
 
-def _two_phase(P, limit=40):
-    """Most balanced split P = N1 N2 with 2 <= N1 <= N2 <= limit, both 7-smooth."""
-    best = None
-    for a in range(2, int(P ** 0.5) + 1):
-        if P % a == 0 and P // a <= limit and _is_7smooth(a) and _is_7smooth(P // a):
-            best = (a, P // a)
-    return best
+def _compiled_pairs():
+    text = open(os.path.join(ROOT, "paper_1508_02766_gb300", "csrc", "fx_pairs.h")).read()
+    body = text[text.index("#define KDE_FX_PAIRS"):text.index("namespace kde")]
+    return [(int(a), int(b)) for a, b in re.findall(r"X\((\d+),\s*(\d+)\)", body)]
+
+
+def _two_phase_plan(need):
+    """The two-phase planner's rule: up to 400, the smallest P >= need with a
+    split into 7-smooth factors <= 20 (most balanced), unless a compiled
+    split is at most 10% longer; above 400, the smallest compiled split."""
+    comp = sorted((a * b, (a, b)) for a, b in _compiled_pairs() if a * b >= need)
+    for P in range(need, 401):
+        splits = [(a, P // a) for a in range(2, int(P ** 0.5) + 1)
+                  if P % a == 0 and P // a <= 20 and _is_7smooth(a) and _is_7smooth(P // a)]
+        if not splits:
+            continue
+        if comp and comp[0][0] <= 1.1 * P:
+            break
+        return P, splits[-1]
+    return comp[0] if comp else (None, None)
 
 
 @pytest.mark.parametrize("name", ["kde2d_128_f64", "kde2d_1024_f32"])
@@ -70,9 +83,7 @@ def test_plan_matches_oracle_support(name, range_mode, engine):
         assert info.P[k] >= need
         assert _is_7smooth(info.P[k])
         if two:
-            # the smallest product of two register-DFT sizes, split most evenly
-            assert info.split[k] == _two_phase(info.P[k])
-            assert all(_two_phase(p) is None for p in range(need, info.P[k]))
+            assert (info.P[k], info.split[k]) == _two_phase_plan(need)
         else:
             assert info.split[k] == (0, 0)
             assert all(not _is_7smooth(p) for p in range(need, info.P[k]))
