@@ -56,7 +56,6 @@ enum { KDE_ENGINE_AUTO = 0, KDE_ENGINE_STOCKHAM = 1, KDE_ENGINE_TWO_PHASE = 2 };
 #define KDE_MAX_D 3
 #define KDE_MAX_P 4096      /* largest padded length of one axis */
 #define KDE_MAX_STAGES 16
-#define KDE_TWO_PHASE_MAX 40 /* largest factor N1, N2 of a two-phase line length */
 
 /* Evaluation options.
  *   tau         Eq. 15's support constant (the paper finds about 3.7 for the
@@ -86,10 +85,11 @@ enum { KDE_ENGINE_AUTO = 0, KDE_ENGINE_STOCKHAM = 1, KDE_ENGINE_TWO_PHASE = 2 };
  *               (2 x 4 x roundup(2Q, 64) x roundup(M_last, 32) bytes).
  *   engine      how kde_kernel_grid and kde_fft_eval transform.
  *               KDE_ENGINE_TWO_PHASE (KDE_F32 plans, d >= 2): every line of
- *               length P_k = N1 N2 (N1, N2 <= KDE_TWO_PHASE_MAX, 7-smooth) is
- *               an N1-point DFT per thread in registers, one exchange
- *               through shared memory, an N2-point DFT per thread; P_k is
- *               then the smallest such product >= M_k + L_k.
+ *               length P_k = N1 N2 is an N1-point DFT per thread in
+ *               registers, one exchange through shared memory, an N2-point
+ *               DFT per thread (P_k <= 400); longer lines, P_k = N1 N2 N3
+ *               (each about 10), take three such phases.  P_k is then the
+ *               smallest supported length >= M_k + L_k (at most 2048).
  *               KDE_ENGINE_STOCKHAM: mixed-radix passes through shared
  *               memory, P_k the smallest 7-smooth size >= M_k + L_k.
  *               KDE_ENGINE_AUTO: two-phase where it applies (KDE_F32, d >= 2,
@@ -110,8 +110,8 @@ typedef struct {
  *   delta[k]   binwidth (Eq. 4); lambda_max  largest eigenvalue of H;
  *   L[k]       effective support (Eq. 15, or the per-axis range);
  *   P[k]       padded FFT length >= M_k + L_k (and >= P_min[k]): the smallest
- *              2^a 3^b 5^c 7^e (Stockham engine) or the smallest product N1 N2
- *              of two such factors <= KDE_TWO_PHASE_MAX (two-phase engine);
+ *              2^a 3^b 5^c 7^e (Stockham engine) or the smallest length the
+ *              two-phase engine supports (see split);
  *              cyclic convolution of that length equals the linear one of
  *              Eq. 7 on [0, M_k) (Eq. 10, zero padding);
  *   Q          P[d-1]/2 + 1, the half-spectrum length of the last axis;
@@ -119,7 +119,10 @@ typedef struct {
  *   workspace_bytes  scratch needed by kde_kernel_grid and kde_fft_eval;
  *   radix/nstages    the mixed-radix factorisation used per axis;
  *   engine     KDE_ENGINE_STOCKHAM or KDE_ENGINE_TWO_PHASE, as chosen;
- *   split[k]   N1, N2 of axis k with the two-phase engine (0 otherwise). */
+ *   split[k]   the factors of P_k with the two-phase engine: N1, N2 and 0
+ *              for lines up to 400, N1, N2, N3 (three exchanges instead of
+ *              two, about 10 values per thread) for longer ones; all 0 with
+ *              the Stockham engine. */
 typedef struct {
   int d;
   int precision;
@@ -136,7 +139,7 @@ typedef struct {
   int nstages[KDE_MAX_D];
   int radix[KDE_MAX_D][KDE_MAX_STAGES];
   int engine;
-  int split[KDE_MAX_D][2];
+  int split[KDE_MAX_D][3];
 } kde_plan_info;
 
 typedef struct kde_plan_s* kde_plan;

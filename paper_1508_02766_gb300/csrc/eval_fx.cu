@@ -29,7 +29,7 @@
 #include <cstdint>
 #include <string>
 
-#include "fx_kernels.cuh"
+#include "fx3_kernels.cuh"
 
 namespace kde {
 namespace fx {
@@ -54,28 +54,57 @@ Line line_of(const kde_plan_info& I, int k) {
   l.P = (int)I.P[k];
   l.N1 = I.split[k][0];
   l.N2 = I.split[k][1];
+  l.N3 = I.split[k][2];
   l.magic1 = (unsigned)((1ull << 32) / (unsigned)l.N1 + 1ull);
   return l;
 }
 
-int cls_of(const Line& l) { return std::max(l.N1, l.N2) <= kSmallMax ? 0 : 1; }
-int max_threads(int cls) { return cls == 0 ? kThreadsSmall : kThreadsLarge; }
+// Entries per k1 row of a line's exchange buffer (N2, or N2 N3).
+int row_entries(const Line& l) { return l.N3 ? l.N2 * l.N3 : l.N2; }
 
-// Lanes in use over both phases of a block of B lines (phase A uses B N2
-// threads, phase B B N1, the block rounds max of them up to whole warps).
+// Threads each phase uses per line: two factors {N2, N1}; three
+// {N2 N3, N1 N3, N1 N2}.
+int phase_threads(const Line& l, int* t) {
+  if (!l.N3) {
+    t[0] = l.N2;
+    t[1] = l.N1;
+    return 2;
+  }
+  t[0] = l.N2 * l.N3;
+  t[1] = l.N1 * l.N3;
+  t[2] = l.N1 * l.N2;
+  return 3;
+}
+
+int threads_per_line(const Line& l) {
+  int t[3];
+  const int np = phase_threads(l, t);
+  return *std::max_element(t, t + np);
+}
+
+int max_threads(const Line& l) {
+  if (l.N3) return kThreads3;
+  return std::max(l.N1, l.N2) <= kSmallMax ? kThreadsSmall : kThreadsLarge;
+}
+
+// Lanes in use, averaged over the phases, of a block of B lines (the block
+// has B x threads_per_line threads rounded up to whole warps).
 double lane_use(int B, const Line& l) {
-  const int T = B * std::max(l.N1, l.N2);
-  const double warps = (double)((T + 31) / 32 * 32);
-  return 0.5 * (B * l.N1 + B * l.N2) / warps;
+  int t[3];
+  const int np = phase_threads(l, t);
+  const double slots = (double)((B * threads_per_line(l) + 31) / 32 * 32);
+  double u = 0.0;
+  for (int i = 0; i < np; ++i) u += B * t[i] / slots;
+  return u / np;
 }
 
 // Lines per block for nlines lines: the block count should cover the SMs,
 // and whole warps should be busy; score = min(1, blocks / SMs) x lane use.
-int pick_lines(int64_t nlines, const Line& l, int cls, bool pow2) {
-  const int maxN = std::max(l.N1, l.N2);
+int pick_lines(int64_t nlines, const Line& l, bool pow2) {
+  const int tpl = threads_per_line(l);
   int best = 1;
   double best_s = -1.0;
-  for (int B = 1; B * maxN <= max_threads(cls) && B <= 64; B = pow2 ? 2 * B : B + 1) {
+  for (int B = 1; B * tpl <= max_threads(l) && B <= 64; B = pow2 ? 2 * B : B + 1) {
     const int64_t blocks = (nlines + B - 1) / B;
     const double cover = std::min(1.0, (double)blocks / (double)num_sms());
     const double s = cover * lane_use(B, l);
@@ -113,16 +142,15 @@ kde_status rows_pass(const kde_plan_s* plan, int kind, int64_t nrows, const long
   a.in = in;
   a.out_real = out_real;
   a.tw = twiddles(plan, dl);
-  a.SK = a.ln.N2 | 1;
-  const int cls = cls_of(a.ln);
+  a.SK = row_entries(a.ln) | 1;
   const int64_t pairs = (nrows + 1) / 2;
-  a.B = pick_lines(pairs, a.ln, cls, false);
-  const int threads = (a.B * std::max(a.ln.N1, a.ln.N2) + 31) / 32 * 32;
+  a.B = pick_lines(pairs, a.ln, false);
+  const int threads = (a.B * threads_per_line(a.ln) + 31) / 32 * 32;
   // exchange buffers, plus the staged kernel values of the kernel-grid rows
   const size_t smem = ((size_t)a.B * a.ln.N1 * a.SK + (kind == SRC_KGEN ? (size_t)a.B * a.ln.P : 0)) *
                       sizeof(float2);
   if (smem > kSmemMax) return fail(KDE_ERR_UNSUPPORTED, "two-phase row block too large");
-  const Launch l{a.ln.N1, a.ln.N2, dim3((unsigned)((pairs + a.B - 1) / a.B)), threads, smem, st};
+  const Launch l{a.ln.N1, a.ln.N2, a.ln.N3, dim3((unsigned)((pairs + a.B - 1) / a.B)), threads, smem, st};
   if (kind == 2) {
     LaunchScope ls("kde_fx_rows_c2r_kernel", st);
     return done(launch_rows_c2r(l, a), "kde_fx_rows_c2r_kernel");
@@ -152,25 +180,21 @@ kde_status cols_pass(const kde_plan_s* plan, int k, const char* name, const floa
   a.Lw = Lw;
   a.ln = line_of(I, k);
   a.tw = twiddles(plan, k);
-  const int cls = cls_of(a.ln);
   const int64_t lines = (MODE == COL_FWD_REAL ? (S + 1) / 2 : S);
   // lines per block over all slabs; at most 16 adjacent columns
-  int B = pick_lines(lines * O, a.ln, cls, true);
+  int B = pick_lines(lines * O, a.ln, true);
   while (B > 1 && B > lines) B /= 2;
   B = std::min(B, 16);
   a.B = B;
   a.lgB = 0;
   while ((1 << a.lgB) < B) ++a.lgB;
-  if (B < 16) {
-    a.SK = B * a.ln.N2;
-    while (a.SK % 16 != B % 16) ++a.SK;
-  } else {
-    a.SK = B * a.ln.N2;
-  }
-  const int threads = (B * std::max(a.ln.N1, a.ln.N2) + 31) / 32 * 32;
+  a.SK = B * row_entries(a.ln);
+  if (B < 16)
+    while (a.SK % 16 != B % 16) ++a.SK;   // conflict-free reads across k1
+  const int threads = (B * threads_per_line(a.ln) + 31) / 32 * 32;
   const size_t smem = (size_t)a.ln.N1 * a.SK * sizeof(float2);
   if (smem > kSmemMax) return fail(KDE_ERR_UNSUPPORTED, "two-phase column block too large");
-  const Launch l{a.ln.N1, a.ln.N2, dim3((unsigned)((lines + B - 1) / B), (unsigned)O), threads, smem, st};
+  const Launch l{a.ln.N1, a.ln.N2, a.ln.N3, dim3((unsigned)((lines + B - 1) / B), (unsigned)O), threads, smem, st};
   LaunchScope ls(name, st);
   cudaError_t e;
   switch (MODE) {

@@ -100,7 +100,7 @@ constexpr int block_limit() {
 // Runtime split of a line: P = N1 N2; k / N1 = umulhi(k, magic1) for the
 // k < 2^13 that occur (magic1 = floor(2^32 / N1) + 1).
 struct Line {
-  int P, N1, N2;
+  int P, N1, N2, N3;  // N3 = 0: two factors
   unsigned magic1;
 };
 
@@ -500,6 +500,13 @@ kde_fx_cols_kernel(ColsArgs a) {
 // Launch of the kernel for the split (N1, N2): the one compiled for it if it
 // is in the list, else the generic kernel for factors up to 20.
 #define KDE_FX_DISPATCH(KERNEL_T, ...)                                                   \
+  if (l.n3) {                                                                          \
+    switch (l.n1 * 4096 + l.n2 * 64 + l.n3) {                                          \
+      KDE_FX_TRIPLES(KDE_FX_CASE_TRIPLE)                                               \
+      default:                                                                         \
+        return cudaErrorInvalidConfiguration;                                          \
+    }                                                                                  \
+  }                                                                                    \
   switch (l.n1 * 64 + l.n2) {                                                          \
     KDE_FX_PAIRS(KDE_FX_CASE_PAIR)                                                     \
     default:                                                                           \
@@ -538,7 +545,7 @@ cudaError_t launch_kernel(Kern* fn, dim3 grid, int threads, size_t smem, cudaStr
 }
 
 struct Launch {
-  int n1, n2;  // the line split
+  int n1, n2, n3;  // the line split (n3 = 0: two factors)
   dim3 grid;
   int threads;
   size_t smem;

@@ -184,20 +184,22 @@ static bool is_7smooth(int64_t x) {
   return x == 1;
 }
 
-// Two-phase engine: a line length P = N1 N2.  Up to 400 the generic kernels
-// take any split with 2 <= N1 <= N2 <= 20, both 7-smooth (the most balanced
-// one, smallest N2), unless a split with kernels of its own (fx_pairs.h) is
-// at most 10% longer; above 400 only those splits are used.  Returns the
-// chosen length >= need and its split, or 0 if there is none.
-static int64_t two_phase_plan(int64_t need, int* N1, int* N2) {
+// Two-phase engine: a line length and its split.  Up to 400 the generic
+// kernels take any P = N1 N2 with 2 <= N1 <= N2 <= 20, both 7-smooth (the
+// most balanced split, smallest N2), unless a split with kernels of its own
+// (fx_pairs.h) is at most 10% longer; longer lines take the smallest listed
+// three-factor length.  Returns the length >= need and its factors (N3 = 0
+// for two), or 0 if there is none.
+static int64_t two_phase_plan(int64_t need, int* sp) {
   int64_t best_c = 0;
-  int c1 = 0, c2 = 0;
+  int c[3] = {0, 0, 0};
   for (int i = 0; i < fxp::kNumPairs; ++i) {
     const int64_t P = (int64_t)fxp::kPairs[i].N1 * fxp::kPairs[i].N2;
     if (P >= need && (best_c == 0 || P < best_c)) {
       best_c = P;
-      c1 = fxp::kPairs[i].N1;
-      c2 = fxp::kPairs[i].N2;
+      c[0] = fxp::kPairs[i].N1;
+      c[1] = fxp::kPairs[i].N2;
+      c[2] = 0;
     }
   }
   for (int64_t P = need; P <= fxp::kGenericMaxP; ++P) {
@@ -210,12 +212,24 @@ static int64_t two_phase_plan(int64_t need, int* N1, int* N2) {
     }
     if (!a_best) continue;
     if (best_c && (double)best_c <= 1.1 * (double)P) break;  // the compiled split
-    *N1 = a_best;
-    *N2 = (int)(P / a_best);
+    sp[0] = a_best;
+    sp[1] = (int)(P / a_best);
+    sp[2] = 0;
     return P;
   }
-  *N1 = c1;
-  *N2 = c2;
+  if (!best_c) {
+    for (int i = 0; i < fxp::kNumTriples; ++i) {
+      const fxp::Triple& t = fxp::kTriples[i];
+      const int64_t P = (int64_t)t.N1 * t.N2 * t.N3;
+      if (P >= need && (best_c == 0 || P < best_c)) {
+        best_c = P;
+        c[0] = t.N1;
+        c[1] = t.N2;
+        c[2] = t.N3;
+      }
+    }
+  }
+  for (int i = 0; i < 3; ++i) sp[i] = c[i];
   return best_c;
 }
 
@@ -352,9 +366,9 @@ static kde_status compute_info(int d, const int64_t* M, const double* lo, const 
     return fail(KDE_ERR_UNSUPPORTED, "the two-phase engine needs a KDE_F32 plan with d >= 2");
   bool tp = tp_ok && o.engine != KDE_ENGINE_STOCKHAM;
   int64_t Ptp[KDE_MAX_D] = {0, 0, 0};
-  int sp[KDE_MAX_D][2] = {};
+  int sp[KDE_MAX_D][3] = {};
   for (int k = 0; tp && k < d; ++k) {
-    const int64_t P = two_phase_plan(info->P[k], &sp[k][0], &sp[k][1]);
+    const int64_t P = two_phase_plan(info->P[k], sp[k]);
     if (P == 0) {
       if (o.engine == KDE_ENGINE_TWO_PHASE)
         return fail(KDE_ERR_UNSUPPORTED, "padded size above the two-phase engine's largest line");
@@ -367,8 +381,7 @@ static kde_status compute_info(int d, const int64_t* M, const double* lo, const 
     int64_t P = info->P[k];
     if (tp) {
       P = Ptp[k];
-      info->split[k][0] = sp[k][0];
-      info->split[k][1] = sp[k][1];
+      for (int i = 0; i < 3; ++i) info->split[k][i] = sp[k][i];
     } else {
       while (!is_7smooth(P)) ++P;
     }

@@ -47,7 +47,7 @@ class PlanInfo(ctypes.Structure):
                 ("kspec_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
                 ("nstages", ctypes.c_int * MAX_D),
                 ("radix", (ctypes.c_int * MAX_STAGES) * MAX_D), ("engine", ctypes.c_int),
-                ("split", (ctypes.c_int * 2) * MAX_D)]
+                ("split", (ctypes.c_int * 3) * MAX_D)]
 
 
 class BatchItem(ctypes.Structure):
@@ -220,7 +220,7 @@ def _info(pi: PlanInfo) -> Info:
                 pi.kspec_elems, pi.kspec_bytes, pi.workspace_bytes,
                 tuple(tuple(pi.radix[k][:pi.nstages[k]]) for k in range(d)),
                 {1: "stockham", 2: "two_phase"}.get(pi.engine, "stockham"),
-                tuple((pi.split[k][0], pi.split[k][1]) for k in range(d)))
+                tuple(tuple(v for v in pi.split[k][:3] if v) or (0, 0) for k in range(d)))
 
 
 def kde_plan_info_compute(M, lo, hi, H, **opts) -> Info:

@@ -1,6 +1,6 @@
 """The two-phase FFT engine (FP32): every factor size of its generic kernels
 as both factors of a line (P = s^2, split s x s) and every split that has
-kernels of its own, on the row axis and on the column axis of small 2-D
+kernels of its own (two and three factors), on the row axis and on the column axis of small 2-D
 grids, each node against the FP64 oracle within the FP32 path's 1e-5 (max
 error over max value); a few unbalanced splits; 3-D grids; and the
 full-size workloads against the Stockham engine."""
@@ -19,15 +19,16 @@ pytestmark = pytest.mark.gpu
 SIZES = [2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 18, 20]
 
 
-def compiled_pairs():
-    """The splits listed in the library's source (KDE_FX_PAIRS)."""
+def compiled(macro):
+    """The splits listed in the library's source (KDE_FX_PAIRS, KDE_FX_TRIPLES)."""
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     text = open(os.path.join(root, "paper_1508_02766_gb300", "csrc", "fx_pairs.h")).read()
-    body = text[text.index("#define KDE_FX_PAIRS"):text.index("namespace kde")]
-    return [(int(a), int(b)) for a, b in re.findall(r"X\((\d+),\s*(\d+)\)", body)]
+    body = text[text.index("#define " + macro):]
+    body = body[:body.index("\n\n")]
+    return [tuple(int(v) for v in m.split(",")) for m in re.findall(r"X\(([\d,\s]+)\)", body)]
 
 
-PAIRS = compiled_pairs()
+PAIRS = compiled("KDE_FX_PAIRS") + compiled("KDE_FX_TRIPLES")
 
 
 @pytest.fixture(scope="module")
@@ -89,7 +90,7 @@ def test_every_factor_size(K, s, axis):
 @pytest.mark.parametrize("axis", [0, 1])
 @pytest.mark.parametrize("split", PAIRS)
 def test_every_compiled_split(K, split, axis):
-    P = split[0] * split[1]
+    P = int(np.prod(split))
     w, Pmin, info = case_with_P(K, 800 + P, axis, P)
     assert info.P[axis] == P and info.split[axis] == split
     dens, counts, _ = run(K, w, P_min=Pmin, engine="two_phase")

@@ -44,17 +44,19 @@ def _is_7smooth(x):
     return x == 1
 
 
-def _compiled_pairs():
+def _compiled(macro):
     text = open(os.path.join(ROOT, "paper_1508_02766_gb300", "csrc", "fx_pairs.h")).read()
-    body = text[text.index("#define KDE_FX_PAIRS"):text.index("namespace kde")]
-    return [(int(a), int(b)) for a, b in re.findall(r"X\((\d+),\s*(\d+)\)", body)]
+    body = text[text.index("#define " + macro):]
+    body = body[:body.index("\n\n")]
+    return [tuple(int(v) for v in m.split(",")) for m in re.findall(r"X\(([\d,\s]+)\)", body)]
 
 
 def _two_phase_plan(need):
     """The two-phase planner's rule: up to 400, the smallest P >= need with a
     split into 7-smooth factors <= 20 (most balanced), unless a compiled
-    split is at most 10% longer; above 400, the smallest compiled split."""
-    comp = sorted((a * b, (a, b)) for a, b in _compiled_pairs() if a * b >= need)
+    pair is at most 10% longer; above that, the smallest compiled
+    three-factor length."""
+    comp = sorted((a * b, (a, b)) for a, b in _compiled("KDE_FX_PAIRS") if a * b >= need)
     for P in range(need, 401):
         splits = [(a, P // a) for a in range(2, int(P ** 0.5) + 1)
                   if P % a == 0 and P // a <= 20 and _is_7smooth(a) and _is_7smooth(P // a)]
@@ -63,7 +65,19 @@ def _two_phase_plan(need):
         if comp and comp[0][0] <= 1.1 * P:
             break
         return P, splits[-1]
-    return comp[0] if comp else (None, None)
+    if comp:
+        return comp[0]
+    tri = sorted((a * b * c, (a, b, c)) for a, b, c in _compiled("KDE_FX_TRIPLES") if a * b * c >= need)
+    return tri[0] if tri else (None, None)
+
+
+def test_compiled_splits_cover_the_lengths():
+    pairs = _compiled("KDE_FX_PAIRS")
+    tri = _compiled("KDE_FX_TRIPLES")
+    assert all(a * b <= 400 and _is_7smooth(a * b) for a, b in pairs)
+    lens = sorted(a * b * c for a, b, c in tri)
+    assert lens[0] > 400 and lens[0] <= 1.12 * 400
+    assert all(b <= 1.125 * a for a, b in zip(lens, lens[1:]))   # spaced by at most 12.5%
 
 
 @pytest.mark.parametrize("name", ["kde2d_128_f64", "kde2d_1024_f32"])
@@ -126,7 +140,7 @@ def test_plan_workload_sizes():
     assert kde.kde_plan_info_compute(w.M, w.lo, w.hi, w.H, precision="f64").P == (144, 144)
     w = W.kde2d_1024_f32(n=100_000)
     info = kde.kde_plan_info_compute(w.M, w.lo, w.hi, w.H)
-    assert info.P == (1080, 1080) and info.split == ((30, 36), (30, 36))
+    assert info.P == (1080, 1080) and info.split == ((9, 10, 12), (9, 10, 12))
     info = kde.kde_plan_info_compute(w.M, w.lo, w.hi, w.H, engine="stockham")
     assert info.P == (1080, 1080) and info.engine == "stockham"
 
