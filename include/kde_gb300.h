@@ -176,15 +176,18 @@ kde_status kde_plan_destroy(kde_plan plan);
  * n_outside: device int64, zeroed then incremented; may be NULL.  n may be 0.
  * workspace: NULL selects the direct method (64-bit atomics into counts);
  * otherwise at least kde_bin_workspace_bytes(n, d, M) bytes, 256-byte
- * aligned, select the tiled method (a counting sort of the samples by grid
- * tile, then shared-memory accumulation per tile).  Both give identical
- * counts.  Requires n < 2^31 and prod(M) < 2^40 (tiled: < 2^32). */
+ * aligned, select the tiled method (the samples partitioned by grid tile,
+ * then each tile accumulated in shared memory and stored once).  Both give
+ * identical counts.  Requires n < 2^31 and prod(M) < 2^40 (tiled: < 2^32). */
 kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, const double* lo,
                    const double* hi, const int64_t* M, int64_t* counts, int64_t* n_outside,
                    void* workspace, size_t workspace_bytes, kde_stream_t stream);
 
-/* Scratch bytes the tiled binning method needs for n samples on grid M
- * (about 16 n bytes plus per-tile tables).  Host only. */
+/* Scratch bytes the tiled binning method needs for n samples on grid M:
+ * a 16-byte record for every tile a sample can touch (2^d of them at most,
+ * so 16 2^d n bytes) plus per-tile tables.  KDE_ERR_UNSUPPORTED for grids
+ * of more than 16384 tiles (64^2 cells in 2-D, 16^3 in 3-D, 4096 in 1-D) or
+ * 2^d n >= 2^32.  Host only. */
 kde_status kde_bin_workspace_bytes(int64_t n, int d, const int64_t* M, size_t* bytes);
 
 /* Kernel grid and its spectrum (Eq. 6, Eq. 10's K = F(k)).  Evaluates

@@ -6,21 +6,21 @@
 //
 // Two implementations of the same arithmetic:
 //   direct  one pass, 64-bit integer atomics straight into the counts (no
-//           scratch; bound by the L2 atomic rate, ~2^d atomics per sample);
-//   tiled   a counting sort of the samples by the grid tile of their base
-//           node, then one block per tile accumulating in shared memory with
-//           shared 64-bit atomics and writing every cell of its tile once
-//           with a plain store (no memset, no global atomics on counts):
-//             hist     per-block histogram of keys (tile, face mask)
-//             scan     exclusive prefix over blocks per key, then over keys
-//             scatter  records {tile-local base, Q_0..Q_{d-1}} into key order
-//             gather   per work item of a tile: own records plus
-//                      neighbours' face records (tiles with more records
-//                      than one item holds are zeroed first and their
-//                      items add with 64-bit atomics)
-//           A sample whose base node is the last row of its tile along axis k
-//           also feeds the next tile (face-mask bit k); the owner of a cell
-//           reads those records from the neighbour's face buckets.
+//           scratch; bound by the rate of scattered L2 sector operations,
+//           ~2^(d-1) + 1/2 per sample);
+//   tiled   the samples partitioned by the grid tile of their base node, then
+//           each tile accumulated in shared memory and written once:
+//             count    records per tile (a sample whose base node is on a
+//                      tile's upper face also feeds the next tile(s): one
+//                      record per tile it touches)
+//             plan     bucket offsets and work items of at most kItemRecords
+//                      records per tile (one block)
+//             scatter  16-byte records {q_0, q_1, q_2, tile-local base} into
+//                      the buckets, block-aggregated cursor reservations
+//             accum    per work item, 32-bit shared atomics with exact carry
+//                      into a 64-bit word pair per cell, then every cell of
+//                      the tile stored (tiles split into several items are
+//                      zeroed during scatter and their items add instead)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,10 +32,6 @@
 namespace {
 
 constexpr unsigned long long kOne = 1ull << 32;
-constexpr int kHistThreads = 512;
-constexpr int kGatherThreads = 256;
-constexpr int kMaxKeys = 32768;
-constexpr int kMaxBlocks = 1024;
 
 // floor((w q + 2^31) / 2^32) for 0 <= w <= 2^32 and 0 <= q < 2^32, exactly,
 // in 32-bit arithmetic: with w = wh 2^32 + wl (wh in {0, 1}) and
@@ -56,6 +52,7 @@ struct BinAxis {
   int tile_log2;
   int ntiles;     // tiles along this axis
   int tstride;    // stride of this axis in the tile index
+  int lstride;    // stride of this axis inside a tile (row-major, last axis fastest)
 };
 
 template <typename T>
@@ -197,85 +194,125 @@ __global__ void __launch_bounds__(256) kde_bin_kernel(const T* __restrict__ X, i
 // ---------------------------------------------------------------------------
 // Tiled path.
 // ---------------------------------------------------------------------------
-// Bits per axis of a record's tile-local base node.
-template <int D> struct LocalBits { static constexpr int value = D == 1 ? 32 : (D == 2 ? 16 : 10); };
+constexpr int kCountThreads = 512;
+constexpr int kScatterThreads = 512;
+constexpr int kScatterU = 4;           // samples per thread per scatter round
+constexpr int kAccumThreads = 512;
+constexpr int kItemRecords = 8192;     // records per work item
+constexpr int kMaxTiles = 16384;       // tiles per grid (shared histograms)
+constexpr int kTileCells = 4096;       // cells per tile (shared accumulators)
 
-// A sample's key (base tile, face mask) and record {tile-local base node,
-// q_0 .. q_{d-1}}.  Face-mask bit (D-1-k) is set when the base node is the
-// last node of its tile along axis k (and not the grid's last node): the
-// sample then also feeds the next tile along k.
+// Targets of one sample: its base tile, the tile-local base node and the
+// axes along which it also feeds the next tile (base on the tile's last row
+// and a nonzero fraction, so the corner there has a nonzero weight).
+template <int D>
+struct Target {
+  int tile;      // base tile index
+  int spill;     // bit k: also the next tile along axis k
+  unsigned q[3];
+  int local[3];  // tile-local base node
+};
+
 template <typename T, int D>
-__device__ __forceinline__ bool sample_key(const T* x, const BinParams<T>& p, int& key, uint4& rec) {
+__device__ __forceinline__ bool sample_target(const T* x, const BinParams<T>& p, Target<D>& g) {
   int i[D];
-  unsigned q[3] = {0, 0, 0};
   bool in = true;
+  g.q[0] = g.q[1] = g.q[2] = 0;
 #pragma unroll
-  for (int k = 0; k < D; ++k) in &= axis_position<T>(x[k], p.ax[k], i[k], q[k]);
+  for (int k = 0; k < D; ++k) in &= axis_position<T>(x[k], p.ax[k], i[k], g.q[k]);
   if (!in) return false;
-  int tile = 0, mask = 0;
-  unsigned local = 0;
+  g.tile = 0;
+  g.spill = 0;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const int tk = i[k] >> p.ax[k].tile_log2;
-    const int li = i[k] & (p.ax[k].tile - 1);
-    tile += tk * p.ax[k].tstride;
-    local |= (unsigned)li << (LocalBits<D>::value * k);
-    if (li == p.ax[k].tile - 1 && i[k] + 1 < p.ax[k].M) mask |= 1 << (D - 1 - k);
+    g.local[k] = i[k] - (tk << p.ax[k].tile_log2);
+    g.tile += tk * p.ax[k].tstride;
+    if (g.local[k] == p.ax[k].tile - 1 && g.q[k] != 0) g.spill |= 1 << k;
   }
-  key = (tile << D) | mask;
-  rec = make_uint4(local, q[0], q[1], q[2]);
   return true;
 }
 
-constexpr int kUnroll = 4;
+// Bits per axis of a record's packed tile-local base node.
+template <int D>
+struct LocalBits {
+  static constexpr int value = D == 1 ? 32 : (D == 2 ? 16 : 10);
+};
 
-// Coordinates of samples base + u blockDim (u < kUnroll) that lie below s1.
+// Record of a sample for target subset S of its spill axes: the tile index
+// and the packed base node relative to that tile (local - tile extent on the
+// axes in S, stored + 1 in LocalBits<D> bits per axis).
 template <typename T, int D>
-__device__ __forceinline__ void load_samples(const T* __restrict__ X, int64_t base, int64_t s1,
-                                             T (&x)[kUnroll][D]) {
+__device__ __forceinline__ int record_for(const Target<D>& g, int S, const BinParams<T>& p,
+                                          uint4& rec) {
+  int tile = g.tile;
+  unsigned packed = 0;
 #pragma unroll
-  for (int u = 0; u < kUnroll; ++u) {
-    const int64_t s = base + u * (int64_t)blockDim.x;
-#pragma unroll
-    for (int k = 0; k < D; ++k) x[u][k] = s < s1 ? X[s * D + k] : T(0);
+  for (int k = 0; k < D; ++k) {
+    const int in_next = (S >> k) & 1;
+    tile += in_next * p.ax[k].tstride;
+    packed |= (unsigned)(g.local[k] - in_next * p.ax[k].tile + 1) << (LocalBits<D>::value * k);
+  }
+  rec = make_uint4(g.q[0], g.q[1], g.q[2], packed);
+  return tile;
+}
+
+// Subsets of the spill mask, visited in increasing order (0 = the base tile).
+template <typename F>
+__device__ __forceinline__ void for_subsets(int spill, F&& f) {
+  int S = 0;
+  while (true) {
+    f(S);
+    if (S == spill) break;
+    S = (S - spill) & spill;  // next subset of spill
   }
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(kHistThreads)
-kde_bin_hist_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, int nkeys, BinParams<T> p,
-                    unsigned* __restrict__ mat, unsigned long long* __restrict__ n_out) {
+__device__ __forceinline__ void load_samples(const T* __restrict__ X, int64_t n, int64_t s0,
+                                             int64_t stride, T (&x)[kScatterU][D]) {
+#pragma unroll
+  for (int u = 0; u < kScatterU; ++u) {
+    const int64_t s = s0 + u * stride;
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[u][k] = s < n ? X[s * D + k] : T(0);
+  }
+}
+
+// Records per tile (block histograms flushed into tile_count) and samples
+// outside the grid.
+template <typename T, int D>
+__global__ void __launch_bounds__(kCountThreads)
+kde_bin_count_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int ntiles,
+                     unsigned* __restrict__ tile_count, unsigned long long* __restrict__ n_out) {
   extern __shared__ unsigned hist[];
-  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) hist[k] = 0;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
   __syncthreads();
-  const int64_t s0 = (int64_t)blockIdx.x * chunk;
-  const int64_t s1 = min(n, s0 + chunk);
   unsigned long long outside = 0;
-  // the next iteration's samples are loaded before this one's are keyed
-  T xc[kUnroll][D], xn[kUnroll][D];
-  load_samples<T, D>(X, s0 + threadIdx.x, s1, xc);
-  for (int64_t base = s0 + threadIdx.x; base < s1; base += kUnroll * (int64_t)blockDim.x) {
-    load_samples<T, D>(X, base + kUnroll * (int64_t)blockDim.x, s1, xn);
-    int key[kUnroll];
-    bool in[kUnroll];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s0 < n;
+       s0 += kScatterU * stride) {
+    T x[kScatterU][D];
+    load_samples<T, D>(X, n, s0, stride, x);
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t s = base + u * (int64_t)blockDim.x;
-      uint4 rec;
-      in[u] = s < s1 && sample_key<T, D>(xc[u], p, key[u], rec);
-      if (s < s1 && !in[u]) ++outside;
+    for (int u = 0; u < kScatterU; ++u) {
+      if (s0 + u * stride >= n) break;
+      Target<D> g;
+      if (!sample_target<T, D>(x[u], p, g)) {
+        ++outside;
+        continue;
+      }
+      for_subsets(g.spill, [&](int S) {
+        int tile = g.tile;
+#pragma unroll
+        for (int k = 0; k < D; ++k) tile += ((S >> k) & 1) * p.ax[k].tstride;
+        atomicAdd(&hist[tile], 1u);
+      });
     }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-      if (in[u]) atomicAdd(&hist[key[u]], 1u);
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-#pragma unroll
-      for (int k = 0; k < D; ++k) xc[u][k] = xn[u][k];
   }
   __syncthreads();
-  unsigned* row = mat + (int64_t)blockIdx.x * nkeys;
-  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) row[k] = hist[k];
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+    if (hist[t]) atomicAdd(&tile_count[t], hist[t]);
   if (n_out) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) outside += __shfl_down_sync(0xffffffffu, outside, off);
@@ -283,443 +320,227 @@ kde_bin_hist_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, int nkeys
   }
 }
 
-// Exclusive prefix over blocks for each key (in place), totals per key.
-// A block takes 32 keys: the [nblocks x 32] slab is staged in shared memory
-// with coalesced rows, each key's column is split into 8 segments scanned by
-// 8 threads, then the segment offsets are applied and the slab written back.
-constexpr int kScanKeys = 32, kScanSegs = 8;
-__global__ void __launch_bounds__(kScanKeys * kScanSegs)
-kde_bin_scan_blocks_kernel(unsigned* __restrict__ mat, int nblocks, int nkeys,
-                           unsigned* __restrict__ totals) {
-  extern __shared__ unsigned slab[];  // [nblocks][kScanKeys + 1]
-  __shared__ unsigned seg_sum[kScanSegs][kScanKeys];
-  const int k0 = blockIdx.x * kScanKeys;
-  const int W = kScanKeys + 1;
-  // eight independent loads in flight per thread before their shared stores
-  constexpr int kBatch = 8;
-  for (int idx0 = threadIdx.x; idx0 < nblocks * kScanKeys; idx0 += kBatch * blockDim.x) {
-    unsigned v[kBatch];
+struct TiledMeta {
+  unsigned nitems;
+  unsigned nsplit;
+};
+
+// Exclusive prefix sum over the 1024 threads of the block of one value each.
+__device__ __forceinline__ unsigned block_scan_1024(unsigned v, unsigned* warp_tot,
+                                                    unsigned* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned x = v;
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int idx = idx0 + u * blockDim.x;
-      const int b = idx / kScanKeys, c = idx % kScanKeys;
-      v[u] = (idx < nblocks * kScanKeys && k0 + c < nkeys) ? mat[(int64_t)b * nkeys + k0 + c] : 0u;
-    }
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned t = warp_tot[lane];
+    unsigned s = t;
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int idx = idx0 + u * blockDim.x;
-      if (idx < nblocks * kScanKeys) slab[(idx / kScanKeys) * W + idx % kScanKeys] = v[u];
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, s, off);
+      if (lane >= off) s += y;
     }
+    warp_tot[lane] = s - t;
+    if (lane == 31) *total = s;
   }
   __syncthreads();
-  const int c = threadIdx.x % kScanKeys, sg = threadIdx.x / kScanKeys;
-  const int len = (nblocks + kScanSegs - 1) / kScanSegs;
-  const int b0 = sg * len, b1 = min(nblocks, b0 + len);
-  unsigned sum = 0;
-  for (int b = b0; b < b1; ++b) sum += slab[b * W + c];
-  seg_sum[sg][c] = sum;
-  __syncthreads();
-  unsigned run = 0, total = 0;
-  for (int g = 0; g < kScanSegs; ++g) {
-    if (g < sg) run += seg_sum[g][c];
-    total += seg_sum[g][c];
+  return warp_tot[w] + x - v;
+}
+
+// Bucket offsets (cursors for scatter), work items (tile, first record,
+// end record, split) and the list of split tiles.  One block of 1024
+// threads; thread j owns tiles [j c, (j+1) c) with c = ceil(ntiles / 1024).
+__global__ void __launch_bounds__(1024)
+kde_bin_plan_kernel(const unsigned* __restrict__ tile_count, int ntiles,
+                    unsigned* __restrict__ cursor, uint4* __restrict__ items,
+                    unsigned* __restrict__ split_list, TiledMeta* __restrict__ meta) {
+  __shared__ unsigned warp_tot[32];
+  __shared__ unsigned totals[3];
+  const int per = (ntiles + 1023) / 1024;
+  const int t0 = threadIdx.x * per, t1 = min(ntiles, t0 + per);
+  unsigned rec = 0, nit = 0, nsp = 0;
+  for (int t = t0; t < t1; ++t) {
+    const unsigned c = tile_count[t];
+    const unsigned it = c == 0 ? 1u : (c + kItemRecords - 1) / kItemRecords;
+    rec += c;
+    nit += it;
+    nsp += it > 1;
   }
-  for (int b = b0; b < b1; ++b) {
-    unsigned v = slab[b * W + c];
-    slab[b * W + c] = run;
-    run += v;
+  unsigned r0 = block_scan_1024(rec, warp_tot, &totals[0]);
+  unsigned i0 = block_scan_1024(nit, warp_tot, &totals[1]);
+  unsigned s0 = block_scan_1024(nsp, warp_tot, &totals[2]);
+  for (int t = t0; t < t1; ++t) {
+    const unsigned c = tile_count[t];
+    const unsigned it = c == 0 ? 1u : (c + kItemRecords - 1) / kItemRecords;
+    cursor[t] = r0;
+    for (unsigned j = 0; j < it; ++j) {
+      const unsigned b = r0 + j * kItemRecords, e = min(r0 + c, b + kItemRecords);
+      items[i0 + j] = make_uint4((unsigned)t, b, e, it > 1 ? 1u : 0u);
+    }
+    if (it > 1) split_list[s0++] = (unsigned)t;
+    r0 += c;
+    i0 += it;
   }
-  if (sg == 0 && k0 + c < nkeys) totals[k0 + c] = total;
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < nblocks * kScanKeys; idx += blockDim.x) {
-    int b = idx / kScanKeys, cc = idx % kScanKeys;
-    if (k0 + cc < nkeys) mat[(int64_t)b * nkeys + k0 + cc] = slab[b * W + cc];
+  if (threadIdx.x == 0) {
+    meta->nitems = totals[1];
+    meta->nsplit = totals[2];
   }
 }
 
-struct TileGeom {
-  int64_t M[KDE_MAX_D];
-  int64_t stride[KDE_MAX_D];
-  int tile[KDE_MAX_D];      // powers of two
-  int tile_log2[KDE_MAX_D];
-  int ntiles[KDE_MAX_D];
-  int tstride[KDE_MAX_D];
-  int ntiles_total;
-  int tile_cells;
-  int item_cap;
-};
-
-template <int D>
-__device__ __forceinline__ void tile_coords(int t, const TileGeom& g, int* tc) {
-  int rem = t;
+// Global cell index of tile-local cell j of tile t (or -1 outside the grid).
+template <typename T, int D>
+__device__ __forceinline__ int64_t tile_cell(const BinParams<T>& p, int t, int j) {
+  int64_t idx = 0;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    tc[k] = rem / g.tstride[k];
-    rem -= tc[k] * g.tstride[k];
+    const int tk = (t / p.ax[k].tstride) % p.ax[k].ntiles;
+    const int lk = (j / p.ax[k].lstride) & (p.ax[k].tile - 1);
+    const int c = (tk << p.ax[k].tile_log2) + lk;
+    if (c >= p.ax[k].M) return -1;
+    idx += (int64_t)c * p.ax[k].stride;
   }
+  return idx;
 }
 
-// Calls f(nb_tile, o, key) for the key ranges feeding tile t, in a fixed
-// order: the tile's own keys (o = 0, all masks), then for each o != 0 the
-// neighbour t - o and its masks that contain o.
-template <int D, typename F>
-__device__ __forceinline__ void for_each_source(const int* tc, const TileGeom& g, F f) {
-  for (int o = 0; o < (1 << D); ++o) {
-    int ntile = 0;
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      int nk = tc[k] - ((o >> (D - 1 - k)) & 1);
-      ok &= nk >= 0;
-      ntile += nk * g.tstride[k];
-    }
-    if (!ok) continue;
-    for (int mask = 0; mask < (1 << D); ++mask)
-      if ((mask & o) == o) f(ntile, o, (ntile << D) | mask);
-  }
-}
-
-// Exclusive prefix of v[0, n) into out[0, n) and the total into out[n],
-// by the whole block: each warp scans a contiguous segment 32 values at a
-// time (coalesced, no bank conflicts), after an exclusive scan of the
-// segments' totals.  v and out may live in global or shared memory.
-__device__ void block_segment_scan(const unsigned* v, int n, unsigned* out, unsigned* warp_sums) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int seg = (n + nw - 1) / nw;
-  const int k0 = min(n, warp * seg), k1 = min(n, k0 + seg);
-  unsigned sum = 0;
-  for (int k = k0 + lane; k < k1; k += 32) sum += v[k];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-  __syncthreads();
-  if (lane == 0) warp_sums[warp] = sum;
-  __syncthreads();
-  if (warp == 0) {
-    const unsigned x = lane < nw ? warp_sums[lane] : 0u;
-    unsigned inc = x;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
-      if (lane >= off) inc += y;
-    }
-    warp_sums[lane] = inc - x;
-    if (lane == 31) warp_sums[32] = inc;
-  }
-  __syncthreads();
-  unsigned carry = warp_sums[warp];
-  for (int kb = k0; kb < k1; kb += 32) {
-    const int k = kb + lane;
-    const unsigned x = k < k1 ? v[k] : 0u;
-    unsigned inc = x;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, inc, off);
-      if (lane >= off) inc += y;
-    }
-    if (k < k1) out[k] = carry + inc - x;
-    carry += __shfl_sync(0xffffffffu, inc, 31);
-  }
-  if (threadIdx.x == 0) out[n] = warp_sums[32];
-  __syncthreads();
-}
-
-// One block: starts[key] = exclusive prefix of key totals (starts[nkeys] =
-// all records); per tile the records feeding it (own plus neighbours' face
-// records), its number of work items (ceil(records / cap), at least 1) and
-// the exclusive prefix of items over tiles (item_start[ntiles] = all
-// items).  The per-tile sums read a mask-major copy of the totals in shared
-// memory, so the lanes of a warp (consecutive tiles) read consecutive words.
-template <int D>
-__global__ void __launch_bounds__(1024)
-kde_bin_scan_keys_kernel(const unsigned* __restrict__ totals, int nkeys, TileGeom g,
-                         unsigned* __restrict__ starts, unsigned* __restrict__ item_start) {
-  extern __shared__ unsigned smem_scan[];
-  __shared__ unsigned warp_sums[33];
-  const int ntiles = g.ntiles_total, nm = 1 << D;
-  unsigned* s_tot = smem_scan;            // [mask][tile]
-  unsigned* s_items = smem_scan + nkeys;  // [tile]
-  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) s_tot[(k & (nm - 1)) * ntiles + (k >> D)] = totals[k];
-  block_segment_scan(totals, nkeys, starts, warp_sums);
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-    int tc[KDE_MAX_D];
-    tile_coords<D>(t, g, tc);
-    unsigned recs = 0;
-    for_each_source<D>(tc, g, [&](int nbt, int, int key) {
-      recs += s_tot[(key & (nm - 1)) * ntiles + nbt];
-    });
-    s_items[t] = recs == 0 ? 1u : (recs + g.item_cap - 1) / g.item_cap;
-  }
-  __syncthreads();
-  block_segment_scan(s_items, ntiles, item_start, warp_sums);
-}
-
+// Split tiles zeroed, then records scattered into their buckets: per round
+// of kScatterU samples per thread, the block counts its records per tile in
+// shared memory (remembering which tiles it touched), reserves one range
+// per touched tile with a global atomic, and writes each record to its slot.
 template <typename T, int D>
-__global__ void __launch_bounds__(kHistThreads)
-kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, int nkeys,
-                       BinParams<T> p, const unsigned* __restrict__ mat,
-                       const unsigned* __restrict__ starts, uint4* __restrict__ recs) {
-  extern __shared__ unsigned cursor[];
-  const unsigned* row = mat + (int64_t)blockIdx.x * nkeys;
-  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) cursor[k] = starts[k] + row[k];
-  __syncthreads();
-  const int64_t s0 = (int64_t)blockIdx.x * chunk;
-  const int64_t s1 = min(n, s0 + chunk);
-  T xc[kUnroll][D], xn[kUnroll][D];
-  load_samples<T, D>(X, s0 + threadIdx.x, s1, xc);
-  for (int64_t base = s0 + threadIdx.x; base < s1; base += kUnroll * (int64_t)blockDim.x) {
-    load_samples<T, D>(X, base + kUnroll * (int64_t)blockDim.x, s1, xn);
-    int key[kUnroll];
-    uint4 rec[kUnroll];
-    bool in[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int64_t s = base + u * (int64_t)blockDim.x;
-      in[u] = s < s1 && sample_key<T, D>(xc[u], p, key[u], rec[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-      if (in[u]) recs[atomicAdd(&cursor[key[u]], 1u)] = rec[u];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-#pragma unroll
-      for (int k = 0; k < D; ++k) xc[u][k] = xn[u][k];
-  }
-}
-
-// Global offset of tile-local cell c (last axis fastest; tile extents are
-// powers of two), or -1 if the cell lies beyond the grid's edge.
-template <int D>
-__device__ __forceinline__ int64_t tile_cell_offset(const int* tc, const TileGeom& g, int c) {
-  int64_t off = 0;
-  bool in = true;
-#pragma unroll
-  for (int k = D - 1; k >= 0; --k) {
-    const int x = c & (g.tile[k] - 1);
-    c >>= g.tile_log2[k];
-    const int64_t gx = (int64_t)tc[k] * g.tile[k] + x;
-    in &= gx < g.M[k];
-    off += gx * g.stride[k];
-  }
-  return in ? off : -1;
-}
-
-// Store a tile's owned cells (clipped at the grid's edge), last axis fastest.
-template <int D, typename F>
-__device__ __forceinline__ void store_tile(const int* tc, const TileGeom& g, int c0, int cstep,
-                                           unsigned long long* __restrict__ counts, F value) {
-  for (int c = c0; c < g.tile_cells; c += cstep) {
-    const int64_t off = tile_cell_offset<D>(tc, g, c);
-    if (off >= 0) counts[off] = value(c);
-  }
-}
-
-// Accumulate records [r0, r1) of one source bucket into this tile's cells.
-// The bucket is (neighbour tile t - o, face mask m ⊇ o): along axis k its
-// records' corners at offset 1 land here if o has axis k (the base is the
-// neighbour's last row), only those at offset 0 if m has axis k but o not
-// (the offset-1 corner belongs to the next tile), and both otherwise.  So
-// the corners to add are the same for every record of the bucket (mask cm)
-// and land inside the tile; a corner beyond the grid's last node has weight
-// 0 and is skipped with every other zero weight.  A weight w <= 2^32 is
-// added as two parts into separate 32-bit words, lo += w mod 2^16 and
-// hi += w >> 16 (shared 32-bit atomics run about six times faster than
-// 64-bit ones).  A work item adds at most item_cap <= 65535 records to a
-// cell, so neither word can overflow; the cell is hi 2^16 + lo.
-// One record's corners (those in cm) added into the tile's two accumulator
-// words per cell; base is the record's base node as a tile-local index.
-template <int D, bool ALL>
-__device__ __forceinline__ void add_record(const uint4& rec, int base, int cm, const int* cstride,
-                                           unsigned cells, unsigned* acc_lo, unsigned* acc_hi) {
-  const unsigned q[3] = {rec.y, rec.z, rec.w};
-  unsigned long long w[1 << D];
-  corner_weights<D>(q, w);
-#pragma unroll
-  for (int c = 0; c < (1 << D); ++c) {
-    if (!ALL && !((cm >> c) & 1)) continue;
-    int lidx = base;
-#pragma unroll
-    for (int k = 0; k < D; ++k)
-      if ((c >> (D - 1 - k)) & 1) lidx += cstride[k];
-    const unsigned wl = (unsigned)w[c] & 0xffffu, wh = (unsigned)(w[c] >> 16);
-    if ((unsigned)lidx < cells) {
-      if (wl) atomicAdd(&acc_lo[lidx], wl);
-      if (wh) atomicAdd(&acc_hi[lidx], wh);
-    }
-  }
-}
-
-// Records [r0, r1) of one bucket, one per thread per iteration, the next
-// record's load issued before the current one is added.
-template <int D, bool ALL>
-__device__ __forceinline__ void add_records(const uint4* __restrict__ recs, unsigned r0, unsigned r1,
-                                            int shift, int cm, const int* cstride, unsigned cells,
-                                            unsigned* acc_lo, unsigned* acc_hi) {
-  constexpr int B = LocalBits<D>::value;
-  const unsigned lmask = B == 32 ? 0xffffffffu : ((1u << B) - 1u);
-  unsigned r = r0 + threadIdx.x;
-  if (r >= r1) return;
-  uint4 cur = recs[r];
-  for (;;) {
-    const unsigned rn = r + blockDim.x;
-    uint4 nxt;
-    if (rn < r1) nxt = recs[rn];
-    int base = shift;
-#pragma unroll
-    for (int k = 0; k < D; ++k) base += (int)((cur.x >> (B * k)) & lmask) * cstride[k];
-    add_record<D, ALL>(cur, base, cm, cstride, cells, acc_lo, acc_hi);
-    if (rn >= r1) break;
-    cur = nxt;
-    r = rn;
-  }
-}
-
-// Accumulate records [r0, r1) of one source bucket into this tile's cells.
-// The bucket is (neighbour tile t - o, face mask m ⊇ o): along axis k its
-// records' corners at offset 1 land here if o has axis k (the base is the
-// neighbour's last row), only those at offset 0 if m has axis k but o not
-// (the offset-1 corner belongs to the next tile), and both otherwise.  So
-// the corners to add are the same for every record of the bucket (mask cm)
-// and land inside the tile; a corner beyond the grid's last node has weight
-// 0 and is skipped with every other zero weight.  Own records off every face
-// (o = m = 0, nearly all of them) take all corners with no mask test.  A
-// weight w <= 2^32 is added as two parts into separate 32-bit words,
-// lo += w mod 2^16 and hi += w >> 16 (shared 32-bit atomics run about six
-// times faster than 64-bit ones).  A work item adds at most
-// item_cap <= 65535 records to a cell, so neither word can overflow; the
-// cell is hi 2^16 + lo.
-template <int D>
-__device__ __forceinline__ void accumulate(const uint4* __restrict__ recs, unsigned r0, unsigned r1,
-                                           int o, int m, const TileGeom& g, unsigned* acc_lo,
-                                           unsigned* acc_hi) {
-  int cm = 0;
-#pragma unroll
-  for (int c = 0; c < (1 << D); ++c) {
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const int bit = D - 1 - k, ck = (c >> bit) & 1;
-      if ((o >> bit) & 1) ok &= ck == 1;
-      else if ((m >> bit) & 1) ok &= ck == 0;
-    }
-    cm |= (int)ok << c;
-  }
-  // tile-local index strides; the base shifts by -tile along every axis of o
-  int cstride[KDE_MAX_D];
-  int shift = 0;
+__global__ void __launch_bounds__(kScatterThreads)
+kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int ntiles,
+                       unsigned* __restrict__ cursor, const unsigned* __restrict__ split_list,
+                       const TiledMeta* __restrict__ meta, uint4* __restrict__ recs,
+                       unsigned long long* __restrict__ counts) {
+  extern __shared__ unsigned sm[];
+  unsigned* hist = sm;               // [ntiles]: count, then next slot
+  unsigned* touched = sm + ntiles;   // tiles touched this round
+  __shared__ unsigned ntouched;
   {
-    int st = 1;
+    const int tile_cells = p.ax[0].lstride * p.ax[0].tile;
+    const int64_t work = (int64_t)meta->nsplit * tile_cells;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < work;
+         w += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t idx = tile_cell<T, D>(p, (int)split_list[w / tile_cells], (int)(w % tile_cells));
+      if (idx >= 0) counts[idx] = 0;
+    }
+  }
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
+  if (threadIdx.x == 0) ntouched = 0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t span = kScatterU * stride;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t rounds = (n + span - 1) / span;
+  for (int64_t rd = 0; rd < rounds; ++rd) {
+    const int64_t s0 = first + rd * span;
+    T x[kScatterU][D];
+    load_samples<T, D>(X, n, s0, stride, x);
+    Target<D> g[kScatterU];
+    bool in[kScatterU];
 #pragma unroll
-    for (int k = D - 1; k >= 0; --k) {
-      cstride[k] = st;
-      if ((o >> (D - 1 - k)) & 1) shift -= g.tile[k] * st;
-      st *= g.tile[k];
+    for (int u = 0; u < kScatterU; ++u) {
+      in[u] = s0 + u * stride < n && sample_target<T, D>(x[u], p, g[u]);
+      if (!in[u]) continue;
+      for_subsets(g[u].spill, [&](int S) {
+        int tile = g[u].tile;
+#pragma unroll
+        for (int k = 0; k < D; ++k) tile += ((S >> k) & 1) * p.ax[k].tstride;
+        if (atomicAdd(&hist[tile], 1u) == 0) touched[atomicAdd(&ntouched, 1u)] = (unsigned)tile;
+      });
     }
-  }
-  const unsigned cells = (unsigned)g.tile_cells;
-  if (cm == (1 << (1 << D)) - 1)
-    add_records<D, true>(recs, r0, r1, shift, cm, cstride, cells, acc_lo, acc_hi);
-  else
-    add_records<D, false>(recs, r0, r1, shift, cm, cstride, cells, acc_lo, acc_hi);
-}
-
-// Zero the cells of tiles that are split into several work items (their
-// items add into the counts with atomics); every other cell is stored once.
-template <int D>
-__global__ void __launch_bounds__(kGatherThreads)
-kde_bin_zero_split_kernel(const unsigned* __restrict__ item_start, TileGeom g,
-                          unsigned long long* __restrict__ counts) {
-  const int t = blockIdx.x;
-  if (item_start[t + 1] - item_start[t] <= 1) return;
-  int tc[KDE_MAX_D];
-  tile_coords<D>(t, g, tc);
-  store_tile<D>(tc, g, blockIdx.y * blockDim.x + threadIdx.x, gridDim.y * blockDim.x, counts,
-                [](int) { return 0ull; });
-}
-
-// One block per work item.  The records feeding tile t (own, then each
-// neighbour's face records, in for_each_source order) are numbered
-// 0 .. R-1; item j takes [j cap, (j+1) cap).  A tile with one item stores
-// its cells; items of a split tile add their nonzero cells with 64-bit
-// atomics (integer sums: the result does not depend on their order).
-template <int D>
-__global__ void __launch_bounds__(kGatherThreads)
-kde_bin_gather_kernel(const uint4* __restrict__ recs, const unsigned* __restrict__ starts,
-                      const unsigned* __restrict__ item_start, TileGeom g,
-                      unsigned long long* __restrict__ counts) {
-  extern __shared__ unsigned acc_words[];
-  unsigned* acc_lo = acc_words;
-  unsigned* acc_hi = acc_words + g.tile_cells;
-  const unsigned b = blockIdx.x;
-  if (b >= item_start[g.ntiles_total]) return;
-  int lo = 0, hi = g.ntiles_total - 1;  // largest t with item_start[t] <= b
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (item_start[mid] <= b) lo = mid; else hi = mid - 1;
-  }
-  const int t = lo;
-  const unsigned j = b - item_start[t];
-  const unsigned items = item_start[t + 1] - item_start[t];
-  int tc[KDE_MAX_D];
-  tile_coords<D>(t, g, tc);
-  for (int c = threadIdx.x; c < 2 * g.tile_cells; c += blockDim.x) acc_words[c] = 0;
-  __syncthreads();
-  const unsigned w0 = j * (unsigned)g.item_cap, w1 = w0 + (unsigned)g.item_cap;
-  unsigned v = 0;  // running record number
-  for_each_source<D>(tc, g, [&](int, int o, int key) {
-    const unsigned a = starts[key], len = starts[key + 1] - a;
-    const unsigned lo_v = max(v, w0), hi_v = min(v + len, w1);
-    if (lo_v < hi_v)
-      accumulate<D>(recs, a + (lo_v - v), a + (hi_v - v), o, key & ((1 << D) - 1), g, acc_lo, acc_hi);
-    v += len;
-  });
-  __syncthreads();
-  auto cell = [&](int c) {
-    return ((unsigned long long)acc_hi[c] << 16) + (unsigned long long)acc_lo[c];
-  };
-  if (items == 1) {
-    store_tile<D>(tc, g, threadIdx.x, blockDim.x, counts, cell);
-  } else {
-    for (int c = threadIdx.x; c < g.tile_cells; c += blockDim.x) {
-      const unsigned long long v = cell(c);
-      if (!v) continue;
-      const int64_t off = tile_cell_offset<D>(tc, g, c);
-      if (off >= 0) atomicAdd(counts + off, v);
+    __syncthreads();
+    const unsigned nt = ntouched;
+    for (unsigned j = threadIdx.x; j < nt; j += blockDim.x) {
+      const unsigned t = touched[j];
+      hist[t] = atomicAdd(&cursor[t], hist[t]);
     }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kScatterU; ++u) {
+      if (!in[u]) continue;
+      for_subsets(g[u].spill, [&](int S) {
+        uint4 rec;
+        const int tile = record_for<T, D>(g[u], S, p, rec);
+        recs[atomicAdd(&hist[tile], 1u)] = rec;
+      });
+    }
+    __syncthreads();
+    for (unsigned j = threadIdx.x; j < nt; j += blockDim.x) hist[touched[j]] = 0;
+    if (threadIdx.x == 0) ntouched = 0;
+    __syncthreads();
   }
 }
 
-// Tile extents: start from 2048 / 32x64 / 16x16x32 cells and grow while the
-// key count (tiles x 2^d) exceeds what one block's shared histogram holds.
-bool choose_tiles(int d, const int64_t* M, int* tile, int* ntiles, int* nkeys) {
-  static const int init[3][3] = {{2048, 0, 0}, {32, 64, 0}, {16, 16, 32}};
-  for (int k = 0; k < d; ++k) tile[k] = init[d - 1][k];
-  for (int iter = 0; iter < 64; ++iter) {
-    int64_t nt = 1;
-    for (int k = 0; k < d; ++k) {
-      ntiles[k] = (int)((M[k] + tile[k] - 1) / tile[k]);
-      nt *= ntiles[k];
+// One work item per block iteration: its tile's records accumulated in
+// shared memory (low and high 32-bit words per cell; a carry out of the low
+// word goes to the high word, so every cell holds the exact 64-bit sum),
+// then every cell of the tile stored (added, for split tiles).
+template <typename T, int D>
+__global__ void __launch_bounds__(kAccumThreads)
+kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ items,
+                     const TiledMeta* __restrict__ meta, BinParams<T> p,
+                     unsigned long long* __restrict__ counts) {
+  __shared__ unsigned lo[kTileCells], hi[kTileCells];
+  const int tile_cells = p.ax[0].lstride * p.ax[0].tile;
+  const unsigned nitems = meta->nitems;
+  for (unsigned it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const uint4 item = items[it];
+    for (int j = threadIdx.x; j < tile_cells; j += blockDim.x) {
+      lo[j] = 0;
+      hi[j] = 0;
     }
-    if (nt * (1 << d) <= kMaxKeys) {
-      *nkeys = (int)(nt << d);
-      return true;
+    __syncthreads();
+    for (unsigned r = item.y + threadIdx.x; r < item.z; r += blockDim.x) {
+      const uint4 rec = recs[r];
+      const unsigned q[3] = {rec.x, rec.y, rec.z};
+      int base[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        constexpr int B = LocalBits<D>::value;
+        const unsigned field = B == 32 ? rec.w : (rec.w >> (B * k)) & ((1u << (B % 32)) - 1u);
+        base[k] = (int)field - 1;
+      }
+      unsigned long long w[1 << D];
+      corner_weights<D>(q, w);
+#pragma unroll
+      for (int c = 0; c < (1 << D); ++c) {
+        if (w[c] == 0) continue;
+        int j = 0;
+        bool inside = true;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const int lk = base[k] + ((c >> (D - 1 - k)) & 1);
+          inside &= lk >= 0 && lk < p.ax[k].tile;
+          j += lk * p.ax[k].lstride;
+        }
+        if (!inside) continue;
+        const unsigned add_lo = (unsigned)w[c];
+        unsigned add_hi = (unsigned)(w[c] >> 32);
+        const unsigned old = atomicAdd(&lo[j], add_lo);
+        if (old + add_lo < old) ++add_hi;  // carry out of the low word
+        if (add_hi) atomicAdd(&hi[j], add_hi);
+      }
     }
-    // grow the axis with the most tiles, keeping shared memory per tile <= 128 KB
-    int best = -1;
-    for (int k = 0; k < d; ++k)
-      if (tile[k] < 256 && (best < 0 || ntiles[k] > ntiles[best])) best = k;
-    int64_t cells = 1;
-    for (int k = 0; k < d; ++k) cells *= tile[k];
-    if (best < 0 || cells * 2 * 8 > 128 * 1024) return false;
-    tile[best] *= 2;
+    __syncthreads();
+    for (int j = threadIdx.x; j < tile_cells; j += blockDim.x) {
+      const int64_t idx = tile_cell<T, D>(p, (int)item.x, j);
+      if (idx < 0) continue;
+      const unsigned long long v = ((unsigned long long)hi[j] << 32) | lo[j];
+      if (item.w) {
+        if (v) atomicAdd(counts + idx, v);
+      } else {
+        counts[idx] = v;
+      }
+    }
+    __syncthreads();
   }
-  return false;
 }
-
-struct TiledLayout {
-  int tile[KDE_MAX_D], ntiles[KDE_MAX_D], nkeys, nblocks, tile_cells, item_cap, ntiles_total;
-  int64_t chunk, max_items;
-  size_t off_mat, off_tot, off_starts, off_items, off_recs, total;
-};
 
 int num_sms() {
   static int sms = 0;
@@ -732,36 +553,37 @@ int num_sms() {
   return sms;
 }
 
+// Tile shape per d (powers of two, kTileCells cells), tile counts and the
+// workspace layout of the tiled path.
+struct TiledLayout {
+  int tile[KDE_MAX_D];
+  int ntiles[KDE_MAX_D];
+  int ntiles_total;
+  int64_t max_records, max_items;
+  size_t off_count, off_cursor, off_meta, off_items, off_split, off_recs, total;
+};
+
 bool tiled_layout(int64_t n, int d, const int64_t* M, TiledLayout* t) {
-  if (!choose_tiles(d, M, t->tile, t->ntiles, &t->nkeys)) return false;
-  // chunks of at least 4096 samples, at most one resident wave of
-  // histogram blocks (their shared key histograms bound the blocks per SM)
-  const int64_t per_sm = std::max<int64_t>(
-      1, std::min<int64_t>(2048 / kHistThreads, (int64_t)(200 * 1024) / ((int64_t)t->nkeys * 4)));
-  const int64_t cap = std::min<int64_t>(kMaxBlocks, per_sm * num_sms());
-  int64_t nb = (n + 4095) / 4096;
-  t->nblocks = (int)(nb < 1 ? 1 : (nb > cap ? cap : nb));
-  t->chunk = (n + t->nblocks - 1) / t->nblocks;
-  t->tile_cells = 1;
+  static const int kTile[3][3] = {{4096, 0, 0}, {64, 64, 0}, {16, 16, 16}};
   t->ntiles_total = 1;
   for (int k = 0; k < d; ++k) {
-    t->tile_cells *= t->tile[k];
+    t->tile[k] = kTile[d - 1][k];
+    t->ntiles[k] = (int)((M[k] + t->tile[k] - 1) / t->tile[k]);
+    if ((int64_t)t->ntiles_total * t->ntiles[k] > kMaxTiles) return false;
     t->ntiles_total *= t->ntiles[k];
   }
-  // records per work item: about twice the tile's cells (each item zeroes
-  // and stores a whole tile; larger items leave the heaviest tiles to few
-  // blocks), at most 65535 (the accumulator bound)
-  t->item_cap = std::max(2048, std::min(65535, 2 * t->tile_cells));
-  // A record feeds at most 2^d tiles: items <= tiles + 2^d n / cap.
-  const int64_t feeds = (int64_t)n << d;
-  t->max_items = t->ntiles_total + feeds / t->item_cap + 1;
+  // every sample feeds at most 2^d tiles
+  t->max_records = (n > 0 ? n : 1) << d;
+  if (t->max_records >= (int64_t(1) << 32)) return false;
+  t->max_items = t->ntiles_total + t->max_records / kItemRecords + 1;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  t->off_mat = 0;
-  t->off_tot = up((size_t)t->nblocks * t->nkeys * 4);
-  t->off_starts = t->off_tot + up((size_t)t->nkeys * 4);
-  t->off_items = t->off_starts + up((size_t)(t->nkeys + 1) * 4);
-  t->off_recs = t->off_items + up((size_t)(t->ntiles_total + 1) * 4);
-  t->total = t->off_recs + up((size_t)(n > 0 ? n : 1) * 16);
+  t->off_count = 0;
+  t->off_cursor = up((size_t)t->ntiles_total * 4);
+  t->off_meta = t->off_cursor + up((size_t)t->ntiles_total * 4);
+  t->off_items = t->off_meta + 256;
+  t->off_split = t->off_items + up((size_t)t->max_items * 16);
+  t->off_recs = t->off_split + up((size_t)t->ntiles_total * 4);
+  t->total = t->off_recs + up((size_t)t->max_records * 16);
   return true;
 }
 
@@ -770,7 +592,7 @@ BinParams<T> make_params(int d, const double* lo, const double* hi, const int64_
                          const TiledLayout* t) {
   BinParams<T> p{};
   int64_t stride = 1;
-  int ts = 1;
+  int ts = 1, ls = 1;
   for (int k = d - 1; k >= 0; --k) {
     double s = (double)(M[k] - 1) / (hi[k] - lo[k]);
     p.ax[k].lo = (T)lo[k];
@@ -786,12 +608,13 @@ BinParams<T> make_params(int d, const double* lo, const double* hi, const int64_
       p.ax[k].tile_log2 = lg;
       p.ax[k].ntiles = t->ntiles[k];
       p.ax[k].tstride = ts;
+      p.ax[k].lstride = ls;
       ts *= t->ntiles[k];
+      ls *= t->tile[k];
     }
   }
   return p;
 }
-
 
 template <typename T>
 kde_status launch_direct(const T* X, int64_t n, int d, const double* lo, const double* hi,
@@ -826,69 +649,45 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
                           unsigned long long* n_out, const TiledLayout& t, char* ws,
                           cudaStream_t stream) {
   BinParams<T> p = make_params<T>(D, lo, hi, M, &t);
-  unsigned* mat = (unsigned*)(ws + t.off_mat);
-  unsigned* tot = (unsigned*)(ws + t.off_tot);
-  unsigned* starts = (unsigned*)(ws + t.off_starts);
-  unsigned* item_start = (unsigned*)(ws + t.off_items);
+  unsigned* tile_count = (unsigned*)(ws + t.off_count);
+  unsigned* cursor = (unsigned*)(ws + t.off_cursor);
+  TiledMeta* meta = (TiledMeta*)(ws + t.off_meta);
+  uint4* items = (uint4*)(ws + t.off_items);
+  unsigned* split = (unsigned*)(ws + t.off_split);
   uint4* recs = (uint4*)(ws + t.off_recs);
-  TileGeom g{};
-  for (int k = 0; k < D; ++k) {
-    g.M[k] = M[k];
-    g.stride[k] = p.ax[k].stride;
-    g.tile[k] = t.tile[k];
-    g.tile_log2[k] = p.ax[k].tile_log2;
-    g.ntiles[k] = t.ntiles[k];
-    g.tstride[k] = p.ax[k].tstride;
-  }
-  g.ntiles_total = t.ntiles_total;
-  g.tile_cells = t.tile_cells;
-  g.item_cap = t.item_cap;
-  const size_t hist_smem = (size_t)t.nkeys * 4;
-  cudaError_t e;
+  const int nt = t.ntiles_total;
+  const int sms = num_sms();
+  cudaError_t e = cudaMemsetAsync(tile_count, 0, (size_t)nt * 4, stream);
+  if (e != cudaSuccess) return kde::cuda_fail(e, "cudaMemsetAsync(tile counts)");
+  const int64_t want = (n + (int64_t)kCountThreads * kScatterU - 1) / ((int64_t)kCountThreads * kScatterU);
+  const int grid_s = (int)std::max<int64_t>(1, std::min<int64_t>(want, 2LL * sms));
   {
-    auto* fn = kde_bin_hist_kernel<T, D>;
-    if ((e = allow_smem(fn, hist_smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
-    kde::LaunchScope ls("kde_bin_hist_kernel", stream);
-    fn<<<t.nblocks, kHistThreads, hist_smem, stream>>>(X, n, t.chunk, t.nkeys, p, mat, n_out);
-    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_hist_kernel");
+    auto* fn = kde_bin_count_kernel<T, D>;
+    const size_t smem = (size_t)nt * 4;
+    if ((e = allow_smem(fn, smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
+    kde::LaunchScope ls("kde_bin_count_kernel", stream);
+    fn<<<grid_s, kCountThreads, smem, stream>>>(X, n, p, nt, tile_count, n_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_count_kernel");
   }
   {
-    const size_t smem = (size_t)t.nblocks * (kScanKeys + 1) * 4;
-    if ((e = allow_smem(kde_bin_scan_blocks_kernel, smem)) != cudaSuccess)
-      return kde::cuda_fail(e, "smem attr");
-    kde::LaunchScope ls("kde_bin_scan_blocks_kernel", stream);
-    kde_bin_scan_blocks_kernel<<<(t.nkeys + kScanKeys - 1) / kScanKeys, kScanKeys * kScanSegs, smem,
-                                 stream>>>(mat, t.nblocks, t.nkeys, tot);
-    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scan_blocks_kernel");
-  }
-  {
-    auto* fn = kde_bin_scan_keys_kernel<D>;
-    const size_t ssmem = (size_t)(t.nkeys + t.ntiles_total) * 4;
-    if ((e = allow_smem(fn, ssmem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
-    kde::LaunchScope ls("kde_bin_scan_keys_kernel", stream);
-    fn<<<1, 1024, ssmem, stream>>>(tot, t.nkeys, g, starts, item_start);
-    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scan_keys_kernel");
+    kde::LaunchScope ls("kde_bin_plan_kernel", stream);
+    kde_bin_plan_kernel<<<1, 1024, 0, stream>>>(tile_count, nt, cursor, items, split, meta);
+    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_plan_kernel");
   }
   {
     auto* fn = kde_bin_scatter_kernel<T, D>;
-    if ((e = allow_smem(fn, hist_smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
+    const int max_touch = (int)std::min<int64_t>(nt, (int64_t)kScatterThreads * kScatterU << D);
+    const size_t smem = (size_t)(nt + max_touch) * 4;
+    if ((e = allow_smem(fn, smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
     kde::LaunchScope ls("kde_bin_scatter_kernel", stream);
-    fn<<<t.nblocks, kHistThreads, hist_smem, stream>>>(X, n, t.chunk, t.nkeys, p, mat, starts, recs);
+    fn<<<grid_s, kScatterThreads, smem, stream>>>(X, n, p, nt, cursor, split, meta, recs, counts);
     if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scatter_kernel");
   }
   {
-    kde::LaunchScope ls("kde_bin_zero_split_kernel", stream);
-    kde_bin_zero_split_kernel<D><<<dim3((unsigned)t.ntiles_total, 4), kGatherThreads, 0, stream>>>(
-        item_start, g, counts);
-    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_zero_split_kernel");
-  }
-  const size_t gsmem = (size_t)t.tile_cells * 8;
-  {
-    auto* fn = kde_bin_gather_kernel<D>;
-    if ((e = allow_smem(fn, gsmem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
-    kde::LaunchScope ls("kde_bin_gather_kernel", stream);
-    fn<<<(unsigned)t.max_items, kGatherThreads, gsmem, stream>>>(recs, starts, item_start, g, counts);
-    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_gather_kernel");
+    kde::LaunchScope ls("kde_bin_accum_kernel", stream);
+    const int grid_a = (int)std::min<int64_t>(t.max_items, 4LL * sms);
+    kde_bin_accum_kernel<T, D><<<grid_a, kAccumThreads, 0, stream>>>(recs, items, meta, p, counts);
+    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_accum_kernel");
   }
   return KDE_OK;
 }

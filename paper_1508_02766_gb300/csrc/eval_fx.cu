@@ -181,8 +181,10 @@ kde_status cols_pass(const kde_plan_s* plan, int k, const char* name, const floa
   a.ln = line_of(I, k);
   a.tw = twiddles(plan, k);
   const int64_t lines = (MODE == COL_FWD_REAL ? (S + 1) / 2 : S);
-  // lines per block over all slabs; at most 16 adjacent columns
-  int B = pick_lines(lines * O, a.ln, true);
+  // lines per block over all slabs: at least 4 adjacent columns (a 32-byte
+  // sector per row; fewer make every load a partial sector), at most 16
+  int B = std::max(4, pick_lines(lines * O, a.ln, true));
+  while (B * threads_per_line(a.ln) > max_threads(a.ln)) B /= 2;
   while (B > 1 && B > lines) B /= 2;
   B = std::min(B, 16);
   a.B = B;

@@ -223,6 +223,24 @@ def test_tiled_binning_heavy_tiles(K):
         assert np.array_equal(counts, c_ref)
 
 
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_tiled_binning_carries(K, d):
+    """Every sample at one point (each adds about 2^31 to the same cells, so
+    the low 32-bit word of a cell overflows on every other sample) or exactly
+    on one node (weight 2^32 to one cell): the shared accumulators carry into
+    the high word exactly."""
+    M = {1: (300,), 2: (40, 50), 3: (12, 10, 14)}[d]
+    lo, hi = np.zeros(d), np.array(M, dtype=np.float64) - 1.0
+    n = 300_000
+    X = np.concatenate([np.full((n, d), 5.7), np.full((n // 3, d), 3.0), np.full((n // 5, d), 7.25)])
+    for dt in (np.float32, np.float64):
+        Xd = torch.from_numpy(np.ascontiguousarray(X.astype(dt))).cuda()
+        counts = K.kde_bin(Xd, lo, hi, M, method="tiled").cpu().numpy()
+        c_ref, _ = O.bin_linear(X.astype(dt), lo, hi, M)
+        assert np.array_equal(counts, c_ref)
+        assert int(counts.sum()) == X.shape[0] << 32
+
+
 @pytest.mark.parametrize("name", ["kde2d_1024_f32", "kde3d_256_f32"])
 def test_tiled_and_direct_binning_identical(K, name):
     """The two binning methods give bit-identical counts at full size, and the
@@ -238,12 +256,12 @@ def test_tiled_and_direct_binning_identical(K, name):
     assert int(a.sum().item()) == w.n << 32
 
 
-@pytest.mark.parametrize("d,M", [(1, (5000,)), (2, (70, 150)), (3, (40, 35, 70))])
+@pytest.mark.parametrize("d,M", [(1, (9000,)), (2, (70, 150)), (3, (40, 35, 70))])
 def test_tiled_binning_tile_faces(K, d, M):
     """Samples whose base node is the last node of a tile along one or more
     axes feed the neighbouring tile; place many samples there and on nodes."""
     rng = np.random.default_rng(31 + d)
-    tile = {1: (2048,), 2: (32, 64), 3: (16, 16, 32)}[d]
+    tile = {1: (4096,), 2: (64, 64), 3: (16, 16, 16)}[d]
     n = 20000
     faces = [np.arange(t - 1, m - 1, t) for t, m in zip(tile, M)]
     idx = np.stack([rng.choice(f, n) if len(f) else rng.integers(0, m - 1, n)

@@ -180,5 +180,6 @@ def test_plan_respects_P_min_and_modes():
 def test_bin_workspace_sizes():
     for d, M, n in [(1, (5000,), 10), (2, (1024, 1024), 10**6), (3, (256, 256, 256), 10**7)]:
         b = kde.kde_bin_workspace_bytes(n, d, M)
-        assert b >= 16 * n
-        assert b < 16 * n + (64 << 20)
+        # a 16-byte record per tile a sample touches (at most 2^d), plus tables
+        assert b >= (16 << d) * n
+        assert b < (16 << d) * n + (8 << 20)
