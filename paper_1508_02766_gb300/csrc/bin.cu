@@ -257,39 +257,15 @@ __device__ __forceinline__ int record_for(const Target<D>& g, int S, const BinPa
   return tile;
 }
 
-// Warp aggregation.  Every lane of the warp calls these together (the loops
-// around them have warp-uniform trip counts); lanes with key < 0 take no
-// part.  Lanes with equal keys form one group whose lowest lane makes the
-// single shared-memory atomic for the group.
-
-// hist[key] += group size; returns the value before the group's add to
-// every lane of the group (0 for lanes without a key).
-__device__ __forceinline__ unsigned warp_group_add(unsigned* hist, int key, unsigned* rank) {
-  const unsigned m = __match_any_sync(0xffffffffu, key);
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(m) - 1;
-  unsigned old = 0;
-  if (key >= 0 && lane == leader) old = atomicAdd(&hist[key], (unsigned)__popc(m));
-  *rank = __popc(m & ((1u << lane) - 1u));
-  return __shfl_sync(0xffffffffu, old, leader);
-}
-
-// Exact add of the group's weights w (each <= 2^32) to the cell pair
-// (lo[key], hi[key]): the weights are summed within the group in two 16-bit
-// halves (each sum < 2^22), then the group's total goes to the low word with
-// its carry and high part to the high word.
-__device__ __forceinline__ void warp_group_add64(unsigned* lo, unsigned* hi, int key,
-                                                 unsigned long long w) {
-  const unsigned m = __match_any_sync(0xffffffffu, key);
-  const unsigned s_lo = __reduce_add_sync(m, (unsigned)(w & 0xFFFFu));
-  const unsigned s_hi = __reduce_add_sync(m, (unsigned)(w >> 16));
-  if (key < 0 || (threadIdx.x & 31) != __ffs(m) - 1) return;
-  const unsigned long long tot = ((unsigned long long)s_hi << 16) + s_lo;
-  const unsigned add_lo = (unsigned)tot;
-  unsigned add_hi = (unsigned)(tot >> 32);
-  const unsigned old = atomicAdd(&lo[key], add_lo);
-  if (old + add_lo < old) ++add_hi;  // carry out of the low word
-  if (add_hi) atomicAdd(&hi[key], add_hi);
+// Subsets of the spill mask, visited in increasing order (0 = the base tile).
+template <typename F>
+__device__ __forceinline__ void for_subsets(int spill, F&& f) {
+  int S = 0;
+  while (true) {
+    f(S);
+    if (S == spill) break;
+    S = (S - spill) & spill;  // next subset of spill
+  }
 }
 
 template <typename T, int D>
@@ -304,7 +280,7 @@ __device__ __forceinline__ void load_samples(const T* __restrict__ X, int64_t n,
 }
 
 // Records per tile (block histograms flushed into tile_count) and samples
-// outside the grid.  Warp-uniform rounds of kScatterU samples per thread.
+// outside the grid.
 template <typename T, int D>
 __global__ void __launch_bounds__(kCountThreads)
 kde_bin_count_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int ntiles,
@@ -314,33 +290,24 @@ kde_bin_count_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int nti
   __syncthreads();
   unsigned long long outside = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t span = kScatterU * stride;
-  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t rounds = (n + span - 1) / span;
-  for (int64_t rd = 0; rd < rounds; ++rd) {
-    const int64_t s0 = first + rd * span;
+  for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s0 < n;
+       s0 += kScatterU * stride) {
     T x[kScatterU][D];
     load_samples<T, D>(X, n, s0, stride, x);
 #pragma unroll
     for (int u = 0; u < kScatterU; ++u) {
+      if (s0 + u * stride >= n) break;
       Target<D> g;
-      const bool valid = s0 + u * stride < n;
-      const bool in = valid && sample_target<T, D>(x[u], p, g);
-      if (valid && !in) ++outside;
-      if (!__any_sync(0xffffffffu, in)) continue;
-      const int any_spill = __any_sync(0xffffffffu, in && g.spill);
-#pragma unroll
-      for (int S = 0; S < (1 << D); ++S) {
-        if (S && !any_spill) break;
-        int key = -1;
-        if (in && (S & ~g.spill) == 0) {
-          key = g.tile;
-#pragma unroll
-          for (int k = 0; k < D; ++k) key += ((S >> k) & 1) * p.ax[k].tstride;
-        }
-        unsigned rank;
-        warp_group_add(hist, key, &rank);
+      if (!sample_target<T, D>(x[u], p, g)) {
+        ++outside;
+        continue;
       }
+      for_subsets(g.spill, [&](int S) {
+        int tile = g.tile;
+#pragma unroll
+        for (int k = 0; k < D; ++k) tile += ((S >> k) & 1) * p.ax[k].tstride;
+        atomicAdd(&hist[tile], 1u);
+      });
     }
   }
   __syncthreads();
@@ -476,28 +443,16 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int n
     load_samples<T, D>(X, n, s0, stride, x);
     Target<D> g[kScatterU];
     bool in[kScatterU];
-    int any_spill = 0;
 #pragma unroll
     for (int u = 0; u < kScatterU; ++u) {
       in[u] = s0 + u * stride < n && sample_target<T, D>(x[u], p, g[u]);
-      any_spill |= in[u] && g[u].spill;
-    }
-    any_spill = __any_sync(0xffffffffu, any_spill);
+      if (!in[u]) continue;
+      for_subsets(g[u].spill, [&](int S) {
+        int tile = g[u].tile;
 #pragma unroll
-    for (int u = 0; u < kScatterU; ++u) {
-#pragma unroll
-      for (int S = 0; S < (1 << D); ++S) {
-        if (S && !any_spill) break;
-        int key = -1;
-        if (in[u] && (S & ~g[u].spill) == 0) {
-          key = g[u].tile;
-#pragma unroll
-          for (int k = 0; k < D; ++k) key += ((S >> k) & 1) * p.ax[k].tstride;
-        }
-        unsigned rank;
-        const unsigned old = warp_group_add(hist, key, &rank);
-        if (key >= 0 && rank == 0 && old == 0) touched[atomicAdd(&ntouched, 1u)] = (unsigned)key;
-      }
+        for (int k = 0; k < D; ++k) tile += ((S >> k) & 1) * p.ax[k].tstride;
+        if (atomicAdd(&hist[tile], 1u) == 0) touched[atomicAdd(&ntouched, 1u)] = (unsigned)tile;
+      });
     }
     __syncthreads();
     const unsigned nt = ntouched;
@@ -508,16 +463,12 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int n
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < kScatterU; ++u) {
-#pragma unroll
-      for (int S = 0; S < (1 << D); ++S) {
-        if (S && !any_spill) break;
-        const bool part = in[u] && (S & ~g[u].spill) == 0;
+      if (!in[u]) continue;
+      for_subsets(g[u].spill, [&](int S) {
         uint4 rec;
-        const int tile = part ? record_for<T, D>(g[u], S, p, rec) : -1;
-        unsigned rank;
-        const unsigned base = warp_group_add(hist, tile, &rank);
-        if (part) recs[base + rank] = rec;
-      }
+        const int tile = record_for<T, D>(g[u], S, p, rec);
+        recs[atomicAdd(&hist[tile], 1u)] = rec;
+      });
     }
     __syncthreads();
     for (unsigned j = threadIdx.x; j < nt; j += blockDim.x) hist[touched[j]] = 0;
@@ -545,11 +496,8 @@ kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ i
       hi[j] = 0;
     }
     __syncthreads();
-    // warp-uniform rounds: lane l of a warp takes record r0 + l
-    for (unsigned r0 = item.y + (threadIdx.x & ~31u); r0 < item.z; r0 += blockDim.x) {
-      const unsigned r = r0 + (threadIdx.x & 31);
-      const bool valid = r < item.z;
-      const uint4 rec = valid ? recs[r] : make_uint4(0, 0, 0, 0);
+    for (unsigned r = item.y + threadIdx.x; r < item.z; r += blockDim.x) {
+      const uint4 rec = recs[r];
       const unsigned q[3] = {rec.x, rec.y, rec.z};
       int base[D];
 #pragma unroll
@@ -562,15 +510,21 @@ kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ i
       corner_weights<D>(q, w);
 #pragma unroll
       for (int c = 0; c < (1 << D); ++c) {
+        if (w[c] == 0) continue;
         int j = 0;
-        bool inside = valid && w[c] != 0;
+        bool inside = true;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           const int lk = base[k] + ((c >> (D - 1 - k)) & 1);
           inside &= lk >= 0 && lk < p.ax[k].tile;
           j += lk * p.ax[k].lstride;
         }
-        warp_group_add64(lo, hi, inside ? j : -1, inside ? w[c] : 0ull);
+        if (!inside) continue;
+        const unsigned add_lo = (unsigned)w[c];
+        unsigned add_hi = (unsigned)(w[c] >> 32);
+        const unsigned old = atomicAdd(&lo[j], add_lo);
+        if (old + add_lo < old) ++add_hi;  // carry out of the low word
+        if (add_hi) atomicAdd(&hi[j], add_hi);
       }
     }
     __syncthreads();
