@@ -257,17 +257,6 @@ __device__ __forceinline__ int record_for(const Target<D>& g, int S, const BinPa
   return tile;
 }
 
-// Subsets of the spill mask, visited in increasing order (0 = the base tile).
-template <typename F>
-__device__ __forceinline__ void for_subsets(int spill, F&& f) {
-  int S = 0;
-  while (true) {
-    f(S);
-    if (S == spill) break;
-    S = (S - spill) & spill;  // next subset of spill
-  }
-}
-
 template <typename T, int D>
 __device__ __forceinline__ void load_samples(const T* __restrict__ X, int64_t n, int64_t s0,
                                              int64_t stride, T (&x)[kScatterU][D]) {
@@ -279,12 +268,15 @@ __device__ __forceinline__ void load_samples(const T* __restrict__ X, int64_t n,
   }
 }
 
-// Records per tile (block histograms flushed into tile_count) and samples
-// outside the grid.
+// Records per tile (block histograms added into tile_count, each block
+// keeping the offset of its range inside every tile's bucket) and samples
+// outside the grid.  The scatter kernel visits the same samples with the same
+// grid, so block b writes its records of tile t into its own range.
 template <typename T, int D>
 __global__ void __launch_bounds__(kCountThreads)
 kde_bin_count_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int ntiles,
-                     unsigned* __restrict__ tile_count, unsigned long long* __restrict__ n_out) {
+                     unsigned* __restrict__ tile_count, unsigned* __restrict__ block_base,
+                     unsigned long long* __restrict__ n_out) {
   extern __shared__ unsigned hist[];
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
   __syncthreads();
@@ -302,17 +294,23 @@ kde_bin_count_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int nti
         ++outside;
         continue;
       }
-      for_subsets(g.spill, [&](int S) {
-        int tile = g.tile;
+      atomicAdd(&hist[g.tile], 1u);
+      if (g.spill) {
+        for (int S = 1; S < (1 << D); ++S) {
+          if (S & ~g.spill) continue;
+          int tile = g.tile;
 #pragma unroll
-        for (int k = 0; k < D; ++k) tile += ((S >> k) & 1) * p.ax[k].tstride;
-        atomicAdd(&hist[tile], 1u);
-      });
+          for (int k = 0; k < D; ++k) tile += ((S >> k) & 1) * p.ax[k].tstride;
+          atomicAdd(&hist[tile], 1u);
+        }
+      }
     }
   }
   __syncthreads();
+  // this block's range in every tile's bucket (offset from the bucket start)
+  unsigned* mine = block_base + (size_t)blockIdx.x * ntiles;
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-    if (hist[t]) atomicAdd(&tile_count[t], hist[t]);
+    mine[t] = hist[t] ? atomicAdd(&tile_count[t], hist[t]) : 0u;
   if (n_out) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) outside += __shfl_down_sync(0xffffffffu, outside, off);
@@ -352,8 +350,8 @@ __device__ __forceinline__ unsigned block_scan_1024(unsigned v, unsigned* warp_t
   return warp_tot[w] + x - v;
 }
 
-// Bucket offsets (cursors for scatter), work items (tile, first record,
-// end record, split) and the list of split tiles.  One block of 1024
+// Bucket starts, work items (tile, first record, end record, split) and the
+// list of split tiles.  One block of 1024
 // threads; thread j owns tiles [j c, (j+1) c) with c = ceil(ntiles / 1024).
 __global__ void __launch_bounds__(1024)
 kde_bin_plan_kernel(const unsigned* __restrict__ tile_count, int ntiles,
@@ -407,20 +405,19 @@ __device__ __forceinline__ int64_t tile_cell(const BinParams<T>& p, int t, int j
   return idx;
 }
 
-// Split tiles zeroed, then records scattered into their buckets: per round
-// of kScatterU samples per thread, the block counts its records per tile in
-// shared memory (remembering which tiles it touched), reserves one range
-// per touched tile with a global atomic, and writes each record to its slot.
+// Split tiles zeroed, then records scattered into their buckets: block b
+// takes the same samples as in the count kernel and writes its records of
+// tile t at bucket start + its range offset + a running count kept in
+// shared memory.
 template <typename T, int D>
 __global__ void __launch_bounds__(kScatterThreads)
 kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int ntiles,
-                       unsigned* __restrict__ cursor, const unsigned* __restrict__ split_list,
+                       const unsigned* __restrict__ tile_start,
+                       const unsigned* __restrict__ block_base,
+                       const unsigned* __restrict__ split_list,
                        const TiledMeta* __restrict__ meta, uint4* __restrict__ recs,
                        unsigned long long* __restrict__ counts) {
-  extern __shared__ unsigned sm[];
-  unsigned* hist = sm;               // [ntiles]: count, then next slot
-  unsigned* touched = sm + ntiles;   // tiles touched this round
-  __shared__ unsigned ntouched;
+  extern __shared__ unsigned next[];   // [ntiles]: next slot of this block per tile
   {
     const int tile_cells = p.ax[0].lstride * p.ax[0].tile;
     const int64_t work = (int64_t)meta->nsplit * tile_cells;
@@ -430,57 +427,41 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int n
       if (idx >= 0) counts[idx] = 0;
     }
   }
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
-  if (threadIdx.x == 0) ntouched = 0;
+  const unsigned* mine = block_base + (size_t)blockIdx.x * ntiles;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) next[t] = tile_start[t] + mine[t];
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t span = kScatterU * stride;
-  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t rounds = (n + span - 1) / span;
-  for (int64_t rd = 0; rd < rounds; ++rd) {
-    const int64_t s0 = first + rd * span;
+  for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s0 < n;
+       s0 += kScatterU * stride) {
     T x[kScatterU][D];
     load_samples<T, D>(X, n, s0, stride, x);
-    Target<D> g[kScatterU];
-    bool in[kScatterU];
 #pragma unroll
     for (int u = 0; u < kScatterU; ++u) {
-      in[u] = s0 + u * stride < n && sample_target<T, D>(x[u], p, g[u]);
-      if (!in[u]) continue;
-      for_subsets(g[u].spill, [&](int S) {
-        int tile = g[u].tile;
-#pragma unroll
-        for (int k = 0; k < D; ++k) tile += ((S >> k) & 1) * p.ax[k].tstride;
-        if (atomicAdd(&hist[tile], 1u) == 0) touched[atomicAdd(&ntouched, 1u)] = (unsigned)tile;
-      });
+      if (s0 + u * stride >= n) break;
+      Target<D> g;
+      if (!sample_target<T, D>(x[u], p, g)) continue;
+      uint4 rec;
+      recs[atomicAdd(&next[record_for<T, D>(g, 0, p, rec)], 1u)] = rec;
+      if (g.spill) {
+        for (int S = 1; S < (1 << D); ++S) {
+          if (S & ~g.spill) continue;
+          const int tile = record_for<T, D>(g, S, p, rec);
+          recs[atomicAdd(&next[tile], 1u)] = rec;
+        }
+      }
     }
-    __syncthreads();
-    const unsigned nt = ntouched;
-    for (unsigned j = threadIdx.x; j < nt; j += blockDim.x) {
-      const unsigned t = touched[j];
-      hist[t] = atomicAdd(&cursor[t], hist[t]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < kScatterU; ++u) {
-      if (!in[u]) continue;
-      for_subsets(g[u].spill, [&](int S) {
-        uint4 rec;
-        const int tile = record_for<T, D>(g[u], S, p, rec);
-        recs[atomicAdd(&hist[tile], 1u)] = rec;
-      });
-    }
-    __syncthreads();
-    for (unsigned j = threadIdx.x; j < nt; j += blockDim.x) hist[touched[j]] = 0;
-    if (threadIdx.x == 0) ntouched = 0;
-    __syncthreads();
   }
 }
 
 // One work item per block iteration: its tile's records accumulated in
-// shared memory (low and high 32-bit words per cell; a carry out of the low
-// word goes to the high word, so every cell holds the exact 64-bit sum),
-// then every cell of the tile stored (added, for split tiles).
+// shared memory, then every cell of the tile stored (added, for split
+// tiles).  A weight w <= 2^32 is added as its low 16 bits and its high part
+// w >> 16 <= 2^16 into two 32-bit sums per cell; an item holds at most
+// kItemRecords = 2^13 records and a record adds to a cell at most once, so
+// neither sum exceeds 2^29 and no carry is ever lost: the cell's total is
+// hi 2^16 + lo exactly.  The adds need no return value (fire-and-forget).
+static_assert(kItemRecords <= (1 << 13), "16-bit split sums must stay below 2^32");
+
 template <typename T, int D>
 __global__ void __launch_bounds__(kAccumThreads)
 kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ items,
@@ -489,49 +470,70 @@ kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ i
   __shared__ unsigned lo[kTileCells], hi[kTileCells];
   const int tile_cells = p.ax[0].lstride * p.ax[0].tile;
   const unsigned nitems = meta->nitems;
+  int lsh[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) lsh[k] = __ffs(p.ax[k].lstride) - 1;
   for (unsigned it = blockIdx.x; it < nitems; it += gridDim.x) {
     const uint4 item = items[it];
+    // the tile's origin and extent inside the grid
+    int64_t origin = 0;
+    int ext[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int tk = ((int)item.x / p.ax[k].tstride) % p.ax[k].ntiles;
+      const int o = tk << p.ax[k].tile_log2;
+      origin += (int64_t)o * p.ax[k].stride;
+      ext[k] = min(p.ax[k].tile, p.ax[k].M - o);
+    }
     for (int j = threadIdx.x; j < tile_cells; j += blockDim.x) {
       lo[j] = 0;
       hi[j] = 0;
     }
     __syncthreads();
     for (unsigned r = item.y + threadIdx.x; r < item.z; r += blockDim.x) {
-      const uint4 rec = recs[r];
+      const uint4 rec = __ldg(recs + r);
       const unsigned q[3] = {rec.x, rec.y, rec.z};
-      int base[D];
+      int j0 = 0;
+      bool ok0[D], ok1[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         constexpr int B = LocalBits<D>::value;
         const unsigned field = B == 32 ? rec.w : (rec.w >> (B * k)) & ((1u << (B % 32)) - 1u);
-        base[k] = (int)field - 1;
+        const int bk = (int)field - 1;   // -1 .. tile - 1
+        ok0[k] = bk >= 0;
+        ok1[k] = bk < p.ax[k].tile - 1;
+        j0 += bk * p.ax[k].lstride;
       }
       unsigned long long w[1 << D];
       corner_weights<D>(q, w);
 #pragma unroll
       for (int c = 0; c < (1 << D); ++c) {
-        if (w[c] == 0) continue;
-        int j = 0;
-        bool inside = true;
+        bool inside = w[c] != 0;
+        int j = j0;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          const int lk = base[k] + ((c >> (D - 1 - k)) & 1);
-          inside &= lk >= 0 && lk < p.ax[k].tile;
-          j += lk * p.ax[k].lstride;
+          const int bit = (c >> (D - 1 - k)) & 1;
+          inside &= bit ? ok1[k] : ok0[k];
+          j += bit * p.ax[k].lstride;
         }
-        if (!inside) continue;
-        const unsigned add_lo = (unsigned)w[c];
-        unsigned add_hi = (unsigned)(w[c] >> 32);
-        const unsigned old = atomicAdd(&lo[j], add_lo);
-        if (old + add_lo < old) ++add_hi;  // carry out of the low word
-        if (add_hi) atomicAdd(&hi[j], add_hi);
+        if (inside) {
+          atomicAdd(&lo[j], (unsigned)(w[c] & 0xFFFFu));
+          atomicAdd(&hi[j], (unsigned)(w[c] >> 16));
+        }
       }
     }
     __syncthreads();
     for (int j = threadIdx.x; j < tile_cells; j += blockDim.x) {
-      const int64_t idx = tile_cell<T, D>(p, (int)item.x, j);
-      if (idx < 0) continue;
-      const unsigned long long v = ((unsigned long long)hi[j] << 32) | lo[j];
+      int64_t idx = origin;
+      bool in = true;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int l = (j >> lsh[k]) & (p.ax[k].tile - 1);
+        in &= l < ext[k];
+        idx += (int64_t)l * p.ax[k].stride;
+      }
+      if (!in) continue;
+      const unsigned long long v = ((unsigned long long)hi[j] << 16) + lo[j];
       if (item.w) {
         if (v) atomicAdd(counts + idx, v);
       } else {
@@ -555,12 +557,18 @@ int num_sms() {
 
 // Tile shape per d (powers of two, kTileCells cells), tile counts and the
 // workspace layout of the tiled path.
+// Grid of the count and scatter kernels (the same in both, and part of the
+// workspace size, so it does not depend on the device): about two blocks per
+// SM of a GB300.
+constexpr int kBinBlocks = 304;
+
 struct TiledLayout {
   int tile[KDE_MAX_D];
   int ntiles[KDE_MAX_D];
   int ntiles_total;
+  int blocks;                     // grid of the count and scatter kernels
   int64_t max_records, max_items;
-  size_t off_count, off_cursor, off_meta, off_items, off_split, off_recs, total;
+  size_t off_count, off_cursor, off_meta, off_items, off_split, off_base, off_recs, total;
 };
 
 bool tiled_layout(int64_t n, int d, const int64_t* M, TiledLayout* t) {
@@ -576,13 +584,16 @@ bool tiled_layout(int64_t n, int d, const int64_t* M, TiledLayout* t) {
   t->max_records = (n > 0 ? n : 1) << d;
   if (t->max_records >= (int64_t(1) << 32)) return false;
   t->max_items = t->ntiles_total + t->max_records / kItemRecords + 1;
+  const int64_t want = (n + (int64_t)kCountThreads * kScatterU - 1) / ((int64_t)kCountThreads * kScatterU);
+  t->blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, kBinBlocks));
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   t->off_count = 0;
   t->off_cursor = up((size_t)t->ntiles_total * 4);
   t->off_meta = t->off_cursor + up((size_t)t->ntiles_total * 4);
   t->off_items = t->off_meta + 256;
   t->off_split = t->off_items + up((size_t)t->max_items * 16);
-  t->off_recs = t->off_split + up((size_t)t->ntiles_total * 4);
+  t->off_base = t->off_split + up((size_t)t->ntiles_total * 4);
+  t->off_recs = t->off_base + up((size_t)t->blocks * t->ntiles_total * 4);
   t->total = t->off_recs + up((size_t)t->max_records * 16);
   return true;
 }
@@ -654,19 +665,19 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
   TiledMeta* meta = (TiledMeta*)(ws + t.off_meta);
   uint4* items = (uint4*)(ws + t.off_items);
   unsigned* split = (unsigned*)(ws + t.off_split);
+  unsigned* block_base = (unsigned*)(ws + t.off_base);
   uint4* recs = (uint4*)(ws + t.off_recs);
   const int nt = t.ntiles_total;
   const int sms = num_sms();
   cudaError_t e = cudaMemsetAsync(tile_count, 0, (size_t)nt * 4, stream);
   if (e != cudaSuccess) return kde::cuda_fail(e, "cudaMemsetAsync(tile counts)");
-  const int64_t want = (n + (int64_t)kCountThreads * kScatterU - 1) / ((int64_t)kCountThreads * kScatterU);
-  const int grid_s = (int)std::max<int64_t>(1, std::min<int64_t>(want, 2LL * sms));
+  const int grid_s = t.blocks;
   {
     auto* fn = kde_bin_count_kernel<T, D>;
     const size_t smem = (size_t)nt * 4;
     if ((e = allow_smem(fn, smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
     kde::LaunchScope ls("kde_bin_count_kernel", stream);
-    fn<<<grid_s, kCountThreads, smem, stream>>>(X, n, p, nt, tile_count, n_out);
+    fn<<<grid_s, kCountThreads, smem, stream>>>(X, n, p, nt, tile_count, block_base, n_out);
     if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_count_kernel");
   }
   {
@@ -676,11 +687,11 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
   }
   {
     auto* fn = kde_bin_scatter_kernel<T, D>;
-    const int max_touch = (int)std::min<int64_t>(nt, (int64_t)kScatterThreads * kScatterU << D);
-    const size_t smem = (size_t)(nt + max_touch) * 4;
+    const size_t smem = (size_t)nt * 4;
     if ((e = allow_smem(fn, smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
     kde::LaunchScope ls("kde_bin_scatter_kernel", stream);
-    fn<<<grid_s, kScatterThreads, smem, stream>>>(X, n, p, nt, cursor, split, meta, recs, counts);
+    fn<<<grid_s, kScatterThreads, smem, stream>>>(X, n, p, nt, cursor, block_base, split, meta,
+                                                   recs, counts);
     if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scatter_kernel");
   }
   {
