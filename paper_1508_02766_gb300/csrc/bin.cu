@@ -441,7 +441,8 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int n
       Target<D> g;
       if (!sample_target<T, D>(x[u], p, g)) continue;
       uint4 rec;
-      recs[atomicAdd(&next[record_for<T, D>(g, 0, p, rec)], 1u)] = rec;
+      const int tile0 = record_for<T, D>(g, 0, p, rec);   // fills rec before it is stored
+      recs[atomicAdd(&next[tile0], 1u)] = rec;
       if (g.spill) {
         for (int S = 1; S < (1 << D); ++S) {
           if (S & ~g.spill) continue;
@@ -499,9 +500,11 @@ kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ i
       for (int k = 0; k < D; ++k) {
         constexpr int B = LocalBits<D>::value;
         const unsigned field = B == 32 ? rec.w : (rec.w >> (B * k)) & ((1u << (B % 32)) - 1u);
-        const int bk = (int)field - 1;   // -1 .. tile - 1
-        ok0[k] = bk >= 0;
-        ok1[k] = bk < p.ax[k].tile - 1;
+        const int bk = (int)field - 1;   // -1 .. tile - 1 for every record scatter writes
+        // corner offset 0 / 1 along axis k lands inside the tile (checked
+        // for any value, so a corrupt record cannot index outside the arrays)
+        ok0[k] = bk >= 0 && bk < p.ax[k].tile;
+        ok1[k] = bk >= -1 && bk < p.ax[k].tile - 1;
         j0 += bk * p.ax[k].lstride;
       }
       unsigned long long w[1 << D];
