@@ -213,6 +213,27 @@ kde_status kde_kernel_grid(kde_plan plan, int64_t n, void* Kspec, void* workspac
 kde_status kde_fft_eval(kde_plan plan, const int64_t* counts, const void* Kspec, void* density,
                         void* workspace, size_t workspace_bytes, kde_stream_t stream);
 
+/* Densities for many bandwidths on one binned grid (Eq. 10: the count
+ * spectrum C = F(c) is computed once and reused, only the kernel spectrum K
+ * changes with H).  H: nH x 2 x 2 host (row-major) bandwidths, each
+ * symmetric positive definite and fitting the plan's padding
+ * (M_k + L_k(H_i) <= P_k, Eq. 15; raise opts.P_min), else
+ * KDE_ERR_NOT_SPD / KDE_ERR_INVALID_ARG before any launch.  n: the samples
+ * binned.  density (device): nH x prod(M) values, bandwidth-major, each
+ * grid exactly what kde_kernel_grid + kde_fft_eval give for that H (same
+ * plan, layout and range rule).  Bandwidths go in chunks of 64 per launch:
+ * kernel-grid rows, kernel spectrum, middle axis and output rows of the
+ * chunk's bandwidths in four launches; their parameters are copied from
+ * pageable host memory on the stream, so the call is not for graph capture.
+ * KDE_F32 2-D plans with the two-phase engine (else KDE_ERR_UNSUPPORTED).
+ * workspace: at least kde_fft_eval_multi_workspace_bytes(plan), 256-byte
+ * aligned.  (Reusing F(c) is Eq. 10's structure; the batching is not in the
+ * paper.) */
+kde_status kde_fft_eval_multi(kde_plan plan, int64_t n, int nH, const double* H,
+                              const int64_t* counts, void* density, void* workspace,
+                              size_t workspace_bytes, kde_stream_t stream);
+kde_status kde_fft_eval_multi_workspace_bytes(kde_plan plan, size_t* bytes);
+
 /* Count spectrum for functionals of the estimate (Sec. 1 and Sec. 5: the
  * same FFT machinery serves fast bandwidth selection).  W receives
  * w_k |F(c)|^2 on the half spectrum, with c the counts in sample units

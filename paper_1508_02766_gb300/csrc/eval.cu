@@ -1781,6 +1781,104 @@ extern "C" kde_status kde_fft_eval(kde_plan plan, const int64_t* counts, const v
 }
 
 // ---------------------------------------------------------------------------
+// Densities for many bandwidths on one grid (Eq. 10: C = F(c) computed once,
+// K computed and applied per bandwidth).  KDE_F32 2-D plans with the
+// two-phase engine; bandwidths in chunks of kMultiChunk per launch.
+// ---------------------------------------------------------------------------
+namespace kde {
+namespace {
+
+constexpr int kMultiChunk = 64;
+
+struct MultiLayout {
+  int Lmax0;
+  size_t off_A, off_gens, off_L0, off_t1, off_K, off_S, total;
+};
+
+kde_status multi_layout(const kde_plan_s* plan, MultiLayout* m) {
+  const kde_plan_info& I = plan->info;
+  if (I.d != 2 || I.precision != KDE_F32 || I.engine != KDE_ENGINE_TWO_PHASE)
+    return fail(KDE_ERR_UNSUPPORTED,
+                "batched densities need a KDE_F32 2-D plan with the two-phase engine");
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  // every accepted bandwidth has M_0 + L_0 <= P_0
+  m->Lmax0 = (int)(I.P[0] - I.M[0]);
+  const size_t Q = (size_t)I.Q, M0 = (size_t)I.M[0], P0 = (size_t)I.P[0];
+  m->off_A = 0;
+  m->off_gens = up(M0 * Q * 8);
+  m->off_L0 = m->off_gens + up(kMultiChunk * sizeof(KGen<float>));
+  m->off_t1 = m->off_L0 + up(kMultiChunk * sizeof(int));
+  m->off_K = m->off_t1 + up((size_t)kMultiChunk * (2 * m->Lmax0 + 1) * Q * 8);
+  m->off_S = m->off_K + up((size_t)kMultiChunk * P0 * Q * 4);
+  m->total = m->off_S + up((size_t)kMultiChunk * M0 * Q * 8);
+  return KDE_OK;
+}
+
+}  // namespace
+}  // namespace kde
+
+extern "C" kde_status kde_fft_eval_multi_workspace_bytes(kde_plan plan, size_t* bytes) {
+  if (!plan || !bytes) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  MultiLayout m;
+  kde_status s = multi_layout(plan, &m);
+  if (s != KDE_OK) return s;
+  *bytes = m.total;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_fft_eval_multi(kde_plan plan, int64_t n, int nH, const double* H,
+                                         const int64_t* counts, void* density, void* workspace,
+                                         size_t workspace_bytes, kde_stream_t stream) {
+  if (!plan || (nH > 0 && (!H || !counts || !density)))
+    return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (nH < 0 || n < 1) return fail(KDE_ERR_INVALID_ARG, "need nH >= 0 and n >= 1");
+  MultiLayout m;
+  kde_status s = multi_layout(plan, &m);
+  if (s != KDE_OK) return s;
+  if (nH == 0) return KDE_OK;
+  if (!workspace || workspace_bytes < m.total)
+    return fail(KDE_ERR_WORKSPACE, "workspace smaller than kde_fft_eval_multi_workspace_bytes");
+  if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  if ((s = check_device(plan)) != KDE_OK) return s;
+  const kde_plan_info& I = plan->info;
+  // every bandwidth's factors and kernel-grid parameters, before any launch
+  std::vector<KGen<float>> gens((size_t)nH);
+  std::vector<int> L0((size_t)nH);
+  double prodP = (double)I.P[0] * (double)I.P[1];
+  for (int h = 0; h < nH; ++h) {
+    double Ainv[9], det;
+    int64_t L[KDE_MAX_D];
+    if ((s = matrix_support(plan, H + 4 * h, Ainv, &det, L)) != KDE_OK) return s;
+    if ((s = kgen_for<float>(I, H + 4 * h, det, L, plan->layout_mode == KDE_LAYOUT_WAND,
+                             &gens[h])) != KDE_OK)
+      return s;
+    gens[h].C = (float)(1.0 / (6.283185307179586476925287 * std::sqrt(det)) /
+                        ((double)n * 4294967296.0 * prodP));
+    L0[h] = (int)L[0];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  float2* A = (float2*)(ws + m.off_A);
+  if ((s = fx_count_spectra(plan, reinterpret_cast<const long long*>(counts), A, st)) != KDE_OK)
+    return s;
+  const size_t cells = (size_t)I.M[0] * I.M[1];
+  for (int h0 = 0; h0 < nH; h0 += kMultiChunk) {
+    const int nh = std::min(kMultiChunk, nH - h0);
+    // the chunk's parameters: stream-ordered after the previous chunk's kernels
+    cudaError_t e = cudaMemcpyAsync(ws + m.off_gens, gens.data() + h0, nh * sizeof(KGen<float>),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ws + m.off_L0, L0.data() + h0, nh * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(bandwidth table)");
+    s = fx_eval_batch2(plan, A, nh, (const KGen<float>*)(ws + m.off_gens), (const int*)(ws + m.off_L0),
+                       m.Lmax0, (float2*)(ws + m.off_t1), (float*)(ws + m.off_K),
+                       (float2*)(ws + m.off_S), (float*)density + (size_t)h0 * cells, st);
+    if (s != KDE_OK) return s;
+  }
+  return KDE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // kde_fft_eval_noalloc: kde_fft_eval with its scratch in a fixed device array
 // instead of a caller-provided workspace, for callers that cannot allocate
 // device memory at the point of the call (for example code running inside a

@@ -126,9 +126,20 @@ const float2* twiddles(const kde_plan_s* plan, int k) {
 
 // Row pass: SRC_COUNTS (counts rows -> half spectra), SRC_KGEN (kernel-grid
 // rows -> half spectra) or the inverse (half spectra -> rows, cropped).
+// Batched bandwidths of one launch (grid.y = bandwidth): per-bandwidth
+// kernel-grid parameters and supports on the device, element offsets between
+// consecutive bandwidths of each array.
+struct Batch {
+  int nh = 1;
+  const KGen<float>* gens = nullptr;
+  const int* L0 = nullptr;
+  int64_t slab_in = 0, slab_out = 0, slab_real = 0, slab_K = 0;
+};
+
 kde_status rows_pass(const kde_plan_s* plan, int kind, int64_t nrows, const long long* counts,
                      int Min, int64_t in_stride, const KGen<float>* g, float2* out,
-                     const float2* in, float* out_real, int Mout, cudaStream_t st) {
+                     const float2* in, float* out_real, int Mout, cudaStream_t st,
+                     const Batch& bt = Batch()) {
   const kde_plan_info& I = plan->info;
   const int dl = I.d - 1;
   RowsArgs a{};
@@ -142,6 +153,10 @@ kde_status rows_pass(const kde_plan_s* plan, int kind, int64_t nrows, const long
   a.in = in;
   a.out_real = out_real;
   a.tw = twiddles(plan, dl);
+  a.gens = bt.gens;
+  a.slab_out = bt.slab_out;
+  a.slab_in = bt.slab_in;
+  a.slab_real = bt.slab_real;
   a.SK = row_entries(a.ln) | 1;
   const int64_t pairs = (nrows + 1) / 2;
   a.B = pick_lines(pairs, a.ln, false);
@@ -150,7 +165,8 @@ kde_status rows_pass(const kde_plan_s* plan, int kind, int64_t nrows, const long
   const size_t smem = ((size_t)a.B * a.ln.N1 * a.SK + (kind == SRC_KGEN ? (size_t)a.B * a.ln.P : 0)) *
                       sizeof(float2);
   if (smem > kSmemMax) return fail(KDE_ERR_UNSUPPORTED, "two-phase row block too large");
-  const Launch l{a.ln.N1, a.ln.N2, a.ln.N3, dim3((unsigned)((pairs + a.B - 1) / a.B)), threads, smem, st};
+  const Launch l{a.ln.N1, a.ln.N2, a.ln.N3, dim3((unsigned)((pairs + a.B - 1) / a.B), (unsigned)bt.nh),
+                 threads, smem, st};
   if (kind == 2) {
     LaunchScope ls("kde_fx_rows_c2r_kernel", st);
     return done(launch_rows_c2r(l, a), "kde_fx_rows_c2r_kernel");
@@ -167,9 +183,20 @@ kde_status rows_pass(const kde_plan_s* plan, int kind, int64_t nrows, const long
 template <int MODE>
 kde_status cols_pass(const kde_plan_s* plan, int k, const char* name, const float2* in,
                      float2* out, float* out_real, const float* K, int64_t S, int64_t O, int Nin,
-                     int Nout, int Lw, cudaStream_t st) {
+                     int Nout, int Lw, cudaStream_t st, const Batch* bt = nullptr) {
   const kde_plan_info& I = plan->info;
   ColsArgs a{};
+  if (bt) {  // slabs are bandwidths
+    O = bt->nh;
+    a.h_L0 = bt->L0;
+    a.slab_in = bt->slab_in;
+    a.slab_out = bt->slab_out;
+    a.slab_real = bt->slab_real;
+    a.slab_K = bt->slab_K;
+  } else {   // outer slabs of a 3-D pass: [O][Nin][S] in, [O][Nout or P][S] out
+    a.slab_in = (int64_t)Nin * S;
+    a.slab_out = (int64_t)(MODE == COL_FWD ? (int)I.P[k] : Nout) * S;
+  }
   a.in = in;
   a.out = out;
   a.out_real = out_real;
@@ -269,6 +296,67 @@ kde_status fx_fft_eval(kde_plan_s* plan, const long long* counts, const float* K
   }
   if (s != KDE_OK) return s;
   return rows_pass(plan, 2, rows, nullptr, 0, 0, nullptr, nullptr, A, density, (int)I.M[dl], st);
+}
+
+}  // namespace kde
+
+namespace kde {
+
+// Densities for nh bandwidths of a 2-D plan that share the counts' half
+// spectra A (Eq. 10 with C = F(c) reused; only K changes with H): per
+// bandwidth the kernel-grid rows, its real spectrum, the middle axis
+// (forward, times K, inverse) and the output rows, each pass one launch over
+// all nh bandwidths.  gens and L0 (device) hold each bandwidth's kernel-grid
+// parameters and support along axis 0; Lmax0 bounds the supports.
+kde_status fx_eval_batch2(kde_plan_s* plan, const float2* A, int nh, const KGen<float>* gens,
+                          const int* L0, int Lmax0, float2* t1, float* Kb, float2* Sb,
+                          float* density, cudaStream_t st) {
+  using namespace fx;
+  const kde_plan_info& I = plan->info;
+  const int64_t Q = I.Q, M0 = I.M[0], M1 = I.M[1], P0 = I.P[0];
+  const int64_t rows_max = 2 * (int64_t)Lmax0 + 1;
+  Batch b;
+  b.nh = nh;
+  b.gens = gens;
+  b.L0 = L0;
+  b.slab_out = rows_max * Q;
+  KGen<float> g0 = {};
+  kde_status s = rows_pass(plan, SRC_KGEN, rows_max, nullptr, 0, 0, &g0, t1, nullptr, nullptr, 0,
+                           st, b);
+  if (s != KDE_OK) return s;
+  b = Batch();
+  b.nh = nh;
+  b.L0 = L0;
+  b.slab_in = rows_max * Q;
+  b.slab_real = P0 * Q;
+  s = cols_pass<COL_FWD_REAL>(plan, 0, "kde_fx_cols_kgen_real_kernel", t1, nullptr, Kb, nullptr,
+                              Q, 1, (int)rows_max, 0, Lmax0, st, &b);
+  if (s != KDE_OK) return s;
+  b = Batch();
+  b.nh = nh;
+  b.slab_in = 0;          // every bandwidth reads the same count spectra
+  b.slab_out = M0 * Q;
+  b.slab_K = P0 * Q;
+  s = cols_pass<COL_MID>(plan, 0, "kde_fx_cols_mid_kernel", A, Sb, nullptr, Kb, Q, 1, (int)M0,
+                         (int)M0, -1, st, &b);
+  if (s != KDE_OK) return s;
+  b = Batch();
+  b.nh = nh;
+  b.slab_in = M0 * Q;
+  b.slab_real = M0 * M1;
+  return rows_pass(plan, 2, M0, nullptr, 0, 0, nullptr, nullptr, Sb, density, (int)M1, st, b);
+}
+
+// The counts' half spectra (first pass of the evaluation) into A.
+kde_status fx_count_spectra(kde_plan_s* plan, const long long* counts, float2* A, cudaStream_t st) {
+  using namespace fx;
+  const kde_plan_info& I = plan->info;
+  const int dl = I.d - 1;
+  int64_t rows = 1;
+  for (int k = 0; k < dl; ++k) rows *= I.M[k];
+  if (plan->dft_tc) return dft_tc_rows(plan, counts, rows, A, st);
+  return rows_pass(plan, SRC_COUNTS, rows, counts, (int)I.M[dl], I.M[dl], nullptr, A, nullptr,
+                   nullptr, 0, st);
 }
 
 }  // namespace kde

@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(kThreads3)
 kde_fx3_rows_fwd_kernel(RowsArgs a, const long long* __restrict__ counts, KGen<float> g) {
   constexpr int N23 = N2 * N3, P = N1 * N23;
   extern __shared__ float2 fx_sm[];
+  rows_slab(a, g);
   const int SK = a.SK, LS = N1 * SK;
   const int t = threadIdx.x;
   if constexpr (SRC == SRC_KGEN) {
@@ -189,6 +190,8 @@ template <int N1, int N2, int N3>
 __global__ void __launch_bounds__(kThreads3) kde_fx3_rows_c2r_kernel(RowsArgs a) {
   constexpr int N23 = N2 * N3, P = N1 * N23;
   extern __shared__ float2 fx_sm[];
+  KGen<float> g_unused;
+  rows_slab(a, g_unused);
   const int SK = a.SK, LS = N1 * SK;
   const int t = threadIdx.x;
   if (t < a.B * N1 * N2) {  // phase C inverse from the half spectra
@@ -244,18 +247,18 @@ template <int N1, int N2, int N3, int MODE>
 __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
   constexpr int N23 = N2 * N3, P = N1 * N23;
   extern __shared__ float2 fx_sm[];
+  cols_slab(a);
   const int W = a.B, SK = a.SK;
   const int t = threadIdx.x;
   const int c = t & (W - 1), r = t >> a.lgB;
   const int64_t first = (int64_t)blockIdx.x * W * (MODE == COL_FWD_REAL ? 2 : 1);
-  const int64_t o = blockIdx.y;
   float2* line = fx_sm + c;
   if constexpr (MODE == COL_INV) {
     if (r < N1 * N2) {  // phase C inverse from the input rows
       const int k1 = r % N1, k2 = r / N1;
       const int64_t s = first + c;
       const bool v = s < a.S;
-      const float2* in = a.in + o * a.Nin * a.S + s;
+      const float2* in = a.in + s;
       float2 z[N3];
 #pragma unroll
       for (int k3 = 0; k3 < N3; ++k3)
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
   } else {
     if (r < N23) {  // phase A
       const int n23 = r;
-      const float2* in = a.in + o * (int64_t)a.Nin * a.S;
+      const float2* in = a.in;
       float2 x[N1];
       if constexpr (MODE == COL_FWD_REAL) {
         const int64_t s = first + 2 * c;
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
       if constexpr (MODE == COL_FWD) {
         const int64_t s = first + c;
         if (s < a.S) {
-          float2* out = a.out + o * P * a.S + s;
+          float2* out = a.out + s;
 #pragma unroll
           for (int k3 = 0; k3 < N3; ++k3) out[(int64_t)(k1 + N1 * (k2 + N2 * k3)) * a.S] = z[k3];
         }
@@ -339,7 +342,7 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
       if (s < a.S) {
         float2 x[N1];
         p3_a_inv<N1, N2, N3>(x, r, line, SK, W);
-        float2* out = a.out + o * a.Nout * a.S + s;
+        float2* out = a.out + s;
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
           const int pos = r + N23 * n1;

@@ -145,7 +145,26 @@ struct RowsArgs {
   const float2* in;   // c2r: half spectra [nrows][Q]
   float* out_real;    // c2r: rows [nrows][Mout]
   const float2* tw;
+  // Batched bandwidths (grid.y = bandwidth h): the kernel grid of h from
+  // gens[h] (nullptr: the kernel argument), and element offsets between
+  // consecutive h of out, in and out_real.
+  const KGen<float>* gens;
+  int64_t slab_out, slab_in, slab_real;
 };
+
+// Per-bandwidth view of the arguments (h = blockIdx.y).
+__device__ __forceinline__ void rows_slab(RowsArgs& a, KGen<float>& g) {
+  const int64_t h = blockIdx.y;
+  if (a.gens) {
+    g = a.gens[h];
+    a.nrows = g.d == 2 ? 2 * g.L[0] + 1 : (int64_t)(2 * g.L[0] + 1) * (2 * g.L[1] + 1);
+  }
+  if (h) {
+    a.out += h * a.slab_out;
+    a.in += h * a.slab_in;
+    a.out_real += h * a.slab_real;
+  }
+}
 
 enum { SRC_COUNTS = 0, SRC_KGEN = 1 };
 
@@ -257,6 +276,7 @@ template <int CLS, int N1T, int N2T, int SRC>
 __global__ void __launch_bounds__(block_limit<N1T, N2T>())
 kde_fx_rows_fwd_kernel(RowsArgs a, const long long* __restrict__ counts, KGen<float> g) {
   extern __shared__ float2 fx_sm[];
+  rows_slab(a, g);
   if constexpr (SRC == SRC_KGEN) {
     rows_stage_kgen(a, g, fx_sm + a.B * a.ln.N1 * a.SK);
     __syncthreads();
@@ -324,6 +344,8 @@ template <int CLS, int N1T, int N2T>
 __global__ void __launch_bounds__(block_limit<N1T, N2T>())
 kde_fx_rows_c2r_kernel(RowsArgs a) {
   extern __shared__ float2 fx_sm[];
+  KGen<float> g_unused;
+  rows_slab(a, g_unused);
   size_call<N2T, CLS>(a.ln.N2, [&](auto N) { rows_b_inv<decltype(N)::value>(a, fx_sm); });
   __syncthreads();
   size_call<N1T, CLS>(a.ln.N1, [&](auto N) { rows_a_inv<decltype(N)::value>(a, fx_sm); });
@@ -350,7 +372,28 @@ struct ColsArgs {
   Line ln;
   int B, lgB, SK;
   const float2* tw;
+  // Element offsets between consecutive slabs (grid.y): outer slabs of a
+  // 3-D pass, or batched bandwidths (in 0 when they share the input); with
+  // h_L0 (batched kernel spectra) the input of slab h holds 2 L0 + 1 wrapped
+  // rows with L0 = h_L0[h].
+  int64_t slab_in, slab_out, slab_real, slab_K;
+  const int* h_L0;
 };
+
+// Per-slab view of the arguments (slab = blockIdx.y).
+__device__ __forceinline__ void cols_slab(ColsArgs& a) {
+  const int64_t h = blockIdx.y;
+  if (a.h_L0) {
+    a.Lw = a.h_L0[h];
+    a.Nin = 2 * a.Lw + 1;
+  }
+  if (h) {
+    a.in += h * a.slab_in;
+    a.out += h * a.slab_out;
+    a.out_real += h * a.slab_real;
+    a.K += h * a.slab_K;
+  }
+}
 
 // Input row feeding transform position pos, or -1 for zero padding.
 __device__ __forceinline__ int col_source(int pos, int P, int Lw, int Nin) {
@@ -370,8 +413,7 @@ __device__ __forceinline__ void cols_a_fwd(const ColsArgs& a, float2* sm) {
   const int t = threadIdx.x;
   if (t >= (a.B << 0) * N2) return;
   const int b = t & (a.B - 1), n2 = t >> a.lgB;
-  const int64_t o = blockIdx.y;
-  const float2* in = a.in + o * (int64_t)a.Nin * a.S;
+  const float2* in = a.in;
   float2 x[N1];
   if constexpr (MODE == COL_FWD_REAL) {
     const int64_t s = col_first<MODE>(a) + 2 * b;
@@ -412,7 +454,7 @@ __device__ __forceinline__ void cols_b_fwd(const ColsArgs& a, float2* sm) {
   if constexpr (MODE == COL_FWD) {
     const int64_t s = col_first<MODE>(a) + b;
     if (s >= a.S) return;
-    float2* out = a.out + (int64_t)blockIdx.y * a.ln.P * a.S + s;
+    float2* out = a.out + s;
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) out[(int64_t)(k1 + N1 * k2) * a.S] = y[k2];
   } else if constexpr (MODE == COL_FWD_REAL) {
@@ -448,7 +490,7 @@ __device__ __forceinline__ void cols_b_inv(const ColsArgs& a, float2* sm) {
   const int b = t & (a.B - 1), k1 = t >> a.lgB;
   const int64_t s = col_first<COL_INV>(a) + b;
   const bool v = s < a.S;
-  const float2* in = a.in + (int64_t)blockIdx.y * a.Nin * a.S + s;
+  const float2* in = a.in + s;
   float2 y[N2];
 #pragma unroll
   for (int k2 = 0; k2 < N2; ++k2)
@@ -470,7 +512,7 @@ __device__ __forceinline__ void cols_a_inv(const ColsArgs& a, const float2* sm) 
 #pragma unroll
   for (int k1 = 0; k1 < N1; ++k1) x[k1] = src[k1 * a.SK];
   idft<N1>(x);
-  float2* out = a.out + (int64_t)blockIdx.y * a.Nout * a.S + s;
+  float2* out = a.out + s;
 #pragma unroll
   for (int n1 = 0; n1 < N1; ++n1) {
     const int pos = n2 + N2 * n1;
@@ -482,6 +524,7 @@ template <int CLS, int N1T, int N2T, int MODE>
 __global__ void __launch_bounds__(block_limit<N1T, N2T>())
 kde_fx_cols_kernel(ColsArgs a) {
   extern __shared__ float2 fx_sm[];
+  cols_slab(a);
   if constexpr (MODE == COL_INV) {
     size_call<N2T, CLS>(a.ln.N2, [&](auto N) { cols_b_inv<decltype(N)::value>(a, fx_sm); });
     __syncthreads();

@@ -60,6 +60,10 @@ kde_status fx_kernel_grid(kde_plan_s* plan, const KGen<float>& gen, void* Kspec,
                           cudaStream_t st);
 kde_status fx_fft_eval(kde_plan_s* plan, const long long* counts, const float* Kspec,
                        float* density, void* ws, cudaStream_t st);
+kde_status fx_count_spectra(kde_plan_s* plan, const long long* counts, float2* A, cudaStream_t st);
+kde_status fx_eval_batch2(kde_plan_s* plan, const float2* A, int nh, const KGen<float>* gens,
+                          const int* L0, int Lmax0, float2* t1, float* Kb, float2* Sb,
+                          float* density, cudaStream_t st);
 
 // Launch bookkeeping: counts launches and, when profiling is on, records a
 // pair of events around each launch on its stream.

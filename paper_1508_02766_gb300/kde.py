@@ -69,6 +69,7 @@ EXPORTS = [
     "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes", "kde_lscv_autocorr_batch",
     "kde_lscv_cands_create", "kde_lscv_cands_destroy", "kde_lscv_autocorr_cands",
     "kde_wait_probe", "kde_plan_check", "kde_outside_check", "kde_noalloc_scratch_bytes",
+    "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes",
 ]
 FEAT_DIM = 1088
 
@@ -129,6 +130,8 @@ def lib():
     L.kde_mlp_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.kde_gemm_bf16.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp,
                                 ctypes.c_int, vp, ctypes.c_int, vp, vp]
+    L.kde_fft_eval_multi.argtypes = [vp, i64, ctypes.c_int, dp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.kde_fft_eval_multi_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.kde_plan_check.argtypes = [vp, vp]
     L.kde_outside_check.argtypes = [vp, vp, i64p]
     L.kde_noalloc_scratch_bytes.argtypes = []
@@ -154,7 +157,7 @@ def lib():
                  "kde_autocorrelation", "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes",
                  "kde_lscv_autocorr_batch", "kde_lscv_cands_create", "kde_lscv_cands_destroy",
                  "kde_lscv_autocorr_cands", "kde_wait_probe", "kde_plan_check",
-                 "kde_outside_check"):
+                 "kde_outside_check", "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -570,6 +573,29 @@ class BatchPlan:
                                     workspace.numel() * workspace.element_size(),
                                     _stream_ptr(stream)))
         return density
+
+
+def kde_fft_eval_multi_workspace_bytes(plan: Plan) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().kde_fft_eval_multi_workspace_bytes(plan.handle, ctypes.byref(b)))
+    return int(b.value)
+
+
+def kde_fft_eval_multi(plan: Plan, n, H, counts, density=None, workspace=None, stream=None):
+    """Densities for every bandwidth in H (k x 2 x 2) on the plan's grid from
+    one count spectrum: returns a (k, M_0, M_1) float32 tensor."""
+    import torch
+    H = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(-1, 2, 2))
+    k = H.shape[0]
+    if density is None:
+        density = torch.empty((k,) + tuple(plan.M), dtype=torch.float32, device=counts.device)
+    if workspace is None:
+        workspace = torch.empty(max(256, kde_fft_eval_multi_workspace_bytes(plan)),
+                                dtype=torch.uint8, device=counts.device)
+    _check(lib().kde_fft_eval_multi(plan.handle, int(n), k, _darr(H.ravel()), _ptr(counts),
+                                    _ptr(density), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), _stream_ptr(stream)))
+    return density
 
 
 def noalloc_scratch_bytes() -> int:
