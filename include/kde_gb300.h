@@ -320,14 +320,22 @@ kde_status kde_lscv_autocorr_cands(kde_lscv_cands cands, int64_t n, const void* 
                                    size_t workspace_bytes, kde_stream_t stream);
 
 /* Ragged batches of independent 2-D problems (each with its own samples,
- * grid and bandwidth; Sec. 2 for each).  The batch runs as seven launches:
- * a memset and one persistent grid-stride kernel per pass (binning, kernel
- * rows, kernel spectrum, count rows, middle axis, output rows), each
- * covering the work of every problem, so small and large grids share the
- * GPU.  The two kernel-grid passes need no samples and run on a stream the
- * plan owns, beside the memset and the binning (fork and join through
- * events on the caller's stream; graph capture follows them), so one plan
- * evaluates one batch at a time.  X: the problems' samples concatenated in problem order (x_rows rows
+ * grid and bandwidth; Sec. 2 for each).  Two modes:
+ *   KDE_BATCH_PERSISTENT (default): one persistent launch.  The work items
+ *     of every problem and stage (zeroing of its counts, kernel rows,
+ *     binning chunks, kernel spectrum, count rows, middle axis, output rows)
+ *     form one device queue in stage order that the blocks claim with an
+ *     atomic counter; an item waits, with a bounded spin, until the stages of
+ *     its own problem that it reads from are complete (per-problem
+ *     counters).  A wait that runs out (about a second by default) records
+ *     a timeout, the launch's remaining items are abandoned and
+ *     kde_batch_check reports KDE_ERR_TIMEOUT.
+ *   KDE_BATCH_STAGED: seven launches, a memset and one grid-stride kernel
+ *     per pass covering every problem; the two kernel-grid passes run on a
+ *     stream the plan owns beside the binning (fork and join through events
+ *     on the caller's stream).
+ * Either way small and large grids share the GPU, the result is the same,
+ * graph capture works and one plan evaluates one batch at a time.  X: the problems' samples concatenated in problem order (x_rows rows
  * of 2 values, the plan's precision).  density: the problems' grids
  * concatenated (density_elems values).  Dropped samples are not reported.
  * The plan allocates device tables (set-up, not per evaluation). */
@@ -346,14 +354,43 @@ kde_status kde_batch_plan_query(kde_batch_plan plan, int64_t* x_rows, int64_t* d
  * 128); chosen by a caller-side tuner. */
 kde_status kde_batch_set_shape(kde_batch_plan plan, int tpl_rows, int tpl_cols);
 kde_status kde_batch_get_shape(kde_batch_plan plan, int* tpl_rows, int* tpl_cols);
-/* Autotuner: times kde_batch_eval on the given buffers for every launch
- * shape in {32, 64, 128}^2 (reps timed runs each, CUDA events on the stream,
- * which it synchronises) and keeps the fastest in the plan; *best_ms (may be
- * NULL) receives its time.  Set-up, not part of an evaluation. */
+/* The padding policy and radix order in use (0 largest radix first, 1
+ * smallest first) and every problem's padded lengths P (host, 2 x count
+ * int64, may be NULL). */
+kde_status kde_batch_get_config(kde_batch_plan plan, int* pad_policy, int* radix_order, int64_t* P);
+/* Autotuner: times kde_batch_eval on the given buffers (reps timed runs each,
+ * CUDA events on the stream, which it synchronises) over
+ *   the padding policy: KDE_BATCH_PAD_SMALLEST (each axis the smallest
+ *     7-smooth length >= M + L) or KDE_BATCH_PAD_FEWEST_STAGES (the length
+ *     with the fewest radix stages up to 25% longer);
+ *   the radix order of every axis (largest radix first or last);
+ *   the mode (KDE_BATCH_PERSISTENT, KDE_BATCH_STAGED);
+ *   the threads per line (32, 64, 128; the same for rows and columns in the
+ *     persistent mode, every pair in the staged mode),
+ * skipping settings whose workspace exceeds workspace_bytes, and keeps the
+ * fastest in the plan (re-planning the problems); *best_ms (may be NULL)
+ * receives its time.  Set-up, not part of an evaluation.  The padded lengths
+ * change the plan's workspace size: query it again after tuning. */
+enum { KDE_BATCH_PAD_SMALLEST = 0, KDE_BATCH_PAD_FEWEST_STAGES = 1 };
 kde_status kde_batch_tune(kde_batch_plan plan, const void* X, void* density, void* workspace,
                           size_t workspace_bytes, kde_stream_t stream, int reps, float* best_ms);
 kde_status kde_batch_eval(kde_batch_plan plan, const void* X, void* density, void* workspace,
                           size_t workspace_bytes, kde_stream_t stream);
+enum { KDE_BATCH_PERSISTENT = 0, KDE_BATCH_STAGED = 1 };
+kde_status kde_batch_set_mode(kde_batch_plan plan, int mode);
+kde_status kde_batch_get_mode(kde_batch_plan plan, int* mode);
+/* Synchronises the stream, reads and clears the persistent kernel's status:
+ * KDE_ERR_TIMEOUT if one of its waits gave up since the last check (the
+ * output of that evaluation is invalid), else KDE_OK. */
+kde_status kde_batch_check(kde_batch_plan plan, kde_stream_t stream);
+/* Diagnostic of the persistent kernel's waits (no counterpart in the paper):
+ * each wait gives up after `polls` polls of about 256 ns (default 2^22), and
+ * completions of stage `withhold_stage` (0 zeroing, 1 kernel rows, 2
+ * binning, 3 kernel spectrum, 4 count rows, 5 middle axis, 6 output rows;
+ * -1 none, the default) are never signalled, so the waits of the stages
+ * after it run out.  Nothing faults or hangs: the blocks leave and the next
+ * launch starts from a clean queue. */
+kde_status kde_batch_set_wait(kde_batch_plan plan, uint32_t polls, int withhold_stage);
 kde_status kde_batch_plan_destroy(kde_batch_plan plan);
 
 /* kde_fft_eval without a workspace argument, for callers that cannot

@@ -39,6 +39,9 @@ namespace {
 
 // Global loads issued back to back by one thread before their values are
 // stored to shared memory (memory-level parallelism of the load phases).
+// Loads of arrays that other blocks produce (counts, spectra) take the
+// L2-only path (__ldcg): the persistent batch kernel reads, within one
+// launch, data that other blocks wrote after a completion counter said so.
 constexpr int kLoadBatch = 8;
 
 // Twiddle table -> shared memory by asynchronous copies (cp.async): they
@@ -131,8 +134,8 @@ __device__ __forceinline__ void rows_counts_body(const long long* __restrict__ c
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
       const int x = x0 + u * g.tpl;
-      u0[u] = x < p.Min ? __ldg(c0 + x) : 0;
-      u1[u] = (x < p.Min && two) ? __ldg(c1 + x) : 0;
+      u0[u] = x < p.Min ? __ldcg(c0 + x) : 0;
+      u1[u] = (x < p.Min && two) ? __ldcg(c1 + x) : 0;
     }
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
@@ -246,8 +249,8 @@ __device__ __forceinline__ void rows_c2r_body(const C2RParams<T>& p, int64_t vb)
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
       const int k = k0 + u * g.tpl;
-      X[u] = k < p.Q ? x0[k] : mk<V>(0, 0);
-      Y[u] = (k < p.Q && two) ? x1[k] : mk<V>(0, 0);
+      X[u] = k < p.Q ? __ldcg(x0 + k) : mk<V>(0, 0);
+      Y[u] = (k < p.Q && two) ? __ldcg(x1 + k) : mk<V>(0, 0);
     }
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
@@ -384,8 +387,8 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
         const int n = source_row(pos, P, p.Lw, p.Nin);
         const int64_t s = s0 + 2 * t;
         const bool ok = idx < P * npair && n < p.Nin;
-        v1[u] = (ok && s < p.S) ? in[(int64_t)n * p.S + s] : mk<V>(0, 0);
-        v2[u] = (ok && s + 1 < p.S) ? in[(int64_t)n * p.S + s + 1] : mk<V>(0, 0);
+        v1[u] = (ok && s < p.S) ? __ldcg(in + (int64_t)n * p.S + s) : mk<V>(0, 0);
+        v2[u] = (ok && s + 1 < p.S) ? __ldcg(in + (int64_t)n * p.S + s + 1) : mk<V>(0, 0);
       }
 #pragma unroll
       for (int u = 0; u < kLoadBatch; ++u) {
@@ -439,7 +442,7 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
       const int pos = idx / W, t = idx - pos * W;
       const int n = source_row(pos, P, p.Lw, p.Nin);
       const int64_t s = s0 + t;
-      v[u] = (idx < P * W && n < p.Nin && s < p.S) ? in[(int64_t)n * p.S + s] : mk<V>(0, 0);
+      v[u] = (idx < P * W && n < p.Nin && s < p.S) ? __ldcg(in + (int64_t)n * p.S + s) : mk<V>(0, 0);
     }
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
@@ -463,7 +466,7 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
 #pragma unroll
       for (int u = 0; u < kLoadBatch; ++u) {
         const int k = g.lt + u * g.tpl;
-        kpre[u] = k < P ? __ldg(Kc + k) : T(0);
+        kpre[u] = k < P ? __ldcg(Kc + k) : T(0);
       }
     }
     if (MODE == COL_INV)
@@ -481,7 +484,7 @@ __device__ __forceinline__ void cols_body_slab(const ColsParams<T>& p, int64_t s
 #pragma unroll
         for (int u = 0; u < kLoadBatch; ++u) {
           const int k = k0 + u * g.tpl;
-          kv[u] = k < P ? __ldg(Kc + k) : T(0);
+          kv[u] = k < P ? __ldcg(Kc + k) : T(0);
         }
 #pragma unroll
         for (int u = 0; u < kLoadBatch; ++u) {
@@ -2238,14 +2241,12 @@ struct BatchArgs {
 // whole work items, so each knows its problem without a per-sample search.
 constexpr int kBinChunk = 8192;
 
+// Chunk vb of problem it's samples (all threads of the block).
 template <typename T>
-__global__ void __launch_bounds__(256) kde_batch_bin_kernel(BatchArgs<T> a) {
-  const int* wst = a.wstart + BP_BIN * (a.count + 1);
-  const int total = wst[a.count];
-  for (int w = blockIdx.x; w < total; w += gridDim.x) {
-    const int it = find_item(wst, a.count, w);
+__device__ __forceinline__ void batch_bin_item(const BatchArgs<T>& a, int it, int64_t vb) {
+  {
     const BatchItem<T>& B = a.items[it];
-    const int64_t c0 = (int64_t)(w - wst[it]) * kBinChunk;
+    const int64_t c0 = vb * kBinChunk;
     const int64_t c1 = min(B.n, c0 + kBinChunk);
     // two adjacent lanes per sample: lane parity p adds the corners at
     // offset p along the last axis, so a lane pair's two words share a
@@ -2285,22 +2286,35 @@ __global__ void __launch_bounds__(256) kde_batch_bin_kernel(BatchArgs<T> a) {
   }
 }
 
-template <typename T, int PASS>
-__global__ void __launch_bounds__(256) kde_batch_pass_kernel(BatchArgs<T> a) {
-  using V = typename Cplx<T>::type;
-  __shared__ RowsParams<T> rp;
-  __shared__ C2RParams<T> cr;
-  __shared__ ColsParams<T> cp;
-  __shared__ KGen<T> gen;
-  __shared__ int item, base;
-  const int* wst = a.wstart + PASS * (a.count + 1);
+template <typename T>
+__global__ void __launch_bounds__(256) kde_batch_bin_kernel(BatchArgs<T> a) {
+  const int* wst = a.wstart + BP_BIN * (a.count + 1);
   const int total = wst[a.count];
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
-    if (threadIdx.x == 0) {
-      const int it = find_item(wst, a.count, w);
+    const int it = find_item(wst, a.count, w);
+    batch_bin_item<T>(a, it, w - wst[it]);
+  }
+}
+
+// Per-block parameters of a pass over one problem (set by one thread).
+template <typename T>
+struct PassShared {
+  RowsParams<T> rp;
+  C2RParams<T> cr;
+  ColsParams<T> cp;
+  KGen<T> gen;
+};
+
+template <typename T>
+__device__ __forceinline__ void batch_pass_params(const BatchArgs<T>& a, int PASS, int it,
+                                                  PassShared<T>& sh) {
+  {
+    {
       const BatchItem<T>& B = a.items[it];
-      item = it;
-      base = wst[it];
+      RowsParams<T>& rp = sh.rp;
+      C2RParams<T>& cr = sh.cr;
+      ColsParams<T>& cp = sh.cp;
+      KGen<T>& gen = sh.gen;
       if (PASS == BP_KROWS || PASS == BP_ROWS) {
         RowsParams<T> r{};
         r.Q = B.Q;
@@ -2351,14 +2365,161 @@ __global__ void __launch_bounds__(256) kde_batch_pass_kernel(BatchArgs<T> a) {
         cp = c;
       }
     }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void batch_pass_body(const BatchArgs<T>& a, int PASS, int it, int64_t vb,
+                                                const PassShared<T>& sh) {
+  if (PASS == BP_KROWS) rows_kgen_body<T>(sh.gen, sh.rp, vb);
+  if (PASS == BP_ROWS) rows_counts_body<T>(a.counts + a.items[it].counts_off, sh.rp, vb);
+  if (PASS == BP_C2R) rows_c2r_body<T>(sh.cr, vb);
+  if (PASS == BP_KCOLS) cols_body_slab<T, COL_FWD_REAL>(sh.cp, 0, vb);
+  if (PASS == BP_MID) cols_body_slab<T, COL_MID>(sh.cp, 0, vb);
+}
+
+template <typename T, int PASS>
+__global__ void __launch_bounds__(256) kde_batch_pass_kernel(BatchArgs<T> a) {
+  __shared__ PassShared<T> sh;
+  __shared__ int item, base;
+  const int* wst = a.wstart + PASS * (a.count + 1);
+  const int total = wst[a.count];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const int it = find_item(wst, a.count, w);
+      item = it;
+      base = wst[it];
+      batch_pass_params<T>(a, PASS, it, sh);
+    }
     __syncthreads();
-    const int64_t vb = w - base;
-    if (PASS == BP_KROWS) rows_kgen_body<T>(gen, rp, vb);
-    if (PASS == BP_ROWS) rows_counts_body<T>(a.counts + a.items[item].counts_off, rp, vb);
-    if (PASS == BP_C2R) rows_c2r_body<T>(cr, vb);
-    if (PASS == BP_KCOLS) cols_body_slab<T, COL_FWD_REAL>(cp, 0, vb);
-    if (PASS == BP_MID) cols_body_slab<T, COL_MID>(cp, 0, vb);
+    batch_pass_body<T>(a, PASS, item, w - base, sh);
     __syncthreads();  // the next item reloads twiddles and parameters
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The whole ragged batch as one persistent launch.  Work items of every
+// problem and stage form one queue in stage order (zero the counts, kernel
+// rows, binning, kernel spectrum, count rows, middle axis, output rows);
+// blocks claim items with an atomic counter.  An item waits for the stages
+// of its own problem it reads from (per-problem completion counters), which
+// all precede it in the queue, so a claimed item only waits on items
+// already claimed by running blocks: the queue always progresses.  Every
+// wait is bounded: after wait_polls polls the block records the timeout in
+// the status word, raises the abort flag (waiters of this launch then give
+// up at once) and leaves.  The last block out resets the queue for the next
+// launch.  Completion: every thread fences its writes, the block barrier,
+// then one thread adds to the counter; a waiter fences after it sees the
+// count, and the stages read produced data through L2 (__ldcg).
+// ---------------------------------------------------------------------------
+enum PersistStage { PS_ZERO = 0, PS_KROWS, PS_BIN, PS_KCOLS, PS_ROWS, PS_MID, PS_C2R, PS_COUNT };
+constexpr int kZeroChunk = 1 << 16;        // int64 counts zeroed per item
+constexpr unsigned kCtlWords = 4;          // next, exited, abort, status; then done[count][PS_COUNT]
+constexpr unsigned kDefaultWaitPolls = 1u << 22;   // about a second of polls
+
+template <typename T>
+struct PersistArgs {
+  BatchArgs<T> a;
+  const int* pstart;                // [PS_COUNT][count + 1] items per problem, prefix
+  int stage_first[PS_COUNT + 1];    // queue index of each stage's first item
+  unsigned* ctl;
+  unsigned wait_polls;
+  int withhold;                     // stage whose completions are never signalled (-1: none)
+};
+
+__device__ __forceinline__ int stage_pass(int st) {
+  switch (st) {
+    case PS_KROWS: return BP_KROWS;
+    case PS_KCOLS: return BP_KCOLS;
+    case PS_ROWS: return BP_ROWS;
+    case PS_MID: return BP_MID;
+    case PS_C2R: return BP_C2R;
+    default: return -1;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kde_batch_persistent_kernel(PersistArgs<T> pa) {
+  __shared__ PassShared<T> sh;
+  __shared__ unsigned s_item;
+  __shared__ int s_ok;
+  const BatchArgs<T>& a = pa.a;
+  unsigned* ctl = pa.ctl;
+  unsigned* done = ctl + kCtlWords;
+  const unsigned total = (unsigned)pa.stage_first[PS_COUNT];
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&ctl[0], 1u);
+    __syncthreads();
+    const unsigned item = s_item;
+    if (item >= total) break;
+    int st = 0;
+    while (item >= (unsigned)pa.stage_first[st + 1]) ++st;
+    const int w = (int)item - pa.stage_first[st];
+    const int* ps = pa.pstart + st * (a.count + 1);
+    const int it = find_item(ps, a.count, w);
+    const int64_t vb = w - ps[it];
+    if (threadIdx.x == 0) {
+      int dep[2] = {-1, -1};
+      if (st == PS_BIN) dep[0] = PS_ZERO;
+      if (st == PS_KCOLS) dep[0] = PS_KROWS;
+      if (st == PS_ROWS) dep[0] = PS_BIN;
+      if (st == PS_MID) {
+        dep[0] = PS_ROWS;
+        dep[1] = PS_KCOLS;
+      }
+      if (st == PS_C2R) dep[0] = PS_MID;
+      bool ok = true;
+      for (int k = 0; k < 2 && ok; ++k) {
+        if (dep[k] < 0) continue;
+        const int* pd = pa.pstart + dep[k] * (a.count + 1);
+        const unsigned need = (unsigned)(pd[it + 1] - pd[it]);
+        volatile unsigned* cnt = done + (size_t)it * PS_COUNT + dep[k];
+        volatile unsigned* abort_flag = ctl + 2;
+        unsigned polls = 0;
+        while (*cnt < need) {
+          if (*abort_flag || ++polls > pa.wait_polls) {
+            ok = false;
+            break;
+          }
+          __nanosleep(256);
+        }
+      }
+      if (!ok) {
+        atomicExch(&ctl[3], 1u);   // status: a wait gave up (kept until checked)
+        atomicExch(&ctl[2], 1u);   // abort this launch
+      }
+      __threadfence();
+      s_ok = ok;
+      if (ok && stage_pass(st) >= 0) batch_pass_params<T>(a, stage_pass(st), it, sh);
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    if (st == PS_ZERO) {
+      const BatchItem<T>& B = a.items[it];
+      const int64_t cells = (int64_t)B.M[0] * B.M[1];
+      long long* c = a.counts + B.counts_off;
+      for (int64_t i = vb * kZeroChunk + threadIdx.x; i < min(cells, (vb + 1) * kZeroChunk);
+           i += blockDim.x)
+        c[i] = 0;
+    } else if (st == PS_BIN) {
+      batch_bin_item<T>(a, it, vb);
+    } else {
+      batch_pass_body<T>(a, stage_pass(st), it, vb, sh);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && st != pa.withhold) atomicAdd(done + (size_t)it * PS_COUNT + st, 1u);
+  }
+  // the last block out resets the queue and the counters for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl[1], 1u) == gridDim.x - 1) {
+      for (int i = 0; i < a.count * PS_COUNT; ++i) done[i] = 0;
+      ctl[0] = 0;
+      ctl[2] = 0;
+      __threadfence();
+      ctl[1] = 0;
+    }
   }
 }
 
@@ -2375,8 +2536,18 @@ struct kde_batch_plan_s {
   int64_t x_total, counts_elems, kspec_elems, A_elems, T1_elems, dens_elems;
   int Pmax;
   int tpl_rows, tpl_cols;           // launch shape (tunable)
+  int mode;                         // KDE_BATCH_PERSISTENT or KDE_BATCH_STAGED (tunable)
+  int* pstart_dev;                  // [PS_COUNT][count + 1] items per problem (persistent queue)
+  std::vector<int> pstart;
+  unsigned* ctl_dev;                // queue control words and completion counters
+  unsigned wait_polls;
+  int withhold;
   size_t workspace_bytes;
   std::vector<int64_t> n;           // samples per problem
+  std::vector<kde_batch_item> items;  // the problems, for re-planning by the tuner
+  kde_opts opts;
+  int pad_policy;                   // KDE_BATCH_PAD_SMALLEST or KDE_BATCH_PAD_FEWEST_STAGES
+  int radix_order;                  // 0: largest radix first, 1: smallest first
   // the kernel-grid passes need no samples: they run on this stream beside
   // the binning (fork and join events on the caller's stream)
   cudaStream_t side;
@@ -2462,9 +2633,57 @@ kde_status batch_work(kde_batch_plan_s* bp) {
     for (int pss = 0; pss < BP_COUNT; ++pss)
       bp->wstart[(size_t)pss * (c + 1) + i + 1] = bp->wstart[(size_t)pss * (c + 1) + i] + w[pss];
   }
+  // the persistent queue's stages: zeroing of the counts, then the passes
+  bp->pstart.assign((size_t)PS_COUNT * (c + 1), 0);
+  for (int i = 0; i < c; ++i) {
+    const kde_plan_info& I = bp->plans[i]->info;
+    int w[PS_COUNT];
+    const int* ws = bp->wstart.data();
+    auto per = [&](int pss) { return ws[(size_t)pss * (c + 1) + i + 1] - ws[(size_t)pss * (c + 1) + i]; };
+    w[PS_ZERO] = (int)((I.M[0] * I.M[1] + kZeroChunk - 1) / kZeroChunk);
+    w[PS_KROWS] = per(BP_KROWS);
+    w[PS_BIN] = per(BP_BIN);
+    w[PS_KCOLS] = per(BP_KCOLS);
+    w[PS_ROWS] = per(BP_ROWS);
+    w[PS_MID] = per(BP_MID);
+    w[PS_C2R] = per(BP_C2R);
+    for (int st = 0; st < PS_COUNT; ++st)
+      bp->pstart[(size_t)st * (c + 1) + i + 1] = bp->pstart[(size_t)st * (c + 1) + i] + w[st];
+  }
   cudaError_t e = cudaMemcpy(bp->wstart_dev, bp->wstart.data(), sizeof(int) * bp->wstart.size(),
                              cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(bp->pstart_dev, bp->pstart.data(), sizeof(int) * bp->pstart.size(),
+                   cudaMemcpyHostToDevice);
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, "cudaMemcpy(batch work)");
+}
+
+template <typename T>
+kde_status batch_persistent(kde_batch_plan_s* bp, const BatchArgs<T>& a0, cudaStream_t st) {
+  PersistArgs<T> pa{};
+  pa.a = a0;
+  pa.a.tpl_cols = pa.a.tpl_rows;   // one block shape for every stage
+  pa.pstart = bp->pstart_dev;
+  const int c = bp->count;
+  pa.stage_first[0] = 0;
+  for (int st2 = 0; st2 < PS_COUNT; ++st2)
+    pa.stage_first[st2 + 1] = pa.stage_first[st2] + bp->pstart[(size_t)st2 * (c + 1) + c];
+  pa.ctl = bp->ctl_dev;
+  pa.wait_polls = bp->wait_polls;
+  pa.withhold = bp->withhold;
+  auto* fn = kde_batch_persistent_kernel<T>;
+  cudaError_t e = allow_smem(fn);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  const size_t smem = line_smem<T>(bp->Pmax, kBatchLines);
+  const int threads = bp->tpl_rows * kBatchLines;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  const int grid = std::max(1, std::min(pa.stage_first[PS_COUNT], std::max(1, per_sm) * num_sms()));
+  LaunchScope ls("kde_batch_persistent_kernel", st);
+  fn<<<grid, threads, smem, st>>>(pa);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? KDE_OK : cuda_fail(e, "kde_batch_persistent_kernel");
 }
 
 template <typename T>
@@ -2488,6 +2707,7 @@ kde_status batch_eval_impl(kde_batch_plan_s* bp, const void* X, void* density, v
   w += up(bp->A_elems * sizeof(V));
   a.T1 = (V*)w;
   a.density = (T*)density;
+  if (bp->mode == KDE_BATCH_PERSISTENT) return batch_persistent<T>(bp, a, st);
   // the kernel-grid passes (no samples needed) fork onto the plan's side
   // stream and join before the count rows
   cudaError_t e = cudaEventRecord(bp->fork, st);
@@ -2529,6 +2749,78 @@ kde_status batch_eval_impl(kde_batch_plan_s* bp, const void* X, void* density, v
 }  // namespace
 }  // namespace kde
 
+namespace kde {
+namespace {
+
+// Padded length of one problem's axis under a batch padding policy: the
+// smallest 7-smooth size >= need, or the one with the fewest radix stages
+// up to 25% longer (ties: the shorter).
+int64_t batch_pad(int64_t need, int policy) {
+  auto smooth = [](int64_t x) {
+    for (int q : {2, 3, 5, 7})
+      while (x % q == 0) x /= q;
+    return x == 1;
+  };
+  int64_t P = need;
+  while (!smooth(P)) ++P;
+  if (policy != KDE_BATCH_PAD_FEWEST_STAGES) return P;
+  auto stages = [](int64_t x) {
+    int n = 0;
+    for (int r : {8, 7, 5, 4, 3, 2})
+      while (x % r == 0) {
+        x /= r;
+        ++n;
+      }
+    return n;
+  };
+  int64_t best = P;
+  for (int64_t q = P; q <= need + need / 4; ++q)
+    if (smooth(q) && stages(q) < stages(best)) best = q;
+  return best;
+}
+
+// (Re)creates every problem's plan under the batch's padding policy and
+// radix order (the Stockham passes run the batch; the radix plan of an axis
+// is applied in the chosen order).
+kde_status batch_plans(kde_batch_plan_s* bp) {
+  for (auto* p : bp->plans) kde_plan_destroy(p);
+  bp->plans.clear();
+  bp->Pmax = 0;
+  for (size_t i = 0; i < bp->items.size(); ++i) {
+    const kde_batch_item& it = bp->items[i];
+    kde_opts o = bp->opts;
+    o.engine = KDE_ENGINE_STOCKHAM;
+    kde_plan_info info{};
+    kde_status s = kde_plan_info_compute(2, it.M, it.lo, it.hi, it.H, &o, &info);
+    if (s != KDE_OK) return s;
+    for (int k = 0; k < 2; ++k)
+      o.P_min[k] = std::max(o.P_min[k], batch_pad(it.M[k] + info.L[k], bp->pad_policy));
+    kde_plan p = nullptr;
+    if ((s = kde_plan_create(2, it.M, it.lo, it.hi, it.H, &o, &p)) != KDE_OK) return s;
+    if (bp->radix_order == 1)
+      for (int k = 0; k < 2; ++k) std::reverse(p->info.radix[k], p->info.radix[k] + p->info.nstages[k]);
+    bp->plans.push_back(p);
+    for (int k = 0; k < 2; ++k) bp->Pmax = std::max(bp->Pmax, (int)p->info.P[k]);
+  }
+  return KDE_OK;
+}
+
+// Re-plans, re-uploads the problem table and the work counts.
+kde_status batch_rebuild(kde_batch_plan_s* bp) {
+  kde_status s = batch_plans(bp);
+  if (s != KDE_OK) return s;
+  if (bp->items_dev) {
+    cudaFree(bp->items_dev);
+    bp->items_dev = nullptr;
+  }
+  s = (bp->precision == KDE_F32) ? batch_upload<float>(bp, bp->items.data())
+                                 : batch_upload<double>(bp, bp->items.data());
+  return s == KDE_OK ? batch_work(bp) : s;
+}
+
+}  // namespace
+}  // namespace kde
+
 extern "C" kde_status kde_batch_plan_create(int count, const kde_batch_item* items,
                                             const kde_opts* opts, kde_batch_plan* out) {
   if (!out || !items || count < 1) return fail(KDE_ERR_INVALID_ARG, "bad argument");
@@ -2540,6 +2832,11 @@ extern "C" kde_status kde_batch_plan_create(int count, const kde_batch_item* ite
   bp->Pmax = 0;
   bp->tpl_rows = 64;
   bp->tpl_cols = 64;
+  bp->mode = KDE_BATCH_PERSISTENT;
+  bp->wait_polls = kDefaultWaitPolls;
+  bp->withhold = -1;
+  bp->pstart_dev = nullptr;
+  bp->ctl_dev = nullptr;
   bp->items_dev = nullptr;
   bp->wstart_dev = nullptr;
   bp->side = nullptr;
@@ -2552,6 +2849,8 @@ extern "C" kde_status kde_batch_plan_create(int count, const kde_batch_item* ite
     for (auto* p : bp->plans) kde_plan_destroy(p);
     if (bp->items_dev) cudaFree(bp->items_dev);
     if (bp->wstart_dev) cudaFree(bp->wstart_dev);
+    if (bp->pstart_dev) cudaFree(bp->pstart_dev);
+    if (bp->ctl_dev) cudaFree(bp->ctl_dev);
     if (bp->side) cudaStreamDestroy(bp->side);
     if (bp->fork) cudaEventDestroy(bp->fork);
     if (bp->join) cudaEventDestroy(bp->join);
@@ -2561,17 +2860,22 @@ extern "C" kde_status kde_batch_plan_create(int count, const kde_batch_item* ite
   for (int i = 0; i < count; ++i) {
     if (items[i].n < 1 || items[i].n >= (int64_t(1) << 31))
       return cleanup(fail(KDE_ERR_INVALID_ARG, "every problem needs 1 <= n < 2^31"));
-    kde_plan p = nullptr;
     bp->n.push_back(items[i].n);
-    kde_status s = kde_plan_create(2, items[i].M, items[i].lo, items[i].hi, items[i].H, &o, &p);
-    if (s != KDE_OK) return cleanup(s);
-    bp->plans.push_back(p);
-    for (int k = 0; k < 2; ++k) bp->Pmax = std::max(bp->Pmax, (int)p->info.P[k]);
+    bp->items.push_back(items[i]);
   }
+  bp->opts = o;
+  bp->pad_policy = KDE_BATCH_PAD_SMALLEST;
+  bp->radix_order = 0;
+  kde_status s0 = batch_plans(bp);
+  if (s0 != KDE_OK) return cleanup(s0);
   const size_t cb = (bp->precision == KDE_F32) ? 8 : 16;
   if (line_smem<float>(bp->Pmax, kBatchLines) / 8 * cb > kSmemMax)
     return cleanup(fail(KDE_ERR_UNSUPPORTED, "padded size too large for the batch passes"));
   cudaError_t e = cudaMalloc((void**)&bp->wstart_dev, sizeof(int) * BP_COUNT * (count + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&bp->pstart_dev, sizeof(int) * PS_COUNT * (count + 1));
+  const size_t ctl_bytes = sizeof(unsigned) * (kCtlWords + (size_t)PS_COUNT * count);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&bp->ctl_dev, ctl_bytes);
+  if (e == cudaSuccess) e = cudaMemset(bp->ctl_dev, 0, ctl_bytes);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc(batch work)"));
   kde_status s = (bp->precision == KDE_F32) ? batch_upload<float>(bp, items) : batch_upload<double>(bp, items);
   if (s == KDE_OK) s = batch_work(bp);
@@ -2604,6 +2908,40 @@ extern "C" kde_status kde_batch_set_shape(kde_batch_plan bp, int tpl_rows, int t
   return KDE_OK;
 }
 
+extern "C" kde_status kde_batch_set_mode(kde_batch_plan bp, int mode) {
+  if (!bp) return fail(KDE_ERR_INVALID_ARG, "NULL plan");
+  if (mode != KDE_BATCH_PERSISTENT && mode != KDE_BATCH_STAGED)
+    return fail(KDE_ERR_INVALID_ARG, "mode: KDE_BATCH_PERSISTENT or KDE_BATCH_STAGED");
+  bp->mode = mode;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_batch_get_mode(kde_batch_plan bp, int* mode) {
+  if (!bp || !mode) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  *mode = bp->mode;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_batch_set_wait(kde_batch_plan bp, uint32_t polls, int withhold_stage) {
+  if (!bp || polls == 0) return fail(KDE_ERR_INVALID_ARG, "need a plan and polls >= 1");
+  if (withhold_stage < -1 || withhold_stage >= PS_COUNT)
+    return fail(KDE_ERR_INVALID_ARG, "withhold_stage: -1 or a stage index 0..6");
+  bp->wait_polls = polls;
+  bp->withhold = withhold_stage;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_batch_check(kde_batch_plan bp, kde_stream_t stream) {
+  if (!bp) return fail(KDE_ERR_INVALID_ARG, "NULL plan");
+  unsigned flag = 0;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&flag, bp->ctl_dev + 3, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && flag) e = cudaMemset(bp->ctl_dev + 3, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(e, "kde_batch_check");
+  if (flag) return fail(KDE_ERR_TIMEOUT, "a wait of the persistent batch kernel gave up; the output is invalid");
+  return KDE_OK;
+}
+
 extern "C" kde_status kde_batch_eval(kde_batch_plan bp, const void* X, void* density, void* workspace,
                                      size_t workspace_bytes, kde_stream_t stream) {
   if (!bp || !density || (!X && bp->x_total > 0)) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
@@ -2624,14 +2962,20 @@ extern "C" kde_status kde_batch_plan_destroy(kde_batch_plan bp) {
   if (bp->join) cudaEventDestroy(bp->join);
   if (bp->items_dev) e = cudaFree(bp->items_dev);
   if (bp->wstart_dev) cudaFree(bp->wstart_dev);
+  if (bp->pstart_dev) cudaFree(bp->pstart_dev);
+  if (bp->ctl_dev) cudaFree(bp->ctl_dev);
   delete bp;
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, "cudaFree(batch)");
 }
 
-// Launch-shape tuner for a batch plan: times kde_batch_eval for every
-// (threads per row line, threads per column line) in {32, 64, 128}^2 with
-// CUDA events on the stream (reps runs each, after one warm-up run) and
-// keeps the fastest.  Synchronises the stream; set-up, not per evaluation.
+// Tuner for a batch plan: times kde_batch_eval with CUDA events on the
+// stream (one warm-up and reps timed runs each) over the padding policy
+// (smallest 7-smooth length, or the fewest radix stages within 25%), the
+// radix order (largest or smallest radix first), the mode (persistent or
+// staged) and the threads per line (32, 64, 128; rows and columns alike in
+// the persistent mode, every pair in the staged one), skipping settings
+// whose workspace exceeds the caller's, and keeps the fastest.  Re-plans
+// the problems (set-up, not per evaluation); synchronises the stream.
 extern "C" kde_status kde_batch_tune(kde_batch_plan bp, const void* X, void* density,
                                      void* workspace, size_t workspace_bytes, kde_stream_t stream,
                                      int reps, float* best_ms) {
@@ -2641,41 +2985,76 @@ extern "C" kde_status kde_batch_tune(kde_batch_plan bp, const void* X, void* den
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(KDE_ERR_CUDA, "cudaEventCreate");
-  float best = 1e30f;
-  int br = bp->tpl_rows, bc = bp->tpl_cols;
-  kde_status s = KDE_OK;
-  for (int tr : {32, 64, 128}) {
-    for (int tc : {32, 64, 128}) {
-      bp->tpl_rows = tr;
-      bp->tpl_cols = tc;
-      if ((s = kde_batch_eval(bp, X, density, workspace, workspace_bytes, stream)) != KDE_OK) break;
-      cudaEventRecord(e0, st);
-      for (int r = 0; r < reps && s == KDE_OK; ++r)
-        s = kde_batch_eval(bp, X, density, workspace, workspace_bytes, stream);
-      cudaEventRecord(e1, st);
-      if (s != KDE_OK) break;
-      cudaError_t e = cudaEventSynchronize(e1);
-      if (e != cudaSuccess) {
-        s = cuda_fail(e, "tuning run");
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= reps;
-      if (ms < best) {
-        best = ms;
-        br = tr;
-        bc = tc;
-      }
+  struct Cfg {
+    int pad, order, mode, tr, tc;
+  };
+  std::vector<Cfg> cfgs;
+  for (int pad : {KDE_BATCH_PAD_SMALLEST, KDE_BATCH_PAD_FEWEST_STAGES})
+    for (int order : {0, 1}) {
+      for (int t : {32, 64, 128}) cfgs.push_back({pad, order, KDE_BATCH_PERSISTENT, t, t});
+      for (int tr : {32, 64, 128})
+        for (int tc : {32, 64, 128}) cfgs.push_back({pad, order, KDE_BATCH_STAGED, tr, tc});
     }
+  float best = 1e30f;
+  Cfg bc = {bp->pad_policy, bp->radix_order, bp->mode, bp->tpl_rows, bp->tpl_cols};
+  kde_status s = KDE_OK;
+  int cur_pad = bp->pad_policy, cur_order = bp->radix_order;
+  for (const Cfg& c : cfgs) {
+    if (c.pad != cur_pad || c.order != cur_order) {
+      bp->pad_policy = c.pad;
+      bp->radix_order = c.order;
+      if ((s = kde::batch_rebuild(bp)) != KDE_OK) break;
+      cur_pad = c.pad;
+      cur_order = c.order;
+    }
+    if (bp->workspace_bytes > workspace_bytes) continue;
+    bp->mode = c.mode;
+    bp->tpl_rows = c.tr;
+    bp->tpl_cols = c.tc;
+    if ((s = kde_batch_eval(bp, X, density, workspace, workspace_bytes, stream)) != KDE_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && s == KDE_OK; ++r)
+      s = kde_batch_eval(bp, X, density, workspace, workspace_bytes, stream);
+    cudaEventRecord(e1, st);
     if (s != KDE_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "tuning run");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms < best) {
+      best = ms;
+      bc = c;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  bp->tpl_rows = br;
-  bp->tpl_cols = bc;
+  if (s != KDE_OK) return s;
+  if (bc.pad != cur_pad || bc.order != cur_order) {
+    bp->pad_policy = bc.pad;
+    bp->radix_order = bc.order;
+    if ((s = kde::batch_rebuild(bp)) != KDE_OK) return s;
+  }
+  bp->mode = bc.mode;
+  bp->tpl_rows = bc.tr;
+  bp->tpl_cols = bc.tc;
   if (best_ms) *best_ms = best;
-  return s;
+  if ((s = kde_batch_check(bp, stream)) != KDE_OK) return s;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_batch_get_config(kde_batch_plan bp, int* pad_policy, int* radix_order,
+                                           int64_t* P) {
+  if (!bp) return fail(KDE_ERR_INVALID_ARG, "NULL plan");
+  if (pad_policy) *pad_policy = bp->pad_policy;
+  if (radix_order) *radix_order = bp->radix_order;
+  if (P)
+    for (int i = 0; i < bp->count; ++i)
+      for (int k = 0; k < 2; ++k) P[2 * i + k] = bp->plans[i]->info.P[k];
+  return KDE_OK;
 }
 
 extern "C" kde_status kde_batch_get_shape(kde_batch_plan bp, int* tpl_rows, int* tpl_cols) {

@@ -180,18 +180,19 @@ __device__ __forceinline__ void rows_a_fwd(const RowsArgs& a, const long long* _
   if (r0 >= a.nrows) return;
   const bool two = r0 + 1 < a.nrows;
   if constexpr (SRC == SRC_COUNTS) {
+    // every load issued before any value is converted (all in flight together)
     const long long* c0 = counts + r0 * a.in_stride;
     const long long* c1 = two ? c0 + a.in_stride : c0;
+    long long v0[N1], v1[N1];
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) {
       const int pos = n2 + N2 * n1;
-      long long v0 = 0, v1 = 0;
-      if (pos < a.Min) {
-        v0 = __ldg(c0 + pos);
-        if (two) v1 = __ldg(c1 + pos);
-      }
-      x[n1] = make_float2(count_value<float>(v0), count_value<float>(v1));
+      v0[n1] = pos < a.Min ? __ldg(c0 + pos) : 0;
+      v1[n1] = (pos < a.Min && two) ? __ldg(c1 + pos) : 0;
     }
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1)
+      x[n1] = make_float2(count_value<float>(v0[n1]), count_value<float>(v1[n1]));
   } else {
     // kernel values staged in shared memory beyond the exchange buffers
     const float2* stage = sm + a.B * N1 * a.SK + (size_t)b * a.ln.P;

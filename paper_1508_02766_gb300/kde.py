@@ -69,7 +69,8 @@ EXPORTS = [
     "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes", "kde_lscv_autocorr_batch",
     "kde_lscv_cands_create", "kde_lscv_cands_destroy", "kde_lscv_autocorr_cands",
     "kde_wait_probe", "kde_plan_check", "kde_outside_check", "kde_noalloc_scratch_bytes",
-    "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes",
+    "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes", "kde_batch_set_mode",
+    "kde_batch_get_mode", "kde_batch_check", "kde_batch_set_wait", "kde_batch_get_config",
 ]
 FEAT_DIM = 1088
 
@@ -132,6 +133,12 @@ def lib():
                                 ctypes.c_int, vp, ctypes.c_int, vp, vp]
     L.kde_fft_eval_multi.argtypes = [vp, i64, ctypes.c_int, dp, vp, vp, vp, ctypes.c_size_t, vp]
     L.kde_fft_eval_multi_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.kde_batch_set_mode.argtypes = [vp, ctypes.c_int]
+    L.kde_batch_get_mode.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.kde_batch_check.argtypes = [vp, vp]
+    L.kde_batch_set_wait.argtypes = [vp, ctypes.c_uint32, ctypes.c_int]
+    L.kde_batch_get_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       i64p]
     L.kde_plan_check.argtypes = [vp, vp]
     L.kde_outside_check.argtypes = [vp, vp, i64p]
     L.kde_noalloc_scratch_bytes.argtypes = []
@@ -157,7 +164,9 @@ def lib():
                  "kde_autocorrelation", "kde_lscv_autocorr", "kde_lscv_autocorr_workspace_bytes",
                  "kde_lscv_autocorr_batch", "kde_lscv_cands_create", "kde_lscv_cands_destroy",
                  "kde_lscv_autocorr_cands", "kde_wait_probe", "kde_plan_check",
-                 "kde_outside_check", "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes"):
+                 "kde_outside_check", "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes",
+                 "kde_batch_set_mode", "kde_batch_get_mode", "kde_batch_check", "kde_batch_set_wait",
+                 "kde_batch_get_config"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -556,12 +565,48 @@ class BatchPlan:
         _check(lib().kde_batch_get_shape(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
+    def _query(self):
+        xr, de, wb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        _check(lib().kde_batch_plan_query(self._h, ctypes.byref(xr), ctypes.byref(de),
+                                          ctypes.byref(wb)))
+        self.x_rows, self.density_elems, self.workspace_bytes = xr.value, de.value, wb.value
+
     def tune(self, X, density, workspace, reps=3, stream=None):
+        """Chooses padding, radix order, mode and threads per line by timing
+        (kde_batch_tune); returns the best time in ms."""
         ms = ctypes.c_float()
         _check(lib().kde_batch_tune(self._h, _ptr(X), _ptr(density), _ptr(workspace),
                                     workspace.numel() * workspace.element_size(),
                                     _stream_ptr(stream), int(reps), ctypes.byref(ms)))
+        self._query()
         return ms.value
+
+    MODES = {"persistent": 0, "staged": 1}
+
+    def set_mode(self, mode):
+        _check(lib().kde_batch_set_mode(self._h, self.MODES[mode]))
+
+    def mode(self):
+        m = ctypes.c_int()
+        _check(lib().kde_batch_get_mode(self._h, ctypes.byref(m)))
+        return {v: k for k, v in self.MODES.items()}[m.value]
+
+    def config(self, count):
+        """(padding policy, radix order, padded lengths per problem)."""
+        pad, order = ctypes.c_int(), ctypes.c_int()
+        P = (ctypes.c_int64 * (2 * count))()
+        _check(lib().kde_batch_get_config(self._h, ctypes.byref(pad), ctypes.byref(order), P))
+        return ({0: "smallest", 1: "fewest_stages"}[pad.value],
+                {0: "largest_first", 1: "smallest_first"}[order.value],
+                [(P[2 * i], P[2 * i + 1]) for i in range(count)])
+
+    def set_wait(self, polls, withhold_stage=-1):
+        _check(lib().kde_batch_set_wait(self._h, int(polls), int(withhold_stage)))
+
+    def check(self, stream=None):
+        """Raises KDEError(KDE_ERR_TIMEOUT) if a wait of the persistent kernel
+        gave up since the last check (synchronises)."""
+        _check(lib().kde_batch_check(self._h, _stream_ptr(stream)))
 
     def eval(self, X, density=None, workspace=None, stream=None):
         import torch

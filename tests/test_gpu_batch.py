@@ -38,8 +38,9 @@ def small_batch(prec, count=9, seed=70):
     return out
 
 
-def run_batch(K, problems, prec, shape=None):
+def run_batch(K, problems, prec, shape=None, mode="persistent"):
     bp = K.BatchPlan([(w.M, w.lo, w.hi, w.H, w.n) for w in problems], precision=prec)
+    bp.set_mode(mode)
     if shape:
         bp.set_shape(*shape)
     X = torch.from_numpy(np.ascontiguousarray(np.concatenate([w.X for w in problems]))).cuda()
@@ -54,19 +55,23 @@ def run_batch(K, problems, prec, shape=None):
     return out, bp, X
 
 
+@pytest.mark.parametrize("mode", ["persistent", "staged"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_small_ragged_batch_every_node(K, prec):
+def test_small_ragged_batch_every_node(K, prec, mode):
     problems = small_batch(prec)
-    dens, _, _ = run_batch(K, problems, prec)
+    dens, bp, _ = run_batch(K, problems, prec, mode=mode)
+    bp.check()
     for w, g in zip(problems, dens):
         f, _, _, _ = O.binned_estimate(w.X, w.H, w.lo, w.hi, w.M, tau=w.tau)
         assert rel_err(g, f) <= TOL[prec]
 
 
-@pytest.mark.parametrize("shape", [(32, 32), (64, 128), (128, 64), (128, 128)])
-def test_every_launch_shape(K, shape):
+@pytest.mark.parametrize("mode,shape", [("staged", (32, 32)), ("staged", (64, 128)),
+                                        ("staged", (128, 64)), ("staged", (128, 128)),
+                                        ("persistent", (32, 32)), ("persistent", (128, 128))])
+def test_every_launch_shape(K, shape, mode):
     problems = small_batch("f64", count=5, seed=90)
-    dens, _, _ = run_batch(K, problems, "f64", shape)
+    dens, _, _ = run_batch(K, problems, "f64", shape, mode)
     for w, g in zip(problems, dens):
         f, _, _, _ = O.binned_estimate(w.X, w.H, w.lo, w.hi, w.M, tau=w.tau)
         assert rel_err(g, f) <= 1e-12
@@ -76,10 +81,16 @@ def test_ragged64_against_single_problem_path_and_tuner(K):
     problems = W.ragged64_f32()
     dens, bp, X = run_batch(K, problems, "f32")
     density = torch.empty(bp.density_elems, dtype=torch.float32, device="cuda")
-    ws = bp.workspace()
+    # room for the longer paddings the tuner may choose
+    ws = torch.empty(2 * bp.workspace_bytes, dtype=torch.uint8, device="cuda")
     ms = bp.tune(X, density, ws, reps=2)
     assert ms > 0 and bp.shape()[0] in (32, 64, 128)
+    pad, order, P = bp.config(len(problems))
+    assert pad in ("smallest", "fewest_stages") and order in ("largest_first", "smallest_first")
+    assert all(Pk >= m for (p2, w) in zip(P, problems) for Pk, m in zip(p2, w.M))
+    assert bp.workspace_bytes <= ws.numel()
     tuned = bp.eval(X, density, ws).cpu().numpy()
+    bp.check()
     off = 0
     rng = np.random.default_rng(2)
     check = set(rng.choice(len(problems), 10, replace=False).tolist())
@@ -119,3 +130,29 @@ def test_samples_on_grid_edges_and_outside(K, prec):
         f, _, _, n_out = O.binned_estimate(w.X, w.H, w.lo, w.hi, w.M, tau=w.tau)
         assert n_out >= 2
         assert rel_err(g, f) <= TOL[prec]
+
+
+def test_persistent_wait_runs_out_and_recovers(K):
+    """A stage whose completions are withheld (count rows): the middle-axis
+    items wait for them, give up after their poll limit, and the status says
+    so; nothing faults or hangs, and the next launch (normal waits) gives the
+    right densities."""
+    import time
+    problems = small_batch("f32", count=4, seed=120)
+    good, bp, X = run_batch(K, problems, "f32")
+    bp.check()
+    bp.set_wait(2000, withhold_stage=4)
+    t0 = time.perf_counter()
+    bp.eval(X)
+    with pytest.raises(K.KDEError) as e:
+        bp.check()
+    assert e.value.status == 6
+    assert time.perf_counter() - t0 < 30.0
+    bp.set_wait(1 << 22, withhold_stage=-1)
+    again = bp.eval(X).cpu().numpy()
+    bp.check()
+    off = 0
+    for g in good:
+        m = g.size
+        assert np.array_equal(again[off:off + m].reshape(g.shape), g)
+        off += m
