@@ -788,33 +788,48 @@ def ragged_main(args):
     stream = torch.cuda.Stream(device=dev)
     X = torch.from_numpy(np.ascontiguousarray(np.concatenate([w.X for w in problems]))).to(dev)
     dens = torch.empty(bp.density_elems, dtype=torch.float32, device=dev)
-    ws = bp.workspace(dev)
+    # room for the longer paddings the tuner may choose
+    ws = torch.empty(2 * bp.workspace_bytes, dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     tuned_ms = bp.tune(X, dens, ws, reps=3, stream=stream)
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+    tuned_mode, tuned_shape = bp.mode(), bp.shape()
+    pad, order, Ps, queue = bp.config(len(problems))
+
+    def timed(mode, shape):
+        """K graph replays of one evaluation in the given mode (L2 flushed)."""
+        bp.set_mode(mode)
+        bp.set_shape(*shape)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                bp.eval(X, dens, ws, stream=stream)
+        torch.cuda.synchronize()
+        bp.check(stream)
+        graph = torch.cuda.CUDAGraph()
+        l0 = kde.launch_count()
+        with torch.cuda.graph(graph, stream=stream):
             bp.eval(X, dens, ws, stream=stream)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    l0 = kde.launch_count()
-    with torch.cuda.graph(graph, stream=stream):
-        bp.eval(X, dens, ws, stream=stream)
-    per_step = kde.launch_count() - l0
+        per_step = kde.launch_count() - l0
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()
+                starts[i].record(stream)
+                graph.replay()
+                ends[i].record(stream)
+        torch.cuda.synchronize()
+        bp.check(stream)
+        return float(sum(a.elapsed_time(b) for a, b in zip(starts, ends))) / args.steps, per_step
+
+    other = "staged" if tuned_mode == "persistent" else "persistent"
+    other_shape = (tuned_shape[0], tuned_shape[0]) if other == "persistent" else tuned_shape
+    ms_other, launches_other = timed(other, other_shape)
     sampler = ClockSampler(0)
     sampler.start()
     time.sleep(0.3)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        for i in range(args.steps):
-            flush.zero_()
-            starts[i].record(stream)
-            graph.replay()
-            ends[i].record(stream)
-    torch.cuda.synchronize()
+    ms_step, per_step = timed(tuned_mode, tuned_shape)
     clocks = sampler.stop()
-    ms_step = float(sum(a.elapsed_time(b) for a, b in zip(starts, ends))) / args.steps
     kde.profile_enable(True)
     with torch.cuda.stream(stream):
         for i in range(args.steps):
@@ -855,8 +870,15 @@ def ragged_main(args):
             "data": "synthetic",
             "config": {"workload": "ragged64_f32", "datasets": len(problems),
                        "grids": sorted({w.M[0] for w in problems}), "total_samples": int(X.shape[0]),
-                       "launch": "one CUDA graph replay per step", "launch_shape": list(bp.shape()),
-                       "tuned_ms": tuned_ms, "l2": "flushed between timed steps (256 MB write)"},
+                       "launch": "one CUDA graph replay per step",
+                       "tuner": {"mode": tuned_mode, "queue_order": queue,
+                                 "threads_per_line": list(tuned_shape),
+                                 "padding": pad, "radix_order": order,
+                                 "padded_lengths": [list(p) for p in Ps], "tuned_ms": tuned_ms},
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "other_mode": {"mode": other, "threads_per_line": list(other_shape),
+                           "ms_per_step": ms_other, "value": len(problems) / (ms_other * 1e-3),
+                           "launches_per_step": launches_other},
             "roofline": roofline, "kernels": kernels, "gpu_launches": per_step * args.steps,
             "clocks": clocks}
     print(json.dumps(line))

@@ -354,9 +354,9 @@ kde_status kde_batch_plan_query(kde_batch_plan plan, int64_t* x_rows, int64_t* d
  * 128); chosen by a caller-side tuner. */
 kde_status kde_batch_set_shape(kde_batch_plan plan, int tpl_rows, int tpl_cols);
 kde_status kde_batch_get_shape(kde_batch_plan plan, int* tpl_rows, int* tpl_cols);
-/* The padding policy and radix order in use (0 largest radix first, 1
- * smallest first) and every problem's padded lengths P (host, 2 x count
- * int64, may be NULL). */
+/* The padding policy, the radix order in use (bits 0-7: 0 largest radix
+ * first, 1 smallest first; bits 8-15: the queue order) and every problem's
+ * padded lengths P (host, 2 x count int64, may be NULL). */
 kde_status kde_batch_get_config(kde_batch_plan plan, int* pad_policy, int* radix_order, int64_t* P);
 /* Autotuner: times kde_batch_eval on the given buffers (reps timed runs each,
  * CUDA events on the stream, which it synchronises) over
@@ -364,7 +364,7 @@ kde_status kde_batch_get_config(kde_batch_plan plan, int* pad_policy, int* radix
  *     7-smooth length >= M + L) or KDE_BATCH_PAD_FEWEST_STAGES (the length
  *     with the fewest radix stages up to 25% longer);
  *   the radix order of every axis (largest radix first or last);
- *   the mode (KDE_BATCH_PERSISTENT, KDE_BATCH_STAGED);
+ *   the mode (KDE_BATCH_PERSISTENT with either queue order, KDE_BATCH_STAGED);
  *   the threads per line (32, 64, 128; the same for rows and columns in the
  *     persistent mode, every pair in the staged mode),
  * skipping settings whose workspace exceeds workspace_bytes, and keeps the
@@ -377,6 +377,12 @@ kde_status kde_batch_tune(kde_batch_plan plan, const void* X, void* density, voi
 kde_status kde_batch_eval(kde_batch_plan plan, const void* X, void* density, void* workspace,
                           size_t workspace_bytes, kde_stream_t stream);
 enum { KDE_BATCH_PERSISTENT = 0, KDE_BATCH_STAGED = 1 };
+/* Order of the persistent queue: every problem's items stage by stage
+ * (KDE_BATCH_QUEUE_STAGES) or problem by problem, the problems with the
+ * most work first (KDE_BATCH_QUEUE_PROBLEMS, the default: a problem's later
+ * stages then run while other problems are still being binned). */
+enum { KDE_BATCH_QUEUE_STAGES = 0, KDE_BATCH_QUEUE_PROBLEMS = 1 };
+kde_status kde_batch_set_queue_order(kde_batch_plan plan, int order);
 kde_status kde_batch_set_mode(kde_batch_plan plan, int mode);
 kde_status kde_batch_get_mode(kde_batch_plan plan, int* mode);
 /* Synchronises the stream, reads and clears the persistent kernel's status:

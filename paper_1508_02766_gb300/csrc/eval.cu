@@ -2399,12 +2399,13 @@ __global__ void __launch_bounds__(256) kde_batch_pass_kernel(BatchArgs<T> a) {
 
 // ---------------------------------------------------------------------------
 // The whole ragged batch as one persistent launch.  Work items of every
-// problem and stage form one queue in stage order (zero the counts, kernel
-// rows, binning, kernel spectrum, count rows, middle axis, output rows);
-// blocks claim items with an atomic counter.  An item waits for the stages
-// of its own problem it reads from (per-problem completion counters), which
-// all precede it in the queue, so a claimed item only waits on items
-// already claimed by running blocks: the queue always progresses.  Every
+// problem and stage (zero the counts, kernel rows, binning, kernel spectrum,
+// count rows, middle axis, output rows) form one queue, in stage order or
+// problem by problem (largest first); blocks claim items with an atomic
+// counter.  An item waits for the stages of its own problem it reads from
+// (per-problem completion counters); in either order those precede it in
+// the queue, so a claimed item only waits on items already claimed by
+// running blocks: the queue always progresses.  Every
 // wait is bounded: after wait_polls polls the block records the timeout in
 // the status word, raises the abort flag (waiters of this launch then give
 // up at once) and leaves.  The last block out resets the queue for the next
@@ -2421,7 +2422,8 @@ template <typename T>
 struct PersistArgs {
   BatchArgs<T> a;
   const int* pstart;                // [PS_COUNT][count + 1] items per problem, prefix
-  int stage_first[PS_COUNT + 1];    // queue index of each stage's first item
+  const int4* queue;                // per queue position: problem, stage, item within it
+  int total;                        // queue length
   unsigned* ctl;
   unsigned wait_polls;
   int withhold;                     // stage whose completions are never signalled (-1: none)
@@ -2446,18 +2448,15 @@ __global__ void __launch_bounds__(256) kde_batch_persistent_kernel(PersistArgs<T
   const BatchArgs<T>& a = pa.a;
   unsigned* ctl = pa.ctl;
   unsigned* done = ctl + kCtlWords;
-  const unsigned total = (unsigned)pa.stage_first[PS_COUNT];
+  const unsigned total = (unsigned)pa.total;
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(&ctl[0], 1u);
     __syncthreads();
     const unsigned item = s_item;
     if (item >= total) break;
-    int st = 0;
-    while (item >= (unsigned)pa.stage_first[st + 1]) ++st;
-    const int w = (int)item - pa.stage_first[st];
-    const int* ps = pa.pstart + st * (a.count + 1);
-    const int it = find_item(ps, a.count, w);
-    const int64_t vb = w - ps[it];
+    const int4 q = pa.queue[item];
+    const int it = q.x, st = q.y;
+    const int64_t vb = q.z;
     if (threadIdx.x == 0) {
       int dep[2] = {-1, -1};
       if (st == PS_BIN) dep[0] = PS_ZERO;
@@ -2539,6 +2538,9 @@ struct kde_batch_plan_s {
   int mode;                         // KDE_BATCH_PERSISTENT or KDE_BATCH_STAGED (tunable)
   int* pstart_dev;                  // [PS_COUNT][count + 1] items per problem (persistent queue)
   std::vector<int> pstart;
+  int4* queue_dev;                  // the persistent queue (problem, stage, item)
+  int queue_len, queue_cap;
+  int queue_order;                  // KDE_BATCH_QUEUE_STAGES or KDE_BATCH_QUEUE_PROBLEMS
   unsigned* ctl_dev;                // queue control words and completion counters
   unsigned wait_polls;
   int withhold;
@@ -2650,11 +2652,45 @@ kde_status batch_work(kde_batch_plan_s* bp) {
     for (int st = 0; st < PS_COUNT; ++st)
       bp->pstart[(size_t)st * (c + 1) + i + 1] = bp->pstart[(size_t)st * (c + 1) + i] + w[st];
   }
-  cudaError_t e = cudaMemcpy(bp->wstart_dev, bp->wstart.data(), sizeof(int) * bp->wstart.size(),
-                             cudaMemcpyHostToDevice);
+  // the queue: stage by stage, or problem by problem with the most work first
+  std::vector<int4> q;
+  auto items_of = [&](int i, int st) {
+    return bp->pstart[(size_t)st * (c + 1) + i + 1] - bp->pstart[(size_t)st * (c + 1) + i];
+  };
+  if (bp->queue_order == KDE_BATCH_QUEUE_PROBLEMS) {
+    std::vector<int> order(c);
+    for (int i = 0; i < c; ++i) order[i] = i;
+    std::vector<int64_t> work(c, 0);
+    for (int i = 0; i < c; ++i) {
+      const kde_plan_info& I = bp->plans[i]->info;
+      work[i] = bp->n[i] + (int64_t)I.P[0] * I.P[1];
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+    for (int i : order)
+      for (int st = 0; st < PS_COUNT; ++st)
+        for (int v = 0; v < items_of(i, st); ++v) q.push_back(make_int4(i, st, v, 0));
+  } else {
+    for (int st = 0; st < PS_COUNT; ++st)
+      for (int i = 0; i < c; ++i)
+        for (int v = 0; v < items_of(i, st); ++v) q.push_back(make_int4(i, st, v, 0));
+  }
+  cudaError_t e = cudaSuccess;
+  if ((int)q.size() > bp->queue_cap) {
+    if (bp->queue_dev) cudaFree(bp->queue_dev);
+    bp->queue_dev = nullptr;
+    bp->queue_cap = 0;
+    e = cudaMalloc((void**)&bp->queue_dev, sizeof(int4) * q.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch queue)");
+    bp->queue_cap = (int)q.size();
+  }
+  bp->queue_len = (int)q.size();
+  e = cudaMemcpy(bp->wstart_dev, bp->wstart.data(), sizeof(int) * bp->wstart.size(),
+                 cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(bp->pstart_dev, bp->pstart.data(), sizeof(int) * bp->pstart.size(),
                    cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(bp->queue_dev, q.data(), sizeof(int4) * q.size(), cudaMemcpyHostToDevice);
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, "cudaMemcpy(batch work)");
 }
 
@@ -2664,10 +2700,8 @@ kde_status batch_persistent(kde_batch_plan_s* bp, const BatchArgs<T>& a0, cudaSt
   pa.a = a0;
   pa.a.tpl_cols = pa.a.tpl_rows;   // one block shape for every stage
   pa.pstart = bp->pstart_dev;
-  const int c = bp->count;
-  pa.stage_first[0] = 0;
-  for (int st2 = 0; st2 < PS_COUNT; ++st2)
-    pa.stage_first[st2 + 1] = pa.stage_first[st2] + bp->pstart[(size_t)st2 * (c + 1) + c];
+  pa.queue = bp->queue_dev;
+  pa.total = bp->queue_len;
   pa.ctl = bp->ctl_dev;
   pa.wait_polls = bp->wait_polls;
   pa.withhold = bp->withhold;
@@ -2679,7 +2713,7 @@ kde_status batch_persistent(kde_batch_plan_s* bp, const BatchArgs<T>& a0, cudaSt
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-  const int grid = std::max(1, std::min(pa.stage_first[PS_COUNT], std::max(1, per_sm) * num_sms()));
+  const int grid = std::max(1, std::min(pa.total, std::max(1, per_sm) * num_sms()));
   LaunchScope ls("kde_batch_persistent_kernel", st);
   fn<<<grid, threads, smem, st>>>(pa);
   e = cudaGetLastError();
@@ -2837,6 +2871,9 @@ extern "C" kde_status kde_batch_plan_create(int count, const kde_batch_item* ite
   bp->withhold = -1;
   bp->pstart_dev = nullptr;
   bp->ctl_dev = nullptr;
+  bp->queue_dev = nullptr;
+  bp->queue_len = bp->queue_cap = 0;
+  bp->queue_order = KDE_BATCH_QUEUE_PROBLEMS;
   bp->items_dev = nullptr;
   bp->wstart_dev = nullptr;
   bp->side = nullptr;
@@ -2851,6 +2888,7 @@ extern "C" kde_status kde_batch_plan_create(int count, const kde_batch_item* ite
     if (bp->wstart_dev) cudaFree(bp->wstart_dev);
     if (bp->pstart_dev) cudaFree(bp->pstart_dev);
     if (bp->ctl_dev) cudaFree(bp->ctl_dev);
+    if (bp->queue_dev) cudaFree(bp->queue_dev);
     if (bp->side) cudaStreamDestroy(bp->side);
     if (bp->fork) cudaEventDestroy(bp->fork);
     if (bp->join) cudaEventDestroy(bp->join);
@@ -2964,6 +3002,7 @@ extern "C" kde_status kde_batch_plan_destroy(kde_batch_plan bp) {
   if (bp->wstart_dev) cudaFree(bp->wstart_dev);
   if (bp->pstart_dev) cudaFree(bp->pstart_dev);
   if (bp->ctl_dev) cudaFree(bp->ctl_dev);
+  if (bp->queue_dev) cudaFree(bp->queue_dev);
   delete bp;
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, "cudaFree(batch)");
 }
@@ -2986,26 +3025,30 @@ extern "C" kde_status kde_batch_tune(kde_batch_plan bp, const void* X, void* den
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(KDE_ERR_CUDA, "cudaEventCreate");
   struct Cfg {
-    int pad, order, mode, tr, tc;
+    int pad, order, mode, tr, tc, queue;
   };
   std::vector<Cfg> cfgs;
   for (int pad : {KDE_BATCH_PAD_SMALLEST, KDE_BATCH_PAD_FEWEST_STAGES})
     for (int order : {0, 1}) {
-      for (int t : {32, 64, 128}) cfgs.push_back({pad, order, KDE_BATCH_PERSISTENT, t, t});
+      for (int qo : {KDE_BATCH_QUEUE_PROBLEMS, KDE_BATCH_QUEUE_STAGES})
+        for (int t : {32, 64, 128}) cfgs.push_back({pad, order, KDE_BATCH_PERSISTENT, t, t, qo});
       for (int tr : {32, 64, 128})
-        for (int tc : {32, 64, 128}) cfgs.push_back({pad, order, KDE_BATCH_STAGED, tr, tc});
+        for (int tc : {32, 64, 128})
+          cfgs.push_back({pad, order, KDE_BATCH_STAGED, tr, tc, bp->queue_order});
     }
   float best = 1e30f;
-  Cfg bc = {bp->pad_policy, bp->radix_order, bp->mode, bp->tpl_rows, bp->tpl_cols};
+  Cfg bc = {bp->pad_policy, bp->radix_order, bp->mode, bp->tpl_rows, bp->tpl_cols, bp->queue_order};
   kde_status s = KDE_OK;
-  int cur_pad = bp->pad_policy, cur_order = bp->radix_order;
+  int cur_pad = bp->pad_policy, cur_order = bp->radix_order, cur_q = bp->queue_order;
   for (const Cfg& c : cfgs) {
-    if (c.pad != cur_pad || c.order != cur_order) {
+    if (c.pad != cur_pad || c.order != cur_order || c.queue != cur_q) {
       bp->pad_policy = c.pad;
       bp->radix_order = c.order;
+      bp->queue_order = c.queue;
       if ((s = kde::batch_rebuild(bp)) != KDE_OK) break;
       cur_pad = c.pad;
       cur_order = c.order;
+      cur_q = c.queue;
     }
     if (bp->workspace_bytes > workspace_bytes) continue;
     bp->mode = c.mode;
@@ -3033,9 +3076,10 @@ extern "C" kde_status kde_batch_tune(kde_batch_plan bp, const void* X, void* den
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != KDE_OK) return s;
-  if (bc.pad != cur_pad || bc.order != cur_order) {
+  if (bc.pad != cur_pad || bc.order != cur_order || bc.queue != cur_q) {
     bp->pad_policy = bc.pad;
     bp->radix_order = bc.order;
+    bp->queue_order = bc.queue;
     if ((s = kde::batch_rebuild(bp)) != KDE_OK) return s;
   }
   bp->mode = bc.mode;
@@ -3046,11 +3090,19 @@ extern "C" kde_status kde_batch_tune(kde_batch_plan bp, const void* X, void* den
   return KDE_OK;
 }
 
+extern "C" kde_status kde_batch_set_queue_order(kde_batch_plan bp, int order) {
+  if (!bp) return fail(KDE_ERR_INVALID_ARG, "NULL plan");
+  if (order != KDE_BATCH_QUEUE_STAGES && order != KDE_BATCH_QUEUE_PROBLEMS)
+    return fail(KDE_ERR_INVALID_ARG, "order: KDE_BATCH_QUEUE_STAGES or KDE_BATCH_QUEUE_PROBLEMS");
+  bp->queue_order = order;
+  return kde::batch_work(bp);
+}
+
 extern "C" kde_status kde_batch_get_config(kde_batch_plan bp, int* pad_policy, int* radix_order,
                                            int64_t* P) {
   if (!bp) return fail(KDE_ERR_INVALID_ARG, "NULL plan");
   if (pad_policy) *pad_policy = bp->pad_policy;
-  if (radix_order) *radix_order = bp->radix_order;
+  if (radix_order) *radix_order = bp->radix_order | (bp->queue_order << 8);
   if (P)
     for (int i = 0; i < bp->count; ++i)
       for (int k = 0; k < 2; ++k) P[2 * i + k] = bp->plans[i]->info.P[k];

@@ -71,6 +71,7 @@ EXPORTS = [
     "kde_wait_probe", "kde_plan_check", "kde_outside_check", "kde_noalloc_scratch_bytes",
     "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes", "kde_batch_set_mode",
     "kde_batch_get_mode", "kde_batch_check", "kde_batch_set_wait", "kde_batch_get_config",
+    "kde_batch_set_queue_order",
 ]
 FEAT_DIM = 1088
 
@@ -134,6 +135,7 @@ def lib():
     L.kde_fft_eval_multi.argtypes = [vp, i64, ctypes.c_int, dp, vp, vp, vp, ctypes.c_size_t, vp]
     L.kde_fft_eval_multi_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.kde_batch_set_mode.argtypes = [vp, ctypes.c_int]
+    L.kde_batch_set_queue_order.argtypes = [vp, ctypes.c_int]
     L.kde_batch_get_mode.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.kde_batch_check.argtypes = [vp, vp]
     L.kde_batch_set_wait.argtypes = [vp, ctypes.c_uint32, ctypes.c_int]
@@ -166,7 +168,7 @@ def lib():
                  "kde_lscv_autocorr_cands", "kde_wait_probe", "kde_plan_check",
                  "kde_outside_check", "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes",
                  "kde_batch_set_mode", "kde_batch_get_mode", "kde_batch_check", "kde_batch_set_wait",
-                 "kde_batch_get_config"):
+                 "kde_batch_get_config", "kde_batch_set_queue_order"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -597,8 +599,12 @@ class BatchPlan:
         P = (ctypes.c_int64 * (2 * count))()
         _check(lib().kde_batch_get_config(self._h, ctypes.byref(pad), ctypes.byref(order), P))
         return ({0: "smallest", 1: "fewest_stages"}[pad.value],
-                {0: "largest_first", 1: "smallest_first"}[order.value],
-                [(P[2 * i], P[2 * i + 1]) for i in range(count)])
+                {0: "largest_first", 1: "smallest_first"}[order.value & 255],
+                [(P[2 * i], P[2 * i + 1]) for i in range(count)],
+                {0: "stages", 1: "problems"}[order.value >> 8])
+
+    def set_queue_order(self, order):
+        _check(lib().kde_batch_set_queue_order(self._h, {"stages": 0, "problems": 1}[order]))
 
     def set_wait(self, polls, withhold_stage=-1):
         _check(lib().kde_batch_set_wait(self._h, int(polls), int(withhold_stage)))

@@ -38,8 +38,9 @@ def small_batch(prec, count=9, seed=70):
     return out
 
 
-def run_batch(K, problems, prec, shape=None, mode="persistent"):
-    bp = K.BatchPlan([(w.M, w.lo, w.hi, w.H, w.n) for w in problems], precision=prec)
+def run_batch(K, problems, prec, shape=None, mode="persistent", bp=None):
+    if bp is None:
+        bp = K.BatchPlan([(w.M, w.lo, w.hi, w.H, w.n) for w in problems], precision=prec)
     bp.set_mode(mode)
     if shape:
         bp.set_shape(*shape)
@@ -55,11 +56,14 @@ def run_batch(K, problems, prec, shape=None, mode="persistent"):
     return out, bp, X
 
 
-@pytest.mark.parametrize("mode", ["persistent", "staged"])
+@pytest.mark.parametrize("mode", ["persistent", "persistent-stages", "staged"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_small_ragged_batch_every_node(K, prec, mode):
     problems = small_batch(prec)
-    dens, bp, _ = run_batch(K, problems, prec, mode=mode)
+    bp = K.BatchPlan([(w.M, w.lo, w.hi, w.H, w.n) for w in problems], precision=prec)
+    if mode == "persistent-stages":
+        bp.set_queue_order("stages")
+    dens, bp, _ = run_batch(K, problems, prec, mode=mode.split("-")[0], bp=bp)
     bp.check()
     for w, g in zip(problems, dens):
         f, _, _, _ = O.binned_estimate(w.X, w.H, w.lo, w.hi, w.M, tau=w.tau)
@@ -85,7 +89,8 @@ def test_ragged64_against_single_problem_path_and_tuner(K):
     ws = torch.empty(2 * bp.workspace_bytes, dtype=torch.uint8, device="cuda")
     ms = bp.tune(X, density, ws, reps=2)
     assert ms > 0 and bp.shape()[0] in (32, 64, 128)
-    pad, order, P = bp.config(len(problems))
+    pad, order, P, queue = bp.config(len(problems))
+    assert queue in ("stages", "problems")
     assert pad in ("smallest", "fewest_stages") and order in ("largest_first", "smallest_first")
     assert all(Pk >= m for (p2, w) in zip(P, problems) for Pk, m in zip(p2, w.M))
     assert bp.workspace_bytes <= ws.numel()
