@@ -438,6 +438,15 @@ kde_status kde_plan_check(kde_plan plan, kde_stream_t stream);
  * KDE_ERR_OUT_OF_RANGE if it is nonzero, KDE_OK if it is zero. */
 kde_status kde_outside_check(const int64_t* n_outside, kde_stream_t stream, int64_t* count);
 
+/* Debug builds (no counterpart in the paper): compiled with KDE_DEBUG the
+ * kernels check their indices (counts, tiles, spectra, output rows) and
+ * record the first failure in a device word instead of accessing out of
+ * range.  *enabled (host, may be NULL) receives 1 for such a build, 0 for a
+ * release build; code (host, may be NULL) receives 0 or the failure's code
+ * (which check), after synchronising the device, and the words are cleared.
+ * With code NULL the call touches no device. */
+kde_status kde_debug_status(int* enabled, int* code);
+
 /* Diagnostics. */
 const char* kde_status_string(kde_status s);
 const char* kde_last_error(void);

@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "kde_debug.cuh"
 #include "kde_internal.h"
 
 namespace {
@@ -58,6 +59,7 @@ struct BinAxis {
 template <typename T>
 struct BinParams {
   BinAxis<T> ax[KDE_MAX_D];
+  int64_t cells;   // prod(M): the counts array's length
 };
 
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(256) kde_bin_kernel(const T* __restrict__ X, i
 #pragma unroll
         for (int k = 0; k < D - 1; ++k)
           if ((c >> (D - 2 - k)) & 1) idx += p.ax[k].stride;
-        atomicAdd(counts + idx, wc);
+        if (KDE_DCHECK(idx >= 0 && idx < p.cells, KDE_DBG_BIN_DIRECT)) atomicAdd(counts + idx, wc);
       }
     }
   }
@@ -416,7 +418,7 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int n
                        const unsigned* __restrict__ block_base,
                        const unsigned* __restrict__ split_list,
                        const TiledMeta* __restrict__ meta, uint4* __restrict__ recs,
-                       unsigned long long* __restrict__ counts) {
+                       unsigned rec_cap, unsigned long long* __restrict__ counts) {
   extern __shared__ unsigned next[];   // [ntiles]: next slot of this block per tile
   {
     const int tile_cells = p.ax[0].lstride * p.ax[0].tile;
@@ -442,12 +444,14 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int n
       if (!sample_target<T, D>(x[u], p, g)) continue;
       uint4 rec;
       const int tile0 = record_for<T, D>(g, 0, p, rec);   // fills rec before it is stored
-      recs[atomicAdd(&next[tile0], 1u)] = rec;
+      const unsigned slot0 = atomicAdd(&next[tile0], 1u);
+      if (KDE_DCHECK(slot0 < rec_cap, KDE_DBG_BIN_SCATTER)) recs[slot0] = rec;
       if (g.spill) {
         for (int S = 1; S < (1 << D); ++S) {
           if (S & ~g.spill) continue;
           const int tile = record_for<T, D>(g, S, p, rec);
-          recs[atomicAdd(&next[tile], 1u)] = rec;
+          const unsigned slot = atomicAdd(&next[tile], 1u);
+          if (KDE_DCHECK(slot < rec_cap, KDE_DBG_BIN_SCATTER)) recs[slot] = rec;
         }
       }
     }
@@ -519,7 +523,7 @@ kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ i
           inside &= bit ? ok1[k] : ok0[k];
           j += bit * p.ax[k].lstride;
         }
-        if (inside) {
+        if (inside && KDE_DCHECK(j >= 0 && j < tile_cells, KDE_DBG_BIN_ACCUM)) {
           atomicAdd(&lo[j], (unsigned)(w[c] & 0xFFFFu));
           atomicAdd(&hi[j], (unsigned)(w[c] >> 16));
         }
@@ -535,7 +539,7 @@ kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ i
         in &= l < ext[k];
         idx += (int64_t)l * p.ax[k].stride;
       }
-      if (!in) continue;
+      if (!in || !KDE_DCHECK(idx >= 0 && idx < p.cells, KDE_DBG_BIN_ACCUM)) continue;
       const unsigned long long v = ((unsigned long long)hi[j] << 16) + lo[j];
       if (item.w) {
         if (v) atomicAdd(counts + idx, v);
@@ -607,6 +611,8 @@ BinParams<T> make_params(int d, const double* lo, const double* hi, const int64_
   BinParams<T> p{};
   int64_t stride = 1;
   int ts = 1, ls = 1;
+  p.cells = 1;
+  for (int k = 0; k < d; ++k) p.cells *= M[k];
   for (int k = d - 1; k >= 0; --k) {
     double s = (double)(M[k] - 1) / (hi[k] - lo[k]);
     p.ax[k].lo = (T)lo[k];
@@ -694,7 +700,7 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
     if ((e = allow_smem(fn, smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
     kde::LaunchScope ls("kde_bin_scatter_kernel", stream);
     fn<<<grid_s, kScatterThreads, smem, stream>>>(X, n, p, nt, cursor, block_base, split, meta,
-                                                   recs, counts);
+                                                   recs, (unsigned)t.max_records, counts);
     if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scatter_kernel");
   }
   {
@@ -783,3 +789,5 @@ extern "C" kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, cons
     return launch_tiled<float>((const float*)X, n, d, lo, hi, M, c, no, t, (char*)workspace, s);
   return launch_tiled<double>((const double*)X, n, d, lo, hi, M, c, no, t, (char*)workspace, s);
 }
+
+KDE_DEBUG_READER(bin)

@@ -31,6 +31,7 @@
 
 #include "fft_engine.cuh"
 #include "kde_internal.h"
+#include "kde_debug.cuh"
 #include "kgen.cuh"
 
 namespace kde {
@@ -95,6 +96,7 @@ __device__ __forceinline__ void store_r2c(const RowsParams<T>& p, const typename
     V zm = z[k == 0 ? 0 : P - k];
     V X = mk<V>(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
     V Y = mk<V>(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x));
+    if (!KDE_DCHECK(r0 < p.nrows, KDE_DBG_STOCKHAM)) continue;
     if (p.out_real) {
       p.out_real[r0 * p.Q + k] = X.x;
     } else {
@@ -3115,3 +3117,5 @@ extern "C" kde_status kde_batch_get_shape(kde_batch_plan bp, int* tpl_rows, int*
   if (tpl_cols) *tpl_cols = bp->tpl_cols;
   return KDE_OK;
 }
+
+KDE_DEBUG_READER(eval)

@@ -35,6 +35,7 @@
 
 #include "fx_dft.cuh"
 #include "fx_pairs.h"
+#include "kde_debug.cuh"
 #include "kde_internal.h"
 #include "kgen.cuh"
 
@@ -234,6 +235,7 @@ __device__ __forceinline__ void rows_split_store(const RowsArgs& a, const float2
       const int qm = (int)__umulhi((unsigned)km, a.ln.magic1);
       const float2 zk = z[(k - q * N1) * a.SK + q];
       const float2 zm = z[(km - qm * N1) * a.SK + qm];
+      if (!KDE_DCHECK(k < a.Q && km < P, KDE_DBG_ROWS_STORE)) continue;
       o0[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
       if (two) o0[a.Q + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
     }
@@ -334,7 +336,7 @@ __device__ __forceinline__ void rows_a_inv(const RowsArgs& a, const float2* sm) 
 #pragma unroll
   for (int n1 = 0; n1 < N1; ++n1) {
     const int pos = n2 + N2 * n1;
-    if (pos < a.Mout) {
+    if (pos < a.Mout && KDE_DCHECK(r0 < a.nrows, KDE_DBG_ROWS_STORE)) {
       o0[pos] = x[n1].x;
       if (two) o0[a.Mout + pos] = x[n1].y;
     }
@@ -435,7 +437,9 @@ __device__ __forceinline__ void cols_a_fwd(const ColsArgs& a, float2* sm) {
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) {
       const int j = col_source(n2 + N2 * n1, a.ln.P, a.Lw, a.Nin);
-      x[n1] = (j >= 0 && v) ? __ldg(in + (int64_t)j * a.S + s) : make_float2(0.f, 0.f);
+      x[n1] = (j >= 0 && v && KDE_DCHECK(j < a.Nin, KDE_DBG_COLS_LOAD))
+                  ? __ldg(in + (int64_t)j * a.S + s)
+                  : make_float2(0.f, 0.f);
     }
   }
   a_fwd_store<N1>(x, n2, a.tw, sm + b + n2 * a.B, a.SK);
@@ -457,7 +461,8 @@ __device__ __forceinline__ void cols_b_fwd(const ColsArgs& a, float2* sm) {
     if (s >= a.S) return;
     float2* out = a.out + s;
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) out[(int64_t)(k1 + N1 * k2) * a.S] = y[k2];
+    for (int k2 = 0; k2 < N2; ++k2)
+      if (KDE_DCHECK(k1 + N1 * k2 < a.ln.P, KDE_DBG_COLS_STORE)) out[(int64_t)(k1 + N1 * k2) * a.S] = y[k2];
   } else if constexpr (MODE == COL_FWD_REAL) {
     const int64_t s = col_first<MODE>(a) + 2 * b;
     if (s >= a.S) return;
@@ -517,7 +522,7 @@ __device__ __forceinline__ void cols_a_inv(const ColsArgs& a, const float2* sm) 
 #pragma unroll
   for (int n1 = 0; n1 < N1; ++n1) {
     const int pos = n2 + N2 * n1;
-    if (pos < a.Nout) out[(int64_t)pos * a.S] = x[n1];
+    if (pos < a.Nout && KDE_DCHECK(s < a.S, KDE_DBG_COLS_STORE)) out[(int64_t)pos * a.S] = x[n1];
   }
 }
 

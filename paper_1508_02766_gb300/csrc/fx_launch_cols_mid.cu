@@ -21,3 +21,5 @@ cudaError_t launch_cols_mid(const Launch& l, const ColsArgs& a) {
 
 }  // namespace fx
 }  // namespace kde
+
+KDE_DEBUG_READER(fx_cols_mid)

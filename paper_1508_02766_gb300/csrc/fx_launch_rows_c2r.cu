@@ -21,3 +21,5 @@ cudaError_t launch_rows_c2r(const Launch& l, const RowsArgs& a) {
 
 }  // namespace fx
 }  // namespace kde
+
+KDE_DEBUG_READER(fx_rows_c2r)

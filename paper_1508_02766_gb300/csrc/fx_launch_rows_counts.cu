@@ -21,3 +21,5 @@ cudaError_t launch_rows_counts(const Launch& l, const RowsArgs& a, const long lo
 
 }  // namespace fx
 }  // namespace kde
+
+KDE_DEBUG_READER(fx_rows_counts)

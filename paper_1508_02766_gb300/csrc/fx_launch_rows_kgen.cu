@@ -21,3 +21,5 @@ cudaError_t launch_rows_kgen(const Launch& l, const RowsArgs& a, const KGen<floa
 
 }  // namespace fx
 }  // namespace kde
+
+KDE_DEBUG_READER(fx_rows_kgen)

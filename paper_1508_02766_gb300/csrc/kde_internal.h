@@ -65,6 +65,18 @@ kde_status fx_eval_batch2(kde_plan_s* plan, const float2* A, int nh, const KGen<
                           const int* L0, int Lmax0, float2* t1, float* Kb, float2* Sb,
                           float* density, cudaStream_t st);
 
+// Readers of the per-translation-unit check words of a debug build (0 in a
+// release build; -1 if the word could not be read).
+int debug_read_bin();
+int debug_read_eval();
+int debug_read_fx_rows_counts();
+int debug_read_fx_rows_kgen();
+int debug_read_fx_rows_c2r();
+int debug_read_fx_cols_fwd();
+int debug_read_fx_cols_real();
+int debug_read_fx_cols_mid();
+int debug_read_fx_cols_inv();
+
 // Launch bookkeeping: counts launches and, when profiling is on, records a
 // pair of events around each launch on its stream.
 struct LaunchScope {

@@ -14,7 +14,10 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fx_pairs.h"
+#include "kde_debug.cuh"
 #include "kde_internal.h"
 
 namespace kde {
@@ -55,7 +58,11 @@ static cudaEvent_t take_event() {
   return e;
 }
 
+// Every launch is also an NVTX range named after its kernel (host side,
+// around the launch call), visible to Nsight tools when one is attached;
+// without a tool the calls return at once.
 LaunchScope::LaunchScope(const char* name, cudaStream_t s) : slot(-1), stream(s) {
+  nvtxRangePushA(name);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return;
@@ -67,6 +74,7 @@ LaunchScope::LaunchScope(const char* name, cudaStream_t s) : slot(-1), stream(s)
 }
 
 LaunchScope::~LaunchScope() {
+  nvtxRangePop();
   if (slot < 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   cudaEventRecord(g_prof[slot].stop, stream);
@@ -520,6 +528,24 @@ kde_status kde_plan_destroy(kde_plan plan) {
   if (plan->dft_tab) cudaFree(plan->dft_tab);
   delete plan;
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, "cudaFree(twiddles)");
+}
+
+kde_status kde_debug_status(int* enabled, int* code) {
+  if (enabled) *enabled = KDE_DEBUG_ENABLED;
+  if (!code) return KDE_OK;
+  *code = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "kde_debug_status");
+  int (*readers[])() = {kde::debug_read_bin, kde::debug_read_eval, kde::debug_read_fx_rows_counts,
+                        kde::debug_read_fx_rows_kgen, kde::debug_read_fx_rows_c2r,
+                        kde::debug_read_fx_cols_fwd, kde::debug_read_fx_cols_real,
+                        kde::debug_read_fx_cols_mid, kde::debug_read_fx_cols_inv};
+  for (auto rd : readers) {
+    const int v = rd();
+    if (v < 0) return fail(KDE_ERR_CUDA, "kde_debug_status: reading a check word failed");
+    if (v && !*code) *code = v;
+  }
+  return KDE_OK;
 }
 
 const char* kde_status_string(kde_status s) {

@@ -71,7 +71,7 @@ EXPORTS = [
     "kde_wait_probe", "kde_plan_check", "kde_outside_check", "kde_noalloc_scratch_bytes",
     "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes", "kde_batch_set_mode",
     "kde_batch_get_mode", "kde_batch_check", "kde_batch_set_wait", "kde_batch_get_config",
-    "kde_batch_set_queue_order",
+    "kde_batch_set_queue_order", "kde_debug_status",
 ]
 FEAT_DIM = 1088
 
@@ -134,6 +134,7 @@ def lib():
                                 ctypes.c_int, vp, ctypes.c_int, vp, vp]
     L.kde_fft_eval_multi.argtypes = [vp, i64, ctypes.c_int, dp, vp, vp, vp, ctypes.c_size_t, vp]
     L.kde_fft_eval_multi_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.kde_debug_status.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.kde_batch_set_mode.argtypes = [vp, ctypes.c_int]
     L.kde_batch_set_queue_order.argtypes = [vp, ctypes.c_int]
     L.kde_batch_get_mode.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
@@ -168,7 +169,7 @@ def lib():
                  "kde_lscv_autocorr_cands", "kde_wait_probe", "kde_plan_check",
                  "kde_outside_check", "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes",
                  "kde_batch_set_mode", "kde_batch_get_mode", "kde_batch_check", "kde_batch_set_wait",
-                 "kde_batch_get_config", "kde_batch_set_queue_order"):
+                 "kde_batch_get_config", "kde_batch_set_queue_order", "kde_debug_status"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
