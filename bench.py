@@ -56,8 +56,10 @@ def parse(argv=None):
     ap.add_argument("--lscv", default="autocorr", choices=["autocorr", "spectrum"],
                     help="lscv2d_512_f32: pair sums from the counts' autocorrelation, or from "
                          "the count spectrum against per-candidate kernel spectra")
-    ap.add_argument("--train-sets", type=int, default=20_000,
+    ap.add_argument("--train-sets", type=int, default=100_000,
                     help="learned2d_256: training datasets labelled by the plain search")
+    ap.add_argument("--eval-sets", type=int, default=10_000,
+                    help="learned2d_256: held-out datasets both methods select for")
     ap.add_argument("--cpu-oracle", default=None, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -1165,38 +1167,72 @@ LEARN_METRIC = ("bandwidth selections/s of the learned proposal (scored and refi
                 "vs the plain batched LSCV search, same grid and accuracy")
 
 
+def _learn_chunk(job):
+    """Worker of the dataset pool: one chunk of the learned workload's
+    datasets (no CUDA in the workers)."""
+    from paper_1508_02766_gb300 import workloads as W
+    seed, chunk, count, n = job
+    return W.mixture_dataset_chunk(seed, chunk, count, n)
+
+
+def _learn_stream(pool, seed, total, chunk, n):
+    """The datasets of one seed in chunks (count x n x 2), drawn by the pool
+    in order."""
+    jobs = [(seed, c, min(chunk, total - c * chunk), n) for c in range((total + chunk - 1) // chunk)]
+    return pool.imap(_learn_chunk, jobs)
+
+
 def learned_main(args):
+    import multiprocessing as mp
+    # the dataset pool starts before any CUDA call (spawned workers)
+    workers = max(1, min(16, (os.cpu_count() or 1) - 1))
+    pool = mp.get_context("spawn").Pool(workers)
     import torch
     from paper_1508_02766_gb300 import build as B
     from paper_1508_02766_gb300 import kde
     from paper_1508_02766_gb300 import learned as Lm
-    from paper_1508_02766_gb300 import workloads as W
     if not os.path.exists(B.LIB):
         B.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    n = 10_000
-    train_sets = W.mixture_datasets(31, args.train_sets, n=n)
-    test_sets = W.mixture_datasets(32, args.warmup + args.steps, n=n)
+    n, chunk, Bsel = 10_000, 1024, 256
+    n_train, n_eval = args.train_sets, args.eval_sets
     sc = Lm.LscvScorer(n)
-    # labels: the plain search on every training dataset
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    lab = Lm.label_datasets(sc, train_sets)
-    torch.cuda.synchronize()
-    t_label = time.perf_counter() - t0
+    # labels: the plain search (every candidate) on every training dataset,
+    # in batches of Bsel datasets per preparation and search call
+    feats = np.empty((n_train, kde.FEAT_DIM), dtype=np.float32)
+    theta = np.empty((n_train, 3))
+    t_label, t_gen, i0 = 0.0, 0.0, 0
+    tg = time.perf_counter()
+    for Xc in _learn_stream(pool, 31, n_train, chunk, n):
+        t_gen += time.perf_counter() - tg
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b0 in range(0, Xc.shape[0], Bsel):
+            part = Xc[b0:b0 + Bsel]
+            off = np.arange(part.shape[0] + 1, dtype=np.int64) * n
+            Xd = torch.from_numpy(part.reshape(-1, 2)).to(dev)
+            F, Rs, ns = sc.prepare_batch(Xd, off)
+            th, _ = sc.search_batch(Rs, ns)
+            k = part.shape[0]
+            theta[i0:i0 + k] = th
+            feats[i0:i0 + k] = F.cpu().numpy()
+            i0 += k
+        torch.cuda.synchronize()
+        t_label += time.perf_counter() - t0
+        tg = time.perf_counter()
     # training, with the library's per-kernel events
     mlp = kde.MLP(in_dim=kde.FEAT_DIM, hidden=256, out_dim=3, max_batch=256, seed=0)
     epochs, batch = 40, 256
     kde.profile_enable(True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hist = Lm.train(mlp, lab.feats, lab.theta, epochs=epochs, batch=batch, lr=1e-3)
+    hist = Lm.train(mlp, feats, theta, epochs=epochs, batch=batch, lr=1e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     prof_train = kde.profile_read()
     kde.profile_enable(False)
-    steps_train = epochs * (len(train_sets) // batch)
+    steps_train = epochs * (n_train // batch)
     Bp, hid, din = 256, 256, kde.FEAT_DIM
     gemm_flops_step = 2.0 * Bp * (din * hid + hid * hid + hid * 16) + 2.0 * (
         hid * 16 * Bp + Bp * hid * 64 + hid * hid * Bp + Bp * hid * hid + hid * din * Bp)
@@ -1207,45 +1243,77 @@ def learned_main(args):
         with open(pp) as fh:
             peak_bf16 = float(json.load(fh).get("bf16_tflops", peak_bf16))
     gemm_tf = gemm_flops_step * steps_train / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
+    # held-out datasets (resident on the host, pinned: each batch is one copy)
+    evals = np.concatenate(list(_learn_stream(pool, 32, n_eval + Bsel, chunk, n)))
+    pool.close()
+    pool.join()
+    pinned = torch.from_numpy(evals.reshape(-1, 2)).pin_memory()
+    warm, evals_t = pinned[:Bsel * n], pinned[Bsel * n:]
+    K = n_eval
 
-    def upload(X):
-        return torch.from_numpy(X).to(dev)
+    todo = [(b0, min(Bsel, K - b0)) for b0 in range(0, K, Bsel)]
+    bufs = [torch.empty(Bsel * n, 2, dtype=torch.float32, device=dev) for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
 
-    for X in test_sets[:args.warmup]:
-        Xd = upload(X)
-        sc.prepare(Xd)
-        sc.search()
-    Lm.select_batch(sc, mlp, [upload(X) for X in test_sets[:args.warmup]])
-    evals = test_sets[args.warmup:]
-    K = len(evals)
+    def batches():
+        """Each batch's samples as a device tensor: batch i + 1 is copied on a
+        copy stream while batch i is processed (two buffers; a buffer is
+        refilled only after the work that read it)."""
+        ready = [torch.cuda.Event() for _ in range(2)]
+        freed = [torch.cuda.Event() for _ in range(2)]
+
+        def upload(i):
+            b0, k = todo[i]
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(freed[i % 2])
+                bufs[i % 2][:k * n].copy_(evals_t[b0 * n:(b0 + k) * n], non_blocking=True)
+                ready[i % 2].record(copy_stream)
+
+        upload(0)
+        for i, (b0, k) in enumerate(todo):
+            if i + 1 < len(todo):
+                upload(i + 1)
+            torch.cuda.current_stream().wait_event(ready[i % 2])
+            yield b0, k, bufs[i % 2][:k * n]
+            freed[i % 2].record()
+
+    off_full = np.arange(Bsel + 1, dtype=np.int64) * n
+    # warm-up of both methods
+    Xd = warm.to(dev, non_blocking=True)
+    F, Rs, ns = sc.prepare_batch(Xd, off_full)
+    sc.search_batch(Rs, ns)
+    Lm.select_batch(sc, mlp, Xd, offsets=off_full)
+    torch.cuda.synchronize()
     sampler = ClockSampler(0)
     sampler.start()
     time.sleep(0.3)
-    # plain method: standardise, bin, count spectrum, LSCV of every candidate, argmin
-    torch.cuda.synchronize()
+    # plain method: batched preparation, every candidate scored, argmin per dataset
+    kde.profile_enable(True)
     l0 = kde.launch_count()
     t0 = time.perf_counter()
-    best = []
-    for X in evals:
-        sc.prepare(upload(X))
-        best.append(sc.search()[1])
+    best = np.empty(K)
+    for b0, k, Xd in batches():
+        F, Rs, ns = sc.prepare_batch(Xd, off_full[:k + 1])
+        best[b0:b0 + k] = sc.search_batch(Rs, ns)[1]
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
     launches_plain = kde.launch_count() - l0
-    # learned method, batches of 256 datasets: features and autocorrelations,
-    # one network pass per batch, 28 scored candidates each, fallback rule
+    prof_plain = kde.profile_read()
+    kde.profile_enable(False)
+    # learned method, batches of Bsel datasets: batched preparation, one
+    # network pass per batch, 28 scored candidates each, fallback rule
     kde.profile_enable(True)
     scored = []
     torch.cuda.synchronize()
     l0 = kde.launch_count()
     t0 = time.perf_counter()
-    got, fell, ncand = [], 0, 0
-    for b0 in range(0, K, 256):
-        for th, v, k, fb in Lm.select_batch(sc, mlp, [upload(X) for X in evals[b0:b0 + 256]],
-                                            scored=scored):
-            got.append(v)
+    got, fell, ncand = np.empty(K), 0, 0
+    for b0, k, Xd in batches():
+        res = Lm.select_batch(sc, mlp, Xd, scored=scored, offsets=off_full[:k + 1])
+        for j, (th, v, c, fb) in enumerate(res):
+            got[b0 + j] = v
             fell += int(fb)
-            ncand += k
+            ncand += c
     torch.cuda.synchronize()
     t_learn = time.perf_counter() - t0
     launches_learn = kde.launch_count() - l0
@@ -1253,27 +1321,42 @@ def learned_main(args):
     kde.profile_enable(False)
     clocks = sampler.stop()
     # the method without the network: the normal-reference bandwidth refined
-    # over the same neighbourhood
+    # over the same neighbourhood (first 512 held-out datasets)
     reg_ref = []
-    for X, b in zip(evals[:200], best[:200]):
-        sc.prepare(upload(X))
-        ref = Lm.normal_reference_theta(X.shape[0])
-        s = sc.scores(np.stack([Lm.theta_to_H(t) for t in Lm.neighbourhood(ref)])).cpu().numpy()
-        reg_ref.append((s.min() - b) / abs(b))
-    best, got = np.array(best), np.array(got)
+    for i in range(min(512, K)):
+        sc.prepare(evals_t[i * n:(i + 1) * n].to(dev))
+        ref = Lm.normal_reference_theta(n)
+        s_ref = sc.scores(np.stack([Lm.theta_to_H(t) for t in Lm.neighbourhood(ref)])).cpu().numpy()
+        reg_ref.append((s_ref.min() - best[i]) / abs(best[i]))
     rel_regret = (got - best) / np.abs(best)
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
                    "share": v[0] / max(1e-12, sum(x[0] for x in prof.values()))}
                for k, v in prof.items()}
     # roofline of the selection loop's dominant kernel
     info = sc.plan.info
-    P0, P1, Q = info.P[0], info.P[1], info.Q
-    Ls = [kde.kde_plan_info_compute(sc.M, sc.lo, sc.hi, A, precision="f32").L
-          for h in scored for A in (h, 2.0 * h)]
-    flops = {"kde_lscv_ac_kernel": sum(ac_flops(L) for L in Ls),
+    # supports of every scored H and 2H (Eq. 15, corrected range), vectorised
+    Hs = np.asarray(scored, dtype=np.float64).reshape(-1, 2, 2)
+    Hs = np.concatenate([Hs, 2.0 * Hs])
+    lam = 0.5 * (Hs[:, 0, 0] + Hs[:, 1, 1]) + np.sqrt(
+        0.25 * (Hs[:, 0, 0] - Hs[:, 1, 1]) ** 2 + Hs[:, 0, 1] ** 2)
+    Mg = np.array(sc.M, dtype=np.float64)
+    dlt = (np.array(sc.hi) - np.array(sc.lo)) / (Mg - 1.0)
+    Lv = np.minimum(Mg - 1.0, np.ceil(sc.tau * np.sqrt(lam)[:, None] / dlt[None, :]))
+    ac_total = float(np.sum(8.0 * (Lv[:, 0] + 1.0) * (2.0 * Lv[:, 1] + 1.0)))
+    flops = {"kde_lscv_ac_kernel": ac_total, "kde_lscv_theta_sums_kernel": ac_total,
              "kde_gemm_tc_kernel": K * 2.0 * 128 * (din * hid + hid * hid + hid * 16)}
     dom = max(prof, key=lambda k: prof[k][0])
     sm_max = clocks.get("sm_max_mhz") or 2070.0
+    cells = Lm.GRID_M * Lm.GRID_M
+    P0, P1, Q = info.P[0], info.P[1], info.Q
+    # per-launch algorithmic bytes of the batched preparation (Bsel datasets)
+    nbytes = {"kde_standardize2_sets_kernel": Bsel * 16.0 * n,
+              "kde_bin_sets_kernel": Bsel * (8.0 * n + 8.0 * cells),
+              "kde_features2_sets_kernel": Bsel * (8.0 * cells + 4.0 * kde.FEAT_DIM),
+              "kde_rows_r2c_counts_kernel": Bsel * (8.0 * cells + Lm.GRID_M * Q * 8.0),
+              "kde_cols_auto_kernel": Bsel * (Lm.GRID_M * Q * 8.0 + P0 * Q * 8.0),
+              "kde_rows_c2r_kernel": Bsel * (P0 * Q * 8.0 + P0 * P1 * 4.0)}
+    hbm, hbm_kind = peaks()
     if dom == "kde_gemm_tc_kernel":
         ach = flops[dom] / (prof[dom][0] * 1e-3) / 1e12
         roofline = {"bound": "tensor", "kernel": dom, "achieved": ach, "peak": peak_bf16,
@@ -1287,44 +1370,40 @@ def learned_main(args):
                     "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x SM max clock",
                     "flops_per_launch": flops[dom] / prof[dom][1]}
+    elif dom in nbytes:
+        ach = nbytes[dom] / (prof[dom][0] / prof[dom][1] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "peak_source": hbm_kind, "traffic": None,
+                    "algorithmic_bytes": nbytes[dom]}
     else:
-        # per-dataset passes: algorithmic bytes (samples read and written,
-        # counts read or written once)
-        cells = Lm.GRID_M * Lm.GRID_M
-        nbytes = {"kde_standardize2_kernel": 16.0 * n, "kde_bin_kernel": 8.0 * n + 8.0 * cells,
-                  "kde_features2_kernel": 8.0 * cells + 4.0 * kde.FEAT_DIM}
-        hbm, hbm_kind = peaks()
-        if dom in nbytes:
-            ach = nbytes[dom] / (prof[dom][0] / prof[dom][1] * 1e-3) / 1e9
-            roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                        "frac": ach / hbm, "peak_source": hbm_kind, "traffic": None,
-                        "algorithmic_bytes": nbytes[dom]}
-        else:
-            roofline = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None,
-                        "unit": "TFLOP/s", "frac": None, "traffic": None}
+        roofline = {"bound": None, "kernel": dom, "achieved": None, "peak": None,
+                    "unit": None, "frac": None, "traffic": None}
     line = {"metric": LEARN_METRIC, "value": K / t_learn, "unit": "datasets/s",
-            "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_learn / K,
+            "n_gpus": 1, "steps": K, "warmup": Bsel, "ms_per_step": 1e3 * t_learn / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
             "data": "synthetic",
             "config": {"workload": "learned2d_256", "grid": [256, 256], "n": n,
-                       "train_datasets": len(train_sets), "test_datasets": K,
+                       "train_datasets": n_train, "test_datasets": K,
                        "candidates_plain": int(len(sc.cand)), "P": list(info.P),
                        "mlp": f"{kde.FEAT_DIM}-256-256-3 ReLU, BF16 operands, FP32 accumulation",
-                       "timing": "wall clock around the loop with device synchronisation, "
-                                 "host-to-device copy of each dataset included",
-                       "learned_batch": 256},
+                       "timing": "wall clock around the loop with device synchronisation; each "
+                                 "batch's samples copied from pinned host memory inside it, on a "
+                                 "copy stream beside the previous batch's work",
+                       "batch": Bsel, "dataset_workers": workers},
             "plain_search": {"value": K / t_plain, "unit": "datasets/s",
                              "ms_per_dataset": 1e3 * t_plain / K,
-                             "gpu_launches": launches_plain},
+                             "gpu_launches": launches_plain,
+                             "kernel_ms_per_dataset": {k: v[0] / K for k, v in prof_plain.items()}},
             "speedup_vs_plain": t_plain / t_learn,
             "quality": {"mean_rel_regret": float(rel_regret.mean()),
                         "p95_rel_regret": float(np.percentile(rel_regret, 95)),
                         "fraction_exact_best": float(np.mean(rel_regret <= 1e-12)),
                         "fallbacks": fell, "mean_candidates": ncand / K,
                         "normal_reference_refined_mean_rel_regret": float(np.mean(reg_ref))},
-            "labels": {"datasets_per_s": len(train_sets) / t_label},
+            "labels": {"datasets_per_s": n_train / t_label, "seconds": t_label,
+                       "generation_wait_s": t_gen},
             "training": {"samples_per_s": steps_train * batch / t_train, "epochs": epochs,
-                         "loss_first_last": [hist[0], hist[-1]],
+                         "seconds": t_train, "loss_first_last": [hist[0], hist[-1]],
                          "gemm_tflops": gemm_tf, "gemm_frac_of_bf16_peak": gemm_tf / peak_bf16},
             "roofline": roofline, "kernels": kernels, "gpu_launches": launches_learn,
             "clocks": clocks}

@@ -318,6 +318,43 @@ kde_status kde_lscv_cands_destroy(kde_lscv_cands cands);
 kde_status kde_lscv_autocorr_cands(kde_lscv_cands cands, int64_t n, const void* R,
                                    double* pair_sums, double* lscv, void* workspace,
                                    size_t workspace_bytes, kde_stream_t stream);
+/* The same candidate set scored against nsets autocorrelations at once
+ * (R: nsets x P_0 x P_1 in the plan's precision, device; n: nsets sample
+ * counts, host, each >= 2): lscv[s nH + i] (and pair_sums[2 (s nH + i)],
+ * [2 (s nH + i) + 1] when not NULL; device) equal what
+ * kde_lscv_autocorr_cands gives for dataset s alone.  Two launches per 1024
+ * candidates whatever nsets (<= 65535).  workspace: at least
+ * kde_lscv_autocorr_cands_batch_workspace_bytes(cands, nsets), 256-byte
+ * aligned; n is copied from pageable memory, so the call is not for
+ * CUDA-graph capture. */
+kde_status kde_lscv_autocorr_cands_batch(kde_lscv_cands cands, int nsets, const int64_t* n,
+                                         const void* R, double* pair_sums, double* lscv,
+                                         void* workspace, size_t workspace_bytes,
+                                         kde_stream_t stream);
+kde_status kde_lscv_autocorr_cands_batch_workspace_bytes(kde_lscv_cands cands, int nsets,
+                                                         size_t* bytes);
+/* Candidates built on the device from per-dataset parameters (the learned
+ * proposal's refinement, so that no bandwidth crosses to the host): theta =
+ * (a, beta, c) stands for H = R R^T with R = [[e^a, 0], [beta e^c, e^c]]
+ * (standardised coordinates).  For dataset s < nsets, candidate j < J is
+ * clip(theta_s, box) + offsets[j] (theta: device, nsets x 3 FP32, e.g. a
+ * network's output; box: host, lo[3] then hi[3]; offsets: host, J x 3) and
+ * candidate J is ref[s] (host, nsets x 3).  Each candidate's H and 2H get the
+ * support of Eq. 15 and the completed-square constants in FP64 on the device
+ * (the host path's steps), then the LSCV of kde_lscv_autocorr against R
+ * (device, nsets x P_0 x P_1 FP32) with n[s] samples (host).  A candidate
+ * whose support does not fit the plan's padding scores +inf (no error).
+ * Outputs (device): lscv[s (J + 1) + j] when not NULL; out[3 s ..] = {index
+ * of the smallest LSCV among j < J (the first on ties; J if none fits), that
+ * LSCV, the reference candidate's LSCV}.  KDE_F32 2-D plans.  workspace: at
+ * least kde_lscv_theta_select_workspace_bytes(plan, nsets, J), 256-byte
+ * aligned; the host inputs are copied from pageable memory, so the call is
+ * not for CUDA-graph capture.  (Not in the paper.) */
+kde_status kde_lscv_theta_select(kde_plan plan, int nsets, const int64_t* n, const float* theta,
+                                 const double* box, int J, const double* offsets,
+                                 const double* ref, const void* R, double* lscv, double* out,
+                                 void* workspace, size_t workspace_bytes, kde_stream_t stream);
+kde_status kde_lscv_theta_select_workspace_bytes(kde_plan plan, int nsets, int J, size_t* bytes);
 
 /* Ragged batches of independent 2-D problems (each with its own samples,
  * grid and bandwidth; Sec. 2 for each).  Two modes:
@@ -492,6 +529,27 @@ kde_status kde_standardize2(const float* X, int64_t n, float* Z, double* moments
  * skewnesses, excess kurtosis, log10(n)/4, 1, then zeros. */
 kde_status kde_features2(const int64_t* counts, int M, int64_t n, const double* moments,
                          float* feat, kde_stream_t stream);
+/* The whole per-dataset preparation of the learned and plain selections for
+ * nsets datasets in one call (<= 65535; kde_standardize2, kde_bin of the
+ * standardised samples on the plan's grid, kde_features2 and
+ * kde_autocorrelation of each, with the same arithmetic, in batched
+ * launches).  plan: d = 2, an M x M grid with M a multiple of 32.
+ * X: concatenated samples (FP32, device), dataset s in rows
+ * [offsets[s], offsets[s+1]) (offsets: host, nsets + 1 entries, offsets[0]
+ * = 0, every dataset at least 2 samples).  Outputs (device): counts
+ * nsets x M x M (int64, units of 2^-32; samples outside the grid are
+ * dropped and still count in n), moments nsets x 8 (as kde_standardize2),
+ * feat nsets x KDE_FEAT_DIM, R nsets x P_0 x P_1 (the plan's precision, as
+ * kde_autocorrelation).  workspace: at least
+ * kde_prepare2_batch_workspace_bytes(plan, nsets, offsets[nsets]), 256-byte
+ * aligned (it holds the standardised samples and the transforms'
+ * intermediates).  offsets are copied from pageable memory, so the call is
+ * not for CUDA-graph capture. */
+kde_status kde_prepare2_batch(kde_plan plan, int nsets, const float* X, const int64_t* offsets,
+                              int64_t* counts, double* moments, float* feat, void* R,
+                              void* workspace, size_t workspace_bytes, kde_stream_t stream);
+kde_status kde_prepare2_batch_workspace_bytes(kde_plan plan, int nsets, int64_t n_total,
+                                              size_t* bytes);
 
 /* Three-layer perceptron y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with
  * BF16 operands and FP32 accumulation on the tensor cores (tcgen05),

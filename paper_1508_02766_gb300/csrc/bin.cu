@@ -133,17 +133,19 @@ __device__ __forceinline__ void corner_weights(const unsigned* q, unsigned long 
 // each warp instruction's lane pairs coalesce into one sector request where
 // one lane per sample would issue two: the scattered-sector rate of the L2
 // is what bounds this kernel.
+// Block blk of nblk blocks on samples [0, n) of X into counts.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) kde_bin_kernel(const T* __restrict__ X, int64_t n,
-                                                      BinParams<T> p,
-                                                      unsigned long long* __restrict__ counts,
-                                                      unsigned long long* __restrict__ n_out) {
+__device__ __forceinline__ void bin_direct_body(const T* __restrict__ X, int64_t n,
+                                                const BinParams<T>& p,
+                                                unsigned long long* __restrict__ counts,
+                                                unsigned long long* __restrict__ n_out, int blk,
+                                                int nblk) {
   constexpr int H = 1 << (D - 1);
   constexpr int U = 8;  // samples whose coordinates are loaded before any is added
   const int par = threadIdx.x & 1;
   unsigned long long outside = 0;
-  const int64_t step = ((int64_t)gridDim.x * blockDim.x) >> 1;
-  for (int64_t s0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 1; s0 < n; s0 += U * step) {
+  const int64_t step = ((int64_t)nblk * blockDim.x) >> 1;
+  for (int64_t s0 = (blk * (int64_t)blockDim.x + threadIdx.x) >> 1; s0 < n; s0 += U * step) {
     T xs[U][D];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -191,6 +193,26 @@ __global__ void __launch_bounds__(256) kde_bin_kernel(const T* __restrict__ X, i
     for (int off = 16; off > 0; off >>= 1) outside += __shfl_down_sync(0xffffffffu, outside, off);
     if ((threadIdx.x & 31) == 0 && outside) atomicAdd(n_out, outside);
   }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) kde_bin_kernel(const T* __restrict__ X, int64_t n,
+                                                      BinParams<T> p,
+                                                      unsigned long long* __restrict__ counts,
+                                                      unsigned long long* __restrict__ n_out) {
+  bin_direct_body<T, D>(X, n, p, counts, n_out, blockIdx.x, gridDim.x);
+}
+
+// Many datasets on one grid: blockIdx.y is the dataset, whose samples are
+// rows [off[y], off[y + 1]) of X and whose counts start at y * cells.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) kde_bin_sets_kernel(const T* __restrict__ X,
+                                                           const int64_t* __restrict__ off,
+                                                           BinParams<T> p,
+                                                           unsigned long long* __restrict__ counts) {
+  const int64_t a = off[blockIdx.y], b = off[blockIdx.y + 1];
+  bin_direct_body<T, D>(X + a * D, b - a, p, counts + (int64_t)blockIdx.y * p.cells, nullptr,
+                        blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -657,6 +679,29 @@ kde_status launch_direct(const T* X, int64_t n, int d, const double* lo, const d
   return e == cudaSuccess ? KDE_OK : kde::cuda_fail(e, "kde_bin_kernel launch");
 }
 
+// kde_bin_sets_kernel for nsets datasets of at most n_max samples each
+// (offsets on the device): counts zeroed, then about 8 blocks per SM in all.
+template <typename T>
+kde_status launch_sets(const T* X, const int64_t* off_dev, int nsets, int64_t n_max, int d,
+                       const double* lo, const double* hi, const int64_t* M,
+                       unsigned long long* counts, cudaStream_t stream) {
+  BinParams<T> p = make_params<T>(d, lo, hi, M, nullptr);
+  cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)nsets * p.cells * sizeof(int64_t), stream);
+  if (e != cudaSuccess) return kde::cuda_fail(e, "cudaMemsetAsync(counts)");
+  if (n_max == 0 || nsets == 0) return KDE_OK;
+  const int64_t want = (2 * n_max + 255) / 256;
+  const int64_t cap = std::max<int64_t>(1, (int64_t)num_sms() * 8 / nsets);
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min(want, cap)), (unsigned)nsets);
+  kde::LaunchScope ls("kde_bin_sets_kernel", stream);
+  switch (d) {
+    case 1: kde_bin_sets_kernel<T, 1><<<grid, 256, 0, stream>>>(X, off_dev, p, counts); break;
+    case 2: kde_bin_sets_kernel<T, 2><<<grid, 256, 0, stream>>>(X, off_dev, p, counts); break;
+    default: kde_bin_sets_kernel<T, 3><<<grid, 256, 0, stream>>>(X, off_dev, p, counts); break;
+  }
+  e = cudaGetLastError();
+  return e == cudaSuccess ? KDE_OK : kde::cuda_fail(e, "kde_bin_sets_kernel launch");
+}
+
 template <typename F>
 cudaError_t allow_smem(F* fn, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
@@ -745,6 +790,15 @@ kde_status check_bin_args(int d, int x_dtype, int64_t n, const void* X, const do
 }
 
 }  // namespace
+
+namespace kde {
+kde_status bin_sets_f32(const float* X, const int64_t* off_dev, int nsets, int64_t n_max, int d,
+                        const double* lo, const double* hi, const int64_t* M, int64_t* counts,
+                        cudaStream_t st) {
+  return launch_sets<float>(X, off_dev, nsets, n_max, d, lo, hi, M,
+                            reinterpret_cast<unsigned long long*>(counts), st);
+}
+}  // namespace kde
 
 extern "C" kde_status kde_bin_workspace_bytes(int64_t n, int d, const int64_t* M, size_t* bytes) {
   if (!bytes || !M || d < 1 || d > KDE_MAX_D || n < 0)

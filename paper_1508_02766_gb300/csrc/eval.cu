@@ -926,7 +926,8 @@ constexpr int kAcRows = 8;
 constexpr int kAcTerms = 4096;
 
 // Block u takes work unit units[u] = (matrix, first row), one warp per lag
-// row, and writes one FP64 partial.
+// row, and writes one FP64 partial.  blockIdx.y > 0 scores the same units
+// against autocorrelation g.set + blockIdx.y, partials at y gridDim.x.
 template <typename T>
 __global__ void __launch_bounds__(256) kde_lscv_ac_kernel(const AcGen<T>* __restrict__ gens,
                                                           const int2* __restrict__ units,
@@ -935,7 +936,8 @@ __global__ void __launch_bounds__(256) kde_lscv_ac_kernel(const AcGen<T>* __rest
                                                           double* __restrict__ partial) {
   const int2 u = units[blockIdx.x];
   const AcGen<T> g = gens[u.x];
-  const T* __restrict__ R = Rall + (int64_t)g.set * set_stride;
+  const T* __restrict__ R = Rall + (int64_t)(g.set + blockIdx.y) * set_stride;
+  partial += (int64_t)blockIdx.y * gridDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int r1 = min(g.L0, u.y + g.rpu - 1);
   T acc = 0;
@@ -985,6 +987,187 @@ __global__ void __launch_bounds__(32) kde_lscv_ac_reduce_kernel(const AcGen<T>* 
     }
     const double K0 = kn[2 * i], n = n_all > 0.0 ? n_all : kn[2 * i + 1];
     lscv_out[i] = s[1] / (n * n) - 2.0 * (s[0] - n * K0) / (n * (n - 1.0));
+  }
+}
+
+// kde_lscv_ac_reduce_kernel for a prepared candidate set scored against
+// many autocorrelations: blockIdx.y is the dataset (its n in nset[y], its
+// partials at y nunits), outputs at y nH_all + i.
+template <typename T>
+__global__ void __launch_bounds__(32) kde_lscv_ac_reduce_sets_kernel(
+    const AcGen<T>* __restrict__ gens, const double* __restrict__ kn,
+    const double* __restrict__ nset, const double* __restrict__ partial, int nunits,
+    int64_t nH_all, double* __restrict__ S_out, double* __restrict__ lscv_out) {
+  const int i = blockIdx.x;
+  const int64_t y = blockIdx.y;
+  partial += y * nunits;
+  double s[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int u0 = gens[2 * i + h].u0, nu = gens[2 * i + h].nu;
+    double v = 0.0;
+    for (int j = threadIdx.x; j < nu; j += 32) v += partial[u0 + j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    s[h] = __shfl_sync(0xffffffffu, v, 0);
+  }
+  if (threadIdx.x == 0) {
+    if (S_out) {
+      S_out[2 * (y * nH_all + i)] = s[0];
+      S_out[2 * (y * nH_all + i) + 1] = s[1];
+    }
+    const double K0 = kn[2 * i], n = nset[y];
+    lscv_out[y * nH_all + i] = s[1] / (n * n) - 2.0 * (s[0] - n * K0) / (n * (n - 1.0));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Candidates of the learned proposal built and scored on the device: for
+// dataset s, candidate j < J is the network's theta_s clipped to a box plus
+// offset j, candidate J the reference theta_s; theta = (a, beta, c) stands
+// for H = R R^T with R = [[e^a, 0], [beta e^c, e^c]].  Each candidate gives
+// the two matrices A = H and A = 2H of the LSCV criterion.
+// ---------------------------------------------------------------------------
+struct ThetaArgs {
+  int nsets, J;
+  const float* theta;     // nsets x 3 (device)
+  const double* n;        // nsets
+  const double* ref;      // nsets x 3
+  const double* off;      // J x 3
+  double box_lo[3], box_hi[3];
+  double tau, delta[2];
+  int M[2], P[2];
+  int wand, per_axis;
+  AcGen<float>* gens;     // [nsets][J + 1][2]; L0 < 0 marks a candidate that does not fit
+  double* K0;             // [nsets][J + 1]: K_H(0)
+};
+
+// One thread per matrix: the same FP64 steps as the host path (H from
+// theta, support by Eq. 15, Cholesky factor, completed-square constants),
+// rounded to the lag sums' FP32 parameters.
+__global__ void __launch_bounds__(128) kde_theta_gen_kernel(ThetaArgs t) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = 2 * (int64_t)(t.J + 1);
+  if (m >= (int64_t)t.nsets * per) return;
+  const int s = (int)(m / per), r = (int)(m % per), j = r >> 1, h = r & 1;
+  double th[3];
+  for (int k = 0; k < 3; ++k) {
+    if (j < t.J) {
+      const double v = (double)t.theta[3 * s + k];
+      th[k] = fmin(fmax(v, t.box_lo[k]), t.box_hi[k]) + t.off[3 * j + k];
+    } else {
+      th[k] = t.ref[3 * s + k];
+    }
+  }
+  const double ea = exp(th[0]), ec = exp(th[2]), b = th[1] * ec, sc = h ? 2.0 : 1.0;
+  const double A00 = sc * (ea * ea), A01 = sc * (ea * b), A11 = sc * (b * b + ec * ec);
+  const double mid = 0.5 * (A00 + A11), hd = 0.5 * (A00 - A11);
+  const double lam = mid + sqrt(hd * hd + A01 * A01);
+  int L[2];
+  bool ok = isfinite(lam) && A00 > 0.0;
+  const double Akk[2] = {A00, A11};
+  for (int k = 0; k < 2; ++k) {
+    const double half = t.per_axis ? t.tau * sqrt(Akk[k]) : t.tau * sqrt(fabs(lam));
+    const double c = ceil(half / t.delta[k]);
+    L[k] = c >= (double)(t.M[k] - 1) ? t.M[k] - 1 : (int)c;
+    ok = ok && t.M[k] + L[k] <= t.P[k];
+  }
+  const double r00 = sqrt(A00), r10 = A01 / r00, r11 = sqrt(A11 - r10 * r10);
+  ok = ok && r11 > 0.0;
+  const double i00 = 1.0 / r00, i11 = 1.0 / r11, i10 = -(r10 * i00) / r11;
+  const double D0 = -0.5 * t.delta[0] * t.delta[0] * i00 * i00;
+  const double D1 = -0.5 * t.delta[1] * t.delta[1] * i11 * i11;
+  const double B = i10 * t.delta[0] / (i11 * t.delta[1]);
+  const double det = (r00 * r11) * (r00 * r11);
+  const double C = (1.0 / 6.283185307179586476925287) / sqrt(det);
+  const double log2e = 1.4426950408889634073599246810;
+  AcGen<float> g{};
+  g.L0 = ok ? L[0] : -1;
+  g.L1 = L[1];
+  g.wand = t.wand;
+  g.set = s;
+  g.D0 = (float)(D0 * log2e);
+  g.D1 = (float)(D1 * log2e);
+  g.b_hi = (float)B;
+  g.b_lo = (float)(B - (double)g.b_hi);
+  g.C = (float)C;
+  t.gens[m] = g;
+  if (h == 0) t.K0[m >> 1] = C;
+}
+
+// One block per matrix: S(A) = sum over the support of K_A(delta o l) R(l)
+// with the lag-row arithmetic of kde_lscv_ac_kernel (one warp per lag row,
+// FP32 terms and row sums, FP64 across warps); NaN for a candidate that
+// does not fit the plan.
+__global__ void __launch_bounds__(256) kde_lscv_theta_sums_kernel(const AcGen<float>* __restrict__ gens,
+                                                                  const float* __restrict__ Rall,
+                                                                  int P1, int64_t set_stride,
+                                                                  double* __restrict__ S) {
+  const AcGen<float> g = gens[blockIdx.x];
+  if (g.L0 < 0) {
+    if (threadIdx.x == 0) S[blockIdx.x] = nan("");
+    return;
+  }
+  const float* __restrict__ R = Rall + (int64_t)g.set * set_stride;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  float acc = 0.f;
+  for (int l0 = warp; l0 <= g.L0; l0 += nw) {
+    const float tl = (float)l0;
+    const float t_hi = g.b_hi * tl;
+    const float t_lo = prod_lo(g.b_hi, g.b_lo, tl, t_hi);
+    const float e0 = g.D0 * tl * tl;
+    const float* Rrow = R + (size_t)l0 * P1;
+    float racc = 0.f;
+    for (int l1 = (l0 == 0 ? 0 : -g.L1) + lane; l1 <= g.L1; l1 += 32) {
+      const float v = ((float)(g.wand ? abs(l1) : l1) + t_hi) + t_lo;
+      racc += ex2(fmaf(g.D1 * v, v, e0)) * __ldg(Rrow + (l1 < 0 ? l1 + P1 : l1));
+    }
+    if (l0 == 0 && lane == 0) racc -= 0.5f * __ldg(Rrow);
+    acc += 2.f * racc;
+  }
+  block_sum_to((double)(g.C * acc), S + blockIdx.x);
+}
+
+// One warp per dataset: LSCV of its J + 1 candidates (optionally stored),
+// the first index of the smallest among the first J (a candidate that does
+// not fit counts as +inf) and out[s] = {that index, its LSCV, the reference
+// candidate's LSCV}.
+__global__ void __launch_bounds__(32) kde_lscv_theta_pick_kernel(int J, const double* __restrict__ n_all,
+                                                                 const double* __restrict__ K0,
+                                                                 const double* __restrict__ S,
+                                                                 double* __restrict__ lscv,
+                                                                 double* __restrict__ out) {
+  const int s = blockIdx.x;
+  const double n = n_all[s];
+  double best = HUGE_VAL;
+  int bi = J;   // no candidate fits
+  double ref = HUGE_VAL;
+  for (int j = threadIdx.x; j <= J; j += 32) {
+    const int64_t c = (int64_t)s * (J + 1) + j;
+    const double s1 = S[2 * c], s2 = S[2 * c + 1];
+    double v = s2 / (n * n) - 2.0 * (s1 - n * K0[c]) / (n * (n - 1.0));
+    if (isnan(v)) v = HUGE_VAL;
+    if (lscv) lscv[c] = v;
+    if (j == J) ref = v;
+    else if (v < best) {   // j increases per lane, so the first smallest is kept
+      best = v;
+      bi = j;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, best, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ov < best || (ov == best && oi < bi)) {
+      best = ov;
+      bi = oi;
+    }
+    ref = fmin(ref, __shfl_down_sync(0xffffffffu, ref, off));
+  }
+  if (threadIdx.x == 0) {
+    out[3 * s] = (double)bi;
+    out[3 * s + 1] = best;
+    out[3 * s + 2] = ref;
   }
 }
 
@@ -1587,20 +1770,22 @@ size_t ac_workspace(const kde_plan_info& I) {
 
 template <typename T>
 kde_status autocorr_impl(kde_plan_s* plan, const int64_t* counts, void* Rout, void* ws,
-                         cudaStream_t st) {
+                         cudaStream_t st, int64_t nsets = 1, void* ws_B = nullptr) {
   using V = typename Cplx<T>::type;
   const kde_plan_info& I = plan->info;
-  V* A = (V*)ws;              // [M_0][Q] half spectra of the counts rows
-  V* B = A + I.M[0] * I.Q;    // [P_0][Q] after the axis-0 round trip
+  // nsets grids one after another: counts [nsets][M_0][M_1], R [nsets][P_0][P_1]
+  V* A = (V*)ws;                                       // [nsets][M_0][Q] half spectra of the rows
+  V* B = ws_B ? (V*)ws_B : A + nsets * I.M[0] * I.Q;   // [nsets][P_0][Q] after the axis-0 pass
   RowsParams<T> rp{};
-  rp.nrows = I.M[0];
+  rp.nrows = nsets * I.M[0];
   rp.Min = (int)I.M[1];
   rp.in_stride = I.M[1];
   rp.Q = (int)I.Q;
   rp.out = A;
   rp.lp = line_plan(I, 1);
   rp.tw = twiddles<T>(plan, 1);
-  kde_status s = counts_rows<T>(plan, reinterpret_cast<const long long*>(counts), I.M[0], rp, st);
+  kde_status s = counts_rows<T>(plan, reinterpret_cast<const long long*>(counts), nsets * I.M[0],
+                                rp, st);
   if (s != KDE_OK) return s;
   ColsParams<T> cp{};
   cp.in = A;
@@ -1614,18 +1799,18 @@ kde_status autocorr_impl(kde_plan_s* plan, const int64_t* counts, void* Rout, vo
   // counts are in units of 2^-32; the inverse transforms are unnormalised
   cp.s_pre = (T)2.3283064365386963e-10;
   cp.s_post = (T)(1.0 / ((double)I.P[0] * (double)I.P[1]));
-  s = launch_cols<T>(KDE_COLS(kde_cols_auto_kernel), cp, 1, plan->cols_variant, st,
+  s = launch_cols<T>(KDE_COLS(kde_cols_auto_kernel), cp, nsets, plan->cols_variant, st,
                      "kde_cols_auto_kernel");
   if (s != KDE_OK) return s;
   C2RParams<T> cr{};
   cr.in = B;
   cr.out = (T*)Rout;
-  cr.nrows = I.P[0];
+  cr.nrows = nsets * I.P[0];
   cr.Mout = (int)I.P[1];
   cr.Q = (int)I.Q;
   cr.lp = line_plan(I, 1);
   cr.tw = twiddles<T>(plan, 1);
-  return launch_rows<T>(kde_rows_c2r_kernel<T>, "kde_rows_c2r_kernel", I.P[0], cr, st);
+  return launch_rows<T>(kde_rows_c2r_kernel<T>, "kde_rows_c2r_kernel", nsets * I.P[0], cr, st);
 }
 
 // Host side of one chunk of lag-sum candidates: candidates c = c0 ..
@@ -2002,6 +2187,85 @@ extern "C" kde_status kde_autocorrelation(kde_plan plan, const int64_t* counts, 
   return autocorr_impl<double>(plan, counts, R, workspace, st);
 }
 
+// Workspace of kde_prepare2_batch: device copy of the offsets, the
+// standardised samples, and the autocorrelation's two intermediates for
+// every grid.
+struct PrepLayout {
+  size_t off_offsets, off_Z, off_A, off_B, total;
+};
+
+static PrepLayout prep_layout(const kde_plan_info& I, int64_t nsets, int64_t n_total) {
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t cb = I.precision == KDE_F32 ? 8 : 16;  // complex element
+  PrepLayout L{};
+  L.off_offsets = 0;
+  L.off_Z = up((size_t)(nsets + 1) * sizeof(int64_t));
+  L.off_A = L.off_Z + up((size_t)n_total * 2 * sizeof(float));
+  L.off_B = L.off_A + up((size_t)nsets * I.M[0] * I.Q * cb);
+  L.total = L.off_B + up((size_t)nsets * I.P[0] * I.Q * cb);
+  return L;
+}
+
+static kde_status prep_check(kde_plan plan, int nsets) {
+  if (!plan) return fail(KDE_ERR_INVALID_ARG, "NULL plan");
+  const kde_plan_info& I = plan->info;
+  if (I.d != 2) return fail(KDE_ERR_UNSUPPORTED, "batched preparation supports d = 2");
+  if (I.M[0] != I.M[1] || I.M[0] < 32 || I.M[0] % 32)
+    return fail(KDE_ERR_UNSUPPORTED, "batched preparation needs an M x M grid, M a multiple of 32");
+  if (nsets < 0 || nsets > 65535) return fail(KDE_ERR_INVALID_ARG, "need 0 <= nsets <= 65535");
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_prepare2_batch_workspace_bytes(kde_plan plan, int nsets, int64_t n_total,
+                                                         size_t* bytes) {
+  kde_status s = prep_check(plan, nsets);
+  if (s != KDE_OK) return s;
+  if (!bytes || n_total < 0) return fail(KDE_ERR_INVALID_ARG, "bad argument");
+  *bytes = prep_layout(plan->info, nsets, n_total).total;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_prepare2_batch(kde_plan plan, int nsets, const float* X,
+                                         const int64_t* offsets, int64_t* counts, double* moments,
+                                         float* feat, void* R, void* workspace,
+                                         size_t workspace_bytes, kde_stream_t stream) {
+  kde_status s = prep_check(plan, nsets);
+  if (s != KDE_OK) return s;
+  if (nsets == 0) return KDE_OK;
+  if (!X || !offsets || !counts || !moments || !feat || !R)
+    return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (offsets[0] != 0) return fail(KDE_ERR_INVALID_ARG, "offsets[0] must be 0");
+  int64_t n_max = 0;
+  for (int b = 0; b < nsets; ++b) {
+    const int64_t n = offsets[b + 1] - offsets[b];
+    if (n < 2) return fail(KDE_ERR_INVALID_ARG, "every dataset needs at least 2 samples");
+    if (n >= (int64_t(1) << 31)) return fail(KDE_ERR_INVALID_ARG, "a dataset has 2^31 samples or more");
+    n_max = std::max(n_max, n);
+  }
+  const int64_t n_total = offsets[nsets];
+  const kde_plan_info& I = plan->info;
+  const PrepLayout L = prep_layout(I, nsets, n_total);
+  if (!workspace || workspace_bytes < L.total)
+    return fail(KDE_ERR_WORKSPACE, "workspace smaller than kde_prepare2_batch_workspace_bytes");
+  if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  if ((s = check_device(plan)) != KDE_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  int64_t* off_dev = (int64_t*)(ws + L.off_offsets);
+  float* Z = (float*)(ws + L.off_Z);
+  // pageable source: staged before this call returns
+  cudaError_t e = cudaMemcpyAsync(off_dev, offsets, (size_t)(nsets + 1) * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(offsets)");
+  if ((s = standardize2_sets(X, off_dev, nsets, Z, moments, st)) != KDE_OK) return s;
+  if ((s = bin_sets_f32(Z, off_dev, nsets, n_max, 2, plan->lo, plan->hi, I.M, counts, st)) != KDE_OK)
+    return s;
+  if ((s = features2_sets(counts, (int)I.M[0], nsets, off_dev, moments, feat, st)) != KDE_OK) return s;
+  if (I.precision == KDE_F32)
+    return autocorr_impl<float>(plan, counts, R, ws + L.off_A, st, nsets, ws + L.off_B);
+  return autocorr_impl<double>(plan, counts, R, ws + L.off_A, st, nsets, ws + L.off_B);
+}
+
 static kde_status lscv_ac_entry(kde_plan plan, int nsets, const int64_t* n, int nH,
                                 const double* H, const void* R, double* pair_sums, double* lscv,
                                 void* workspace, size_t workspace_bytes, kde_stream_t stream) {
@@ -2118,6 +2382,194 @@ extern "C" kde_status kde_lscv_autocorr_cands(kde_lscv_cands cands, int64_t n, c
             : ac_launch_chunk<double>(plan->info, ch.dev, ch.nh, ch.nunits, R, partial, (double)n, S,
                                       lscv + ch.c0, st);
     if (s != KDE_OK) return s;
+  }
+  return KDE_OK;
+}
+
+// Scratch of kde_lscv_autocorr_cands_batch: the datasets' n, then one FP64
+// partial per work unit of the largest chunk and dataset.
+static size_t cands_batch_bytes(const kde_lscv_cands_s* c, int nsets) {
+  int units = 0;
+  for (const auto& ch : c->chunks) units = std::max(units, ch.nunits);
+  const size_t nb = ((size_t)nsets * sizeof(double) + 255) & ~(size_t)255;
+  return nb + (size_t)nsets * units * sizeof(double);
+}
+
+extern "C" kde_status kde_lscv_autocorr_cands_batch_workspace_bytes(kde_lscv_cands cands, int nsets,
+                                                                    size_t* bytes) {
+  if (!cands || !bytes) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (nsets < 0 || nsets > 65535) return fail(KDE_ERR_INVALID_ARG, "need 0 <= nsets <= 65535");
+  *bytes = cands_batch_bytes(cands, nsets);
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_lscv_autocorr_cands_batch(kde_lscv_cands cands, int nsets,
+                                                    const int64_t* n, const void* R,
+                                                    double* pair_sums, double* lscv,
+                                                    void* workspace, size_t workspace_bytes,
+                                                    kde_stream_t stream) {
+  if (!cands) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (nsets < 0 || nsets > 65535) return fail(KDE_ERR_INVALID_ARG, "need 0 <= nsets <= 65535");
+  if (nsets == 0) return KDE_OK;
+  if (!n || !R || !lscv) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  std::vector<double> nd((size_t)nsets);
+  for (int b = 0; b < nsets; ++b) {
+    if (n[b] < 2) return fail(KDE_ERR_INVALID_ARG, "LSCV needs n >= 2");
+    nd[b] = (double)n[b];
+  }
+  if (!workspace || workspace_bytes < cands_batch_bytes(cands, nsets))
+    return fail(KDE_ERR_WORKSPACE, "workspace smaller than kde_lscv_autocorr_cands_batch_workspace_bytes");
+  if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  kde_plan_s* plan = cands->plan;
+  kde_status s = check_device(plan);
+  if (s != KDE_OK) return s;
+  const kde_plan_info& I = plan->info;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* nset = (double*)workspace;
+  double* partial = (double*)((char*)workspace + (((size_t)nsets * sizeof(double) + 255) & ~(size_t)255));
+  // pageable source: staged before this call returns
+  cudaError_t e = cudaMemcpyAsync(nset, nd.data(), nd.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(n)");
+  const bool f32 = I.precision == KDE_F32;
+  const size_t gsz = f32 ? sizeof(AcGen<float>) : sizeof(AcGen<double>);
+  for (const auto& ch : cands->chunks) {
+    const char* img = (const char*)ch.dev;
+    const double* kn_dev = (const double*)(img + 2 * ch.nh * gsz);
+    const int2* units_dev = (const int2*)((const char*)kn_dev + 2 * ch.nh * sizeof(double));
+    const dim3 g1((unsigned)ch.nunits, (unsigned)nsets), g2((unsigned)ch.nh, (unsigned)nsets);
+    double* S = pair_sums ? pair_sums + 2 * ch.c0 : nullptr;
+    {
+      LaunchScope ls("kde_lscv_ac_kernel", st);
+      if (f32)
+        kde_lscv_ac_kernel<float><<<g1, 256, 0, st>>>((const AcGen<float>*)img, units_dev,
+                                                       (const float*)R, (int)I.P[1],
+                                                       (int64_t)I.P[0] * I.P[1], partial);
+      else
+        kde_lscv_ac_kernel<double><<<g1, 256, 0, st>>>((const AcGen<double>*)img, units_dev,
+                                                        (const double*)R, (int)I.P[1],
+                                                        (int64_t)I.P[0] * I.P[1], partial);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_kernel");
+    }
+    {
+      LaunchScope ls("kde_lscv_ac_reduce_sets_kernel", st);
+      if (f32)
+        kde_lscv_ac_reduce_sets_kernel<float><<<g2, 32, 0, st>>>(
+            (const AcGen<float>*)img, kn_dev, nset, partial, ch.nunits, cands->nH, S, lscv + ch.c0);
+      else
+        kde_lscv_ac_reduce_sets_kernel<double><<<g2, 32, 0, st>>>(
+            (const AcGen<double>*)img, kn_dev, nset, partial, ch.nunits, cands->nH, S, lscv + ch.c0);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_reduce_sets_kernel");
+    }
+  }
+  return KDE_OK;
+}
+
+// Workspace of kde_lscv_theta_select: the uploaded n, reference thetas and
+// offsets; the candidates' parameters, K_H(0) and pair sums.
+struct ThetaLayout {
+  size_t off_up, off_gens, off_K0, off_S, total;
+};
+
+static ThetaLayout theta_layout(int64_t nsets, int64_t J) {
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int64_t cands = nsets * (J + 1);
+  ThetaLayout L{};
+  L.off_up = 0;
+  L.off_gens = up((size_t)(nsets + 3 * nsets + 3 * J) * sizeof(double));
+  L.off_K0 = L.off_gens + up((size_t)2 * cands * sizeof(AcGen<float>));
+  L.off_S = L.off_K0 + up((size_t)cands * sizeof(double));
+  L.total = L.off_S + up((size_t)2 * cands * sizeof(double));
+  return L;
+}
+
+extern "C" kde_status kde_lscv_theta_select_workspace_bytes(kde_plan plan, int nsets, int J,
+                                                            size_t* bytes) {
+  if (!plan || !bytes) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  if (nsets < 0 || J < 1 || (int64_t)nsets * 2 * (J + 1) >= (int64_t(1) << 31))
+    return fail(KDE_ERR_INVALID_ARG, "need nsets >= 0, J >= 1 and fewer than 2^31 matrices");
+  *bytes = theta_layout(nsets, J).total;
+  return KDE_OK;
+}
+
+extern "C" kde_status kde_lscv_theta_select(kde_plan plan, int nsets, const int64_t* n,
+                                            const float* theta, const double* box, int J,
+                                            const double* offsets, const double* ref, const void* R,
+                                            double* lscv, double* out, void* workspace,
+                                            size_t workspace_bytes, kde_stream_t stream) {
+  if (!plan) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  const kde_plan_info& I = plan->info;
+  if (I.d != 2 || I.precision != KDE_F32)
+    return fail(KDE_ERR_UNSUPPORTED, "device-built candidates need a KDE_F32 2-D plan");
+  if (nsets < 0 || J < 1 || (int64_t)nsets * 2 * (J + 1) >= (int64_t(1) << 31))
+    return fail(KDE_ERR_INVALID_ARG, "need nsets >= 0, J >= 1 and fewer than 2^31 matrices");
+  if (nsets == 0) return KDE_OK;
+  if (!n || !theta || !box || !offsets || !ref || !R || !out)
+    return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  const ThetaLayout L = theta_layout(nsets, J);
+  if (!workspace || workspace_bytes < L.total)
+    return fail(KDE_ERR_WORKSPACE, "workspace smaller than kde_lscv_theta_select_workspace_bytes");
+  if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  std::vector<double> up((size_t)(nsets + 3 * nsets + 3 * J));
+  for (int s = 0; s < nsets; ++s) {
+    if (n[s] < 2) return fail(KDE_ERR_INVALID_ARG, "LSCV needs n >= 2");
+    up[s] = (double)n[s];
+  }
+  for (int i = 0; i < 3 * nsets; ++i) {
+    if (!std::isfinite(ref[i])) return fail(KDE_ERR_INVALID_ARG, "non-finite reference theta");
+    up[nsets + i] = ref[i];
+  }
+  for (int i = 0; i < 3 * J; ++i) {
+    if (!std::isfinite(offsets[i])) return fail(KDE_ERR_INVALID_ARG, "non-finite offset");
+    up[4 * (size_t)nsets + i] = offsets[i];
+  }
+  for (int k = 0; k < 6; ++k)
+    if (!std::isfinite(box[k])) return fail(KDE_ERR_INVALID_ARG, "non-finite box");
+  kde_status s = check_device(plan);
+  if (s != KDE_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  double* upd = (double*)(ws + L.off_up);
+  // pageable source: staged before this call returns
+  cudaError_t e = cudaMemcpyAsync(upd, up.data(), up.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(candidate inputs)");
+  ThetaArgs t{};
+  t.nsets = nsets;
+  t.J = J;
+  t.theta = theta;
+  t.n = upd;
+  t.ref = upd + nsets;
+  t.off = upd + 4 * (size_t)nsets;
+  for (int k = 0; k < 3; ++k) {
+    t.box_lo[k] = box[k];
+    t.box_hi[k] = box[3 + k];
+  }
+  t.tau = plan->tau;
+  for (int k = 0; k < 2; ++k) {
+    t.delta[k] = I.delta[k];
+    t.M[k] = (int)I.M[k];
+    t.P[k] = (int)I.P[k];
+  }
+  t.wand = plan->layout_mode == KDE_LAYOUT_WAND;
+  t.per_axis = plan->range_mode != KDE_RANGE_CORRECTED;
+  t.gens = (AcGen<float>*)(ws + L.off_gens);
+  t.K0 = (double*)(ws + L.off_K0);
+  double* S = (double*)(ws + L.off_S);
+  const int64_t nmat = (int64_t)nsets * 2 * (J + 1);
+  {
+    LaunchScope ls("kde_theta_gen_kernel", st);
+    kde_theta_gen_kernel<<<(unsigned)((nmat + 127) / 128), 128, 0, st>>>(t);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_theta_gen_kernel");
+  }
+  {
+    LaunchScope ls("kde_lscv_theta_sums_kernel", st);
+    kde_lscv_theta_sums_kernel<<<(unsigned)nmat, 256, 0, st>>>(t.gens, (const float*)R, (int)I.P[1],
+                                                               (int64_t)I.P[0] * I.P[1], S);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_lscv_theta_sums_kernel");
+  }
+  {
+    LaunchScope ls("kde_lscv_theta_pick_kernel", st);
+    kde_lscv_theta_pick_kernel<<<nsets, 32, 0, st>>>(J, t.n, t.K0, S, lscv, out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_lscv_theta_pick_kernel");
   }
   return KDE_OK;
 }

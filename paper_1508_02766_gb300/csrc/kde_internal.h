@@ -65,6 +65,19 @@ kde_status fx_eval_batch2(kde_plan_s* plan, const float2* A, int nh, const KGen<
                           const int* L0, int Lmax0, float2* t1, float* Kb, float2* Sb,
                           float* density, cudaStream_t st);
 
+// Prepared batches of 2-D datasets (kde_prepare2_batch): binning of nsets
+// datasets onto one grid (bin.cu; samples rows [off[s], off[s+1]) of X,
+// offsets on the device, counts [nsets][prod M] zeroed first), and the
+// standardisation and features of each (learn.cu; same offsets, moments
+// [nsets][8], features [nsets][KDE_FEAT_DIM]).
+kde_status bin_sets_f32(const float* X, const int64_t* off_dev, int nsets, int64_t n_max, int d,
+                        const double* lo, const double* hi, const int64_t* M, int64_t* counts,
+                        cudaStream_t st);
+kde_status standardize2_sets(const float* X, const int64_t* off_dev, int nsets, float* Z,
+                             double* moments, cudaStream_t st);
+kde_status features2_sets(const int64_t* counts, int M, int nsets, const int64_t* off_dev,
+                          const double* moments, float* feat, cudaStream_t st);
+
 // Readers of the per-translation-unit check words of a debug build (0 in a
 // release build; -1 if the word could not be read).
 int debug_read_bin();

@@ -425,9 +425,8 @@ __device__ float block_sum_f(float v, float* wbuf) {
 // One block of 1024 threads.  moments = {mean0, mean1, sd0, sd1, corr,
 // skew0, skew1, (kurt0 + kurt1)/2 - 3} (population moments); Z = (X - mean)
 // / sd in FP32.
-__global__ void __launch_bounds__(1024) kde_standardize2_kernel(const float* __restrict__ X,
-                                                                int64_t n, float* __restrict__ Z,
-                                                                double* __restrict__ mom) {
+__device__ __forceinline__ void standardize2_body(const float* __restrict__ X, int64_t n,
+                                                  float* __restrict__ Z, double* __restrict__ mom) {
   __shared__ float wbuf[33];
   const float inv_n = 1.0f / (float)n;
   float s0 = 0.f, s1 = 0.f;
@@ -472,18 +471,32 @@ __global__ void __launch_bounds__(1024) kde_standardize2_kernel(const float* __r
   }
 }
 
+__global__ void __launch_bounds__(1024) kde_standardize2_kernel(const float* __restrict__ X,
+                                                                int64_t n, float* __restrict__ Z,
+                                                                double* __restrict__ mom) {
+  standardize2_body(X, n, Z, mom);
+}
+
+// One block per dataset of a batch: rows [off[b], off[b + 1]) of X and Z,
+// moments at 8 b.
+__global__ void __launch_bounds__(1024) kde_standardize2_sets_kernel(
+    const float* __restrict__ X, const int64_t* __restrict__ off, float* __restrict__ Z,
+    double* __restrict__ mom) {
+  const int64_t a = off[blockIdx.x], b = off[blockIdx.x + 1];
+  standardize2_body(X + 2 * a, b - a, Z + 2 * a, mom + 8 * (int64_t)blockIdx.x);
+}
+
 // 32 blocks of 256 threads, block `by` for the 32 block-features of one
 // block row of the M x M grid (w = M/32 cells a side): thread (y0, bx) sums
 // rows y0, y0 + 8, ... of block (by, bx); the rows are then added in shared
 // memory.  feat[32 by + bx] = 8 sqrt(mass / n) with mass the block's counts
 // times 2^-32; block 0 also writes feat[1024..] = corr, skew0, skew1, excess
 // kurtosis, log10(n)/4, 1, then zeros.
-__global__ void __launch_bounds__(256) kde_features2_kernel(const long long* __restrict__ counts,
-                                                            int M, int64_t n,
-                                                            const double* __restrict__ mom,
-                                                            float* __restrict__ feat) {
+__device__ __forceinline__ void features2_body(int by, const long long* __restrict__ counts,
+                                               int M, int64_t n, const double* __restrict__ mom,
+                                               float* __restrict__ feat) {
   __shared__ unsigned long long part[8][32];
-  const int by = blockIdx.x, t = threadIdx.x, bx = t & 31, y0 = t >> 5, w = M / 32;
+  const int t = threadIdx.x, bx = t & 31, y0 = t >> 5, w = M / 32;
   unsigned long long s = 0;
   for (int y = y0; y < w; y += 8) {
     const long long* row = counts + (size_t)(by * w + y) * M + bx * w;
@@ -512,7 +525,45 @@ __global__ void __launch_bounds__(256) kde_features2_kernel(const long long* __r
   }
 }
 
+__global__ void __launch_bounds__(256) kde_features2_kernel(const long long* __restrict__ counts,
+                                                            int M, int64_t n,
+                                                            const double* __restrict__ mom,
+                                                            float* __restrict__ feat) {
+  features2_body(blockIdx.x, counts, M, n, mom, feat);
+}
+
+// Grid (32, nsets): block row blockIdx.x of dataset blockIdx.y, whose
+// counts start at y M^2, moments at 8 y and features at y KDE_FEAT_DIM.
+__global__ void __launch_bounds__(256) kde_features2_sets_kernel(
+    const long long* __restrict__ counts, int M, const int64_t* __restrict__ off,
+    const double* __restrict__ mom, float* __restrict__ feat) {
+  const int64_t y = blockIdx.y;
+  features2_body(blockIdx.x, counts + y * M * M, M, off[y + 1] - off[y], mom + 8 * y,
+                 feat + y * KDE_FEAT_DIM);
+}
+
 }  // namespace
+}  // namespace kde
+
+namespace kde {
+
+kde_status standardize2_sets(const float* X, const int64_t* off_dev, int nsets, float* Z,
+                             double* moments, cudaStream_t st) {
+  LaunchScope ls("kde_standardize2_sets_kernel", st);
+  kde_standardize2_sets_kernel<<<nsets, 1024, 0, st>>>(X, off_dev, Z, moments);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? KDE_OK : cuda_fail(e, "kde_standardize2_sets_kernel");
+}
+
+kde_status features2_sets(const int64_t* counts, int M, int nsets, const int64_t* off_dev,
+                          const double* moments, float* feat, cudaStream_t st) {
+  LaunchScope ls("kde_features2_sets_kernel", st);
+  kde_features2_sets_kernel<<<dim3(32, (unsigned)nsets), 256, 0, st>>>(
+      (const long long*)counts, M, off_dev, moments, feat);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? KDE_OK : cuda_fail(e, "kde_features2_sets_kernel");
+}
+
 }  // namespace kde
 
 using namespace kde;

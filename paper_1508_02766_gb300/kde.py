@@ -71,7 +71,10 @@ EXPORTS = [
     "kde_wait_probe", "kde_plan_check", "kde_outside_check", "kde_noalloc_scratch_bytes",
     "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes", "kde_batch_set_mode",
     "kde_batch_get_mode", "kde_batch_check", "kde_batch_set_wait", "kde_batch_get_config",
-    "kde_batch_set_queue_order", "kde_debug_status",
+    "kde_batch_set_queue_order", "kde_debug_status", "kde_prepare2_batch",
+    "kde_prepare2_batch_workspace_bytes", "kde_lscv_autocorr_cands_batch",
+    "kde_lscv_autocorr_cands_batch_workspace_bytes", "kde_lscv_theta_select",
+    "kde_lscv_theta_select_workspace_bytes",
 ]
 FEAT_DIM = 1088
 
@@ -142,6 +145,18 @@ def lib():
     L.kde_batch_set_wait.argtypes = [vp, ctypes.c_uint32, ctypes.c_int]
     L.kde_batch_get_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        i64p]
+    L.kde_prepare2_batch.argtypes = [vp, ctypes.c_int, vp, i64p, vp, vp, vp, vp, vp,
+                                     ctypes.c_size_t, vp]
+    L.kde_prepare2_batch_workspace_bytes.argtypes = [vp, ctypes.c_int, i64,
+                                                     ctypes.POINTER(ctypes.c_size_t)]
+    L.kde_lscv_autocorr_cands_batch.argtypes = [vp, ctypes.c_int, i64p, vp, vp, vp, vp,
+                                                ctypes.c_size_t, vp]
+    L.kde_lscv_autocorr_cands_batch_workspace_bytes.argtypes = [vp, ctypes.c_int,
+                                                                ctypes.POINTER(ctypes.c_size_t)]
+    L.kde_lscv_theta_select.argtypes = [vp, ctypes.c_int, i64p, vp, dp, ctypes.c_int, dp, dp, vp,
+                                        vp, vp, vp, ctypes.c_size_t, vp]
+    L.kde_lscv_theta_select_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int,
+                                                        ctypes.POINTER(ctypes.c_size_t)]
     L.kde_plan_check.argtypes = [vp, vp]
     L.kde_outside_check.argtypes = [vp, vp, i64p]
     L.kde_noalloc_scratch_bytes.argtypes = []
@@ -169,7 +184,11 @@ def lib():
                  "kde_lscv_autocorr_cands", "kde_wait_probe", "kde_plan_check",
                  "kde_outside_check", "kde_fft_eval_multi", "kde_fft_eval_multi_workspace_bytes",
                  "kde_batch_set_mode", "kde_batch_get_mode", "kde_batch_check", "kde_batch_set_wait",
-                 "kde_batch_get_config", "kde_batch_set_queue_order", "kde_debug_status"):
+                 "kde_batch_get_config", "kde_batch_set_queue_order", "kde_debug_status",
+                 "kde_prepare2_batch", "kde_prepare2_batch_workspace_bytes",
+                 "kde_lscv_autocorr_cands_batch",
+                 "kde_lscv_autocorr_cands_batch_workspace_bytes", "kde_lscv_theta_select",
+                 "kde_lscv_theta_select_workspace_bytes"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -509,6 +528,32 @@ class LscvCands:
                                              _stream_ptr(stream)))
         return lscv
 
+    def batch_workspace_bytes(self, nsets):
+        b = ctypes.c_size_t()
+        _check(lib().kde_lscv_autocorr_cands_batch_workspace_bytes(self.handle, int(nsets),
+                                                                   ctypes.byref(b)))
+        return b.value
+
+    def score_batch(self, ns, Rs, lscv=None, pair_sums=None, workspace=None, stream=None):
+        """LSCV of every candidate for every dataset: ns (nsets sample
+        counts), Rs (nsets x P_0 x P_1 autocorrelations); returns an
+        nsets x nH tensor (kde_lscv_autocorr_cands_batch)."""
+        import torch
+        ns = np.ascontiguousarray(np.asarray(ns, dtype=np.int64))
+        B = int(ns.shape[0])
+        if Rs.shape[0] != B or not Rs.is_contiguous():
+            raise ValueError("Rs must be a contiguous (nsets, P_0, P_1) tensor")
+        if lscv is None:
+            lscv = torch.empty(B, self.nH, dtype=torch.float64, device=Rs.device)
+        if workspace is None:
+            workspace = torch.empty(max(256, self.batch_workspace_bytes(B)), dtype=torch.uint8,
+                                    device=Rs.device)
+        _check(lib().kde_lscv_autocorr_cands_batch(
+            self.handle, B, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(Rs),
+            _ptr(pair_sums), _ptr(lscv), _ptr(workspace),
+            workspace.numel() * workspace.element_size(), _stream_ptr(stream)))
+        return lscv
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value and _lib is not None:
@@ -820,6 +865,82 @@ class FeaturePrep:
         _check(L.kde_autocorrelation(self.plan.handle, self._pc, ctypes.c_void_p(R.data_ptr()),
                                      self._pws, self._wsb, s))
         return feat
+
+
+def lscv_theta_select_workspace_bytes(plan: Plan, nsets, J):
+    b = ctypes.c_size_t()
+    _check(lib().kde_lscv_theta_select_workspace_bytes(plan.handle, int(nsets), int(J),
+                                                       ctypes.byref(b)))
+    return b.value
+
+
+def kde_lscv_theta_select(plan: Plan, ns, theta, box_lo, box_hi, offsets, ref, R, lscv=None,
+                          out=None, workspace=None, stream=None):
+    """Candidates built on the device (kde_lscv_theta_select): theta (nsets x
+    3 FP32 CUDA tensor), box and offsets (J x 3) and ref (nsets x 3) on the
+    host, R the nsets autocorrelations.  Returns out (nsets x 3 FP64 CUDA:
+    best index among the J offsets, its LSCV, the reference's LSCV)."""
+    import torch
+    ns = np.ascontiguousarray(np.asarray(ns, dtype=np.int64))
+    B = int(ns.shape[0])
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.float64).reshape(-1, 3))
+    J = int(off.shape[0])
+    refa = np.ascontiguousarray(np.asarray(ref, dtype=np.float64).reshape(B, 3))
+    box = np.ascontiguousarray(np.concatenate([np.asarray(box_lo, dtype=np.float64).reshape(3),
+                                               np.asarray(box_hi, dtype=np.float64).reshape(3)]))
+    if theta.dtype != torch.float32 or not theta.is_contiguous() or tuple(theta.shape) != (B, 3):
+        raise ValueError("theta must be a contiguous (nsets, 3) float32 tensor")
+    if out is None:
+        out = torch.empty(B, 3, dtype=torch.float64, device=theta.device)
+    if workspace is None:
+        workspace = torch.empty(max(256, lscv_theta_select_workspace_bytes(plan, B, J)),
+                                dtype=torch.uint8, device=theta.device)
+    dptr = ctypes.POINTER(ctypes.c_double)
+    _check(lib().kde_lscv_theta_select(
+        plan.handle, B, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(theta),
+        box.ctypes.data_as(dptr), J, off.ctypes.data_as(dptr), refa.ctypes.data_as(dptr), _ptr(R),
+        _ptr(lscv), _ptr(out), _ptr(workspace), workspace.numel() * workspace.element_size(),
+        _stream_ptr(stream)))
+    return out
+
+
+class BatchPrep:
+    """kde_prepare2_batch: the per-dataset preparation (standardise, bin on
+    the plan's grid, features, autocorrelation) of up to nsets_max datasets
+    holding up to n_total_max samples in all, in one call.  Owns the counts,
+    moments and workspace; run() writes the features and autocorrelations
+    into the caller's tensors."""
+
+    def __init__(self, plan: Plan, nsets_max, n_total_max, device="cuda"):
+        import torch
+        self.plan = plan
+        self.nsets_max, self.n_total_max = int(nsets_max), int(n_total_max)
+        b = ctypes.c_size_t()
+        _check(lib().kde_prepare2_batch_workspace_bytes(plan.handle, self.nsets_max,
+                                                        self.n_total_max, ctypes.byref(b)))
+        self.ws = torch.empty(max(256, b.value), dtype=torch.uint8, device=device)
+        self.counts = torch.empty((self.nsets_max,) + tuple(plan.M), dtype=torch.int64,
+                                  device=device)
+        self.moments = torch.empty(self.nsets_max, 8, dtype=torch.float64, device=device)
+
+    def run(self, X, offsets, feat, R, stream=None):
+        """X: concatenated (n_total, 2) float32 CUDA tensor; offsets: nsets + 1
+        row offsets (host); feat (nsets, FEAT_DIM) and R (nsets, P_0, P_1)
+        receive the features and the autocorrelations."""
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        B = int(off.shape[0]) - 1
+        if B < 0 or B > self.nsets_max or int(off[-1]) > self.n_total_max:
+            raise ValueError("batch larger than this BatchPrep was made for")
+        if X.dim() != 2 or X.shape[1] != 2 or not X.is_contiguous() or X.dtype.itemsize != 4 \
+                or not X.is_cuda or X.shape[0] < int(off[-1]):
+            raise ValueError("X must be a contiguous (n_total, 2) float32 CUDA tensor")
+        if feat.shape[0] < B or R.shape[0] < B or not feat.is_contiguous() or not R.is_contiguous():
+            raise ValueError("feat and R need one contiguous row per dataset")
+        _check(lib().kde_prepare2_batch(
+            self.plan.handle, B, _ptr(X), off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+            _ptr(self.counts), _ptr(self.moments), _ptr(feat), _ptr(R), _ptr(self.ws),
+            self.ws.numel() * self.ws.element_size(), _stream_ptr(stream)))
+        return feat, R
 
 
 def kde_gemm_bf16(A, B, C=None, status=None, stream=None):

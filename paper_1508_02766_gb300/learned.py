@@ -64,6 +64,12 @@ def normal_reference_theta(n):
     return np.array([0.5 * math.log(h2), 0.0, 0.5 * math.log(h2)])
 
 
+def normal_reference_thetas(ns):
+    """normal_reference_theta for every sample count in ns (B x 3)."""
+    h = 0.5 * np.log((4.0 / 4.0) ** (2.0 / 6.0) * np.asarray(ns, dtype=np.float64) ** (-2.0 / 6.0))
+    return np.stack([h, np.zeros_like(h), h], axis=1)
+
+
 NEIGHBOUR_OFFSETS = np.array(list(itertools.product((-1, 0, 1), repeat=3)), dtype=np.float64)
 
 
@@ -106,6 +112,9 @@ class LscvScorer:
         self.cand_H = thetas_to_H(cand)
         # the plain search scores the same candidates on every dataset
         self.cand_set = kde.LscvCands(self.plan, self.cand_H)
+        self.bprep = None   # batched preparation, sized on first use
+        self.bws = None     # workspace of the batched plain search
+        self.tws = None     # workspace of the device-built candidates
 
     def prepare(self, X, feat=None, R=None):
         """X: n x 2 float32 CUDA tensor of one dataset.  Features go to feat
@@ -135,6 +144,54 @@ class LscvScorer:
     def moments(self):
         return self.mom.cpu().numpy()
 
+    def concat(self, datasets):
+        """One (n_total, 2) float32 CUDA tensor and the host row offsets of
+        a list of datasets (numpy arrays or CUDA tensors), in one upload."""
+        torch = self.torch
+        ns = [int(X.shape[0]) for X in datasets]
+        off = np.zeros(len(ns) + 1, dtype=np.int64)
+        off[1:] = np.cumsum(ns)
+        if datasets and torch.is_tensor(datasets[0]):
+            Xc = torch.cat([X.to(self.device, torch.float32) for X in datasets]).contiguous()
+        else:
+            Xc = torch.from_numpy(np.ascontiguousarray(
+                np.concatenate(datasets).astype(np.float32, copy=False))).to(self.device)
+        return Xc, off
+
+    def prepare_batch(self, X, offsets, F=None, Rs=None):
+        """The preparation of many datasets in one call (kde_prepare2_batch):
+        X the concatenated samples (CUDA), offsets their host row offsets.
+        Returns features (B x FEAT_DIM), autocorrelations (B x P_0 x P_1) and
+        the sample counts (numpy)."""
+        torch = self.torch
+        off = np.asarray(offsets, dtype=np.int64)
+        B, total = len(off) - 1, int(off[-1])
+        if self.bprep is None or B > self.bprep.nsets_max or total > self.bprep.n_total_max:
+            nb = max(B, self.bprep.nsets_max if self.bprep else 0)
+            nt = max(total, self.bprep.n_total_max if self.bprep else 0)
+            self.bprep = kde.BatchPrep(self.plan, nb, nt, device=self.device)
+        info = self.plan.info
+        if F is None:
+            F = torch.empty(B, kde.FEAT_DIM, dtype=torch.float32, device=self.device)
+        if Rs is None:
+            Rs = torch.empty(B, info.P[0], info.P[1], dtype=torch.float32, device=self.device)
+        self.bprep.run(X, off, F, Rs)
+        return F, Rs, np.diff(off)
+
+    def search_batch(self, Rs, ns):
+        """The plain method on many datasets: every candidate scored against
+        every autocorrelation in one call, argmin per dataset on the device.
+        Returns (thetas B x 3, LSCV minima B)."""
+        torch = self.torch
+        B = len(ns)
+        need = self.cand_set.batch_workspace_bytes(B)
+        if self.bws is None or self.bws.numel() < need:
+            self.bws = torch.empty(max(256, need), dtype=torch.uint8, device=self.device)
+        s = self.cand_set.score_batch(ns, Rs, workspace=self.bws)
+        v, i = torch.min(s, dim=1)
+        i = i.cpu().numpy()
+        return self.cand[i], v.cpu().numpy()
+
 
 @dataclass
 class LabelledSet:
@@ -144,20 +201,22 @@ class LabelledSet:
     n: np.ndarray          # D
 
 
-def label_datasets(scorer, datasets):
-    """Features and plain-search labels for every dataset."""
-    torch = scorer.torch
+def label_datasets(scorer, datasets, batch=256):
+    """Features and plain-search labels for every dataset, batch datasets
+    per call: one upload, one batched preparation, one batched search."""
     D = len(datasets)
     feats = np.empty((D, kde.FEAT_DIM), dtype=np.float32)
     theta = np.empty((D, 3))
     best = np.empty(D)
     ns = np.empty(D, dtype=np.int64)
-    for i, X in enumerate(datasets):
-        Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(scorer.device)
-        f = scorer.prepare(Xd)
-        theta[i], best[i] = scorer.search()
-        feats[i] = f.cpu().numpy()
-        ns[i] = X.shape[0]
+    for b0 in range(0, D, batch):
+        part = datasets[b0:b0 + batch]
+        Xc, off = scorer.concat(part)
+        F, Rs, n = scorer.prepare_batch(Xc, off)
+        th, v = scorer.search_batch(Rs, n)
+        b1 = b0 + len(part)
+        theta[b0:b1], best[b0:b1], ns[b0:b1] = th, v, n
+        feats[b0:b1] = F.cpu().numpy()
     return LabelledSet(feats, theta, best, ns)
 
 
@@ -213,35 +272,64 @@ def select(scorer, mlp, X, refine=True, fallback=True, scored=None):
     return cands[i], float(s[i]), len(H), False
 
 
-def select_batch(scorer, mlp, datasets, fallback=True, scored=None):
+def select_batch(scorer, mlp, datasets, fallback=True, scored=None, offsets=None,
+                 device_candidates=True):
     """The learned method on many datasets at once: features and
-    autocorrelations of every dataset, one network forward pass for the
-    batch (at most mlp.max_batch rows per pass), then the 27-candidate
-    neighbourhoods and normal-reference scores of every dataset enqueued
-    before one host synchronisation; datasets whose proposal is worse than
-    the normal-reference score fall back to the plain search.  Returns a list
-    of (theta, lscv, candidates scored, fell back)."""
+    autocorrelations of every dataset in one batched preparation call, one
+    network forward pass for the batch (at most mlp.max_batch rows per
+    pass), then the 27-candidate neighbourhoods and normal-reference scores
+    of every dataset enqueued before one host synchronisation; datasets
+    whose proposal is worse than the normal-reference score fall back to the
+    plain search.  datasets: a list of datasets, or, with offsets (host row
+    offsets), their samples already concatenated in one CUDA tensor.  With
+    device_candidates the candidates are built and scored on the device
+    from the network's output (kde_lscv_theta_select); otherwise they are
+    built on the host and scored by kde_lscv_autocorr_batch.
+    Returns a list of (theta, lscv, candidates scored, fell back)."""
     torch = scorer.torch
     dev = scorer.device
-    B = len(datasets)
-    info = scorer.plan.info
-    F = torch.empty(B, kde.FEAT_DIM, dtype=torch.float32, device=dev)
-    Rs = torch.empty(B, info.P[0], info.P[1], dtype=torch.float32, device=dev)
-    ns = []
-    for i, X in enumerate(datasets):
-        Xd = X if torch.is_tensor(X) else torch.from_numpy(np.ascontiguousarray(X)).to(dev)
-        scorer.prepare(Xd, feat=F[i], R=Rs[i])
-        ns.append(int(Xd.shape[0]))
+    if offsets is None:
+        Xc, off = scorer.concat(datasets)
+    else:
+        Xc, off = datasets, np.asarray(offsets, dtype=np.int64)
+    B = len(off) - 1
+    F, Rs, ns = scorer.prepare_batch(Xc, off)
+    ns = [int(v) for v in ns]
     TH = torch.empty(B, 3, dtype=torch.float32, device=dev)
     for s0 in range(0, B, mlp.max_batch):
         mlp.forward(F[s0:s0 + mlp.max_batch], Y=TH[s0:s0 + mlp.max_batch])
-    mlp.check()
-    TH = TH.cpu().numpy().astype(np.float64)
     lo = np.array([A_GRID[0], BETA_GRID[0], C_GRID[0]]) - 0.5 * STEP
     hi = np.array([A_GRID[-1], BETA_GRID[-1], C_GRID[-1]]) + 0.5 * STEP
+    if device_candidates:
+        offs = 0.5 * NEIGHBOUR_OFFSETS * STEP
+        refs = normal_reference_thetas(ns)
+        need = kde.lscv_theta_select_workspace_bytes(scorer.plan, B, len(offs))
+        if scorer.tws is None or scorer.tws.numel() < need:
+            scorer.tws = torch.empty(max(256, need), dtype=torch.uint8, device=dev)
+        out = kde.kde_lscv_theta_select(scorer.plan, ns, TH, lo, hi, offs, refs, Rs,
+                                        workspace=scorer.tws)
+        mlp.check()
+        o = out.cpu().numpy()
+        base = np.clip(TH.cpu().numpy().astype(np.float64), lo, hi)
+        if scored is not None:
+            scored.extend(thetas_to_H(np.concatenate(
+                [base[:, None, :] + offs, refs[:, None, :]], axis=1)).reshape(-1, 2, 2))
+        res = []
+        for i in range(B):
+            j, v, vref = int(o[i, 0]), float(o[i, 1]), float(o[i, 2])
+            if j >= len(offs) or (fallback and v > vref):
+                t, v2 = scorer.search(R=Rs[i], n=ns[i])
+                if scored is not None:
+                    scored.extend(scorer.cand_H)
+                res.append((t, v2, 28 + len(scorer.cand), True))
+            else:
+                res.append((base[i] + offs[j], v, 28, False))
+        return res
+    mlp.check()
+    TH = TH.cpu().numpy().astype(np.float64)
     # every dataset's 27 neighbours and its normal-reference bandwidth, at once
     cands = neighbourhood(np.clip(TH, lo, hi))                        # B x 27 x 3
-    refs = np.stack([normal_reference_theta(n) for n in ns])          # B x 3
+    refs = normal_reference_thetas(ns)                                # B x 3
     Hs = thetas_to_H(np.concatenate([cands, refs[:, None, :]], axis=1))  # B x 28 x 2 x 2
     out = kde.kde_lscv_autocorr_batch(scorer.plan, ns, Hs, Rs, workspace=scorer.lws)
     if scored is not None:

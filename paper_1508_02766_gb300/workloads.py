@@ -237,6 +237,37 @@ def ragged64_f32(seed=5, count=64):
     return out
 
 
+def mixture_dataset_chunk(seed, chunk, count, n=10_000):
+    """Chunk `chunk` of a stream of learned-proposal datasets, as one
+    count x n x 2 float32 array: the recipe of mixture_datasets (2-5
+    components, weights Dirichlet(2), means U[-3, 3]^2, covariances
+    Q diag(s1, s2) Q^T with s ~ exp(U[log 0.05, log 1.5]) and Q a random
+    rotation), with the component sizes drawn multinomially and each
+    component's samples stored together.  Chunks are seeded by (seed,
+    chunk), so any subset can be drawn in any order or process."""
+    rng = np.random.default_rng([seed, chunk])
+    out = np.empty((count, n, 2), dtype=np.float32)
+    z = rng.standard_normal((count, n, 2), dtype=np.float32)
+    for b in range(count):
+        k = int(rng.integers(2, 6))
+        w = rng.dirichlet(np.full(k, 2.0))
+        means = rng.uniform(-3.0, 3.0, size=(k, 2)).astype(np.float32)
+        ang = rng.uniform(0.0, np.pi, size=k)
+        sd = np.sqrt(np.exp(rng.uniform(np.log(0.05), np.log(1.5), size=(k, 2))))
+        sizes = rng.multinomial(n, w)
+        a = 0
+        for j in range(k):
+            c, s = np.cos(ang[j]), np.sin(ang[j])
+            # Q diag(sd): its product with its transpose is the covariance
+            A = np.array([[c * sd[j, 0], -s * sd[j, 1]], [s * sd[j, 0], c * sd[j, 1]]],
+                         dtype=np.float32)
+            e = a + int(sizes[j])
+            np.matmul(z[b, a:e], A.T, out=out[b, a:e])
+            out[b, a:e] += means[j]
+            a = e
+    return out
+
+
 def mixture_datasets(seed, count, n=10_000):
     """Datasets for the learned bandwidth proposal: 2-D Gaussian mixtures with
     2-5 components, weights Dirichlet(2), means U[-3, 3]^2 and covariances

@@ -183,3 +183,21 @@ def test_bin_workspace_sizes():
         # a 16-byte record per tile a sample touches (at most 2^d), plus tables
         assert b >= (16 << d) * n
         assert b < (16 << d) * n + (8 << 20)
+
+
+def test_batch_preparation_and_search_reject_bad_handles():
+    """Host checks of the batched calls run before any device work: a NULL
+    plan or candidate set, or too many datasets, is refused."""
+    L = kde.lib()
+    b = ctypes.c_size_t(7)
+    assert L.kde_prepare2_batch_workspace_bytes(None, 4, 100, ctypes.byref(b)) == 1
+    assert L.kde_lscv_autocorr_cands_batch_workspace_bytes(None, 4, ctypes.byref(b)) == 1
+    off = (ctypes.c_int64 * 2)(0, 10)
+    null = ctypes.c_void_p(0)
+    assert L.kde_prepare2_batch(None, 1, null, off, null, null, null, null, null, 0, null) == 1
+    n = (ctypes.c_int64 * 1)(10)
+    assert L.kde_lscv_autocorr_cands_batch(None, 1, n, null, null, null, null, 0, null) == 1
+    d6 = (ctypes.c_double * 6)()
+    assert L.kde_lscv_theta_select(None, 1, n, null, d6, 1, d6, d6, null, null, null, null, 0,
+                                   null) == 1
+    assert L.kde_lscv_theta_select_workspace_bytes(None, 1, 1, ctypes.byref(b)) == 1
