@@ -220,21 +220,51 @@ __global__ void __launch_bounds__(256) kde_bin_sets_kernel(const T* __restrict__
 // ---------------------------------------------------------------------------
 constexpr int kCountThreads = 512;
 constexpr int kScatterThreads = 512;
-constexpr int kScatterU = 4;           // samples per thread per scatter round
+constexpr int kScatterU = 8;           // samples per thread per round, loaded before any is used
 constexpr int kAccumThreads = 512;
 constexpr int kItemRecords = 8192;     // records per work item
 constexpr int kMaxTiles = 16384;       // tiles per grid (shared histograms)
-constexpr int kTileCells = 4096;       // cells per tile (shared accumulators)
+constexpr int kTileCells = 8192;       // cells per tile (shared accumulators)
 
-// Targets of one sample: its base tile, the tile-local base node and the
-// axes along which it also feeds the next tile (base on the tile's last row
-// and a nonzero fraction, so the corner there has a nonzero weight).
+// Tile shape per d: powers of two, kTileCells cells, the last axis the
+// longest so that a tile's rows are long runs of the counts.  ls: strides
+// inside a tile (row-major); bits: bits per axis of a record's packed base.
+template <int D>
+struct Geo;
+template <>
+struct Geo<1> {
+  __host__ __device__ static constexpr int ext(int k) { return k == 0 ? 8192 : 1; }
+  __host__ __device__ static constexpr int lg(int k) { return k == 0 ? 13 : 0; }
+  __host__ __device__ static constexpr int ls(int k) { return k == 0 ? 1 : 0; }
+  __host__ __device__ static constexpr int lsh(int) { return 0; }
+  static constexpr int bits = 16;
+};
+template <>
+struct Geo<2> {
+  __host__ __device__ static constexpr int ext(int k) { return k == 0 ? 64 : k == 1 ? 128 : 1; }
+  __host__ __device__ static constexpr int lg(int k) { return k == 0 ? 6 : k == 1 ? 7 : 0; }
+  __host__ __device__ static constexpr int ls(int k) { return k == 0 ? 128 : k == 1 ? 1 : 0; }
+  __host__ __device__ static constexpr int lsh(int k) { return k == 0 ? 7 : 0; }
+  static constexpr int bits = 8;
+};
+template <>
+struct Geo<3> {
+  __host__ __device__ static constexpr int ext(int k) { return k == 2 ? 32 : 16; }
+  __host__ __device__ static constexpr int lg(int k) { return k == 2 ? 5 : 4; }
+  __host__ __device__ static constexpr int ls(int k) { return k == 0 ? 512 : k == 1 ? 32 : 1; }
+  __host__ __device__ static constexpr int lsh(int k) { return k == 0 ? 9 : k == 1 ? 5 : 0; }
+  static constexpr int bits = 8;
+};
+
+// Targets of one sample: its tile coordinates, the tile-local base node and
+// the axes along which it also feeds the next tile (base on the tile's last
+// row and a nonzero fraction, so the corners there can have weight).
 template <int D>
 struct Target {
-  int tile;      // base tile index
-  int spill;     // bit k: also the next tile along axis k
-  unsigned q[3];
+  int tc[3];     // tile coordinate per axis
   int local[3];  // tile-local base node
+  unsigned q[3];
+  int spill;     // bit k: also the next tile along axis k
 };
 
 template <typename T, int D>
@@ -245,39 +275,56 @@ __device__ __forceinline__ bool sample_target(const T* x, const BinParams<T>& p,
 #pragma unroll
   for (int k = 0; k < D; ++k) in &= axis_position<T>(x[k], p.ax[k], i[k], g.q[k]);
   if (!in) return false;
-  g.tile = 0;
   g.spill = 0;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    const int tk = i[k] >> p.ax[k].tile_log2;
-    g.local[k] = i[k] - (tk << p.ax[k].tile_log2);
-    g.tile += tk * p.ax[k].tstride;
-    if (g.local[k] == p.ax[k].tile - 1 && g.q[k] != 0) g.spill |= 1 << k;
+    g.tc[k] = i[k] >> Geo<D>::lg(k);
+    g.local[k] = i[k] - (g.tc[k] << Geo<D>::lg(k));
+    if (g.local[k] == Geo<D>::ext(k) - 1 && g.q[k] != 0) g.spill |= 1 << k;
   }
   return true;
 }
 
-// Bits per axis of a record's packed tile-local base node.
-template <int D>
-struct LocalBits {
-  static constexpr int value = D == 1 ? 32 : (D == 2 ? 16 : 10);
-};
+// Tile index of target subset S of a sample's spill axes.
+template <typename T, int D>
+__device__ __forceinline__ int target_tile(const Target<D>& g, int S, const BinParams<T>& p) {
+  int tile = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) tile += (g.tc[k] + ((S >> k) & 1)) * p.ax[k].tstride;
+  return tile;
+}
 
-// Record of a sample for target subset S of its spill axes: the tile index
-// and the packed base node relative to that tile (local - tile extent on the
-// axes in S, stored + 1 in LocalBits<D> bits per axis).
+// Record of a sample for target subset S of its spill axes: {q_0, q_1, q_2,
+// packed} with packed = the base node relative to that tile (local - tile
+// extent on the axes in S, so -1 there), stored + 1 in Geo<D>::bits bits per
+// axis, and in bits 24.. the mask of the 2^d corners (corner c has offset
+// (c >> (d-1-k)) & 1 on axis k) that lie inside the tile and the grid.
 template <typename T, int D>
 __device__ __forceinline__ int record_for(const Target<D>& g, int S, const BinParams<T>& p,
                                           uint4& rec) {
-  int tile = g.tile;
+  int tile = 0, b[D], ext[D];
   unsigned packed = 0;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    const int in_next = (S >> k) & 1;
-    tile += in_next * p.ax[k].tstride;
-    packed |= (unsigned)(g.local[k] - in_next * p.ax[k].tile + 1) << (LocalBits<D>::value * k);
+    const int nx = (S >> k) & 1;
+    const int tck = g.tc[k] + nx;
+    tile += tck * p.ax[k].tstride;
+    b[k] = g.local[k] - nx * Geo<D>::ext(k);
+    ext[k] = min(Geo<D>::ext(k), p.ax[k].M - (tck << Geo<D>::lg(k)));
+    packed |= (unsigned)(b[k] + 1) << (Geo<D>::bits * k);
   }
-  rec = make_uint4(g.q[0], g.q[1], g.q[2], packed);
+  unsigned mask = 0;
+#pragma unroll
+  for (int c = 0; c < (1 << D); ++c) {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int v = b[k] + ((c >> (D - 1 - k)) & 1);
+      ok &= v >= 0 && v < ext[k];
+    }
+    mask |= (unsigned)ok << c;
+  }
+  rec = make_uint4(g.q[0], g.q[1], g.q[2], packed | (mask << 24));
   return tile;
 }
 
@@ -318,14 +365,11 @@ kde_bin_count_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int nti
         ++outside;
         continue;
       }
-      atomicAdd(&hist[g.tile], 1u);
+      atomicAdd(&hist[target_tile<T, D>(g, 0, p)], 1u);
       if (g.spill) {
         for (int S = 1; S < (1 << D); ++S) {
           if (S & ~g.spill) continue;
-          int tile = g.tile;
-#pragma unroll
-          for (int k = 0; k < D; ++k) tile += ((S >> k) & 1) * p.ax[k].tstride;
-          atomicAdd(&hist[tile], 1u);
+          atomicAdd(&hist[target_tile<T, D>(g, S, p)], 1u);
         }
       }
     }
@@ -421,8 +465,8 @@ __device__ __forceinline__ int64_t tile_cell(const BinParams<T>& p, int t, int j
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const int tk = (t / p.ax[k].tstride) % p.ax[k].ntiles;
-    const int lk = (j / p.ax[k].lstride) & (p.ax[k].tile - 1);
-    const int c = (tk << p.ax[k].tile_log2) + lk;
+    const int lk = (j >> Geo<D>::lsh(k)) & (Geo<D>::ext(k) - 1);
+    const int c = (tk << Geo<D>::lg(k)) + lk;
     if (c >= p.ax[k].M) return -1;
     idx += (int64_t)c * p.ax[k].stride;
   }
@@ -443,11 +487,10 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int n
                        unsigned rec_cap, unsigned long long* __restrict__ counts) {
   extern __shared__ unsigned next[];   // [ntiles]: next slot of this block per tile
   {
-    const int tile_cells = p.ax[0].lstride * p.ax[0].tile;
-    const int64_t work = (int64_t)meta->nsplit * tile_cells;
+    const int64_t work = (int64_t)meta->nsplit * kTileCells;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < work;
          w += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t idx = tile_cell<T, D>(p, (int)split_list[w / tile_cells], (int)(w % tile_cells));
+      const int64_t idx = tile_cell<T, D>(p, (int)split_list[w / kTileCells], (int)(w % kTileCells));
       if (idx >= 0) counts[idx] = 0;
     }
   }
@@ -487,19 +530,44 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int n
 // kItemRecords = 2^13 records and a record adds to a cell at most once, so
 // neither sum exceeds 2^29 and no carry is ever lost: the cell's total is
 // hi 2^16 + lo exactly.  The adds need no return value (fire-and-forget).
+// A record names the corners it adds to (its mask), so the loop has no
+// per-axis tests; every index is still checked against the tile, so a
+// corrupt record cannot reach outside the shared arrays.
 static_assert(kItemRecords <= (1 << 13), "16-bit split sums must stay below 2^32");
+
+// Offset inside a tile of corner c from the record's base node.
+template <int D>
+__host__ __device__ constexpr int corner_off(int c) {
+  int o = 0;
+  for (int k = 0; k < D; ++k) o += ((c >> (D - 1 - k)) & 1) * Geo<D>::ls(k);
+  return o;
+}
+
+template <int D, int C>
+__device__ __forceinline__ void add_corners(unsigned* lo, unsigned* hi, int j0, unsigned mask,
+                                            const unsigned long long* w) {
+  if constexpr (C < (1 << D)) {
+    constexpr int off = corner_off<D>(C);
+    const int j = j0 + off;
+    if (((mask >> C) & 1) && KDE_DCHECK((unsigned)j < (unsigned)kTileCells, KDE_DBG_BIN_ACCUM) &&
+        (unsigned)j < (unsigned)kTileCells) {
+      atomicAdd(&lo[j], (unsigned)w[C] & 0xFFFFu);
+      atomicAdd(&hi[j], (unsigned)(w[C] >> 16));
+    }
+    add_corners<D, C + 1>(lo, hi, j0, mask, w);
+  }
+}
 
 template <typename T, int D>
 __global__ void __launch_bounds__(kAccumThreads)
 kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ items,
                      const TiledMeta* __restrict__ meta, BinParams<T> p,
                      unsigned long long* __restrict__ counts) {
-  __shared__ unsigned lo[kTileCells], hi[kTileCells];
-  const int tile_cells = p.ax[0].lstride * p.ax[0].tile;
+  extern __shared__ __align__(16) unsigned acc_sm[];
+  unsigned* lo = acc_sm;
+  unsigned* hi = acc_sm + kTileCells;
+  constexpr unsigned kFieldMask = (1u << Geo<D>::bits) - 1u;
   const unsigned nitems = meta->nitems;
-  int lsh[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) lsh[k] = __ffs(p.ax[k].lstride) - 1;
   for (unsigned it = blockIdx.x; it < nitems; it += gridDim.x) {
     const uint4 item = items[it];
     // the tile's origin and extent inside the grid
@@ -508,56 +576,33 @@ kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ i
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const int tk = ((int)item.x / p.ax[k].tstride) % p.ax[k].ntiles;
-      const int o = tk << p.ax[k].tile_log2;
+      const int o = tk << Geo<D>::lg(k);
       origin += (int64_t)o * p.ax[k].stride;
-      ext[k] = min(p.ax[k].tile, p.ax[k].M - o);
+      ext[k] = min(Geo<D>::ext(k), p.ax[k].M - o);
     }
-    for (int j = threadIdx.x; j < tile_cells; j += blockDim.x) {
-      lo[j] = 0;
-      hi[j] = 0;
+    for (int j = threadIdx.x; j < kTileCells / 4; j += blockDim.x) {
+      reinterpret_cast<uint4*>(lo)[j] = make_uint4(0, 0, 0, 0);
+      reinterpret_cast<uint4*>(hi)[j] = make_uint4(0, 0, 0, 0);
     }
     __syncthreads();
     for (unsigned r = item.y + threadIdx.x; r < item.z; r += blockDim.x) {
-      const uint4 rec = __ldg(recs + r);
+      const uint4 rec = __ldcs(recs + r);   // read once: stream past L1
       const unsigned q[3] = {rec.x, rec.y, rec.z};
       int j0 = 0;
-      bool ok0[D], ok1[D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        constexpr int B = LocalBits<D>::value;
-        const unsigned field = B == 32 ? rec.w : (rec.w >> (B * k)) & ((1u << (B % 32)) - 1u);
-        const int bk = (int)field - 1;   // -1 .. tile - 1 for every record scatter writes
-        // corner offset 0 / 1 along axis k lands inside the tile (checked
-        // for any value, so a corrupt record cannot index outside the arrays)
-        ok0[k] = bk >= 0 && bk < p.ax[k].tile;
-        ok1[k] = bk >= -1 && bk < p.ax[k].tile - 1;
-        j0 += bk * p.ax[k].lstride;
-      }
+      for (int k = 0; k < D; ++k)
+        j0 += ((int)((rec.w >> (Geo<D>::bits * k)) & kFieldMask) - 1) * Geo<D>::ls(k);
       unsigned long long w[1 << D];
       corner_weights<D>(q, w);
-#pragma unroll
-      for (int c = 0; c < (1 << D); ++c) {
-        bool inside = w[c] != 0;
-        int j = j0;
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const int bit = (c >> (D - 1 - k)) & 1;
-          inside &= bit ? ok1[k] : ok0[k];
-          j += bit * p.ax[k].lstride;
-        }
-        if (inside && KDE_DCHECK(j >= 0 && j < tile_cells, KDE_DBG_BIN_ACCUM)) {
-          atomicAdd(&lo[j], (unsigned)(w[c] & 0xFFFFu));
-          atomicAdd(&hi[j], (unsigned)(w[c] >> 16));
-        }
-      }
+      add_corners<D, 0>(lo, hi, j0, rec.w >> 24, w);
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < tile_cells; j += blockDim.x) {
+    for (int j = threadIdx.x; j < kTileCells; j += blockDim.x) {
       int64_t idx = origin;
       bool in = true;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const int l = (j >> lsh[k]) & (p.ax[k].tile - 1);
+        const int l = (j >> Geo<D>::lsh(k)) & (Geo<D>::ext(k) - 1);
         in &= l < ext[k];
         idx += (int64_t)l * p.ax[k].stride;
       }
@@ -584,8 +629,8 @@ int num_sms() {
   return sms;
 }
 
-// Tile shape per d (powers of two, kTileCells cells), tile counts and the
-// workspace layout of the tiled path.
+// Tile counts (tile shapes: Geo<d>) and the workspace layout of the tiled
+// path.
 // Grid of the count and scatter kernels (the same in both, and part of the
 // workspace size, so it does not depend on the device): about two blocks per
 // SM of a GB300.
@@ -601,10 +646,9 @@ struct TiledLayout {
 };
 
 bool tiled_layout(int64_t n, int d, const int64_t* M, TiledLayout* t) {
-  static const int kTile[3][3] = {{4096, 0, 0}, {64, 64, 0}, {16, 16, 16}};
   t->ntiles_total = 1;
   for (int k = 0; k < d; ++k) {
-    t->tile[k] = kTile[d - 1][k];
+    t->tile[k] = d == 1 ? Geo<1>::ext(k) : d == 2 ? Geo<2>::ext(k) : Geo<3>::ext(k);
     t->ntiles[k] = (int)((M[k] + t->tile[k] - 1) / t->tile[k]);
     if ((int64_t)t->ntiles_total * t->ntiles[k] > kMaxTiles) return false;
     t->ntiles_total *= t->ntiles[k];
@@ -749,9 +793,15 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
     if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scatter_kernel");
   }
   {
+    auto* fn = kde_bin_accum_kernel<T, D>;
+    const size_t smem = 2 * (size_t)kTileCells * sizeof(unsigned);
+    if ((e = allow_smem(fn, smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kAccumThreads, smem);
+    if (e != cudaSuccess) return kde::cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    const int grid_a = (int)std::min<int64_t>(t.max_items, (int64_t)std::max(1, per_sm) * sms);
     kde::LaunchScope ls("kde_bin_accum_kernel", stream);
-    const int grid_a = (int)std::min<int64_t>(t.max_items, 4LL * sms);
-    kde_bin_accum_kernel<T, D><<<grid_a, kAccumThreads, 0, stream>>>(recs, items, meta, p, counts);
+    fn<<<grid_a, kAccumThreads, smem, stream>>>(recs, items, meta, p, counts);
     if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_accum_kernel");
   }
   return KDE_OK;

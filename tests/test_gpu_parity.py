@@ -261,7 +261,7 @@ def test_tiled_binning_tile_faces(K, d, M):
     """Samples whose base node is the last node of a tile along one or more
     axes feed the neighbouring tile; place many samples there and on nodes."""
     rng = np.random.default_rng(31 + d)
-    tile = {1: (4096,), 2: (64, 64), 3: (16, 16, 16)}[d]
+    tile = {1: (8192,), 2: (64, 128), 3: (16, 16, 32)}[d]
     n = 20000
     faces = [np.arange(t - 1, m - 1, t) for t, m in zip(tile, M)]
     idx = np.stack([rng.choice(f, n) if len(f) else rng.integers(0, m - 1, n)
