@@ -344,9 +344,10 @@ kde_status kde_lscv_autocorr_cands_batch_workspace_bytes(kde_lscv_cands cands, i
  * (the host path's steps), then the LSCV of kde_lscv_autocorr against R
  * (device, nsets x P_0 x P_1 FP32) with n[s] samples (host).  A candidate
  * whose support does not fit the plan's padding scores +inf (no error).
- * Outputs (device): lscv[s (J + 1) + j] when not NULL; out[3 s ..] = {index
+ * Outputs (device): lscv[s (J + 1) + j] when not NULL; out[6 s ..] = {index
  * of the smallest LSCV among j < J (the first on ties; J if none fits), that
- * LSCV, the reference candidate's LSCV}.  KDE_F32 2-D plans.  workspace: at
+ * LSCV, the reference candidate's LSCV, that candidate's theta (3 values; 0
+ * if none fits)}.  KDE_F32 2-D plans.  workspace: at
  * least kde_lscv_theta_select_workspace_bytes(plan, nsets, J), 256-byte
  * aligned; the host inputs are copied from pageable memory, so the call is
  * not for CUDA-graph capture.  (Not in the paper.) */
@@ -578,6 +579,10 @@ kde_status kde_mlp_loss_grad(kde_mlp mlp, const float* X, const float* T, int B,
 kde_status kde_mlp_train_step(kde_mlp mlp, const float* X, const float* T, int B, float lr,
                               float* loss, kde_stream_t stream);
 kde_status kde_mlp_status(kde_mlp mlp, int* flag);
+/* The same flag copied, in stream order and without synchronising, into
+ * *dst (one int, device or page-locked host memory), for callers that read
+ * it together with other results. */
+kde_status kde_mlp_status_copy(kde_mlp mlp, int* dst, kde_stream_t stream);
 
 /* The tensor-core matrix product behind the network, exposed for testing:
  * C[M x N] (FP32, row stride ldc) = A[M x K] B[N x K]^T with A and B BF16

@@ -29,6 +29,7 @@
 
 #include "kde_debug.cuh"
 #include "kde_internal.h"
+#include "pdl.cuh"
 
 namespace {
 
@@ -153,6 +154,9 @@ __device__ __forceinline__ void bin_direct_body(const T* __restrict__ X, int64_t
 #pragma unroll
       for (int k = 0; k < D; ++k) xs[u][k] = s < n ? X[s * D + k] : T(0);
     }
+    // launched as a dependent of the kernel that zeroes the counts: the
+    // samples' loads above overlap it; the adds below wait for it
+    kde::pdl_wait();
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (s0 + u * step >= n) break;
@@ -200,7 +204,27 @@ __global__ void __launch_bounds__(256) kde_bin_kernel(const T* __restrict__ X, i
                                                       BinParams<T> p,
                                                       unsigned long long* __restrict__ counts,
                                                       unsigned long long* __restrict__ n_out) {
+  // X is complete before the zeroing kernel starts; the counts and n_out
+  // are touched only after bin_direct_body's pdl_wait
+  kde::pdl_trigger();
   bin_direct_body<T, D>(X, n, p, counts, n_out, blockIdx.x, gridDim.x);
+}
+
+// Zeroes the counts before kde_bin_kernel (an ordinary launch, so it starts
+// after everything before it on the stream; the binning kernel after it is
+// a programmatic dependent).
+__global__ void __launch_bounds__(256) kde_zero_counts_kernel(unsigned long long* __restrict__ c,
+                                                              int64_t cells) {
+  kde::pdl_trigger();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (((uintptr_t)c & 15) == 0) {
+    ulonglong2* c2 = reinterpret_cast<ulonglong2*>(c);
+    for (; i < cells / 2; i += stride) c2[i] = make_ulonglong2(0, 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (cells & 1)) c[cells - 1] = 0;
+  } else {
+    for (; i < cells; i += stride) c[i] = 0;
+  }
 }
 
 // Many datasets on one grid: blockIdx.y is the dataset, whose samples are
@@ -706,8 +730,14 @@ template <typename T>
 kde_status launch_direct(const T* X, int64_t n, int d, const double* lo, const double* hi,
                          const int64_t* M, unsigned long long* counts, int64_t cells,
                          unsigned long long* n_out, cudaStream_t stream) {
-  cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)cells * sizeof(int64_t), stream);
-  if (e != cudaSuccess) return kde::cuda_fail(e, "cudaMemsetAsync(counts)");
+  cudaError_t e;
+  {
+    const int64_t want = (cells / 2 + 255) / 256;
+    const int zb = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
+    kde::LaunchScope ls("kde_zero_counts_kernel", stream);
+    kde_zero_counts_kernel<<<zb, 256, 0, stream>>>(counts, cells);
+    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_zero_counts_kernel");
+  }
   if (n == 0) return KDE_OK;
   BinParams<T> p = make_params<T>(d, lo, hi, M, nullptr);
   int64_t want = (2 * n + 255) / 256;  // two lanes per sample
@@ -715,11 +745,11 @@ kde_status launch_direct(const T* X, int64_t n, int d, const double* lo, const d
   int blocks = (int)(want < cap ? want : cap);
   kde::LaunchScope ls("kde_bin_kernel", stream);
   switch (d) {
-    case 1: kde_bin_kernel<T, 1><<<blocks, 256, 0, stream>>>(X, n, p, counts, n_out); break;
-    case 2: kde_bin_kernel<T, 2><<<blocks, 256, 0, stream>>>(X, n, p, counts, n_out); break;
-    default: kde_bin_kernel<T, 3><<<blocks, 256, 0, stream>>>(X, n, p, counts, n_out); break;
+    case 1: e = kde::launch_pdl(kde_bin_kernel<T, 1>, blocks, 256, 0, stream, X, n, p, counts, n_out); break;
+    case 2: e = kde::launch_pdl(kde_bin_kernel<T, 2>, blocks, 256, 0, stream, X, n, p, counts, n_out); break;
+    default: e = kde::launch_pdl(kde_bin_kernel<T, 3>, blocks, 256, 0, stream, X, n, p, counts, n_out); break;
   }
-  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   return e == cudaSuccess ? KDE_OK : kde::cuda_fail(e, "kde_bin_kernel launch");
 }
 

@@ -994,11 +994,14 @@ __global__ void __launch_bounds__(32) kde_lscv_ac_reduce_kernel(const AcGen<T>* 
 // many autocorrelations: blockIdx.y is the dataset (its n in nset[y], its
 // partials at y nunits), outputs at y nH_all + i.
 template <typename T>
-__global__ void __launch_bounds__(32) kde_lscv_ac_reduce_sets_kernel(
+__global__ void __launch_bounds__(256) kde_lscv_ac_reduce_sets_kernel(
     const AcGen<T>* __restrict__ gens, const double* __restrict__ kn,
-    const double* __restrict__ nset, const double* __restrict__ partial, int nunits,
+    const double* __restrict__ nset, const double* __restrict__ partial, int nunits, int nh,
     int64_t nH_all, double* __restrict__ S_out, double* __restrict__ lscv_out) {
-  const int i = blockIdx.x;
+  // one warp per candidate, eight per block
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= nh) return;
+  const int lane = threadIdx.x & 31;
   const int64_t y = blockIdx.y;
   partial += y * nunits;
   double s[2];
@@ -1006,12 +1009,12 @@ __global__ void __launch_bounds__(32) kde_lscv_ac_reduce_sets_kernel(
   for (int h = 0; h < 2; ++h) {
     const int u0 = gens[2 * i + h].u0, nu = gens[2 * i + h].nu;
     double v = 0.0;
-    for (int j = threadIdx.x; j < nu; j += 32) v += partial[u0 + j];
+    for (int j = lane; j < nu; j += 32) v += partial[u0 + j];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     s[h] = __shfl_sync(0xffffffffu, v, 0);
   }
-  if (threadIdx.x == 0) {
+  if (lane == 0) {
     if (S_out) {
       S_out[2 * (y * nH_all + i)] = s[0];
       S_out[2 * (y * nH_all + i) + 1] = s[1];
@@ -1131,12 +1134,14 @@ __global__ void __launch_bounds__(256) kde_lscv_theta_sums_kernel(const AcGen<fl
 // One warp per dataset: LSCV of its J + 1 candidates (optionally stored),
 // the first index of the smallest among the first J (a candidate that does
 // not fit counts as +inf) and out[s] = {that index, its LSCV, the reference
-// candidate's LSCV}.
-__global__ void __launch_bounds__(32) kde_lscv_theta_pick_kernel(int J, const double* __restrict__ n_all,
-                                                                 const double* __restrict__ K0,
+// candidate's LSCV, that candidate's theta}.
+__global__ void __launch_bounds__(32) kde_lscv_theta_pick_kernel(ThetaArgs t,
                                                                  const double* __restrict__ S,
                                                                  double* __restrict__ lscv,
                                                                  double* __restrict__ out) {
+  const int J = t.J;
+  const double* __restrict__ n_all = t.n;
+  const double* __restrict__ K0 = t.K0;
   const int s = blockIdx.x;
   const double n = n_all[s];
   double best = HUGE_VAL;
@@ -1165,9 +1170,19 @@ __global__ void __launch_bounds__(32) kde_lscv_theta_pick_kernel(int J, const do
     ref = fmin(ref, __shfl_down_sync(0xffffffffu, ref, off));
   }
   if (threadIdx.x == 0) {
-    out[3 * s] = (double)bi;
-    out[3 * s + 1] = best;
-    out[3 * s + 2] = ref;
+    double th[3] = {0.0, 0.0, 0.0};
+    if (bi < J)
+      for (int k = 0; k < 3; ++k) {
+        const double v = (double)t.theta[3 * s + k];
+        th[k] = fmin(fmax(v, t.box_lo[k]), t.box_hi[k]) + t.off[3 * bi + k];
+      }
+    double* o = out + 6 * (int64_t)s;
+    o[0] = (double)bi;
+    o[1] = best;
+    o[2] = ref;
+    o[3] = th[0];
+    o[4] = th[1];
+    o[5] = th[2];
   }
 }
 
@@ -2436,7 +2451,7 @@ extern "C" kde_status kde_lscv_autocorr_cands_batch(kde_lscv_cands cands, int ns
     const char* img = (const char*)ch.dev;
     const double* kn_dev = (const double*)(img + 2 * ch.nh * gsz);
     const int2* units_dev = (const int2*)((const char*)kn_dev + 2 * ch.nh * sizeof(double));
-    const dim3 g1((unsigned)ch.nunits, (unsigned)nsets), g2((unsigned)ch.nh, (unsigned)nsets);
+    const dim3 g1((unsigned)ch.nunits, (unsigned)nsets), g2((unsigned)((ch.nh + 7) / 8), (unsigned)nsets);
     double* S = pair_sums ? pair_sums + 2 * ch.c0 : nullptr;
     {
       LaunchScope ls("kde_lscv_ac_kernel", st);
@@ -2453,11 +2468,13 @@ extern "C" kde_status kde_lscv_autocorr_cands_batch(kde_lscv_cands cands, int ns
     {
       LaunchScope ls("kde_lscv_ac_reduce_sets_kernel", st);
       if (f32)
-        kde_lscv_ac_reduce_sets_kernel<float><<<g2, 32, 0, st>>>(
-            (const AcGen<float>*)img, kn_dev, nset, partial, ch.nunits, cands->nH, S, lscv + ch.c0);
+        kde_lscv_ac_reduce_sets_kernel<float><<<g2, 256, 0, st>>>(
+            (const AcGen<float>*)img, kn_dev, nset, partial, ch.nunits, ch.nh, cands->nH, S,
+            lscv + ch.c0);
       else
-        kde_lscv_ac_reduce_sets_kernel<double><<<g2, 32, 0, st>>>(
-            (const AcGen<double>*)img, kn_dev, nset, partial, ch.nunits, cands->nH, S, lscv + ch.c0);
+        kde_lscv_ac_reduce_sets_kernel<double><<<g2, 256, 0, st>>>(
+            (const AcGen<double>*)img, kn_dev, nset, partial, ch.nunits, ch.nh, cands->nH, S,
+            lscv + ch.c0);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_lscv_ac_reduce_sets_kernel");
     }
   }
@@ -2568,7 +2585,7 @@ extern "C" kde_status kde_lscv_theta_select(kde_plan plan, int nsets, const int6
   }
   {
     LaunchScope ls("kde_lscv_theta_pick_kernel", st);
-    kde_lscv_theta_pick_kernel<<<nsets, 32, 0, st>>>(J, t.n, t.K0, S, lscv, out);
+    kde_lscv_theta_pick_kernel<<<nsets, 32, 0, st>>>(t, S, lscv, out);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "kde_lscv_theta_pick_kernel");
   }
   return KDE_OK;

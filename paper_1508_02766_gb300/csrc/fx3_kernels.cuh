@@ -117,6 +117,8 @@ __device__ __forceinline__ int p3_slot(int k, int SK) {
 template <int N1, int N2, int N3, int SRC>
 __global__ void __launch_bounds__(kThreads3)
 kde_fx3_rows_fwd_kernel(RowsArgs a, const long long* __restrict__ counts, KGen<float> g) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int N23 = N2 * N3, P = N1 * N23;
   extern __shared__ float2 fx_sm[];
   rows_slab(a, g);
@@ -188,6 +190,8 @@ kde_fx3_rows_fwd_kernel(RowsArgs a, const long long* __restrict__ counts, KGen<f
 
 template <int N1, int N2, int N3>
 __global__ void __launch_bounds__(kThreads3) kde_fx3_rows_c2r_kernel(RowsArgs a) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int N23 = N2 * N3, P = N1 * N23;
   extern __shared__ float2 fx_sm[];
   KGen<float> g_unused;
@@ -245,6 +249,8 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_rows_c2r_kernel(RowsArgs a)
 // (column c, k1, j) at c + j W + k1 SK ------------------------------------------
 template <int N1, int N2, int N3, int MODE>
 __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
+  pdl_trigger();
+  pdl_wait();
   constexpr int N23 = N2 * N3, P = N1 * N23;
   extern __shared__ float2 fx_sm[];
   cols_slab(a);

@@ -38,6 +38,7 @@
 #include "kde_debug.cuh"
 #include "kde_internal.h"
 #include "kgen.cuh"
+#include "pdl.cuh"
 
 namespace kde {
 namespace fx {
@@ -278,6 +279,8 @@ __device__ __forceinline__ void rows_stage_kgen(const RowsArgs& a, const KGen<fl
 template <int CLS, int N1T, int N2T, int SRC>
 __global__ void __launch_bounds__(block_limit<N1T, N2T>())
 kde_fx_rows_fwd_kernel(RowsArgs a, const long long* __restrict__ counts, KGen<float> g) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ float2 fx_sm[];
   rows_slab(a, g);
   if constexpr (SRC == SRC_KGEN) {
@@ -346,6 +349,8 @@ __device__ __forceinline__ void rows_a_inv(const RowsArgs& a, const float2* sm) 
 template <int CLS, int N1T, int N2T>
 __global__ void __launch_bounds__(block_limit<N1T, N2T>())
 kde_fx_rows_c2r_kernel(RowsArgs a) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ float2 fx_sm[];
   KGen<float> g_unused;
   rows_slab(a, g_unused);
@@ -529,6 +534,8 @@ __device__ __forceinline__ void cols_a_inv(const ColsArgs& a, const float2* sm) 
 template <int CLS, int N1T, int N2T, int MODE>
 __global__ void __launch_bounds__(block_limit<N1T, N2T>())
 kde_fx_cols_kernel(ColsArgs a) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ float2 fx_sm[];
   cols_slab(a);
   if constexpr (MODE == COL_INV) {
@@ -584,13 +591,15 @@ cudaError_t allow_smem(F* fn) {
   return e;
 }
 
+// Every pass kernel starts with pdl_trigger(); pdl_wait(); so it may be
+// launched as a programmatic dependent of the kernel before it.
 template <typename Kern, typename... Args>
 cudaError_t launch_kernel(Kern* fn, dim3 grid, int threads, size_t smem, cudaStream_t st,
                           Args... args) {
   cudaError_t e = allow_smem(fn);
   if (e != cudaSuccess) return e;
-  fn<<<grid, threads, smem, st>>>(args...);
-  return cudaGetLastError();
+  e = launch_pdl(fn, grid, dim3(threads), smem, st, args...);
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 struct Launch {

@@ -903,6 +903,13 @@ kde_status kde_mlp_status(kde_mlp m, int* flag) {
   return e == cudaSuccess ? KDE_OK : cuda_fail(e, "kde_mlp_status");
 }
 
+kde_status kde_mlp_status_copy(kde_mlp m, int* dst, kde_stream_t stream) {
+  if (!m || !dst) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  cudaError_t e = cudaMemcpyAsync(dst, m->status, sizeof(int), cudaMemcpyDefault,
+                                  (cudaStream_t)stream);
+  return e == cudaSuccess ? KDE_OK : cuda_fail(e, "kde_mlp_status_copy");
+}
+
 kde_status kde_standardize2(const float* X, int64_t n, float* Z, double* moments,
                             kde_stream_t stream) {
   if (!X || !Z || !moments || n < 2) return fail(KDE_ERR_INVALID_ARG, "bad standardisation input");

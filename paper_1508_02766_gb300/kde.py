@@ -74,7 +74,7 @@ EXPORTS = [
     "kde_batch_set_queue_order", "kde_debug_status", "kde_prepare2_batch",
     "kde_prepare2_batch_workspace_bytes", "kde_lscv_autocorr_cands_batch",
     "kde_lscv_autocorr_cands_batch_workspace_bytes", "kde_lscv_theta_select",
-    "kde_lscv_theta_select_workspace_bytes",
+    "kde_lscv_theta_select_workspace_bytes", "kde_mlp_status_copy",
 ]
 FEAT_DIM = 1088
 
@@ -133,6 +133,7 @@ def lib():
     L.kde_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, vp]
     L.kde_mlp_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, vp, vp]
     L.kde_mlp_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.kde_mlp_status_copy.argtypes = [vp, vp, vp]
     L.kde_gemm_bf16.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp,
                                 ctypes.c_int, vp, ctypes.c_int, vp, vp]
     L.kde_fft_eval_multi.argtypes = [vp, i64, ctypes.c_int, dp, vp, vp, vp, ctypes.c_size_t, vp]
@@ -188,7 +189,7 @@ def lib():
                  "kde_prepare2_batch", "kde_prepare2_batch_workspace_bytes",
                  "kde_lscv_autocorr_cands_batch",
                  "kde_lscv_autocorr_cands_batch_workspace_bytes", "kde_lscv_theta_select",
-                 "kde_lscv_theta_select_workspace_bytes"):
+                 "kde_lscv_theta_select_workspace_bytes", "kde_mlp_status_copy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -878,8 +879,9 @@ def kde_lscv_theta_select(plan: Plan, ns, theta, box_lo, box_hi, offsets, ref, R
                           out=None, workspace=None, stream=None):
     """Candidates built on the device (kde_lscv_theta_select): theta (nsets x
     3 FP32 CUDA tensor), box and offsets (J x 3) and ref (nsets x 3) on the
-    host, R the nsets autocorrelations.  Returns out (nsets x 3 FP64 CUDA:
-    best index among the J offsets, its LSCV, the reference's LSCV)."""
+    host, R the nsets autocorrelations.  Returns out (nsets x 6 FP64 CUDA:
+    best index among the J offsets, its LSCV, the reference's LSCV, its
+    theta)."""
     import torch
     ns = np.ascontiguousarray(np.asarray(ns, dtype=np.int64))
     B = int(ns.shape[0])
@@ -891,7 +893,7 @@ def kde_lscv_theta_select(plan: Plan, ns, theta, box_lo, box_hi, offsets, ref, R
     if theta.dtype != torch.float32 or not theta.is_contiguous() or tuple(theta.shape) != (B, 3):
         raise ValueError("theta must be a contiguous (nsets, 3) float32 tensor")
     if out is None:
-        out = torch.empty(B, 3, dtype=torch.float64, device=theta.device)
+        out = torch.empty(B, 6, dtype=torch.float64, device=theta.device)
     if workspace is None:
         workspace = torch.empty(max(256, lscv_theta_select_workspace_bytes(plan, B, J)),
                                 dtype=torch.uint8, device=theta.device)
@@ -1034,3 +1036,10 @@ class MLP:
         network gave up (its last results are then invalid); synchronises."""
         if self.status():
             raise KDEError(6, "a tensor-core wait of the network gave up; results are invalid")
+
+    def status_copy(self, dst, stream=None):
+        """Enqueues a copy of the status flag into dst (one int32, device or
+        pinned host tensor) on the stream, without synchronising; a caller
+        that reads its results anyway then checks dst (kde_mlp_status_copy)."""
+        _check(lib().kde_mlp_status_copy(self.handle, _ptr(dst), _stream_ptr(stream)))
+        return dst

@@ -115,6 +115,7 @@ class LscvScorer:
         self.bprep = None   # batched preparation, sized on first use
         self.bws = None     # workspace of the batched plain search
         self.tws = None     # workspace of the device-built candidates
+        self.mlp_flag = None  # the network's status, copied back with the results
 
     def prepare(self, X, feat=None, R=None):
         """X: n x 2 float32 CUDA tensor of one dataset.  Features go to feat
@@ -273,7 +274,7 @@ def select(scorer, mlp, X, refine=True, fallback=True, scored=None):
 
 
 def select_batch(scorer, mlp, datasets, fallback=True, scored=None, offsets=None,
-                 device_candidates=True):
+                 device_candidates=True, as_arrays=False):
     """The learned method on many datasets at once: features and
     autocorrelations of every dataset in one batched preparation call, one
     network forward pass for the batch (at most mlp.max_batch rows per
@@ -285,7 +286,8 @@ def select_batch(scorer, mlp, datasets, fallback=True, scored=None, offsets=None
     device_candidates the candidates are built and scored on the device
     from the network's output (kde_lscv_theta_select); otherwise they are
     built on the host and scored by kde_lscv_autocorr_batch.
-    Returns a list of (theta, lscv, candidates scored, fell back)."""
+    Returns a list of (theta, lscv, candidates scored, fell back), or with
+    as_arrays (device candidates only) the four as arrays over the batch."""
     torch = scorer.torch
     dev = scorer.device
     if offsets is None:
@@ -308,23 +310,31 @@ def select_batch(scorer, mlp, datasets, fallback=True, scored=None, offsets=None
             scorer.tws = torch.empty(max(256, need), dtype=torch.uint8, device=dev)
         out = kde.kde_lscv_theta_select(scorer.plan, ns, TH, lo, hi, offs, refs, Rs,
                                         workspace=scorer.tws)
-        mlp.check()
+        # the network's status travels with the results: one copy back, no
+        # device-wide synchronisation
+        if scorer.mlp_flag is None:
+            scorer.mlp_flag = torch.zeros(1, dtype=torch.int32, device=dev)
+        mlp.status_copy(scorer.mlp_flag)
         o = out.cpu().numpy()
-        base = np.clip(TH.cpu().numpy().astype(np.float64), lo, hi)
+        if int(scorer.mlp_flag.item()):
+            raise kde.KDEError(6, "a tensor-core wait of the network gave up; results are invalid")
+        J = len(offs)
         if scored is not None:
+            base = o[:, 3:6] - offs[np.minimum(o[:, 0].astype(np.int64), J - 1)]
             scored.extend(thetas_to_H(np.concatenate(
                 [base[:, None, :] + offs, refs[:, None, :]], axis=1)).reshape(-1, 2, 2))
-        res = []
-        for i in range(B):
-            j, v, vref = int(o[i, 0]), float(o[i, 1]), float(o[i, 2])
-            if j >= len(offs) or (fallback and v > vref):
-                t, v2 = scorer.search(R=Rs[i], n=ns[i])
-                if scored is not None:
-                    scored.extend(scorer.cand_H)
-                res.append((t, v2, 28 + len(scorer.cand), True))
-            else:
-                res.append((base[i] + offs[j], v, 28, False))
-        return res
+        # results as arrays; only the datasets that fall back are visited
+        theta, best = o[:, 3:6].copy(), o[:, 1].copy()
+        ncand = np.full(B, 28, dtype=np.int64)
+        fell = (o[:, 0] >= J) | ((o[:, 1] > o[:, 2]) if fallback else False)
+        for i in np.nonzero(fell)[0]:
+            theta[i], best[i] = scorer.search(R=Rs[i], n=ns[i])
+            ncand[i] += len(scorer.cand)
+            if scored is not None:
+                scored.extend(scorer.cand_H)
+        if as_arrays:
+            return theta, best, ncand, fell
+        return [(theta[i], float(best[i]), int(ncand[i]), bool(fell[i])) for i in range(B)]
     mlp.check()
     TH = TH.cpu().numpy().astype(np.float64)
     # every dataset's 27 neighbours and its normal-reference bandwidth, at once

@@ -142,6 +142,7 @@ def test_device_candidates_match_host_candidates(scorer):
         order = np.argsort(ref[i, :-1])
         j = int(o[i, 0])
         assert o[i, 1] == got[i, j] and o[i, 2] == got[i, -1]
+        assert np.array_equal(o[i, 3:6], th_all[i, j])
         if ref[i, order[1]] - ref[i, order[0]] > 1e-6 * abs(ref[i, order[0]]):
             assert j == order[0], i
 
