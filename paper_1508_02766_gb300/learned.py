@@ -115,7 +115,7 @@ class LscvScorer:
         self.bprep = None   # batched preparation, sized on first use
         self.bws = None     # workspace of the batched plain search
         self.tws = None     # workspace of the device-built candidates
-        self.mlp_flag = None  # the network's status, copied back with the results
+        self.th_buf = None    # the network's proposals of a submitted batch
 
     def prepare(self, X, feat=None, R=None):
         """X: n x 2 float32 CUDA tensor of one dataset.  Features go to feat
@@ -303,38 +303,8 @@ def select_batch(scorer, mlp, datasets, fallback=True, scored=None, offsets=None
     lo = np.array([A_GRID[0], BETA_GRID[0], C_GRID[0]]) - 0.5 * STEP
     hi = np.array([A_GRID[-1], BETA_GRID[-1], C_GRID[-1]]) + 0.5 * STEP
     if device_candidates:
-        offs = 0.5 * NEIGHBOUR_OFFSETS * STEP
-        refs = normal_reference_thetas(ns)
-        need = kde.lscv_theta_select_workspace_bytes(scorer.plan, B, len(offs))
-        if scorer.tws is None or scorer.tws.numel() < need:
-            scorer.tws = torch.empty(max(256, need), dtype=torch.uint8, device=dev)
-        out = kde.kde_lscv_theta_select(scorer.plan, ns, TH, lo, hi, offs, refs, Rs,
-                                        workspace=scorer.tws)
-        # the network's status travels with the results: one copy back, no
-        # device-wide synchronisation
-        if scorer.mlp_flag is None:
-            scorer.mlp_flag = torch.zeros(1, dtype=torch.int32, device=dev)
-        mlp.status_copy(scorer.mlp_flag)
-        o = out.cpu().numpy()
-        if int(scorer.mlp_flag.item()):
-            raise kde.KDEError(6, "a tensor-core wait of the network gave up; results are invalid")
-        J = len(offs)
-        if scored is not None:
-            base = o[:, 3:6] - offs[np.minimum(o[:, 0].astype(np.int64), J - 1)]
-            scored.extend(thetas_to_H(np.concatenate(
-                [base[:, None, :] + offs, refs[:, None, :]], axis=1)).reshape(-1, 2, 2))
-        # results as arrays; only the datasets that fall back are visited
-        theta, best = o[:, 3:6].copy(), o[:, 1].copy()
-        ncand = np.full(B, 28, dtype=np.int64)
-        fell = (o[:, 0] >= J) | ((o[:, 1] > o[:, 2]) if fallback else False)
-        for i in np.nonzero(fell)[0]:
-            theta[i], best[i] = scorer.search(R=Rs[i], n=ns[i])
-            ncand[i] += len(scorer.cand)
-            if scored is not None:
-                scored.extend(scorer.cand_H)
-        if as_arrays:
-            return theta, best, ncand, fell
-        return [(theta[i], float(best[i]), int(ncand[i]), bool(fell[i])) for i in range(B)]
+        job = _submit(scorer, mlp, F, Rs, ns, TH, lo, hi)
+        return select_collect(scorer, job, fallback=fallback, scored=scored, as_arrays=as_arrays)
     mlp.check()
     TH = TH.cpu().numpy().astype(np.float64)
     # every dataset's 27 neighbours and its normal-reference bandwidth, at once
@@ -357,3 +327,93 @@ def select_batch(scorer, mlp, datasets, fallback=True, scored=None, offsets=None
         else:
             res.append((cands[i][j], float(s[j]), 28, False))
     return res
+
+
+@dataclass
+class SelectionJob:
+    """A learned selection enqueued on the device (select_submit): its
+    packed results and the network's status are read by select_collect."""
+    out: object          # B x 6 FP64 (pinned host, filled in stream order): best index,
+                         # its LSCV, reference LSCV, theta
+    flag: object         # the network's status word (pinned host int32)
+    done: object         # event recorded after both copies
+    ns: list
+    refs: np.ndarray     # B x 3 reference thetas
+    Rs: object           # the autocorrelations (valid until the next preparation)
+    offs: np.ndarray     # J x 3 neighbourhood offsets
+
+
+def _submit(scorer, mlp, F, Rs, ns, TH, lo, hi):
+    torch = scorer.torch
+    B = len(ns)
+    offs = 0.5 * NEIGHBOUR_OFFSETS * STEP
+    refs = normal_reference_thetas(ns)
+    need = kde.lscv_theta_select_workspace_bytes(scorer.plan, B, len(offs))
+    if scorer.tws is None or scorer.tws.numel() < need:
+        scorer.tws = torch.empty(max(256, need), dtype=torch.uint8, device=scorer.device)
+    out = kde.kde_lscv_theta_select(scorer.plan, ns, TH, lo, hi, offs, refs, Rs,
+                                    workspace=scorer.tws)
+    # results and the network's status go to pinned host memory in stream
+    # order; collecting waits for this batch's event only, not for batches
+    # enqueued after it
+    out_h = torch.empty(B, 6, dtype=torch.float64, pin_memory=True)
+    out_h.copy_(out, non_blocking=True)
+    flag_h = torch.empty(1, dtype=torch.int32, pin_memory=True)
+    mlp.status_copy(flag_h)
+    done = torch.cuda.Event()
+    done.record()
+    return SelectionJob(out_h, flag_h, done, ns, refs, Rs, offs)
+
+
+def select_submit(scorer, mlp, Xc, offsets):
+    """Enqueues the learned selection of a batch (samples concatenated in the
+    CUDA tensor Xc, host row offsets): batched preparation, the network,
+    candidates built and scored on the device.  Nothing is synchronised, so
+    the next batch can be enqueued before this one is collected; buffers
+    are reused in stream order."""
+    torch = scorer.torch
+    off = np.asarray(offsets, dtype=np.int64)
+    B = len(off) - 1
+    F, Rs, ns = scorer.prepare_batch(Xc, off)
+    ns = [int(v) for v in ns]
+    if scorer.th_buf is None or scorer.th_buf.shape[0] < B:
+        scorer.th_buf = torch.empty(max(B, 256), 3, dtype=torch.float32, device=scorer.device)
+    TH = scorer.th_buf[:B]
+    for s0 in range(0, B, mlp.max_batch):
+        mlp.forward(F[s0:s0 + mlp.max_batch], Y=TH[s0:s0 + mlp.max_batch])
+    lo = np.array([A_GRID[0], BETA_GRID[0], C_GRID[0]]) - 0.5 * STEP
+    hi = np.array([A_GRID[-1], BETA_GRID[-1], C_GRID[-1]]) + 0.5 * STEP
+    return _submit(scorer, mlp, F, Rs, ns, TH, lo, hi)
+
+
+def select_collect(scorer, job, fallback=True, scored=None, as_arrays=False, fetch=None):
+    """Reads a submitted selection (one copy back) and runs the plain search
+    for the datasets whose proposal scores worse than the normal reference.
+    fetch(i), when given, returns dataset i's samples for that search (needed
+    once a later batch has been prepared, which reuses the autocorrelation
+    buffer); otherwise the job's autocorrelations are used."""
+    job.done.synchronize()
+    o = job.out.numpy()
+    if int(job.flag[0]):
+        raise kde.KDEError(6, "a tensor-core wait of the network gave up; results are invalid")
+    B, J, offs = len(job.ns), len(job.offs), job.offs
+    if scored is not None:
+        base = o[:, 3:6] - offs[np.minimum(o[:, 0].astype(np.int64), J - 1)]
+        scored.extend(thetas_to_H(np.concatenate(
+            [base[:, None, :] + offs, job.refs[:, None, :]], axis=1)).reshape(-1, 2, 2))
+    # results as arrays; only the datasets that fall back are visited
+    theta, best = o[:, 3:6].copy(), o[:, 1].copy()
+    ncand = np.full(B, 28, dtype=np.int64)
+    fell = (o[:, 0] >= J) | ((o[:, 1] > o[:, 2]) if fallback else False)
+    for i in np.nonzero(fell)[0]:
+        if fetch is None:
+            theta[i], best[i] = scorer.search(R=job.Rs[i], n=job.ns[i])
+        else:
+            scorer.prepare(fetch(int(i)))
+            theta[i], best[i] = scorer.search()
+        ncand[i] += len(scorer.cand)
+        if scored is not None:
+            scored.extend(scorer.cand_H)
+    if as_arrays:
+        return theta, best, ncand, fell
+    return [(theta[i], float(best[i]), int(ncand[i]), bool(fell[i])) for i in range(B)]

@@ -177,3 +177,31 @@ def test_select_batch_device_and_host_candidates_agree(scorer):
         assert fa == fb and ka == kb
         assert abs(va - vb) <= 1e-6 * abs(vb)
         assert np.allclose(ta, tb, atol=1e-12) or abs(va - vb) <= 1e-6 * abs(vb)
+
+
+def test_submitted_batches_collect_like_select_batch(scorer):
+    """Two batches enqueued before either is read back give what
+    select_batch gives each (the autocorrelations of the first stay valid
+    after the second is prepared)."""
+    mlp = kde.MLP(in_dim=kde.FEAT_DIM, hidden=256, out_dim=3, max_batch=256, seed=4)
+    lab = Lm.label_datasets(scorer, W.mixture_datasets(79, 128))
+    Lm.train(mlp, lab.feats, lab.theta, epochs=3, batch=64)
+    a_sets, b_sets = W.mixture_datasets(80, 9), W.mixture_datasets(81, 7)
+    ref_a = Lm.select_batch(scorer, mlp, a_sets, as_arrays=True)
+    ref_b = Lm.select_batch(scorer, mlp, b_sets, as_arrays=True)
+    ja = Lm.select_submit(scorer, mlp, *scorer.concat(a_sets))
+    jb = Lm.select_submit(scorer, mlp, *scorer.concat(b_sets))
+    got_a = Lm.select_collect(scorer, ja, as_arrays=True)
+    got_b = Lm.select_collect(scorer, jb, as_arrays=True)
+    for got, ref in ((got_a, ref_a), (got_b, ref_b)):
+        for g, r in zip(got, ref):
+            assert np.array_equal(g, r)
+    # fallback of a batch collected after another was prepared: every
+    # proposal made worse than the reference by an untrained network
+    bad = kde.MLP(in_dim=kde.FEAT_DIM, hidden=256, out_dim=3, max_batch=256, seed=5)
+    jc = Lm.select_submit(scorer, bad, *scorer.concat(a_sets))
+    Lm.select_submit(scorer, bad, *scorer.concat(b_sets))
+    th, v, c, fb = Lm.select_collect(scorer, jc, as_arrays=True)
+    ref_c = Lm.select_batch(scorer, bad, a_sets, as_arrays=True)
+    for g, r in zip((th, v, c, fb), ref_c):
+        assert np.array_equal(g, r)
