@@ -16,8 +16,11 @@
  *   - d is 1, 2 or 3.  Arrays are row-major with the last axis contiguous.
  *   - Pointers named X, counts, n_outside, Kspec, density and workspace are
  *     CUDA device pointers owned by the caller; the library never frees or
- *     keeps them.  lo, hi, M, H and opts are host pointers read during the
- *     call only.
+ *     keeps them.  X (read once, in order, by binning) and density (written
+ *     once by the last pass) may also be page-locked host memory, which the
+ *     kernels then read or write in place over the host link (unified
+ *     addressing makes such memory device-accessible).  lo, hi, M, H and
+ *     opts are host pointers read during the call only.
  *   - Calls taking a stream are asynchronous on that stream (NULL = legacy
  *     default stream).  Host-side argument checks happen before any launch
  *     and a failed check launches nothing.
