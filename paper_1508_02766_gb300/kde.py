@@ -337,25 +337,27 @@ def bin_workspace(n, d, M, device="cuda"):
 def kde_bin(X, lo, hi, M, counts=None, n_outside=None, workspace=None, method="auto",
             stream=None):
     """Linear binning into int64 counts (units 2^-32).  X: (n, d) float32/float64
-    CUDA tensor.  method "direct" (global atomics), "tiled" (sort by tile,
-    shared-memory accumulation; uses a workspace, allocated here if not
-    given) or "auto" (direct: the faster on every workload measured).  Both
-    methods give bit-identical counts."""
+    CUDA tensor, or a pinned host tensor that the kernels read in place.
+    method "direct" (global atomics), "tiled" (sort by tile, shared-memory
+    accumulation; uses a workspace, allocated here if not given) or "auto"
+    (direct: the faster on every workload measured).  Both methods give
+    bit-identical counts."""
     import torch
-    if not X.is_cuda or X.dim() != 2 or not X.is_contiguous():
-        raise ValueError("X must be a contiguous (n, d) CUDA tensor")
+    if not (X.is_cuda or X.is_pinned()) or X.dim() != 2 or not X.is_contiguous():
+        raise ValueError("X must be a contiguous (n, d) CUDA or pinned host tensor")
     if X.dtype not in (torch.float32, torch.float64):
         raise ValueError("X must be float32 or float64")
     n, d = X.shape
     M = tuple(int(m) for m in M)
+    dev = X.device if X.is_cuda else torch.device("cuda")
     if method == "auto":
         method = "direct"
     if method not in ("direct", "tiled"):
         raise ValueError("method must be 'auto', 'direct' or 'tiled'")
     if counts is None:
-        counts = torch.empty(M, dtype=torch.int64, device=X.device)
+        counts = torch.empty(M, dtype=torch.int64, device=dev)
     if method == "tiled" and workspace is None:
-        workspace = bin_workspace(n, d, M, X.device)
+        workspace = bin_workspace(n, d, M, dev)
     if method == "direct":
         workspace = None
     wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
@@ -379,8 +381,11 @@ def kde_kernel_grid(plan: Plan, n, Kspec=None, workspace=None, stream=None):
 
 
 def kde_fft_eval(plan: Plan, counts, Kspec, density=None, workspace=None, stream=None):
-    """Density on the grid: F^{-1}(F(c) K) cropped to M (Eq. 10, Eq. 14)."""
+    """Density on the grid: F^{-1}(F(c) K) cropped to M (Eq. 10, Eq. 14).
+    density may be a pinned host tensor, which the last pass writes in place."""
     import torch
+    if density is not None and not (density.is_cuda or density.is_pinned()):
+        raise ValueError("density must be a CUDA or pinned host tensor")
     if density is None:
         density = torch.empty(plan.M, dtype=plan.real_dtype(), device="cuda")
     if workspace is None:
