@@ -1425,6 +1425,9 @@ def learned_main(args):
               "kde_rows_r2c_counts_kernel": Bsel * (8.0 * cells + Lm.GRID_M * Q * 8.0),
               "kde_cols_auto_kernel": Bsel * (Lm.GRID_M * Q * 8.0 + P0 * Q * 8.0),
               "kde_rows_c2r_kernel": Bsel * (P0 * Q * 8.0 + P0 * P1 * 4.0)}
+    # the same passes on the two-phase engine
+    for k in ("kde_rows_r2c_counts_kernel", "kde_cols_auto_kernel", "kde_rows_c2r_kernel"):
+        nbytes[k.replace("kde_", "kde_fx_", 1)] = nbytes[k]
     hbm, hbm_kind = peaks()
     if dom == "kde_gemm_tc_kernel":
         ach = flops[dom] / (prof[dom][0] * 1e-3) / 1e12

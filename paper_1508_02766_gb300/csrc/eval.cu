@@ -1791,6 +1791,11 @@ kde_status autocorr_impl(kde_plan_s* plan, const int64_t* counts, void* Rout, vo
   // nsets grids one after another: counts [nsets][M_0][M_1], R [nsets][P_0][P_1]
   V* A = (V*)ws;                                       // [nsets][M_0][Q] half spectra of the rows
   V* B = ws_B ? (V*)ws_B : A + nsets * I.M[0] * I.Q;   // [nsets][P_0][Q] after the axis-0 pass
+  if constexpr (std::is_same<T, float>::value) {
+    if (I.engine == KDE_ENGINE_TWO_PHASE && !plan->dft_tc)
+      return fx_autocorr(plan, reinterpret_cast<const long long*>(counts), (float*)Rout, A, B,
+                         nsets, st);
+  }
   RowsParams<T> rp{};
   rp.nrows = nsets * I.M[0];
   rp.Min = (int)I.M[1];
@@ -1929,9 +1934,7 @@ kde_status lscv_ac_impl(kde_plan_s* plan, int nsets, const int64_t* ns, int nH, 
     int nunits = 0;
     kde_status s = ac_build_chunk<T>(plan, h0, nh, nH, Hs, ns, up, &nunits);
     if (s != KDE_OK) return s;
-    // pageable source: the copy is staged before this call returns
-    cudaError_t e = cudaMemcpyAsync(ws, up.data(), up.size(), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(kernel parameters)");
+    if ((s = upload_async(ws, up.data(), up.size(), st)) != KDE_OK) return s;
     s = ac_launch_chunk<T>(I, ws, nh, nunits, R, partial, 0.0, S_out ? S_out + 2 * h0 : nullptr,
                            lscv_out + h0, st);
     if (s != KDE_OK) return s;
@@ -2070,11 +2073,9 @@ extern "C" kde_status kde_fft_eval_multi(kde_plan plan, int64_t n, int nH, const
   for (int h0 = 0; h0 < nH; h0 += kMultiChunk) {
     const int nh = std::min(kMultiChunk, nH - h0);
     // the chunk's parameters: stream-ordered after the previous chunk's kernels
-    cudaError_t e = cudaMemcpyAsync(ws + m.off_gens, gens.data() + h0, nh * sizeof(KGen<float>),
-                                    cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(ws + m.off_L0, L0.data() + h0, nh * sizeof(int), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(bandwidth table)");
+    if ((s = upload_async(ws + m.off_gens, gens.data() + h0, nh * sizeof(KGen<float>), st)) != KDE_OK ||
+        (s = upload_async(ws + m.off_L0, L0.data() + h0, nh * sizeof(int), st)) != KDE_OK)
+      return s;
     s = fx_eval_batch2(plan, A, nh, (const KGen<float>*)(ws + m.off_gens), (const int*)(ws + m.off_L0),
                        m.Lmax0, (float2*)(ws + m.off_t1), (float*)(ws + m.off_K),
                        (float2*)(ws + m.off_S), (float*)density + (size_t)h0 * cells, st);
@@ -2268,10 +2269,8 @@ extern "C" kde_status kde_prepare2_batch(kde_plan plan, int nsets, const float* 
   char* ws = (char*)workspace;
   int64_t* off_dev = (int64_t*)(ws + L.off_offsets);
   float* Z = (float*)(ws + L.off_Z);
-  // pageable source: staged before this call returns
-  cudaError_t e = cudaMemcpyAsync(off_dev, offsets, (size_t)(nsets + 1) * sizeof(int64_t),
-                                  cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(offsets)");
+  if ((s = upload_async(off_dev, offsets, (size_t)(nsets + 1) * sizeof(int64_t), st)) != KDE_OK)
+    return s;
   if ((s = standardize2_sets(X, off_dev, nsets, Z, moments, st)) != KDE_OK) return s;
   if ((s = bin_sets_f32(Z, off_dev, nsets, n_max, 2, plan->lo, plan->hi, I.M, counts, st)) != KDE_OK)
     return s;
@@ -2442,9 +2441,8 @@ extern "C" kde_status kde_lscv_autocorr_cands_batch(kde_lscv_cands cands, int ns
   cudaStream_t st = (cudaStream_t)stream;
   double* nset = (double*)workspace;
   double* partial = (double*)((char*)workspace + (((size_t)nsets * sizeof(double) + 255) & ~(size_t)255));
-  // pageable source: staged before this call returns
-  cudaError_t e = cudaMemcpyAsync(nset, nd.data(), nd.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(n)");
+  if ((s = upload_async(nset, nd.data(), nd.size() * sizeof(double), st)) != KDE_OK) return s;
+  cudaError_t e = cudaSuccess;
   const bool f32 = I.precision == KDE_F32;
   const size_t gsz = f32 ? sizeof(AcGen<float>) : sizeof(AcGen<double>);
   for (const auto& ch : cands->chunks) {
@@ -2546,9 +2544,8 @@ extern "C" kde_status kde_lscv_theta_select(kde_plan plan, int nsets, const int6
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   double* upd = (double*)(ws + L.off_up);
-  // pageable source: staged before this call returns
-  cudaError_t e = cudaMemcpyAsync(upd, up.data(), up.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(candidate inputs)");
+  if ((s = upload_async(upd, up.data(), up.size() * sizeof(double), st)) != KDE_OK) return s;
+  cudaError_t e = cudaSuccess;
   ThetaArgs t{};
   t.nsets = nsets;
   t.J = J;

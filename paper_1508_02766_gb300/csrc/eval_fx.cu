@@ -183,9 +183,12 @@ kde_status rows_pass(const kde_plan_s* plan, int kind, int64_t nrows, const long
 template <int MODE>
 kde_status cols_pass(const kde_plan_s* plan, int k, const char* name, const float2* in,
                      float2* out, float* out_real, const float* K, int64_t S, int64_t O, int Nin,
-                     int Nout, int Lw, cudaStream_t st, const Batch* bt = nullptr) {
+                     int Nout, int Lw, cudaStream_t st, const Batch* bt = nullptr,
+                     float s_pre = 0.f, float s_post = 0.f) {
   const kde_plan_info& I = plan->info;
   ColsArgs a{};
+  a.s_pre = s_pre;
+  a.s_post = s_post;
   if (bt) {  // slabs are bandwidths
     O = bt->nh;
     a.h_L0 = bt->L0;
@@ -345,6 +348,24 @@ kde_status fx_eval_batch2(kde_plan_s* plan, const float2* A, int nh, const KGen<
   b.slab_in = M0 * Q;
   b.slab_real = M0 * M1;
   return rows_pass(plan, 2, M0, nullptr, 0, 0, nullptr, nullptr, Sb, density, (int)M1, st, b);
+}
+
+// The counts' autocorrelation R = F^{-1}(|F(c)|^2) of nsets grids (2-D,
+// counts [nsets][M_0][M_1] -> R [nsets][P_0][P_1]): rows of every grid to
+// half spectra A, axis 0 forward, |2^-32 z|^2 / (P_0 P_1), inverse (all P_0
+// rows kept) into B, then full rows.  A: nsets M_0 Q, B: nsets P_0 Q complex.
+kde_status fx_autocorr(kde_plan_s* plan, const long long* counts, float* R, float2* A, float2* B,
+                       int64_t nsets, cudaStream_t st) {
+  using namespace fx;
+  const kde_plan_info& I = plan->info;
+  kde_status s = rows_pass(plan, SRC_COUNTS, nsets * I.M[0], counts, (int)I.M[1], I.M[1], nullptr,
+                           A, nullptr, nullptr, 0, st);
+  if (s != KDE_OK) return s;
+  s = cols_pass<COL_MID>(plan, 0, "kde_fx_cols_auto_kernel", A, B, nullptr, nullptr, I.Q, nsets,
+                         (int)I.M[0], (int)I.P[0], -1, st, nullptr, 2.3283064365386963e-10f,
+                         (float)(1.0 / ((double)I.P[0] * (double)I.P[1])));
+  if (s != KDE_OK) return s;
+  return rows_pass(plan, 2, nsets * I.P[0], nullptr, 0, 0, nullptr, nullptr, B, R, (int)I.P[1], st);
 }
 
 // The counts' half spectra (first pass of the evaluation) into A.

@@ -386,6 +386,9 @@ struct ColsArgs {
   // rows with L0 = h_L0[h].
   int64_t slab_in, slab_out, slab_real, slab_K;
   const int* h_L0;
+  // COL_MID with K == NULL: z <- |s_pre z|^2 s_post between the transforms
+  // (the counts' power spectrum, for their autocorrelation)
+  float s_pre, s_post;
 };
 
 // Per-slab view of the arguments (slab = blockIdx.y).
@@ -479,14 +482,22 @@ __device__ __forceinline__ void cols_b_fwd(const ColsArgs& a, float2* sm) {
       out[k * a.S] = y[k2].x;
       if (v1) out[k * a.S + 1] = y[k2].y;
     }
-  } else {  // COL_MID: times K, inverse, back to the same slots
+  } else {  // COL_MID: times K (or the power spectrum), inverse, back to the same slots
     const int64_t s = col_first<MODE>(a) + b;
     const bool v = s < a.S;
+    if (a.K) {
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) {
-      const float kv = v ? __ldg(a.K + (int64_t)(k1 + N1 * k2) * a.S + s) : 0.f;
-      y[k2].x *= kv;
-      y[k2].y *= kv;
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const float kv = v ? __ldg(a.K + (int64_t)(k1 + N1 * k2) * a.S + s) : 0.f;
+        y[k2].x *= kv;
+        y[k2].y *= kv;
+      }
+    } else {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const float re = y[k2].x * a.s_pre, im = y[k2].y * a.s_pre;
+        y[k2] = make_float2((re * re + im * im) * a.s_post, 0.f);
+      }
     }
     b_inv_store<N2>(y, k1, a.tw, src, a.B);
   }

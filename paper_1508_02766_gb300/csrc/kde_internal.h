@@ -41,6 +41,10 @@ kde_status fail(kde_status s, const std::string& msg);
 kde_status matrix_support(const kde_plan_s* plan, const double* A, double* Ainv, double* detA,
                           int64_t* L);
 kde_status cuda_fail(cudaError_t e, const char* what);
+// Asynchronous upload of a small host array (copied into a page-locked
+// staging slot first, so the caller's array may be reused at once).  Not for
+// stream capture: a captured copy would replay the slot's later contents.
+kde_status upload_async(void* dst, const void* src, size_t bytes, cudaStream_t st);
 // K_A(delta o l) = C exp(sum_k D_k (l_k + sum_{j<k} B_kj l_j)^2) from the
 // Cholesky factor of A (no cancellation when A is nearly singular);
 // B = {B_10, B_20, B_21}, entries beyond d zero.
@@ -61,6 +65,8 @@ kde_status fx_kernel_grid(kde_plan_s* plan, const KGen<float>& gen, void* Kspec,
 kde_status fx_fft_eval(kde_plan_s* plan, const long long* counts, const float* Kspec,
                        float* density, void* ws, cudaStream_t st);
 kde_status fx_count_spectra(kde_plan_s* plan, const long long* counts, float2* A, cudaStream_t st);
+kde_status fx_autocorr(kde_plan_s* plan, const long long* counts, float* R, float2* A, float2* B,
+                       int64_t nsets, cudaStream_t st);
 kde_status fx_eval_batch2(kde_plan_s* plan, const float2* A, int nh, const KGen<float>* gens,
                           const int* L0, int Lmax0, float2* t1, float* Kb, float2* Sb,
                           float* density, cudaStream_t st);

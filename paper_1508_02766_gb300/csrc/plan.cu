@@ -35,6 +35,65 @@ kde_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 // ---------------------------------------------------------------------------
+// Small host-to-device uploads of call arguments (offsets, sample counts,
+// per-candidate parameters) through page-locked staging slots, so that the
+// copy is asynchronous: a copy from pageable memory may wait for the stream,
+// which would stop the host from enqueueing the next batch while the GPU
+// works on this one.  Each thread keeps, per device, a ring of slots; a slot
+// is refilled only after the event recorded behind its last copy completed.
+// ---------------------------------------------------------------------------
+namespace {
+struct UploadSlot {
+  void* host = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ev = nullptr;
+  bool pending = false;
+};
+constexpr int kUploadSlots = 8;
+constexpr int kUploadDevices = 64;
+struct UploadRing {
+  UploadSlot slot[kUploadSlots];
+  int next = 0;
+};
+thread_local UploadRing g_upload[kUploadDevices];
+}  // namespace
+
+kde_status upload_async(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return KDE_OK;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kUploadDevices) {   // no ring: a plain (possibly waiting) copy
+    e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    return e == cudaSuccess ? KDE_OK : cuda_fail(e, "cudaMemcpyAsync(upload)");
+  }
+  UploadRing& r = g_upload[dev];
+  UploadSlot& sl = r.slot[r.next];
+  r.next = (r.next + 1) % kUploadSlots;
+  if (sl.pending) {
+    if ((e = cudaEventSynchronize(sl.ev)) != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize(upload)");
+    sl.pending = false;
+  }
+  if (!sl.ev && (e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "cudaEventCreate(upload)");
+  if (sl.cap < bytes) {
+    if (sl.host) cudaFreeHost(sl.host);
+    sl.host = nullptr;
+    sl.cap = 0;
+    const size_t cap = std::max<size_t>(bytes, 64 << 10);
+    if ((e = cudaHostAlloc(&sl.host, cap, cudaHostAllocPortable)) != cudaSuccess)
+      return cuda_fail(e, "cudaHostAlloc(upload)");
+    sl.cap = cap;
+  }
+  std::memcpy(sl.host, src, bytes);
+  if ((e = cudaMemcpyAsync(dst, sl.host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync(upload)");
+  if ((e = cudaEventRecord(sl.ev, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord(upload)");
+  sl.pending = true;
+  return KDE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Launch counting and per-kernel event timing.
 // ---------------------------------------------------------------------------
 static std::atomic<int64_t> g_launches{0};

@@ -301,3 +301,22 @@ def test_many_line_lengths(K, prec):
         f, c_ref, _, _ = oracle_full(w)
         assert rel_err(dens, f) <= TOL[prec], (M, plan.info.P)
     assert seen >= {2, 3, 4, 5, 7, 8}, sorted(seen)
+
+
+def test_direct_binning_after_producer_kernel_and_unaligned_counts(K):
+    """The binning kernel starts as a programmatic dependent of the kernel
+    that zeroes the counts and loads its first samples before it waits:
+    samples written by a kernel just before the call, and counts that start
+    8 bytes past a 16-byte boundary (the zeroing kernel's scalar path),
+    still give the oracle's counts exactly."""
+    w = W.small_case(77, 2, (300, 257), n=200_000, precision="f32")
+    base = torch.from_numpy(np.ascontiguousarray(w.X)).cuda()
+    for _ in range(3):
+        X = (base * 1.0).contiguous()          # produced by a kernel on the stream
+        store = torch.full((300 * 257 + 1,), -3, dtype=torch.int64, device="cuda")
+        counts = store[1:].view(300, 257)       # 8-byte offset
+        K.kde_bin(X, w.lo, w.hi, w.M, counts=counts, method="direct")
+        torch.cuda.synchronize()
+        c_ref, _ = O.bin_linear(w.X, w.lo, w.hi, w.M)
+        assert np.array_equal(counts.cpu().numpy(), c_ref)
+        assert int(store[0].item()) == -3
