@@ -1352,7 +1352,7 @@ def learned_main(args):
     # host's work on one batch overlaps the GPU's on the next
     def collect(b0, k, job):
         nonlocal fell, ncand
-        th, v, c, fb = Lm.select_collect(sc, job, scored=scored, as_arrays=True)
+        th, v, c, fb = Lm.select_collect(sc, job, as_arrays=True)
         got[b0:b0 + k] = v
         fell += int(fb.sum())
         ncand += int(c.sum())
@@ -1384,7 +1384,8 @@ def learned_main(args):
     for b0 in range(0, nprof, Bsel):
         k = min(Bsel, nprof - b0)
         Xd = evals_t[b0 * n:(b0 + k) * n].to(dev)
-        Lm.select_collect(sc, Lm.select_submit(sc, mlp, Xd, off_full[:k + 1]), as_arrays=True)
+        Lm.select_collect(sc, Lm.select_submit(sc, mlp, Xd, off_full[:k + 1]), scored=scored,
+                          as_arrays=True)
     torch.cuda.synchronize()
     prof = kde.profile_read()
     kde.profile_enable(False)
@@ -1410,8 +1411,8 @@ def learned_main(args):
     Mg = np.array(sc.M, dtype=np.float64)
     dlt = (np.array(sc.hi) - np.array(sc.lo)) / (Mg - 1.0)
     Lv = np.minimum(Mg - 1.0, np.ceil(sc.tau * np.sqrt(lam)[:, None] / dlt[None, :]))
-    # the profiled pass covers the first nprof of the K datasets
-    ac_total = float(np.sum(8.0 * (Lv[:, 0] + 1.0) * (2.0 * Lv[:, 1] + 1.0))) * nprof / K
+    # every matrix scored in the profiled pass (its first nprof datasets)
+    ac_total = float(np.sum(8.0 * (Lv[:, 0] + 1.0) * (2.0 * Lv[:, 1] + 1.0)))
     flops = {"kde_lscv_ac_kernel": ac_total, "kde_lscv_theta_sums_kernel": ac_total,
              "kde_gemm_tc_kernel": nprof * 2.0 * 128 * (din * hid + hid * hid + hid * 16)}
     dom = max(prof, key=lambda k: prof[k][0])
