@@ -346,6 +346,17 @@ def cpu_oracle_child(spec_json):
     cells = float(np.prod(w.M))
     out = {"reps": reps, "cells": cells, "n": w.n, "n_bin": int(min(n_bin, w.n)),
            "n_nodes": n_nodes, "workers": workers}
+    if spec.get("o1_nodes"):
+        # O1 (Eq. 1, the direct sum over every sample, no binning) at a few
+        # random grid points
+        rng = np.random.default_rng(spec["seed"] + 99)
+        j = np.stack([rng.integers(0, m, spec["o1_nodes"]) for m in w.M], axis=1)
+        lo, hi, M = (np.asarray(v, dtype=np.float64) for v in (w.lo, w.hi, w.M))
+        pts = lo + j * ((hi - lo) / (M - 1.0))
+        t0 = time.perf_counter()
+        O.direct_kde(w.X, w.H, pts, chunk=1)
+        out["o1_s"] = time.perf_counter() - t0
+        out["o1_nodes"] = int(spec["o1_nodes"])
     if spec.get("o3"):
         # O3 (Eq. 10-14 with a plain separable DFT, the literal corrected
         # layout) on the whole grid, once
@@ -356,13 +367,13 @@ def cpu_oracle_child(spec_json):
 
 
 def run_cpu_oracle(workload, n_bin, n_nodes, seed=0, workers=1, reps=1, nodes_file="",
-                   range_mode="corrected", layout="corrected", o3=False):
+                   range_mode="corrected", layout="corrected", o3=False, o1_nodes=0):
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
     spec = json.dumps({"workload": workload, "n_bin": n_bin, "n_nodes": n_nodes, "seed": seed,
                        "workers": workers, "reps": reps, "nodes_file": nodes_file,
-                       "range": range_mode, "layout": layout, "o3": o3})
+                       "range": range_mode, "layout": layout, "o3": o3, "o1_nodes": o1_nodes})
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-oracle", spec],
                        capture_output=True, text=True, env=env)
     if r.returncode != 0:
@@ -394,6 +405,8 @@ def oracle_rates(r, n):
 # about a second of single-core oracle work each
 CPU_SAMPLE = {"kde2d_1024_f32": (1_000_000, 40_000), "kde2d_128_f64": (10_000, 16_384),
               "kde3d_256_f32": (1_000_000, 4_000)}
+# grid points at which O1 (the direct sum over all samples) is timed
+O1_NODES = {"kde2d_1024_f32": 16, "kde2d_128_f64": 64, "kde3d_256_f32": 2}
 
 
 def cpu_baseline(workload, range_mode="corrected", layout="corrected", nodes_file=""):
@@ -402,7 +415,8 @@ def cpu_baseline(workload, range_mode="corrected", layout="corrected", nodes_fil
     n_bin, n_nodes = CPU_SAMPLE[workload]
     cores = host_cores()
     one = run_cpu_oracle(workload, n_bin, n_nodes, seed=123, workers=1, nodes_file=nodes_file,
-                         range_mode=range_mode, layout=layout, o3=workload == "kde2d_128_f64")
+                         range_mode=range_mode, layout=layout, o3=workload == "kde2d_128_f64",
+                         o1_nodes=O1_NODES.get(workload, 0))
     allc = run_cpu_oracle(workload, n_bin, n_nodes, seed=123, workers=cores,
                           range_mode=range_mode, layout=layout) if cores > 1 else one
     r1, ra = oracle_rates(one, one["n"]), oracle_rates(allc, allc["n"])
@@ -416,6 +430,11 @@ def cpu_baseline(workload, range_mode="corrected", layout="corrected", nodes_fil
                         "sample_seconds": r1["t_sample_s"],
                         "extrapolated_full_step_s": r1["t_full_s"]},
            "host_cores": cores}
+    if "o1_s" in one:
+        out["o1_direct_kde"] = {"seconds": one["o1_s"], "cores": 1, "nodes": one["o1_nodes"],
+                                "grid_points_per_s": one["o1_nodes"] / one["o1_s"],
+                                "what": "O1: Eq. 1 summed over every sample (no binning) at "
+                                        "random grid points"}
     if "o3_s" in one:
         out["o3_naive_dft"] = {"seconds": one["o3_s"], "cores": 1,
                                "grid_points_per_s": one["cells"] / one["o3_s"],
