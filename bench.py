@@ -624,8 +624,21 @@ def kde_arm(args, workload, world, rank, local, dev):
         dist.barrier()
     clocks = sampler.stop()
     kde.plan_check(plan, stream)
-    ms = rank_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), dev)
+    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = rank_max(sum(per_step), dev)
     ms_step = ms / args.steps
+    ms_median = float(np.median(per_step))
+    # the same steps launched call by call, without the graph
+    ms_plain = None
+    if graph is not None:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()
+                starts[i].record(stream)
+                enqueue(step_dev)
+                ends[i].record(stream)
+        torch.cuda.synchronize()
+        ms_plain = float(np.median([s.elapsed_time(e) for s, e in zip(starts, ends)]))
     cells = int(np.prod(w.M))
     value = job_throughput(world, cells, ms_step)
     samples_s = job_throughput(world, w.n, ms_step)
@@ -767,6 +780,7 @@ def kde_arm(args, workload, world, rank, local, dev):
 
     line = {"metric": METRIC, "value": value, "unit": "grid points/s", "samples_per_s": samples_s,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "ms_per_step_median": ms_median, "ms_per_step_without_graph_median": ms_plain,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if info.precision == "f32" else "f64", "data": "synthetic",
             "config": {"workload": workload, "d": w.d, "n": w.n, "grid": list(w.M),
