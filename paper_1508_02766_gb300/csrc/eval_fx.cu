@@ -233,6 +233,7 @@ kde_status cols_pass(const kde_plan_s* plan, int k, const char* name, const floa
     case COL_FWD: e = launch_cols_fwd(l, a); break;
     case COL_FWD_REAL: e = launch_cols_real(l, a); break;
     case COL_MID: e = launch_cols_mid(l, a); break;
+    case COL_AUTO: e = launch_cols_auto(l, a); break;
     default: e = launch_cols_inv(l, a); break;
   }
   return done(e, name);
@@ -361,7 +362,7 @@ kde_status fx_autocorr(kde_plan_s* plan, const long long* counts, float* R, floa
   kde_status s = rows_pass(plan, SRC_COUNTS, nsets * I.M[0], counts, (int)I.M[1], I.M[1], nullptr,
                            A, nullptr, nullptr, 0, st);
   if (s != KDE_OK) return s;
-  s = cols_pass<COL_MID>(plan, 0, "kde_fx_cols_auto_kernel", A, B, nullptr, nullptr, I.Q, nsets,
+  s = cols_pass<COL_AUTO>(plan, 0, "kde_fx_cols_auto_kernel", A, B, nullptr, nullptr, I.Q, nsets,
                          (int)I.M[0], (int)I.P[0], -1, st, nullptr, 2.3283064365386963e-10f,
                          (float)(1.0 / ((double)I.P[0] * (double)I.P[1])));
   if (s != KDE_OK) return s;

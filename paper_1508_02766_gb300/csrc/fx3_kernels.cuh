@@ -327,27 +327,27 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
           }
         }
       } else {  // COL_MID: times K, inverse phase C back to the slots
-        const int64_t s = first + c;
-        const bool v = s < a.S;
-        if (a.K) {
+        if constexpr (MODE == COL_AUTO) {  // the power spectrum, for the autocorrelation
+#pragma unroll
+          for (int k3 = 0; k3 < N3; ++k3) {
+            const float re = z[k3].x * a.s_pre, im = z[k3].y * a.s_pre;
+            z[k3] = make_float2((re * re + im * im) * a.s_post, 0.f);
+          }
+        } else {
+          const int64_t s = first + c;
+          const bool v = s < a.S;
 #pragma unroll
           for (int k3 = 0; k3 < N3; ++k3) {
             const float kv = v ? __ldg(a.K + (int64_t)(k1 + N1 * (k2 + N2 * k3)) * a.S + s) : 0.f;
             z[k3].x *= kv;
             z[k3].y *= kv;
           }
-        } else {  // the power spectrum, for the counts' autocorrelation
-#pragma unroll
-          for (int k3 = 0; k3 < N3; ++k3) {
-            const float re = z[k3].x * a.s_pre, im = z[k3].y * a.s_pre;
-            z[k3] = make_float2((re * re + im * im) * a.s_post, 0.f);
-          }
         }
         p3_c_inv<N1, N2, N3>(z, k1, k2, a.tw, line, SK, W);
       }
     }
   }
-  if constexpr (MODE == COL_MID || MODE == COL_INV) {
+  if constexpr (MODE == COL_MID || MODE == COL_AUTO || MODE == COL_INV) {
     __syncthreads();
     if (r < N1 * N3) p3_b_inv<N1, N2, N3>(r / N3, r % N3, a.tw, line, SK, W);
     __syncthreads();

@@ -366,7 +366,9 @@ kde_fx_rows_c2r_kernel(RowsArgs a) {
 // b + n2 B + k1 SK with SK = B (mod 16) for B < 16 (conflict-free phase-B
 // reads) and B N2 otherwise.
 // ---------------------------------------------------------------------------
-enum { COL_FWD = 0, COL_FWD_REAL = 1, COL_MID = 2, COL_INV = 3 };
+// COL_AUTO: COL_MID with z <- |s_pre z|^2 s_post in place of the product
+// with K (the counts' power spectrum, for their autocorrelation).
+enum { COL_FWD = 0, COL_FWD_REAL = 1, COL_MID = 2, COL_INV = 3, COL_AUTO = 4 };
 
 struct ColsArgs {
   const float2* in;
@@ -386,9 +388,7 @@ struct ColsArgs {
   // rows with L0 = h_L0[h].
   int64_t slab_in, slab_out, slab_real, slab_K;
   const int* h_L0;
-  // COL_MID with K == NULL: z <- |s_pre z|^2 s_post between the transforms
-  // (the counts' power spectrum, for their autocorrelation)
-  float s_pre, s_post;
+  float s_pre, s_post;  // COL_AUTO scales
 };
 
 // Per-slab view of the arguments (slab = blockIdx.y).
@@ -482,22 +482,21 @@ __device__ __forceinline__ void cols_b_fwd(const ColsArgs& a, float2* sm) {
       out[k * a.S] = y[k2].x;
       if (v1) out[k * a.S + 1] = y[k2].y;
     }
-  } else {  // COL_MID: times K (or the power spectrum), inverse, back to the same slots
+  } else if constexpr (MODE == COL_AUTO) {  // power spectrum, inverse, back to the slots
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const float re = y[k2].x * a.s_pre, im = y[k2].y * a.s_pre;
+      y[k2] = make_float2((re * re + im * im) * a.s_post, 0.f);
+    }
+    b_inv_store<N2>(y, k1, a.tw, src, a.B);
+  } else {  // COL_MID: times K, inverse, back to the same slots
     const int64_t s = col_first<MODE>(a) + b;
     const bool v = s < a.S;
-    if (a.K) {
 #pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) {
-        const float kv = v ? __ldg(a.K + (int64_t)(k1 + N1 * k2) * a.S + s) : 0.f;
-        y[k2].x *= kv;
-        y[k2].y *= kv;
-      }
-    } else {
-#pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) {
-        const float re = y[k2].x * a.s_pre, im = y[k2].y * a.s_pre;
-        y[k2] = make_float2((re * re + im * im) * a.s_post, 0.f);
-      }
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const float kv = v ? __ldg(a.K + (int64_t)(k1 + N1 * k2) * a.S + s) : 0.f;
+      y[k2].x *= kv;
+      y[k2].y *= kv;
     }
     b_inv_store<N2>(y, k1, a.tw, src, a.B);
   }
@@ -557,7 +556,7 @@ kde_fx_cols_kernel(ColsArgs a) {
     size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_fwd<decltype(N)::value, MODE>(a, fx_sm); });
     __syncthreads();
     size_call<N2T, CLS>(a.ln.N2, [&](auto N) { cols_b_fwd<decltype(N)::value, MODE>(a, fx_sm); });
-    if constexpr (MODE == COL_MID) {
+    if constexpr (MODE == COL_MID || MODE == COL_AUTO) {
       __syncthreads();
       size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_inv<decltype(N)::value, MODE>(a, fx_sm); });
     }
@@ -627,6 +626,7 @@ cudaError_t launch_rows_c2r(const Launch& l, const RowsArgs& a);
 cudaError_t launch_cols_fwd(const Launch& l, const ColsArgs& a);
 cudaError_t launch_cols_real(const Launch& l, const ColsArgs& a);
 cudaError_t launch_cols_mid(const Launch& l, const ColsArgs& a);
+cudaError_t launch_cols_auto(const Launch& l, const ColsArgs& a);
 cudaError_t launch_cols_inv(const Launch& l, const ColsArgs& a);
 
 }  // namespace fx

@@ -94,6 +94,7 @@ int debug_read_fx_rows_c2r();
 int debug_read_fx_cols_fwd();
 int debug_read_fx_cols_real();
 int debug_read_fx_cols_mid();
+int debug_read_fx_cols_auto();
 int debug_read_fx_cols_inv();
 
 // Launch bookkeeping: counts launches and, when profiling is on, records a

@@ -598,7 +598,8 @@ kde_status kde_debug_status(int* enabled, int* code) {
   int (*readers[])() = {kde::debug_read_bin, kde::debug_read_eval, kde::debug_read_fx_rows_counts,
                         kde::debug_read_fx_rows_kgen, kde::debug_read_fx_rows_c2r,
                         kde::debug_read_fx_cols_fwd, kde::debug_read_fx_cols_real,
-                        kde::debug_read_fx_cols_mid, kde::debug_read_fx_cols_inv};
+                        kde::debug_read_fx_cols_mid, kde::debug_read_fx_cols_inv,
+                        kde::debug_read_fx_cols_auto};
   for (auto rd : readers) {
     const int v = rd();
     if (v < 0) return fail(KDE_ERR_CUDA, "kde_debug_status: reading a check word failed");
