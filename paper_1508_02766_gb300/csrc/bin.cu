@@ -741,7 +741,7 @@ kde_status launch_direct(const T* X, int64_t n, int d, const double* lo, const d
   if (n == 0) return KDE_OK;
   BinParams<T> p = make_params<T>(d, lo, hi, M, nullptr);
   int64_t want = (2 * n + 255) / 256;  // two lanes per sample
-  int64_t cap = (int64_t)num_sms() * 8;
+  int64_t cap = (int64_t)num_sms() * 16;
   int blocks = (int)(want < cap ? want : cap);
   kde::LaunchScope ls("kde_bin_kernel", stream);
   switch (d) {
