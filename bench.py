@@ -53,6 +53,9 @@ def parse(argv=None):
                          "supported size at or above it and at or above M + L)")
     ap.add_argument("--dft", default="fft", choices=["fft", "tc"],
                     help="first pass: mixed-radix FFT, or split-TF32 DFT matrix on the tensor cores")
+    ap.add_argument("--slab", default="off", choices=["off", "on"],
+                    help="3-D: last two axes slab by slab on thread-block clusters (one "
+                         "launch each way) instead of separate row and column passes")
     ap.add_argument("--lscv", default="autocorr", choices=["autocorr", "spectrum"],
                     help="lscv2d_512_f32: pair sums from the counts' autocorrelation, or from "
                          "the count spectrum against per-candidate kernel spectra")
@@ -100,6 +103,10 @@ def algorithmic_bytes(info, n, x_itemsize):
         b["kde_cols_mid_kernel"] = 2 * M[0] * P[1] * Q * cs + P[0] * P[1] * Q * r
         b["kde_cols_inv_kernel"] = M[0] * P[1] * Q * cs + M[0] * M[1] * Q * cs
         b["kde_rows_c2r_kernel"] = M[0] * M[1] * Q * cs + cells * r
+        # slab passes: axes 2 and 1 in one launch each way, the half spectra
+        # between them kept on chip
+        b["kde_fx_slab_fwd_kernel"] = 8 * cells + M[0] * P[1] * Q * cs
+        b["kde_fx_slab_inv_kernel"] = M[0] * P[1] * Q * cs + cells * r
     if "kde_rows_r2c_counts_kernel" in b:
         b["kde_rows_r2c_tc_kernel"] = b["kde_rows_r2c_counts_kernel"]
     # the two-phase FFT passes do the same passes as the Stockham ones
@@ -541,7 +548,7 @@ def kde_arm(args, workload, world, rank, local, dev):
     w = W.WORKLOADS[workload]()
     stream = torch.cuda.Stream(device=dev)
     plan = kde.Plan(w.M, w.lo, w.hi, w.H, precision=w.precision, tau=w.tau, dft=args.dft,
-                    range_mode=args.range, layout=args.layout, P_min=args.P_min)
+                    range_mode=args.range, layout=args.layout, P_min=args.P_min, slab=args.slab)
     info = plan.info
     X_host = torch.from_numpy(np.ascontiguousarray(w.X)).pin_memory()
     X = X_host.to(dev)
@@ -791,6 +798,8 @@ def kde_arm(args, workload, world, rank, local, dev):
                        "binning": method, "range": args.range, "layout": args.layout,
                        "first_pass": "split-TF32 DFT matrix on the tensor cores" if args.dft == "tc"
                        else "FFT",
+                       **({"slab_passes": "last two axes per slab on 8-block clusters"}
+                          if info.slab_passes else {}),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline, "path_roofline": path_roof, "kernels": kernels,
             "kernel_timing": "CUDA events around each kernel, over the same K steps launched "

@@ -55,6 +55,7 @@ enum { KDE_RANGE_CORRECTED = 0, KDE_RANGE_PER_AXIS = 1 };
 enum { KDE_LAYOUT_CORRECTED = 0, KDE_LAYOUT_WAND = 1 };
 enum { KDE_COLS_AUTO = 0, KDE_COLS_LINES = 1, KDE_COLS_SIMD = 2 };
 enum { KDE_ENGINE_AUTO = 0, KDE_ENGINE_STOCKHAM = 1, KDE_ENGINE_TWO_PHASE = 2 };
+enum { KDE_SLAB_OFF = 0, KDE_SLAB_ON = 1 };
 
 #define KDE_MAX_D 3
 #define KDE_MAX_P 4096      /* largest padded length of one axis */
@@ -97,7 +98,20 @@ enum { KDE_ENGINE_AUTO = 0, KDE_ENGINE_STOCKHAM = 1, KDE_ENGINE_TWO_PHASE = 2 };
  *               memory, P_k the smallest 7-smooth size >= M_k + L_k.
  *               KDE_ENGINE_AUTO: two-phase where it applies (KDE_F32, d >= 2,
  *               every padded length a product as above), else Stockham.
- *               The result is the same up to rounding. */
+ *               The result is the same up to rounding.
+ *   slab_passes KDE_SLAB_OFF (default): separate row and column passes
+ *               through global memory.  KDE_SLAB_ON (3-D two-phase plans
+ *               without dft_tc, where the slab fits, see
+ *               kde_plan_info.slab_passes): kde_fft_eval transforms the last
+ *               two axes of each slab of the leading axis in one launch per
+ *               direction, on clusters of 8 thread blocks that pass the
+ *               intermediate half spectra between them in distributed shared
+ *               memory (st.async stores counted on the receiver's mbarrier;
+ *               bounded waits report through kde_plan_check).  The same
+ *               arithmetic as the separate passes: the same result up to
+ *               rounding.  Measured on GB300 at 256^3 it is not faster (the
+ *               separate passes are bound by their transforms, not by the
+ *               intermediate's round trip), so it is off by default. */
 typedef struct {
   double tau;
   int precision;
@@ -107,6 +121,7 @@ typedef struct {
   int cols_variant;
   int dft_tc;
   int engine;
+  int slab_passes;
 } kde_opts;
 
 /* Everything the plan derives on the host, in FP64.
@@ -125,7 +140,13 @@ typedef struct {
  *   split[k]   the factors of P_k with the two-phase engine: N1, N2 and 0
  *              for lines up to 400, N1, N2, N3 (three exchanges instead of
  *              two, about 10 values per thread) for longer ones; all 0 with
- *              the Stockham engine. */
+ *              the Stockham engine;
+ *   slab_passes  1 if kde_fft_eval takes the last two axes slab by slab on
+ *              thread-block clusters (opts.slab_passes): d = 3, two-phase
+ *              engine, two-factor splits of axes 1 and 2 with factors <= 20,
+ *              no dft_tc, and a slab whose exchange fits in at most 113 KB
+ *              of shared memory per block (2 blocks per SM).
+ *              0 otherwise. */
 typedef struct {
   int d;
   int precision;
@@ -143,6 +164,7 @@ typedef struct {
   int radix[KDE_MAX_D][KDE_MAX_STAGES];
   int engine;
   int split[KDE_MAX_D][3];
+  int slab_passes;
 } kde_plan_info;
 
 typedef struct kde_plan_s* kde_plan;

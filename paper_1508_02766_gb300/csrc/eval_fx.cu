@@ -30,6 +30,7 @@
 #include <string>
 
 #include "fx3_kernels.cuh"
+#include "fx_slab.cuh"
 
 namespace kde {
 namespace fx {
@@ -239,6 +240,40 @@ kde_status cols_pass(const kde_plan_s* plan, int k, const char* name, const floa
   return done(e, name);
 }
 
+// Slab pass of a 3-D plan (fwd: counts -> spec [M0][P1][Q]; else spec ->
+// density [M0][M1][M2]): one cluster of kSlabC blocks per slab of axis 0.
+kde_status slab_pass(const kde_plan_s* plan, bool fwd, const long long* counts, float2* spec,
+                     float* density, cudaStream_t st) {
+  const kde_plan_info& I = plan->info;
+  const fxp::SlabGeo g = fxp::slab_geometry(I.M[1], I.Q, I.split[2], I.split[1]);
+  if (!g.ok) return fail(KDE_ERR_UNSUPPORTED, "slab passes do not fit this plan");
+  SlabArgs a{};
+  a.counts = counts;
+  a.spec = spec;
+  a.out_real = density;
+  a.M1 = (int)I.M[1];
+  a.M2 = (int)I.M[2];
+  a.Q = (int)I.Q;
+  a.lr = line_of(I, 2);
+  a.lc = line_of(I, 1);
+  a.twr = twiddles(plan, 2);
+  a.twc = twiddles(plan, 1);
+  a.RP = g.RP;
+  a.W = g.W;
+  a.SKr = g.SKr;
+  a.SKc = g.SKc;
+  a.ex_elems = g.ex_elems;
+  a.status = plan->status_dev;
+  const Launch l{a.lr.N1, a.lr.N2, 0, dim3((unsigned)(I.M[0] * kSlabC)), g.threads,
+                 (size_t)(fwd ? g.smem_fwd : g.smem_inv), st};
+  if (fwd) {
+    LaunchScope ls("kde_fx_slab_fwd_kernel", st);
+    return done(launch_slab_fwd(l, a), "kde_fx_slab_fwd_kernel");
+  }
+  LaunchScope ls("kde_fx_slab_inv_kernel", st);
+  return done(launch_slab_inv(l, a), "kde_fx_slab_inv_kernel");
+}
+
 }  // namespace
 }  // namespace fx
 
@@ -278,6 +313,15 @@ kde_status fx_fft_eval(kde_plan_s* plan, const long long* counts, const float* K
   int64_t rows = 1;
   for (int k = 0; k < dl; ++k) rows *= I.M[k];
   kde_status s;
+  if (I.slab_passes) {  // d == 3: axes 2 and 1 slab by slab, axis 0 between
+    float2* Bf = A + rows * I.Q;  // [M_0][P_1][Q]
+    s = slab_pass(plan, true, counts, Bf, nullptr, st);
+    if (s != KDE_OK) return s;
+    s = cols_pass<COL_MID>(plan, 0, "kde_fx_cols_mid_kernel", Bf, Bf, nullptr, Kspec,
+                           I.P[1] * I.Q, 1, (int)I.M[0], (int)I.M[0], -1, st);
+    if (s != KDE_OK) return s;
+    return slab_pass(plan, false, nullptr, Bf, density, st);
+  }
   if (plan->dft_tc)
     s = dft_tc_rows(plan, counts, rows, A, st);
   else

@@ -39,5 +39,6 @@ enum {
   KDE_DBG_ROWS_STORE = 4,
   KDE_DBG_COLS_STORE = 5,
   KDE_DBG_COLS_LOAD = 6,
-  KDE_DBG_STOCKHAM = 7
+  KDE_DBG_STOCKHAM = 7,
+  KDE_DBG_SLAB = 8
 };

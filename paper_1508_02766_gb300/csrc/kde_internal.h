@@ -96,6 +96,8 @@ int debug_read_fx_cols_real();
 int debug_read_fx_cols_mid();
 int debug_read_fx_cols_auto();
 int debug_read_fx_cols_inv();
+int debug_read_fx_slab_fwd();
+int debug_read_fx_slab_inv();
 
 // Launch bookkeeping: counts launches and, when profiling is on, records a
 // pair of events around each launch on its stream.

@@ -457,6 +457,10 @@ static kde_status compute_info(int d, const int64_t* M, const double* lo, const 
     info->nstages[k] = radix_plan(P, info->radix[k]);
   }
   info->Q = info->P[d - 1] / 2 + 1;
+  if (o.slab_passes != KDE_SLAB_OFF && o.slab_passes != KDE_SLAB_ON)
+    return fail(KDE_ERR_INVALID_ARG, "bad slab_passes");
+  if (d == 3 && tp && !o.dft_tc && o.slab_passes == KDE_SLAB_ON)
+    info->slab_passes = kde::fxp::slab_geometry(M[1], info->Q, info->split[2], info->split[1]).ok;
   int64_t ke = info->Q;
   for (int k = 0; k < d - 1; ++k) ke *= info->P[k];
   info->kspec_elems = ke;
@@ -599,7 +603,8 @@ kde_status kde_debug_status(int* enabled, int* code) {
                         kde::debug_read_fx_rows_kgen, kde::debug_read_fx_rows_c2r,
                         kde::debug_read_fx_cols_fwd, kde::debug_read_fx_cols_real,
                         kde::debug_read_fx_cols_mid, kde::debug_read_fx_cols_inv,
-                        kde::debug_read_fx_cols_auto};
+                        kde::debug_read_fx_cols_auto, kde::debug_read_fx_slab_fwd,
+                        kde::debug_read_fx_slab_inv};
   for (auto rd : readers) {
     const int v = rd();
     if (v < 0) return fail(KDE_ERR_CUDA, "kde_debug_status: reading a check word failed");

@@ -35,7 +35,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("precision", ctypes.c_int),
                 ("range_mode", ctypes.c_int), ("layout_mode", ctypes.c_int),
                 ("P_min", ctypes.c_int64 * MAX_D), ("cols_variant", ctypes.c_int),
-                ("dft_tc", ctypes.c_int), ("engine", ctypes.c_int)]
+                ("dft_tc", ctypes.c_int), ("engine", ctypes.c_int), ("slab_passes", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -47,7 +47,7 @@ class PlanInfo(ctypes.Structure):
                 ("kspec_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
                 ("nstages", ctypes.c_int * MAX_D),
                 ("radix", (ctypes.c_int * MAX_STAGES) * MAX_D), ("engine", ctypes.c_int),
-                ("split", (ctypes.c_int * 3) * MAX_D)]
+                ("split", (ctypes.c_int * 3) * MAX_D), ("slab_passes", ctypes.c_int)]
 
 
 class BatchItem(ctypes.Structure):
@@ -212,13 +212,15 @@ def _iarr(vals):
 
 COLS_VARIANTS = {"auto": 0, "lines": 1, "simd": 2}
 ENGINES = {"auto": 0, "stockham": 1, "two_phase": 2}
+SLAB_PASSES = {"off": 0, "on": 1}
 
 
 def _opts(tau=3.7, precision="f32", range_mode="corrected", layout="corrected", P_min=None,
-          cols="auto", dft="fft", engine="auto"):
+          cols="auto", dft="fft", engine="auto", slab="off"):
     o = Opts()
     o.cols_variant = COLS_VARIANTS[cols]
     o.engine = ENGINES[engine]
+    o.slab_passes = SLAB_PASSES[slab]
     o.dft_tc = {"fft": 0, "tc": 1}[dft]
     o.tau = tau
     o.precision = F32 if precision == "f32" else F64
@@ -246,6 +248,7 @@ class Info:
     radices: tuple
     engine: str
     split: tuple
+    slab_passes: bool
 
 
 def _info(pi: PlanInfo) -> Info:
@@ -255,7 +258,8 @@ def _info(pi: PlanInfo) -> Info:
                 pi.kspec_elems, pi.kspec_bytes, pi.workspace_bytes,
                 tuple(tuple(pi.radix[k][:pi.nstages[k]]) for k in range(d)),
                 {1: "stockham", 2: "two_phase"}.get(pi.engine, "stockham"),
-                tuple(tuple(v for v in pi.split[k][:3] if v) or (0, 0) for k in range(d)))
+                tuple(tuple(v for v in pi.split[k][:3] if v) or (0, 0) for k in range(d)),
+                bool(pi.slab_passes))
 
 
 def kde_plan_info_compute(M, lo, hi, H, **opts) -> Info:

@@ -201,3 +201,50 @@ def test_batch_preparation_and_search_reject_bad_handles():
     assert L.kde_lscv_theta_select(None, 1, n, null, d6, 1, d6, d6, null, null, null, null, 0,
                                    null) == 1
     assert L.kde_lscv_theta_select_workspace_bytes(None, 1, 1, ctypes.byref(b)) == 1
+
+
+def _slab_fits(M1, Q, sr, sc):
+    """The slab passes' block shape (8 blocks per slab, RP row pairs and W
+    half-spectrum columns each) and its limit: 113 KB of shared memory."""
+    RP = -(-((M1 + 1) // 2) // 8)
+    W_ = -(-Q // 8)
+    SKr = sr[1] | 1
+    SKc = W_ * sc[1]
+    while SKc % 16 != W_ % 16:
+        SKc += 1
+    ex = max(RP * sr[0] * SKr, sc[0] * SKc)
+    smem = 16 + max(ex + M1 * W_, ex + 2 * RP * Q) * 8
+    return smem <= 113 * 1024
+
+
+@pytest.mark.parametrize("M,opts,expect", [
+    ((256, 256, 256), {}, True),
+    ((20, 17, 24), {}, True),
+    ((2, 2, 2), {}, True),
+    ((256, 256, 256), {"slab": "off"}, False),
+    ((40, 50, 60), {"slab": None}, False),   # the default: separate passes
+    ((256, 256, 256), {"dft": "tc"}, False),
+    ((256, 256, 256), {"engine": "stockham"}, False),
+    ((40, 50, 60), {"precision": "f64"}, False),
+    ((64, 320, 300), {"tau": 1.0}, True),   # P = 320 or so: more tasks than threads
+    ((4, 400, 390), {"tau": 0.5}, False),  # exchange and cluster buffer above 113 KB
+    ((4, 500, 40), {}, False),           # axis 1 longer than 400: three factors
+])
+def test_slab_pass_eligibility(M, opts, expect):
+    H = np.diag([0.002, 0.002, 0.002]) if M[1] >= 256 else np.diag([0.01, 0.02, 0.015])
+    o = {"precision": "f32", "slab": "on", **opts}
+    if o["slab"] is None:
+        del o["slab"]
+    info = kde.kde_plan_info_compute(M, (0, 0, 0), (1, 1, 1), H, **o)
+    assert info.slab_passes == expect
+    if info.engine == "two_phase" and len(info.split[1]) == 2 and len(info.split[2]) == 2 \
+            and not set(opts) - {"tau"}:
+        assert _slab_fits(M[1], info.Q, info.split[2], info.split[1]) == expect
+    two_d = kde.kde_plan_info_compute((64, 64), (0, 0), (1, 1), np.diag([0.01, 0.01]))
+    assert not two_d.slab_passes
+    with pytest.raises(kde.KDEError):
+        bad = kde.Opts()
+        bad.slab_passes = 7
+        kde._check(kde.lib().kde_plan_info_compute(
+            3, kde._iarr(M), kde._darr((0, 0, 0)), kde._darr((1, 1, 1)), kde._darr(H),
+            ctypes.byref(bad), ctypes.byref(kde.PlanInfo())))
