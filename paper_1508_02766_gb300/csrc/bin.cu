@@ -9,18 +9,22 @@
 //           scratch; bound by the rate of scattered L2 sector operations,
 //           ~2^(d-1) + 1/2 per sample);
 //   tiled   the samples partitioned by the grid tile of their base node, then
-//           each tile accumulated in shared memory and written once:
+//           each tile accumulated in shared memory and written once (no
+//           zeroing pass, no global atomics on the counts):
 //             count    records per tile (a sample whose base node is on a
 //                      tile's upper face also feeds the next tile(s): one
-//                      record per tile it touches)
-//             plan     bucket offsets and work items of at most kItemRecords
-//                      records per tile (one block)
-//             scatter  16-byte records {q_0, q_1, q_2, tile-local base} into
-//                      the buckets, block-aggregated cursor reservations
-//             accum    per work item, 32-bit shared atomics with exact carry
-//                      into a 64-bit word pair per cell, then every cell of
-//                      the tile stored (tiles split into several items are
-//                      zeroed during scatter and their items add instead)
+//                      record per tile it touches), each block keeping its
+//                      range inside every tile's bucket
+//             scatter  bucket starts and work items of at most kItemRecords
+//                      records (every block scans the tile counts), then
+//                      16-byte records {q_0, q_1, q_2, tile-local base and
+//                      corner mask} written into the block's ranges
+//             accum    per work item, 32-bit shared atomics on split sums
+//                      (exact), then every cell of the tile stored (tiles
+//                      split into several items are zeroed during scatter
+//                      and their items add instead)
+//           the scatter and accumulation kernels are programmatic dependents
+//           of the kernel before each.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -242,17 +246,17 @@ __global__ void __launch_bounds__(256) kde_bin_sets_kernel(const T* __restrict__
 // ---------------------------------------------------------------------------
 // Tiled path.
 // ---------------------------------------------------------------------------
-constexpr int kCountThreads = 512;
-constexpr int kScatterThreads = 512;
-constexpr int kScatterU = 8;           // samples per thread per round, loaded before any is used
+constexpr int kBinThreads = 512;       // count and scatter kernels
+constexpr int kBinU = 4;               // samples per thread per round, loaded before any is used
 constexpr int kAccumThreads = 512;
+constexpr int kAccumU = 4;             // records per thread per round, loaded before any is used
 constexpr int kItemRecords = 8192;     // records per work item
 constexpr int kMaxTiles = 16384;       // tiles per grid (shared histograms)
 constexpr int kTileCells = 8192;       // cells per tile (shared accumulators)
 
 // Tile shape per d: powers of two, kTileCells cells, the last axis the
 // longest so that a tile's rows are long runs of the counts.  ls: strides
-// inside a tile (row-major); bits: bits per axis of a record's packed base.
+// inside a tile (row-major); lsh: log2 of ls.
 template <int D>
 struct Geo;
 template <>
@@ -261,7 +265,6 @@ struct Geo<1> {
   __host__ __device__ static constexpr int lg(int k) { return k == 0 ? 13 : 0; }
   __host__ __device__ static constexpr int ls(int k) { return k == 0 ? 1 : 0; }
   __host__ __device__ static constexpr int lsh(int) { return 0; }
-  static constexpr int bits = 16;
 };
 template <>
 struct Geo<2> {
@@ -269,7 +272,6 @@ struct Geo<2> {
   __host__ __device__ static constexpr int lg(int k) { return k == 0 ? 6 : k == 1 ? 7 : 0; }
   __host__ __device__ static constexpr int ls(int k) { return k == 0 ? 128 : k == 1 ? 1 : 0; }
   __host__ __device__ static constexpr int lsh(int k) { return k == 0 ? 7 : 0; }
-  static constexpr int bits = 8;
 };
 template <>
 struct Geo<3> {
@@ -277,132 +279,180 @@ struct Geo<3> {
   __host__ __device__ static constexpr int lg(int k) { return k == 2 ? 5 : 4; }
   __host__ __device__ static constexpr int ls(int k) { return k == 0 ? 512 : k == 1 ? 32 : 1; }
   __host__ __device__ static constexpr int lsh(int k) { return k == 0 ? 9 : k == 1 ? 5 : 0; }
-  static constexpr int bits = 8;
 };
 
-// Targets of one sample: its tile coordinates, the tile-local base node and
-// the axes along which it also feeds the next tile (base on the tile's last
-// row and a nonzero fraction, so the corners there can have weight).
+// The shared accumulators of a tile carry one halo row before and after it
+// along every axis (extent ext + 2), so that every corner of every record,
+// the tile's own and its neighbours', has a cell: the accumulation needs no
+// corner masks and no range tests, and the halo cells are not stored.
+// pst: strides of the padded tile (row-major).
 template <int D>
-struct Target {
-  int tc[3];     // tile coordinate per axis
-  int local[3];  // tile-local base node
-  unsigned q[3];
-  int spill;     // bit k: also the next tile along axis k
+__host__ __device__ constexpr int pad_ext(int k) {
+  return k < D ? Geo<D>::ext(k) + 2 : 1;
+}
+template <int D>
+__host__ __device__ constexpr int pst(int k) {
+  int s = 1;
+  for (int j = k + 1; j < D; ++j) s *= pad_ext<D>(j);
+  return s;
+}
+template <int D>
+__host__ __device__ constexpr int pad_cells() {
+  int c = 1;
+  for (int k = 0; k < D; ++k) c *= pad_ext<D>(k);
+  return c;
+}
+// words per accumulator array (a multiple of 4: cleared as uint4)
+template <int D>
+__host__ __device__ constexpr int pad_alloc() {
+  return (pad_cells<D>() + 3) & ~3;
+}
+// Offset in the padded tile of corner c from the record's base node.
+template <int D>
+__host__ __device__ constexpr int corner_off(int c) {
+  int o = 0;
+  for (int k = 0; k < D; ++k) o += ((c >> (D - 1 - k)) & 1) * pst<D>(k);
+  return o;
+}
+static_assert(pad_cells<3>() < (1 << 16) && pad_cells<2>() < (1 << 16) && pad_cells<1>() < (1 << 16),
+              "a padded tile-local index fits the record's low 16 bits");
+
+// Position of one coordinate, the same (i, q) as axis_position: the node
+// i = floor t and q from f = t - i (exact).  At t = M - 1 this gives
+// (M - 1, q = 0), which is axis_position's (M - 2, f = 1) written as its
+// fixed_frac writes a fraction of one.  kWithQ = false leaves q = 0 for
+// FP32 inputs, where i does not depend on it (f < 1 - 2^-25, so f 2^32
+// never rounds up to 2^32); FP64 fractions can round up, which moves i, so
+// they are always computed.
+template <typename T, bool kWithQ = true>
+__device__ __forceinline__ bool axis_node(T x, const BinAxis<T>& a, int& i, unsigned& q) {
+  const T t = mul_rn(sub_rn(x, a.lo), a.s);
+  const bool in = t >= T(0) && t <= a.top;
+  const T fl = floor(t);
+  i = (int)fl;
+  q = 0;
+  if (kWithQ || sizeof(T) == 8) fixed_frac(sub_rn(t, fl), i, q);
+  return in;
+}
+
+// One sample located on the grid: base node i and fractions q per axis, its
+// tile t0, and the axes along which it also feeds the next tile: those
+// where the base is on the tile's last row and not the grid's last node.
+// (Along such an axis the corners after the base lie in the next tile; if
+// q = 0 there they have weight zero and the extra record adds zeros.  The
+// count and scatter kernels apply the same rule, which is all the bucket
+// offsets need.)  kWithQ = false: q is not computed (the count kernel).
+template <int D>
+struct Located {
+  int i[D];
+  unsigned q[D];
+  int t0;
+  int spill;
 };
 
-template <typename T, int D>
-__device__ __forceinline__ bool sample_target(const T* x, const BinParams<T>& p, Target<D>& g) {
-  int i[D];
+template <typename T, int D, bool kWithQ = true>
+__device__ __forceinline__ bool locate(const T* x, const BinParams<T>& p, Located<D>& g) {
   bool in = true;
-  g.q[0] = g.q[1] = g.q[2] = 0;
 #pragma unroll
-  for (int k = 0; k < D; ++k) in &= axis_position<T>(x[k], p.ax[k], i[k], g.q[k]);
-  if (!in) return false;
+  for (int k = 0; k < D; ++k) in &= axis_node<T, kWithQ>(x[k], p.ax[k], g.i[k], g.q[k]);
+  g.t0 = 0;
   g.spill = 0;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    g.tc[k] = i[k] >> Geo<D>::lg(k);
-    g.local[k] = i[k] - (g.tc[k] << Geo<D>::lg(k));
-    if (g.local[k] == Geo<D>::ext(k) - 1 && g.q[k] != 0) g.spill |= 1 << k;
+    g.t0 += (g.i[k] >> Geo<D>::lg(k)) * p.ax[k].tstride;
+    const bool last = (g.i[k] & (Geo<D>::ext(k) - 1)) == Geo<D>::ext(k) - 1;
+    g.spill |= (last && g.i[k] < p.ax[k].M - 1) << k;
   }
-  return true;
+  return in;
 }
 
-// Tile index of target subset S of a sample's spill axes.
+// Tile of target subset S of a sample's spill axes (the tile after t0 along
+// every axis in S).
 template <typename T, int D>
-__device__ __forceinline__ int target_tile(const Target<D>& g, int S, const BinParams<T>& p) {
-  int tile = 0;
+__device__ __forceinline__ int spill_tile(const Located<D>& g, int S, const BinParams<T>& p) {
+  int t = g.t0;
 #pragma unroll
-  for (int k = 0; k < D; ++k) tile += (g.tc[k] + ((S >> k) & 1)) * p.ax[k].tstride;
-  return tile;
+  for (int k = 0; k < D; ++k)
+    if ((S >> k) & 1) t += p.ax[k].tstride;
+  return t;
 }
 
 // Record of a sample for target subset S of its spill axes: {q_0, q_1, q_2,
-// packed} with packed = the base node relative to that tile (local - tile
-// extent on the axes in S, so -1 there), stored + 1 in Geo<D>::bits bits per
-// axis, and in bits 24.. the mask of the 2^d corners (corner c has offset
-// (c >> (d-1-k)) & 1 on axis k) that lie inside the tile and the grid.
-template <typename T, int D>
-__device__ __forceinline__ int record_for(const Target<D>& g, int S, const BinParams<T>& p,
-                                          uint4& rec) {
-  int tile = 0, b[D], ext[D];
-  unsigned packed = 0;
+// j0} with j0 the index in the padded tile of the base node relative to
+// that tile (the base is one row before the tile on the axes in S, in the
+// halo).  Corners that fall in a halo are added there and not stored: on
+// the axes in S the lower corner belongs to the tile before (its record
+// adds it there), and an upper corner past the tile's last row belongs to
+// the tile after, where the sample's spill record adds it, or lies past the
+// grid's last node with weight zero (q = 0).
+template <int D>
+__device__ __forceinline__ uint4 make_record(const Located<D>& g, int S) {
+  int j0 = 0;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    const int nx = (S >> k) & 1;
-    const int tck = g.tc[k] + nx;
-    tile += tck * p.ax[k].tstride;
-    b[k] = g.local[k] - nx * Geo<D>::ext(k);
-    ext[k] = min(Geo<D>::ext(k), p.ax[k].M - (tck << Geo<D>::lg(k)));
-    packed |= (unsigned)(b[k] + 1) << (Geo<D>::bits * k);
+    const int l = g.i[k] & (Geo<D>::ext(k) - 1);
+    const int b = ((S >> k) & 1) ? l - Geo<D>::ext(k) : l;
+    j0 += (b + 1) * pst<D>(k);
   }
-  unsigned mask = 0;
+  return make_uint4(g.q[0], D > 1 ? g.q[D > 1 ? 1 : 0] : 0u, D > 2 ? g.q[D > 2 ? 2 : 0] : 0u,
+                    (unsigned)j0);
+}
+
+// Samples of block b: the contiguous chunk [b chunk, min(n, (b + 1) chunk)),
+// visited in the same order by the count and scatter kernels, each thread
+// loading kBinU samples before it uses any.
+template <typename T, int D, typename F>
+__device__ __forceinline__ void for_block_samples(const T* __restrict__ X, int64_t n, int64_t chunk,
+                                                  F&& f) {
+  const int64_t beg = (int64_t)blockIdx.x * chunk;
+  const int64_t end = beg + chunk < n ? beg + chunk : n;
+  for (int64_t s0 = beg + threadIdx.x; s0 < end; s0 += (int64_t)kBinU * blockDim.x) {
+    T x[kBinU][D];
 #pragma unroll
-  for (int c = 0; c < (1 << D); ++c) {
-    bool ok = true;
+    for (int u = 0; u < kBinU; ++u) {
+      const int64_t s = s0 + (int64_t)u * blockDim.x;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const int v = b[k] + ((c >> (D - 1 - k)) & 1);
-      ok &= v >= 0 && v < ext[k];
+      for (int k = 0; k < D; ++k) x[u][k] = s < end ? X[s * D + k] : T(0);
     }
-    mask |= (unsigned)ok << c;
-  }
-  rec = make_uint4(g.q[0], g.q[1], g.q[2], packed | (mask << 24));
-  return tile;
-}
-
-template <typename T, int D>
-__device__ __forceinline__ void load_samples(const T* __restrict__ X, int64_t n, int64_t s0,
-                                             int64_t stride, T (&x)[kScatterU][D]) {
 #pragma unroll
-  for (int u = 0; u < kScatterU; ++u) {
-    const int64_t s = s0 + u * stride;
-#pragma unroll
-    for (int k = 0; k < D; ++k) x[u][k] = s < n ? X[s * D + k] : T(0);
+    for (int u = 0; u < kBinU; ++u)
+      if (s0 + (int64_t)u * blockDim.x < end) f(x[u]);
   }
 }
 
-// Records per tile (block histograms added into tile_count, each block
-// keeping the offset of its range inside every tile's bucket) and samples
-// outside the grid.  The scatter kernel visits the same samples with the same
-// grid, so block b writes its records of tile t into its own range.
+// Records per tile and samples outside the grid.  Each block adds its
+// shared histogram into tile_count and keeps the offset of its range inside
+// every tile's bucket (the atomicAdd's old value); the scatter kernel's
+// block b writes its records of tile t into that range.  The tile counts
+// start at zero (cleared before this launch).
 template <typename T, int D>
-__global__ void __launch_bounds__(kCountThreads)
-kde_bin_count_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int ntiles,
-                     unsigned* __restrict__ tile_count, unsigned* __restrict__ block_base,
-                     unsigned long long* __restrict__ n_out) {
+__global__ void __launch_bounds__(kBinThreads, 2)
+kde_bin_count_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, BinParams<T> p,
+                     int ntiles, unsigned* __restrict__ tile_count,
+                     unsigned* __restrict__ block_off, unsigned long long* __restrict__ n_out) {
   extern __shared__ unsigned hist[];
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
   __syncthreads();
+  // the scatter kernel may start now; it waits for this grid before it
+  // reads anything written here
+  kde::pdl_trigger();
   unsigned long long outside = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s0 < n;
-       s0 += kScatterU * stride) {
-    T x[kScatterU][D];
-    load_samples<T, D>(X, n, s0, stride, x);
-#pragma unroll
-    for (int u = 0; u < kScatterU; ++u) {
-      if (s0 + u * stride >= n) break;
-      Target<D> g;
-      if (!sample_target<T, D>(x[u], p, g)) {
-        ++outside;
-        continue;
-      }
-      atomicAdd(&hist[target_tile<T, D>(g, 0, p)], 1u);
-      if (g.spill) {
-        for (int S = 1; S < (1 << D); ++S) {
-          if (S & ~g.spill) continue;
-          atomicAdd(&hist[target_tile<T, D>(g, S, p)], 1u);
-        }
-      }
+  for_block_samples<T, D>(X, n, chunk, [&](const T* x) {
+    Located<D> g;
+    if (!locate<T, D, false>(x, p, g)) {
+      ++outside;
+      return;
     }
-  }
+    atomicAdd(&hist[g.t0], 1u);
+    // every nonempty subset of the spill axes (usually one axis)
+    for (int S = g.spill; S; S = (S - 1) & g.spill) atomicAdd(&hist[spill_tile<T, D>(g, S, p)], 1u);
+  });
   __syncthreads();
-  // this block's range in every tile's bucket (offset from the bucket start)
-  unsigned* mine = block_base + (size_t)blockIdx.x * ntiles;
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-    mine[t] = hist[t] ? atomicAdd(&tile_count[t], hist[t]) : 0u;
+  unsigned* mine = block_off + (size_t)blockIdx.x * ntiles;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    const unsigned v = hist[t];
+    mine[t] = v ? atomicAdd(&tile_count[t], v) : 0u;
+  }
   if (n_out) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) outside += __shfl_down_sync(0xffffffffu, outside, off);
@@ -412,13 +462,13 @@ kde_bin_count_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int nti
 
 struct TiledMeta {
   unsigned nitems;
-  unsigned nsplit;
+  unsigned cursor;   // next work item of the accumulation (zero before it starts)
 };
 
-// Exclusive prefix sum over the 1024 threads of the block of one value each.
-__device__ __forceinline__ unsigned block_scan_1024(unsigned v, unsigned* warp_tot,
-                                                    unsigned* total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// Exclusive prefix sum of one value per thread over the block (a multiple
+// of 32 threads, at most 1024); *total gets the sum.
+__device__ __forceinline__ unsigned block_scan(unsigned v, unsigned* warp_tot, unsigned* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   unsigned x = v;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -428,58 +478,24 @@ __device__ __forceinline__ unsigned block_scan_1024(unsigned v, unsigned* warp_t
   if (lane == 31) warp_tot[w] = x;
   __syncthreads();
   if (w == 0) {
-    unsigned t = warp_tot[lane];
+    const unsigned t = lane < nw ? warp_tot[lane] : 0u;
     unsigned s = t;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const unsigned y = __shfl_up_sync(0xffffffffu, s, off);
       if (lane >= off) s += y;
     }
-    warp_tot[lane] = s - t;
+    if (lane < nw) warp_tot[lane] = s - t;
     if (lane == 31) *total = s;
   }
   __syncthreads();
-  return warp_tot[w] + x - v;
+  const unsigned r = warp_tot[w] + x - v;
+  __syncthreads();  // warp_tot may be reused by the next scan
+  return r;
 }
 
-// Bucket starts, work items (tile, first record, end record, split) and the
-// list of split tiles.  One block of 1024
-// threads; thread j owns tiles [j c, (j+1) c) with c = ceil(ntiles / 1024).
-__global__ void __launch_bounds__(1024)
-kde_bin_plan_kernel(const unsigned* __restrict__ tile_count, int ntiles,
-                    unsigned* __restrict__ cursor, uint4* __restrict__ items,
-                    unsigned* __restrict__ split_list, TiledMeta* __restrict__ meta) {
-  __shared__ unsigned warp_tot[32];
-  __shared__ unsigned totals[3];
-  const int per = (ntiles + 1023) / 1024;
-  const int t0 = threadIdx.x * per, t1 = min(ntiles, t0 + per);
-  unsigned rec = 0, nit = 0, nsp = 0;
-  for (int t = t0; t < t1; ++t) {
-    const unsigned c = tile_count[t];
-    const unsigned it = c == 0 ? 1u : (c + kItemRecords - 1) / kItemRecords;
-    rec += c;
-    nit += it;
-    nsp += it > 1;
-  }
-  unsigned r0 = block_scan_1024(rec, warp_tot, &totals[0]);
-  unsigned i0 = block_scan_1024(nit, warp_tot, &totals[1]);
-  unsigned s0 = block_scan_1024(nsp, warp_tot, &totals[2]);
-  for (int t = t0; t < t1; ++t) {
-    const unsigned c = tile_count[t];
-    const unsigned it = c == 0 ? 1u : (c + kItemRecords - 1) / kItemRecords;
-    cursor[t] = r0;
-    for (unsigned j = 0; j < it; ++j) {
-      const unsigned b = r0 + j * kItemRecords, e = min(r0 + c, b + kItemRecords);
-      items[i0 + j] = make_uint4((unsigned)t, b, e, it > 1 ? 1u : 0u);
-    }
-    if (it > 1) split_list[s0++] = (unsigned)t;
-    r0 += c;
-    i0 += it;
-  }
-  if (threadIdx.x == 0) {
-    meta->nitems = totals[1];
-    meta->nsplit = totals[2];
-  }
+__device__ __forceinline__ unsigned items_of(unsigned c) {
+  return c == 0 ? 1u : (c + kItemRecords - 1) / kItemRecords;
 }
 
 // Global cell index of tile-local cell j of tile t (or -1 outside the grid).
@@ -497,103 +513,121 @@ __device__ __forceinline__ int64_t tile_cell(const BinParams<T>& p, int t, int j
   return idx;
 }
 
-// Split tiles zeroed, then records scattered into their buckets: block b
-// takes the same samples as in the count kernel and writes its records of
-// tile t at bucket start + its range offset + a running count kept in
-// shared memory.
+// Bucket starts (every block, from the tile counts), work items (block 0:
+// (tile, first record, end record, split) with at most kItemRecords records
+// each, one item for an empty tile so that its cells are stored as zeros),
+// split tiles' cells zeroed (tile t by block t mod gridDim.x: their items
+// add), then block b takes the same samples as in the count kernel and
+// writes its records of tile t at bucket start + its range offset + a
+// running count kept in shared memory.
 template <typename T, int D>
-__global__ void __launch_bounds__(kScatterThreads)
-kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, BinParams<T> p, int ntiles,
-                       const unsigned* __restrict__ tile_start,
-                       const unsigned* __restrict__ block_base,
-                       const unsigned* __restrict__ split_list,
-                       const TiledMeta* __restrict__ meta, uint4* __restrict__ recs,
-                       unsigned rec_cap, unsigned long long* __restrict__ counts) {
+__global__ void __launch_bounds__(kBinThreads, 2)
+kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, BinParams<T> p,
+                       int ntiles, const unsigned* __restrict__ tile_count,
+                       const unsigned* __restrict__ block_off, uint4* __restrict__ items,
+                       TiledMeta* __restrict__ meta, uint4* __restrict__ recs, unsigned rec_cap,
+                       unsigned long long* __restrict__ counts) {
   extern __shared__ unsigned next[];   // [ntiles]: next slot of this block per tile
-  {
-    const int64_t work = (int64_t)meta->nsplit * kTileCells;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < work;
-         w += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t idx = tile_cell<T, D>(p, (int)split_list[w / kTileCells], (int)(w % kTileCells));
+  __shared__ unsigned warp_tot[32];
+  __shared__ unsigned totals[2];
+  kde::pdl_trigger();
+  kde::pdl_wait();   // tile counts and block offsets of the count kernel
+  const int per = (ntiles + blockDim.x - 1) / blockDim.x;
+  const int t0 = threadIdx.x * per, t1 = min(ntiles, t0 + per);
+  unsigned rec = 0, nit = 0;
+  for (int t = t0; t < t1; ++t) {
+    const unsigned c = __ldcg(tile_count + t);
+    rec += c;
+    nit += items_of(c);
+  }
+  unsigned r0 = block_scan(rec, warp_tot, &totals[0]);
+  unsigned i0 = block_scan(nit, warp_tot, &totals[1]);
+  const unsigned* mine = block_off + (size_t)blockIdx.x * ntiles;
+  for (int t = t0; t < t1; ++t) {
+    const unsigned c = __ldcg(tile_count + t);
+    next[t] = r0 + __ldcg(mine + t);
+    const unsigned it = items_of(c);
+    if (blockIdx.x == 0) {
+      for (unsigned j = 0; j < it; ++j) {
+        const unsigned b = r0 + j * kItemRecords, e = min(r0 + c, b + kItemRecords);
+        items[i0 + j] = make_uint4((unsigned)t, b, e, it > 1 ? 1u : 0u);
+      }
+    }
+    r0 += c;
+    i0 += it;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) meta->nitems = totals[1];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (__ldcg(tile_count + t) <= (unsigned)kItemRecords) continue;
+    for (int j = threadIdx.x; j < kTileCells; j += blockDim.x) {
+      const int64_t idx = tile_cell<T, D>(p, t, j);
       if (idx >= 0) counts[idx] = 0;
     }
   }
-  const unsigned* mine = block_base + (size_t)blockIdx.x * ntiles;
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) next[t] = tile_start[t] + mine[t];
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s0 < n;
-       s0 += kScatterU * stride) {
-    T x[kScatterU][D];
-    load_samples<T, D>(X, n, s0, stride, x);
-#pragma unroll
-    for (int u = 0; u < kScatterU; ++u) {
-      if (s0 + u * stride >= n) break;
-      Target<D> g;
-      if (!sample_target<T, D>(x[u], p, g)) continue;
-      uint4 rec;
-      const int tile0 = record_for<T, D>(g, 0, p, rec);   // fills rec before it is stored
-      const unsigned slot0 = atomicAdd(&next[tile0], 1u);
-      if (KDE_DCHECK(slot0 < rec_cap, KDE_DBG_BIN_SCATTER)) recs[slot0] = rec;
-      if (g.spill) {
-        for (int S = 1; S < (1 << D); ++S) {
-          if (S & ~g.spill) continue;
-          const int tile = record_for<T, D>(g, S, p, rec);
-          const unsigned slot = atomicAdd(&next[tile], 1u);
-          if (KDE_DCHECK(slot < rec_cap, KDE_DBG_BIN_SCATTER)) recs[slot] = rec;
-        }
-      }
+  for_block_samples<T, D>(X, n, chunk, [&](const T* x) {
+    Located<D> g;
+    if (!locate<T, D>(x, p, g)) return;
+    {
+      const uint4 r = make_record<D>(g, 0);   // filled before its slot is taken
+      const unsigned slot = atomicAdd(&next[g.t0], 1u);
+      if (slot < rec_cap) recs[slot] = r;
     }
-  }
+    for (int S = g.spill; S; S = (S - 1) & g.spill) {
+      const uint4 r = make_record<D>(g, S);
+      const unsigned slot = atomicAdd(&next[spill_tile<T, D>(g, S, p)], 1u);
+      if (slot < rec_cap) recs[slot] = r;
+    }
+  });
 }
 
-// One work item per block iteration: its tile's records accumulated in
-// shared memory, then every cell of the tile stored (added, for split
-// tiles).  A weight w <= 2^32 is added as its low 16 bits and its high part
+// Work items taken in turn from meta->cursor: the item's records
+// accumulated in shared memory, then every cell of its tile stored (added,
+// for split tiles; an empty tile's cells are stored as zeros directly).  A
+// weight w <= 2^32 is added as its low 16 bits and its high part
 // w >> 16 <= 2^16 into two 32-bit sums per cell; an item holds at most
 // kItemRecords = 2^13 records and a record adds to a cell at most once, so
 // neither sum exceeds 2^29 and no carry is ever lost: the cell's total is
 // hi 2^16 + lo exactly.  The adds need no return value (fire-and-forget).
-// A record names the corners it adds to (its mask), so the loop has no
-// per-axis tests; every index is still checked against the tile, so a
-// corrupt record cannot reach outside the shared arrays.
+// Every corner of a record is added, into the padded tile (halo corners
+// are not stored); a corrupt record cannot reach outside the shared arrays.
 static_assert(kItemRecords <= (1 << 13), "16-bit split sums must stay below 2^32");
 
-// Offset inside a tile of corner c from the record's base node.
 template <int D>
-__host__ __device__ constexpr int corner_off(int c) {
-  int o = 0;
-  for (int k = 0; k < D; ++k) o += ((c >> (D - 1 - k)) & 1) * Geo<D>::ls(k);
-  return o;
-}
-
-template <int D, int C>
-__device__ __forceinline__ void add_corners(unsigned* lo, unsigned* hi, int j0, unsigned mask,
-                                            const unsigned long long* w) {
-  if constexpr (C < (1 << D)) {
-    constexpr int off = corner_off<D>(C);
-    const int j = j0 + off;
-    if (((mask >> C) & 1) && KDE_DCHECK((unsigned)j < (unsigned)kTileCells, KDE_DBG_BIN_ACCUM) &&
-        (unsigned)j < (unsigned)kTileCells) {
-      atomicAdd(&lo[j], (unsigned)w[C] & 0xFFFFu);
-      atomicAdd(&hi[j], (unsigned)(w[C] >> 16));
-    }
-    add_corners<D, C + 1>(lo, hi, j0, mask, w);
+__device__ __forceinline__ void accumulate_record(unsigned* lo, unsigned* hi, const uint4& rec) {
+  const unsigned q[3] = {rec.x, rec.y, rec.z};
+  // clamped so that every corner stays inside the padded tile, whatever
+  // the record holds
+  constexpr int kMaxBase = pad_cells<D>() - 1 - corner_off<D>((1 << D) - 1);
+  const int j0 = min((int)(rec.w & 0xFFFFu), kMaxBase);
+  unsigned long long w[1 << D];
+  corner_weights<D>(q, w);
+#pragma unroll
+  for (int c = 0; c < (1 << D); ++c) {
+    atomicAdd(&lo[j0 + corner_off<D>(c)], (unsigned)w[c] & 0xFFFFu);
+    atomicAdd(&hi[j0 + corner_off<D>(c)], (unsigned)(w[c] >> 16));
   }
 }
 
 template <typename T, int D>
-__global__ void __launch_bounds__(kAccumThreads)
+__global__ void __launch_bounds__(kAccumThreads, 2)
 kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ items,
-                     const TiledMeta* __restrict__ meta, BinParams<T> p,
+                     TiledMeta* __restrict__ meta, BinParams<T> p,
                      unsigned long long* __restrict__ counts) {
   extern __shared__ __align__(16) unsigned acc_sm[];
   unsigned* lo = acc_sm;
-  unsigned* hi = acc_sm + kTileCells;
-  constexpr unsigned kFieldMask = (1u << Geo<D>::bits) - 1u;
-  const unsigned nitems = meta->nitems;
-  for (unsigned it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const uint4 item = items[it];
+  unsigned* hi = acc_sm + pad_alloc<D>();
+  __shared__ unsigned cur_item;
+  kde::pdl_trigger();
+  kde::pdl_wait();   // items and records of the scatter kernel
+  const unsigned nitems = __ldcg(&meta->nitems);
+  for (;;) {
+    if (threadIdx.x == 0) cur_item = atomicAdd(&meta->cursor, 1u);
+    __syncthreads();
+    const unsigned it = cur_item;
+    __syncthreads();   // cur_item is rewritten at the next turn
+    if (it >= nitems) break;
+    const uint4 item = __ldcg(items + it);
     // the tile's origin and extent inside the grid
     int64_t origin = 0;
     int ext[D];
@@ -604,41 +638,44 @@ kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ i
       origin += (int64_t)o * p.ax[k].stride;
       ext[k] = min(Geo<D>::ext(k), p.ax[k].M - o);
     }
-    for (int j = threadIdx.x; j < kTileCells / 4; j += blockDim.x) {
-      reinterpret_cast<uint4*>(lo)[j] = make_uint4(0, 0, 0, 0);
-      reinterpret_cast<uint4*>(hi)[j] = make_uint4(0, 0, 0, 0);
-    }
-    __syncthreads();
-    for (unsigned r = item.y + threadIdx.x; r < item.z; r += blockDim.x) {
-      const uint4 rec = __ldcs(recs + r);   // read once: stream past L1
-      const unsigned q[3] = {rec.x, rec.y, rec.z};
-      int j0 = 0;
+    const bool empty = item.y >= item.z;
+    if (!empty) {
+      for (int j = threadIdx.x; j < pad_alloc<D>() / 2; j += blockDim.x)
+        reinterpret_cast<uint4*>(lo)[j] = make_uint4(0, 0, 0, 0);   // lo and hi
+      __syncthreads();
+      for (unsigned r0 = item.y + threadIdx.x; r0 < item.z; r0 += kAccumU * blockDim.x) {
+        uint4 rec[kAccumU];
 #pragma unroll
-      for (int k = 0; k < D; ++k)
-        j0 += ((int)((rec.w >> (Geo<D>::bits * k)) & kFieldMask) - 1) * Geo<D>::ls(k);
-      unsigned long long w[1 << D];
-      corner_weights<D>(q, w);
-      add_corners<D, 0>(lo, hi, j0, rec.w >> 24, w);
+        for (int u = 0; u < kAccumU; ++u) {
+          const unsigned r = r0 + u * blockDim.x;
+          rec[u] = r < item.z ? __ldcg(recs + r) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < kAccumU; ++u)
+          if (r0 + u * blockDim.x < item.z) accumulate_record<D>(lo, hi, rec[u]);
+      }
+      __syncthreads();
     }
-    __syncthreads();
     for (int j = threadIdx.x; j < kTileCells; j += blockDim.x) {
       int64_t idx = origin;
+      int jp = 0;
       bool in = true;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const int l = (j >> Geo<D>::lsh(k)) & (Geo<D>::ext(k) - 1);
         in &= l < ext[k];
         idx += (int64_t)l * p.ax[k].stride;
+        jp += (l + 1) * pst<D>(k);
       }
       if (!in || !KDE_DCHECK(idx >= 0 && idx < p.cells, KDE_DBG_BIN_ACCUM)) continue;
-      const unsigned long long v = ((unsigned long long)hi[j] << 16) + lo[j];
+      const unsigned long long v = empty ? 0ull : ((unsigned long long)hi[jp] << 16) + lo[jp];
       if (item.w) {
         if (v) atomicAdd(counts + idx, v);
       } else {
         counts[idx] = v;
       }
     }
-    __syncthreads();
+    __syncthreads();   // the shared sums are cleared at the next turn
   }
 }
 
@@ -654,19 +691,20 @@ int num_sms() {
 }
 
 // Tile counts (tile shapes: Geo<d>) and the workspace layout of the tiled
-// path.
-// Grid of the count and scatter kernels (the same in both, and part of the
-// workspace size, so it does not depend on the device): about two blocks per
-// SM of a GB300.
+// path.  Grid of the count and scatter kernels (the same in both, and part
+// of the workspace size, so it does not depend on the device): at most 304
+// blocks (two per SM of a GB300), at least 2048 samples each.
 constexpr int kBinBlocks = 304;
+constexpr int64_t kMinBlockSamples = 2048;
 
 struct TiledLayout {
   int tile[KDE_MAX_D];
   int ntiles[KDE_MAX_D];
   int ntiles_total;
   int blocks;                     // grid of the count and scatter kernels
+  int64_t chunk;                  // samples per block (a multiple of kBinThreads)
   int64_t max_records, max_items;
-  size_t off_count, off_cursor, off_meta, off_items, off_split, off_base, off_recs, total;
+  size_t off_count, off_meta, off_items, off_base, off_recs, total;
 };
 
 bool tiled_layout(int64_t n, int d, const int64_t* M, TiledLayout* t) {
@@ -681,15 +719,15 @@ bool tiled_layout(int64_t n, int d, const int64_t* M, TiledLayout* t) {
   t->max_records = (n > 0 ? n : 1) << d;
   if (t->max_records >= (int64_t(1) << 32)) return false;
   t->max_items = t->ntiles_total + t->max_records / kItemRecords + 1;
-  const int64_t want = (n + (int64_t)kCountThreads * kScatterU - 1) / ((int64_t)kCountThreads * kScatterU);
+  const int64_t want = (n + kMinBlockSamples - 1) / kMinBlockSamples;
   t->blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, kBinBlocks));
+  const int64_t per = (std::max<int64_t>(n, 1) + t->blocks - 1) / t->blocks;
+  t->chunk = (per + kBinThreads - 1) / kBinThreads * kBinThreads;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   t->off_count = 0;
-  t->off_cursor = up((size_t)t->ntiles_total * 4);
-  t->off_meta = t->off_cursor + up((size_t)t->ntiles_total * 4);
+  t->off_meta = up((size_t)t->ntiles_total * 4);
   t->off_items = t->off_meta + 256;
-  t->off_split = t->off_items + up((size_t)t->max_items * 16);
-  t->off_base = t->off_split + up((size_t)t->ntiles_total * 4);
+  t->off_base = t->off_items + up((size_t)t->max_items * 16);
   t->off_recs = t->off_base + up((size_t)t->blocks * t->ntiles_total * 4);
   t->total = t->off_recs + up((size_t)t->max_records * 16);
   return true;
@@ -782,6 +820,9 @@ cudaError_t allow_smem(F* fn, size_t bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Three launches: the count kernel (after the tile counts and the item
+// cursor are cleared), then the scatter and accumulation kernels as
+// programmatic dependents of the kernel before each.
 template <typename T, int D>
 kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double* hi,
                           const int64_t* M, unsigned long long* counts,
@@ -789,50 +830,46 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
                           cudaStream_t stream) {
   BinParams<T> p = make_params<T>(D, lo, hi, M, &t);
   unsigned* tile_count = (unsigned*)(ws + t.off_count);
-  unsigned* cursor = (unsigned*)(ws + t.off_cursor);
   TiledMeta* meta = (TiledMeta*)(ws + t.off_meta);
   uint4* items = (uint4*)(ws + t.off_items);
-  unsigned* split = (unsigned*)(ws + t.off_split);
-  unsigned* block_base = (unsigned*)(ws + t.off_base);
+  unsigned* block_off = (unsigned*)(ws + t.off_base);
   uint4* recs = (uint4*)(ws + t.off_recs);
   const int nt = t.ntiles_total;
   const int sms = num_sms();
-  cudaError_t e = cudaMemsetAsync(tile_count, 0, (size_t)nt * 4, stream);
+  cudaError_t e = cudaMemsetAsync(ws, 0, t.off_meta + sizeof(TiledMeta), stream);
   if (e != cudaSuccess) return kde::cuda_fail(e, "cudaMemsetAsync(tile counts)");
-  const int grid_s = t.blocks;
+  const size_t smem_t = (size_t)nt * 4;
   {
     auto* fn = kde_bin_count_kernel<T, D>;
-    const size_t smem = (size_t)nt * 4;
-    if ((e = allow_smem(fn, smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
+    if ((e = allow_smem(fn, smem_t)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
     kde::LaunchScope ls("kde_bin_count_kernel", stream);
-    fn<<<grid_s, kCountThreads, smem, stream>>>(X, n, p, nt, tile_count, block_base, n_out);
+    fn<<<t.blocks, kBinThreads, smem_t, stream>>>(X, n, t.chunk, p, nt, tile_count, block_off,
+                                                  n_out);
     if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_count_kernel");
   }
   {
-    kde::LaunchScope ls("kde_bin_plan_kernel", stream);
-    kde_bin_plan_kernel<<<1, 1024, 0, stream>>>(tile_count, nt, cursor, items, split, meta);
-    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_plan_kernel");
-  }
-  {
     auto* fn = kde_bin_scatter_kernel<T, D>;
-    const size_t smem = (size_t)nt * 4;
-    if ((e = allow_smem(fn, smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
+    if ((e = allow_smem(fn, smem_t)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
     kde::LaunchScope ls("kde_bin_scatter_kernel", stream);
-    fn<<<grid_s, kScatterThreads, smem, stream>>>(X, n, p, nt, cursor, block_base, split, meta,
-                                                   recs, (unsigned)t.max_records, counts);
-    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scatter_kernel");
+    e = kde::launch_pdl(fn, t.blocks, kBinThreads, smem_t, stream, X, n, t.chunk, p, nt,
+                        (const unsigned*)tile_count, (const unsigned*)block_off, items, meta, recs,
+                        (unsigned)t.max_records, counts);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scatter_kernel");
   }
   {
     auto* fn = kde_bin_accum_kernel<T, D>;
-    const size_t smem = 2 * (size_t)kTileCells * sizeof(unsigned);
+    const size_t smem = 2 * (size_t)pad_alloc<D>() * sizeof(unsigned);
     if ((e = allow_smem(fn, smem)) != cudaSuccess) return kde::cuda_fail(e, "smem attr");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kAccumThreads, smem);
     if (e != cudaSuccess) return kde::cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     const int grid_a = (int)std::min<int64_t>(t.max_items, (int64_t)std::max(1, per_sm) * sms);
     kde::LaunchScope ls("kde_bin_accum_kernel", stream);
-    fn<<<grid_a, kAccumThreads, smem, stream>>>(recs, items, meta, p, counts);
-    if ((e = cudaGetLastError()) != cudaSuccess) return kde::cuda_fail(e, "kde_bin_accum_kernel");
+    e = kde::launch_pdl(fn, grid_a, kAccumThreads, smem, stream, (const uint4*)recs,
+                        (const uint4*)items, meta, p, counts);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return kde::cuda_fail(e, "kde_bin_accum_kernel");
   }
   return KDE_OK;
 }
