@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/kde_gb300.h"
+#include "fx_dft.cuh"
 
 namespace kde {
 
@@ -160,6 +161,21 @@ template <typename V, int R, bool INV> struct SmallDFT {
 #pragma unroll
     for (int k = 0; k < R; ++k) x[k] = y[k];
   }
+};
+
+// FP32: the same DFTs in packed f32x2 arithmetic (the two-phase engine's
+// base radices); each component is rounded as in the scalar form.
+template <int R, bool INV> struct SmallDFT<float2, R, INV> {
+  __device__ __forceinline__ static void run(float2* x) { fx::BaseDFT<R, INV>::run(x); }
+};
+template <bool INV> struct SmallDFT<float2, 2, INV> {
+  __device__ __forceinline__ static void run(float2* x) { fx::BaseDFT<2, INV>::run(x); }
+};
+template <bool INV> struct SmallDFT<float2, 4, INV> {
+  __device__ __forceinline__ static void run(float2* x) { fx::BaseDFT<4, INV>::run(x); }
+};
+template <bool INV> struct SmallDFT<float2, 8, INV> {
+  __device__ __forceinline__ static void run(float2* x) { fx::BaseDFT<8, INV>::run(x); }
 };
 
 // The threads of one line: index lt in [0, tpl) and the barrier they share.

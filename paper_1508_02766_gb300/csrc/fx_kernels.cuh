@@ -99,6 +99,13 @@ constexpr int block_limit() {
   return (N1T > 0 && N1T <= kSmallMax && N2T <= kSmallMax) || N1T == 0 ? kThreadsSmall : kThreadsLarge;
 }
 
+// A factor of the line split: the compile-time one where the kernel was
+// compiled for its split (NT > 0), else the runtime one.
+template <int NT>
+__device__ __forceinline__ int factor(int runtime) {
+  return NT > 0 ? NT : runtime;
+}
+
 // Runtime split of a line: P = N1 N2; k / N1 = umulhi(k, magic1) for the
 // k < 2^13 that occur (magic1 = floor(2^32 / N1) + 1).
 struct Line {
@@ -170,10 +177,10 @@ __device__ __forceinline__ void rows_slab(RowsArgs& a, KGen<float>& g) {
 
 enum { SRC_COUNTS = 0, SRC_KGEN = 1 };
 
-template <int N1, int SRC>
+template <int N1, int SRC, int N2T = 0>
 __device__ __forceinline__ void rows_a_fwd(const RowsArgs& a, const long long* __restrict__ counts,
                                            const KGen<float>& g, float2* sm) {
-  const int N2 = a.ln.N2;
+  const int N2 = factor<N2T>(a.ln.N2);
   const int t = threadIdx.x;
   if (t >= a.B * N2) return;
   const int b = t / N2, n2 = t - b * N2;
@@ -206,9 +213,9 @@ __device__ __forceinline__ void rows_a_fwd(const RowsArgs& a, const long long* _
 
 // Phase B of the forward row pass: Z[k1 + N1 k2] written back to the slots
 // (k1, k2) the thread read from.
-template <int N2>
+template <int N2, int N1T = 0>
 __device__ __forceinline__ void rows_b_fwd(const RowsArgs& a, float2* sm) {
-  const int N1 = a.ln.N1;
+  const int N1 = factor<N1T>(a.ln.N1);
   const int t = threadIdx.x;
   if (t >= a.B * N1) return;
   const int b = t / N1, k1 = t - b * N1;
@@ -222,8 +229,9 @@ __device__ __forceinline__ void rows_b_fwd(const RowsArgs& a, float2* sm) {
 }
 
 // X = F(x), Y = F(y) from Z = F(x + i y) on [0, Q), stored to both rows.
+template <int N1T = 0, int N2T = 0>
 __device__ __forceinline__ void rows_split_store(const RowsArgs& a, const float2* sm) {
-  const int N1 = a.ln.N1, P = a.ln.P;
+  const int N1 = factor<N1T>(a.ln.N1), P = N1T > 0 && N2T > 0 ? N1T * N2T : a.ln.P;
   for (int b = 0; b < a.B; ++b) {
     const int64_t r0 = 2 * ((int64_t)blockIdx.x * a.B + b);
     if (r0 >= a.nrows) break;
@@ -232,8 +240,8 @@ __device__ __forceinline__ void rows_split_store(const RowsArgs& a, const float2
     float2* o0 = a.out + r0 * a.Q;
     for (int k = threadIdx.x; k < a.Q; k += blockDim.x) {
       const int km = k == 0 ? 0 : P - k;
-      const int q = (int)__umulhi((unsigned)k, a.ln.magic1);
-      const int qm = (int)__umulhi((unsigned)km, a.ln.magic1);
+      const int q = N1T > 0 ? k / N1T : (int)__umulhi((unsigned)k, a.ln.magic1);
+      const int qm = N1T > 0 ? km / N1T : (int)__umulhi((unsigned)km, a.ln.magic1);
       const float2 zk = z[(k - q * N1) * a.SK + q];
       const float2 zm = z[(km - qm * N1) * a.SK + qm];
       if (!KDE_DCHECK(k < a.Q && km < P, KDE_DBG_ROWS_STORE)) continue;
@@ -287,18 +295,19 @@ kde_fx_rows_fwd_kernel(RowsArgs a, const long long* __restrict__ counts, KGen<fl
     rows_stage_kgen(a, g, fx_sm + a.B * a.ln.N1 * a.SK);
     __syncthreads();
   }
-  size_call<N1T, CLS>(a.ln.N1, [&](auto N) { rows_a_fwd<decltype(N)::value, SRC>(a, counts, g, fx_sm); });
+  size_call<N1T, CLS>(a.ln.N1,
+                      [&](auto N) { rows_a_fwd<decltype(N)::value, SRC, N2T>(a, counts, g, fx_sm); });
   __syncthreads();
-  size_call<N2T, CLS>(a.ln.N2, [&](auto N) { rows_b_fwd<decltype(N)::value>(a, fx_sm); });
+  size_call<N2T, CLS>(a.ln.N2, [&](auto N) { rows_b_fwd<decltype(N)::value, N1T>(a, fx_sm); });
   __syncthreads();
-  rows_split_store(a, fx_sm);
+  rows_split_store<N1T, N2T>(a, fx_sm);
 }
 
 // Inverse row pass, phase B: the full line Z_k = X_k + i Y_k rebuilt from
 // the two half spectra (Hermitian symmetry above Q), inverse N2-point DFT.
-template <int N2>
+template <int N2, int N1T = 0>
 __device__ __forceinline__ void rows_b_inv(const RowsArgs& a, float2* sm) {
-  const int N1 = a.ln.N1, P = a.ln.P;
+  const int N1 = factor<N1T>(a.ln.N1), P = N1T > 0 ? N1T * N2 : a.ln.P;
   const int t = threadIdx.x;
   if (t >= a.B * N1) return;
   const int b = t / N1, k1 = t - b * N1;
@@ -321,9 +330,9 @@ __device__ __forceinline__ void rows_b_inv(const RowsArgs& a, float2* sm) {
 }
 
 // Inverse row pass, phase A: inverse N1-point DFT, rows cropped to Mout.
-template <int N1>
+template <int N1, int N2T = 0>
 __device__ __forceinline__ void rows_a_inv(const RowsArgs& a, const float2* sm) {
-  const int N2 = a.ln.N2;
+  const int N2 = factor<N2T>(a.ln.N2);
   const int t = threadIdx.x;
   if (t >= a.B * N2) return;
   const int b = t / N2, n2 = t - b * N2;
@@ -354,9 +363,9 @@ kde_fx_rows_c2r_kernel(RowsArgs a) {
   extern __shared__ float2 fx_sm[];
   KGen<float> g_unused;
   rows_slab(a, g_unused);
-  size_call<N2T, CLS>(a.ln.N2, [&](auto N) { rows_b_inv<decltype(N)::value>(a, fx_sm); });
+  size_call<N2T, CLS>(a.ln.N2, [&](auto N) { rows_b_inv<decltype(N)::value, N1T>(a, fx_sm); });
   __syncthreads();
-  size_call<N1T, CLS>(a.ln.N1, [&](auto N) { rows_a_inv<decltype(N)::value>(a, fx_sm); });
+  size_call<N1T, CLS>(a.ln.N1, [&](auto N) { rows_a_inv<decltype(N)::value, N2T>(a, fx_sm); });
 }
 
 // ---------------------------------------------------------------------------
@@ -418,9 +427,9 @@ __device__ __forceinline__ int64_t col_first(const ColsArgs& a) {
   return (int64_t)blockIdx.x * a.B * (MODE == COL_FWD_REAL ? 2 : 1);
 }
 
-template <int N1, int MODE>
+template <int N1, int MODE, int N2T = 0>
 __device__ __forceinline__ void cols_a_fwd(const ColsArgs& a, float2* sm) {
-  const int N2 = a.ln.N2;
+  const int N2 = factor<N2T>(a.ln.N2);
   const int t = threadIdx.x;
   if (t >= (a.B << 0) * N2) return;
   const int b = t & (a.B - 1), n2 = t >> a.lgB;
@@ -442,20 +451,33 @@ __device__ __forceinline__ void cols_a_fwd(const ColsArgs& a, float2* sm) {
   } else {
     const int64_t s = col_first<MODE>(a) + b;
     const bool v = s < a.S;
+    if (a.Lw < 0) {
+      // plain rows: position pos reads row pos < Nin; the row pointer steps
+      // by N2 rows per value
+      const float2* p = in + s + (int64_t)n2 * a.S;
+      const int64_t step = (int64_t)N2 * a.S;
 #pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) {
-      const int j = col_source(n2 + N2 * n1, a.ln.P, a.Lw, a.Nin);
-      x[n1] = (j >= 0 && v && KDE_DCHECK(j < a.Nin, KDE_DBG_COLS_LOAD))
-                  ? __ldg(in + (int64_t)j * a.S + s)
-                  : make_float2(0.f, 0.f);
+      for (int n1 = 0; n1 < N1; ++n1) {
+        const int pos = n2 + N2 * n1;
+        x[n1] = (pos < a.Nin && v) ? __ldg(p) : make_float2(0.f, 0.f);
+        p += step;
+      }
+    } else {
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) {
+        const int j = col_source(n2 + N2 * n1, a.ln.P, a.Lw, a.Nin);
+        x[n1] = (j >= 0 && v && KDE_DCHECK(j < a.Nin, KDE_DBG_COLS_LOAD))
+                    ? __ldg(in + (int64_t)j * a.S + s)
+                    : make_float2(0.f, 0.f);
+      }
     }
   }
   a_fwd_store<N1>(x, n2, a.tw, sm + b + n2 * a.B, a.SK);
 }
 
-template <int N2, int MODE>
+template <int N2, int MODE, int N1T = 0>
 __device__ __forceinline__ void cols_b_fwd(const ColsArgs& a, float2* sm) {
-  const int N1 = a.ln.N1;
+  const int N1 = factor<N1T>(a.ln.N1);
   const int t = threadIdx.x;
   if (t >= a.B * N1) return;
   const int b = t & (a.B - 1), k1 = t >> a.lgB;
@@ -467,10 +489,13 @@ __device__ __forceinline__ void cols_b_fwd(const ColsArgs& a, float2* sm) {
   if constexpr (MODE == COL_FWD) {
     const int64_t s = col_first<MODE>(a) + b;
     if (s >= a.S) return;
-    float2* out = a.out + s;
+    float2* out = a.out + s + (int64_t)k1 * a.S;
+    const int64_t step = (int64_t)N1 * a.S;
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2)
-      if (KDE_DCHECK(k1 + N1 * k2 < a.ln.P, KDE_DBG_COLS_STORE)) out[(int64_t)(k1 + N1 * k2) * a.S] = y[k2];
+    for (int k2 = 0; k2 < N2; ++k2) {
+      if (KDE_DCHECK(k1 + N1 * k2 < a.ln.P, KDE_DBG_COLS_STORE)) *out = y[k2];
+      out += step;
+    }
   } else if constexpr (MODE == COL_FWD_REAL) {
     const int64_t s = col_first<MODE>(a) + 2 * b;
     if (s >= a.S) return;
@@ -492,9 +517,12 @@ __device__ __forceinline__ void cols_b_fwd(const ColsArgs& a, float2* sm) {
   } else {  // COL_MID: times K, inverse, back to the same slots
     const int64_t s = col_first<MODE>(a) + b;
     const bool v = s < a.S;
+    const float* pk = a.K + s + (int64_t)k1 * a.S;
+    const int64_t step = (int64_t)N1 * a.S;
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) {
-      const float kv = v ? __ldg(a.K + (int64_t)(k1 + N1 * k2) * a.S + s) : 0.f;
+      const float kv = v ? __ldg(pk) : 0.f;
+      pk += step;
       y[k2].x *= kv;
       y[k2].y *= kv;
     }
@@ -503,26 +531,29 @@ __device__ __forceinline__ void cols_b_fwd(const ColsArgs& a, float2* sm) {
 }
 
 // COL_INV phase B: X[k1 + N1 k2] from the input rows, inverse N2-point DFT.
-template <int N2>
+template <int N2, int N1T = 0>
 __device__ __forceinline__ void cols_b_inv(const ColsArgs& a, float2* sm) {
-  const int N1 = a.ln.N1;
+  const int N1 = factor<N1T>(a.ln.N1);
   const int t = threadIdx.x;
   if (t >= a.B * N1) return;
   const int b = t & (a.B - 1), k1 = t >> a.lgB;
   const int64_t s = col_first<COL_INV>(a) + b;
   const bool v = s < a.S;
-  const float2* in = a.in + s;
+  const float2* in = a.in + s + (int64_t)k1 * a.S;
+  const int64_t step = (int64_t)N1 * a.S;
   float2 y[N2];
 #pragma unroll
-  for (int k2 = 0; k2 < N2; ++k2)
-    y[k2] = v ? __ldg(in + (int64_t)(k1 + N1 * k2) * a.S) : make_float2(0.f, 0.f);
+  for (int k2 = 0; k2 < N2; ++k2) {
+    y[k2] = v ? __ldg(in) : make_float2(0.f, 0.f);
+    in += step;
+  }
   b_inv_store<N2>(y, k1, a.tw, sm + b + k1 * a.SK, a.B);
 }
 
 // Inverse phase A: inverse N1-point DFT, rows cropped to Nout.
-template <int N1, int MODE>
+template <int N1, int MODE, int N2T = 0>
 __device__ __forceinline__ void cols_a_inv(const ColsArgs& a, const float2* sm) {
-  const int N2 = a.ln.N2;
+  const int N2 = factor<N2T>(a.ln.N2);
   const int t = threadIdx.x;
   if (t >= a.B * N2) return;
   const int b = t & (a.B - 1), n2 = t >> a.lgB;
@@ -533,11 +564,13 @@ __device__ __forceinline__ void cols_a_inv(const ColsArgs& a, const float2* sm) 
 #pragma unroll
   for (int k1 = 0; k1 < N1; ++k1) x[k1] = src[k1 * a.SK];
   idft<N1>(x);
-  float2* out = a.out + s;
+  float2* out = a.out + s + (int64_t)n2 * a.S;
+  const int64_t step = (int64_t)N2 * a.S;
 #pragma unroll
   for (int n1 = 0; n1 < N1; ++n1) {
     const int pos = n2 + N2 * n1;
-    if (pos < a.Nout && KDE_DCHECK(s < a.S, KDE_DBG_COLS_STORE)) out[(int64_t)pos * a.S] = x[n1];
+    if (pos < a.Nout && KDE_DCHECK(s < a.S, KDE_DBG_COLS_STORE)) *out = x[n1];
+    out += step;
   }
 }
 
@@ -549,16 +582,16 @@ kde_fx_cols_kernel(ColsArgs a) {
   extern __shared__ float2 fx_sm[];
   cols_slab(a);
   if constexpr (MODE == COL_INV) {
-    size_call<N2T, CLS>(a.ln.N2, [&](auto N) { cols_b_inv<decltype(N)::value>(a, fx_sm); });
+    size_call<N2T, CLS>(a.ln.N2, [&](auto N) { cols_b_inv<decltype(N)::value, N1T>(a, fx_sm); });
     __syncthreads();
-    size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_inv<decltype(N)::value, MODE>(a, fx_sm); });
+    size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_inv<decltype(N)::value, MODE, N2T>(a, fx_sm); });
   } else {
-    size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_fwd<decltype(N)::value, MODE>(a, fx_sm); });
+    size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_fwd<decltype(N)::value, MODE, N2T>(a, fx_sm); });
     __syncthreads();
-    size_call<N2T, CLS>(a.ln.N2, [&](auto N) { cols_b_fwd<decltype(N)::value, MODE>(a, fx_sm); });
+    size_call<N2T, CLS>(a.ln.N2, [&](auto N) { cols_b_fwd<decltype(N)::value, MODE, N1T>(a, fx_sm); });
     if constexpr (MODE == COL_MID || MODE == COL_AUTO) {
       __syncthreads();
-      size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_inv<decltype(N)::value, MODE>(a, fx_sm); });
+      size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_inv<decltype(N)::value, MODE, N2T>(a, fx_sm); });
     }
   }
 }
