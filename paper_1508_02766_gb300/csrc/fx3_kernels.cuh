@@ -264,11 +264,15 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
       const int k1 = r % N1, k2 = r / N1;
       const int64_t s = first + c;
       const bool v = s < a.S;
-      const float2* in = a.in + s;
+      // rows k1 + N1 (k2 + N2 k3): one pointer stepped by N1 N2 rows
+      const float2* in = a.in + s + (int64_t)(k1 + N1 * k2) * a.S;
+      const int64_t step = (int64_t)(N1 * N2) * a.S;
       float2 z[N3];
 #pragma unroll
-      for (int k3 = 0; k3 < N3; ++k3)
-        z[k3] = v ? __ldg(in + (int64_t)(k1 + N1 * (k2 + N2 * k3)) * a.S) : make_float2(0.f, 0.f);
+      for (int k3 = 0; k3 < N3; ++k3) {
+        z[k3] = v ? __ldg(in) : make_float2(0.f, 0.f);
+        in += step;
+      }
       p3_c_inv<N1, N2, N3>(z, k1, k2, a.tw, line, SK, W);
     }
   } else {
@@ -292,10 +296,20 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
       } else {
         const int64_t s = first + c;
         const bool v = s < a.S;
+        if (a.Lw < 0) {  // plain rows: position pos reads row pos < Nin
+          const float2* p = in + s + (int64_t)n23 * a.S;
+          const int64_t step = (int64_t)N23 * a.S;
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) {
-          const int j = col_source(n23 + N23 * n1, P, a.Lw, a.Nin);
-          x[n1] = (j >= 0 && v) ? __ldg(in + (int64_t)j * a.S + s) : make_float2(0.f, 0.f);
+          for (int n1 = 0; n1 < N1; ++n1) {
+            x[n1] = (n23 + N23 * n1 < a.Nin && v) ? __ldg(p) : make_float2(0.f, 0.f);
+            p += step;
+          }
+        } else {
+#pragma unroll
+          for (int n1 = 0; n1 < N1; ++n1) {
+            const int j = col_source(n23 + N23 * n1, P, a.Lw, a.Nin);
+            x[n1] = (j >= 0 && v) ? __ldg(in + (int64_t)j * a.S + s) : make_float2(0.f, 0.f);
+          }
         }
       }
       p3_a_fwd<N1, N2, N3>(x, n23, a.tw, line, SK, W);
@@ -310,9 +324,13 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
       if constexpr (MODE == COL_FWD) {
         const int64_t s = first + c;
         if (s < a.S) {
-          float2* out = a.out + s;
+          float2* out = a.out + s + (int64_t)(k1 + N1 * k2) * a.S;
+          const int64_t step = (int64_t)(N1 * N2) * a.S;
 #pragma unroll
-          for (int k3 = 0; k3 < N3; ++k3) out[(int64_t)(k1 + N1 * (k2 + N2 * k3)) * a.S] = z[k3];
+          for (int k3 = 0; k3 < N3; ++k3) {
+            *out = z[k3];
+            out += step;
+          }
         }
       } else if constexpr (MODE == COL_FWD_REAL) {
         const int64_t s = first + 2 * c;
@@ -336,9 +354,12 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
         } else {
           const int64_t s = first + c;
           const bool v = s < a.S;
+          const float* pk = a.K + s + (int64_t)(k1 + N1 * k2) * a.S;
+          const int64_t step = (int64_t)(N1 * N2) * a.S;
 #pragma unroll
           for (int k3 = 0; k3 < N3; ++k3) {
-            const float kv = v ? __ldg(a.K + (int64_t)(k1 + N1 * (k2 + N2 * k3)) * a.S + s) : 0.f;
+            const float kv = v ? __ldg(pk) : 0.f;
+            pk += step;
             z[k3].x *= kv;
             z[k3].y *= kv;
           }
@@ -356,11 +377,12 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
       if (s < a.S) {
         float2 x[N1];
         p3_a_inv<N1, N2, N3>(x, r, line, SK, W);
-        float2* out = a.out + s;
+        float2* out = a.out + s + (int64_t)r * a.S;
+        const int64_t step = (int64_t)N23 * a.S;
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
-          const int pos = r + N23 * n1;
-          if (pos < a.Nout) out[(int64_t)pos * a.S] = x[n1];
+          if (r + N23 * n1 < a.Nout) *out = x[n1];
+          out += step;
         }
       }
     }
