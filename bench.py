@@ -45,6 +45,10 @@ def parse(argv=None):
     ap.add_argument("--e2e-graph-stages", type=int, default=2,
                     help="pipeline stages (datasets) captured per CUDA graph in the e2e stream")
     ap.add_argument("--bin-method", default="auto", choices=["auto", "direct", "tiled"])
+    ap.add_argument("--counts", default="zeroed_per_step", choices=["zeroed_per_step", "kept_zero"],
+                    help="zeroed_per_step: kde_bin zeroes them before binning; kept_zero: "
+                         "binning adds (kde_bin_accumulate) and the evaluation clears the counts "
+                         "(kde_fft_eval_consume), measured slower with L2 flushed between steps")
     ap.add_argument("--range", default="corrected", choices=["corrected", "per_axis"],
                     help="support of the kernel grid: the corrected range of Eq. 15 or the "
                          "per-axis (diagonal) range")
@@ -559,7 +563,10 @@ def kde_arm(args, workload, world, rank, local, dev):
     info = plan.info
     X_host = torch.from_numpy(np.ascontiguousarray(w.X)).pin_memory()
     X = X_host.to(dev)
-    counts = torch.empty(w.M, dtype=torch.int64, device=dev)
+    # kept_zero: zeroed once here; every step then bins by adding and its
+    # evaluation leaves them zeroed for the next step
+    kept = args.counts == "kept_zero"
+    counts = torch.zeros(w.M, dtype=torch.int64, device=dev)
     Ks = torch.empty(info.kspec_elems, dtype=plan.real_dtype(), device=dev)
     dens = torch.empty(w.M, dtype=plan.real_dtype(), device=dev)
     ws = plan.workspace(dev)
@@ -577,10 +584,10 @@ def kde_arm(args, workload, world, rank, local, dev):
     # stream while the samples are binned; the FFT evaluation waits for both.
     side = torch.cuda.Stream(device=dev, priority=-1)
     step_dev = kde.PreparedPath(plan, X, counts, Ks, dens, ws, bin_workspace=bws, stream=stream,
-                                kgen_stream=side)
+                                kgen_stream=side, counts_kept_zero=kept)
     Xe = torch.empty_like(X)
     step_e2e = kde.PreparedPath(plan, Xe, counts, Ks, dens, ws, bin_workspace=bws, stream=stream,
-                                kgen_stream=side)
+                                kgen_stream=side, counts_kept_zero=kept)
     fork = torch.cuda.Event()
     join = torch.cuda.Event()
 
@@ -660,7 +667,8 @@ def kde_arm(args, workload, world, rank, local, dev):
     # Per-kernel durations: the same steps launched one by one on one stream
     # (no overlap, so each event pair measures its kernel alone) with the
     # library's event pairs around every kernel (graph replays carry none).
-    step_serial = kde.PreparedPath(plan, X, counts, Ks, dens, ws, bin_workspace=bws, stream=stream)
+    step_serial = kde.PreparedPath(plan, X, counts, Ks, dens, ws, bin_workspace=bws, stream=stream,
+                                   counts_kept_zero=kept)
     kde.profile_enable(True)
     with torch.cuda.stream(stream):
         for i in range(args.steps):
@@ -688,7 +696,7 @@ def kde_arm(args, workload, world, rank, local, dev):
     Db = [dens, torch.empty_like(dens)]
     Hb = [dens_host, torch.empty(w.M, dtype=plan.real_dtype()).pin_memory()]
     paths = [step_e2e, kde.PreparedPath(plan, Xb[1], counts, Ks, Db[1], ws, bin_workspace=bws,
-                                        stream=stream, kgen_stream=side)]
+                                        stream=stream, kgen_stream=side, counts_kept_zero=kept)]
     ev_fork, ev_up, ev_down = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
 
     def stage(b):
@@ -754,7 +762,7 @@ def kde_arm(args, workload, world, rank, local, dev):
     # between steps (the counts and spectra are rewritten each step).
     dens_zc = torch.empty(w.M, dtype=plan.real_dtype()).pin_memory()
     path_zc = kde.PreparedPath(plan, X_host, counts, Ks, dens_zc, ws, bin_workspace=bws,
-                               stream=stream, kgen_stream=side)
+                               stream=stream, kgen_stream=side, counts_kept_zero=kept)
     with torch.cuda.stream(stream):
         for _ in range(2):
             enqueue(path_zc)
@@ -813,6 +821,11 @@ def kde_arm(args, workload, world, rank, local, dev):
                        "launch": "CUDA graph replay per step" if graph is not None else "stream launches",
                        "streams": "kernel grid on a side stream, concurrent with binning",
                        "binning": method, "range": args.range, "layout": args.layout,
+                       "counts": ("kept at zero between steps: binning adds into them "
+                                  "(kde_bin_accumulate) and the evaluation's second pass clears "
+                                  "them once its first pass has read them (kde_fft_eval_consume); "
+                                  "zeroed once before the first step") if kept else
+                                 "zeroed by kde_bin before every binning",
                        "first_pass": "split-TF32 DFT matrix on the tensor cores" if args.dft == "tc"
                        else "FFT",
                        **({"slab_passes": "last two axes per slab on 8-block clusters"}
@@ -866,8 +879,10 @@ def kde_arm(args, workload, world, rank, local, dev):
         wsc = pc.workspace(dev)
         with torch.cuda.stream(stream):
             enqueue(step_dev)
+            # the same samples' counts (the step's own are cleared by its evaluation)
+            cc = kde.kde_bin(X, w.lo, w.hi, w.M, stream=stream)
             Kc = kde.kde_kernel_grid(pc, w.n, workspace=wsc)
-            dc = kde.kde_fft_eval(pc, counts, Kc, workspace=wsc)
+            dc = kde.kde_fft_eval(pc, cc, Kc, workspace=wsc)
         torch.cuda.synchronize()
         line["vs_corrected"] = {
             "max_rel_diff": float((dens - dc).abs().max() / dc.abs().max()),

@@ -208,6 +208,20 @@ kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, const double* l
                    const double* hi, const int64_t* M, int64_t* counts, int64_t* n_outside,
                    void* workspace, size_t workspace_bytes, kde_stream_t stream);
 
+/* Linear binning added to existing counts (Sec. 2, first step; the binned
+ * counts of Eq. 7 are a sum over samples, so binning the samples in parts
+ * and adding gives the counts of all of them, bit for bit).  Arguments and
+ * rounding as kde_bin, except that counts is not overwritten: every sample
+ * inside the grid adds its 2^d weights to what counts holds, and the number
+ * of samples outside is added to *n_outside (not zeroed).  Both methods
+ * (workspace NULL or not) add; the tiled one touches only the tiles that
+ * receive samples.  Counts that start at zero (for example after
+ * kde_fft_eval_consume) give kde_bin's result. */
+kde_status kde_bin_accumulate(const void* X, int x_dtype, int64_t n, int d, const double* lo,
+                              const double* hi, const int64_t* M, int64_t* counts,
+                              int64_t* n_outside, void* workspace, size_t workspace_bytes,
+                              kde_stream_t stream);
+
 /* Scratch bytes the tiled binning method needs for n samples on grid M:
  * a 16-byte record for every tile a sample can touch (2^d of them at most,
  * so 16 2^d n bytes) plus per-tile tables.  KDE_ERR_UNSUPPORTED for grids
@@ -237,6 +251,17 @@ kde_status kde_kernel_grid(kde_plan plan, int64_t n, void* Kspec, void* workspac
  * it may be shared with kde_kernel_grid's when the calls are ordered. */
 kde_status kde_fft_eval(kde_plan plan, const int64_t* counts, const void* Kspec, void* density,
                         void* workspace, size_t workspace_bytes, kde_stream_t stream);
+
+/* kde_fft_eval (Eq. 10, Eq. 14), after which the counts are all zero, ready
+ * for the next kde_bin_accumulate: a stream of datasets on one grid then
+ * needs no separate zeroing before each binning.  The density is the same,
+ * bit for bit, as kde_fft_eval's.  FP32 plans on the two-phase engine clear
+ * the counts inside the evaluation's second pass, once the first pass (the
+ * only one that reads them) has finished; other plans clear them with one
+ * more operation at the end.  Arguments as kde_fft_eval; counts is
+ * written. */
+kde_status kde_fft_eval_consume(kde_plan plan, int64_t* counts, const void* Kspec, void* density,
+                                void* workspace, size_t workspace_bytes, kde_stream_t stream);
 
 /* Densities for many bandwidths on one binned grid (Eq. 10: the count
  * spectrum C = F(c) is computed once and reused, only the kernel spectrum K

@@ -526,7 +526,7 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, BinPar
                        int ntiles, const unsigned* __restrict__ tile_count,
                        const unsigned* __restrict__ block_off, uint4* __restrict__ items,
                        TiledMeta* __restrict__ meta, uint4* __restrict__ recs, unsigned rec_cap,
-                       unsigned long long* __restrict__ counts) {
+                       unsigned long long* __restrict__ counts, int add) {
   extern __shared__ unsigned next[];   // [ntiles]: next slot of this block per tile
   __shared__ unsigned warp_tot[32];
   __shared__ unsigned totals[2];
@@ -557,7 +557,8 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, BinPar
     i0 += it;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) meta->nitems = totals[1];
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  // (adding into existing counts: nothing to zero)
+  for (int t = blockIdx.x; t < ntiles && !add; t += gridDim.x) {
     if (__ldcg(tile_count + t) <= (unsigned)kItemRecords) continue;
     for (int j = threadIdx.x; j < kTileCells; j += blockDim.x) {
       const int64_t idx = tile_cell<T, D>(p, t, j);
@@ -583,7 +584,8 @@ kde_bin_scatter_kernel(const T* __restrict__ X, int64_t n, int64_t chunk, BinPar
 
 // Work items taken in turn from meta->cursor: the item's records
 // accumulated in shared memory, then every cell of its tile stored (added,
-// for split tiles; an empty tile's cells are stored as zeros directly).  A
+// for split tiles and when adding into existing counts; an empty tile's
+// cells are stored as zeros directly, or skipped when adding).  A
 // weight w <= 2^32 is added as its low 16 bits and its high part
 // w >> 16 <= 2^16 into two 32-bit sums per cell; an item holds at most
 // kItemRecords = 2^13 records and a record adds to a cell at most once, so
@@ -613,7 +615,7 @@ template <typename T, int D>
 __global__ void __launch_bounds__(kAccumThreads, 2)
 kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ items,
                      TiledMeta* __restrict__ meta, BinParams<T> p,
-                     unsigned long long* __restrict__ counts) {
+                     unsigned long long* __restrict__ counts, int add) {
   extern __shared__ __align__(16) unsigned acc_sm[];
   unsigned* lo = acc_sm;
   unsigned* hi = acc_sm + pad_alloc<D>();
@@ -639,6 +641,7 @@ kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ i
       ext[k] = min(Geo<D>::ext(k), p.ax[k].M - o);
     }
     const bool empty = item.y >= item.z;
+    if (empty && add) continue;   // nothing to add
     if (!empty) {
       for (int j = threadIdx.x; j < pad_alloc<D>() / 2; j += blockDim.x)
         reinterpret_cast<uint4*>(lo)[j] = make_uint4(0, 0, 0, 0);   // lo and hi
@@ -669,7 +672,7 @@ kde_bin_accum_kernel(const uint4* __restrict__ recs, const uint4* __restrict__ i
       }
       if (!in || !KDE_DCHECK(idx >= 0 && idx < p.cells, KDE_DBG_BIN_ACCUM)) continue;
       const unsigned long long v = empty ? 0ull : ((unsigned long long)hi[jp] << 16) + lo[jp];
-      if (item.w) {
+      if (item.w || add) {
         if (v) atomicAdd(counts + idx, v);
       } else {
         counts[idx] = v;
@@ -767,9 +770,9 @@ BinParams<T> make_params(int d, const double* lo, const double* hi, const int64_
 template <typename T>
 kde_status launch_direct(const T* X, int64_t n, int d, const double* lo, const double* hi,
                          const int64_t* M, unsigned long long* counts, int64_t cells,
-                         unsigned long long* n_out, cudaStream_t stream) {
+                         unsigned long long* n_out, cudaStream_t stream, bool zero) {
   cudaError_t e;
-  {
+  if (zero) {
     const int64_t want = (cells / 2 + 255) / 256;
     const int zb = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 8));
     kde::LaunchScope ls("kde_zero_counts_kernel", stream);
@@ -827,7 +830,7 @@ template <typename T, int D>
 kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double* hi,
                           const int64_t* M, unsigned long long* counts,
                           unsigned long long* n_out, const TiledLayout& t, char* ws,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, int add) {
   BinParams<T> p = make_params<T>(D, lo, hi, M, &t);
   unsigned* tile_count = (unsigned*)(ws + t.off_count);
   TiledMeta* meta = (TiledMeta*)(ws + t.off_meta);
@@ -853,7 +856,7 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
     kde::LaunchScope ls("kde_bin_scatter_kernel", stream);
     e = kde::launch_pdl(fn, t.blocks, kBinThreads, smem_t, stream, X, n, t.chunk, p, nt,
                         (const unsigned*)tile_count, (const unsigned*)block_off, items, meta, recs,
-                        (unsigned)t.max_records, counts);
+                        (unsigned)t.max_records, counts, add);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return kde::cuda_fail(e, "kde_bin_scatter_kernel");
   }
@@ -867,7 +870,7 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
     const int grid_a = (int)std::min<int64_t>(t.max_items, (int64_t)std::max(1, per_sm) * sms);
     kde::LaunchScope ls("kde_bin_accum_kernel", stream);
     e = kde::launch_pdl(fn, grid_a, kAccumThreads, smem, stream, (const uint4*)recs,
-                        (const uint4*)items, meta, p, counts);
+                        (const uint4*)items, meta, p, counts, add);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return kde::cuda_fail(e, "kde_bin_accum_kernel");
   }
@@ -877,11 +880,11 @@ kde_status launch_tiled_d(const T* X, int64_t n, const double* lo, const double*
 template <typename T>
 kde_status launch_tiled(const T* X, int64_t n, int d, const double* lo, const double* hi,
                         const int64_t* M, unsigned long long* counts, unsigned long long* n_out,
-                        const TiledLayout& t, char* ws, cudaStream_t stream) {
+                        const TiledLayout& t, char* ws, cudaStream_t stream, int add) {
   switch (d) {
-    case 1: return launch_tiled_d<T, 1>(X, n, lo, hi, M, counts, n_out, t, ws, stream);
-    case 2: return launch_tiled_d<T, 2>(X, n, lo, hi, M, counts, n_out, t, ws, stream);
-    default: return launch_tiled_d<T, 3>(X, n, lo, hi, M, counts, n_out, t, ws, stream);
+    case 1: return launch_tiled_d<T, 1>(X, n, lo, hi, M, counts, n_out, t, ws, stream, add);
+    case 2: return launch_tiled_d<T, 2>(X, n, lo, hi, M, counts, n_out, t, ws, stream, add);
+    default: return launch_tiled_d<T, 3>(X, n, lo, hi, M, counts, n_out, t, ws, stream, add);
   }
 }
 
@@ -929,10 +932,12 @@ extern "C" kde_status kde_bin_workspace_bytes(int64_t n, int d, const int64_t* M
   return KDE_OK;
 }
 
-extern "C" kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, const double* lo,
-                              const double* hi, const int64_t* M, int64_t* counts,
-                              int64_t* n_outside, void* workspace, size_t workspace_bytes,
-                              kde_stream_t stream) {
+namespace {
+// kde_bin (add = false: counts and *n_outside overwritten) and
+// kde_bin_accumulate (add = true: added to).
+kde_status bin_impl(const void* X, int x_dtype, int64_t n, int d, const double* lo, const double* hi,
+                    const int64_t* M, int64_t* counts, int64_t* n_outside, void* workspace,
+                    size_t workspace_bytes, kde_stream_t stream, bool add) {
   using kde::fail;
   int64_t cells = 0;
   kde_status st = check_bin_args(d, x_dtype, n, X, lo, hi, M, &cells);
@@ -941,14 +946,14 @@ extern "C" kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, cons
   cudaStream_t s = (cudaStream_t)stream;
   auto* c = reinterpret_cast<unsigned long long*>(counts);
   auto* no = reinterpret_cast<unsigned long long*>(n_outside);
-  if (n_outside) {
+  if (n_outside && !add) {
     cudaError_t e = cudaMemsetAsync(n_outside, 0, sizeof(int64_t), s);
     if (e != cudaSuccess) return kde::cuda_fail(e, "cudaMemsetAsync(n_outside)");
   }
   if (!workspace) {
     if (x_dtype == KDE_F32)
-      return launch_direct<float>((const float*)X, n, d, lo, hi, M, c, cells, no, s);
-    return launch_direct<double>((const double*)X, n, d, lo, hi, M, c, cells, no, s);
+      return launch_direct<float>((const float*)X, n, d, lo, hi, M, c, cells, no, s, !add);
+    return launch_direct<double>((const double*)X, n, d, lo, hi, M, c, cells, no, s, !add);
   }
   TiledLayout t{};
   if (!tiled_layout(n, d, M, &t))
@@ -956,9 +961,27 @@ extern "C" kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, cons
   if (cells >= (int64_t(1) << 32)) return fail(KDE_ERR_UNSUPPORTED, "tiled binning needs prod(M) < 2^32");
   if (workspace_bytes < t.total) return fail(KDE_ERR_WORKSPACE, "binning workspace too small");
   if (((uintptr_t)workspace & 255) != 0) return fail(KDE_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  if (n == 0 && add) return KDE_OK;
   if (x_dtype == KDE_F32)
-    return launch_tiled<float>((const float*)X, n, d, lo, hi, M, c, no, t, (char*)workspace, s);
-  return launch_tiled<double>((const double*)X, n, d, lo, hi, M, c, no, t, (char*)workspace, s);
+    return launch_tiled<float>((const float*)X, n, d, lo, hi, M, c, no, t, (char*)workspace, s, add);
+  return launch_tiled<double>((const double*)X, n, d, lo, hi, M, c, no, t, (char*)workspace, s, add);
+}
+}  // namespace
+
+extern "C" kde_status kde_bin(const void* X, int x_dtype, int64_t n, int d, const double* lo,
+                              const double* hi, const int64_t* M, int64_t* counts,
+                              int64_t* n_outside, void* workspace, size_t workspace_bytes,
+                              kde_stream_t stream) {
+  return bin_impl(X, x_dtype, n, d, lo, hi, M, counts, n_outside, workspace, workspace_bytes,
+                  stream, false);
+}
+
+extern "C" kde_status kde_bin_accumulate(const void* X, int x_dtype, int64_t n, int d,
+                                         const double* lo, const double* hi, const int64_t* M,
+                                         int64_t* counts, int64_t* n_outside, void* workspace,
+                                         size_t workspace_bytes, kde_stream_t stream) {
+  return bin_impl(X, x_dtype, n, d, lo, hi, M, counts, n_outside, workspace, workspace_bytes,
+                  stream, true);
 }
 
 KDE_DEBUG_READER(bin)

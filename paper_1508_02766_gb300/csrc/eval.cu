@@ -1988,6 +1988,31 @@ extern "C" kde_status kde_fft_eval(kde_plan plan, const int64_t* counts, const v
   return fft_eval_impl<double>(plan, counts, Kspec, density, workspace, st);
 }
 
+// kde_fft_eval, then the counts set to zero: inside the second pass of the
+// two-phase engine (the first pass is the only reader of the counts), else
+// by one more operation after the evaluation.
+extern "C" kde_status kde_fft_eval_consume(kde_plan plan, int64_t* counts, const void* Kspec,
+                                           void* density, void* workspace, size_t workspace_bytes,
+                                           kde_stream_t stream) {
+  if (!plan || !counts || !Kspec || !density) return fail(KDE_ERR_INVALID_ARG, "NULL argument");
+  kde_status s = check_ws(plan, workspace, workspace_bytes);
+  if (s != KDE_OK) return s;
+  if ((s = check_device(plan)) != KDE_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const kde_plan_info& I = plan->info;
+  if (I.precision == KDE_F32 && I.engine == KDE_ENGINE_TWO_PHASE)
+    return kde::fx_fft_eval(plan, reinterpret_cast<const long long*>(counts), (const float*)Kspec,
+                            (float*)density, workspace, st,
+                            reinterpret_cast<unsigned long long*>(counts));
+  s = I.precision == KDE_F32 ? fft_eval_impl<float>(plan, counts, Kspec, density, workspace, st)
+                             : fft_eval_impl<double>(plan, counts, Kspec, density, workspace, st);
+  if (s != KDE_OK) return s;
+  int64_t cells = 1;
+  for (int k = 0; k < I.d; ++k) cells *= I.M[k];
+  cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)cells * sizeof(int64_t), st);
+  return e == cudaSuccess ? KDE_OK : cuda_fail(e, "cudaMemsetAsync(counts)");
+}
+
 // ---------------------------------------------------------------------------
 // Densities for many bandwidths on one grid (Eq. 10: C = F(c) computed once,
 // K computed and applied per bandwidth).  KDE_F32 2-D plans with the

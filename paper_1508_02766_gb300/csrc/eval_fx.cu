@@ -185,11 +185,14 @@ template <int MODE>
 kde_status cols_pass(const kde_plan_s* plan, int k, const char* name, const float2* in,
                      float2* out, float* out_real, const float* K, int64_t S, int64_t O, int Nin,
                      int Nout, int Lw, cudaStream_t st, const Batch* bt = nullptr,
-                     float s_pre = 0.f, float s_post = 0.f) {
+                     float s_pre = 0.f, float s_post = 0.f, unsigned long long* clear = nullptr,
+                     int64_t clear_n = 0) {
   const kde_plan_info& I = plan->info;
   ColsArgs a{};
   a.s_pre = s_pre;
   a.s_post = s_post;
+  a.clear = clear;
+  a.clear_n = clear_n;
   if (bt) {  // slabs are bandwidths
     O = bt->nh;
     a.h_L0 = bt->L0;
@@ -303,22 +306,26 @@ kde_status fx_kernel_grid(kde_plan_s* plan, const KGen<float>& gen, void* Kspec,
                                  (int)I.L[0], st);
 }
 
-// Density from counts and the kernel spectrum, two-phase engine.
+// Density from counts and the kernel spectrum, two-phase engine.  With
+// clear (the counts), the second pass also sets the counts to zero once the
+// first has read them.
 kde_status fx_fft_eval(kde_plan_s* plan, const long long* counts, const float* Kspec,
-                       float* density, void* ws, cudaStream_t st) {
+                       float* density, void* ws, cudaStream_t st, unsigned long long* clear) {
   using namespace fx;
   const kde_plan_info& I = plan->info;
   const int d = I.d, dl = d - 1;
   float2* A = (float2*)ws;  // [M_0 .. M_{d-2}][Q]
   int64_t rows = 1;
   for (int k = 0; k < dl; ++k) rows *= I.M[k];
+  const int64_t cells = rows * I.M[dl];
   kde_status s;
   if (I.slab_passes) {  // d == 3: axes 2 and 1 slab by slab, axis 0 between
     float2* Bf = A + rows * I.Q;  // [M_0][P_1][Q]
     s = slab_pass(plan, true, counts, Bf, nullptr, st);
     if (s != KDE_OK) return s;
     s = cols_pass<COL_MID>(plan, 0, "kde_fx_cols_mid_kernel", Bf, Bf, nullptr, Kspec,
-                           I.P[1] * I.Q, 1, (int)I.M[0], (int)I.M[0], -1, st);
+                           I.P[1] * I.Q, 1, (int)I.M[0], (int)I.M[0], -1, st, nullptr, 0.f, 0.f,
+                           clear, clear ? cells : 0);
     if (s != KDE_OK) return s;
     return slab_pass(plan, false, nullptr, Bf, density, st);
   }
@@ -330,11 +337,13 @@ kde_status fx_fft_eval(kde_plan_s* plan, const long long* counts, const float* K
   if (s != KDE_OK) return s;
   if (d == 2) {
     s = cols_pass<COL_MID>(plan, 0, "kde_fx_cols_mid_kernel", A, A, nullptr, Kspec, I.Q, 1,
-                           (int)I.M[0], (int)I.M[0], -1, st);
+                           (int)I.M[0], (int)I.M[0], -1, st, nullptr, 0.f, 0.f, clear,
+                           clear ? cells : 0);
   } else {
     float2* Bf = A + rows * I.Q;  // [M_0][P_1][Q]
     s = cols_pass<COL_FWD>(plan, 1, "kde_fx_cols_fwd_kernel", A, Bf, nullptr, nullptr, I.Q, I.M[0],
-                           (int)I.M[1], (int)I.P[1], -1, st);
+                           (int)I.M[1], (int)I.P[1], -1, st, nullptr, 0.f, 0.f, clear,
+                           clear ? cells : 0);
     if (s != KDE_OK) return s;
     s = cols_pass<COL_MID>(plan, 0, "kde_fx_cols_mid_kernel", Bf, Bf, nullptr, Kspec,
                            I.P[1] * I.Q, 1, (int)I.M[0], (int)I.M[0], -1, st);

@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
       }
     }
   }
+  if (a.clear) clear_words(a.clear, a.clear_n);
 }
 
 }  // namespace fx

@@ -398,7 +398,25 @@ struct ColsArgs {
   int64_t slab_in, slab_out, slab_real, slab_K;
   const int* h_L0;
   float s_pre, s_post;  // COL_AUTO scales
+  // Optional: counts (clear_n words) that the pass before this one has
+  // consumed, set to zero by this pass's threads once their work is done.
+  unsigned long long* clear;
+  int64_t clear_n;
 };
+
+// Zeroes words [0, n) of c with every thread of the grid (16-byte stores
+// where c is aligned).  Called where every thread of the kernel arrives.
+__device__ __forceinline__ void clear_words(unsigned long long* c, int64_t n) {
+  const int64_t nthr = (int64_t)gridDim.x * gridDim.y * blockDim.x;
+  const int64_t tid = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+  if (((uintptr_t)c & 15) == 0) {
+    ulonglong2* c2 = reinterpret_cast<ulonglong2*>(c);
+    for (int64_t i = tid; i < n / 2; i += nthr) c2[i] = make_ulonglong2(0ull, 0ull);
+    if (tid == 0 && (n & 1)) c[n - 1] = 0ull;
+  } else {
+    for (int64_t i = tid; i < n; i += nthr) c[i] = 0ull;
+  }
+}
 
 // Per-slab view of the arguments (slab = blockIdx.y).
 __device__ __forceinline__ void cols_slab(ColsArgs& a) {
@@ -594,6 +612,7 @@ kde_fx_cols_kernel(ColsArgs a) {
       size_call<N1T, CLS>(a.ln.N1, [&](auto N) { cols_a_inv<decltype(N)::value, MODE, N2T>(a, fx_sm); });
     }
   }
+  if (a.clear) clear_words(a.clear, a.clear_n);
 }
 
 // Launch of the kernel for the split (N1, N2): the one compiled for it if it

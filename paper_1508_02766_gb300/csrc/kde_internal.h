@@ -63,7 +63,8 @@ struct KGen;
 kde_status fx_kernel_grid(kde_plan_s* plan, const KGen<float>& gen, void* Kspec, void* ws,
                           cudaStream_t st);
 kde_status fx_fft_eval(kde_plan_s* plan, const long long* counts, const float* Kspec,
-                       float* density, void* ws, cudaStream_t st);
+                       float* density, void* ws, cudaStream_t st,
+                       unsigned long long* clear = nullptr);
 kde_status fx_count_spectra(kde_plan_s* plan, const long long* counts, float2* A, cudaStream_t st);
 kde_status fx_autocorr(kde_plan_s* plan, const long long* counts, float* R, float2* A, float2* B,
                        int64_t nsets, cudaStream_t st);

@@ -74,7 +74,8 @@ EXPORTS = [
     "kde_batch_set_queue_order", "kde_debug_status", "kde_prepare2_batch",
     "kde_prepare2_batch_workspace_bytes", "kde_lscv_autocorr_cands_batch",
     "kde_lscv_autocorr_cands_batch_workspace_bytes", "kde_lscv_theta_select",
-    "kde_lscv_theta_select_workspace_bytes", "kde_mlp_status_copy",
+    "kde_lscv_theta_select_workspace_bytes", "kde_mlp_status_copy", "kde_bin_accumulate",
+    "kde_fft_eval_consume",
 ]
 FEAT_DIM = 1088
 
@@ -99,9 +100,11 @@ def lib():
     L.kde_plan_destroy.argtypes = [vp]
     L.kde_bin.argtypes = [vp, ctypes.c_int, i64, ctypes.c_int, dp, dp, i64p, vp, vp, vp,
                           ctypes.c_size_t, vp]
+    L.kde_bin_accumulate.argtypes = L.kde_bin.argtypes
     L.kde_bin_workspace_bytes.argtypes = [i64, ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_size_t)]
     L.kde_kernel_grid.argtypes = [vp, i64, vp, vp, ctypes.c_size_t, vp]
     L.kde_fft_eval.argtypes = [vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.kde_fft_eval_consume.argtypes = L.kde_fft_eval.argtypes
     L.kde_fft_eval_noalloc.argtypes = [vp, vp, vp, vp, vp]
     L.kde_power_spectrum.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp]
     L.kde_lscv.argtypes = [vp, i64, ctypes.c_int, dp, vp, vp, vp, vp, ctypes.c_size_t, vp]
@@ -189,7 +192,8 @@ def lib():
                  "kde_prepare2_batch", "kde_prepare2_batch_workspace_bytes",
                  "kde_lscv_autocorr_cands_batch",
                  "kde_lscv_autocorr_cands_batch_workspace_bytes", "kde_lscv_theta_select",
-                 "kde_lscv_theta_select_workspace_bytes", "kde_mlp_status_copy"):
+                 "kde_lscv_theta_select_workspace_bytes", "kde_mlp_status_copy",
+                 "kde_bin_accumulate", "kde_fft_eval_consume"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -339,13 +343,14 @@ def bin_workspace(n, d, M, device="cuda"):
 
 
 def kde_bin(X, lo, hi, M, counts=None, n_outside=None, workspace=None, method="auto",
-            stream=None):
+            stream=None, accumulate=False):
     """Linear binning into int64 counts (units 2^-32).  X: (n, d) float32/float64
     CUDA tensor, or a pinned host tensor that the kernels read in place.
     method "direct" (global atomics), "tiled" (sort by tile, shared-memory
     accumulation; uses a workspace, allocated here if not given) or "auto"
     (direct: the faster on every workload measured).  Both methods give
-    bit-identical counts."""
+    bit-identical counts.  accumulate=True adds to the given counts and
+    n_outside (kde_bin_accumulate) instead of overwriting them."""
     import torch
     if not (X.is_cuda or X.is_pinned()) or X.dim() != 2 or not X.is_contiguous():
         raise ValueError("X must be a contiguous (n, d) CUDA or pinned host tensor")
@@ -364,8 +369,11 @@ def kde_bin(X, lo, hi, M, counts=None, n_outside=None, workspace=None, method="a
         workspace = bin_workspace(n, d, M, dev)
     if method == "direct":
         workspace = None
+    if accumulate and counts is None:
+        raise ValueError("accumulate=True needs the counts to add to")
     wsb = 0 if workspace is None else workspace.numel() * workspace.element_size()
-    _check(lib().kde_bin(_ptr(X) if n else ctypes.c_void_p(0),
+    fn = lib().kde_bin_accumulate if accumulate else lib().kde_bin
+    _check(fn(_ptr(X) if n else ctypes.c_void_p(0),
                          F32 if X.dtype == torch.float32 else F64, n, d,
                          _darr(lo), _darr(hi), _iarr(M), _ptr(counts), _ptr(n_outside),
                          _ptr(workspace), wsb, _stream_ptr(stream)))
@@ -384,9 +392,12 @@ def kde_kernel_grid(plan: Plan, n, Kspec=None, workspace=None, stream=None):
     return Kspec
 
 
-def kde_fft_eval(plan: Plan, counts, Kspec, density=None, workspace=None, stream=None):
+def kde_fft_eval(plan: Plan, counts, Kspec, density=None, workspace=None, stream=None,
+                 consume=False):
     """Density on the grid: F^{-1}(F(c) K) cropped to M (Eq. 10, Eq. 14).
-    density may be a pinned host tensor, which the last pass writes in place."""
+    density may be a pinned host tensor, which the last pass writes in place.
+    consume=True (kde_fft_eval_consume) leaves the counts zeroed, ready for
+    the next kde_bin(..., accumulate=True)."""
     import torch
     if density is not None and not (density.is_cuda or density.is_pinned()):
         raise ValueError("density must be a CUDA or pinned host tensor")
@@ -394,9 +405,10 @@ def kde_fft_eval(plan: Plan, counts, Kspec, density=None, workspace=None, stream
         density = torch.empty(plan.M, dtype=plan.real_dtype(), device="cuda")
     if workspace is None:
         workspace = plan.workspace()
-    _check(lib().kde_fft_eval(plan.handle, _ptr(counts), _ptr(Kspec), _ptr(density),
-                              _ptr(workspace), workspace.numel() * workspace.element_size(),
-                              _stream_ptr(stream)))
+    fn = lib().kde_fft_eval_consume if consume else lib().kde_fft_eval
+    _check(fn(plan.handle, _ptr(counts), _ptr(Kspec), _ptr(density),
+              _ptr(workspace), workspace.numel() * workspace.element_size(),
+              _stream_ptr(stream)))
     return density
 
 
@@ -773,10 +785,15 @@ class PreparedPath:
     """bin, kernel grid and FFT evaluation on fixed buffers, with every C
     argument marshalled once.  ``bin()``, ``kernel_grid()`` and ``fft_eval()``
     enqueue one call each on their stream (kernel_grid may use its own
-    stream); ``__call__`` enqueues all three in order on one stream."""
+    stream); ``__call__`` enqueues all three in order on one stream.
+    counts_kept_zero=True: the counts start at zero (the caller zeroes them
+    once) and every step keeps them so: bin() adds (kde_bin_accumulate) and
+    fft_eval() leaves them zeroed (kde_fft_eval_consume), so no step zeroes
+    them before binning."""
 
     def __init__(self, plan: Plan, X, counts, Kspec, density, workspace, n=None,
-                 n_outside=None, bin_workspace=None, stream=None, kgen_stream=None):
+                 n_outside=None, bin_workspace=None, stream=None, kgen_stream=None,
+                 counts_kept_zero=False):
         import torch
         L = lib()
         self._L = L
@@ -794,15 +811,17 @@ class PreparedPath:
         self._kg = (plan.handle, int(nX if n is None else n), _ptr(Kspec), _ptr(workspace), wsb, sk)
         self._ev = (plan.handle, _ptr(counts), _ptr(Kspec), _ptr(density), _ptr(workspace), wsb, s)
         self._keep = (X, counts, Kspec, density, workspace, n_outside, bin_workspace)
+        self._bin_fn = L.kde_bin_accumulate if counts_kept_zero else L.kde_bin
+        self._ev_fn = L.kde_fft_eval_consume if counts_kept_zero else L.kde_fft_eval
 
     def bin(self):
-        _check(self._L.kde_bin(*self._bin))
+        _check(self._bin_fn(*self._bin))
 
     def kernel_grid(self):
         _check(self._L.kde_kernel_grid(*self._kg))
 
     def fft_eval(self):
-        _check(self._L.kde_fft_eval(*self._ev))
+        _check(self._ev_fn(*self._ev))
 
     def __call__(self):
         self.bin()
