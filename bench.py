@@ -910,8 +910,9 @@ def ragged_main(args):
     stream = torch.cuda.Stream(device=dev)
     X = torch.from_numpy(np.ascontiguousarray(np.concatenate([w.X for w in problems]))).to(dev)
     dens = torch.empty(bp.density_elems, dtype=torch.float32, device=dev)
-    # room for the longer paddings the tuner may choose
-    ws = torch.empty(2 * bp.workspace_bytes, dtype=torch.uint8, device=dev)
+    # room for the longer paddings the tuner may choose, and at least 256 MB
+    # so that the tuner can start each timed run with the caches cold
+    ws = torch.empty(max(2 * bp.workspace_bytes, 256 << 20), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     tuned_ms = bp.tune(X, dens, ws, reps=3, stream=stream)
     tuned_mode, tuned_shape = bp.mode(), bp.shape()

@@ -457,8 +457,11 @@ kde_status kde_batch_get_config(kde_batch_plan plan, int* pad_policy, int* radix
  *     persistent mode, every pair in the staged mode),
  * skipping settings whose workspace exceeds workspace_bytes, and keeps the
  * fastest in the plan (re-planning the problems); *best_ms (may be NULL)
- * receives its time.  Set-up, not part of an evaluation.  The padded lengths
- * change the plan's workspace size: query it again after tuning. */
+ * receives its time.  Each timed run starts with cold caches when the
+ * workspace is at least 64 MB: up to 256 MB of it (scratch) is overwritten
+ * before the run, outside its timing, so that the choice holds for batches
+ * that arrive with new data.  Set-up, not part of an evaluation.  The padded
+ * lengths change the plan's workspace size: query it again after tuning. */
 enum { KDE_BATCH_PAD_SMALLEST = 0, KDE_BATCH_PAD_FEWEST_STAGES = 1 };
 kde_status kde_batch_tune(kde_batch_plan plan, const void* X, void* density, void* workspace,
                           size_t workspace_bytes, kde_stream_t stream, int reps, float* best_ms);
