@@ -259,6 +259,20 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
   const int c = t & (W - 1), r = t >> a.lgB;
   const int64_t first = (int64_t)blockIdx.x * W * (MODE == COL_FWD_REAL ? 2 : 1);
   float2* line = fx_sm + c;
+  // COL_MID: the kernel spectrum values of this thread's phase C, loaded
+  // now so that their latency hides behind phases A and B
+  float kpre[MODE == COL_MID ? N3 : 1];
+  if constexpr (MODE == COL_MID) {
+    const int64_t s = first + c;
+    const bool v = s < a.S && r < N1 * N2;
+    const float* pk = a.K + s + (int64_t)(r % N1 + N1 * (r / N1)) * a.S;
+    const int64_t step = (int64_t)(N1 * N2) * a.S;
+#pragma unroll
+    for (int k3 = 0; k3 < N3; ++k3) {
+      kpre[k3] = v ? __ldg(pk) : 0.f;
+      pk += step;
+    }
+  }
   if constexpr (MODE == COL_INV) {
     if (r < N1 * N2) {  // phase C inverse from the input rows
       const int k1 = r % N1, k2 = r / N1;
@@ -352,16 +366,10 @@ __global__ void __launch_bounds__(kThreads3) kde_fx3_cols_kernel(ColsArgs a) {
             z[k3] = make_float2((re * re + im * im) * a.s_post, 0.f);
           }
         } else {
-          const int64_t s = first + c;
-          const bool v = s < a.S;
-          const float* pk = a.K + s + (int64_t)(k1 + N1 * k2) * a.S;
-          const int64_t step = (int64_t)(N1 * N2) * a.S;
 #pragma unroll
           for (int k3 = 0; k3 < N3; ++k3) {
-            const float kv = v ? __ldg(pk) : 0.f;
-            pk += step;
-            z[k3].x *= kv;
-            z[k3].y *= kv;
+            z[k3].x *= kpre[k3];
+            z[k3].y *= kpre[k3];
           }
         }
         p3_c_inv<N1, N2, N3>(z, k1, k2, a.tw, line, SK, W);
