@@ -126,3 +126,27 @@ def test_full_size_against_the_stockham_engine(K, name):
     d1, _, p1 = run(K, w, engine="stockham")
     assert p2.info.engine == "two_phase" and p1.info.engine == "stockham"
     assert rel_err(d2, d1) <= 1e-5
+
+
+@pytest.mark.parametrize("rows", [12, 3300])
+def test_three_factor_rows_few_and_many(K, rows):
+    """Long rows of a three-factor split (448 = 7 x 8 x 8), few (12) and many
+    (3300, two per line in 1650 lines), against Eq. 7 at sampled nodes
+    (every node of the small grid), within the FP32 1e-5."""
+    w = W.small_case(77, 2, (rows, 430), n=20000 if rows > 100 else 3000, precision="f32")
+    info = K.kde_plan_info_compute(w.M, w.lo, w.hi, w.H, precision="f32")
+    assert info.P[1] > 400   # a three-factor line
+    dens, counts, plan = run(K, w)
+    L = tuple(plan.info.L)
+    c = O.counts_to_c(counts.cpu().numpy())
+    k = O.kernel_weights(w.H, w.lo, w.hi, w.M, L, w.n)
+    rng = np.random.default_rng(3)
+    if rows * 430 <= 6000:
+        nodes = np.argwhere(np.ones(w.M, dtype=bool))
+    else:
+        nodes = np.stack([rng.integers(0, m, size=2500) for m in w.M], axis=1)
+        peak = np.array(np.unravel_index(int(np.argmax(dens)), w.M))
+        nodes = np.concatenate([nodes, peak[None, :]], axis=0)
+    ref = O.binned_direct_at(c, k, L, nodes)
+    got = dens[tuple(nodes.T)]
+    assert rel_err(got, ref) <= 1e-5
