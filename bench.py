@@ -42,6 +42,8 @@ def parse(argv=None):
                     help="one workload; default: kde2d_1024_f32 with a kde3d_256_f32 record")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--learned-batch", type=int, default=256,
+                    help="datasets per preparation, search and selection call (learned2d_256)")
     ap.add_argument("--e2e-graph-stages", type=int, default=2,
                     help="pipeline stages (datasets) captured per CUDA graph in the e2e stream")
     ap.add_argument("--bin-method", default="auto", choices=["auto", "direct", "tiled"])
@@ -1316,7 +1318,7 @@ def learned_main(args):
         B.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    n, chunk, Bsel = 10_000, 1024, 256
+    n, chunk, Bsel = 10_000, 1024, args.learned_batch
     n_train, n_eval = args.train_sets, args.eval_sets
     sc = Lm.LscvScorer(n)
     # labels: the plain search (every candidate) on every training dataset,
