@@ -62,3 +62,20 @@ def test_step_bytes_reports_unmodelled_kernels():
     total, missing = bench.step_bytes(alg, {"kde_bin_kernel": (1.0, 2), "mystery": (1.0, 2)}, 2)
     assert missing == ["mystery"]
     assert total == pytest.approx(w.n * 2 * 8 + 8 * int(np.prod(w.M)))
+
+
+@pytest.mark.parametrize("name", ["kde2d_1024_f32", "kde3d_256_f32"])
+def test_tiled_binning_counts_the_same_bytes_as_direct(name):
+    """The tiled binning's three kernels together count the samples read once
+    and the counts written once, like the direct kernel; zeroing counts
+    nothing."""
+    w, info = _info(name)
+    alg = bench.algorithmic_bytes(info, w.n, 4)
+    steps = 5
+    direct, _ = bench.step_bytes(alg, {"kde_bin_kernel": (1.0, steps),
+                                       "kde_zero_counts_kernel": (1.0, steps)}, steps)
+    tiled, missing = bench.step_bytes(
+        alg, {k: (1.0, steps) for k in ("kde_bin_count_kernel", "kde_bin_scatter_kernel",
+                                        "kde_bin_accum_kernel")}, steps)
+    assert missing == []
+    assert tiled == direct == w.n * info.d * 4 + 8 * int(np.prod(w.M))
