@@ -320,3 +320,37 @@ def test_direct_binning_after_producer_kernel_and_unaligned_counts(K):
         c_ref, _ = O.bin_linear(w.X, w.lo, w.hi, w.M)
         assert np.array_equal(counts.cpu().numpy(), c_ref)
         assert int(store[0].item()) == -3
+
+
+def test_binning_size_limits_are_refused_before_any_launch(K):
+    """The bounds under which the int64 counts in units of 2^-32 cannot
+    overflow (every cell below n 2^32 < 2^63 needs n < 2^31) and the grid
+    limits are checked on the host: each call below returns
+    KDE_ERR_INVALID_ARG (1) or KDE_ERR_UNSUPPORTED (7) and writes nothing
+    (the counts keep their marker value); the same call inside the bounds
+    then bins."""
+    import ctypes
+    L = K.lib()
+    X = torch.zeros((4, 3), dtype=torch.float32, device="cuda")
+    counts = torch.full((8,), 5, dtype=torch.int64, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call(fn, n, d, M, x=X):
+        return fn(ctypes.c_void_p(x.data_ptr()), K.F32, n, d, K._darr([0.0] * d), K._darr([1.0] * d),
+                  K._iarr(M), ctypes.c_void_p(counts.data_ptr()), ctypes.c_void_p(0),
+                  ctypes.c_void_p(0), 0, s)
+
+    for fn in (L.kde_bin, L.kde_bin_accumulate):
+        assert call(fn, 1 << 31, 2, (4, 2)) == 1          # n >= 2^31
+        assert call(fn, -1, 2, (4, 2)) == 1
+        assert call(fn, 4, 2, ((1 << 24) + 1, 2)) == 1    # M_k > 2^24
+        assert call(fn, 4, 3, (1 << 14, 1 << 14, 1 << 12)) == 1   # prod(M) >= 2^40
+        assert call(fn, 4, 2, (1, 8)) == 1                # M_k < 2
+        assert call(fn, 4, 4, (2, 2, 2, 2)) == 7          # d = 4
+    torch.cuda.synchronize()
+    assert torch.all(counts == 5)
+    # the same call with sizes inside the bounds runs: four samples at lo,
+    # all on node 0
+    assert call(L.kde_bin, 4, 2, (4, 2)) == 0
+    torch.cuda.synchronize()
+    assert int(counts[0].item()) == 4 << 32 and int(counts[1:].abs().sum().item()) == 0
